@@ -1,0 +1,423 @@
+"""Benchmark of the dedispersion + detection hot path on GB300.
+
+One step = one pass of the whole path over one synthetic filterbank block
+resident in HBM: dd_execute (brute-force dedispersion) then dd_detect
+(per-DM statistics, n-sigma threshold, candidate list, count to host).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is DM-trial*samples/s summed over ranks
+(each rank processes its own beam: weak scaling, no collective on the data
+path).  ``e2e`` repeats the metric through dd_process_host with pinned host
+buffers (host->device copy, dedispersion, detection, candidates back to the
+host).  ``roofline`` reports the dedispersion kernel against the add-pipe
+peak.  ``cpu_baseline`` times the CPU oracle on a bounded sample of the same
+workload on this machine's host cores.  ``--impl reference`` times only the
+oracle (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "DM-trial*samples/s"
+UNIT = "DM-trial*samples/s"
+NSIGMA = 6.0
+L2_FLUSH_BYTES = 256 << 20
+LANES_PER_SM = 128  # 32-bit add lanes per SM (4 partitions x 32)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="full_block_u8")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the bounded oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, flag in zip(names, parts[5:9]):
+                if flag.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ------------------------------------------------------------------ helpers
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def kernel_source_sha() -> str:
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1401_8258_gb300", "csrc", "dd_dedisp*.cu"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(workload: str) -> tuple[float | None, str | None]:
+    """DRAM bytes per dedispersion launch from the committed ncu summary, if
+    it was taken on the current kernel source (``source_sha`` line)."""
+    path = os.path.join(ROOT, "profiles", f"dedisperse_{workload}.md")
+    if not os.path.exists(path):
+        return None, None
+    text = open(path).read()
+    m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
+    m_s = re.search(r"source_sha:\s*([0-9a-f]+)", text)
+    if not (m_b and m_s) or m_s.group(1) != kernel_source_sha():
+        return None, os.path.relpath(path, ROOT)
+    return float(m_b.group(1)), os.path.relpath(path, ROOT)
+
+
+def geometry(wl):
+    from paper_1401_8258_gb300 import dd_compute_delays
+    delays, mx = dd_compute_delays(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    return delays, mx, wl.nsamp - mx
+
+
+# ----------------------------------------------------------- CPU baseline
+
+def time_oracle_sample(wl, block, delays, nsamp_out, target_s: float) -> dict:
+    """Oracle dedispersion + stats + detection on a DM subset sized for about
+    ``target_s`` seconds on all host cores; throughput scaled to the metric."""
+    import oracle
+    oracle.build()
+    ndm_total = wl.ndm
+    probe = max(1, min(ndm_total, 8))
+    idx = np.linspace(0, ndm_total - 1, probe).astype(int)
+    t0 = time.perf_counter()
+    D = oracle.dedisperse(block, delays[:, idx], nsamp_out=nsamp_out, nsamp_in=wl.nsamp)
+    m, s = oracle.stats(D)
+    oracle.detect(D, m, s, NSIGMA, capacity=0)
+    dt = time.perf_counter() - t0
+    per_dm = dt / probe
+    n = int(min(ndm_total, max(probe, target_s / max(per_dm, 1e-9))))
+    idx = np.linspace(0, ndm_total - 1, n).astype(int)
+    t0 = time.perf_counter()
+    D = oracle.dedisperse(block, delays[:, idx], nsamp_out=nsamp_out, nsamp_in=wl.nsamp)
+    m, s = oracle.stats(D)
+    oracle.detect(D, m, s, NSIGMA, capacity=0)
+    dt = time.perf_counter() - t0
+    return {"value": n * nsamp_out / dt, "unit": UNIT, "cores": oracle.max_threads(),
+            "kind": "oracle", "seconds": dt,
+            "sample": f"{n} of {ndm_total} DM trials (evenly spaced) x {nsamp_out} samples x "
+                      f"{wl.nchan} channels of the same block; dedispersion + stats + detection"}
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ------------------------------------------------------------- reference arm
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    wl = synth.workload(args.workload)
+    delays, mx, nsamp_out = geometry_oracle(wl)
+    block, _ = synth.make_block(wl, args.seed, delays)
+    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+    for _ in range(args.warmup):
+        time_oracle_sample(wl, block, delays, nsamp_out, min(per_step, 2.0))
+    vals, secs = [], 0.0
+    samples = []
+    for _ in range(args.steps):
+        r = time_oracle_sample(wl, block, delays, nsamp_out, per_step)
+        vals.append(r["value"])
+        secs += r["seconds"]
+        samples.append(r["sample"])
+    value = statistics.median(vals)
+    import oracle
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64" if wl.dtype == "u8" else "f64",
+        "data": "synthetic", "config": workload_config(wl, nsamp_out, args.gpus),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                         "kind": "oracle", "sample": samples[-1], "cpu_model": cpu_model()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def geometry_oracle(wl):
+    import oracle
+    oracle.build()
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    return delays, mx, wl.nsamp - mx
+
+
+def workload_config(wl, nsamp_out, n_gpus):
+    return {
+        "workload": wl.name, "nchan": wl.nchan, "nsamp_in": wl.nsamp, "nsamp_out": nsamp_out,
+        "ndm": wl.ndm, "dm_range": [float(wl.dms[0]), float(wl.dms[-1])],
+        "f_top_mhz": wl.f_top_mhz, "chan_width_mhz": wl.chan_width_mhz,
+        "t_samp_s": wl.t_samp_s, "input_dtype": wl.dtype, "nsigma": NSIGMA,
+        "beams_per_gpu": 1, "parallelism": f"replicas{n_gpus}",
+        "l2": "L2 flushed (256 MiB write) before every timed step",
+    }
+
+
+# ------------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1401_8258_gb300 as dd
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dd.build()
+
+    wl = synth.workload(args.workload)
+    plan = dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, wl.dtype, local)
+    delays = plan.delays()
+    nsamp_out = plan.nsamp_out(wl.nsamp)
+    block_np, pulses = synth.make_block(wl, args.seed + rank, delays)
+    block = torch.from_numpy(block_np).to(dev)
+    out = torch.empty((wl.ndm, nsamp_out), dtype=plan.out_torch_dtype, device=dev)
+    cap = 1 << 20
+    cands = torch.empty((cap, 16), dtype=torch.uint8, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        dd.dd_execute(plan.handle, block, wl.nsamp, block.stride(0), out, stream)
+        ev_mid.record(stream)
+        st, total = dd.dd_detect(plan.handle, out, nsamp_out, NSIGMA, cands, cap, stream)
+        return total
+
+    ev_mid = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = plan.launch_count()
+    totals = []
+    for i in range(args.steps):
+        flush.fill_(1.0)
+        starts[i].record(stream)
+        ev_mid = mids[i]
+        totals.append(step())
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = plan.launch_count() - launches0
+    clock = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    kern_ms = [s.elapsed_time(m) for s, m in zip(starts, mids)]
+    t_total = sum(step_ms) / 1e3
+    t_kernel = sum(kern_ms) / len(kern_ms) / 1e3
+    if world > 1:
+        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    units_per_step = wl.ndm * nsamp_out
+    value = world * units_per_step * args.steps / t_total
+
+    # end to end through the C ABI on pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        host_block = torch.from_numpy(block_np).pin_memory()
+        host_cands = torch.empty((cap, 16), dtype=torch.uint8).pin_memory()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        counts = []
+        for _ in range(max(1, args.warmup)):
+            dd.dd_process_host(plan.handle, host_block, wl.nsamp, wl.nsamp, NSIGMA, host_cands,
+                               cap, stream)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            st, total = dd.dd_process_host(plan.handle, host_block, wl.nsamp, wl.nsamp, NSIGMA,
+                                           host_cands, cap, stream)
+            counts.append(total)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = ev0.elapsed_time(ev1) / 1e3
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * units_per_step * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(block_np.nbytes),
+               "d2h_bytes_per_step": int(8 + 16 * statistics.mean(min(c, cap) for c in counts))}
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        plan.close()
+        return
+
+    # roofline of the dedispersion kernel (plain 32-bit add pipes)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    adds = float(wl.ndm) * nsamp_out * wl.nchan
+    achieved = adds / t_kernel / 1e12
+    peak = sms * LANES_PER_SM * smax * 1e6 / 1e12
+    probes = {}
+    for kind in ("fadd", "fadd2", "iadd", "iadd3", "imad", "lop3", "prmt", "prmt_iadd",
+                 "lop3_iadd", "fadd_f16", "hadd2"):
+        try:
+            ops, per_clk = dd._native.dd_measure_add_peak(kind, local)
+            probes[kind] = {"Tops_per_s": ops / 1e12, "ops_per_clk_per_sm": per_clk}
+        except Exception as e:  # probe failure must not hide the bench line
+            probes[kind] = {"error": str(e)}
+    traffic, prof = recorded_traffic(wl.name)
+    algo_bytes = block_np.nbytes + wl.ndm * nsamp_out * 4
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+            "frac": achieved / peak, "traffic": traffic,
+            "kernel": "dd_dedisperse", "kernel_ms": t_kernel * 1e3,
+            "peak_basis": f"{sms} SMs x {LANES_PER_SM} add lanes x {smax:.0f} MHz (max clock)",
+            "frac_at_observed_clock": (achieved / (sms * LANES_PER_SM * clock["sm_mhz"] * 1e6 / 1e12)
+                                       if clock.get("sm_mhz") else None),
+            "algorithmic_bytes": algo_bytes,
+            "hbm_frac_of_measured": (algo_bytes / t_kernel / 1e9) / float(peaks.get("hbm_gbs", 6784.5)),
+            "traffic_source": prof, "add_pipe_probes": probes}
+
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu = time_oracle_sample(wl, block_np, delays, nsamp_out, args.cpu_seconds)
+        cpu["cpu_model"] = cpu_model()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32" if wl.dtype == "u8" else "f32", "data": "synthetic",
+        "config": workload_config(wl, nsamp_out, world),
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
+        "gpu_launches": int(launches),
+        "candidates_per_step": int(statistics.median(totals)),
+        "step_ms_median": statistics.median(step_ms),
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    plan.close()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,169 @@
+/*
+ * dd.h -- C ABI of libdd: brute-force incoherent dedispersion of a
+ * channelised filterbank block, per-DM-trial normalisation and n-sigma
+ * candidate extraction on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (A. Magro, "A Real-Time, GPU-Based, Non-Imaging Back-End for Radio
+ * Telescopes", 2013):
+ *   D[d][t] = sum_{c=0}^{nchan-1} I[c][t + delay(c,d)]        (Sec. 2.1.1, brute-force equation)
+ *   delay(c,d) = round(DM_d * dT(c)),
+ *   dT(c) = K * ((f_top - c*df)^-2 - f_top^-2) / t_samp       (Sec. 2.1.1, deltaT equation)
+ *   K = 4.148808e3 MHz^2 pc^-1 cm^3 s                          (Sec. 1.3, dispersion constant)
+ *   valid output length nsamp_out = nsamp_in - maxshift        (Sec. 3.4, maxshift overlap)
+ *   per-DM mean and rms, snr = (D - mean)/rms                  (Sec. 3.5, normalisation)
+ *   candidates = (DM, time, intensity) with snr > nsigma       (Sec. 3.6, thresholding)
+ *
+ * Conventions fixed by this library where the text is silent:
+ *   - channel c has centre frequency f_top - c*df (df > 0), so channel 0 is
+ *     the band top and has delay 0;
+ *   - round() is round half away from zero; dT(c) and DM_d*dT(c) are formed
+ *     in IEEE double, left to right, with no fused multiply-add;
+ *   - rms is the population standard deviation (1/N) about the mean of the
+ *     row, no detrending; the threshold is strict (snr > nsigma); rows with
+ *     rms == 0 yield no candidates; candidates are ordered by (dm_idx, t).
+ *
+ * Layouts:
+ *   block  [nchan][pitch] elements, time fastest (channel 0 = band top);
+ *          elements u8 (DD_U8), IEEE binary16 bits (DD_F16) or f32 (DD_F32).
+ *   out    [ndm][nsamp_out], dense rows; int32 for DD_U8 input (exact sums),
+ *          f32 for DD_F16 / DD_F32 input (f32 accumulation).
+ *   delays [nchan][ndm] int32 (channel-major: one channel's DM trials are
+ *          contiguous).
+ *
+ * Errors: every entry point returns DD_OK (0) or a negative dd_status; none
+ * throws, aborts or exits.  Argument errors are detected synchronously before
+ * anything is queued.  Device-side faults caught by the kernels themselves
+ * (bounded waits that ran out) are recorded in the plan and reported by the
+ * next synchronising call (dd_detect, dd_sync, dd_process_host).
+ *
+ * Threads and streams: a plan may be used by one host thread at a time; work
+ * queued with one plan on different streams must not overlap in time
+ * (the plan's workspace is shared).  Use one plan per concurrent beam.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum { DD_U8 = 0, DD_F16 = 1, DD_F32 = 2 } dd_dtype;
+
+typedef enum {
+  DD_OK = 0,
+  DD_ERR_ARG = -1,            /* invalid argument (null pointer, bad geometry, non-finite DM) */
+  DD_ERR_SIZE = -2,           /* size out of range (nsamp_in <= maxshift, pitch < nsamp_in, ...) */
+  DD_ERR_DTYPE = -3,          /* unknown input dtype */
+  DD_ERR_CUDA = -4,           /* a CUDA runtime call failed */
+  DD_ERR_OOM = -5,            /* device or host allocation failed */
+  DD_ERR_OVERFLOW = -6,       /* more candidates than capacity; the first capacity are written */
+  DD_ERR_DEVICE_TIMEOUT = -7, /* a bounded device wait ran out; results of that launch are invalid */
+  DD_ERR_RANGE = -8           /* a delay does not fit in int32, or a sum may overflow int32 */
+} dd_status;
+
+/* One detection: DM trial index, output sample (arrival sample at f_top,
+ * relative to the block), dedispersed value D[dm_idx][t] and its snr. */
+typedef struct {
+  int32_t dm_idx;
+  int32_t t;
+  float value;
+  float snr;
+} dd_candidate;
+
+typedef struct dd_plan dd_plan; /* opaque; owns the device delay table and workspace */
+
+/* Host-only delay table, Sec. 2.1.1 deltaT equation, with the conventions
+ * above.  delays_out: host int32 [nchan][ndm] (caller-owned); maxshift_out:
+ * largest delay.  Needs no GPU.  DD_ERR_ARG for nchan < 1, ndm < 1, df <= 0,
+ * t_samp <= 0, a band whose bottom channel frequency is <= 0, or a DM that is
+ * negative or not finite; DD_ERR_RANGE if a delay exceeds INT32_MAX. */
+int dd_compute_delays(int32_t nchan, double f_top_mhz, double chan_width_mhz,
+                      double t_samp_s, const double *dm_list, int32_t ndm,
+                      int32_t *delays_out, int32_t *maxshift_out);
+
+/* Create a plan on CUDA device `device` for blocks of `nchan` channels of
+ * in_dtype samples and the DM trials dm_list[0..ndm) (host array, copied).
+ * Computes the delay table (dd_compute_delays) and uploads it once
+ * (Sec. 3.4: delays are computed once at start-up and stored channel/DM
+ * order).  *out receives the plan, or NULL on error. */
+int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz, double chan_width_mhz,
+                   double t_samp_s, const double *dm_list, int32_t ndm, int32_t in_dtype,
+                   int32_t device);
+
+/* Free the plan and all device memory it owns.  NULL-safe.  Synchronises the
+ * plan's device first. */
+int dd_plan_destroy(dd_plan *p);
+
+/* Largest delay of the plan (maxshift, Sec. 3.4). */
+int dd_plan_max_delay(const dd_plan *p, int32_t *maxshift);
+
+/* Valid output length nsamp_in - maxshift (Sec. 3.4); DD_ERR_SIZE if
+ * nsamp_in <= maxshift. */
+int dd_plan_nsamp_out(const dd_plan *p, int64_t nsamp_in, int64_t *nsamp_out);
+
+/* Copy the plan's delay table to host_out, int32 [nchan][ndm]. */
+int dd_plan_delays(const dd_plan *p, int32_t *host_out);
+
+/* Dedisperse one block (Sec. 2.1.1) on `stream` (a cudaStream_t; NULL = the
+ * legacy default stream).
+ *   block: device pointer, [nchan][pitch_elems] elements of the plan's dtype,
+ *          of which the first nsamp_in of each row are read;
+ *   out:   device pointer, [ndm][nsamp_out] with nsamp_out = nsamp_in - maxshift,
+ *          int32 (DD_U8) or float (DD_F16, DD_F32); every element is written.
+ * Asynchronous: returns once the kernel is queued.  Caller owns block and out
+ * and must keep them alive until the stream reaches this work.  For DD_U8,
+ * DD_ERR_RANGE if nchan * 255 could overflow int32.  Any 16-byte-aligned
+ * block with a pitch of a whole number of 16-byte units takes the staged
+ * (bulk-copy) kernel; other layouts take a plain-load kernel with identical
+ * results. */
+int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
+               void *out, void *stream);
+
+/* Normalise and threshold a dedispersed block (Sec. 3.5, 3.6) on `stream`.
+ *   out:   device pointer to [ndm][nsamp_out] as written by dd_execute;
+ *   cands: device pointer to `capacity` dd_candidate slots (may be NULL when
+ *          capacity == 0); filled in (dm_idx, t) order;
+ *   count: host pointer; receives the total number of candidates found, even
+ *          if it exceeds capacity.
+ * Per-DM mean and rms: for DD_U8 plans from exact integer sums S1, S2 and
+ * the finaliser mean = S1/N, rms = sqrt((double)(N*S2 - S1^2))/N (128-bit
+ * exact numerator, round-to-nearest conversion); for float plans from double
+ * sums about a per-row shift.  snr = ((double)D - mean)/rms in IEEE double.
+ * Synchronises `stream` once (to return *count).  Returns DD_ERR_OVERFLOW if
+ * *count > capacity (the first `capacity` candidates are still written), or
+ * DD_ERR_DEVICE_TIMEOUT if an earlier launch on this plan reported one. */
+int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma, dd_candidate *cands,
+              int64_t capacity, int64_t *count, void *stream);
+
+/* Host copies of the per-DM mean and rms computed by the last dd_detect on
+ * this plan (double[ndm] each; either pointer may be NULL). */
+int dd_get_stats(const dd_plan *p, double *mean, double *sigma);
+
+/* Synchronise `stream` and return the plan's sticky device status
+ * (DD_OK or DD_ERR_DEVICE_TIMEOUT), clearing it. */
+int dd_sync(dd_plan *p, void *stream);
+
+/* Whole path on host buffers: copy `host_block` ([nchan][pitch_elems],
+ * host memory, pinned for full speed) to plan-owned device memory, dedisperse
+ * (dd_execute), detect (dd_detect) and copy the candidates back to
+ * `host_cands` (host, `capacity` slots).  *count as for dd_detect.  The plan
+ * grows its device buffers on first use for a given nsamp_in / pitch and keeps
+ * them until destroyed.  Synchronises `stream` before returning. */
+int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp_in, int64_t pitch_elems,
+                    float nsigma, dd_candidate *host_cands, int64_t capacity, int64_t *count,
+                    void *stream);
+
+/* Number of kernel launches queued by this plan since creation (all entry
+ * points); used to account for device work. */
+int dd_plan_launch_count(const dd_plan *p, int64_t *launches);
+
+/* Static description of a status code. */
+const char *dd_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

@@ -1,0 +1,112 @@
+"""GB300-native brute-force incoherent dedispersion and n-sigma detection.
+
+The compute path lives in ``libdd.so`` (hand-written CUDA for sm_103a behind
+the C ABI of ``include/dd.h``).  This package is the thin Python side:
+
+* :mod:`._native` -- one ctypes function per C entry point (same names);
+* :class:`Plan`   -- a small owner of a plan handle that passes torch device
+  tensors and streams to those functions (PyTorch supplies memory and
+  streams only).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _native
+from ._native import (CANDIDATE_DTYPE, DD_ERR_OVERFLOW, DD_F16, DD_F32, DD_OK, DD_U8, DTYPE_CODES,
+                      DDError, dd_compute_delays, dd_detect, dd_execute, dd_get_stats,
+                      dd_plan_create, dd_plan_delays, dd_plan_destroy, dd_plan_launch_count,
+                      dd_plan_max_delay, dd_plan_nsamp_out, dd_process_host, dd_status_string,
+                      dd_sync)
+from .build import build
+
+__all__ = [
+    "Plan", "build", "DDError", "CANDIDATE_DTYPE", "DD_U8", "DD_F16", "DD_F32", "DD_OK",
+    "DD_ERR_OVERFLOW", "DTYPE_CODES", "dd_compute_delays", "dd_plan_create", "dd_plan_destroy",
+    "dd_plan_max_delay", "dd_plan_nsamp_out", "dd_plan_delays", "dd_execute", "dd_detect",
+    "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
+]
+
+_TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
+
+
+class Plan:
+    """A dedispersion plan on one CUDA device (wraps ``dd_plan``)."""
+
+    def __init__(self, nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype="u8", device=0):
+        self.nchan = int(nchan)
+        self.dms = np.ascontiguousarray(dms, dtype=np.float64)
+        self.ndm = int(self.dms.size)
+        self.dtype = dtype
+        self.device = int(device)
+        self.handle = dd_plan_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, self.dms, dtype,
+                                     device)
+        self.maxshift = dd_plan_max_delay(self.handle)
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            dd_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def delays(self) -> np.ndarray:
+        return dd_plan_delays(self.handle, self.nchan, self.ndm)
+
+    def nsamp_out(self, nsamp_in: int) -> int:
+        return dd_plan_nsamp_out(self.handle, nsamp_in)
+
+    @property
+    def out_torch_dtype(self):
+        import torch
+        return torch.int32 if self.dtype == "u8" else torch.float32
+
+    def execute(self, block, out=None, nsamp_in=None, stream=None):
+        """Dedisperse a device tensor ``block[nchan][pitch]`` into ``out``.
+
+        f16 blocks may be passed as ``torch.float16`` tensors.  Returns ``out``
+        (allocated on the block's device when not given).
+        """
+        import torch
+        if block.dim() != 2 or block.stride(1) != 1 or block.shape[0] != self.nchan:
+            raise ValueError("block must be [nchan][pitch] with unit time stride")
+        if str(block.dtype).split(".")[-1] != _TORCH_IN[self.dtype]:
+            raise TypeError(f"block dtype {block.dtype} does not match plan dtype {self.dtype}")
+        nsamp_in = block.shape[1] if nsamp_in is None else int(nsamp_in)
+        n_out = self.nsamp_out(nsamp_in)
+        if out is None:
+            out = torch.empty((self.ndm, n_out), dtype=self.out_torch_dtype, device=block.device)
+        dd_execute(self.handle, block, nsamp_in, block.stride(0), out, stream)
+        return out
+
+    def detect(self, out, nsigma, cands=None, capacity=None, stream=None):
+        """Threshold ``out``; returns ``(candidates numpy array, total)``."""
+        import torch
+        n_out = out.shape[1]
+        if cands is None:
+            capacity = 1 << 16 if capacity is None else int(capacity)
+            cands = torch.empty((max(capacity, 1), 16), dtype=torch.uint8, device=out.device)
+        else:
+            capacity = cands.numel() * cands.element_size() // 16 if capacity is None else capacity
+        st, total = dd_detect(self.handle, out, n_out, nsigma, cands if capacity else None,
+                              capacity, stream)
+        k = min(total, capacity)
+        host = cands[:k].cpu().numpy().view(CANDIDATE_DTYPE).reshape(-1) if k else \
+            np.zeros(0, dtype=CANDIDATE_DTYPE)
+        return host, total
+
+    def stats(self):
+        return dd_get_stats(self.handle, self.ndm)
+
+    def launch_count(self) -> int:
+        return dd_plan_launch_count(self.handle)

@@ -1,0 +1,212 @@
+"""ctypes binding of ``libdd.so`` (declared in ``include/dd.h``).
+
+One Python function per C entry point, with the same name; each only
+marshals arguments (pointers, sizes, stream handles) and turns a negative
+status into :class:`DDError`.  No arithmetic of the method happens here: every
+step runs in the library's CUDA kernels, and loading fails loudly when the
+library has not been built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+DD_U8, DD_F16, DD_F32 = 0, 1, 2
+DTYPE_CODES = {"u8": DD_U8, "f16": DD_F16, "f32": DD_F32}
+
+DD_OK = 0
+DD_ERR_ARG = -1
+DD_ERR_SIZE = -2
+DD_ERR_DTYPE = -3
+DD_ERR_CUDA = -4
+DD_ERR_OOM = -5
+DD_ERR_OVERFLOW = -6
+DD_ERR_DEVICE_TIMEOUT = -7
+DD_ERR_RANGE = -8
+
+CANDIDATE_DTYPE = np.dtype(
+    [("dm_idx", np.int32), ("t", np.int32), ("value", np.float32), ("snr", np.float32)]
+)
+
+
+class DDError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {dd_status_string(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+# (name, restype, argtypes) for every entry point in dd.h
+_i32, _i64, _f32, _f64, _vp = (ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double,
+                               ctypes.c_void_p)
+SIGNATURES = [
+    ("dd_compute_delays", ctypes.c_int, [_i32, _f64, _f64, _f64, _vp, _i32, _vp, _vp]),
+    ("dd_plan_create", ctypes.c_int, [_vp, _i32, _f64, _f64, _f64, _vp, _i32, _i32, _i32]),
+    ("dd_plan_destroy", ctypes.c_int, [_vp]),
+    ("dd_plan_max_delay", ctypes.c_int, [_vp, _vp]),
+    ("dd_plan_nsamp_out", ctypes.c_int, [_vp, _i64, _vp]),
+    ("dd_plan_delays", ctypes.c_int, [_vp, _vp]),
+    ("dd_execute", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp]),
+    ("dd_detect", ctypes.c_int, [_vp, _vp, _i64, _f32, _vp, _i64, _vp, _vp]),
+    ("dd_get_stats", ctypes.c_int, [_vp, _vp, _vp]),
+    ("dd_sync", ctypes.c_int, [_vp, _vp]),
+    ("dd_process_host", ctypes.c_int, [_vp, _vp, _i64, _i64, _f32, _vp, _i64, _vp, _vp]),
+    ("dd_plan_launch_count", ctypes.c_int, [_vp, _vp]),
+    ("dd_status_string", ctypes.c_char_p, [ctypes.c_int]),
+    ("dd_measure_add_peak", ctypes.c_int, [_i32, _i32, _vp, _vp]),
+]
+
+PEAK_KINDS = {"fadd": 0, "fadd2": 1, "iadd": 2, "iadd3": 3, "imad": 4, "lop3": 5, "prmt": 6,
+              "hadd2": 7, "fadd_f16": 8, "prmt_iadd": 9, "lop3_iadd": 10}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load ``libdd.so``; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = library_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libdd.so is not built ({path}); run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(status: int, what: str, allow=()) -> int:
+    if status < 0 and status not in allow:
+        raise DDError(status, what)
+    return status
+
+
+def _addr(x) -> int | None:
+    """Device or host address of a torch tensor / numpy array / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream  # torch.cuda.Stream
+
+
+def dd_status_string(status: int) -> str:
+    return load().dd_status_string(int(status)).decode()
+
+
+def dd_compute_delays(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms):
+    dms = np.ascontiguousarray(dms, dtype=np.float64)
+    out = np.empty((nchan, dms.size), dtype=np.int32)
+    mx = ctypes.c_int32(0)
+    _check(load().dd_compute_delays(int(nchan), float(f_top_mhz), float(chan_width_mhz),
+                                    float(t_samp_s), dms.ctypes.data, int(dms.size),
+                                    out.ctypes.data, ctypes.addressof(mx)), "dd_compute_delays")
+    return out, int(mx.value)
+
+
+def dd_plan_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype, device=0):
+    dms = np.ascontiguousarray(dms, dtype=np.float64)
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    handle = ctypes.c_void_p()
+    _check(load().dd_plan_create(ctypes.addressof(handle), int(nchan), float(f_top_mhz),
+                                 float(chan_width_mhz), float(t_samp_s), dms.ctypes.data,
+                                 int(dms.size), code, int(device)), "dd_plan_create")
+    return handle.value
+
+
+def dd_plan_destroy(plan) -> None:
+    _check(load().dd_plan_destroy(plan), "dd_plan_destroy")
+
+
+def dd_plan_max_delay(plan) -> int:
+    v = ctypes.c_int32(0)
+    _check(load().dd_plan_max_delay(plan, ctypes.addressof(v)), "dd_plan_max_delay")
+    return int(v.value)
+
+
+def dd_plan_nsamp_out(plan, nsamp_in) -> int:
+    v = ctypes.c_int64(0)
+    _check(load().dd_plan_nsamp_out(plan, int(nsamp_in), ctypes.addressof(v)), "dd_plan_nsamp_out")
+    return int(v.value)
+
+
+def dd_plan_delays(plan, nchan, ndm) -> np.ndarray:
+    out = np.empty((nchan, ndm), dtype=np.int32)
+    _check(load().dd_plan_delays(plan, out.ctypes.data), "dd_plan_delays")
+    return out
+
+
+def dd_plan_launch_count(plan) -> int:
+    v = ctypes.c_int64(0)
+    _check(load().dd_plan_launch_count(plan, ctypes.addressof(v)), "dd_plan_launch_count")
+    return int(v.value)
+
+
+def dd_execute(plan, block, nsamp_in, pitch_elems, out, stream=None) -> None:
+    _check(load().dd_execute(plan, _addr(block), int(nsamp_in), int(pitch_elems), _addr(out),
+                             _stream(stream)), "dd_execute")
+
+
+def dd_detect(plan, out, nsamp_out, nsigma, cands, capacity, stream=None) -> tuple[int, int]:
+    """Returns ``(status, count)``; status is DD_OK or DD_ERR_OVERFLOW."""
+    cnt = ctypes.c_int64(0)
+    st = load().dd_detect(plan, _addr(out), int(nsamp_out), float(nsigma), _addr(cands),
+                          int(capacity), ctypes.addressof(cnt), _stream(stream))
+    _check(st, "dd_detect", allow=(DD_ERR_OVERFLOW,))
+    return st, int(cnt.value)
+
+
+def dd_get_stats(plan, ndm) -> tuple[np.ndarray, np.ndarray]:
+    mean = np.empty(ndm, dtype=np.float64)
+    sigma = np.empty(ndm, dtype=np.float64)
+    _check(load().dd_get_stats(plan, mean.ctypes.data, sigma.ctypes.data), "dd_get_stats")
+    return mean, sigma
+
+
+def dd_sync(plan, stream=None) -> None:
+    _check(load().dd_sync(plan, _stream(stream)), "dd_sync")
+
+
+def dd_process_host(plan, host_block, nsamp_in, pitch_elems, nsigma, host_cands, capacity,
+                    stream=None) -> tuple[int, int]:
+    cnt = ctypes.c_int64(0)
+    st = load().dd_process_host(plan, _addr(host_block), int(nsamp_in), int(pitch_elems),
+                                float(nsigma), _addr(host_cands), int(capacity),
+                                ctypes.addressof(cnt), _stream(stream))
+    _check(st, "dd_process_host", allow=(DD_ERR_OVERFLOW,))
+    return st, int(cnt.value)
+
+
+def dd_measure_add_peak(kind, device=0) -> tuple[float, float]:
+    """(ops/s, ops per clock per SM) of one add-pipe instruction form."""
+    code = PEAK_KINDS[kind] if isinstance(kind, str) else int(kind)
+    a, b = ctypes.c_double(0), ctypes.c_double(0)
+    _check(load().dd_measure_add_peak(code, int(device), ctypes.addressof(a), ctypes.addressof(b)),
+           "dd_measure_add_peak")
+    return a.value, b.value

@@ -1,0 +1,308 @@
+// dd_api.cu -- the extern "C" entry points of libdd (declared in dd.h):
+// plan life cycle, argument validation, kernel dispatch and the host-buffer
+// path.  Every entry point returns a dd_status and restores the caller's
+// current CUDA device.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <new>
+
+#include "dd.h"
+#include "dd_internal.h"
+
+namespace {
+
+// Makes the plan's device current for the scope of one call.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int device) {
+    ok_ = cudaGetDevice(&prev_) == cudaSuccess;
+    if (ok_ && prev_ != device) ok_ = cudaSetDevice(device) == cudaSuccess;
+    switched_ = ok_ && prev_ != device;
+  }
+  ~DeviceScope() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = 0;
+  bool ok_ = false;
+  bool switched_ = false;
+};
+
+int cuda_status(cudaError_t e) {
+  if (e == cudaSuccess) return DD_OK;
+  return e == cudaErrorMemoryAllocation ? DD_ERR_OOM : DD_ERR_CUDA;
+}
+
+template <typename T>
+void free_device(T *&ptr) {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+}
+
+// Grows the per-(row, chunk) detection workspace to hold `entries`.
+int ensure_chunk_workspace(dd_plan *p, size_t entries) {
+  if (entries <= p->chunk_cap) return DD_OK;
+  free_device(p->d_counts);
+  free_device(p->d_offsets);
+  p->chunk_cap = 0;
+  if (cudaMalloc(&p->d_counts, entries * sizeof(int64_t)) != cudaSuccess ||
+      cudaMalloc(&p->d_offsets, entries * sizeof(int64_t)) != cudaSuccess) {
+    free_device(p->d_counts);
+    free_device(p->d_offsets);
+    return DD_ERR_OOM;
+  }
+  p->chunk_cap = entries;
+  return DD_OK;
+}
+
+// Reads and clears the sticky device status word (caller has synchronised).
+int take_device_status(dd_plan *p) {
+  int32_t flag = 0;
+  if (cudaMemcpy(&flag, p->d_error, sizeof(flag), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DD_ERR_CUDA;
+  if (flag == 0) return DD_OK;
+  cudaMemset(p->d_error, 0, sizeof(int32_t));
+  return DD_ERR_DEVICE_TIMEOUT;
+}
+
+void destroy_plan(dd_plan *p) {
+  if (!p) return;
+  free_device(p->d_delays);
+  free_device(p->d_error);
+  free_device(p->d_stats);
+  free_device(p->d_counts);
+  free_device(p->d_offsets);
+  free_device(p->d_total);
+  free_device(p->d_block);
+  free_device(p->d_out);
+  free_device(p->d_cands);
+  if (p->h_total) cudaFreeHost(p->h_total);
+  delete p;
+}
+
+int validate_execute(const dd_plan *p, int64_t nsamp_in, int64_t pitch, int64_t *nsamp_out) {
+  if (nsamp_in <= p->maxshift) return DD_ERR_SIZE;
+  if (pitch < nsamp_in) return DD_ERR_SIZE;
+  *nsamp_out = nsamp_in - p->maxshift;
+  if (*nsamp_out > INT32_MAX) return DD_ERR_SIZE;  // candidate times are int32
+  return DD_OK;
+}
+
+}  // namespace
+
+extern "C" int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz,
+                              double chan_width_mhz, double t_samp_s, const double *dm_list,
+                              int32_t ndm, int32_t in_dtype, int32_t device) {
+  if (!out) return DD_ERR_ARG;
+  *out = nullptr;
+  if (in_dtype != DD_U8 && in_dtype != DD_F16 && in_dtype != DD_F32) return DD_ERR_DTYPE;
+  if (nchan < 1 || ndm < 1 || !dm_list || device < 0) return DD_ERR_ARG;
+  if (ndm > 65535) return DD_ERR_SIZE;  // one grid row per trial in the detection passes
+  if (in_dtype == DD_U8 && static_cast<int64_t>(nchan) * 255 > INT32_MAX) return DD_ERR_RANGE;
+
+  dd_plan *p = new (std::nothrow) dd_plan();
+  if (!p) return DD_ERR_OOM;
+  p->device = device;
+  p->nchan = nchan;
+  p->ndm = ndm;
+  p->dtype = in_dtype;
+  p->f_top = f_top_mhz;
+  p->df = chan_width_mhz;
+  p->t_samp = t_samp_s;
+  try {
+    p->dms.assign(dm_list, dm_list + ndm);
+    p->h_delays.resize(static_cast<size_t>(nchan) * ndm);
+    p->h_mean.resize(ndm);
+    p->h_sigma.resize(ndm);
+  } catch (...) {
+    delete p;
+    return DD_ERR_OOM;
+  }
+  int st = dd_compute_delays(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dm_list, ndm,
+                             p->h_delays.data(), &p->maxshift);
+  if (st != DD_OK) {
+    delete p;
+    return st;
+  }
+  DeviceScope scope(device);
+  if (!scope.ok()) {
+    delete p;
+    return DD_ERR_CUDA;
+  }
+  cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, device);
+  const size_t table_bytes = p->h_delays.size() * sizeof(int32_t);
+  cudaError_t e = cudaMalloc(&p->d_delays, table_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_error, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_stats, sizeof(dd_row_stats) * ndm);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_total, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_total, sizeof(int64_t));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(p->d_delays, p->h_delays.data(), table_bytes, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    destroy_plan(p);
+    return cuda_status(e);
+  }
+  *out = p;
+  return DD_OK;
+}
+
+extern "C" int dd_plan_destroy(dd_plan *p) {
+  if (!p) return DD_OK;
+  DeviceScope scope(p->device);
+  if (scope.ok()) cudaDeviceSynchronize();
+  destroy_plan(p);
+  return DD_OK;
+}
+
+extern "C" int dd_plan_max_delay(const dd_plan *p, int32_t *maxshift) {
+  if (!p || !maxshift) return DD_ERR_ARG;
+  *maxshift = p->maxshift;
+  return DD_OK;
+}
+
+extern "C" int dd_plan_nsamp_out(const dd_plan *p, int64_t nsamp_in, int64_t *nsamp_out) {
+  if (!p || !nsamp_out) return DD_ERR_ARG;
+  if (nsamp_in <= p->maxshift) return DD_ERR_SIZE;
+  *nsamp_out = nsamp_in - p->maxshift;
+  return DD_OK;
+}
+
+extern "C" int dd_plan_delays(const dd_plan *p, int32_t *host_out) {
+  if (!p || !host_out) return DD_ERR_ARG;
+  std::memcpy(host_out, p->h_delays.data(), p->h_delays.size() * sizeof(int32_t));
+  return DD_OK;
+}
+
+extern "C" int dd_plan_launch_count(const dd_plan *p, int64_t *launches) {
+  if (!p || !launches) return DD_ERR_ARG;
+  *launches = p->launches;
+  return DD_OK;
+}
+
+extern "C" int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
+                          void *out, void *stream) {
+  if (!p || !block || !out) return DD_ERR_ARG;
+  int64_t nsamp_out = 0;
+  int st = validate_execute(p, nsamp_in, pitch_elems, &nsamp_out);
+  if (st != DD_OK) return st;
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  cudaError_t err = cudaSuccess;
+  const int n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out,
+                                              static_cast<cudaStream_t>(stream), &err);
+  if (n < 0) return cuda_status(err);
+  p->launches += n;
+  return DD_OK;
+}
+
+extern "C" int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                         dd_candidate *cands, int64_t capacity, int64_t *count, void *stream) {
+  if (!p || !out || !count || capacity < 0 || (capacity > 0 && !cands)) return DD_ERR_ARG;
+  if (!std::isfinite(nsigma)) return DD_ERR_ARG;
+  if (nsamp_out < 1 || nsamp_out > INT32_MAX) return DD_ERR_SIZE;
+  *count = 0;
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t nchunks = (nsamp_out + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
+  int st = ensure_chunk_workspace(p, static_cast<size_t>(nchunks) * p->ndm);
+  if (st != DD_OK) return st;
+  p->stats_valid = false;
+  cudaError_t err = cudaSuccess;
+  int n = ddk::launch_stats(p, out, nsamp_out, s, &err);
+  if (n < 0) return cuda_status(err);
+  p->launches += n;
+  n = ddk::launch_candidates(p, out, nsamp_out, nsigma, cands, capacity, s, &err);
+  if (n < 0) return cuda_status(err);
+  p->launches += n;
+  err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_status(err);
+  st = take_device_status(p);
+  if (st != DD_OK) return st;
+  p->stats_valid = true;
+  *count = *p->h_total;
+  return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
+}
+
+extern "C" int dd_get_stats(const dd_plan *p, double *mean, double *sigma) {
+  if (!p) return DD_ERR_ARG;
+  if (!p->stats_valid) return DD_ERR_ARG;
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  dd_row_stats *tmp = new (std::nothrow) dd_row_stats[p->ndm];
+  if (!tmp) return DD_ERR_OOM;
+  cudaError_t e = cudaMemcpy(tmp, p->d_stats, sizeof(dd_row_stats) * p->ndm,
+                             cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) {
+    for (int32_t d = 0; d < p->ndm; ++d) {
+      if (mean) mean[d] = tmp[d].mean;
+      if (sigma) sigma[d] = tmp[d].sigma;
+    }
+  }
+  delete[] tmp;
+  return cuda_status(e);
+}
+
+extern "C" int dd_sync(dd_plan *p, void *stream) {
+  if (!p) return DD_ERR_ARG;
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_status(e);
+  return take_device_status(p);
+}
+
+extern "C" int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp_in,
+                               int64_t pitch_elems, float nsigma, dd_candidate *host_cands,
+                               int64_t capacity, int64_t *count, void *stream) {
+  if (!p || !host_block || !count || capacity < 0 || (capacity > 0 && !host_cands))
+    return DD_ERR_ARG;
+  int64_t nsamp_out = 0;
+  int st = validate_execute(p, nsamp_in, pitch_elems, &nsamp_out);
+  if (st != DD_OK) return st;
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const size_t in_bytes = static_cast<size_t>(p->nchan) * pitch_elems * ddk::elem_size(p->dtype);
+  const size_t out_bytes = static_cast<size_t>(p->ndm) * nsamp_out * 4;
+  if (in_bytes > p->d_block_bytes) {
+    free_device(p->d_block);
+    p->d_block_bytes = 0;
+    if (cudaMalloc(&p->d_block, in_bytes) != cudaSuccess) return DD_ERR_OOM;
+    p->d_block_bytes = in_bytes;
+  }
+  if (out_bytes > p->d_out_bytes) {
+    free_device(p->d_out);
+    p->d_out_bytes = 0;
+    if (cudaMalloc(&p->d_out, out_bytes) != cudaSuccess) return DD_ERR_OOM;
+    p->d_out_bytes = out_bytes;
+  }
+  if (static_cast<size_t>(capacity) > p->d_cands_cap) {
+    free_device(p->d_cands);
+    p->d_cands_cap = 0;
+    if (cudaMalloc(&p->d_cands, sizeof(dd_candidate) * capacity) != cudaSuccess)
+      return DD_ERR_OOM;
+    p->d_cands_cap = capacity;
+  }
+  cudaError_t e = cudaMemcpyAsync(p->d_block, host_block, in_bytes, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_status(e);
+  st = dd_execute(p, p->d_block, nsamp_in, pitch_elems, p->d_out, stream);
+  if (st != DD_OK) return st;
+  const int dst = dd_detect(p, p->d_out, nsamp_out, nsigma, p->d_cands, capacity, count, stream);
+  if (dst != DD_OK && dst != DD_ERR_OVERFLOW) return dst;
+  const int64_t ncopy = *count < capacity ? *count : capacity;
+  if (ncopy > 0) {
+    e = cudaMemcpyAsync(host_cands, p->d_cands, sizeof(dd_candidate) * ncopy,
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return dst;
+}

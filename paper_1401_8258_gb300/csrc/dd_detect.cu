@@ -1,0 +1,280 @@
+// dd_detect.cu -- per-DM-trial normalisation and n-sigma candidate extraction
+// (Sec. 3.5 normalisation, Sec. 3.6 thresholding into (DM, time, intensity)
+// triplets), moved from the host onto the GPU.
+//
+// Passes over D[ndm][n]:
+//   1. dd_stats_*      one CTA per DM row: exact integer sums (int32 rows) or
+//                      shifted double sums (float rows), then mean and rms;
+//   2. dd_count        per (row, 4096-sample chunk): number of samples with
+//                      snr > nsigma;
+//   3. dd_scan         exclusive prefix over the chunk counts in (row, chunk)
+//                      order, plus the total;
+//   4. dd_write        chunks with a non-zero count write their candidates
+//                      in time order at their prefix offset.
+// The candidate list is therefore ordered by (dm_idx, t) and independent of
+// scheduling.  The predicate is evaluated identically in passes 2 and 4.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "dd_internal.h"
+
+namespace {
+
+constexpr int kStatsThreads = 512;
+constexpr int kCountThreads = 256;
+constexpr int kPerThread = ddk::kDetectChunk / kCountThreads;  // 16 contiguous samples
+constexpr int kScanThreads = 1024;
+
+// Correctly rounded (round-to-nearest-even) conversion of an unsigned
+// 128-bit integer to double.  Values below 2^64 use the hardware
+// conversion; larger ones are cut to their top 64 bits with every dropped
+// bit folded into bit 0 (a sticky bit below the rounding position, which
+// leaves the nearest-even decision unchanged), converted, and rescaled by an
+// exact power of two.
+__device__ double u128_to_double_rn(unsigned __int128 v) {
+  const unsigned long long hi = static_cast<unsigned long long>(v >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(v);
+  if (hi == 0) return __ull2double_rn(lo);
+  const int drop = 64 - __clzll(static_cast<long long>(hi));
+  const unsigned __int128 mask = (static_cast<unsigned __int128>(1) << drop) - 1;
+  const unsigned long long top =
+      static_cast<unsigned long long>(v >> drop) | static_cast<unsigned long long>((v & mask) != 0);
+  return scalbn(__ull2double_rn(top), drop);
+}
+
+// One CTA per row: S1 = sum D, S2 = sum D^2 exactly, then
+//   mean = S1 / N,  rms = sqrt((double)(N*S2 - S1^2)) / N.
+__global__ void __launch_bounds__(kStatsThreads)
+dd_stats_i32(const int32_t *__restrict__ D, int64_t n, dd_row_stats *__restrict__ stats) {
+  __shared__ long long s_s1[kStatsThreads];
+  __shared__ unsigned __int128 s_s2[kStatsThreads];
+  const int32_t *row = D + static_cast<int64_t>(blockIdx.x) * n;
+  long long s1 = 0;
+  unsigned __int128 s2 = 0;
+  for (int64_t t = threadIdx.x; t < n; t += kStatsThreads) {
+    const long long v = row[t];
+    s1 += v;
+    s2 += static_cast<unsigned __int128>(static_cast<unsigned long long>(v * v));
+  }
+  s_s1[threadIdx.x] = s1;
+  s_s2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = kStatsThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_s1[threadIdx.x] += s_s1[threadIdx.x + w];
+      s_s2[threadIdx.x] += s_s2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const __int128 S1 = s_s1[0];
+    const __int128 S2 = static_cast<__int128>(s_s2[0]);
+    const __int128 num = static_cast<__int128>(n) * S2 - S1 * S1;  // >= 0
+    const double dn = __ll2double_rn(n);
+    dd_row_stats st;
+    st.mean = __ddiv_rn(__ll2double_rn(s_s1[0]), dn);
+    st.sigma = __ddiv_rn(__dsqrt_rn(u128_to_double_rn(static_cast<unsigned __int128>(num))), dn);
+    stats[blockIdx.x] = st;
+  }
+}
+
+// One CTA per row of f32 values: double sums of (x - K) with K the row's
+// first value, combined in a fixed tree order (deterministic), then
+//   mean = K + S1/N,  rms = sqrt(max(S2/N - (S1/N)^2, 0)).
+__global__ void __launch_bounds__(kStatsThreads)
+dd_stats_f32(const float *__restrict__ D, int64_t n, dd_row_stats *__restrict__ stats) {
+  __shared__ double s_s1[kStatsThreads];
+  __shared__ double s_s2[kStatsThreads];
+  const float *row = D + static_cast<int64_t>(blockIdx.x) * n;
+  const double K = static_cast<double>(row[0]);
+  double s1 = 0.0, s2 = 0.0;
+  for (int64_t t = threadIdx.x; t < n; t += kStatsThreads) {
+    const double x = static_cast<double>(row[t]) - K;
+    s1 += x;
+    s2 += x * x;
+  }
+  s_s1[threadIdx.x] = s1;
+  s_s2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int w = kStatsThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      s_s1[threadIdx.x] += s_s1[threadIdx.x + w];
+      s_s2[threadIdx.x] += s_s2[threadIdx.x + w];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double dn = static_cast<double>(n);
+    const double m1 = s_s1[0] / dn;
+    const double var = s_s2[0] / dn - m1 * m1;
+    dd_row_stats st;
+    st.mean = K + m1;
+    st.sigma = sqrt(var > 0.0 ? var : 0.0);
+    stats[blockIdx.x] = st;
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ double as_double(T v) { return static_cast<double>(v); }
+
+// snr > nsigma in IEEE double: ((double)v - mean) / sigma, rows with sigma 0
+// never pass.
+__device__ __forceinline__ bool is_candidate(double v, dd_row_stats st, double thr) {
+  if (!(st.sigma > 0.0)) return false;
+  return __ddiv_rn(__dsub_rn(v, st.mean), st.sigma) > thr;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCountThreads)
+dd_count(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__restrict__ stats,
+         double thr, int64_t *__restrict__ counts) {
+  __shared__ int s_cnt[kCountThreads / 32];
+  const int d = blockIdx.y;
+  const int chunk = blockIdx.x;
+  const dd_row_stats st = stats[d];
+  const T *row = D + static_cast<int64_t>(d) * n;
+  const int64_t t0 = static_cast<int64_t>(chunk) * ddk::kDetectChunk;
+  int cnt = 0;
+  // coalesced sweep: sample t0 + k*256 + tid
+#pragma unroll 4
+  for (int k = 0; k < kPerThread; ++k) {
+    const int64_t t = t0 + k * kCountThreads + threadIdx.x;
+    if (t < n) cnt += is_candidate(as_double(row[t]), st, thr) ? 1 : 0;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+  if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5] = cnt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int total = 0;
+    for (int w = 0; w < kCountThreads / 32; ++w) total += s_cnt[w];
+    counts[static_cast<int64_t>(d) * nchunks + chunk] = total;
+  }
+}
+
+// Single-CTA exclusive scan of m counts (each thread owns a contiguous run).
+__global__ void __launch_bounds__(kScanThreads)
+dd_scan(const int64_t *__restrict__ counts, int64_t m, int64_t *__restrict__ offsets,
+        int64_t *__restrict__ total) {
+  __shared__ int64_t s_part[kScanThreads];
+  const int64_t per = (m + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = threadIdx.x * per;
+  const int64_t hi = lo + per < m ? lo + per : m;
+  int64_t sum = 0;
+  for (int64_t i = lo; i < hi; ++i) sum += counts[i];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the per-thread sums.
+  for (int o = 1; o < kScanThreads; o <<= 1) {
+    const int64_t add = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int64_t run = s_part[threadIdx.x] - sum;
+  for (int64_t i = lo; i < hi; ++i) {
+    offsets[i] = run;
+    run += counts[i];
+  }
+  if (threadIdx.x == kScanThreads - 1) *total = s_part[kScanThreads - 1];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCountThreads)
+dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__restrict__ stats,
+         double thr, const int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
+         dd_candidate *__restrict__ cands, int64_t capacity) {
+  __shared__ int s_scan[kCountThreads];
+  const int d = blockIdx.y;
+  const int chunk = blockIdx.x;
+  const int64_t slot = static_cast<int64_t>(d) * nchunks + chunk;
+  if (counts[slot] == 0) return;  // uniform across the CTA
+  const int64_t base = offsets[slot];
+  if (base >= capacity) return;
+  const dd_row_stats st = stats[d];
+  const T *row = D + static_cast<int64_t>(d) * n;
+  // thread owns samples [t0 + tid*16, +16) so that output order is time order
+  const int64_t t0 = static_cast<int64_t>(chunk) * ddk::kDetectChunk + threadIdx.x * kPerThread;
+  unsigned mask = 0;
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    const int64_t t = t0 + k;
+    if (t < n && is_candidate(as_double(row[t]), st, thr)) mask |= 1u << k;
+  }
+  const int mine = __popc(mask);
+  s_scan[threadIdx.x] = mine;
+  __syncthreads();
+  for (int o = 1; o < kCountThreads; o <<= 1) {
+    const int add = threadIdx.x >= o ? s_scan[threadIdx.x - o] : 0;
+    __syncthreads();
+    s_scan[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int64_t idx = base + s_scan[threadIdx.x] - mine;
+  while (mask) {
+    const int k = __ffs(mask) - 1;
+    mask &= mask - 1;
+    if (idx < capacity) {
+      const double v = as_double(row[t0 + k]);
+      dd_candidate c;
+      c.dm_idx = d;
+      c.t = static_cast<int32_t>(t0 + k);
+      c.value = static_cast<float>(v);
+      c.snr = static_cast<float>(__ddiv_rn(__dsub_rn(v, st.mean), st.sigma));
+      cands[idx] = c;
+    }
+    ++idx;
+  }
+}
+
+}  // namespace
+
+namespace ddk {
+
+int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, cudaStream_t stream,
+                 cudaError_t *err) {
+  if (p->dtype == DD_U8)
+    dd_stats_i32<<<p->ndm, kStatsThreads, 0, stream>>>(static_cast<const int32_t *>(out), nsamp_out,
+                                                        p->d_stats);
+  else
+    dd_stats_f32<<<p->ndm, kStatsThreads, 0, stream>>>(static_cast<const float *>(out), nsamp_out,
+                                                        p->d_stats);
+  *err = cudaGetLastError();
+  return *err == cudaSuccess ? 1 : -1;
+}
+
+int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                      dd_candidate *cands, int64_t capacity, cudaStream_t stream,
+                      cudaError_t *err) {
+  const int nchunks = static_cast<int>((nsamp_out + kDetectChunk - 1) / kDetectChunk);
+  const int64_t m = static_cast<int64_t>(p->ndm) * nchunks;
+  const dim3 grid(nchunks, p->ndm);
+  const double thr = static_cast<double>(nsigma);
+  int n = 0;
+  if (p->dtype == DD_U8)
+    dd_count<int32_t><<<grid, kCountThreads, 0, stream>>>(static_cast<const int32_t *>(out),
+                                                          nsamp_out, nchunks, p->d_stats, thr,
+                                                          p->d_counts);
+  else
+    dd_count<float><<<grid, kCountThreads, 0, stream>>>(static_cast<const float *>(out), nsamp_out,
+                                                        nchunks, p->d_stats, thr, p->d_counts);
+  ++n;
+  dd_scan<<<1, kScanThreads, 0, stream>>>(p->d_counts, m, p->d_offsets, p->d_total);
+  ++n;
+  if (capacity > 0) {
+    if (p->dtype == DD_U8)
+      dd_write<int32_t><<<grid, kCountThreads, 0, stream>>>(
+          static_cast<const int32_t *>(out), nsamp_out, nchunks, p->d_stats, thr, p->d_counts,
+          p->d_offsets, cands, capacity);
+    else
+      dd_write<float><<<grid, kCountThreads, 0, stream>>>(
+          static_cast<const float *>(out), nsamp_out, nchunks, p->d_stats, thr, p->d_counts,
+          p->d_offsets, cands, capacity);
+    ++n;
+  }
+  *err = cudaGetLastError();
+  return *err == cudaSuccess ? n : -1;
+}
+
+}  // namespace ddk

@@ -1,0 +1,72 @@
+// dd_internal.h -- plan object and kernel launchers shared by the libdd
+// translation units (not part of the public C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "dd.h"
+
+// Per-DM-row normalisation result written by the statistics kernels.
+struct dd_row_stats {
+  double mean;
+  double sigma;
+};
+
+struct dd_plan {
+  int device = 0;
+  int32_t nchan = 0;
+  int32_t ndm = 0;
+  int32_t dtype = DD_U8;
+  double f_top = 0, df = 0, t_samp = 0;
+  std::vector<double> dms;
+  std::vector<int32_t> h_delays;  // [nchan][ndm]
+  int32_t maxshift = 0;
+  int sm_count = 0;
+
+  int32_t *d_delays = nullptr;    // [nchan][ndm]
+  int32_t *d_error = nullptr;     // sticky device status word (0 = ok)
+
+  // detection workspace
+  dd_row_stats *d_stats = nullptr;  // [ndm]
+  int64_t *d_counts = nullptr;      // [ndm * nchunks] per-chunk candidate counts
+  int64_t *d_offsets = nullptr;     // [ndm * nchunks] exclusive prefix of d_counts
+  int64_t *d_total = nullptr;       // [1]
+  int64_t *h_total = nullptr;       // pinned [1]
+  size_t chunk_cap = 0;             // entries allocated in d_counts / d_offsets
+  std::vector<double> h_mean, h_sigma;
+  bool stats_valid = false;
+
+  // buffers owned for dd_process_host
+  void *d_block = nullptr;
+  size_t d_block_bytes = 0;
+  void *d_out = nullptr;
+  size_t d_out_bytes = 0;
+  dd_candidate *d_cands = nullptr;
+  size_t d_cands_cap = 0;
+
+  int64_t launches = 0;
+};
+
+namespace ddk {
+
+// Element size of a dd_dtype.
+inline int elem_size(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F16 ? 2 : 4); }
+
+// Dedispersion: out[d][t] = sum_c block[c][t + delays[c][d]] for t < nsamp_out.
+// Each launcher returns the number of kernels queued, or -1 with the CUDA
+// error in *err.
+int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
+                             void *out, cudaStream_t stream, cudaError_t *err);
+
+// Detection passes over out[ndm][nsamp_out]; see dd_detect in dd.h.
+constexpr int kDetectChunk = 4096;  // samples per (row, chunk) work unit
+int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, cudaStream_t stream,
+                 cudaError_t *err);
+int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                      dd_candidate *cands, int64_t capacity, cudaStream_t stream,
+                      cudaError_t *err);
+
+}  // namespace ddk

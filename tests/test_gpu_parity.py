@@ -1,0 +1,304 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+Integer (u8) input must match bit for bit, including the per-DM statistics
+and the candidate list.  Float input (f16, f32) must satisfy, per output,
+  |D_gpu - D_oracle| <= 1e-5 * sum_c |I[c][t + delay(c,d)]|
+i.e. a relative error of 1e-5 against the conditioning of each sum (the
+oracle sums in double); candidates must agree except for samples whose oracle
+snr lies within 1e-4*max(1,|nsigma|) of the threshold.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1401_8258_gb300 as dd
+import synth
+
+pytestmark = pytest.mark.gpu
+
+FLOAT_RTOL = 1e-5
+BAND = 1e-4
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    dd.build()
+    oracle.build()
+
+
+def _to_dev(block: np.ndarray) -> torch.Tensor:
+    return torch.from_numpy(np.ascontiguousarray(block)).to(DEV)
+
+
+def run_plan(wl, block, nsamp_in=None, offset=0, nsigma=None, capacity=1 << 16):
+    """Dedisperse (and optionally detect) ``block`` on the GPU.
+
+    ``offset`` shifts the block's start by that many elements inside a larger
+    device buffer, so that misaligned pointers are exercised.
+    """
+    nchan, pitch = block.shape
+    nsamp_in = pitch if nsamp_in is None else nsamp_in
+    with dd.Plan(nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, wl.dtype) as plan:
+        flat = np.zeros(nchan * pitch + offset + 64, dtype=block.dtype)
+        flat[offset:offset + nchan * pitch] = block.reshape(-1)
+        dbuf = _to_dev(flat)
+        dblock = dbuf[offset:offset + nchan * pitch].view(nchan, pitch)
+        out = plan.execute(dblock, nsamp_in=nsamp_in)
+        res = {"D": None, "cands": None, "total": None, "mean": None, "sigma": None}
+        if nsigma is not None:
+            cands, total = plan.detect(out, nsigma, capacity=capacity)
+            mean, sigma = plan.stats()
+            res.update(cands=cands, total=total, mean=mean, sigma=sigma)
+        torch.cuda.synchronize()
+        res["D"] = out.cpu().numpy()
+        res["delays"] = plan.delays()
+        res["launches"] = plan.launch_count()
+    return res
+
+
+def float_rel_err(block, delays, got, ref, nsamp_in=None, rows=None):
+    """max |got - ref| / sum_c |I[c][t + delay]| over all outputs."""
+    absblock = np.abs(block.astype(np.float32))
+    d = delays if rows is None else delays[:, rows]
+    scale = oracle.dedisperse(absblock, d, nsamp_out=ref.shape[1], nsamp_in=nsamp_in)
+    return float(np.max(np.abs(got.astype(np.float64) - ref) / np.maximum(scale, 1e-30)))
+
+
+def assert_parity(wl, block, res, nsamp_in=None):
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    assert np.array_equal(res["delays"], delays)
+    ref = oracle.dedisperse(block, delays, nsamp_in=nsamp_in)
+    got = res["D"]
+    assert got.shape == ref.shape
+    if wl.dtype == "u8":
+        assert got.dtype == np.int32
+        bad = np.argwhere(got != ref)
+        assert bad.size == 0, f"{bad.shape[0]} mismatches, first {bad[:5].tolist()}"
+    else:
+        err = float_rel_err(block, delays, got, ref, nsamp_in)
+        assert err <= FLOAT_RTOL, err
+    return ref
+
+
+def assert_detection(wl, ref, res, nsigma):
+    if wl.dtype == "u8":
+        mean, sigma = oracle.stats(ref)
+        assert np.array_equal(res["mean"], mean)
+        assert np.array_equal(res["sigma"], sigma)
+        cands, total = oracle.detect(ref, mean, sigma, nsigma)
+        assert res["total"] == total
+        assert np.array_equal(res["cands"], cands)
+    else:
+        mean, sigma = oracle.stats(ref)
+        np.testing.assert_allclose(res["mean"], mean, rtol=1e-5, atol=1e-4 * np.sqrt(wl.nchan))
+        np.testing.assert_allclose(res["sigma"], sigma, rtol=1e-5)
+        ok = sigma > 0
+        snr = np.full(ref.shape, -np.inf)
+        snr[ok] = (ref[ok] - mean[ok, None]) / sigma[ok, None]
+        band = BAND * max(1.0, abs(nsigma))
+        sure = set(map(tuple, np.argwhere(snr > nsigma + band)))
+        maybe = set(map(tuple, np.argwhere(snr > nsigma - band)))
+        got = set(zip(res["cands"]["dm_idx"].tolist(), res["cands"]["t"].tolist()))
+        assert sure <= got <= maybe
+        order = list(zip(res["cands"]["dm_idx"].tolist(), res["cands"]["t"].tolist()))
+        assert order == sorted(order)
+
+
+# ------------------------------------------------------------------ tiny
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
+@pytest.mark.parametrize("seed", range(6))
+def test_tiny_random_shapes(dtype, seed):
+    rng = np.random.default_rng(1000 + seed)
+    nchan = int(rng.integers(1, 38))
+    ndm = int(rng.integers(1, 20))
+    f_top = float(rng.uniform(300, 1500))
+    df = float(rng.uniform(0.001, 0.05)) * f_top / max(nchan, 1)
+    ts = float(rng.uniform(20e-6, 200e-6))
+    dms = np.sort(rng.uniform(0, 40, ndm))
+    wl = synth.Workload("tiny", nchan, 0, f_top, df, ts, dms, dtype)
+    _, mx = oracle.delay_table(nchan, f_top, df, ts, dms)
+    nsamp = mx + int(rng.integers(1, 300))
+    pitch = nsamp + int(rng.integers(0, 19))
+    block = synth.random_block(rng, nchan, nsamp, dtype, pitch)
+    offset = int(rng.integers(0, 5))
+    res = run_plan(wl, block, nsamp_in=nsamp, offset=offset, nsigma=1.5)
+    ref = assert_parity(wl, block, res, nsamp_in=nsamp)
+    assert_detection(wl, ref, res, 1.5)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
+def test_single_output_sample_and_single_trial(dtype):
+    rng = np.random.default_rng(5)
+    wl = synth.Workload("edge", 8, 0, 416.0, 0.25, 100e-6, np.array([17.0]), dtype)
+    _, mx = oracle.delay_table(8, 416.0, 0.25, 100e-6, wl.dms)
+    block = synth.random_block(rng, 8, mx + 1, dtype)
+    res = run_plan(wl, block)
+    assert res["D"].shape == (1, 1)
+    assert_parity(wl, block, res)
+
+
+def test_all_zero_dm_and_one_channel():
+    rng = np.random.default_rng(6)
+    wl = synth.Workload("zero", 1, 0, 416.0, 0.25, 100e-6, np.zeros(5), "u8")
+    block = synth.random_block(rng, 1, 777, "u8")
+    res = run_plan(wl, block, nsigma=2.0)
+    ref = assert_parity(wl, block, res)
+    assert np.array_equal(res["D"][0], block[0].astype(np.int32))
+    assert_detection(wl, ref, res, 2.0)
+
+
+def test_constant_input_gives_zero_sigma_and_no_candidates():
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=32, ndm=40)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block = np.full((32, mx + 5000), 200, dtype=np.uint8)
+    res = run_plan(wl, block, nsigma=0.0)
+    assert np.all(res["sigma"] == 0) and res["total"] == 0
+    assert np.all(res["D"] == 200 * 32)
+
+
+# ---------------------------------------------------------------- configs
+
+@pytest.mark.parametrize("dtype", ["f32", "f16", "u8"])
+def test_single_beam_full_config(dtype):
+    """64 ch x 8192, DM 0..63: every output against the oracle."""
+    wl = synth.workload("single_beam_f32")
+    wl.dtype = dtype
+    if dtype == "u8":
+        wl.pulse_amp = 80.0
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, pulses = synth.make_block(wl, seed=1, delays=delays)
+    res = run_plan(wl, block, nsigma=6.0)
+    ref = assert_parity(wl, block, res)
+    assert_detection(wl, ref, res, 6.0)
+    p = pulses[0]
+    hit = (res["cands"]["dm_idx"] == p.dm_idx) & (res["cands"]["t"] >= p.t0) & \
+        (res["cands"]["t"] < p.t0 + p.width)
+    assert hit.any()
+
+
+@pytest.mark.parametrize("pitch_pad, offset", [(0, 0), (13, 0), (0, 3), (16, 16)])
+def test_full_block_geometry_reduced_size(pitch_pad, offset):
+    """400-416 MHz, 51.2 us geometry at 256 channels, 128 trials: covers
+    many time tiles, a ragged tail, odd pitches and misaligned pointers."""
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=256, nsamp=12000, ndm=128)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, _ = synth.make_block(wl, seed=2, delays=delays, pitch=wl.nsamp + pitch_pad)
+    res = run_plan(wl, block, nsamp_in=wl.nsamp, offset=offset, nsigma=4.0)
+    ref = assert_parity(wl, block, res, nsamp_in=wl.nsamp)
+    assert_detection(wl, ref, res, 4.0)
+
+
+def test_full_block_u8_full_size_sampled_rows():
+    """1024 ch x 65536 u8, 2048 trials DM 0..204.7: rows sampled across the
+    DM range (first, last and spread) against the oracle, bit-exact, with
+    their statistics and candidates; pulses recovered at their true trial."""
+    wl = synth.workload("full_block_u8")
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, pulses = synth.make_block(wl, seed=1, delays=delays)
+    res = run_plan(wl, block, nsigma=6.0)
+    D = res["D"]
+    rows = sorted(set([0, 1, 2, 1023, 2046, 2047] + [p.dm_idx for p in pulses] +
+                      np.random.default_rng(3).integers(0, wl.ndm, 10).tolist()))
+    ref = oracle.dedisperse(block, delays[:, rows], nsamp_out=D.shape[1])
+    assert np.array_equal(D[rows], ref)
+    mean, sigma = oracle.stats(ref)
+    assert np.array_equal(res["mean"][rows], mean)
+    assert np.array_equal(res["sigma"][rows], sigma)
+    for p in pulses:
+        hit = (res["cands"]["dm_idx"] == p.dm_idx) & (res["cands"]["t"] >= p.t0) & \
+            (res["cands"]["t"] < p.t0 + p.width)
+        assert hit.any(), p
+    for i, r in enumerate(rows):
+        c_ref, tot = oracle.detect(ref[i:i + 1], mean[i:i + 1], sigma[i:i + 1], 6.0)
+        mine = res["cands"][res["cands"]["dm_idx"] == r]
+        assert mine.size == tot
+        assert np.array_equal(mine["t"], c_ref["t"])
+        assert np.array_equal(mine["value"], c_ref["value"])
+        assert np.array_equal(mine["snr"], c_ref["snr"])
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_lband_full_size_sampled_rows(dtype):
+    """4096 ch x 131072, 4096 trials DM 0..409.5 with narrowband RFI: sampled
+    rows within 1e-5 of the FP64 oracle (relative to the sum of |I|)."""
+    wl = synth.workload("lband_" + dtype)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, pulses = synth.make_block(wl, seed=1, delays=delays)
+    res = run_plan(wl, block)
+    rows = [0, 1, 2048, 4094, 4095, pulses[0].dm_idx]
+    ref = oracle.dedisperse(block, delays[:, rows], nsamp_out=res["D"].shape[1])
+    err = float_rel_err(block, delays, res["D"][rows], ref, rows=rows)
+    print(f"lband {dtype}: max relative error {err:.3e}")
+    assert err <= FLOAT_RTOL
+
+
+# ------------------------------------------------------------ error paths
+
+def test_argument_errors():
+    wl = synth.workload("single_beam_f32")
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "f32") as plan:
+        h = plan.handle
+        blk = torch.zeros((wl.nchan, 2000), device=DEV)
+        out = torch.zeros((wl.ndm, 2000), device=DEV)
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_execute(h, blk, plan.maxshift, 2000, out)          # nsamp_in <= maxshift
+        assert e.value.status == -2
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_execute(h, blk, 2000, 1999, out)                    # pitch < nsamp_in
+        assert e.value.status == -2
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_execute(h, None, 2000, 2000, out)
+        assert e.value.status == -1
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_detect(h, out, 100, 5.0, None, 10)                  # capacity without buffer
+        assert e.value.status == -1
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_get_stats(h, wl.ndm)                                # no detect yet
+        assert e.value.status == -1
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_plan_create(64, 416.0, 0.25, 1e-4, [1.0], 7)
+    assert e.value.status == -3
+    with pytest.raises(dd.DDError) as e:
+        dd.dd_plan_create(64, 416.0, 0.25, 1e-4, np.zeros(70000), "u8")
+    assert e.value.status == -2
+
+
+def test_capacity_overflow_keeps_first_candidates_in_order():
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=64, nsamp=8000, ndm=32)
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, _ = synth.make_block(wl, seed=4, delays=delays)
+    full = run_plan(wl, block, nsigma=1.0)
+    part = run_plan(wl, block, nsigma=1.0, capacity=100)
+    assert full["total"] == part["total"] > 100
+    assert np.array_equal(part["cands"], full["cands"][:100])
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as plan:
+        out = plan.execute(_to_dev(block))
+        cands = torch.empty((10, 16), dtype=torch.uint8, device=DEV)
+        st, total = dd.dd_detect(plan.handle, out, out.shape[1], 1.0, cands, 10)
+        assert st == dd.DD_ERR_OVERFLOW and total == full["total"]
+        st, total = dd.dd_detect(plan.handle, out, out.shape[1], 1.0, None, 0)
+        assert total == full["total"]
+
+
+def test_process_host_matches_device_path():
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=128, nsamp=9000, ndm=64)
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, _ = synth.make_block(wl, seed=5, delays=delays)
+    dev = run_plan(wl, block, nsigma=3.0)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as plan:
+        host = torch.from_numpy(block).pin_memory()
+        cands = np.zeros(1 << 16, dtype=dd.CANDIDATE_DTYPE)
+        for _ in range(2):  # second call reuses the plan's buffers
+            st, total = dd.dd_process_host(plan.handle, host, wl.nsamp, wl.nsamp, 3.0, cands,
+                                           cands.size)
+            assert st == 0 and total == dev["total"]
+            assert np.array_equal(cands[:total], dev["cands"])
+
+
+def test_add_pipe_probe_reports_positive_rates():
+    ops, per_clk = dd._native.dd_measure_add_peak("fadd")
+    assert ops > 1e12 and 16 <= per_clk <= 512
