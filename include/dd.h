@@ -159,6 +159,29 @@ int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp_in, int64_
  * points); used to account for device work. */
 int dd_plan_launch_count(const dd_plan *p, int64_t *launches);
 
+/* Kernel selection: path 0 (default) lets dd_execute take the staged kernel
+ * whenever the plan and the block's layout allow it; path 1 forces the
+ * plain-load kernel (same results; used to cross-check the two). */
+int dd_plan_set_path(dd_plan *p, int32_t path);
+
+/* Upper bound, in nanoseconds, on every device-side wait of the staged
+ * kernel (default 2e9).  A wait that runs out makes the launch record
+ * DD_ERR_DEVICE_TIMEOUT (reported by the next synchronising call) and leave
+ * its output unwritten.  DD_ERR_ARG below 1000 ns. */
+int dd_plan_set_wait_timeout(dd_plan *p, int64_t timeout_ns);
+
+/* Fault injection for tests of the timeout path: with skip_copies != 0 the
+ * staged kernel queues none of its bulk copies, so its first bounded wait
+ * runs out (no device fault, no hang).  0 restores normal operation. */
+int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies);
+
+/* Which kernel dd_execute would use for `block` / `pitch_elems`:
+ * *staged = 1 for the staged (bulk-copy) kernel, 0 for the plain-load one;
+ * *dms_per_cta and *smem_bytes describe the staged kernel's tiling (0 when
+ * the plan has none).  Either of the last two may be NULL. */
+int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems,
+                        int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes);
+
 /* Static description of a status code. */
 const char *dd_status_string(int status);
 

@@ -61,6 +61,10 @@ SIGNATURES = [
     ("dd_plan_launch_count", ctypes.c_int, [_vp, _vp]),
     ("dd_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("dd_measure_add_peak", ctypes.c_int, [_i32, _i32, _vp, _vp]),
+    ("dd_plan_set_path", ctypes.c_int, [_vp, _i32]),
+    ("dd_plan_set_wait_timeout", ctypes.c_int, [_vp, _i64]),
+    ("dd_plan_inject_fault", ctypes.c_int, [_vp, _i32]),
+    ("dd_plan_kernel_info", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
 ]
 
 PEAK_KINDS = {"fadd": 0, "fadd2": 1, "iadd": 2, "iadd3": 3, "imad": 4, "lop3": 5, "prmt": 6,
@@ -210,3 +214,23 @@ def dd_measure_add_peak(kind, device=0) -> tuple[float, float]:
     _check(load().dd_measure_add_peak(code, int(device), ctypes.addressof(a), ctypes.addressof(b)),
            "dd_measure_add_peak")
     return a.value, b.value
+
+
+def dd_plan_set_path(plan, path) -> None:
+    _check(load().dd_plan_set_path(plan, int(path)), "dd_plan_set_path")
+
+
+def dd_plan_set_wait_timeout(plan, timeout_ns) -> None:
+    _check(load().dd_plan_set_wait_timeout(plan, int(timeout_ns)), "dd_plan_set_wait_timeout")
+
+
+def dd_plan_inject_fault(plan, skip_copies) -> None:
+    _check(load().dd_plan_inject_fault(plan, int(skip_copies)), "dd_plan_inject_fault")
+
+
+def dd_plan_kernel_info(plan, block, pitch_elems) -> dict:
+    st, nd, sm = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    _check(load().dd_plan_kernel_info(plan, _addr(block), int(pitch_elems), ctypes.addressof(st),
+                                      ctypes.addressof(nd), ctypes.addressof(sm)),
+           "dd_plan_kernel_info")
+    return {"staged": bool(st.value), "dms_per_cta": nd.value, "smem_bytes": sm.value}

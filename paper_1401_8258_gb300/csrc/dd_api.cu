@@ -72,6 +72,12 @@ int take_device_status(dd_plan *p) {
 
 void destroy_plan(dd_plan *p) {
   if (!p) return;
+  if (p->quad) {
+    free_device(p->quad->d_recs);
+    free_device(p->quad->d_raw_meta);
+    delete p->quad;
+    p->quad = nullptr;
+  }
   free_device(p->d_delays);
   free_device(p->d_error);
   free_device(p->d_stats);
@@ -83,6 +89,27 @@ void destroy_plan(dd_plan *p) {
   free_device(p->d_cands);
   if (p->h_total) cudaFreeHost(p->h_total);
   delete p;
+}
+
+// Plan-time tables of the staged u8 kernel: 64 DM trials per CTA where the
+// delay patterns allow, else 32; none if neither fits (plain-load kernel).
+int setup_quad(dd_plan *p) {
+  ddq::Tables t;
+  int rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 16, &t);
+  if (rc != 0) rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 8, &t);
+  if (rc != 0) return DD_OK;
+  QuadDevice *q = new (std::nothrow) QuadDevice();
+  if (!q) return DD_ERR_OOM;
+  q->tables = std::move(t);
+  const size_t rb = q->tables.recs.size() * sizeof(int32_t);
+  const size_t mb = q->tables.raw_meta.size() * sizeof(int32_t);
+  cudaError_t e = cudaMalloc(&q->d_recs, rb);
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_raw_meta, mb);
+  if (e == cudaSuccess) e = cudaMemcpy(q->d_recs, q->tables.recs.data(), rb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
+  p->quad = q;  // freed with the plan on error
+  return cuda_status(e);
 }
 
 int validate_execute(const dd_plan *p, int64_t nsamp_in, int64_t pitch, int64_t *nsamp_out) {
@@ -148,6 +175,13 @@ extern "C" int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz,
     destroy_plan(p);
     return cuda_status(e);
   }
+  if (in_dtype == DD_U8) {
+    st = setup_quad(p);
+    if (st != DD_OK) {
+      destroy_plan(p);
+      return st;
+    }
+  }
   *out = p;
   return DD_OK;
 }
@@ -194,8 +228,10 @@ extern "C" int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64
   DeviceScope scope(p->device);
   if (!scope.ok()) return DD_ERR_CUDA;
   cudaError_t err = cudaSuccess;
-  const int n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out,
-                                              static_cast<cudaStream_t>(stream), &err);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int n = (p->path == 0 && ddk::quad_supported(p, block, pitch_elems))
+                    ? ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, s, &err)
+                    : ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
   return DD_OK;
@@ -305,4 +341,32 @@ extern "C" int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp
     if (e != cudaSuccess) return cuda_status(e);
   }
   return dst;
+}
+
+extern "C" int dd_plan_set_path(dd_plan *p, int32_t path) {
+  if (!p || path < 0 || path > 1) return DD_ERR_ARG;
+  p->path = path;
+  return DD_OK;
+}
+
+extern "C" int dd_plan_set_wait_timeout(dd_plan *p, int64_t timeout_ns) {
+  if (!p || timeout_ns < 1000) return DD_ERR_ARG;
+  p->wait_timeout_ns = static_cast<uint64_t>(timeout_ns);
+  return DD_OK;
+}
+
+extern "C" int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies) {
+  if (!p) return DD_ERR_ARG;
+  p->debug_skip_copies = skip_copies ? 1 : 0;
+  return DD_OK;
+}
+
+extern "C" int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems,
+                                   int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes) {
+  if (!p || !staged) return DD_ERR_ARG;
+  const bool q = p->path == 0 && block && ddk::quad_supported(p, block, pitch_elems);
+  *staged = q ? 1 : 0;
+  if (dms_per_cta) *dms_per_cta = p->quad ? p->quad->tables.nd_cta : 0;
+  if (smem_bytes) *smem_bytes = p->quad ? p->quad->tables.smem_bytes : 0;
+  return DD_OK;
 }

@@ -8,6 +8,14 @@
 #include <vector>
 
 #include "dd.h"
+#include "dd_quad.h"
+
+// Device copies of the staged quad kernel's plan-time tables.
+struct QuadDevice {
+  ddq::Tables tables;
+  int32_t *d_recs = nullptr;
+  int32_t *d_raw_meta = nullptr;
+};
 
 // Per-DM-row normalisation result written by the statistics kernels.
 struct dd_row_stats {
@@ -47,6 +55,11 @@ struct dd_plan {
   dd_candidate *d_cands = nullptr;
   size_t d_cands_cap = 0;
 
+  QuadDevice *quad = nullptr;       // staged u8 kernel tables (null: not applicable)
+  int32_t path = 0;                 // 0 = automatic, 1 = plain-load kernel only
+  uint64_t wait_timeout_ns = 2000000000ull;  // bound on every device-side wait
+  int32_t debug_skip_copies = 0;    // fault injection: staged kernel queues no copies
+
   int64_t launches = 0;
 };
 
@@ -60,6 +73,11 @@ inline int elem_size(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F
 // error in *err.
 int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                              void *out, cudaStream_t stream, cudaError_t *err);
+// Staged quad kernel (u8): needs the plan's quad tables, a 16-byte aligned
+// block and a pitch that is a multiple of 16 bytes.
+bool quad_supported(const dd_plan *p, const void *block, int64_t pitch);
+int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
+                           void *out, cudaStream_t stream, cudaError_t *err);
 
 // Detection passes over out[ndm][nsamp_out]; see dd_detect in dd.h.
 constexpr int kDetectChunk = 4096;  // samples per (row, chunk) work unit

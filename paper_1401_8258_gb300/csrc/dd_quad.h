@@ -1,0 +1,66 @@
+// dd_quad.h -- shape constants and plan-time tables of the staged quad
+// kernel for u8 input (internal to libdd).
+//
+// CTA tile: kDmGroups x nd_thr DM trials by kTimeTile output samples.
+// 8 warps = kDmGroups DM groups x kTimeGroups time groups; a thread owns
+// nd_thr trials x kTimesPerThread samples (sample = base + lane + 32*j).
+// Channels are processed in chunks of kQuadsPerChunk quads (4 channels each).
+//
+// Per (DM tile, chunk) record, int32 words:
+//   [0] number of pattern rows   [1] total 16-byte build items
+//   [2] quads in this chunk      [3] unused
+//   A[kQuadsPerChunk][nd_cta]    word offset, within the chunk's pattern-row
+//                                area, of the row word that holds output
+//                                sample 0 of the tile for that quad and trial
+//   rows[kQuadsPerChunk * kMaxPatterns][kRowWords]:
+//     {row word offset, items (= words/4), first item, quad,
+//      raw byte offset of channel k's first sample in its window slot (k=0..3),
+//      -1 for a padding channel}
+// raw_meta[tile][nchan_pad][2]: {window start relative to the tile's first
+// output sample (a multiple of 16), bytes needed (0 = padding channel)}.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+namespace ddq {
+
+constexpr int kThreads = 256;
+constexpr int kDmGroups = 4;
+constexpr int kTimeGroups = 2;
+constexpr int kTimesPerThread = 8;
+constexpr int kTimeTile = kTimeGroups * 32 * kTimesPerThread;  // 512
+constexpr int kQuadsPerChunk = 4;
+constexpr int kMaxPatterns = 8;
+constexpr int kRecHeader = 4;
+constexpr int kRowWords = 8;
+constexpr int kMaxSmem = 227 * 1024;
+
+constexpr int rec_words(int nd_cta) {
+  return (kRecHeader + kQuadsPerChunk * nd_cta + kQuadsPerChunk * kMaxPatterns * kRowWords + 3) / 4 * 4;
+}
+
+struct Tables {
+  int nd_thr = 0, nd_cta = 0;
+  int ntiles = 0, nquads = 0, nchan_pad = 0, nchunks = 0;
+  int rec_words = 0;
+  int32_t raw_stride = 0;   // bytes per channel window slot (multiple of 16)
+  int32_t prow_words = 0;   // largest pattern-row area of any chunk, in words
+  int32_t smem_bytes = 0;
+  std::vector<int32_t> recs;      // [ntiles][nchunks][rec_words]
+  std::vector<int32_t> raw_meta;  // [ntiles][nchan_pad][2]
+};
+
+// Shared-memory layout: two mbarriers (16 B), two records, two raw window
+// buffers (4*kQuadsPerChunk slots of raw_stride bytes), one pattern-row area.
+inline int32_t rec_bytes(const Tables &t) { return t.rec_words * 4; }
+inline int32_t raw_buf_bytes(const Tables &t) { return 4 * kQuadsPerChunk * t.raw_stride; }
+inline int32_t smem_bytes(const Tables &t) {
+  return 16 + 2 * rec_bytes(t) + 2 * raw_buf_bytes(t) + t.prow_words * 4;
+}
+
+// Returns 0 and fills *tb, or 1 if this geometry needs more than
+// kMaxPatterns patterns per quad and tile or more shared memory than a CTA has.
+int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, Tables *tb);
+
+}  // namespace ddq

@@ -1,0 +1,158 @@
+// dd_quad_plan.cpp -- plan-time tables of the staged quad kernel
+// (dd_dedisp_quad.cu) for u8 input.
+//
+// The kernel sums four channels per instruction (a byte dot product with
+// weights 1,1,1,1).  For that it needs, for each group of four adjacent
+// channels ("quad") and each DM trial of the CTA's tile, a shared-memory row
+// whose 32-bit word i holds the four channels' samples that the trial adds
+// at one output time.  Within a quad the delays of channels 1..3 relative to
+// channel 0 take only a few distinct values over a tile of trials (they are
+// differences of two rounded delays, Sec. 2.1.1), so one interleaved row per
+// distinct relative pattern serves every trial of the tile that has it.
+//
+// Everything here is integer bookkeeping on the plan's delay table; no part
+// of the dedispersion sum happens on the host.
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <vector>
+
+#include "dd_quad.h"
+
+namespace {
+
+inline int32_t round_up(int32_t v, int32_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+namespace ddq {
+
+int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, Tables *tb) {
+  const int nd_cta = kDmGroups * nd_thr;
+  Tables t;
+  t.nd_thr = nd_thr;
+  t.nd_cta = nd_cta;
+  t.ntiles = (ndm + nd_cta - 1) / nd_cta;
+  t.nquads = (nchan + 3) / 4;
+  t.nchan_pad = t.nquads * 4;
+  t.nchunks = (t.nquads + kQuadsPerChunk - 1) / kQuadsPerChunk;
+  t.rec_words = rec_words(nd_cta);
+  t.recs.assign(static_cast<size_t>(t.ntiles) * t.nchunks * t.rec_words, 0);
+  t.raw_meta.assign(static_cast<size_t>(t.ntiles) * t.nchan_pad * 2, 0);
+
+  // delay of (channel c, i-th trial of tile); padded channels reuse their
+  // quad's channel 0 (their data is forced to zero), padded trials reuse the
+  // last trial.
+  auto delay = [&](int tile, int c, int i) -> int32_t {
+    const int d = std::min(tile * nd_cta + i, ndm - 1);
+    const int cc = c < nchan ? c : (c & ~3);
+    return delays[static_cast<int64_t>(cc) * ndm + d];
+  };
+
+  int32_t raw_stride = 16;
+  int32_t prow_words = 4;
+  std::vector<int32_t> base(nd_cta), lo(4), hi(4);
+  for (int tile = 0; tile < t.ntiles; ++tile) {
+    // raw windows: channel c needs samples [t_cta + min delay, t_cta + T + max delay)
+    std::vector<int32_t> start(t.nchan_pad), need(t.nchan_pad);
+    for (int c = 0; c < t.nchan_pad; ++c) {
+      int32_t mn = delay(tile, c, 0), mx = mn;
+      for (int i = 1; i < nd_cta; ++i) {
+        mn = std::min(mn, delay(tile, c, i));
+        mx = std::max(mx, delay(tile, c, i));
+      }
+      start[c] = mn & ~15;
+      need[c] = c < nchan ? mx + kTimeTile - start[c] : 0;
+      int32_t *m = &t.raw_meta[(static_cast<size_t>(tile) * t.nchan_pad + c) * 2];
+      m[0] = start[c];
+      m[1] = need[c];
+      raw_stride = std::max(raw_stride, round_up(need[c], 16));
+    }
+    for (int ch = 0; ch < t.nchunks; ++ch) {
+      int32_t *rec = &t.recs[(static_cast<size_t>(tile) * t.nchunks + ch) * t.rec_words];
+      int32_t *A = rec + kRecHeader;
+      int32_t *rows = A + kQuadsPerChunk * nd_cta;
+      int nrows = 0, row_words = 0, items = 0;
+      const int q_lo = ch * kQuadsPerChunk;
+      const int nq = std::min(kQuadsPerChunk, t.nquads - q_lo);
+      for (int q = 0; q < nq; ++q) {
+        const int c0 = 4 * (q_lo + q);
+        // distinct relative patterns (delay of channel k minus channel 0)
+        std::vector<std::array<int32_t, 3>> pats;
+        std::vector<int> pid(nd_cta);
+        for (int i = 0; i < nd_cta; ++i) {
+          const int32_t d0 = delay(tile, c0, i);
+          std::array<int32_t, 3> rel{delay(tile, c0 + 1, i) - d0, delay(tile, c0 + 2, i) - d0,
+                                     delay(tile, c0 + 3, i) - d0};
+          auto it = std::find(pats.begin(), pats.end(), rel);
+          pid[i] = static_cast<int>(it - pats.begin());
+          if (it == pats.end()) pats.push_back(rel);
+        }
+        if (static_cast<int>(pats.size()) > kMaxPatterns) return 1;
+        for (size_t p = 0; p < pats.size(); ++p) {
+          int32_t bmin = INT32_MAX, bmax = INT32_MIN;
+          for (int i = 0; i < nd_cta; ++i)
+            if (pid[i] == static_cast<int>(p)) {
+              bmin = std::min(bmin, delay(tile, c0, i));
+              bmax = std::max(bmax, delay(tile, c0, i));
+            }
+          const int32_t len = round_up(kTimeTile + bmax - bmin, 4);
+          int32_t *r = rows + nrows * kRowWords;
+          r[0] = row_words;
+          r[1] = len / 4;
+          r[2] = items;
+          r[3] = q;
+          for (int k = 0; k < 4; ++k) {
+            const int c = c0 + k;
+            const int32_t e = k == 0 ? 0 : pats[p][k - 1];
+            if (c >= nchan) {
+              r[4 + k] = -1;
+            } else {
+              r[4 + k] = bmin + e - start[c];  // >= 0: bmin + e is a delay of channel c
+              raw_stride = std::max(raw_stride, round_up(r[4 + k] + len + 4, 16));
+            }
+          }
+          for (int i = 0; i < nd_cta; ++i)
+            if (pid[i] == static_cast<int>(p))
+              A[q * nd_cta + i] = row_words + delay(tile, c0, i) - bmin;
+          row_words += len;
+          items += len / 4;
+          ++nrows;
+        }
+      }
+      rec[0] = nrows;
+      rec[1] = items;
+      rec[2] = nq;
+      prow_words = std::max(prow_words, row_words);
+    }
+  }
+  t.raw_stride = raw_stride;
+  t.prow_words = prow_words;
+  t.smem_bytes = smem_bytes(t);
+  if (t.smem_bytes > kMaxSmem) return 1;
+  *tb = std::move(t);
+  return 0;
+}
+
+}  // namespace ddq
+
+// Host-side access to the tables for the CPU tests (not part of dd.h).
+// info[0..8) = {ok, nd_cta, ntiles, nchunks, nchan_pad, rec_words, raw_stride,
+// prow_words}; recs / raw_meta may be NULL (sizes come from info).
+extern "C" int ddi_quad_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int32_t nd_thr,
+                               int32_t *info, int32_t *recs, int32_t *raw_meta) {
+  ddq::Tables t;
+  const int rc = ddq::build_tables(delays, nchan, ndm, nd_thr, &t);
+  info[0] = rc == 0;
+  if (rc != 0) return 0;
+  info[1] = t.nd_cta;
+  info[2] = t.ntiles;
+  info[3] = t.nchunks;
+  info[4] = t.nchan_pad;
+  info[5] = t.rec_words;
+  info[6] = t.raw_stride;
+  info[7] = t.prow_words;
+  if (recs) std::copy(t.recs.begin(), t.recs.end(), recs);
+  if (raw_meta) std::copy(t.raw_meta.begin(), t.raw_meta.end(), raw_meta);
+  return 0;
+}

@@ -302,3 +302,69 @@ def test_process_host_matches_device_path():
 def test_add_pipe_probe_reports_positive_rates():
     ops, per_clk = dd._native.dd_measure_add_peak("fadd")
     assert ops > 1e12 and 16 <= per_clk <= 512
+
+
+# ------------------------------------------------------- staged u8 kernel
+
+STAGED_CASES = [
+    # (workload, nchan, ndm, extra samples past maxshift, pitch pad)
+    ("full_block_u8", 1024, 128, 1100, 0),
+    ("full_block_u8", 1021, 100, 700, 16),
+    ("full_block_u8", 1024, 2048, 3000, 0),
+    ("lband_f32", 4096, 96, 1500, 32),
+]
+
+
+@pytest.mark.parametrize("name,nchan,ndm,extra,pad", STAGED_CASES)
+def test_staged_kernel_matches_oracle_and_plain_kernel(name, nchan, ndm, extra, pad):
+    base = synth.workload(name)
+    wl = synth.scaled(base, nchan=nchan, ndm=ndm)
+    wl.chan_width_mhz = base.chan_width_mhz
+    wl.dtype = "u8"
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    nsamp = mx + extra
+    pitch = (nsamp + 15) // 16 * 16 + pad
+    rng = np.random.default_rng(77)
+    block = synth.random_block(rng, wl.nchan, nsamp, "u8", pitch)
+    block[:, nsamp:] = 0xEE
+    dblock = _to_dev(block)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as plan:
+        info = dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)
+        assert info["staged"], info
+        staged = plan.execute(dblock, nsamp_in=nsamp)
+        dd._native.dd_plan_set_path(plan.handle, 1)
+        assert not dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)["staged"]
+        plain = plan.execute(dblock, nsamp_in=nsamp)
+        dd.dd_sync(plan.handle)
+        s, p = staged.cpu().numpy(), plain.cpu().numpy()
+    assert np.array_equal(s, p)
+    rows = sorted(set([0, ndm - 1] + np.random.default_rng(1).integers(0, ndm, 12).tolist()))
+    ref = oracle.dedisperse(block, delays[:, rows], nsamp_out=s.shape[1], nsamp_in=nsamp)
+    assert np.array_equal(s[rows], ref)
+
+
+def test_staged_kernel_bounded_wait_reports_timeout_and_recovers():
+    """Fault injection: the staged kernel queues no copies, so its first
+    bounded wait (50 ms) runs out; the launch reports DD_ERR_DEVICE_TIMEOUT
+    through dd_sync, the context stays usable, and the next launch is exact."""
+    base = synth.workload("full_block_u8")
+    wl = synth.scaled(base, nchan=256, ndm=64)
+    wl.chan_width_mhz = base.chan_width_mhz
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    nsamp = mx + 2000
+    pitch = (nsamp + 15) // 16 * 16
+    block = synth.random_block(np.random.default_rng(3), wl.nchan, nsamp, "u8", pitch)
+    dblock = _to_dev(block)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as plan:
+        assert dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)["staged"]
+        dd._native.dd_plan_set_wait_timeout(plan.handle, 50_000_000)
+        dd._native.dd_plan_inject_fault(plan.handle, 1)
+        plan.execute(dblock, nsamp_in=nsamp)
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_sync(plan.handle)
+        assert e.value.status == -7
+        dd._native.dd_plan_inject_fault(plan.handle, 0)
+        out = plan.execute(dblock, nsamp_in=nsamp)
+        dd.dd_sync(plan.handle)
+        got = out.cpu().numpy()
+    assert np.array_equal(got, oracle.dedisperse(block, delays, nsamp_in=nsamp))

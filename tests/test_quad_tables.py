@@ -1,0 +1,152 @@
+"""CPU checks of the staged u8 kernel's plan-time tables.
+
+The tables (dd_quad_plan.cpp) tell the kernel which bytes to bulk-copy,
+how to interleave four channels into pattern rows and where each DM trial
+reads.  A numpy model of the kernel's three phases (copy, build, accumulate)
+runs on them here, asserting every shared-memory and global index against the
+buffer it addresses, and its result must equal the oracle bit for bit.
+Uncopied / unbuilt bytes hold garbage so that a read of them shows up.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import paper_1401_8258_gb300 as dd
+import synth
+
+T_TILE = 512
+QUADS_PER_CHUNK = 4
+REC_HEADER = 4
+ROW_WORDS = 8
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    dd.build()
+    oracle.build()
+
+
+def quad_tables(delays, nchan, ndm, nd_thr):
+    lib = ctypes.CDLL(dd._native.library_path())
+    fn = lib.ddi_quad_tables
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    delays = np.ascontiguousarray(delays, dtype=np.int32)
+    info = np.zeros(8, dtype=np.int32)
+    fn(delays.ctypes.data, nchan, ndm, nd_thr, info.ctypes.data, None, None)
+    if not info[0]:
+        return None
+    ok, nd_cta, ntiles, nchunks, nchan_pad, rec_words, raw_stride, prow_words = info.tolist()
+    recs = np.zeros(ntiles * nchunks * rec_words, dtype=np.int32)
+    meta = np.zeros(ntiles * nchan_pad * 2, dtype=np.int32)
+    fn(delays.ctypes.data, nchan, ndm, nd_thr, info.ctypes.data, recs.ctypes.data, meta.ctypes.data)
+    return dict(nd_cta=nd_cta, ntiles=ntiles, nchunks=nchunks, nchan_pad=nchan_pad,
+                rec_words=rec_words, raw_stride=raw_stride, prow_words=prow_words,
+                recs=recs.reshape(ntiles, nchunks, rec_words),
+                meta=meta.reshape(ntiles, nchan_pad, 2))
+
+
+def emulate(block, nsamp_in, tb, ndm, nsamp_out):
+    """Model of dd_dedisperse_quad_u8 on the tables; asserts all indexes."""
+    nchan, pitch = block.shape
+    nd = tb["nd_cta"]
+    rs = tb["raw_stride"]
+    pw = tb["prow_words"]
+    out = np.zeros((ndm, nsamp_out), dtype=np.int64)
+    ntt = (nsamp_out + T_TILE - 1) // T_TILE
+    garbage = np.uint8(0xA5)
+    for tile in range(tb["ntiles"]):
+        for tt in range(ntt):
+            t_cta = tt * T_TILE
+            acc = np.zeros((nd, T_TILE), dtype=np.int64)
+            for ch in range(tb["nchunks"]):
+                rec = tb["recs"][tile, ch]
+                raw = np.full((4 * QUADS_PER_CHUNK, rs), garbage, dtype=np.uint8)
+                for s in range(4 * QUADS_PER_CHUNK):
+                    c = ch * 4 * QUADS_PER_CHUNK + s
+                    if c >= tb["nchan_pad"]:
+                        continue
+                    start, need = tb["meta"][tile, c]
+                    if need <= 0:
+                        assert c >= nchan
+                        continue
+                    off = t_cta + start
+                    n = (need + 15) // 16 * 16
+                    if off + n > pitch:
+                        n = pitch - off
+                    assert off % 16 == 0 and n % 16 == 0 and 0 < n <= rs and off >= 0
+                    raw[s, :n] = block[c, off:off + n]
+                nrows, items, nq = rec[0], rec[1], rec[2]
+                rows = rec[REC_HEADER + QUADS_PER_CHUNK * nd:].reshape(-1, ROW_WORDS)[:nrows]
+                assert nrows <= QUADS_PER_CHUNK * 8
+                prow = np.full((pw, 4), garbage, dtype=np.uint8)
+                assert rows[:, 1].sum() == items
+                for row_off, nitems, first, q, *o in rows:
+                    assert row_off % 4 == 0 and row_off + 4 * nitems <= pw
+                    words = np.arange(4 * nitems)
+                    for k in range(4):
+                        if o[k] < 0:
+                            assert 4 * (ch * QUADS_PER_CHUNK + q) + k >= nchan
+                            prow[row_off + words, k] = 0
+                        else:
+                            pos = o[k] + words
+                            assert (pos[-1] & ~3) + 8 <= rs  # two aligned words read
+                            prow[row_off + words, k] = raw[4 * q + k, pos]
+                A = rec[REC_HEADER:REC_HEADER + QUADS_PER_CHUNK * nd].reshape(QUADS_PER_CHUNK, nd)
+                for q in range(nq):
+                    for i in range(nd):
+                        w = A[q, i] + np.arange(T_TILE)
+                        assert w[0] >= 0 and w[-1] < pw
+                        acc[i] += prow[w].astype(np.int64).sum(axis=1)
+            d0 = tile * nd
+            dn = min(nd, ndm - d0)
+            tn = min(T_TILE, nsamp_out - t_cta)
+            out[d0:d0 + dn, t_cta:t_cta + tn] = acc[:dn, :tn]
+    return out
+
+
+CASES = [
+    # (workload, nchan, ndm, extra samples past maxshift, pitch pad)
+    ("full_block_u8", 1024, 128, 1100, 0),
+    ("full_block_u8", 1021, 100, 700, 16),
+    ("lband_f32", 512, 70, 600, 48),
+]
+
+
+@pytest.mark.parametrize("name,nchan,ndm,extra,pad", CASES)
+def test_quad_kernel_model_matches_oracle(name, nchan, ndm, extra, pad):
+    wl = synth.scaled(synth.workload(name), nchan=nchan, ndm=ndm)
+    # keep the channel width of the full band so that pattern counts are realistic
+    wl.chan_width_mhz = synth.workload(name).chan_width_mhz
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    tb = quad_tables(delays, wl.nchan, wl.ndm, 16) or quad_tables(delays, wl.nchan, wl.ndm, 8)
+    assert tb is not None
+    nsamp = mx + extra
+    pitch = (nsamp + 15) // 16 * 16 + pad
+    rng = np.random.default_rng(12)
+    block = synth.random_block(rng, wl.nchan, nsamp, "u8", pitch)
+    block[:, nsamp:] = 0xEE  # row padding must never reach a valid output
+    nout = nsamp - mx
+    got = emulate(block, nsamp, tb, wl.ndm, nout)
+    ref = oracle.dedisperse(block, delays, nsamp_in=nsamp)
+    assert np.array_equal(got, ref)
+
+
+def test_tables_fit_shared_memory_for_the_workloads():
+    for name in ("full_block_u8", "lband_f32"):
+        wl = synth.workload(name)
+        delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+        tb = quad_tables(delays, wl.nchan, wl.ndm, 16)
+        assert tb is not None, name
+        smem = 16 + 2 * tb["rec_words"] * 4 + 2 * 16 * tb["raw_stride"] + tb["prow_words"] * 4
+        assert smem <= 227 * 1024
+
+
+def test_tables_refuse_geometries_with_too_many_patterns():
+    # 64 channels of 0.25 MHz at DM step 1: relative delays change at almost
+    # every trial, so the plan must fall back to the plain-load kernel
+    wl = synth.workload("single_beam_f32")
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    assert quad_tables(delays, wl.nchan, wl.ndm, 16) is None
