@@ -55,6 +55,7 @@ def parse():
                     help="target CPU time of the bounded oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-probes", action="store_true", help="skip the add-pipe probes")
     return ap.parse_args()
 
 
@@ -370,7 +371,7 @@ def run_ours(args):
     achieved = adds / t_kernel / 1e12
     peak = sms * LANES_PER_SM * smax * 1e6 / 1e12
     probes = {}
-    for kind in ("fadd", "fadd2", "iadd", "iadd3", "imad", "lop3", "prmt", "prmt_iadd",
+    for kind in () if args.no_probes else ("fadd", "fadd2", "iadd", "iadd3", "imad", "lop3", "prmt", "prmt_iadd",
                  "lop3_iadd", "fadd_f16", "hadd2"):
         try:
             ops, per_clk = dd._native.dd_measure_add_peak(kind, local)
