@@ -95,8 +95,8 @@ void destroy_plan(dd_plan *p) {
 // delay patterns allow, else 32; none if neither fits (plain-load kernel).
 int setup_quad(dd_plan *p) {
   ddq::Tables t;
-  int rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 16, &t);
-  if (rc != 0) rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 8, &t);
+  int rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 8, &t);
+  if (rc != 0) rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 4, &t);
   if (rc != 0) return DD_OK;
   QuadDevice *q = new (std::nothrow) QuadDevice();
   if (!q) return DD_ERR_OOM;
@@ -251,7 +251,7 @@ extern "C" int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float n
   if (st != DD_OK) return st;
   p->stats_valid = false;
   cudaError_t err = cudaSuccess;
-  int n = ddk::launch_stats(p, out, nsamp_out, s, &err);
+  int n = ddk::launch_stats(p, out, nsamp_out, nsigma, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
   n = ddk::launch_candidates(p, out, nsamp_out, nsigma, cands, capacity, s, &err);

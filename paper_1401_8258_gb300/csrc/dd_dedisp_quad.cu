@@ -5,14 +5,16 @@
 //
 // Data flow per CTA (one DM tile x one 512-sample time tile), per chunk of
 // 16 channels:
-//   1. one thread queues bulk copies (cp.async.bulk, the TMA engine) of each
+//   1. one warp queues bulk copies (cp.async.bulk, the TMA engine) of each
 //      channel's input window -- the "channel vector" of Sec. 2.2, sized by
 //      the largest and smallest delay of the tile -- plus the chunk's plan
-//      record into shared memory, signalling an mbarrier; the copies for the
-//      next chunk are in flight while this one is used (double buffer);
+//      record into shared memory, signalling an mbarrier; copies run three
+//      chunks ahead of the accumulation (triple-buffered windows);
 //   2. all threads interleave the four channels of every quad into pattern
 //      rows: word i of a row holds the four channels' samples that one
 //      relative-delay pattern adds at one output time (dd_quad_plan.cpp);
+//      rows of chunk k+1 are built while chunk k is accumulated (double
+//      buffer), with a single CTA barrier per chunk;
 //   3. every thread adds, for each of its DM trials and output samples, one
 //      32-bit row word with a 4-way byte dot product (dp4a, weights 1) into
 //      an int32 register accumulator: four channel-adds per instruction and
@@ -109,44 +111,87 @@ struct QuadArgs {
   int32_t nchan_pad;
   int32_t rec_words;
   int32_t raw_stride;
+  int32_t prow_words;
   int32_t *status;  // plan's sticky device status word
   uint64_t timeout_ns;
   int32_t skip_copies;  // test hook: queue nothing, so the first wait runs out
 };
 
-// Queue the bulk copies of chunk `ch` into buffer `buf` (one thread).
-__device__ void issue_chunk(const QuadArgs &a, int tile, int64_t t_cta, int ch, uint32_t bar,
-                            uint32_t rec_dst, uint32_t raw_dst) {
-  const int32_t *rec_src = a.recs + (static_cast<int64_t>(tile) * a.nchunks + ch) * a.rec_words;
-  const int32_t *meta = a.raw_meta + (static_cast<int64_t>(tile) * a.nchan_pad + ch * 4 * kQuadsPerChunk) * 2;
-  uint32_t len[4 * kQuadsPerChunk];
-  uint32_t total = static_cast<uint32_t>(a.rec_words) * 4;
-  for (int s = 0; s < 4 * kQuadsPerChunk; ++s) {
-    len[s] = 0;
-    if (ch * 4 * kQuadsPerChunk + s >= a.nchan_pad) continue;
-    const int32_t start = meta[2 * s], need = meta[2 * s + 1];
-    if (need <= 0) continue;
-    const int64_t off = t_cta + start;                       // multiple of 16
-    int64_t n = (static_cast<int64_t>(need) + 15) & ~static_cast<int64_t>(15);
-    if (off + n > a.pitch) n = a.pitch - off;                // stay inside the row
-    len[s] = static_cast<uint32_t>(n);
-    total += len[s];
+// Queue the bulk copies of chunk `ch` (its record and the raw windows of its
+// 4*kQuadsPerChunk channels) on mbarrier `bar`.  Called by all 32 lanes of
+// one warp: lane s < 16 owns channel slot s; lane 0 posts the byte count.
+__device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, int64_t t_cta,
+                            int ch, uint32_t bar, uint32_t rec_dst, uint32_t raw_dst, int lane) {
+  constexpr int kSlots = 4 * kQuadsPerChunk;
+  uint32_t len = 0;
+  const int c = ch * kSlots + lane;
+  if (lane < kSlots && c < a.nchan_pad) {
+    const int32_t start = meta_s[2 * c], need = meta_s[2 * c + 1];
+    if (need > 0) {
+      const int64_t off = t_cta + start;                     // multiple of 16
+      int64_t n = (static_cast<int64_t>(need) + 15) & ~static_cast<int64_t>(15);
+      if (off + n > a.pitch) n = a.pitch - off;              // stay inside the row
+      len = static_cast<uint32_t>(n);
+    }
   }
-  mbar_expect_tx(bar, total);
-  bulk_g2s(rec_dst, rec_src, static_cast<uint32_t>(a.rec_words) * 4, bar);
-  for (int s = 0; s < 4 * kQuadsPerChunk; ++s) {
-    if (len[s] == 0) continue;
-    const int c = ch * 4 * kQuadsPerChunk + s;
-    const uint8_t *src = a.block + static_cast<int64_t>(c) * a.pitch + t_cta + meta[2 * s];
-    bulk_g2s(raw_dst + s * a.raw_stride, src, len[s], bar);
+  uint32_t total = len;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
+  if (lane == 0) {
+    mbar_expect_tx(bar, total + static_cast<uint32_t>(a.rec_words) * 4);
+    const int32_t *rec_src = a.recs + (static_cast<int64_t>(tile) * a.nchunks + ch) * a.rec_words;
+    bulk_g2s(rec_dst, rec_src, static_cast<uint32_t>(a.rec_words) * 4, bar);
+  }
+  __syncwarp();
+  if (len > 0) {
+    const uint8_t *src = a.block + static_cast<int64_t>(c) * a.pitch + t_cta + meta_s[2 * c];
+    bulk_g2s(raw_dst + lane * a.raw_stride, src, len, bar);
+  }
+}
+
+// Every thread spins (bounded) on the mbarrier phase of chunk m.
+__device__ __forceinline__ bool wait_chunk(uint32_t bar0, int m, uint64_t timeout_ns) {
+  return mbar_wait_bounded(bar0 + 8 * (m % kRawStages), (m / kRawStages) & 1, timeout_ns);
+}
+
+// Interleave the four channels of every quad of a chunk into its pattern
+// rows: item it = 4 row words = 16 output samples of one (quad, pattern).
+__device__ __forceinline__ void build_rows(const int32_t *rec, uint32_t raw, uint32_t prow,
+                                           int32_t raw_stride, int rows_off, int tid) {
+  const int nrows = rec[0];
+  const int items = rec[1];
+  const int32_t *rows = rec + rows_off;
+  int r = 0;
+  for (int it = tid; it < items; it += kThreads) {
+    while (r + 1 < nrows && it >= rows[(r + 1) * kRowWords + 2]) ++r;
+    const int32_t *row = rows + r * kRowWords;
+    const int i4 = it - row[2];
+    const uint32_t slot = raw + static_cast<uint32_t>(row[3] * 4) * raw_stride;
+    uint32_t v[4];
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      const int32_t o = row[4 + ch];
+      if (o < 0) {
+        v[ch] = 0;
+      } else {
+        const uint32_t pos = static_cast<uint32_t>(o + 4 * i4);
+        const uint32_t w = slot + ch * raw_stride + (pos & ~3u);
+        v[ch] = prmt(lds32(w), lds32(w + 4), 0x3210u + 0x1111u * (pos & 3u));
+      }
+    }
+    // 4x4 byte transpose: word j = {ch0[j], ch1[j], ch2[j], ch3[j]}
+    const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
+    const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
+    sts128(prow + 4u * static_cast<uint32_t>(row[0] + 4 * i4), prmt(lo01, lo23, 0x5410u),
+           prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u), prmt(hi01, hi23, 0x7632u));
   }
 }
 
 template <int ND_THR>
 __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
+  constexpr int kRowsOff = kRecHeader + kQuadsPerChunk * ND_CTA;
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ int s_abort;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int tg = warp & (kTimeGroups - 1);
@@ -154,81 +199,74 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   const int tile = blockIdx.y;
   const int64_t t_cta = static_cast<int64_t>(blockIdx.x) * kTimeTile;
 
+  // shared-memory layout (dd_quad.h)
   const uint32_t bar0 = smem_addr(smem);
-  const uint32_t rec0 = bar0 + 16;
+  int32_t *meta_s = reinterpret_cast<int32_t *>(smem + 32);
+  const uint32_t meta_bytes = static_cast<uint32_t>((a.nchan_pad * 8 + 15) / 16 * 16);
   const uint32_t rec_bytes = static_cast<uint32_t>(a.rec_words) * 4;
-  const uint32_t raw0 = rec0 + 2 * rec_bytes;
+  const uint32_t rec_off = 32 + meta_bytes;
+  const uint32_t raw_off = rec_off + kRecStages * rec_bytes;
   const uint32_t raw_bytes = 4u * kQuadsPerChunk * static_cast<uint32_t>(a.raw_stride);
-  const uint32_t prow = raw0 + 2 * raw_bytes;
+  const uint32_t prow_off = raw_off + kRawStages * raw_bytes;
+  const uint32_t prow_bytes = static_cast<uint32_t>(a.prow_words) * 4;
+  auto rec_ptr = [&](int m) {
+    return reinterpret_cast<const int32_t *>(smem + rec_off + (m % kRecStages) * rec_bytes);
+  };
+  auto rec_addr = [&](int m) { return bar0 + rec_off + (m % kRecStages) * rec_bytes; };
+  auto raw_addr = [&](int m) { return bar0 + raw_off + (m % kRawStages) * raw_bytes; };
+  auto prow_addr = [&](int m) { return bar0 + prow_off + (m % kRowStages) * prow_bytes; };
 
+  // the tile's raw window table, and the pipeline's mbarriers
+  const int32_t *meta_g = a.raw_meta + static_cast<int64_t>(tile) * a.nchan_pad * 2;
+  for (int i = tid; i < 2 * a.nchan_pad; i += kThreads) meta_s[i] = meta_g[i];
   if (tid == 0) {
-    mbar_init(bar0, 1);
-    mbar_init(bar0 + 8, 1);
+    for (int b = 0; b < kRawStages; ++b) mbar_init(bar0 + 8 * b, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = -1;
-    if (!a.skip_copies) {
-      issue_chunk(a, tile, t_cta, 0, bar0, rec0, raw0);
-      if (a.nchunks > 1) issue_chunk(a, tile, t_cta, 1, bar0 + 8, rec0 + rec_bytes, raw0 + raw_bytes);
-    }
   }
   __syncthreads();
+  const int prefill = a.nchunks < kRawStages ? a.nchunks : kRawStages;
+  if (warp == 0 && !a.skip_copies)
+    for (int m = 0; m < prefill; ++m)
+      issue_chunk(a, meta_s, tile, t_cta, m, bar0 + 8 * m, rec_addr(m), raw_addr(m), lane);
 
   int acc[ND_THR][kTimesPerThread];
 #pragma unroll
   for (int i = 0; i < ND_THR; ++i)
 #pragma unroll
     for (int j = 0; j < kTimesPerThread; ++j) acc[i][j] = 0;
-
   const uint32_t my_word = static_cast<uint32_t>(tg * 32 * kTimesPerThread + lane);
 
-  for (int k = 0; k < a.nchunks; ++k) {
-    const int buf = k & 1;
-    const uint32_t bar = bar0 + 8 * buf;
-    const uint32_t parity = (k >> 1) & 1;
-    // thread 0 alone spins (bounded); the outcome is made CTA-uniform
-    if (tid == 0 && !mbar_wait_bounded(bar, parity, a.timeout_ns)) {
-      s_abort = k;
-      atomicExch(a.status, 1);
-    }
-    __syncthreads();
-    if (s_abort >= 0) break;
-    mbar_try_wait(bar, parity);  // phase complete: acquire the copied bytes
+  // chunk 0: wait, then interleave
+  int abort_at = -1;
+  if (__syncthreads_or(!wait_chunk(bar0, 0, a.timeout_ns))) {
+    abort_at = 0;
+  } else {
+    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), a.raw_stride, kRowsOff, tid);
+  }
 
-    // ---- build pattern rows from the raw channel windows
-    const int32_t *rec = reinterpret_cast<const int32_t *>(smem + 16 + buf * rec_bytes);
-    const int nrows = rec[0];
-    const int items = rec[1];
+  for (int k = 0; abort_at < 0 && k < a.nchunks; ++k) {
+    // one barrier per chunk: rows of chunk k are built, rows of k-1 consumed,
+    // and (if any) chunk k+1 has landed in shared memory
+    const bool ok = k + 1 >= a.nchunks || wait_chunk(bar0, k + 1, a.timeout_ns);
+    if (__syncthreads_or(!ok)) {
+      abort_at = k + 1;
+      break;
+    }
+    if (warp == 0 && k + kRawStages < a.nchunks && !a.skip_copies) {
+      // raw buffer of chunk k and record of chunk k-1 are free again
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      const int m = k + kRawStages;
+      issue_chunk(a, meta_s, tile, t_cta, m, bar0 + 8 * (m % kRawStages), rec_addr(m), raw_addr(m),
+                  lane);
+    }
+    if (k + 1 < a.nchunks)
+      build_rows(rec_ptr(k + 1), raw_addr(k + 1), prow_addr(k + 1), a.raw_stride, kRowsOff, tid);
+
+    // accumulate chunk k: four channels per dp4a
+    const int32_t *rec = rec_ptr(k);
     const int nq = rec[2];
-    const int32_t *rows = rec + kRecHeader + kQuadsPerChunk * ND_CTA;
-    const uint32_t raw = raw0 + buf * raw_bytes;
-    int r = 0;
-    for (int it = tid; it < items; it += kThreads) {
-      while (r + 1 < nrows && it >= rows[(r + 1) * kRowWords + 2]) ++r;
-      const int32_t *row = rows + r * kRowWords;
-      const int i4 = it - row[2];
-      const uint32_t slot = raw + static_cast<uint32_t>(row[3] * 4) * a.raw_stride;
-      uint32_t v[4];
-#pragma unroll
-      for (int ch = 0; ch < 4; ++ch) {
-        const int32_t o = row[4 + ch];
-        if (o < 0) {
-          v[ch] = 0;
-        } else {
-          const uint32_t pos = static_cast<uint32_t>(o + 4 * i4);
-          const uint32_t w = slot + ch * a.raw_stride + (pos & ~3u);
-          v[ch] = prmt(lds32(w), lds32(w + 4), 0x3210u + 0x1111u * (pos & 3u));
-        }
-      }
-      // 4x4 byte transpose: word j = {ch0[j], ch1[j], ch2[j], ch3[j]}
-      const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
-      const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
-      sts128(prow + 4u * static_cast<uint32_t>(row[0] + 4 * i4), prmt(lo01, lo23, 0x5410u),
-             prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u), prmt(hi01, hi23, 0x7632u));
-    }
-    __syncthreads();  // pattern rows ready
-
-    // ---- accumulate: four channels per dp4a
     const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
+    const uint32_t prow = prow_addr(k);
 #pragma unroll 1
     for (int q = 0; q < nq; ++q) {
       const int4 *A4 = reinterpret_cast<const int4 *>(A + q * ND_CTA);
@@ -247,20 +285,17 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
         }
       }
     }
-    __syncthreads();  // record, raw window and pattern rows of buffer `buf` consumed
-
-    if (tid == 0 && k + 2 < a.nchunks && !a.skip_copies) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue_chunk(a, tile, t_cta, k + 2, bar, rec0 + buf * rec_bytes, raw);
-    }
   }
 
-  if (s_abort >= 0) {
-    // wait (bounded) for this CTA's own copies still in flight: chunks k and
-    // k+1 were queued when chunk k's wait ran out; then leave
-    if (tid == 0 && !a.skip_copies) {
-      for (int m = s_abort; m < a.nchunks && m <= s_abort + 1; ++m)
-        mbar_wait_bounded(bar0 + 8 * (m & 1), (m >> 1) & 1, a.timeout_ns);
+  if (abort_at >= 0) {
+    // a bounded wait ran out: record it, wait (bounded) for this CTA's own
+    // copies still in flight, then leave.  Queued when chunk abort_at's wait
+    // ran out: chunks 0..2 (prologue) or up to abort_at + 1 (loop).
+    if (tid == 0) {
+      atomicExch(a.status, 1);
+      const int last = abort_at == 0 ? kRawStages - 1 : abort_at + 1;
+      if (!a.skip_copies)
+        for (int m = abort_at; m < a.nchunks && m <= last; ++m) wait_chunk(bar0, m, a.timeout_ns);
     }
     return;
   }
@@ -302,20 +337,21 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
   a.nchan_pad = q.tables.nchan_pad;
   a.rec_words = q.tables.rec_words;
   a.raw_stride = q.tables.raw_stride;
+  a.prow_words = q.tables.prow_words;
   a.status = p->d_error;
   a.timeout_ns = p->wait_timeout_ns;
   a.skip_copies = p->debug_skip_copies;
   const dim3 grid(static_cast<unsigned>((nsamp_out + kTimeTile - 1) / kTimeTile),
                   static_cast<unsigned>(q.tables.ntiles));
   const int smem = q.tables.smem_bytes;
-  if (q.tables.nd_thr == 16) {
-    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<16>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (*err == cudaSuccess) dd_dedisperse_quad_u8<16><<<grid, kThreads, smem, stream>>>(a);
-  } else {
+  if (q.tables.nd_thr == 8) {
     *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<8>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (*err == cudaSuccess) dd_dedisperse_quad_u8<8><<<grid, kThreads, smem, stream>>>(a);
+  } else {
+    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<4>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (*err == cudaSuccess) dd_dedisperse_quad_u8<4><<<grid, kThreads, smem, stream>>>(a);
   }
   if (*err == cudaSuccess) *err = cudaGetLastError();
   return *err == cudaSuccess ? 1 : -1;

@@ -5,8 +5,9 @@
 // Passes over D[ndm][n]:
 //   1. dd_stats_*      one CTA per DM row: exact integer sums (int32 rows) or
 //                      shifted double sums (float rows), then mean and rms;
+//                      and the row's candidate threshold (see dd_row_stats);
 //   2. dd_count        per (row, 4096-sample chunk): number of samples with
-//                      snr > nsigma;
+//                      snr > nsigma, tested as D >= threshold;
 //   3. dd_scan         exclusive prefix over the chunk counts in (row, chunk)
 //                      order, plus the total;
 //   4. dd_write        chunks with a non-zero count write their candidates
@@ -43,20 +44,69 @@ __device__ double u128_to_double_rn(unsigned __int128 v) {
   return scalbn(__ull2double_rn(top), drop);
 }
 
+__device__ __forceinline__ double snr_of(double v, double mean, double sigma) {
+  return __ddiv_rn(__dsub_rn(v, mean), sigma);
+}
+
+// Smallest int64 v in [INT32_MIN, INT32_MAX + 1] with snr_of(v) > thr, where
+// INT32_MAX + 1 stands for "none".  snr_of is monotone non-decreasing in v
+// (IEEE subtraction and division by sigma > 0 are monotone), so a bisection
+// finds the exact boundary of the double-precision decision.
+__device__ int64_t int_threshold(double mean, double sigma, double thr) {
+  int64_t lo = INT32_MIN, hi = static_cast<int64_t>(INT32_MAX) + 1;
+  if (snr_of(static_cast<double>(lo), mean, sigma) > thr) return lo;
+  while (hi - lo > 1) {  // pred(lo) false, pred(hi) true
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (snr_of(static_cast<double>(mid), mean, sigma) > thr) hi = mid; else lo = mid;
+  }
+  return hi;
+}
+
+// Order-preserving map of non-NaN floats onto uint32.
+__device__ __forceinline__ uint32_t float_order(float x) {
+  const uint32_t b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float order_float(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+
+// Smallest float x (-inf .. +inf) with snr_of((double)x) > thr; +inf passes
+// for any finite thr, so it bounds the search.
+__device__ float float_threshold(double mean, double sigma, double thr) {
+  uint32_t lo = float_order(-INFINITY), hi = float_order(INFINITY);
+  if (snr_of(-static_cast<double>(INFINITY), mean, sigma) > thr) return -INFINITY;
+  while (hi - lo > 1) {
+    const uint32_t mid = lo + (hi - lo) / 2;
+    if (snr_of(static_cast<double>(order_float(mid)), mean, sigma) > thr) hi = mid; else lo = mid;
+  }
+  return order_float(hi);
+}
+
 // One CTA per row: S1 = sum D, S2 = sum D^2 exactly, then
-//   mean = S1 / N,  rms = sqrt((double)(N*S2 - S1^2)) / N.
+//   mean = S1 / N,  rms = sqrt((double)(N*S2 - S1^2)) / N,
+// and the row's integer candidate threshold.
 __global__ void __launch_bounds__(kStatsThreads)
-dd_stats_i32(const int32_t *__restrict__ D, int64_t n, dd_row_stats *__restrict__ stats) {
+dd_stats_i32(const int32_t *__restrict__ D, int64_t n, double thr,
+             dd_row_stats *__restrict__ stats) {
   __shared__ long long s_s1[kStatsThreads];
   __shared__ unsigned __int128 s_s2[kStatsThreads];
   const int32_t *row = D + static_cast<int64_t>(blockIdx.x) * n;
   long long s1 = 0;
   unsigned __int128 s2 = 0;
+  unsigned long long part = 0;
+  int pending = 0;
   for (int64_t t = threadIdx.x; t < n; t += kStatsThreads) {
     const long long v = row[t];
     s1 += v;
-    s2 += static_cast<unsigned __int128>(static_cast<unsigned long long>(v * v));
+    part += static_cast<unsigned long long>(v * v);  // < 2^62 each
+    if (++pending == 3) {  // flush before two more terms could overflow 64 bits
+      s2 += part;
+      part = 0;
+      pending = 0;
+    }
   }
+  s2 += part;
   s_s1[threadIdx.x] = s1;
   s_s2[threadIdx.x] = s2;
   __syncthreads();
@@ -75,15 +125,20 @@ dd_stats_i32(const int32_t *__restrict__ D, int64_t n, dd_row_stats *__restrict_
     dd_row_stats st;
     st.mean = __ddiv_rn(__ll2double_rn(s_s1[0]), dn);
     st.sigma = __ddiv_rn(__dsqrt_rn(u128_to_double_rn(static_cast<unsigned __int128>(num))), dn);
+    st.any = st.sigma > 0.0;
+    st.ithr = st.any ? int_threshold(st.mean, st.sigma, thr) : static_cast<int64_t>(INT32_MAX) + 1;
+    st.fthr = INFINITY;
     stats[blockIdx.x] = st;
   }
 }
 
 // One CTA per row of f32 values: double sums of (x - K) with K the row's
 // first value, combined in a fixed tree order (deterministic), then
-//   mean = K + S1/N,  rms = sqrt(max(S2/N - (S1/N)^2, 0)).
+//   mean = K + S1/N,  rms = sqrt(max(S2/N - (S1/N)^2, 0)),
+// and the row's float candidate threshold.
 __global__ void __launch_bounds__(kStatsThreads)
-dd_stats_f32(const float *__restrict__ D, int64_t n, dd_row_stats *__restrict__ stats) {
+dd_stats_f32(const float *__restrict__ D, int64_t n, double thr,
+             dd_row_stats *__restrict__ stats) {
   __shared__ double s_s1[kStatsThreads];
   __shared__ double s_s2[kStatsThreads];
   const float *row = D + static_cast<int64_t>(blockIdx.x) * n;
@@ -111,24 +166,25 @@ dd_stats_f32(const float *__restrict__ D, int64_t n, dd_row_stats *__restrict__ 
     dd_row_stats st;
     st.mean = K + m1;
     st.sigma = sqrt(var > 0.0 ? var : 0.0);
+    st.any = st.sigma > 0.0;
+    st.fthr = st.any ? float_threshold(st.mean, st.sigma, thr) : INFINITY;
+    st.ithr = static_cast<int64_t>(INT32_MAX) + 1;
     stats[blockIdx.x] = st;
   }
 }
 
-template <typename T>
-__device__ __forceinline__ double as_double(T v) { return static_cast<double>(v); }
-
-// snr > nsigma in IEEE double: ((double)v - mean) / sigma, rows with sigma 0
-// never pass.
-__device__ __forceinline__ bool is_candidate(double v, dd_row_stats st, double thr) {
-  if (!(st.sigma > 0.0)) return false;
-  return __ddiv_rn(__dsub_rn(v, st.mean), st.sigma) > thr;
+// The candidate test, equivalent to snr > nsigma in IEEE double.
+__device__ __forceinline__ bool is_candidate(int32_t v, const dd_row_stats &st) {
+  return st.any && static_cast<int64_t>(v) >= st.ithr;
+}
+__device__ __forceinline__ bool is_candidate(float v, const dd_row_stats &st) {
+  return st.any && v >= st.fthr;
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kCountThreads)
 dd_count(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__restrict__ stats,
-         double thr, int64_t *__restrict__ counts) {
+         int64_t *__restrict__ counts) {
   __shared__ int s_cnt[kCountThreads / 32];
   const int d = blockIdx.y;
   const int chunk = blockIdx.x;
@@ -140,7 +196,7 @@ dd_count(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__
 #pragma unroll 4
   for (int k = 0; k < kPerThread; ++k) {
     const int64_t t = t0 + k * kCountThreads + threadIdx.x;
-    if (t < n) cnt += is_candidate(as_double(row[t]), st, thr) ? 1 : 0;
+    if (t < n) cnt += is_candidate(row[t], st) ? 1 : 0;
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -183,7 +239,7 @@ dd_scan(const int64_t *__restrict__ counts, int64_t m, int64_t *__restrict__ off
 template <typename T>
 __global__ void __launch_bounds__(kCountThreads)
 dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__restrict__ stats,
-         double thr, const int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
+         const int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
          dd_candidate *__restrict__ cands, int64_t capacity) {
   __shared__ int s_scan[kCountThreads];
   const int d = blockIdx.y;
@@ -200,7 +256,7 @@ dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__
 #pragma unroll
   for (int k = 0; k < kPerThread; ++k) {
     const int64_t t = t0 + k;
-    if (t < n && is_candidate(as_double(row[t]), st, thr)) mask |= 1u << k;
+    if (t < n && is_candidate(row[t], st)) mask |= 1u << k;
   }
   const int mine = __popc(mask);
   s_scan[threadIdx.x] = mine;
@@ -216,12 +272,12 @@ dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__
     const int k = __ffs(mask) - 1;
     mask &= mask - 1;
     if (idx < capacity) {
-      const double v = as_double(row[t0 + k]);
+      const double v = static_cast<double>(row[t0 + k]);
       dd_candidate c;
       c.dm_idx = d;
       c.t = static_cast<int32_t>(t0 + k);
       c.value = static_cast<float>(v);
-      c.snr = static_cast<float>(__ddiv_rn(__dsub_rn(v, st.mean), st.sigma));
+      c.snr = static_cast<float>(snr_of(v, st.mean, st.sigma));
       cands[idx] = c;
     }
     ++idx;
@@ -232,14 +288,15 @@ dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__
 
 namespace ddk {
 
-int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, cudaStream_t stream,
-                 cudaError_t *err) {
+int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                 cudaStream_t stream, cudaError_t *err) {
+  const double thr = static_cast<double>(nsigma);
   if (p->dtype == DD_U8)
     dd_stats_i32<<<p->ndm, kStatsThreads, 0, stream>>>(static_cast<const int32_t *>(out), nsamp_out,
-                                                        p->d_stats);
+                                                        thr, p->d_stats);
   else
     dd_stats_f32<<<p->ndm, kStatsThreads, 0, stream>>>(static_cast<const float *>(out), nsamp_out,
-                                                        p->d_stats);
+                                                        thr, p->d_stats);
   *err = cudaGetLastError();
   return *err == cudaSuccess ? 1 : -1;
 }
@@ -250,26 +307,26 @@ int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsig
   const int nchunks = static_cast<int>((nsamp_out + kDetectChunk - 1) / kDetectChunk);
   const int64_t m = static_cast<int64_t>(p->ndm) * nchunks;
   const dim3 grid(nchunks, p->ndm);
-  const double thr = static_cast<double>(nsigma);
+  (void)nsigma;  // already folded into the per-row thresholds
   int n = 0;
   if (p->dtype == DD_U8)
     dd_count<int32_t><<<grid, kCountThreads, 0, stream>>>(static_cast<const int32_t *>(out),
-                                                          nsamp_out, nchunks, p->d_stats, thr,
+                                                          nsamp_out, nchunks, p->d_stats,
                                                           p->d_counts);
   else
     dd_count<float><<<grid, kCountThreads, 0, stream>>>(static_cast<const float *>(out), nsamp_out,
-                                                        nchunks, p->d_stats, thr, p->d_counts);
+                                                        nchunks, p->d_stats, p->d_counts);
   ++n;
   dd_scan<<<1, kScanThreads, 0, stream>>>(p->d_counts, m, p->d_offsets, p->d_total);
   ++n;
   if (capacity > 0) {
     if (p->dtype == DD_U8)
       dd_write<int32_t><<<grid, kCountThreads, 0, stream>>>(
-          static_cast<const int32_t *>(out), nsamp_out, nchunks, p->d_stats, thr, p->d_counts,
+          static_cast<const int32_t *>(out), nsamp_out, nchunks, p->d_stats, p->d_counts,
           p->d_offsets, cands, capacity);
     else
       dd_write<float><<<grid, kCountThreads, 0, stream>>>(
-          static_cast<const float *>(out), nsamp_out, nchunks, p->d_stats, thr, p->d_counts,
+          static_cast<const float *>(out), nsamp_out, nchunks, p->d_stats, p->d_counts,
           p->d_offsets, cands, capacity);
     ++n;
   }

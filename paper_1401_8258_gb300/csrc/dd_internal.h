@@ -17,10 +17,18 @@ struct QuadDevice {
   int32_t *d_raw_meta = nullptr;
 };
 
-// Per-DM-row normalisation result written by the statistics kernels.
+// Per-DM-row normalisation result written by the statistics kernels, with
+// the row's candidate threshold for the current nsigma: the smallest value v
+// (an int32 for integer rows, a float for real rows) whose snr,
+// ((double)v - mean) / sigma in IEEE double, exceeds nsigma.  Because that
+// double expression is monotone in v, "v >= threshold" decides exactly what
+// "snr > nsigma" decides.
 struct dd_row_stats {
   double mean;
   double sigma;
+  int64_t ithr;  // integer rows: candidates are D >= ithr
+  float fthr;    // real rows: candidates are D >= fthr
+  int32_t any;   // 0: no sample of this row can be a candidate (sigma == 0)
 };
 
 struct dd_plan {
@@ -81,8 +89,8 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
 
 // Detection passes over out[ndm][nsamp_out]; see dd_detect in dd.h.
 constexpr int kDetectChunk = 4096;  // samples per (row, chunk) work unit
-int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, cudaStream_t stream,
-                 cudaError_t *err);
+int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                 cudaStream_t stream, cudaError_t *err);
 int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
                       dd_candidate *cands, int64_t capacity, cudaStream_t stream,
                       cudaError_t *err);

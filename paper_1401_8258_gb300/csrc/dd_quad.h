@@ -2,7 +2,7 @@
 // kernel for u8 input (internal to libdd).
 //
 // CTA tile: kDmGroups x nd_thr DM trials by kTimeTile output samples.
-// 8 warps = kDmGroups DM groups x kTimeGroups time groups; a thread owns
+// 16 warps = kDmGroups DM groups x kTimeGroups time groups; a thread owns
 // nd_thr trials x kTimesPerThread samples (sample = base + lane + 32*j).
 // Channels are processed in chunks of kQuadsPerChunk quads (4 channels each).
 //
@@ -25,8 +25,8 @@
 
 namespace ddq {
 
-constexpr int kThreads = 256;
-constexpr int kDmGroups = 4;
+constexpr int kThreads = 512;
+constexpr int kDmGroups = 8;
 constexpr int kTimeGroups = 2;
 constexpr int kTimesPerThread = 8;
 constexpr int kTimeTile = kTimeGroups * 32 * kTimesPerThread;  // 512
@@ -51,12 +51,22 @@ struct Tables {
   std::vector<int32_t> raw_meta;  // [ntiles][nchan_pad][2]
 };
 
-// Shared-memory layout: two mbarriers (16 B), two records, two raw window
-// buffers (4*kQuadsPerChunk slots of raw_stride bytes), one pattern-row area.
+// Pipeline depth: raw windows of chunks k+1 and k+2 are in flight while
+// chunk k+1 is interleaved and chunk k accumulated.
+constexpr int kRawStages = 3;
+constexpr int kRecStages = 4;
+constexpr int kRowStages = 2;
+
+// Shared-memory layout: kRawStages mbarriers (32 B reserved), the tile's raw
+// window table (nchan_pad x 2 int32), kRecStages records, kRawStages raw
+// window buffers (4*kQuadsPerChunk slots of raw_stride bytes), kRowStages
+// pattern-row areas.
 inline int32_t rec_bytes(const Tables &t) { return t.rec_words * 4; }
 inline int32_t raw_buf_bytes(const Tables &t) { return 4 * kQuadsPerChunk * t.raw_stride; }
+inline int32_t meta_bytes(const Tables &t) { return (t.nchan_pad * 8 + 15) / 16 * 16; }
 inline int32_t smem_bytes(const Tables &t) {
-  return 16 + 2 * rec_bytes(t) + 2 * raw_buf_bytes(t) + t.prow_words * 4;
+  return 32 + meta_bytes(t) + kRecStages * rec_bytes(t) + kRawStages * raw_buf_bytes(t) +
+         kRowStages * t.prow_words * 4;
 }
 
 // Returns 0 and fills *tb, or 1 if this geometry needs more than

@@ -137,8 +137,8 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
 }  // namespace ddq
 
 // Host-side access to the tables for the CPU tests (not part of dd.h).
-// info[0..8) = {ok, nd_cta, ntiles, nchunks, nchan_pad, rec_words, raw_stride,
-// prow_words}; recs / raw_meta may be NULL (sizes come from info).
+// info[0..9) = {ok, nd_cta, ntiles, nchunks, nchan_pad, rec_words, raw_stride,
+// prow_words, smem_bytes}; recs / raw_meta may be NULL (sizes come from info).
 extern "C" int ddi_quad_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int32_t nd_thr,
                                int32_t *info, int32_t *recs, int32_t *raw_meta) {
   ddq::Tables t;
@@ -152,6 +152,7 @@ extern "C" int ddi_quad_tables(const int32_t *delays, int32_t nchan, int32_t ndm
   info[5] = t.rec_words;
   info[6] = t.raw_stride;
   info[7] = t.prow_words;
+  info[8] = t.smem_bytes;
   if (recs) std::copy(t.recs.begin(), t.recs.end(), recs);
   if (raw_meta) std::copy(t.raw_meta.begin(), t.raw_meta.end(), raw_meta);
   return 0;

@@ -34,16 +34,16 @@ def quad_tables(delays, nchan, ndm, nd_thr):
     fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     delays = np.ascontiguousarray(delays, dtype=np.int32)
-    info = np.zeros(8, dtype=np.int32)
+    info = np.zeros(9, dtype=np.int32)
     fn(delays.ctypes.data, nchan, ndm, nd_thr, info.ctypes.data, None, None)
     if not info[0]:
         return None
-    ok, nd_cta, ntiles, nchunks, nchan_pad, rec_words, raw_stride, prow_words = info.tolist()
+    ok, nd_cta, ntiles, nchunks, nchan_pad, rec_words, raw_stride, prow_words, smem = info.tolist()
     recs = np.zeros(ntiles * nchunks * rec_words, dtype=np.int32)
     meta = np.zeros(ntiles * nchan_pad * 2, dtype=np.int32)
     fn(delays.ctypes.data, nchan, ndm, nd_thr, info.ctypes.data, recs.ctypes.data, meta.ctypes.data)
     return dict(nd_cta=nd_cta, ntiles=ntiles, nchunks=nchunks, nchan_pad=nchan_pad,
-                rec_words=rec_words, raw_stride=raw_stride, prow_words=prow_words,
+                rec_words=rec_words, raw_stride=raw_stride, prow_words=prow_words, smem=smem,
                 recs=recs.reshape(ntiles, nchunks, rec_words),
                 meta=meta.reshape(ntiles, nchan_pad, 2))
 
@@ -121,7 +121,7 @@ def test_quad_kernel_model_matches_oracle(name, nchan, ndm, extra, pad):
     # keep the channel width of the full band so that pattern counts are realistic
     wl.chan_width_mhz = synth.workload(name).chan_width_mhz
     delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
-    tb = quad_tables(delays, wl.nchan, wl.ndm, 16) or quad_tables(delays, wl.nchan, wl.ndm, 8)
+    tb = quad_tables(delays, wl.nchan, wl.ndm, 8) or quad_tables(delays, wl.nchan, wl.ndm, 4)
     assert tb is not None
     nsamp = mx + extra
     pitch = (nsamp + 15) // 16 * 16 + pad
@@ -138,10 +138,11 @@ def test_tables_fit_shared_memory_for_the_workloads():
     for name in ("full_block_u8", "lband_f32"):
         wl = synth.workload(name)
         delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
-        tb = quad_tables(delays, wl.nchan, wl.ndm, 16)
-        assert tb is not None, name
-        smem = 16 + 2 * tb["rec_words"] * 4 + 2 * 16 * tb["raw_stride"] + tb["prow_words"] * 4
-        assert smem <= 227 * 1024
+        tb = quad_tables(delays, wl.nchan, wl.ndm, 8)
+        assert tb is not None and tb["nd_cta"] == 64, name
+        meta = (tb["nchan_pad"] * 8 + 15) // 16 * 16
+        smem = 32 + meta + 4 * tb["rec_words"] * 4 + 3 * 16 * tb["raw_stride"] + 2 * tb["prow_words"] * 4
+        assert smem == tb["smem"] <= 227 * 1024
 
 
 def test_tables_refuse_geometries_with_too_many_patterns():
@@ -149,4 +150,5 @@ def test_tables_refuse_geometries_with_too_many_patterns():
     # every trial, so the plan must fall back to the plain-load kernel
     wl = synth.workload("single_beam_f32")
     delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
-    assert quad_tables(delays, wl.nchan, wl.ndm, 16) is None
+    assert quad_tables(delays, wl.nchan, wl.ndm, 8) is None
+    assert quad_tables(delays, wl.nchan, wl.ndm, 4) is None
