@@ -86,6 +86,33 @@ __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
   return v;
 }
 
+// Shared load with a compile-time byte offset folded into the instruction.
+template <int OFF>
+__device__ __forceinline__ uint32_t lds32_off(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1+%2];" : "=r"(v) : "r"(addr), "n"(OFF));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t dp4a_ones(uint32_t a, uint32_t acc) {
+  uint32_t r;
+  asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(0x01010101u), "r"(acc));
+  return r;
+}
+
+template <int J>
+struct Acc8 {
+  // acc[j] += dp4a(word at base + 128 j) for j = J..7
+  static __device__ __forceinline__ void run(int (&acc)[kTimesPerThread], uint32_t base) {
+    acc[J] = static_cast<int>(dp4a_ones(lds32_off<128 * J>(base), static_cast<uint32_t>(acc[J])));
+    Acc8<J + 1>::run(acc, base);
+  }
+};
+template <>
+struct Acc8<kTimesPerThread> {
+  static __device__ __forceinline__ void run(int (&)[kTimesPerThread], uint32_t) {}
+};
+
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
                                        uint32_t d) {
   asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(a), "r"(b), "r"(c),
@@ -155,34 +182,38 @@ __device__ __forceinline__ bool wait_chunk(uint32_t bar0, int m, uint64_t timeou
 }
 
 // Interleave the four channels of every quad of a chunk into its pattern
-// rows: item it = 4 row words = 16 output samples of one (quad, pattern).
+// rows.  One item = 4 row words = 16 output samples of one (quad, pattern);
+// a segment = up to 32 consecutive items of one row, one per lane, so the
+// row descriptor is a broadcast read per warp.
 __device__ __forceinline__ void build_rows(const int32_t *rec, uint32_t raw, uint32_t prow,
-                                           int32_t raw_stride, int rows_off, int tid) {
-  const int nrows = rec[0];
-  const int items = rec[1];
+                                           int32_t raw_stride, int rows_off, int segs_off,
+                                           int warp, int lane) {
+  const int nsegs = rec[3];
   const int32_t *rows = rec + rows_off;
-  int r = 0;
-  for (int it = tid; it < items; it += kThreads) {
-    while (r + 1 < nrows && it >= rows[(r + 1) * kRowWords + 2]) ++r;
-    const int32_t *row = rows + r * kRowWords;
-    const int i4 = it - row[2];
-    const uint32_t slot = raw + static_cast<uint32_t>(row[3] * 4) * raw_stride;
+  const int32_t *segs = rec + segs_off;
+  for (int sg = warp; sg < nsegs; sg += kThreads / 32) {
+    const uint32_t sd = static_cast<uint32_t>(segs[sg]);
+    const int4 ra = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[0];
+    const int4 rb = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[1];
+    const int i4 = static_cast<int>(sd & 0xffffu) + lane;
+    if (i4 >= ra.y) continue;  // ra = {row word offset, items, first item, quad}
+    const uint32_t slot = raw + static_cast<uint32_t>(ra.w * 4) * raw_stride;
+    const int o[4] = {rb.x, rb.y, rb.z, rb.w};
     uint32_t v[4];
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
-      const int32_t o = row[4 + ch];
-      if (o < 0) {
+      if (o[ch] < 0) {
         v[ch] = 0;
       } else {
-        const uint32_t pos = static_cast<uint32_t>(o + 4 * i4);
+        const uint32_t pos = static_cast<uint32_t>(o[ch] + 4 * i4);
         const uint32_t w = slot + ch * raw_stride + (pos & ~3u);
-        v[ch] = prmt(lds32(w), lds32(w + 4), 0x3210u + 0x1111u * (pos & 3u));
+        v[ch] = prmt(lds32(w), lds32_off<4>(w), 0x3210u + 0x1111u * (pos & 3u));
       }
     }
     // 4x4 byte transpose: word j = {ch0[j], ch1[j], ch2[j], ch3[j]}
     const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
     const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
-    sts128(prow + 4u * static_cast<uint32_t>(row[0] + 4 * i4), prmt(lo01, lo23, 0x5410u),
+    sts128(prow + 4u * static_cast<uint32_t>(ra.x + 4 * i4), prmt(lo01, lo23, 0x5410u),
            prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u), prmt(hi01, hi23, 0x7632u));
   }
 }
@@ -190,7 +221,8 @@ __device__ __forceinline__ void build_rows(const int32_t *rec, uint32_t raw, uin
 template <int ND_THR>
 __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
-  constexpr int kRowsOff = kRecHeader + kQuadsPerChunk * ND_CTA;
+  constexpr int kRowsOff = rows_offset(ND_CTA);
+  constexpr int kSegsOff = segs_offset(ND_CTA);
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -241,7 +273,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   if (__syncthreads_or(!wait_chunk(bar0, 0, a.timeout_ns))) {
     abort_at = 0;
   } else {
-    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), a.raw_stride, kRowsOff, tid);
+    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), a.raw_stride, kRowsOff, kSegsOff, warp, lane);
   }
 
   for (int k = 0; abort_at < 0 && k < a.nchunks; ++k) {
@@ -260,7 +292,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
                   lane);
     }
     if (k + 1 < a.nchunks)
-      build_rows(rec_ptr(k + 1), raw_addr(k + 1), prow_addr(k + 1), a.raw_stride, kRowsOff, tid);
+      build_rows(rec_ptr(k + 1), raw_addr(k + 1), prow_addr(k + 1), a.raw_stride, kRowsOff,
+                 kSegsOff, warp, lane);
 
     // accumulate chunk k: four channels per dp4a
     const int32_t *rec = rec_ptr(k);
@@ -275,14 +308,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
         const int4 a4 = A4[i4];
         const int off[4] = {a4.x, a4.y, a4.z, a4.w};
 #pragma unroll
-        for (int ii = 0; ii < 4; ++ii) {
-          const int i = 4 * i4 + ii;
-          const uint32_t base = prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word);
-#pragma unroll
-          for (int j = 0; j < kTimesPerThread; ++j)
-            acc[i][j] = static_cast<int>(
-                __dp4a(lds32(base + 128u * j), 0x01010101u, static_cast<uint32_t>(acc[i][j])));
-        }
+        for (int ii = 0; ii < 4; ++ii)
+          Acc8<0>::run(acc[4 * i4 + ii], prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word));
       }
     }
   }

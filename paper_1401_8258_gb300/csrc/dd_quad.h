@@ -8,7 +8,7 @@
 //
 // Per (DM tile, chunk) record, int32 words:
 //   [0] number of pattern rows   [1] total 16-byte build items
-//   [2] quads in this chunk      [3] unused
+//   [2] quads in this chunk      [3] number of build segments
 //   A[kQuadsPerChunk][nd_cta]    word offset, within the chunk's pattern-row
 //                                area, of the row word that holds output
 //                                sample 0 of the tile for that quad and trial
@@ -16,12 +16,20 @@
 //     {row word offset, items (= words/4), first item, quad,
 //      raw byte offset of channel k's first sample in its window slot (k=0..3),
 //      -1 for a padding channel}
+//   segs[kMaxSegments]: (row << 16) | first item -- the build work split into
+//     runs of at most 32 items of one row, one warp-wide step each
 // raw_meta[tile][nchan_pad][2]: {window start relative to the tile's first
 // output sample (a multiple of 16), bytes needed (0 = padding channel)}.
 #pragma once
 
 #include <cstdint>
 #include <vector>
+
+#ifdef __CUDACC__
+#define DDQ_HD __host__ __device__
+#else
+#define DDQ_HD
+#endif
 
 namespace ddq {
 
@@ -34,11 +42,14 @@ constexpr int kQuadsPerChunk = 4;
 constexpr int kMaxPatterns = 8;
 constexpr int kRecHeader = 4;
 constexpr int kRowWords = 8;
+constexpr int kMaxSegments = 256;
 constexpr int kMaxSmem = 227 * 1024;
 
-constexpr int rec_words(int nd_cta) {
-  return (kRecHeader + kQuadsPerChunk * nd_cta + kQuadsPerChunk * kMaxPatterns * kRowWords + 3) / 4 * 4;
+DDQ_HD constexpr int rows_offset(int nd_cta) { return kRecHeader + kQuadsPerChunk * nd_cta; }
+DDQ_HD constexpr int segs_offset(int nd_cta) {
+  return rows_offset(nd_cta) + kQuadsPerChunk * kMaxPatterns * kRowWords;
 }
+DDQ_HD constexpr int rec_words(int nd_cta) { return (segs_offset(nd_cta) + kMaxSegments + 3) / 4 * 4; }
 
 struct Tables {
   int nd_thr = 0, nd_cta = 0;

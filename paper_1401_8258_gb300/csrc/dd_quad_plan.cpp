@@ -71,7 +71,9 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     for (int ch = 0; ch < t.nchunks; ++ch) {
       int32_t *rec = &t.recs[(static_cast<size_t>(tile) * t.nchunks + ch) * t.rec_words];
       int32_t *A = rec + kRecHeader;
-      int32_t *rows = A + kQuadsPerChunk * nd_cta;
+      int32_t *rows = rec + rows_offset(nd_cta);
+      int32_t *segs = rec + segs_offset(nd_cta);
+      int nsegs = 0;
       int nrows = 0, row_words = 0, items = 0;
       const int q_lo = ch * kQuadsPerChunk;
       const int nq = std::min(kQuadsPerChunk, t.nquads - q_lo);
@@ -115,6 +117,10 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
           for (int i = 0; i < nd_cta; ++i)
             if (pid[i] == static_cast<int>(p))
               A[q * nd_cta + i] = row_words + delay(tile, c0, i) - bmin;
+          for (int first = 0; first < len / 4; first += 32) {
+            if (nsegs == kMaxSegments || first > 0xffff) return 1;
+            segs[nsegs++] = (nrows << 16) | first;
+          }
           row_words += len;
           items += len / 4;
           ++nrows;
@@ -123,6 +129,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
       rec[0] = nrows;
       rec[1] = items;
       rec[2] = nq;
+      rec[3] = nsegs;
       prow_words = std::max(prow_words, row_words);
     }
   }
