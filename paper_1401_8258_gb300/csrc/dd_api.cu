@@ -95,8 +95,8 @@ void destroy_plan(dd_plan *p) {
 // delay patterns allow, else 32; none if neither fits (plain-load kernel).
 int setup_quad(dd_plan *p) {
   ddq::Tables t;
-  int rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 8, &t);
-  if (rc != 0) rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, 4, &t);
+  int rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddq::kNdThr, &t);
+  if (rc != 0) rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddq::kNdThr / 2, &t);
   if (rc != 0) return DD_OK;
   QuadDevice *q = new (std::nothrow) QuadDevice();
   if (!q) return DD_ERR_OOM;

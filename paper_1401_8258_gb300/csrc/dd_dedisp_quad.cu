@@ -54,6 +54,15 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 
 __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   uint32_t ok;
+#ifdef DDQ_SUSPEND_NS
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "n"(DDQ_SUSPEND_NS)
+      : "memory");
+#else
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
@@ -61,6 +70,7 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
       : "=r"(ok)
       : "r"(bar), "r"(parity)
       : "memory");
+#endif
   return ok != 0;
 }
 
@@ -371,14 +381,14 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
   const dim3 grid(static_cast<unsigned>((nsamp_out + kTimeTile - 1) / kTimeTile),
                   static_cast<unsigned>(q.tables.ntiles));
   const int smem = q.tables.smem_bytes;
-  if (q.tables.nd_thr == 8) {
-    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<8>,
+  if (q.tables.nd_thr == kNdThr) {
+    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<kNdThr>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (*err == cudaSuccess) dd_dedisperse_quad_u8<8><<<grid, kThreads, smem, stream>>>(a);
+    if (*err == cudaSuccess) dd_dedisperse_quad_u8<kNdThr><<<grid, kThreads, smem, stream>>>(a);
   } else {
-    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<4>,
+    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<kNdThr / 2>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (*err == cudaSuccess) dd_dedisperse_quad_u8<4><<<grid, kThreads, smem, stream>>>(a);
+    if (*err == cudaSuccess) dd_dedisperse_quad_u8<kNdThr / 2><<<grid, kThreads, smem, stream>>>(a);
   }
   if (*err == cudaSuccess) *err = cudaGetLastError();
   return *err == cudaSuccess ? 1 : -1;

@@ -33,12 +33,29 @@
 
 namespace ddq {
 
-constexpr int kThreads = 512;
-constexpr int kDmGroups = 8;
-constexpr int kTimeGroups = 2;
-constexpr int kTimesPerThread = 8;
-constexpr int kTimeTile = kTimeGroups * 32 * kTimesPerThread;  // 512
-constexpr int kQuadsPerChunk = 4;
+// Tile shape; the DDQ_* macros exist only to build shape variants for tuning.
+#ifndef DDQ_DM_GROUPS
+#define DDQ_DM_GROUPS 8
+#endif
+#ifndef DDQ_TIME_GROUPS
+#define DDQ_TIME_GROUPS 2
+#endif
+#ifndef DDQ_TIMES_PER_THREAD
+#define DDQ_TIMES_PER_THREAD 8
+#endif
+#ifndef DDQ_QUADS_PER_CHUNK
+#define DDQ_QUADS_PER_CHUNK 4
+#endif
+#ifndef DDQ_ND_THR
+#define DDQ_ND_THR 8
+#endif
+constexpr int kDmGroups = DDQ_DM_GROUPS;
+constexpr int kTimeGroups = DDQ_TIME_GROUPS;
+constexpr int kThreads = 32 * kDmGroups * kTimeGroups;                // 512
+constexpr int kTimesPerThread = DDQ_TIMES_PER_THREAD;
+constexpr int kTimeTile = kTimeGroups * 32 * kTimesPerThread;         // 512
+constexpr int kQuadsPerChunk = DDQ_QUADS_PER_CHUNK;
+constexpr int kNdThr = DDQ_ND_THR;  // DM trials per thread of the wide variant
 constexpr int kMaxPatterns = 8;
 constexpr int kRecHeader = 4;
 constexpr int kRowWords = 8;
