@@ -192,40 +192,62 @@ __device__ __forceinline__ bool wait_chunk(uint32_t bar0, int m, uint64_t timeou
 }
 
 // Interleave the four channels of every quad of a chunk into its pattern
-// rows.  One item = 4 row words = 16 output samples of one (quad, pattern);
-// a segment = up to 32 consecutive items of one row, one per lane, so the
-// row descriptor is a broadcast read per warp.
+// rows.  One item = 4 row words = 4 output samples x 4 channels of one
+// (quad, pattern); a segment = up to 32 consecutive items of one row, one per
+// lane, so the row descriptor is a broadcast read per warp.  Channel k of the
+// row starts at byte o_k of its raw window: item i needs bytes o_k + 4i ..
+// o_k + 4i + 3, i.e. the aligned words at (o_k & ~3) + 4i and the next one,
+// funnelled by the row-uniform byte selector of (o_k & 3).
+__device__ __forceinline__ void build_segment(const int32_t *rows, uint32_t sd, uint32_t raw,
+                                              uint32_t prow, int32_t raw_stride, int lane) {
+  const int4 ra = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[0];
+  const int4 rb = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[1];
+  const int i4 = static_cast<int>(sd & 0xffffu) + lane;
+  if (i4 >= ra.y) return;  // ra = {row word offset, items, first item, quad}
+  const uint32_t slot = raw + static_cast<uint32_t>(ra.w * 4) * raw_stride;
+  const int o[4] = {rb.x, rb.y, rb.z, rb.w};
+  uint32_t v[4];
+#pragma unroll
+  for (int ch = 0; ch < 4; ++ch) {
+    if (o[ch] < 0) {
+      v[ch] = 0;
+    } else {
+      const uint32_t w = slot + ch * raw_stride + static_cast<uint32_t>(o[ch] & ~3) + 4u * i4;
+      v[ch] = prmt(lds32(w), lds32_off<4>(w), 0x3210u + 0x1111u * static_cast<uint32_t>(o[ch] & 3));
+    }
+  }
+  // 4x4 byte transpose: word j = {ch0[j], ch1[j], ch2[j], ch3[j]}
+  const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
+  const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
+  sts128(prow + 4u * static_cast<uint32_t>(ra.x + 4 * i4), prmt(lo01, lo23, 0x5410u),
+         prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u), prmt(hi01, hi23, 0x7632u));
+}
+
+// This warp's segments m = m0, m0 + 1, ... < m1 of a chunk (segment index
+// warp + 16*m), two at a time so that their loads overlap.
 __device__ __forceinline__ void build_rows(const int32_t *rec, uint32_t raw, uint32_t prow,
                                            int32_t raw_stride, int rows_off, int segs_off,
-                                           int warp, int lane) {
+                                           int warp, int lane, int m0, int m1) {
+  constexpr int kWarps = kThreads / 32;
   const int nsegs = rec[3];
   const int32_t *rows = rec + rows_off;
   const int32_t *segs = rec + segs_off;
-  for (int sg = warp; sg < nsegs; sg += kThreads / 32) {
-    const uint32_t sd = static_cast<uint32_t>(segs[sg]);
-    const int4 ra = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[0];
-    const int4 rb = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[1];
-    const int i4 = static_cast<int>(sd & 0xffffu) + lane;
-    if (i4 >= ra.y) continue;  // ra = {row word offset, items, first item, quad}
-    const uint32_t slot = raw + static_cast<uint32_t>(ra.w * 4) * raw_stride;
-    const int o[4] = {rb.x, rb.y, rb.z, rb.w};
-    uint32_t v[4];
-#pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-      if (o[ch] < 0) {
-        v[ch] = 0;
-      } else {
-        const uint32_t pos = static_cast<uint32_t>(o[ch] + 4 * i4);
-        const uint32_t w = slot + ch * raw_stride + (pos & ~3u);
-        v[ch] = prmt(lds32(w), lds32_off<4>(w), 0x3210u + 0x1111u * (pos & 3u));
-      }
-    }
-    // 4x4 byte transpose: word j = {ch0[j], ch1[j], ch2[j], ch3[j]}
-    const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
-    const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
-    sts128(prow + 4u * static_cast<uint32_t>(ra.x + 4 * i4), prmt(lo01, lo23, 0x5410u),
-           prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u), prmt(hi01, hi23, 0x7632u));
+  for (int m = m0; m < m1; m += 2) {
+    const int s0 = warp + kWarps * m, s1 = s0 + kWarps;
+    const bool has1 = m + 1 < m1 && s1 < nsegs;
+    if (s0 >= nsegs) break;
+    const uint32_t sd0 = static_cast<uint32_t>(segs[s0]);
+    const uint32_t sd1 = has1 ? static_cast<uint32_t>(segs[s1]) : 0u;
+    build_segment(rows, sd0, raw, prow, raw_stride, lane);
+    if (has1) build_segment(rows, sd1, raw, prow, raw_stride, lane);
   }
+}
+
+// Segments a warp builds per chunk: ceil((nsegs - warp) / 16).
+__device__ __forceinline__ int warp_segments(const int32_t *rec, int warp) {
+  constexpr int kWarps = kThreads / 32;
+  const int nsegs = rec[3];
+  return nsegs > warp ? (nsegs - warp + kWarps - 1) / kWarps : 0;
 }
 
 template <int ND_THR>
@@ -283,7 +305,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   if (__syncthreads_or(!wait_chunk(bar0, 0, a.timeout_ns))) {
     abort_at = 0;
   } else {
-    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), a.raw_stride, kRowsOff, kSegsOff, warp, lane);
+    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), a.raw_stride, kRowsOff, kSegsOff, warp, lane,
+               0, warp_segments(rec_ptr(0), warp));
   }
 
   for (int k = 0; abort_at < 0 && k < a.nchunks; ++k) {
@@ -301,17 +324,25 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
       issue_chunk(a, meta_s, tile, t_cta, m, bar0 + 8 * (m % kRawStages), rec_addr(m), raw_addr(m),
                   lane);
     }
-    if (k + 1 < a.nchunks)
-      build_rows(rec_ptr(k + 1), raw_addr(k + 1), prow_addr(k + 1), a.raw_stride, kRowsOff,
-                 kSegsOff, warp, lane);
-
-    // accumulate chunk k: four channels per dp4a
+    // accumulate chunk k (four channels per dp4a) while building the rows
+    // of chunk k+1: this warp's build segments are spread over the quads
     const int32_t *rec = rec_ptr(k);
     const int nq = rec[2];
     const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
     const uint32_t prow = prow_addr(k);
+    const bool next = k + 1 < a.nchunks;
+    const int32_t *rec_n = rec_ptr(k + 1);
+    const int nseg_w = next ? warp_segments(rec_n, warp) : 0;
+    int m_done = 0;
 #pragma unroll 1
-    for (int q = 0; q < nq; ++q) {
+    for (int q = 0; q < kQuadsPerChunk; ++q) {
+      const int m_to = (nseg_w * (q + 1) + kQuadsPerChunk - 1) / kQuadsPerChunk;
+      if (m_to > m_done) {
+        build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), a.raw_stride, kRowsOff, kSegsOff,
+                   warp, lane, m_done, m_to);
+        m_done = m_to;
+      }
+      if (q >= nq) continue;
       const int4 *A4 = reinterpret_cast<const int4 *>(A + q * ND_CTA);
 #pragma unroll
       for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
