@@ -186,61 +186,59 @@ __device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, 
   }
 }
 
-// Every thread spins (bounded) on the mbarrier phase of chunk m.
+// Bounded spin on the mbarrier phase of chunk m.
 __device__ __forceinline__ bool wait_chunk(uint32_t bar0, int m, uint64_t timeout_ns) {
   return mbar_wait_bounded(bar0 + 8 * (m % kRawStages), (m / kRawStages) & 1, timeout_ns);
 }
 
+// CTA-uniform wait for chunk m: thread 0 alone spins (bounded), the others
+// wait at the barrier, which also makes the outcome uniform; after a
+// completed phase every thread acquires it with one try_wait.  Returns false
+// if the wait ran out.
+__device__ __forceinline__ bool cta_wait_chunk(uint32_t bar0, int m, uint64_t timeout_ns, int tid) {
+  const bool ok = tid != 0 || wait_chunk(bar0, m, timeout_ns);
+  if (__syncthreads_or(!ok)) return false;
+  mbar_try_wait(bar0 + 8 * (m % kRawStages), (m / kRawStages) & 1);
+  return true;
+}
+
 // Interleave the four channels of every quad of a chunk into its pattern
-// rows.  One item = 4 row words = 4 output samples x 4 channels of one
-// (quad, pattern); a segment = up to 32 consecutive items of one row, one per
-// lane, so the row descriptor is a broadcast read per warp.  Channel k of the
-// row starts at byte o_k of its raw window: item i needs bytes o_k + 4i ..
-// o_k + 4i + 3, i.e. the aligned words at (o_k & ~3) + 4i and the next one,
-// funnelled by the row-uniform byte selector of (o_k & 3).
-__device__ __forceinline__ void build_segment(const int32_t *rows, uint32_t sd, uint32_t raw,
-                                              uint32_t prow, int32_t raw_stride, int lane) {
-  const int4 ra = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[0];
-  const int4 rb = reinterpret_cast<const int4 *>(rows + (sd >> 16) * kRowWords)[1];
-  const int i4 = static_cast<int>(sd & 0xffffu) + lane;
-  if (i4 >= ra.y) return;  // ra = {row word offset, items, first item, quad}
-  const uint32_t slot = raw + static_cast<uint32_t>(ra.w * 4) * raw_stride;
-  const int o[4] = {rb.x, rb.y, rb.z, rb.w};
+// rows, one segment (a warp-wide step, dd_quad.h) at a time: lane l builds
+// item l, i.e. the row words of 4 output samples.  For channel k it reads the
+// aligned word at the segment's byte offset + 4l and the next one, and
+// funnels out the 4 samples with the segment's byte shift; a 4x4 byte
+// transpose turns the four channels' words into four row words.
+__device__ __forceinline__ void build_segment(const int32_t *sd, uint32_t raw, uint32_t prow,
+                                              int lane) {
+  const int4 d = *reinterpret_cast<const int4 *>(sd);
+  const uint32_t items = static_cast<uint32_t>(d.z) >> 20;
+  if (static_cast<uint32_t>(lane) >= items) return;
+  const uint32_t off[4] = {static_cast<uint32_t>(d.x) & 0xffffu, static_cast<uint32_t>(d.x) >> 16,
+                           static_cast<uint32_t>(d.y) & 0xffffu, static_cast<uint32_t>(d.y) >> 16};
   uint32_t v[4];
 #pragma unroll
   for (int ch = 0; ch < 4; ++ch) {
-    if (o[ch] < 0) {
-      v[ch] = 0;
-    } else {
-      const uint32_t w = slot + ch * raw_stride + static_cast<uint32_t>(o[ch] & ~3) + 4u * i4;
-      v[ch] = prmt(lds32(w), lds32_off<4>(w), 0x3210u + 0x1111u * static_cast<uint32_t>(o[ch] & 3));
-    }
+    const uint32_t sh = (static_cast<uint32_t>(d.w) >> (2 * ch)) & 3u;
+    const bool pad = off[ch] == 0xffffu;               // padding channel: zeros
+    const uint32_t w = raw + (pad ? 0u : off[ch]) + 4u * lane;  // always in bounds
+    const uint32_t x = prmt(lds32(w), lds32_off<4>(w), 0x3210u + 0x1111u * sh);
+    v[ch] = pad ? 0u : x;
   }
-  // 4x4 byte transpose: word j = {ch0[j], ch1[j], ch2[j], ch3[j]}
   const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
   const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
-  sts128(prow + 4u * static_cast<uint32_t>(ra.x + 4 * i4), prmt(lo01, lo23, 0x5410u),
-         prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u), prmt(hi01, hi23, 0x7632u));
+  sts128(prow + 4u * (static_cast<uint32_t>(d.z) & 0xfffffu) + 16u * lane,
+         prmt(lo01, lo23, 0x5410u), prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u),
+         prmt(hi01, hi23, 0x7632u));
 }
 
-// This warp's segments m = m0, m0 + 1, ... < m1 of a chunk (segment index
-// warp + 16*m), two at a time so that their loads overlap.
+// This warp's segments m = m0 .. m1-1 of a chunk (segment index warp + 16*m).
 __device__ __forceinline__ void build_rows(const int32_t *rec, uint32_t raw, uint32_t prow,
-                                           int32_t raw_stride, int rows_off, int segs_off,
-                                           int warp, int lane, int m0, int m1) {
+                                           int segs_off, int warp, int lane, int m0, int m1) {
   constexpr int kWarps = kThreads / 32;
-  const int nsegs = rec[3];
-  const int32_t *rows = rec + rows_off;
   const int32_t *segs = rec + segs_off;
-  for (int m = m0; m < m1; m += 2) {
-    const int s0 = warp + kWarps * m, s1 = s0 + kWarps;
-    const bool has1 = m + 1 < m1 && s1 < nsegs;
-    if (s0 >= nsegs) break;
-    const uint32_t sd0 = static_cast<uint32_t>(segs[s0]);
-    const uint32_t sd1 = has1 ? static_cast<uint32_t>(segs[s1]) : 0u;
-    build_segment(rows, sd0, raw, prow, raw_stride, lane);
-    if (has1) build_segment(rows, sd1, raw, prow, raw_stride, lane);
-  }
+#pragma unroll 2
+  for (int m = m0; m < m1; ++m)
+    build_segment(segs + (warp + kWarps * m) * kSegWords, raw, prow, lane);
 }
 
 // Segments a warp builds per chunk: ceil((nsegs - warp) / 16).
@@ -253,7 +251,6 @@ __device__ __forceinline__ int warp_segments(const int32_t *rec, int warp) {
 template <int ND_THR>
 __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
-  constexpr int kRowsOff = rows_offset(ND_CTA);
   constexpr int kSegsOff = segs_offset(ND_CTA);
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
@@ -302,18 +299,18 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
 
   // chunk 0: wait, then interleave
   int abort_at = -1;
-  if (__syncthreads_or(!wait_chunk(bar0, 0, a.timeout_ns))) {
+  if (!cta_wait_chunk(bar0, 0, a.timeout_ns, tid)) {
     abort_at = 0;
   } else {
-    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), a.raw_stride, kRowsOff, kSegsOff, warp, lane,
-               0, warp_segments(rec_ptr(0), warp));
+    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), kSegsOff, warp, lane, 0,
+               warp_segments(rec_ptr(0), warp));
   }
 
   for (int k = 0; abort_at < 0 && k < a.nchunks; ++k) {
     // one barrier per chunk: rows of chunk k are built, rows of k-1 consumed,
     // and (if any) chunk k+1 has landed in shared memory
-    const bool ok = k + 1 >= a.nchunks || wait_chunk(bar0, k + 1, a.timeout_ns);
-    if (__syncthreads_or(!ok)) {
+    if (k + 1 < a.nchunks ? !cta_wait_chunk(bar0, k + 1, a.timeout_ns, tid)
+                          : __syncthreads_or(0) != 0) {
       abort_at = k + 1;
       break;
     }
@@ -338,8 +335,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     for (int q = 0; q < kQuadsPerChunk; ++q) {
       const int m_to = (nseg_w * (q + 1) + kQuadsPerChunk - 1) / kQuadsPerChunk;
       if (m_to > m_done) {
-        build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), a.raw_stride, kRowsOff, kSegsOff,
-                   warp, lane, m_done, m_to);
+        build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), kSegsOff, warp, lane, m_done, m_to);
         m_done = m_to;
       }
       if (q >= nq) continue;

@@ -7,17 +7,19 @@
 // Channels are processed in chunks of kQuadsPerChunk quads (4 channels each).
 //
 // Per (DM tile, chunk) record, int32 words:
-//   [0] number of pattern rows   [1] total 16-byte build items
+//   [0] unused                   [1] unused
 //   [2] quads in this chunk      [3] number of build segments
 //   A[kQuadsPerChunk][nd_cta]    word offset, within the chunk's pattern-row
 //                                area, of the row word that holds output
 //                                sample 0 of the tile for that quad and trial
-//   rows[kQuadsPerChunk * kMaxPatterns][kRowWords]:
-//     {row word offset, items (= words/4), first item, quad,
-//      raw byte offset of channel k's first sample in its window slot (k=0..3),
-//      -1 for a padding channel}
-//   segs[kMaxSegments]: (row << 16) | first item -- the build work split into
-//     runs of at most 32 items of one row, one warp-wide step each
+//   segs[kMaxSegments][4]: one warp-wide build step each -- up to 32
+//     consecutive items (4 row words = 4 samples x 4 channels) of one
+//     pattern row; lane l builds item l:
+//     [0] raw-buffer byte offsets of channel 0 | channel 1 << 16, [1] of
+//         channels 2 | 3 << 16: the aligned word holding the channel's first
+//         sample of the segment (0xffff = padding channel, reads as zero);
+//     [2] row-area word offset of the segment's first item | items << 20;
+//     [3] byte shift (0..3) of channel k in bits 2k..2k+1.
 // raw_meta[tile][nchan_pad][2]: {window start relative to the tile's first
 // output sample (a multiple of 16), bytes needed (0 = padding channel)}.
 #pragma once
@@ -58,15 +60,14 @@ constexpr int kQuadsPerChunk = DDQ_QUADS_PER_CHUNK;
 constexpr int kNdThr = DDQ_ND_THR;  // DM trials per thread of the wide variant
 constexpr int kMaxPatterns = 8;
 constexpr int kRecHeader = 4;
-constexpr int kRowWords = 8;
-constexpr int kMaxSegments = 256;
+constexpr int kSegWords = 4;
+constexpr int kMaxSegments = 160;
 constexpr int kMaxSmem = 227 * 1024;
 
-DDQ_HD constexpr int rows_offset(int nd_cta) { return kRecHeader + kQuadsPerChunk * nd_cta; }
-DDQ_HD constexpr int segs_offset(int nd_cta) {
-  return rows_offset(nd_cta) + kQuadsPerChunk * kMaxPatterns * kRowWords;
+DDQ_HD constexpr int segs_offset(int nd_cta) { return kRecHeader + kQuadsPerChunk * nd_cta; }
+DDQ_HD constexpr int rec_words(int nd_cta) {
+  return (segs_offset(nd_cta) + kMaxSegments * kSegWords + 3) / 4 * 4;
 }
-DDQ_HD constexpr int rec_words(int nd_cta) { return (segs_offset(nd_cta) + kMaxSegments + 3) / 4 * 4; }
 
 struct Tables {
   int nd_thr = 0, nd_cta = 0;

@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <array>
 #include <cstdint>
+#include <cstdint>
 #include <vector>
 
 #include "dd_quad.h"
@@ -51,7 +52,12 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
 
   int32_t raw_stride = 16;
   int32_t prow_words = 4;
-  std::vector<int32_t> base(nd_cta), lo(4), hi(4);
+  // rows of one chunk, kept until raw_stride is known: {row word offset,
+  // items, quad, raw byte offset of channel k (-1 = padding)}
+  struct Row {
+    int32_t off, items, quad, o[4];
+  };
+  std::vector<std::vector<Row>> chunk_rows(static_cast<size_t>(t.ntiles) * t.nchunks);
   for (int tile = 0; tile < t.ntiles; ++tile) {
     // raw windows: channel c needs samples [t_cta + min delay, t_cta + T + max delay)
     std::vector<int32_t> start(t.nchan_pad), need(t.nchan_pad);
@@ -71,10 +77,8 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     for (int ch = 0; ch < t.nchunks; ++ch) {
       int32_t *rec = &t.recs[(static_cast<size_t>(tile) * t.nchunks + ch) * t.rec_words];
       int32_t *A = rec + kRecHeader;
-      int32_t *rows = rec + rows_offset(nd_cta);
-      int32_t *segs = rec + segs_offset(nd_cta);
-      int nsegs = 0;
-      int nrows = 0, row_words = 0, items = 0;
+      std::vector<Row> &rows = chunk_rows[static_cast<size_t>(tile) * t.nchunks + ch];
+      int row_words = 0;
       const int q_lo = ch * kQuadsPerChunk;
       const int nq = std::min(kQuadsPerChunk, t.nquads - q_lo);
       for (int q = 0; q < nq; ++q) {
@@ -98,40 +102,55 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
               bmin = std::min(bmin, delay(tile, c0, i));
               bmax = std::max(bmax, delay(tile, c0, i));
             }
-          const int32_t len = round_up(kTimeTile + bmax - bmin, 4);
-          int32_t *r = rows + nrows * kRowWords;
-          r[0] = row_words;
-          r[1] = len / 4;
-          r[2] = items;
-          r[3] = q;
+          Row r;
+          r.off = row_words;
+          r.items = round_up(kTimeTile + bmax - bmin, 4) / 4;
+          r.quad = q;
           for (int k = 0; k < 4; ++k) {
             const int c = c0 + k;
             const int32_t e = k == 0 ? 0 : pats[p][k - 1];
-            if (c >= nchan) {
-              r[4 + k] = -1;
-            } else {
-              r[4 + k] = bmin + e - start[c];  // >= 0: bmin + e is a delay of channel c
-              raw_stride = std::max(raw_stride, round_up(r[4 + k] + len + 4, 16));
-            }
+            // bmin + e is a delay of channel c, so the offset is >= 0
+            r.o[k] = c >= nchan ? -1 : bmin + e - start[c];
+            if (r.o[k] >= 0) raw_stride = std::max(raw_stride, round_up(r.o[k] + 4 * r.items + 4, 16));
           }
           for (int i = 0; i < nd_cta; ++i)
-            if (pid[i] == static_cast<int>(p))
-              A[q * nd_cta + i] = row_words + delay(tile, c0, i) - bmin;
-          for (int first = 0; first < len / 4; first += 32) {
-            if (nsegs == kMaxSegments || first > 0xffff) return 1;
-            segs[nsegs++] = (nrows << 16) | first;
-          }
-          row_words += len;
-          items += len / 4;
-          ++nrows;
+            if (pid[i] == static_cast<int>(p)) A[q * nd_cta + i] = row_words + delay(tile, c0, i) - bmin;
+          row_words += 4 * r.items;
+          rows.push_back(r);
         }
       }
-      rec[0] = nrows;
-      rec[1] = items;
       rec[2] = nq;
-      rec[3] = nsegs;
       prow_words = std::max(prow_words, row_words);
     }
+  }
+  // segment descriptors (need the final raw_stride for the byte offsets)
+  if (4 * kQuadsPerChunk * static_cast<int64_t>(raw_stride) >= 0xffff) return 1;
+  for (size_t rc = 0; rc < chunk_rows.size(); ++rc) {
+    int32_t *rec = &t.recs[rc * t.rec_words];
+    int32_t *segs = rec + segs_offset(nd_cta);
+    int nsegs = 0;
+    for (const Row &r : chunk_rows[rc]) {
+      for (int first = 0; first < r.items; first += 32) {
+        if (nsegs == kMaxSegments) return 1;
+        uint32_t addr[4], shift = 0;
+        for (int k = 0; k < 4; ++k) {
+          if (r.o[k] < 0) {
+            addr[k] = 0xffff;
+          } else {
+            addr[k] = static_cast<uint32_t>((4 * r.quad + k) * raw_stride + (r.o[k] & ~3) + 4 * first);
+            shift |= static_cast<uint32_t>(r.o[k] & 3) << (2 * k);
+          }
+        }
+        const int32_t items = std::min(32, r.items - first);
+        int32_t *sd = segs + nsegs * kSegWords;
+        sd[0] = static_cast<int32_t>(addr[0] | (addr[1] << 16));
+        sd[1] = static_cast<int32_t>(addr[2] | (addr[3] << 16));
+        sd[2] = (r.off + 4 * first) | (items << 20);
+        sd[3] = static_cast<int32_t>(shift);
+        ++nsegs;
+      }
+    }
+    rec[3] = nsegs;
   }
   t.raw_stride = raw_stride;
   t.prow_words = prow_words;

@@ -19,8 +19,7 @@ import synth
 T_TILE = 512
 QUADS_PER_CHUNK = 4
 REC_HEADER = 4
-ROW_WORDS = 8
-MAX_PATTERNS = 8
+SEG_WORDS = 4
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -79,33 +78,31 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                         n = pitch - off
                     assert off % 16 == 0 and n % 16 == 0 and 0 < n <= rs and off >= 0
                     raw[s, :n] = block[c, off:off + n]
-                nrows, items, nq, nsegs = rec[0], rec[1], rec[2], rec[3]
-                rows_off = REC_HEADER + QUADS_PER_CHUNK * nd
-                segs_off = rows_off + QUADS_PER_CHUNK * MAX_PATTERNS * ROW_WORDS
-                rows = rec[rows_off:segs_off].reshape(-1, ROW_WORDS)[:nrows]
-                segs = rec[segs_off:segs_off + nsegs]
-                assert nrows <= QUADS_PER_CHUNK * MAX_PATTERNS
-                assert rows[:, 1].sum() == items
+                nq, nsegs = rec[2], rec[3]
+                segs_off = REC_HEADER + QUADS_PER_CHUNK * nd
+                segs = rec[segs_off:segs_off + SEG_WORDS * nsegs].reshape(-1, SEG_WORDS)
+                raw_flat = raw.reshape(-1)
                 prow = np.full((pw, 4), garbage, dtype=np.uint8)
-                covered = np.zeros(items, dtype=np.int64)
-                for sd in segs:  # one warp-wide step: items first .. first+31 of a row
-                    r, first = sd >> 16, sd & 0xFFFF
-                    assert r < nrows
-                    row_off, nitems, first_item, q, *o = rows[r]
-                    i4 = first + np.arange(32)
-                    i4 = i4[i4 < nitems]
-                    covered[first_item + i4] += 1
-                    assert row_off % 4 == 0 and row_off + 4 * nitems <= pw
-                    words = (4 * i4[:, None] + np.arange(4)[None, :]).reshape(-1)
+                written = np.zeros(pw, dtype=np.int64)
+                for d0w, d1w, d2w, d3w in segs.astype(np.int64) & 0xFFFFFFFF:  # one warp-wide step
+                    items = d2w >> 20
+                    word0 = d2w & 0xFFFFF
+                    assert 1 <= items <= 32 and word0 % 4 == 0
+                    offs = [d0w & 0xFFFF, d0w >> 16, d1w & 0xFFFF, d1w >> 16]
+                    lanes = np.arange(items)
+                    words = (word0 + 4 * lanes[:, None] + np.arange(4)[None, :]).reshape(-1)
+                    assert words.max() < pw
+                    written[words] += 1
                     for k in range(4):
-                        if o[k] < 0:
-                            assert 4 * (ch * QUADS_PER_CHUNK + q) + k >= nchan
-                            prow[row_off + words, k] = 0
-                        else:
-                            pos = o[k] + words
-                            assert (pos.max() & ~3) + 8 <= rs  # two aligned words read
-                            prow[row_off + words, k] = raw[4 * q + k, pos]
-                assert np.all(covered == 1)
+                        if offs[k] == 0xFFFF:
+                            prow[words, k] = 0
+                            continue
+                        sh = (d3w >> (2 * k)) & 3
+                        w = offs[k] + 4 * lanes
+                        assert w.min() % 4 == 0 and w.max() + 8 <= raw_flat.size  # two words
+                        byte = (w[:, None] + sh + np.arange(4)[None, :]).reshape(-1)
+                        prow[words, k] = raw_flat[byte]
+                assert written.max() <= 1  # no row word is built twice
                 A = rec[REC_HEADER:REC_HEADER + QUADS_PER_CHUNK * nd].reshape(QUADS_PER_CHUNK, nd)
                 for q in range(nq):
                     for i in range(nd):
