@@ -182,6 +182,36 @@ int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies);
 int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems,
                         int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes);
 
+/* dd_detect without allocation.  The thesis has no counterpart: this entry
+ * point exists for callers that must not allocate device memory at run time
+ * -- for example a process whose device memory is entirely reserved up front
+ * by another allocator (a framework's caching allocator), or a real-time loop
+ * that may not call cudaMalloc because it can synchronise the device and stall
+ * the stream -- and that therefore cannot create a plan.
+ *
+ * It runs the same normalisation and threshold passes as dd_detect on
+ *   out: device pointer, [ndm][nsamp_out], int32 when in_dtype is DD_U8,
+ *        float when it is DD_F16 or DD_F32 (the dd_execute output types),
+ * writes up to `capacity` candidates to the device array `cands` in (dm_idx,
+ * t) order and the total found to the host pointer *count, with the same
+ * statistics, threshold rule and status codes as dd_detect.
+ *
+ * Scratch memory: one file-scope device array of 4.5 MiB (per-row statistics,
+ * per-chunk counts and offsets), which every GPU that loads the library keeps
+ * until the process exits.  Limits: ndm <= 16384 and
+ * ndm * ceil(nsamp_out / 4096) <= 262144; larger sizes return DD_ERR_SIZE
+ * before anything is queued.  The call makes no cudaMalloc, cudaFree or other
+ * allocating call; it runs on the calling thread's current device.  Its first
+ * call on a device looks up the array's device address
+ * (cudaGetSymbolAddress), so make that first call before any stream capture.
+ * Every call uses the same array and leaves its contents behind (nothing in
+ * it needs to start at zero): calls whose work overlaps on the GPU -- on
+ * different streams, or from different host threads -- race and must be
+ * serialised by the caller.  Synchronises `stream` once (to return *count). */
+int dd_detect_noalloc(const void *out, int32_t in_dtype, int32_t ndm, int64_t nsamp_out,
+                      float nsigma, dd_candidate *cands, int64_t capacity, int64_t *count,
+                      void *stream);
+
 /* Static description of a status code. */
 const char *dd_status_string(int status);
 

@@ -65,6 +65,7 @@ SIGNATURES = [
     ("dd_plan_set_wait_timeout", ctypes.c_int, [_vp, _i64]),
     ("dd_plan_inject_fault", ctypes.c_int, [_vp, _i32]),
     ("dd_plan_kernel_info", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    ("dd_detect_noalloc", ctypes.c_int, [_vp, _i32, _i32, _i64, _f32, _vp, _i64, _vp, _vp]),
 ]
 
 PEAK_KINDS = {"fadd": 0, "fadd2": 1, "iadd": 2, "iadd3": 3, "imad": 4, "lop3": 5, "prmt": 6,
@@ -234,3 +235,14 @@ def dd_plan_kernel_info(plan, block, pitch_elems) -> dict:
                                       ctypes.addressof(nd), ctypes.addressof(sm)),
            "dd_plan_kernel_info")
     return {"staged": bool(st.value), "dms_per_cta": nd.value, "smem_bytes": sm.value}
+
+
+def dd_detect_noalloc(out, dtype, ndm, nsamp_out, nsigma, cands, capacity, stream=None):
+    """Returns ``(status, count)``; status is DD_OK or DD_ERR_OVERFLOW."""
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    cnt = ctypes.c_int64(0)
+    st = load().dd_detect_noalloc(_addr(out), code, int(ndm), int(nsamp_out), float(nsigma),
+                                  _addr(cands), int(capacity), ctypes.addressof(cnt),
+                                  _stream(stream))
+    _check(st, "dd_detect_noalloc", allow=(DD_ERR_OVERFLOW,))
+    return st, int(cnt.value)

@@ -16,7 +16,9 @@
 // scheduling.  The predicate is evaluated identically in passes 2 and 4.
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <mutex>
 
 #include "dd_internal.h"
 
@@ -335,3 +337,86 @@ int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsig
 }
 
 }  // namespace ddk
+
+// ---------------------------------------------------------------------------
+// dd_detect_noalloc: the detection passes above with their scratch (per-row
+// statistics, per-chunk counts and offsets, the total) in one file-scope
+// device array instead of plan-owned cudaMalloc memory, for callers that must
+// not allocate (dd.h).  Every GPU that loads the library holds the array until
+// the process exits.
+namespace {
+
+constexpr int32_t kNoAllocMaxRows = 16384;        // DM trials per call
+constexpr int64_t kNoAllocMaxChunks = 1 << 18;    // rows x ceil(nsamp_out / 4096)
+constexpr size_t kNoAllocStatsBytes = sizeof(dd_row_stats) * kNoAllocMaxRows;
+constexpr size_t kNoAllocChunkBytes = sizeof(int64_t) * kNoAllocMaxChunks;
+constexpr size_t kNoAllocBytes = kNoAllocStatsBytes + 2 * kNoAllocChunkBytes + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on the current device, looked up once
+// per device (cudaGetSymbolAddress; the host-side symbol is not a device
+// address).  Returns nullptr on failure.
+void *noalloc_scratch(int device) {
+  if (device < 0 || device >= kNoAllocMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[device]) {
+    void *ptr = nullptr;
+    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return nullptr;
+    g_noalloc_addr[device] = ptr;
+  }
+  return g_noalloc_addr[device];
+}
+
+}  // namespace
+
+extern "C" int dd_detect_noalloc(const void *out, int32_t in_dtype, int32_t ndm, int64_t nsamp_out,
+                                 float nsigma, dd_candidate *cands, int64_t capacity,
+                                 int64_t *count, void *stream) {
+  if (!out || !count || capacity < 0 || (capacity > 0 && !cands)) return DD_ERR_ARG;
+  if (in_dtype != DD_U8 && in_dtype != DD_F16 && in_dtype != DD_F32) return DD_ERR_DTYPE;
+  if (!std::isfinite(nsigma) || ndm < 1) return DD_ERR_ARG;
+  if (nsamp_out < 1 || nsamp_out > INT32_MAX) return DD_ERR_SIZE;
+  const int64_t nchunks = (nsamp_out + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
+  if (ndm > kNoAllocMaxRows || nchunks * ndm > kNoAllocMaxChunks) return DD_ERR_SIZE;
+  *count = 0;
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return DD_ERR_CUDA;
+  unsigned char *base = static_cast<unsigned char *>(noalloc_scratch(device));
+  if (!base) return DD_ERR_CUDA;
+  dd_row_stats *stats = reinterpret_cast<dd_row_stats *>(base);
+  int64_t *counts = reinterpret_cast<int64_t *>(base + kNoAllocStatsBytes);
+  int64_t *offsets = reinterpret_cast<int64_t *>(base + kNoAllocStatsBytes + kNoAllocChunkBytes);
+  int64_t *total = reinterpret_cast<int64_t *>(base + kNoAllocStatsBytes + 2 * kNoAllocChunkBytes);
+
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const double thr = static_cast<double>(nsigma);
+  const int nch = static_cast<int>(nchunks);
+  const dim3 grid(nch, ndm);
+  if (in_dtype == DD_U8) {
+    const int32_t *D = static_cast<const int32_t *>(out);
+    dd_stats_i32<<<ndm, kStatsThreads, 0, s>>>(D, nsamp_out, thr, stats);
+    dd_count<int32_t><<<grid, kCountThreads, 0, s>>>(D, nsamp_out, nch, stats, counts);
+    dd_scan<<<1, kScanThreads, 0, s>>>(counts, nchunks * ndm, offsets, total);
+    if (capacity > 0)
+      dd_write<int32_t><<<grid, kCountThreads, 0, s>>>(D, nsamp_out, nch, stats, counts, offsets,
+                                                        cands, capacity);
+  } else {
+    const float *D = static_cast<const float *>(out);
+    dd_stats_f32<<<ndm, kStatsThreads, 0, s>>>(D, nsamp_out, thr, stats);
+    dd_count<float><<<grid, kCountThreads, 0, s>>>(D, nsamp_out, nch, stats, counts);
+    dd_scan<<<1, kScanThreads, 0, s>>>(counts, nchunks * ndm, offsets, total);
+    if (capacity > 0)
+      dd_write<float><<<grid, kCountThreads, 0, s>>>(D, nsamp_out, nch, stats, counts, offsets,
+                                                      cands, capacity);
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemcpyAsync(count, total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? DD_ERR_OOM : DD_ERR_CUDA;
+  return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
+}
