@@ -229,7 +229,7 @@ extern "C" int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64
   if (!scope.ok()) return DD_ERR_CUDA;
   cudaError_t err = cudaSuccess;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int n = (p->path == 0 && ddk::quad_supported(p, block, pitch_elems))
+  const int n = (p->path == 0 && ddk::quad_supported(p, block, pitch_elems, nsamp_out))
                     ? ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, s, &err)
                     : ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, s, &err);
   if (n < 0) return cuda_status(err);
@@ -364,7 +364,7 @@ extern "C" int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies) {
 extern "C" int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems,
                                    int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes) {
   if (!p || !staged) return DD_ERR_ARG;
-  const bool q = p->path == 0 && block && ddk::quad_supported(p, block, pitch_elems);
+  const bool q = p->path == 0 && block && ddk::quad_supported(p, block, pitch_elems, p->maxshift + 1);
   *staged = q ? 1 : 0;
   if (dms_per_cta) *dms_per_cta = p->quad ? p->quad->tables.nd_cta : 0;
   if (smem_bytes) *smem_bytes = p->quad ? p->quad->tables.smem_bytes : 0;

@@ -257,8 +257,11 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   const int lane = tid & 31, warp = tid >> 5;
   const int tg = warp & (kTimeGroups - 1);
   const int dg = warp / kTimeGroups;
-  const int tile = blockIdx.y;
-  const int64_t t_cta = static_cast<int64_t>(blockIdx.x) * kTimeTile;
+  // DM tiles vary fastest across the grid, so the CTAs resident at any time
+  // cover a narrow span of input samples for all DM tiles and share the
+  // input windows through L2 instead of re-reading them from HBM.
+  const int tile = blockIdx.x;
+  const int64_t t_cta = static_cast<int64_t>(blockIdx.y) * kTimeTile;
 
   // shared-memory layout (dd_quad.h)
   const uint32_t bar0 = smem_addr(smem);
@@ -381,8 +384,9 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
 
 namespace ddk {
 
-bool quad_supported(const dd_plan *p, const void *block, int64_t pitch) {
+bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out) {
   if (!p->quad || p->dtype != DD_U8) return false;
+  if ((nsamp_out + kTimeTile - 1) / kTimeTile > 65535) return false;  // grid.y limit
   return (reinterpret_cast<uintptr_t>(block) & 15) == 0 && (pitch & 15) == 0;
 }
 
@@ -405,8 +409,8 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
   a.status = p->d_error;
   a.timeout_ns = p->wait_timeout_ns;
   a.skip_copies = p->debug_skip_copies;
-  const dim3 grid(static_cast<unsigned>((nsamp_out + kTimeTile - 1) / kTimeTile),
-                  static_cast<unsigned>(q.tables.ntiles));
+  const dim3 grid(static_cast<unsigned>(q.tables.ntiles),
+                  static_cast<unsigned>((nsamp_out + kTimeTile - 1) / kTimeTile));
   const int smem = q.tables.smem_bytes;
   if (q.tables.nd_thr == kNdThr) {
     *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<kNdThr>,

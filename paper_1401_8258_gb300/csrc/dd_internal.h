@@ -82,8 +82,8 @@ inline int elem_size(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F
 int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                              void *out, cudaStream_t stream, cudaError_t *err);
 // Staged quad kernel (u8): needs the plan's quad tables, a 16-byte aligned
-// block and a pitch that is a multiple of 16 bytes.
-bool quad_supported(const dd_plan *p, const void *block, int64_t pitch);
+// block, a pitch that is a multiple of 16 bytes and at most 65535 time tiles.
+bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
 int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                            void *out, cudaStream_t stream, cudaError_t *err);
 
