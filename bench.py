@@ -139,10 +139,16 @@ def measured_peaks() -> dict:
 
 
 def kernel_source_sha() -> str:
+    """Hash of the dedispersion kernels' code (comments and blank lines
+    dropped), to tell whether a recorded ncu traffic figure still applies."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1401_8258_gb300", "csrc", "dd_dedisp*.cu"))):
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1401_8258_gb300", "csrc", "dd_dedisp*.cu")) +
+                    glob.glob(os.path.join(ROOT, "paper_1401_8258_gb300", "csrc", "dd_quad*"))):
+        with open(f) as fh:
+            for line in fh:
+                code = line.split("//", 1)[0].strip()
+                if code:
+                    h.update(code.encode())
     return h.hexdigest()[:12]
 
 

@@ -8,7 +8,7 @@
  *   D[d][t] = sum_{c=0}^{nchan-1} I[c][t + delay(c,d)]        (Sec. 2.1.1, brute-force equation)
  *   delay(c,d) = round(DM_d * dT(c)),
  *   dT(c) = K * ((f_top - c*df)^-2 - f_top^-2) / t_samp       (Sec. 2.1.1, deltaT equation)
- *   K = 4.148808e3 MHz^2 pc^-1 cm^3 s                          (Sec. 1.3, dispersion constant)
+ *   K = 4.148808e3 MHz^2 pc^-1 cm^3 s                          (Sec. 1.2.1, dispersion constant)
  *   valid output length nsamp_out = nsamp_in - maxshift        (Sec. 3.4, maxshift overlap)
  *   per-DM mean and rms, snr = (D - mean)/rms                  (Sec. 3.5, normalisation)
  *   candidates = (DM, time, intensity) with snr > nsigma       (Sec. 3.6, thresholding)

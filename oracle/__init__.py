@@ -7,7 +7,7 @@ nothing from the library: the arithmetic lives in ``dd_oracle.c`` (plain C,
 compiled with ``-ffp-contract=off``), written from the thesis:
 
 * ``delay_table``   -- Sec. 2.1.1, the discretised-delay (deltaT) equation,
-                       with the dispersion constant of Sec. 1.3;
+                       with the dispersion constant of Sec. 1.2.1;
 * ``dedisperse``    -- Sec. 2.1.1, the brute-force dedispersion equation,
                        valid length nsamp - maxshift per Sec. 3.4;
 * ``stats``         -- Sec. 3.5, per-DM normalisation (mean, population rms);

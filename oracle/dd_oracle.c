@@ -11,8 +11,8 @@
  *
  * Thesis passages followed (A. Magro, "A Real-Time, GPU-Based, Non-Imaging
  * Back-End for Radio Telescopes", 2013):
- *   - dispersion constant D = 4.148808e3 MHz^2 pc^-1 cm^3 s       (Sec. 1.3, dispersion equation)
- *   - delay between two frequencies, k_DM * DM * (f1^-2 - f2^-2)  (Sec. 1.3, dispersion relationship equation)
+ *   - dispersion constant D = 4.148808e3 MHz^2 pc^-1 cm^3 s       (Sec. 1.2.1, dispersion equation)
+ *   - delay between two frequencies, k_DM * DM * (f1^-2 - f2^-2)  (Sec. 1.2.1, dispersion relationship equation)
  *   - direct dedispersion D[d][t] = sum_c A[c][t + dt(d,c)]       (Sec. 2.1.1, brute-force equation)
  *   - discretised delay dT(c), dt(d,c) = round(DM(d) dT(c))       (Sec. 2.1.1, deltaT equation)
  *   - valid output length = nsamp - maxshift (overlap carry)      (Sec. 3.4, Dedispersion)
@@ -43,7 +43,7 @@
 #include <omp.h>
 #endif
 
-/* Dispersion constant in MHz^2 pc^-1 cm^3 s (Sec. 1.3). */
+/* Dispersion constant in MHz^2 pc^-1 cm^3 s (Sec. 1.2.1). */
 static const double ORACLE_KDM = 4.148808e3;
 
 enum { OR_U8 = 0, OR_F16 = 1, OR_F32 = 2 };

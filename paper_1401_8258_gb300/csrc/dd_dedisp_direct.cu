@@ -4,7 +4,7 @@
 // D[d][t] = sum_c I[c][t + delay(c,d)]  (Sec. 2.1.1, brute-force equation).
 // The grid maps onto the output (DM tile, time tile) space; each thread owns
 // one output sample for kDirectDms consecutive DM trials, with one register
-// accumulator per trial (the thesis's Sec. 2.2 layout), and reads the input
+// accumulator per trial (the thesis's Sec. 2.4 layout), and reads the input
 // through the L1/L2 caches.  Delays of a group of channels for the CTA's DM
 // tile are staged in shared memory (channel/DM order keeps that load
 // coalesced, Sec. 3.4).

@@ -6,7 +6,7 @@
 // Data flow per CTA (one DM tile x one 512-sample time tile), per chunk of
 // 16 channels:
 //   1. one warp queues bulk copies (cp.async.bulk, the TMA engine) of each
-//      channel's input window -- the "channel vector" of Sec. 2.2, sized by
+//      channel's input window -- the "channel vector" of Sec. 2.4, sized by
 //      the largest and smallest delay of the tile -- plus the chunk's plan
 //      record into shared memory, signalling an mbarrier; copies run three
 //      chunks ahead of the accumulation (triple-buffered windows);

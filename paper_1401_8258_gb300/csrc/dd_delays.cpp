@@ -10,7 +10,7 @@
 
 namespace {
 
-// Dispersion constant in MHz^2 pc^-1 cm^3 s (Sec. 1.3, dispersion equation).
+// Dispersion constant in MHz^2 pc^-1 cm^3 s (Sec. 1.2.1, dispersion equation).
 constexpr double kDispersionConstant = 4.148808e3;
 
 }  // namespace

@@ -6,9 +6,9 @@ injected, the caller passes the integer delay of every channel for the pulse's
 DM trial (taken from whichever delay table it is testing), and the generator
 only adds the pulse amplitude at those samples.
 
-Workloads follow the shapes of the thesis's observations (Sec. 4: BEST-II at
-400-416 MHz with 1024 channels and 51.2 us sampling; Sec. 2.2 functional test
-with a boxcar pulse in N(0,1) noise; Sec. 3.3 narrowband RFI with a 6.5 ms
+Workloads follow the shapes of the thesis's observations (Ch. 4: BEST-II at
+400-416 MHz with 1024 channels and 51.2 us sampling; Sec. 2.4 functional test
+with a boxcar pulse in N(0,1) noise; Sec. 3.3.4 narrowband RFI with a 6.5 ms
 period) and an L-band survey shape (1200-1500 MHz, 4096 channels).  All draws
 come from ``numpy.random.default_rng(seed)`` (PCG64).
 """

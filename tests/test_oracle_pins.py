@@ -97,7 +97,7 @@ def test_adjacent_channel_delay_matches_channel_smear_formula():
 
 
 def test_dm_max_closed_form_gives_one_sample_smear():
-    """Sec. 6: DM_max = dt f0^3 / (8300 df) keeps the smear within one
+    """Sec. 6.3: DM_max = dt f0^3 / (8300 df) keeps the smear within one
     channel to one sample at the band bottom f0; at that DM the delay step
     between the two lowest channels is 1 sample to within rounding."""
     c8300 = GOLDEN["dm_max_one_sample_smear_constant"]["value"]
@@ -242,7 +242,7 @@ def test_injected_on_grid_pulse_adds_amp_times_nchan_and_peaks_at_truth():
 
 
 def test_functional_test_snr_matches_thesis_closed_form():
-    """Sec. 2.2 functional test: top-hat height a = 8/sqrt(1024) in N(0,1)
+    """Sec. 2.4 functional test: top-hat height a = 8/sqrt(1024) in N(0,1)
     noise over 1024 channels is recovered at S/N a*sqrt(N_c) = 8 at its DM.
     (t_samp is not printed; 1 ms is used; DM trials around the pulse DM.)"""
     ft = GOLDEN["functional_test"]
@@ -388,7 +388,7 @@ def test_false_alarm_count_on_dedispersed_noise():
 
 
 def test_realtime_op_rate_accounting_matches_thesis():
-    """Sec. 3.8: 138e9 ops/s is beams x samples/s x channels x DM trials."""
+    """Sec. 3.9 (for the benchmark of Sec. 3.8.3): 138e9 ops/s is beams x samples/s x channels x DM trials."""
     r = GOLDEN["realtime_op_rate"]
     ops = r["n_beams"] * r["samples_per_s"] * r["nchan"] * r["n_dm"]
     assert abs(ops / r["ops_per_s"] - 1) < 0.01
