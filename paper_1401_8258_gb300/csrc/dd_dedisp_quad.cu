@@ -14,7 +14,8 @@
 //      rows: word i of a row holds the four channels' samples that one
 //      relative-delay pattern adds at one output time (dd_quad_plan.cpp);
 //      rows of chunk k+1 are built while chunk k is accumulated (double
-//      buffer), with a single CTA barrier per chunk;
+//      buffer), handed between warps through mbarriers (rows ready / rows
+//      consumed) rather than CTA-wide barriers, so warps drift within a chunk;
 //   3. every thread adds, for each of its DM trials and output samples, one
 //      32-bit row word with a 4-way byte dot product (dp4a, weights 1) into
 //      an int32 register accumulator: four channel-adds per instruction and
@@ -186,22 +187,6 @@ __device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, 
   }
 }
 
-// Bounded spin on the mbarrier phase of chunk m.
-__device__ __forceinline__ bool wait_chunk(uint32_t bar0, int m, uint64_t timeout_ns) {
-  return mbar_wait_bounded(bar0 + 8 * (m % kRawStages), (m / kRawStages) & 1, timeout_ns);
-}
-
-// CTA-uniform wait for chunk m: thread 0 alone spins (bounded), the others
-// wait at the barrier, which also makes the outcome uniform; after a
-// completed phase every thread acquires it with one try_wait.  Returns false
-// if the wait ran out.
-__device__ __forceinline__ bool cta_wait_chunk(uint32_t bar0, int m, uint64_t timeout_ns, int tid) {
-  const bool ok = tid != 0 || wait_chunk(bar0, m, timeout_ns);
-  if (__syncthreads_or(!ok)) return false;
-  mbar_try_wait(bar0 + 8 * (m % kRawStages), (m / kRawStages) & 1);
-  return true;
-}
-
 // Interleave the four channels of every quad of a chunk into its pattern
 // rows, one segment (a warp-wide step, dd_quad.h) at a time: lane l builds
 // item l, i.e. the row words of 4 output samples.  For channel k it reads the
@@ -248,11 +233,38 @@ __device__ __forceinline__ int warp_segments(const int32_t *rec, int warp) {
   return nsegs > warp ? (nsegs - warp + kWarps - 1) / kWarps : 0;
 }
 
+// Arrive on an mbarrier (every thread of the CTA arrives on the row
+// barriers, so that each releases its own shared-memory stores).
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// Warp-wide bounded wait on an mbarrier phase: lane 0 spins until the phase
+// completes, the CTA's abort flag is raised or timeout_ns passes; then every
+// lane acquires the completed phase.  Returns false if the wait gave up.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns,
+                                          const volatile int *abort_flag, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    const uint64_t t0 = global_timer();
+    while (!mbar_try_wait(bar, parity)) {
+      if (*abort_flag || global_timer() - t0 > timeout_ns) {
+        ok = 0;
+        break;
+      }
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok) mbar_try_wait(bar, parity);
+  return ok != 0;
+}
+
 template <int ND_THR>
 __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
   constexpr int kSegsOff = segs_offset(ND_CTA);
   extern __shared__ __align__(128) uint8_t smem[];
+  __shared__ int s_abort;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int tg = warp & (kTimeGroups - 1);
@@ -263,12 +275,16 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   const int tile = blockIdx.x;
   const int64_t t_cta = static_cast<int64_t>(blockIdx.y) * kTimeTile;
 
-  // shared-memory layout (dd_quad.h)
+  // shared-memory layout (dd_quad.h): mbarriers, raw window table, records,
+  // raw window buffers, pattern-row buffers
   const uint32_t bar0 = smem_addr(smem);
-  int32_t *meta_s = reinterpret_cast<int32_t *>(smem + 32);
+  auto tma_bar = [&](int m) { return bar0 + 8u * (m % kRawStages); };
+  auto ready_bar = [&](int m) { return bar0 + 8u * (kRawStages + (m % kRowStages)); };
+  auto free_bar = [&](int m) { return bar0 + 8u * (kRawStages + kRowStages + (m % kRowStages)); };
+  int32_t *meta_s = reinterpret_cast<int32_t *>(smem + kBarrierBytes);
   const uint32_t meta_bytes = static_cast<uint32_t>((a.nchan_pad * 8 + 15) / 16 * 16);
   const uint32_t rec_bytes = static_cast<uint32_t>(a.rec_words) * 4;
-  const uint32_t rec_off = 32 + meta_bytes;
+  const uint32_t rec_off = kBarrierBytes + meta_bytes;
   const uint32_t raw_off = rec_off + kRecStages * rec_bytes;
   const uint32_t raw_bytes = 4u * kQuadsPerChunk * static_cast<uint32_t>(a.raw_stride);
   const uint32_t prow_off = raw_off + kRawStages * raw_bytes;
@@ -280,18 +296,34 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   auto raw_addr = [&](int m) { return bar0 + raw_off + (m % kRawStages) * raw_bytes; };
   auto prow_addr = [&](int m) { return bar0 + prow_off + (m % kRowStages) * prow_bytes; };
 
-  // the tile's raw window table, and the pipeline's mbarriers
   const int32_t *meta_g = a.raw_meta + static_cast<int64_t>(tile) * a.nchan_pad * 2;
   for (int i = tid; i < 2 * a.nchan_pad; i += kThreads) meta_s[i] = meta_g[i];
   if (tid == 0) {
-    for (int b = 0; b < kRawStages; ++b) mbar_init(bar0 + 8 * b, 1);
+    for (int b = 0; b < kRawStages; ++b) mbar_init(tma_bar(b), 1);
+    for (int b = 0; b < kRowStages; ++b) {
+      mbar_init(ready_bar(b), kThreads);
+      mbar_init(free_bar(b), kThreads);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_abort = 0;
   }
   __syncthreads();
-  const int prefill = a.nchunks < kRawStages ? a.nchunks : kRawStages;
-  if (warp == 0 && !a.skip_copies)
+
+  // Synchronisation (all waits bounded, chunk m uses raw stage m%3, record
+  // stage m%4 and row stage m%2):
+  //   tma(m)   -- the bulk copies of chunk m landed;
+  //   ready(m) -- every thread built its segments of chunk m's rows;
+  //   free(m)  -- every thread finished accumulating chunk m.
+  // Iteration k: wait ready(k); warp 0 (after free(k-1)) queues chunk k+3;
+  // wait tma(k+1) and free(k-1), then build chunk k+1 spread over the
+  // accumulation of chunk k; arrive ready(k+1) and free(k).
+  int issued = 0;  // chunks queued (warp 0)
+  if (warp == 0 && !a.skip_copies) {
+    const int prefill = a.nchunks < kRawStages ? a.nchunks : kRawStages;
     for (int m = 0; m < prefill; ++m)
-      issue_chunk(a, meta_s, tile, t_cta, m, bar0 + 8 * m, rec_addr(m), raw_addr(m), lane);
+      issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
+    issued = prefill;
+  }
 
   int acc[ND_THR][kTimesPerThread];
 #pragma unroll
@@ -300,29 +332,33 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     for (int j = 0; j < kTimesPerThread; ++j) acc[i][j] = 0;
   const uint32_t my_word = static_cast<uint32_t>(tg * 32 * kTimesPerThread + lane);
 
-  // chunk 0: wait, then interleave
-  int abort_at = -1;
-  if (!cta_wait_chunk(bar0, 0, a.timeout_ns, tid)) {
-    abort_at = 0;
-  } else {
+  bool ok = warp_wait(tma_bar(0), 0, a.timeout_ns, &s_abort, lane);
+  if (ok) {
     build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), kSegsOff, warp, lane, 0,
                warp_segments(rec_ptr(0), warp));
+    mbar_arrive(ready_bar(0));
   }
 
-  for (int k = 0; abort_at < 0 && k < a.nchunks; ++k) {
-    // one barrier per chunk: rows of chunk k are built, rows of k-1 consumed,
-    // and (if any) chunk k+1 has landed in shared memory
-    if (k + 1 < a.nchunks ? !cta_wait_chunk(bar0, k + 1, a.timeout_ns, tid)
-                          : __syncthreads_or(0) != 0) {
-      abort_at = k + 1;
-      break;
-    }
+  for (int k = 0; ok && k < a.nchunks; ++k) {
+    ok = warp_wait(ready_bar(k), (k / kRowStages) & 1, a.timeout_ns, &s_abort, lane);
+    if (!ok) break;
     if (warp == 0 && k + kRawStages < a.nchunks && !a.skip_copies) {
-      // raw buffer of chunk k and record of chunk k-1 are free again
+      // raw stage of chunk k is free (rows of k built); the record stage of
+      // chunk k-1 is free once every thread has accumulated chunk k-1
+      if (k >= 1) ok = warp_wait(free_bar(k - 1), ((k - 1) / kRowStages) & 1, a.timeout_ns,
+                                 &s_abort, lane);
+      if (!ok) break;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const int m = k + kRawStages;
-      issue_chunk(a, meta_s, tile, t_cta, m, bar0 + 8 * (m % kRawStages), rec_addr(m), raw_addr(m),
-                  lane);
+      issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
+      issued = m + 1;
+    }
+    const bool next = k + 1 < a.nchunks;
+    if (next) {
+      ok = warp_wait(tma_bar(k + 1), ((k + 1) / kRawStages) & 1, a.timeout_ns, &s_abort, lane);
+      if (ok && k >= 1)  // row stage of chunk k+1 held chunk k-1
+        ok = warp_wait(free_bar(k - 1), ((k - 1) / kRowStages) & 1, a.timeout_ns, &s_abort, lane);
+      if (!ok) break;
     }
     // accumulate chunk k (four channels per dp4a) while building the rows
     // of chunk k+1: this warp's build segments are spread over the quads
@@ -330,7 +366,6 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     const int nq = rec[2];
     const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
     const uint32_t prow = prow_addr(k);
-    const bool next = k + 1 < a.nchunks;
     const int32_t *rec_n = rec_ptr(k + 1);
     const int nseg_w = next ? warp_segments(rec_n, warp) : 0;
     int m_done = 0;
@@ -352,17 +387,20 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
           Acc8<0>::run(acc[4 * i4 + ii], prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word));
       }
     }
+    if (next) mbar_arrive(ready_bar(k + 1));
+    mbar_arrive(free_bar(k));
   }
 
-  if (abort_at >= 0) {
-    // a bounded wait ran out: record it, wait (bounded) for this CTA's own
-    // copies still in flight, then leave.  Queued when chunk abort_at's wait
-    // ran out: chunks 0..2 (prologue) or up to abort_at + 1 (loop).
-    if (tid == 0) {
-      atomicExch(a.status, 1);
-      const int last = abort_at == 0 ? kRawStages - 1 : abort_at + 1;
-      if (!a.skip_copies)
-        for (int m = abort_at; m < a.nchunks && m <= last; ++m) wait_chunk(bar0, m, a.timeout_ns);
+  if (!ok) {
+    // a bounded wait ran out: raise the CTA's abort flag (the other warps'
+    // waits give up on it) and the plan's status word; warp 0 then waits,
+    // bounded, for the copies it queued that may still be in flight (the last
+    // kRawStages queued, each on its own barrier) before leaving
+    s_abort = 1;
+    if (lane == 0) atomicExch(a.status, 1);
+    if (warp == 0 && lane == 0) {
+      for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
+        mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, a.timeout_ns);
     }
     return;
   }

@@ -85,8 +85,9 @@ struct Tables {
 constexpr int kRawStages = 3;
 constexpr int kRecStages = 4;
 constexpr int kRowStages = 2;
+constexpr int kBarrierBytes = 64;  // 3 copy + 2 rows-ready + 2 rows-free mbarriers
 
-// Shared-memory layout: kRawStages mbarriers (32 B reserved), the tile's raw
+// Shared-memory layout: the mbarriers (kBarrierBytes), the tile's raw
 // window table (nchan_pad x 2 int32), kRecStages records, kRawStages raw
 // window buffers (4*kQuadsPerChunk slots of raw_stride bytes), kRowStages
 // pattern-row areas.
@@ -94,7 +95,7 @@ inline int32_t rec_bytes(const Tables &t) { return t.rec_words * 4; }
 inline int32_t raw_buf_bytes(const Tables &t) { return 4 * kQuadsPerChunk * t.raw_stride; }
 inline int32_t meta_bytes(const Tables &t) { return (t.nchan_pad * 8 + 15) / 16 * 16; }
 inline int32_t smem_bytes(const Tables &t) {
-  return 32 + meta_bytes(t) + kRecStages * rec_bytes(t) + kRawStages * raw_buf_bytes(t) +
+  return kBarrierBytes + meta_bytes(t) + kRecStages * rec_bytes(t) + kRawStages * raw_buf_bytes(t) +
          kRowStages * t.prow_words * 4;
 }
 

@@ -150,7 +150,7 @@ def test_tables_fit_shared_memory_for_the_workloads():
         tb = quad_tables(delays, wl.nchan, wl.ndm, 8)
         assert tb is not None and tb["nd_cta"] == 64, name
         meta = (tb["nchan_pad"] * 8 + 15) // 16 * 16
-        smem = 32 + meta + 4 * tb["rec_words"] * 4 + 3 * 16 * tb["raw_stride"] + 2 * tb["prow_words"] * 4
+        smem = 64 + meta + 4 * tb["rec_words"] * 4 + 3 * 16 * tb["raw_stride"] + 2 * tb["prow_words"] * 4
         assert smem == tb["smem"] <= 227 * 1024
 
 
