@@ -233,10 +233,11 @@ __device__ __forceinline__ int warp_segments(const int32_t *rec, int warp) {
   return nsegs > warp ? (nsegs - warp + kWarps - 1) / kWarps : 0;
 }
 
-// Arrive on an mbarrier (every thread of the CTA arrives on the row
-// barriers, so that each releases its own shared-memory stores).
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+// Arrive on a row mbarrier once per warp: __syncwarp orders the stores of
+// all lanes before lane 0's (releasing) arrival.
+__device__ __forceinline__ void warp_arrive(uint32_t bar, int lane) {
+  __syncwarp();
+  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 // Warp-wide bounded wait on an mbarrier phase: lane 0 spins until the phase
@@ -301,8 +302,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   if (tid == 0) {
     for (int b = 0; b < kRawStages; ++b) mbar_init(tma_bar(b), 1);
     for (int b = 0; b < kRowStages; ++b) {
-      mbar_init(ready_bar(b), kThreads);
-      mbar_init(free_bar(b), kThreads);
+      mbar_init(ready_bar(b), kThreads / 32);
+      mbar_init(free_bar(b), kThreads / 32);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_abort = 0;
@@ -312,8 +313,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   // Synchronisation (all waits bounded, chunk m uses raw stage m%3, record
   // stage m%4 and row stage m%2):
   //   tma(m)   -- the bulk copies of chunk m landed;
-  //   ready(m) -- every thread built its segments of chunk m's rows;
-  //   free(m)  -- every thread finished accumulating chunk m.
+  //   ready(m) -- every warp built its segments of chunk m's rows;
+  //   free(m)  -- every warp finished accumulating chunk m.
   // Iteration k: wait ready(k); warp 0 (after free(k-1)) queues chunk k+3;
   // wait tma(k+1) and free(k-1), then build chunk k+1 spread over the
   // accumulation of chunk k; arrive ready(k+1) and free(k).
@@ -336,7 +337,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   if (ok) {
     build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), kSegsOff, warp, lane, 0,
                warp_segments(rec_ptr(0), warp));
-    mbar_arrive(ready_bar(0));
+    warp_arrive(ready_bar(0), lane);
   }
 
   for (int k = 0; ok && k < a.nchunks; ++k) {
@@ -387,8 +388,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
           Acc8<0>::run(acc[4 * i4 + ii], prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word));
       }
     }
-    if (next) mbar_arrive(ready_bar(k + 1));
-    mbar_arrive(free_bar(k));
+    if (next) warp_arrive(ready_bar(k + 1), lane);
+    warp_arrive(free_bar(k), lane);
   }
 
   if (!ok) {
