@@ -14,8 +14,7 @@
 //      rows: word i of a row holds the four channels' samples that one
 //      relative-delay pattern adds at one output time (dd_quad_plan.cpp);
 //      rows of chunk k+1 are built while chunk k is accumulated (double
-//      buffer), handed between warps through mbarriers (rows ready / rows
-//      consumed) rather than CTA-wide barriers, so warps drift within a chunk;
+//      buffer), with one CTA barrier per chunk;
 //   3. every thread adds, for each of its DM trials and output samples, one
 //      32-bit row word with a 4-way byte dot product (dp4a, weights 1) into
 //      an int32 register accumulator: four channel-adds per instruction and
@@ -240,28 +239,13 @@ __device__ __forceinline__ int warp_segments(const int32_t *rec, int warp) {
   return nsegs > warp ? (nsegs - warp + kWarps - 1) / kWarps : 0;
 }
 
-// Arrive on a row mbarrier once per warp: __syncwarp orders the stores of
-// all lanes before lane 0's (releasing) arrival.
-__device__ __forceinline__ void warp_arrive(uint32_t bar, int lane) {
-  __syncwarp();
-  if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Warp-wide bounded wait on an mbarrier phase: lane 0 spins until the phase
-// completes, the CTA's abort flag is raised or timeout_ns passes; then every
-// lane acquires the completed phase.  Returns false if the wait gave up.
+// Warp-wide bounded wait on an mbarrier phase: lane 0 waits (sleeping in
+// try_wait) until the phase completes or timeout_ns passes; then every lane
+// acquires the completed phase.  Returns false if the wait gave up.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_t timeout_ns,
-                                          const volatile int *abort_flag, int lane) {
+                                          int lane) {
   int ok = 1;
-  if (lane == 0 && !mbar_try_wait(bar, parity)) {
-    const uint64_t t0 = global_timer();
-    while (!mbar_try_wait_sleep(bar, parity)) {
-      if (*abort_flag || global_timer() - t0 > timeout_ns) {
-        ok = 0;
-        break;
-      }
-    }
-  }
+  if (lane == 0) ok = mbar_wait_bounded(bar, parity, timeout_ns) ? 1 : 0;
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (ok) mbar_try_wait(bar, parity);
   return ok != 0;
@@ -272,7 +256,6 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   constexpr int ND_CTA = kDmGroups * ND_THR;
   constexpr int kSegsOff = segs_offset(ND_CTA);
   extern __shared__ __align__(128) uint8_t smem[];
-  __shared__ int s_abort;
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int tg = warp & (kTimeGroups - 1);
@@ -283,12 +266,10 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   const int tile = blockIdx.x;
   const int64_t t_cta = static_cast<int64_t>(blockIdx.y) * kTimeTile;
 
-  // shared-memory layout (dd_quad.h): mbarriers, raw window table, records,
-  // raw window buffers, pattern-row buffers
+  // shared-memory layout (dd_quad.h): copy mbarriers, raw window table,
+  // records, raw window buffers, pattern-row buffers
   const uint32_t bar0 = smem_addr(smem);
   auto tma_bar = [&](int m) { return bar0 + 8u * (m % kRawStages); };
-  auto ready_bar = [&](int m) { return bar0 + 8u * (kRawStages + (m % kRowStages)); };
-  auto free_bar = [&](int m) { return bar0 + 8u * (kRawStages + kRowStages + (m % kRowStages)); };
   int32_t *meta_s = reinterpret_cast<int32_t *>(smem + kBarrierBytes);
   const uint32_t meta_bytes = static_cast<uint32_t>((a.nchan_pad * 8 + 15) / 16 * 16);
   const uint32_t rec_bytes = static_cast<uint32_t>(a.rec_words) * 4;
@@ -308,23 +289,17 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   for (int i = tid; i < 2 * a.nchan_pad; i += kThreads) meta_s[i] = meta_g[i];
   if (tid == 0) {
     for (int b = 0; b < kRawStages; ++b) mbar_init(tma_bar(b), 1);
-    for (int b = 0; b < kRowStages; ++b) {
-      mbar_init(ready_bar(b), kThreads / 32);
-      mbar_init(free_bar(b), kThreads / 32);
-    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    s_abort = 0;
   }
   __syncthreads();
 
-  // Synchronisation (all waits bounded, chunk m uses raw stage m%3, record
-  // stage m%4 and row stage m%2):
-  //   tma(m)   -- the bulk copies of chunk m landed;
-  //   ready(m) -- every warp built its segments of chunk m's rows;
-  //   free(m)  -- every warp finished accumulating chunk m.
-  // Iteration k: wait ready(k); warp 0 (after free(k-1)) queues chunk k+3;
-  // wait tma(k+1) and free(k-1), then build chunk k+1 spread over the
-  // accumulation of chunk k; arrive ready(k+1) and free(k).
+  // Pipeline (chunk m uses raw stage m%3, record stage m%4, row stage m%2):
+  // iteration k starts with a CTA barrier (rows of chunk k built, chunk k-1
+  // consumed); warp 0 then queues the copies of chunk k+3 into the stages of
+  // chunks k (raw) and k-1 (record); every warp waits (bounded) for the copies
+  // of chunk k+1 and builds its share of chunk k+1's rows, spread over the
+  // accumulation of chunk k.  A copy wait that runs out is folded into the
+  // next barrier (barrier-or), so every thread leaves the loop together.
   int issued = 0;  // chunks queued (warp 0)
   if (warp == 0 && !a.skip_copies) {
     const int prefill = a.nchunks < kRawStages ? a.nchunks : kRawStages;
@@ -340,34 +315,26 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     for (int j = 0; j < kTimesPerThread; ++j) acc[i][j] = 0;
   const uint32_t my_word = static_cast<uint32_t>(tg * 32 * kTimesPerThread + lane);
 
-  bool ok = warp_wait(tma_bar(0), 0, a.timeout_ns, &s_abort, lane);
-  if (ok) {
+  bool ok = warp_wait(tma_bar(0), 0, a.timeout_ns, lane);
+  if (ok)
     build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), kSegsOff, warp, lane, 0,
                warp_segments(rec_ptr(0), warp));
-    warp_arrive(ready_bar(0), lane);
-  }
 
-  for (int k = 0; ok && k < a.nchunks; ++k) {
-    ok = warp_wait(ready_bar(k), (k / kRowStages) & 1, a.timeout_ns, &s_abort, lane);
-    if (!ok) break;
+  bool aborted = false;
+  for (int k = 0; k < a.nchunks; ++k) {
+    if (__syncthreads_or(!ok)) {
+      aborted = true;
+      break;
+    }
     if (warp == 0 && k + kRawStages < a.nchunks && !a.skip_copies) {
-      // raw stage of chunk k is free (rows of k built); the record stage of
-      // chunk k-1 is free once every thread has accumulated chunk k-1
-      if (k >= 1) ok = warp_wait(free_bar(k - 1), ((k - 1) / kRowStages) & 1, a.timeout_ns,
-                                 &s_abort, lane);
-      if (!ok) break;
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       const int m = k + kRawStages;
       issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
       issued = m + 1;
     }
     const bool next = k + 1 < a.nchunks;
-    if (next) {
-      ok = warp_wait(tma_bar(k + 1), ((k + 1) / kRawStages) & 1, a.timeout_ns, &s_abort, lane);
-      if (ok && k >= 1)  // row stage of chunk k+1 held chunk k-1
-        ok = warp_wait(free_bar(k - 1), ((k - 1) / kRowStages) & 1, a.timeout_ns, &s_abort, lane);
-      if (!ok) break;
-    }
+    if (next) ok = warp_wait(tma_bar(k + 1), ((k + 1) / kRawStages) & 1, a.timeout_ns, lane);
+    if (!ok) continue;  // reported at the next barrier
     // accumulate chunk k (four channels per dp4a) while building the rows
     // of chunk k+1: this warp's build segments are spread over the quads
     const int32_t *rec = rec_ptr(k);
@@ -395,18 +362,15 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
           Acc8<0>::run(acc[4 * i4 + ii], prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word));
       }
     }
-    if (next) warp_arrive(ready_bar(k + 1), lane);
-    warp_arrive(free_bar(k), lane);
   }
+  if (!aborted && __syncthreads_or(!ok)) aborted = true;  // last chunk's copy wait
 
-  if (!ok) {
-    // a bounded wait ran out: raise the CTA's abort flag (the other warps'
-    // waits give up on it) and the plan's status word; warp 0 then waits,
-    // bounded, for the copies it queued that may still be in flight (the last
-    // kRawStages queued, each on its own barrier) before leaving
-    s_abort = 1;
-    if (lane == 0) atomicExch(a.status, 1);
-    if (warp == 0 && lane == 0) {
+  if (aborted) {
+    // a bounded wait ran out: record it; warp 0 waits, bounded, for the
+    // copies it queued that may still be in flight (the last kRawStages
+    // queued, each on its own barrier) before the CTA leaves
+    if (tid == 0) {
+      atomicExch(a.status, 1);
       for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
         mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, a.timeout_ns);
     }

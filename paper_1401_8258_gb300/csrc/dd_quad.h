@@ -85,7 +85,7 @@ struct Tables {
 constexpr int kRawStages = 3;
 constexpr int kRecStages = 4;
 constexpr int kRowStages = 2;
-constexpr int kBarrierBytes = 64;  // 3 copy + 2 rows-ready + 2 rows-free mbarriers
+constexpr int kBarrierBytes = 64;  // the copy mbarriers (3 x 8 bytes) and padding
 
 // Shared-memory layout: the mbarriers (kBarrierBytes), the tile's raw
 // window table (nchan_pad x 2 int32), kRecStages records, kRawStages raw
