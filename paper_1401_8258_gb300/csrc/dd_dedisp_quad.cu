@@ -193,50 +193,69 @@ __device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, 
   }
 }
 
-// Interleave the four channels of every quad of a chunk into its pattern
-// rows, one segment (a warp-wide step, dd_quad.h) at a time: lane l builds
-// item l, i.e. the row words of 4 output samples.  For channel k it reads the
-// aligned word at the segment's byte offset + 4l and the next one, and
-// funnels out the 4 samples with the segment's byte shift; a 4x4 byte
-// transpose turns the four channels' words into four row words.
-__device__ __forceinline__ void build_segment(const int32_t *sd, uint32_t raw, uint32_t prow,
-                                              int lane) {
-  const int4 d = *reinterpret_cast<const int4 *>(sd);
-  const uint32_t items = static_cast<uint32_t>(d.z) >> 20;
+// Interleave the four channels of a quad into all of its pattern rows, one
+// build unit (dd_quad.h) at a time: lane l builds item first+l (4 output
+// samples) of every row.  Per channel it loads the three aligned words that
+// hold the earliest needed sample and the next 8 bytes -- enough for every
+// pattern, whose first samples differ by at most 2 -- then for each pattern
+// funnels out the 4 samples at that pattern's byte shift; a 4x4 byte transpose
+// turns the four channels' words into four row words.
+__device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint32_t prow,
+                                           int lane) {
+  const int4 d0 = reinterpret_cast<const int4 *>(ud)[0];
+  const int4 d1 = reinterpret_cast<const int4 *>(ud)[1];
+  const uint32_t items = (static_cast<uint32_t>(d0.z) >> 20) & 63u;
   if (static_cast<uint32_t>(lane) >= items) return;
-  const uint32_t off[4] = {static_cast<uint32_t>(d.x) & 0xffffu, static_cast<uint32_t>(d.x) >> 16,
-                           static_cast<uint32_t>(d.y) & 0xffffu, static_cast<uint32_t>(d.y) >> 16};
-  uint32_t v[4];
+  const uint32_t npat = static_cast<uint32_t>(d0.z) >> 26;
+  const uint32_t off[4] = {static_cast<uint32_t>(d0.x) & 0xffffu, static_cast<uint32_t>(d0.x) >> 16,
+                           static_cast<uint32_t>(d0.y) & 0xffffu, static_cast<uint32_t>(d0.y) >> 16};
+  uint32_t w0[4], w1[4], w2[4];
 #pragma unroll
   for (int ch = 0; ch < 4; ++ch) {
-    const uint32_t sh = (static_cast<uint32_t>(d.w) >> (2 * ch)) & 3u;
-    const bool pad = off[ch] == 0xffffu;               // padding channel: zeros
+    const bool pad = off[ch] == 0xffffu;                         // padding channel: zeros
     const uint32_t w = raw + (pad ? 0u : off[ch]) + 4u * lane;  // always in bounds
-    const uint32_t x = prmt(lds32(w), lds32_off<4>(w), 0x3210u + 0x1111u * sh);
-    v[ch] = pad ? 0u : x;
+    w0[ch] = pad ? 0u : lds32(w);
+    w1[ch] = pad ? 0u : lds32_off<4>(w);
+    w2[ch] = pad ? 0u : lds32_off<8>(w);
   }
-  const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
-  const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
-  sts128(prow + 4u * (static_cast<uint32_t>(d.z) & 0xfffffu) + 16u * lane,
-         prmt(lo01, lo23, 0x5410u), prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u),
-         prmt(hi01, hi23, 0x7632u));
+  const uint32_t codes[4] = {static_cast<uint32_t>(d1.x), static_cast<uint32_t>(d1.y),
+                             static_cast<uint32_t>(d1.z), static_cast<uint32_t>(d1.w)};
+  uint32_t dst = prow + 4u * (static_cast<uint32_t>(d0.z) & 0xfffffu) + 16u * lane;
+  const uint32_t row_bytes = 4u * static_cast<uint32_t>(d0.w);
+#pragma unroll
+  for (int p = 0; p < kMaxPatterns; ++p) {
+    if (static_cast<uint32_t>(p) >= npat) break;
+    const uint32_t code = (codes[p >> 1] >> (12 * (p & 1))) & 0xfffu;
+    uint32_t v[4];
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+      const uint32_t sh = (code >> (3 * ch)) & 7u;  // 0..5 bytes into w0:w1:w2
+      const uint32_t lo = sh >= 4u ? w1[ch] : w0[ch];
+      const uint32_t hi = sh >= 4u ? w2[ch] : w1[ch];
+      v[ch] = prmt(lo, hi, 0x3210u + 0x1111u * (sh & 3u));
+    }
+    const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
+    const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
+    sts128(dst, prmt(lo01, lo23, 0x5410u), prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u),
+           prmt(hi01, hi23, 0x7632u));
+    dst += row_bytes;
+  }
 }
 
-// This warp's segments m = m0 .. m1-1 of a chunk (segment index warp + 16*m).
+// This warp's build units m = m0 .. m1-1 of a chunk (unit index warp + 16*m).
 __device__ __forceinline__ void build_rows(const int32_t *rec, uint32_t raw, uint32_t prow,
-                                           int segs_off, int warp, int lane, int m0, int m1) {
+                                           int units_off, int warp, int lane, int m0, int m1) {
   constexpr int kWarps = kThreads / 32;
-  const int32_t *segs = rec + segs_off;
-#pragma unroll 2
-  for (int m = m0; m < m1; ++m)
-    build_segment(segs + (warp + kWarps * m) * kSegWords, raw, prow, lane);
+  const int32_t *units = rec + units_off;
+#pragma unroll 1
+  for (int m = m0; m < m1; ++m) build_unit(units + (warp + kWarps * m) * kUnitWords, raw, prow, lane);
 }
 
-// Segments a warp builds per chunk: ceil((nsegs - warp) / 16).
+// Build units a warp takes per chunk: ceil((nunits - warp) / 16).
 __device__ __forceinline__ int warp_segments(const int32_t *rec, int warp) {
   constexpr int kWarps = kThreads / 32;
-  const int nsegs = rec[3];
-  return nsegs > warp ? (nsegs - warp + kWarps - 1) / kWarps : 0;
+  const int nunits = rec[3];
+  return nunits > warp ? (nunits - warp + kWarps - 1) / kWarps : 0;
 }
 
 // Warp-wide bounded wait on an mbarrier phase: lane 0 waits (sleeping in
@@ -254,7 +273,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_
 template <int ND_THR>
 __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
-  constexpr int kSegsOff = segs_offset(ND_CTA);
+  constexpr int kSegsOff = units_offset(ND_CTA);
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;

@@ -6,20 +6,31 @@
 // nd_thr trials x kTimesPerThread samples (sample = base + lane + 32*j).
 // Channels are processed in chunks of kQuadsPerChunk quads (4 channels each).
 //
+// Pattern rows.  For quad q of a DM tile, let b be the smallest channel-0
+// delay over the tile's trials.  Each distinct relative-delay pattern p of
+// the quad has a row of L words (L = kTimeTile + largest channel-0 delay - b,
+// rounded up to 4); word i of row p holds, for channels k = 0..3, the sample
+// at time t_cta + b + e_k(p) + i, e_k(p) being channel k's delay minus channel
+// 0's in that pattern.  The rows of a quad are contiguous.
+//
 // Per (DM tile, chunk) record, int32 words:
 //   [0] unused                   [1] unused
-//   [2] quads in this chunk      [3] number of build segments
+//   [2] quads in this chunk      [3] number of build units
 //   A[kQuadsPerChunk][nd_cta]    word offset, within the chunk's pattern-row
 //                                area, of the row word that holds output
 //                                sample 0 of the tile for that quad and trial
-//   segs[kMaxSegments][4]: one warp-wide build step each -- up to 32
-//     consecutive items (4 row words = 4 samples x 4 channels) of one
-//     pattern row; lane l builds item l:
-//     [0] raw-buffer byte offsets of channel 0 | channel 1 << 16, [1] of
-//         channels 2 | 3 << 16: the aligned word holding the channel's first
-//         sample of the segment (0xffff = padding channel, reads as zero);
-//     [2] row-area word offset of the segment's first item | items << 20;
-//     [3] byte shift (0..3) of channel k in bits 2k..2k+1.
+//   units[kMaxUnits][8]: one warp-wide build step each -- items first ..
+//     first+31 (item = 4 row words) of every pattern row of one quad; lane l
+//     builds item first+l of each row:
+//     [0] raw-buffer byte offsets of channels 0 | 1 << 16, [1] of 2 | 3 << 16:
+//         the aligned word holding the earliest sample any pattern of the
+//         quad needs for this item block (0xffff = padding channel, zeros);
+//     [2] row-area word offset of item `first` of row 0 | items << 20 |
+//         patterns << 26;
+//     [3] row length L in words;
+//     [4..7] per pattern p (two per word, 12 bits each): for channel k a
+//         3-bit byte shift 0..5 of the pattern's first sample within the
+//         three loaded words.
 // raw_meta[tile][nchan_pad][2]: {window start relative to the tile's first
 // output sample (a multiple of 16), bytes needed (0 = padding channel)}.
 #pragma once
@@ -60,13 +71,13 @@ constexpr int kQuadsPerChunk = DDQ_QUADS_PER_CHUNK;
 constexpr int kNdThr = DDQ_ND_THR;  // DM trials per thread of the wide variant
 constexpr int kMaxPatterns = 8;
 constexpr int kRecHeader = 4;
-constexpr int kSegWords = 4;
-constexpr int kMaxSegments = 160;
+constexpr int kUnitWords = 8;
+constexpr int kMaxUnits = 32;
 constexpr int kMaxSmem = 227 * 1024;
 
-DDQ_HD constexpr int segs_offset(int nd_cta) { return kRecHeader + kQuadsPerChunk * nd_cta; }
+DDQ_HD constexpr int units_offset(int nd_cta) { return kRecHeader + kQuadsPerChunk * nd_cta; }
 DDQ_HD constexpr int rec_words(int nd_cta) {
-  return (segs_offset(nd_cta) + kMaxSegments * kSegWords + 3) / 4 * 4;
+  return (units_offset(nd_cta) + kMaxUnits * kUnitWords + 3) / 4 * 4;
 }
 
 struct Tables {

@@ -52,32 +52,21 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
 
   int32_t raw_stride = 16;
   int32_t prow_words = 4;
-  // rows of one chunk, kept until raw_stride is known: {row word offset,
-  // items, quad, raw byte offset of channel k (-1 = padding)}
-  struct Row {
-    int32_t off, items, quad, o[4];
+  // quads of one chunk, kept until raw_stride is known
+  struct Quad {
+    int32_t row_off, L, npat;
+    int32_t emin[4];               // smallest relative delay of channel k over the patterns
+    int32_t shift[kMaxPatterns][4];  // e_k(p) - emin[k]
+    bool pad[4];
+    int32_t raw_off[4];            // byte offset of time b + emin[k] in channel k's window
   };
-  std::vector<std::vector<Row>> chunk_rows(static_cast<size_t>(t.ntiles) * t.nchunks);
+  std::vector<std::vector<Quad>> chunk_quads(static_cast<size_t>(t.ntiles) * t.nchunks);
   for (int tile = 0; tile < t.ntiles; ++tile) {
-    // raw windows: channel c needs samples [t_cta + min delay, t_cta + T + max delay)
-    std::vector<int32_t> start(t.nchan_pad), need(t.nchan_pad);
-    for (int c = 0; c < t.nchan_pad; ++c) {
-      int32_t mn = delay(tile, c, 0), mx = mn;
-      for (int i = 1; i < nd_cta; ++i) {
-        mn = std::min(mn, delay(tile, c, i));
-        mx = std::max(mx, delay(tile, c, i));
-      }
-      start[c] = mn & ~15;
-      need[c] = c < nchan ? mx + kTimeTile - start[c] : 0;
-      int32_t *m = &t.raw_meta[(static_cast<size_t>(tile) * t.nchan_pad + c) * 2];
-      m[0] = start[c];
-      m[1] = need[c];
-      raw_stride = std::max(raw_stride, round_up(need[c], 16));
-    }
+    std::vector<int32_t> start(t.nchan_pad, 0), need(t.nchan_pad, 0);
     for (int ch = 0; ch < t.nchunks; ++ch) {
       int32_t *rec = &t.recs[(static_cast<size_t>(tile) * t.nchunks + ch) * t.rec_words];
       int32_t *A = rec + kRecHeader;
-      std::vector<Row> &rows = chunk_rows[static_cast<size_t>(tile) * t.nchunks + ch];
+      std::vector<Quad> &quads = chunk_quads[static_cast<size_t>(tile) * t.nchunks + ch];
       int row_words = 0;
       const int q_lo = ch * kQuadsPerChunk;
       const int nq = std::min(kQuadsPerChunk, t.nquads - q_lo);
@@ -86,8 +75,11 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
         // distinct relative patterns (delay of channel k minus channel 0)
         std::vector<std::array<int32_t, 3>> pats;
         std::vector<int> pid(nd_cta);
+        int32_t b = INT32_MAX, bmax = INT32_MIN;
         for (int i = 0; i < nd_cta; ++i) {
           const int32_t d0 = delay(tile, c0, i);
+          b = std::min(b, d0);
+          bmax = std::max(bmax, d0);
           std::array<int32_t, 3> rel{delay(tile, c0 + 1, i) - d0, delay(tile, c0 + 2, i) - d0,
                                      delay(tile, c0 + 3, i) - d0};
           auto it = std::find(pats.begin(), pats.end(), rel);
@@ -95,62 +87,79 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
           if (it == pats.end()) pats.push_back(rel);
         }
         if (static_cast<int>(pats.size()) > kMaxPatterns) return 1;
-        for (size_t p = 0; p < pats.size(); ++p) {
-          int32_t bmin = INT32_MAX, bmax = INT32_MIN;
-          for (int i = 0; i < nd_cta; ++i)
-            if (pid[i] == static_cast<int>(p)) {
-              bmin = std::min(bmin, delay(tile, c0, i));
-              bmax = std::max(bmax, delay(tile, c0, i));
-            }
-          Row r;
-          r.off = row_words;
-          r.items = round_up(kTimeTile + bmax - bmin, 4) / 4;
-          r.quad = q;
-          for (int k = 0; k < 4; ++k) {
-            const int c = c0 + k;
+        Quad Q;
+        Q.row_off = row_words;
+        Q.L = round_up(kTimeTile + bmax - b, 4);
+        Q.npat = static_cast<int32_t>(pats.size());
+        for (int k = 0; k < 4; ++k) {
+          const int c = c0 + k;
+          Q.pad[k] = c >= nchan;
+          int32_t emin = INT32_MAX, emax = INT32_MIN;
+          for (int p = 0; p < Q.npat; ++p) {
             const int32_t e = k == 0 ? 0 : pats[p][k - 1];
-            // bmin + e is a delay of channel c, so the offset is >= 0
-            r.o[k] = c >= nchan ? -1 : bmin + e - start[c];
-            if (r.o[k] >= 0) raw_stride = std::max(raw_stride, round_up(r.o[k] + 4 * r.items + 4, 16));
+            emin = std::min(emin, e);
+            emax = std::max(emax, e);
           }
-          for (int i = 0; i < nd_cta; ++i)
-            if (pid[i] == static_cast<int>(p)) A[q * nd_cta + i] = row_words + delay(tile, c0, i) - bmin;
-          row_words += 4 * r.items;
-          rows.push_back(r);
+          Q.emin[k] = emin;
+          for (int p = 0; p < Q.npat; ++p) Q.shift[p][k] = (k == 0 ? 0 : pats[p][k - 1]) - emin;
+          // three loaded words must hold bytes (first & 3) + shift .. + 3
+          if (emax - emin > 2) return 1;
+          if (!Q.pad[k]) {
+            // channel window: times b + emin .. b + emax + L (+ the over-read)
+            start[c] = (b + emin) & ~15;
+            need[c] = b + emax + Q.L + 12 - start[c];
+            Q.raw_off[k] = b + emin - start[c];
+            raw_stride = std::max(raw_stride, round_up(need[c], 16));
+          } else {
+            Q.raw_off[k] = 0;
+          }
         }
+        for (int i = 0; i < nd_cta; ++i)
+          A[q * nd_cta + i] = row_words + pid[i] * Q.L + delay(tile, c0, i) - b;
+        row_words += Q.npat * Q.L;
+        quads.push_back(Q);
       }
       rec[2] = nq;
       prow_words = std::max(prow_words, row_words);
     }
+    for (int c = 0; c < t.nchan_pad; ++c) {
+      int32_t *m = &t.raw_meta[(static_cast<size_t>(tile) * t.nchan_pad + c) * 2];
+      m[0] = start[c];
+      m[1] = c < nchan ? need[c] : 0;
+    }
   }
-  // segment descriptors (need the final raw_stride for the byte offsets)
+  // build units (need the final raw_stride for the byte offsets)
   if (4 * kQuadsPerChunk * static_cast<int64_t>(raw_stride) >= 0xffff) return 1;
-  for (size_t rc = 0; rc < chunk_rows.size(); ++rc) {
+  for (size_t rc = 0; rc < chunk_quads.size(); ++rc) {
     int32_t *rec = &t.recs[rc * t.rec_words];
-    int32_t *segs = rec + segs_offset(nd_cta);
-    int nsegs = 0;
-    for (const Row &r : chunk_rows[rc]) {
-      for (int first = 0; first < r.items; first += 32) {
-        if (nsegs == kMaxSegments) return 1;
-        uint32_t addr[4], shift = 0;
-        for (int k = 0; k < 4; ++k) {
-          if (r.o[k] < 0) {
-            addr[k] = 0xffff;
-          } else {
-            addr[k] = static_cast<uint32_t>((4 * r.quad + k) * raw_stride + (r.o[k] & ~3) + 4 * first);
-            shift |= static_cast<uint32_t>(r.o[k] & 3) << (2 * k);
-          }
+    int32_t *units = rec + units_offset(nd_cta);
+    int nunits = 0;
+    for (size_t q = 0; q < chunk_quads[rc].size(); ++q) {
+      const Quad &Q = chunk_quads[rc][q];
+      const int items = Q.L / 4;
+      for (int first = 0; first < items; first += 32) {
+        if (nunits == kMaxUnits) return 1;
+        uint32_t addr[4];
+        for (int k = 0; k < 4; ++k)
+          addr[k] = Q.pad[k] ? 0xffffu
+                             : static_cast<uint32_t>((4 * static_cast<int>(q) + k) * raw_stride +
+                                                     (Q.raw_off[k] & ~3) + 4 * first);
+        int32_t *u = units + nunits * kUnitWords;
+        u[0] = static_cast<int32_t>(addr[0] | (addr[1] << 16));
+        u[1] = static_cast<int32_t>(addr[2] | (addr[3] << 16));
+        u[2] = (Q.row_off + 4 * first) | (std::min(32, items - first) << 20) | (Q.npat << 26);
+        u[3] = Q.L;
+        for (int w = 0; w < 4; ++w) u[4 + w] = 0;
+        for (int p = 0; p < Q.npat; ++p) {
+          uint32_t code = 0;
+          for (int k = 0; k < 4; ++k)
+            code |= static_cast<uint32_t>((Q.raw_off[k] & 3) + Q.shift[p][k]) << (3 * k);
+          u[4 + p / 2] |= static_cast<int32_t>(code << (12 * (p & 1)));
         }
-        const int32_t items = std::min(32, r.items - first);
-        int32_t *sd = segs + nsegs * kSegWords;
-        sd[0] = static_cast<int32_t>(addr[0] | (addr[1] << 16));
-        sd[1] = static_cast<int32_t>(addr[2] | (addr[3] << 16));
-        sd[2] = (r.off + 4 * first) | (items << 20);
-        sd[3] = static_cast<int32_t>(shift);
-        ++nsegs;
+        ++nunits;
       }
     }
-    rec[3] = nsegs;
+    rec[3] = nunits;
   }
   t.raw_stride = raw_stride;
   t.prow_words = prow_words;

@@ -19,7 +19,7 @@ import synth
 T_TILE = 512
 QUADS_PER_CHUNK = 4
 REC_HEADER = 4
-SEG_WORDS = 4
+UNIT_WORDS = 8
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -78,30 +78,37 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                         n = pitch - off
                     assert off % 16 == 0 and n % 16 == 0 and 0 < n <= rs and off >= 0
                     raw[s, :n] = block[c, off:off + n]
-                nq, nsegs = rec[2], rec[3]
-                segs_off = REC_HEADER + QUADS_PER_CHUNK * nd
-                segs = rec[segs_off:segs_off + SEG_WORDS * nsegs].reshape(-1, SEG_WORDS)
+                nq, nunits = rec[2], rec[3]
+                units_off = REC_HEADER + QUADS_PER_CHUNK * nd
+                units = rec[units_off:units_off + UNIT_WORDS * nunits].reshape(-1, UNIT_WORDS)
                 raw_flat = raw.reshape(-1)
                 prow = np.full((pw, 4), garbage, dtype=np.uint8)
                 written = np.zeros(pw, dtype=np.int64)
-                for d0w, d1w, d2w, d3w in segs.astype(np.int64) & 0xFFFFFFFF:  # one warp-wide step
-                    items = d2w >> 20
-                    word0 = d2w & 0xFFFFF
-                    assert 1 <= items <= 32 and word0 % 4 == 0
-                    offs = [d0w & 0xFFFF, d0w >> 16, d1w & 0xFFFF, d1w >> 16]
+                for u in units.astype(np.int64) & 0xFFFFFFFF:  # one warp-wide step
+                    items = (u[2] >> 20) & 63
+                    npat = u[2] >> 26
+                    dest0 = u[2] & 0xFFFFF
+                    L = u[3]
+                    assert 1 <= items <= 32 and 1 <= npat <= 8 and dest0 % 4 == 0 and L % 4 == 0
+                    offs = [u[0] & 0xFFFF, u[0] >> 16, u[1] & 0xFFFF, u[1] >> 16]
                     lanes = np.arange(items)
-                    words = (word0 + 4 * lanes[:, None] + np.arange(4)[None, :]).reshape(-1)
-                    assert words.max() < pw
-                    written[words] += 1
-                    for k in range(4):
-                        if offs[k] == 0xFFFF:
-                            prow[words, k] = 0
-                            continue
-                        sh = (d3w >> (2 * k)) & 3
-                        w = offs[k] + 4 * lanes
-                        assert w.min() % 4 == 0 and w.max() + 8 <= raw_flat.size  # two words
-                        byte = (w[:, None] + sh + np.arange(4)[None, :]).reshape(-1)
-                        prow[words, k] = raw_flat[byte]
+                    for p in range(npat):
+                        code = (u[4 + p // 2] >> (12 * (p & 1))) & 0xFFF
+                        words = (dest0 + p * L + 4 * lanes[:, None] + np.arange(4)[None, :]).reshape(-1)
+                        assert words.max() < pw
+                        written[words] += 1
+                        for k in range(4):
+                            if offs[k] == 0xFFFF:
+                                prow[words, k] = 0
+                                continue
+                            sh = (code >> (3 * k)) & 7
+                            assert 0 <= sh <= 5
+                            base = offs[k] + 4 * lanes
+                            slot = offs[k] // rs
+                            # three aligned words, all inside this channel's slot
+                            assert base.min() % 4 == 0 and (base.max() + 11) // rs == slot
+                            byte = (base[:, None] + sh + np.arange(4)[None, :]).reshape(-1)
+                            prow[words, k] = raw_flat[byte]
                 assert written.max() <= 1  # no row word is built twice
                 A = rec[REC_HEADER:REC_HEADER + QUADS_PER_CHUNK * nd].reshape(QUADS_PER_CHUNK, nd)
                 for q in range(nq):
