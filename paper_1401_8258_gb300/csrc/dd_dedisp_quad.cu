@@ -351,34 +351,51 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
       issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
       issued = m + 1;
     }
+    // accumulate chunk k (four channels per dp4a) and build this warp's share
+    // of chunk k+1's rows after each quad; the copies of chunk k+1 are waited
+    // for (bounded) just before the first build step, and each quad's offset
+    // table is fetched one quad ahead
     const bool next = k + 1 < a.nchunks;
-    if (next) ok = warp_wait(tma_bar(k + 1), ((k + 1) / kRawStages) & 1, a.timeout_ns, lane);
-    if (!ok) continue;  // reported at the next barrier
-    // accumulate chunk k (four channels per dp4a) while building the rows
-    // of chunk k+1: this warp's build segments are spread over the quads
     const int32_t *rec = rec_ptr(k);
     const int nq = rec[2];
     const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
     const uint32_t prow = prow_addr(k);
     const int32_t *rec_n = rec_ptr(k + 1);
-    const int nseg_w = next ? warp_segments(rec_n, warp) : 0;
+    int nseg_w = -1;  // build units of chunk k+1 for this warp, once its copies landed
     int m_done = 0;
+    int4 a_next[ND_THR / 4];
+#pragma unroll
+    for (int i4 = 0; i4 < ND_THR / 4; ++i4) a_next[i4] = reinterpret_cast<const int4 *>(A)[i4];
 #pragma unroll 1
     for (int q = 0; q < kQuadsPerChunk; ++q) {
-      const int m_to = (nseg_w * (q + 1) + kQuadsPerChunk - 1) / kQuadsPerChunk;
-      if (m_to > m_done) {
-        build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), kSegsOff, warp, lane, m_done, m_to);
-        m_done = m_to;
+      if (q < nq) {
+        int4 a_cur[ND_THR / 4];
+#pragma unroll
+        for (int i4 = 0; i4 < ND_THR / 4; ++i4) a_cur[i4] = a_next[i4];
+        if (q + 1 < nq) {
+#pragma unroll
+          for (int i4 = 0; i4 < ND_THR / 4; ++i4)
+            a_next[i4] = reinterpret_cast<const int4 *>(A + (q + 1) * ND_CTA)[i4];
+        }
+#pragma unroll
+        for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
+          const int off[4] = {a_cur[i4].x, a_cur[i4].y, a_cur[i4].z, a_cur[i4].w};
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii)
+            Acc8<0>::run(acc[4 * i4 + ii], prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word));
+        }
       }
-      if (q >= nq) continue;
-      const int4 *A4 = reinterpret_cast<const int4 *>(A + q * ND_CTA);
-#pragma unroll
-      for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
-        const int4 a4 = A4[i4];
-        const int off[4] = {a4.x, a4.y, a4.z, a4.w};
-#pragma unroll
-        for (int ii = 0; ii < 4; ++ii)
-          Acc8<0>::run(acc[4 * i4 + ii], prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word));
+      if (next && ok) {
+        if (nseg_w < 0) {
+          ok = warp_wait(tma_bar(k + 1), ((k + 1) / kRawStages) & 1, a.timeout_ns, lane);
+          if (!ok) continue;  // reported at the next barrier
+          nseg_w = warp_segments(rec_n, warp);
+        }
+        const int m_to = (nseg_w * (q + 1) + kQuadsPerChunk - 1) / kQuadsPerChunk;
+        if (m_to > m_done) {
+          build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), kSegsOff, warp, lane, m_done, m_to);
+          m_done = m_to;
+        }
       }
     }
   }
