@@ -197,7 +197,7 @@ __device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, 
 // build unit (dd_quad.h) at a time: lane l builds item first+l (4 output
 // samples) of every row.  Per channel it loads the three aligned words that
 // hold the earliest needed sample and the next 8 bytes -- enough for every
-// pattern, whose first samples differ by at most 2 -- then for each pattern
+// pattern, whose first samples differ by at most 4 -- then for each pattern
 // funnels out the 4 samples at that pattern's byte shift; a 4x4 byte transpose
 // turns the four channels' words into four row words.
 __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint32_t prow,
@@ -229,7 +229,7 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint
     uint32_t v[4];
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
-      const uint32_t sh = (code >> (3 * ch)) & 7u;  // 0..5 bytes into w0:w1:w2
+      const uint32_t sh = (code >> (3 * ch)) & 7u;  // 0..7 bytes into w0:w1:w2
       const uint32_t lo = sh >= 4u ? w1[ch] : w0[ch];
       const uint32_t hi = sh >= 4u ? w2[ch] : w1[ch];
       v[ch] = prmt(lo, hi, 0x3210u + 0x1111u * (sh & 3u));
@@ -242,20 +242,20 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint
   }
 }
 
-// This warp's build units m = m0 .. m1-1 of a chunk (unit index warp + 16*m).
+// This warp's build units m0 .. m1-1 (counted within its own list).
 __device__ __forceinline__ void build_rows(const int32_t *rec, uint32_t raw, uint32_t prow,
-                                           int units_off, int warp, int lane, int m0, int m1) {
-  constexpr int kWarps = kThreads / 32;
+                                           int units_off, int warp, int lane, int m0, int m1,
+                                           int starts_off) {
+  const int first = reinterpret_cast<const uint16_t *>(rec + starts_off)[warp];
   const int32_t *units = rec + units_off;
 #pragma unroll 1
-  for (int m = m0; m < m1; ++m) build_unit(units + (warp + kWarps * m) * kUnitWords, raw, prow, lane);
+  for (int m = m0; m < m1; ++m) build_unit(units + (first + m) * kUnitWords, raw, prow, lane);
 }
 
-// Build units a warp takes per chunk: ceil((nunits - warp) / 16).
-__device__ __forceinline__ int warp_segments(const int32_t *rec, int warp) {
-  constexpr int kWarps = kThreads / 32;
-  const int nunits = rec[3];
-  return nunits > warp ? (nunits - warp + kWarps - 1) / kWarps : 0;
+// Build units this warp takes in a chunk.
+__device__ __forceinline__ int warp_segments(const int32_t *rec, int warp, int starts_off) {
+  const uint16_t *starts = reinterpret_cast<const uint16_t *>(rec + starts_off);
+  return starts[warp + 1] - starts[warp];
 }
 
 // Warp-wide bounded wait on an mbarrier phase: lane 0 waits (sleeping in
@@ -274,6 +274,7 @@ template <int ND_THR>
 __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
   constexpr int kSegsOff = units_offset(ND_CTA);
+  constexpr int kStartsOff = warp_start_offset(ND_CTA);
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -337,7 +338,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   bool ok = warp_wait(tma_bar(0), 0, a.timeout_ns, lane);
   if (ok)
     build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), kSegsOff, warp, lane, 0,
-               warp_segments(rec_ptr(0), warp));
+               warp_segments(rec_ptr(0), warp, kStartsOff), kStartsOff);
 
   bool aborted = false;
   for (int k = 0; k < a.nchunks; ++k) {
@@ -389,11 +390,12 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
         if (nseg_w < 0) {
           ok = warp_wait(tma_bar(k + 1), ((k + 1) / kRawStages) & 1, a.timeout_ns, lane);
           if (!ok) continue;  // reported at the next barrier
-          nseg_w = warp_segments(rec_n, warp);
+          nseg_w = warp_segments(rec_n, warp, kStartsOff);
         }
         const int m_to = (nseg_w * (q + 1) + kQuadsPerChunk - 1) / kQuadsPerChunk;
         if (m_to > m_done) {
-          build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), kSegsOff, warp, lane, m_done, m_to);
+          build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), kSegsOff, warp, lane, m_done, m_to,
+                     kStartsOff);
           m_done = m_to;
         }
       }

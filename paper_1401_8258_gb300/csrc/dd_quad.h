@@ -29,8 +29,12 @@
 //         patterns << 26;
 //     [3] row length L in words;
 //     [4..7] per pattern p (two per word, 12 bits each): for channel k a
-//         3-bit byte shift 0..5 of the pattern's first sample within the
+//         3-bit byte shift 0..7 of the pattern's first sample within the
 //         three loaded words.
+//   warp_start[kThreads/32 + 1] (int16 pairs, after the units): the units are
+//     ordered by the warp that builds them (balanced on the host, largest
+//     first onto the least loaded warp); warp w builds units
+//     warp_start[w] .. warp_start[w+1]-1.
 // raw_meta[tile][nchan_pad][2]: {window start relative to the tile's first
 // output sample (a multiple of 16), bytes needed (0 = padding channel)}.
 #pragma once
@@ -76,8 +80,9 @@ constexpr int kMaxUnits = 32;
 constexpr int kMaxSmem = 227 * 1024;
 
 DDQ_HD constexpr int units_offset(int nd_cta) { return kRecHeader + kQuadsPerChunk * nd_cta; }
+DDQ_HD constexpr int warp_start_offset(int nd_cta) { return units_offset(nd_cta) + kMaxUnits * kUnitWords; }
 DDQ_HD constexpr int rec_words(int nd_cta) {
-  return (units_offset(nd_cta) + kMaxUnits * kUnitWords + 3) / 4 * 4;
+  return (warp_start_offset(nd_cta) + (kThreads / 32 + 2) / 2 + 3) / 4 * 4;
 }
 
 struct Tables {

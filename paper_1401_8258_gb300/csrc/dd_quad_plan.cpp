@@ -102,8 +102,9 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
           }
           Q.emin[k] = emin;
           for (int p = 0; p < Q.npat; ++p) Q.shift[p][k] = (k == 0 ? 0 : pats[p][k - 1]) - emin;
-          // three loaded words must hold bytes (first & 3) + shift .. + 3
-          if (emax - emin > 2) return 1;
+          // the three loaded words hold bytes (first & 3) + shift .. + 3 when
+          // the shift code (first & 3) + e - emin stays within 0..7
+          if (emax - emin > 4) return 1;
           if (!Q.pad[k]) {
             // channel window: times b + emin .. b + emax + L (+ the over-read)
             start[c] = (b + emin) & ~15;
@@ -130,36 +131,59 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
   }
   // build units (need the final raw_stride for the byte offsets)
   if (4 * kQuadsPerChunk * static_cast<int64_t>(raw_stride) >= 0xffff) return 1;
+  constexpr int kWarps = kThreads / 32;
   for (size_t rc = 0; rc < chunk_quads.size(); ++rc) {
     int32_t *rec = &t.recs[rc * t.rec_words];
-    int32_t *units = rec + units_offset(nd_cta);
-    int nunits = 0;
+    std::vector<std::array<int32_t, kUnitWords>> list;
     for (size_t q = 0; q < chunk_quads[rc].size(); ++q) {
       const Quad &Q = chunk_quads[rc][q];
       const int items = Q.L / 4;
       for (int first = 0; first < items; first += 32) {
-        if (nunits == kMaxUnits) return 1;
         uint32_t addr[4];
         for (int k = 0; k < 4; ++k)
           addr[k] = Q.pad[k] ? 0xffffu
                              : static_cast<uint32_t>((4 * static_cast<int>(q) + k) * raw_stride +
                                                      (Q.raw_off[k] & ~3) + 4 * first);
-        int32_t *u = units + nunits * kUnitWords;
+        std::array<int32_t, kUnitWords> u{};
         u[0] = static_cast<int32_t>(addr[0] | (addr[1] << 16));
         u[1] = static_cast<int32_t>(addr[2] | (addr[3] << 16));
         u[2] = (Q.row_off + 4 * first) | (std::min(32, items - first) << 20) | (Q.npat << 26);
         u[3] = Q.L;
-        for (int w = 0; w < 4; ++w) u[4 + w] = 0;
         for (int p = 0; p < Q.npat; ++p) {
           uint32_t code = 0;
           for (int k = 0; k < 4; ++k)
             code |= static_cast<uint32_t>((Q.raw_off[k] & 3) + Q.shift[p][k]) << (3 * k);
           u[4 + p / 2] |= static_cast<int32_t>(code << (12 * (p & 1)));
         }
-        ++nunits;
+        list.push_back(u);
       }
     }
-    rec[3] = nunits;
+    if (static_cast<int>(list.size()) > kMaxUnits) return 1;
+    // balance: largest unit first onto the least loaded warp (cost ~ loads +
+    // one row store per pattern), then order the units by warp
+    std::vector<int> order(list.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
+    auto cost = [&](int i) { return 2 + (static_cast<uint32_t>(list[i][2]) >> 26); };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<int> load(kWarps, 0);
+    std::vector<std::vector<int>> per_warp(kWarps);
+    for (int i : order) {
+      const int w = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+      load[w] += cost(i);
+      per_warp[w].push_back(i);
+    }
+    int32_t *units = rec + units_offset(nd_cta);
+    uint16_t *starts = reinterpret_cast<uint16_t *>(rec + warp_start_offset(nd_cta));
+    int n = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      starts[w] = static_cast<uint16_t>(n);
+      for (int i : per_warp[w]) {
+        for (int j = 0; j < kUnitWords; ++j) units[n * kUnitWords + j] = list[i][j];
+        ++n;
+      }
+    }
+    starts[kWarps] = static_cast<uint16_t>(n);
+    rec[3] = n;
   }
   t.raw_stride = raw_stride;
   t.prow_words = prow_words;

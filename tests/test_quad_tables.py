@@ -81,6 +81,9 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                 nq, nunits = rec[2], rec[3]
                 units_off = REC_HEADER + QUADS_PER_CHUNK * nd
                 units = rec[units_off:units_off + UNIT_WORDS * nunits].reshape(-1, UNIT_WORDS)
+                # per-warp unit ranges (16 warps), int16 pairs after the unit array
+                starts = rec[units_off + UNIT_WORDS * 32:].view(np.uint16)[:17]
+                assert starts[0] == 0 and starts[16] == nunits and np.all(np.diff(starts.astype(int)) >= 0)
                 raw_flat = raw.reshape(-1)
                 prow = np.full((pw, 4), garbage, dtype=np.uint8)
                 written = np.zeros(pw, dtype=np.int64)
@@ -102,7 +105,7 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                                 prow[words, k] = 0
                                 continue
                             sh = (code >> (3 * k)) & 7
-                            assert 0 <= sh <= 5
+                            assert 0 <= sh <= 7
                             base = offs[k] + 4 * lanes
                             slot = offs[k] // rs
                             # three aligned words, all inside this channel's slot
