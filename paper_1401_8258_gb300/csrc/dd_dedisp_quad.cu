@@ -1,27 +1,30 @@
 // dd_dedisp_quad.cu -- staged dedispersion kernel for u8 filterbanks.
 //
 // D[d][t] = sum_c I[c][t + delay(c,d)]   (Sec. 2.1.1, brute-force equation),
-// exact in int32.
+// exact in integers.
 //
-// Data flow per CTA (one DM tile x one 512-sample time tile), per chunk of
-// 16 channels:
+// Data flow per CTA (one DM tile x one 512-sample time tile, taken as 256
+// sample pairs (t, t + 256)), per chunk of 16 channels:
 //   1. one warp queues bulk copies (cp.async.bulk, the TMA engine) of each
 //      channel's input window -- the "channel vector" of Sec. 2.4, sized by
 //      the largest and smallest delay of the tile -- plus the chunk's plan
 //      record into shared memory, signalling an mbarrier; copies run three
 //      chunks ahead of the accumulation (triple-buffered windows);
-//   2. all threads interleave the four channels of every quad into pattern
-//      rows: word i of a row holds the four channels' samples that one
-//      relative-delay pattern adds at one output time (dd_quad_plan.cpp);
-//      rows of chunk k+1 are built while chunk k is accumulated (double
-//      buffer), with one CTA barrier per chunk;
-//   3. every thread adds, for each of its DM trials and output samples, one
-//      32-bit row word with a 4-way byte dot product (dp4a, weights 1) into
-//      an int32 register accumulator: four channel-adds per instruction and
-//      one shared-memory word per four adds.
+//   2. all threads build pattern rows: word i of a row holds, for one
+//      relative-delay pattern of a quad of channels, the four channels' sum
+//      at pair i as two 16-bit halves (dd_quad_plan.cpp); rows of chunk k+1
+//      are built while chunk k is accumulated (double buffer), with one CTA
+//      barrier per chunk;
+//   3. every thread adds, for each of its DM trials and sample pairs, the
+//      row words of two quads to a packed accumulator with one three-input
+//      integer add: 16 channel-samples per instruction and 8 per 32-bit
+//      shared-memory word.  Every 64 quads the 16-bit halves are drained into
+//      32-bit sums kept in tensor memory (tcgen05.st / tcgen05.ld), which
+//      spares the 64 registers per thread they would take.
 // Waits on the mbarriers are bounded (globaltimer): on expiry the CTA records
 // DD_ERR_DEVICE_TIMEOUT in the plan's status word, waits (bounded) for its
-// own copies still in flight, and returns without writing output.
+// own copies still in flight, frees its tensor memory and returns without
+// writing output.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -111,24 +114,63 @@ __device__ __forceinline__ uint32_t lds32_off(uint32_t addr) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t dp4a_ones(uint32_t a, uint32_t acc) {
-  uint32_t r;
-  asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(a), "r"(0x01010101u), "r"(acc));
-  return r;
-}
-
+// acc[j] += word at a + 128 j (+ word at b + 128 j) for j = J..kPairsPerThread-1
 template <int J>
-struct Acc8 {
-  // acc[j] += dp4a(word at base + 128 j) for j = J..7
-  static __device__ __forceinline__ void run(int (&acc)[kTimesPerThread], uint32_t base) {
-    acc[J] = static_cast<int>(dp4a_ones(lds32_off<128 * J>(base), static_cast<uint32_t>(acc[J])));
-    Acc8<J + 1>::run(acc, base);
+struct AccPairs {
+  static __device__ __forceinline__ void two(uint32_t (&acc)[kPairsPerThread], uint32_t a,
+                                             uint32_t b) {
+    acc[J] += lds32_off<128 * J>(a) + lds32_off<128 * J>(b);
+    AccPairs<J + 1>::two(acc, a, b);
+  }
+  static __device__ __forceinline__ void one(uint32_t (&acc)[kPairsPerThread], uint32_t a) {
+    acc[J] += lds32_off<128 * J>(a);
+    AccPairs<J + 1>::one(acc, a);
   }
 };
 template <>
-struct Acc8<kTimesPerThread> {
-  static __device__ __forceinline__ void run(int (&)[kTimesPerThread], uint32_t) {}
+struct AccPairs<kPairsPerThread> {
+  static __device__ __forceinline__ void two(uint32_t (&)[kPairsPerThread], uint32_t, uint32_t) {}
+  static __device__ __forceinline__ void one(uint32_t (&)[kPairsPerThread], uint32_t) {}
 };
+
+// ---- tensor memory (per-CTA scratch for the 32-bit sums) ----
+__device__ __forceinline__ void tmem_alloc(uint32_t dst_smem, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(dst_smem),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols)
+               : "memory");
+}
+__device__ __forceinline__ void tmem_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// 16 consecutive 32-bit columns of this thread's lane
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]),
+      "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+      "%12, %13, %14, %15}, [%16];\n\t"
+      "tcgen05.wait::ld.sync.aligned;"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+        "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+        "=r"(v[14]), "=r"(v[15])
+      : "r"(taddr)
+      : "memory");
+}
 
 __device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c,
                                        uint32_t d) {
@@ -167,15 +209,23 @@ struct QuadArgs {
 __device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, int64_t t_cta,
                             int ch, uint32_t bar, uint32_t rec_dst, uint32_t raw_dst, int lane) {
   constexpr int kSlots = 4 * kQuadsPerChunk;
-  uint32_t len = 0;
+  uint32_t len = 0, skip = 0;
+  int64_t lo = 0;
   const int c = ch * kSlots + lane;
   if (lane < kSlots && c < a.nchan_pad) {
     const int32_t start = meta_s[2 * c], need = meta_s[2 * c + 1];
     if (need > 0) {
-      const int64_t off = t_cta + start;                     // multiple of 16
-      int64_t n = (static_cast<int64_t>(need) + 15) & ~static_cast<int64_t>(15);
-      if (off + n > a.pitch) n = a.pitch - off;              // stay inside the row
-      len = static_cast<uint32_t>(n);
+      // window [off, off + need) rounded to 16 bytes and clipped to the row;
+      // its part before the row start (off = -16 in the first time tile)
+      // feeds only row words no trial reads
+      const int64_t off = t_cta + start;  // multiple of 16
+      int64_t hi = off + ((static_cast<int64_t>(need) + 15) & ~static_cast<int64_t>(15));
+      if (hi > a.pitch) hi = a.pitch;
+      lo = off < 0 ? 0 : off;
+      if (hi > lo) {
+        len = static_cast<uint32_t>(hi - lo);
+        skip = static_cast<uint32_t>(lo - off);
+      }
     }
   }
   uint32_t total = len;
@@ -188,18 +238,19 @@ __device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, 
   }
   __syncwarp();
   if (len > 0) {
-    const uint8_t *src = a.block + static_cast<int64_t>(c) * a.pitch + t_cta + meta_s[2 * c];
-    bulk_g2s(raw_dst + lane * a.raw_stride, src, len, bar);
+    const uint8_t *src = a.block + static_cast<int64_t>(c) * a.pitch + lo;
+    bulk_g2s(raw_dst + lane * a.raw_stride + skip, src, len, bar);
   }
 }
 
-// Interleave the four channels of a quad into all of its pattern rows, one
-// build unit (dd_quad.h) at a time: lane l builds item first+l (4 output
-// samples) of every row.  Per channel it loads the three aligned words that
-// hold the earliest needed sample and the next 8 bytes -- enough for every
-// pattern, whose first samples differ by at most 4 -- then for each pattern
-// funnels out the 4 samples at that pattern's byte shift; a 4x4 byte transpose
-// turns the four channels' words into four row words.
+// Build all pattern rows of a quad, one build unit (dd_quad.h) at a time:
+// lane l builds item first+l (4 row words) of every row.  Per channel it
+// loads the two aligned words that hold the earliest needed sample and the
+// next 4 bytes, for the first and the second half of the pair (kHalf bytes
+// on) -- enough for every pattern, whose byte shifts stay within 0..4.  For
+// each pattern it funnels out the 4 samples at that pattern's shift and sums
+// the four channels in 16-bit lanes: the odd bytes (prmt) and the whole words
+// are summed, and the even-byte sum is their difference (exact modulo 2^32).
 __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint32_t prow,
                                            int lane) {
   const int4 d0 = reinterpret_cast<const int4 *>(ud)[0];
@@ -209,14 +260,15 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint
   const uint32_t npat = static_cast<uint32_t>(d0.z) >> 26;
   const uint32_t off[4] = {static_cast<uint32_t>(d0.x) & 0xffffu, static_cast<uint32_t>(d0.x) >> 16,
                            static_cast<uint32_t>(d0.y) & 0xffffu, static_cast<uint32_t>(d0.y) >> 16};
-  uint32_t w0[4], w1[4], w2[4];
+  uint32_t a0[4], a1[4], b0[4], b1[4];
 #pragma unroll
   for (int ch = 0; ch < 4; ++ch) {
     const bool pad = off[ch] == 0xffffu;                         // padding channel: zeros
     const uint32_t w = raw + (pad ? 0u : off[ch]) + 4u * lane;  // always in bounds
-    w0[ch] = pad ? 0u : lds32(w);
-    w1[ch] = pad ? 0u : lds32_off<4>(w);
-    w2[ch] = pad ? 0u : lds32_off<8>(w);
+    a0[ch] = pad ? 0u : lds32(w);
+    a1[ch] = pad ? 0u : lds32_off<4>(w);
+    b0[ch] = pad ? 0u : lds32_off<kHalf>(w);
+    b1[ch] = pad ? 0u : lds32_off<kHalf + 4>(w);
   }
   const uint32_t codes[4] = {static_cast<uint32_t>(d1.x), static_cast<uint32_t>(d1.y),
                              static_cast<uint32_t>(d1.z), static_cast<uint32_t>(d1.w)};
@@ -226,18 +278,20 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint
   for (int p = 0; p < kMaxPatterns; ++p) {
     if (static_cast<uint32_t>(p) >= npat) break;
     const uint32_t code = (codes[p >> 1] >> (12 * (p & 1))) & 0xfffu;
-    uint32_t v[4];
+    uint32_t sa = 0, sb = 0, oa = 0, ob = 0;  // word sums and odd-byte sums
 #pragma unroll
     for (int ch = 0; ch < 4; ++ch) {
-      const uint32_t sh = (code >> (3 * ch)) & 7u;  // 0..7 bytes into w0:w1:w2
-      const uint32_t lo = sh >= 4u ? w1[ch] : w0[ch];
-      const uint32_t hi = sh >= 4u ? w2[ch] : w1[ch];
-      v[ch] = prmt(lo, hi, 0x3210u + 0x1111u * (sh & 3u));
+      const uint32_t sel = 0x3210u + 0x1111u * ((code >> (3 * ch)) & 7u);  // shift 0..4
+      const uint32_t va = prmt(a0[ch], a1[ch], sel), vb = prmt(b0[ch], b1[ch], sel);
+      sa += va;
+      sb += vb;
+      oa += prmt(va, 0u, 0x4341u);  // bytes 1, 3 -> 16-bit lanes
+      ob += prmt(vb, 0u, 0x4341u);
     }
-    const uint32_t lo01 = prmt(v[0], v[1], 0x5140u), hi01 = prmt(v[0], v[1], 0x7362u);
-    const uint32_t lo23 = prmt(v[2], v[3], 0x5140u), hi23 = prmt(v[2], v[3], 0x7362u);
-    sts128(dst, prmt(lo01, lo23, 0x5410u), prmt(lo01, lo23, 0x7632u), prmt(hi01, hi23, 0x5410u),
-           prmt(hi01, hi23, 0x7632u));
+    const uint32_t ea = sa - (oa << 8), eb = sb - (ob << 8);  // bytes 0, 2 sums
+    // word w + j: low half = first-half sum at sample j, high half = second
+    sts128(dst, prmt(ea, eb, 0x5410u), prmt(oa, ob, 0x5410u), prmt(ea, eb, 0x7632u),
+           prmt(oa, ob, 0x7632u));
     dst += row_bytes;
   }
 }
@@ -270,11 +324,49 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_
   return ok != 0;
 }
 
+// Drain the packed accumulators into the 32-bit sums in tensor memory
+// (column 8 i + 2 j + h of this thread's lane holds trial i, pair j, half h).
+// FINAL: add the stored sums (if `load`) and write the output instead.
+template <int ND_THR>
+__device__ __forceinline__ void drain(uint32_t (&acc)[ND_THR][kPairsPerThread], uint32_t taddr,
+                                      bool load) {
+#pragma unroll
+  for (int blk = 0; blk < ND_THR / 2; ++blk) {
+    uint32_t v[16];
+    if (load) {
+      tmem_ld16(taddr + 16u * blk, v);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 16; ++m) v[m] = 0;
+    }
+#pragma unroll
+    for (int ii = 0; ii < 2; ++ii)
+#pragma unroll
+      for (int j = 0; j < kPairsPerThread; ++j) {
+        const uint32_t w = acc[2 * blk + ii][j];
+        v[8 * ii + 2 * j] += w & 0xffffu;
+        v[8 * ii + 2 * j + 1] += w >> 16;
+        acc[2 * blk + ii][j] = 0;
+      }
+    tmem_st16(taddr + 16u * blk, v);
+  }
+}
+
 template <int ND_THR>
 __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
   constexpr int kSegsOff = units_offset(ND_CTA);
   constexpr int kStartsOff = warp_start_offset(ND_CTA);
+  // tensor-memory columns: 4 warps share each 32-lane quarter, each thread
+  // keeps 2 * ND_THR * kPairsPerThread sums
+  constexpr uint32_t kColsPerThread = 2 * ND_THR * kPairsPerThread;
+  constexpr uint32_t kTmemCols = 4 * kColsPerThread;
+  static_assert(kColsPerThread % 16 == 0 && kTmemCols >= 32 && kTmemCols <= 512 &&
+                    (kTmemCols & (kTmemCols - 1)) == 0,
+                "tensor-memory allocation must be a power of two in 32..512 columns");
+  static_assert(kThreads / 32 == 16, "four warps per tensor-memory lane quarter");
+  static_assert(kFlushQuads % kQuadsPerChunk == 0, "drain at chunk boundaries");
+  constexpr int kFlushChunks = kFlushQuads / kQuadsPerChunk;
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -286,8 +378,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   const int tile = blockIdx.x;
   const int64_t t_cta = static_cast<int64_t>(blockIdx.y) * kTimeTile;
 
-  // shared-memory layout (dd_quad.h): copy mbarriers, raw window table,
-  // records, raw window buffers, pattern-row buffers
+  // shared-memory layout (dd_quad.h): copy mbarriers and tensor-memory
+  // address, raw window table, records, raw window buffers, pattern rows
   const uint32_t bar0 = smem_addr(smem);
   auto tma_bar = [&](int m) { return bar0 + 8u * (m % kRawStages); };
   int32_t *meta_s = reinterpret_cast<int32_t *>(smem + kBarrierBytes);
@@ -311,7 +403,14 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     for (int b = 0; b < kRawStages; ++b) mbar_init(tma_bar(b), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  if (warp == 0) tmem_alloc(bar0 + kTmemSlot, kTmemCols);
+  tmem_fence_before();
   __syncthreads();
+  tmem_fence_after();
+  const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem + kTmemSlot);
+  // this warp's lane quarter (bits 31..16) and column block
+  const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                         static_cast<uint32_t>(warp >> 2) * kColsPerThread;
 
   // Pipeline (chunk m uses raw stage m%3, record stage m%4, row stage m%2):
   // iteration k starts with a CTA barrier (rows of chunk k built, chunk k-1
@@ -328,19 +427,21 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     issued = prefill;
   }
 
-  int acc[ND_THR][kTimesPerThread];
+  uint32_t acc[ND_THR][kPairsPerThread];
 #pragma unroll
   for (int i = 0; i < ND_THR; ++i)
 #pragma unroll
-    for (int j = 0; j < kTimesPerThread; ++j) acc[i][j] = 0;
-  const uint32_t my_word = static_cast<uint32_t>(tg * 32 * kTimesPerThread + lane);
+    for (int j = 0; j < kPairsPerThread; ++j) acc[i][j] = 0;
+  const uint32_t my_pair = static_cast<uint32_t>(tg * 32 * kPairsPerThread + lane);
 
   bool ok = warp_wait(tma_bar(0), 0, a.timeout_ns, lane);
   if (ok)
     build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), kSegsOff, warp, lane, 0,
                warp_segments(rec_ptr(0), warp, kStartsOff), kStartsOff);
 
+  constexpr int kSteps = kQuadsPerChunk / 2;  // two quads per step
   bool aborted = false;
+  bool drained = false;  // tensor memory holds sums
   for (int k = 0; k < a.nchunks; ++k) {
     if (__syncthreads_or(!ok)) {
       aborted = true;
@@ -352,10 +453,10 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
       issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
       issued = m + 1;
     }
-    // accumulate chunk k (four channels per dp4a) and build this warp's share
-    // of chunk k+1's rows after each quad; the copies of chunk k+1 are waited
-    // for (bounded) just before the first build step, and each quad's offset
-    // table is fetched one quad ahead
+    // accumulate chunk k (two quads per step) and build this warp's share of
+    // chunk k+1's rows after each step; the copies of chunk k+1 are waited
+    // for (bounded) just before the first build step, and each step's offset
+    // table is fetched one step ahead
     const bool next = k + 1 < a.nchunks;
     const int32_t *rec = rec_ptr(k);
     const int nq = rec[2];
@@ -364,26 +465,48 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     const int32_t *rec_n = rec_ptr(k + 1);
     int nseg_w = -1;  // build units of chunk k+1 for this warp, once its copies landed
     int m_done = 0;
-    int4 a_next[ND_THR / 4];
+    int4 a_next[2][ND_THR / 4];
 #pragma unroll
-    for (int i4 = 0; i4 < ND_THR / 4; ++i4) a_next[i4] = reinterpret_cast<const int4 *>(A)[i4];
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int i4 = 0; i4 < ND_THR / 4; ++i4)
+        a_next[h][i4] = reinterpret_cast<const int4 *>(A + h * ND_CTA)[i4];
 #pragma unroll 1
-    for (int q = 0; q < kQuadsPerChunk; ++q) {
+    for (int st = 0; st < kSteps; ++st) {
+      const int q = 2 * st;
       if (q < nq) {
-        int4 a_cur[ND_THR / 4];
+        int4 a_cur[2][ND_THR / 4];
 #pragma unroll
-        for (int i4 = 0; i4 < ND_THR / 4; ++i4) a_cur[i4] = a_next[i4];
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int i4 = 0; i4 < ND_THR / 4; ++i4) a_cur[h][i4] = a_next[h][i4];
+        if (q + 2 < nq) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i4 = 0; i4 < ND_THR / 4; ++i4)
+              a_next[h][i4] = reinterpret_cast<const int4 *>(A + (q + 2 + h) * ND_CTA)[i4];
+        }
         if (q + 1 < nq) {
 #pragma unroll
-          for (int i4 = 0; i4 < ND_THR / 4; ++i4)
-            a_next[i4] = reinterpret_cast<const int4 *>(A + (q + 1) * ND_CTA)[i4];
-        }
+          for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
+            const int o0[4] = {a_cur[0][i4].x, a_cur[0][i4].y, a_cur[0][i4].z, a_cur[0][i4].w};
+            const int o1[4] = {a_cur[1][i4].x, a_cur[1][i4].y, a_cur[1][i4].z, a_cur[1][i4].w};
 #pragma unroll
-        for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
-          const int off[4] = {a_cur[i4].x, a_cur[i4].y, a_cur[i4].z, a_cur[i4].w};
+            for (int ii = 0; ii < 4; ++ii)
+              AccPairs<0>::two(acc[4 * i4 + ii],
+                               prow + 4u * (static_cast<uint32_t>(o0[ii]) + my_pair),
+                               prow + 4u * (static_cast<uint32_t>(o1[ii]) + my_pair));
+          }
+        } else {
 #pragma unroll
-          for (int ii = 0; ii < 4; ++ii)
-            Acc8<0>::run(acc[4 * i4 + ii], prow + 4u * (static_cast<uint32_t>(off[ii]) + my_word));
+          for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
+            const int o0[4] = {a_cur[0][i4].x, a_cur[0][i4].y, a_cur[0][i4].z, a_cur[0][i4].w};
+#pragma unroll
+            for (int ii = 0; ii < 4; ++ii)
+              AccPairs<0>::one(acc[4 * i4 + ii],
+                               prow + 4u * (static_cast<uint32_t>(o0[ii]) + my_pair));
+          }
         }
       }
       if (next && ok) {
@@ -392,13 +515,18 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
           if (!ok) continue;  // reported at the next barrier
           nseg_w = warp_segments(rec_n, warp, kStartsOff);
         }
-        const int m_to = (nseg_w * (q + 1) + kQuadsPerChunk - 1) / kQuadsPerChunk;
+        const int m_to = (nseg_w * (st + 1) + kSteps - 1) / kSteps;
         if (m_to > m_done) {
           build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), kSegsOff, warp, lane, m_done, m_to,
                      kStartsOff);
           m_done = m_to;
         }
       }
+    }
+    // at most kFlushQuads quads in the 16-bit halves
+    if ((k + 1) % kFlushChunks == 0 && next) {
+      drain<ND_THR>(acc, taddr, drained);
+      drained = true;
     }
   }
   if (!aborted && __syncthreads_or(!ok)) aborted = true;  // last chunk's copy wait
@@ -412,20 +540,41 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
       for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
         mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, a.timeout_ns);
     }
-    return;
-  }
-
+  } else {
+    // final sums: stored part (if any) + the packed halves; pair j of trial
+    // i covers samples my_pair + 32 j and my_pair + 32 j + kHalf
 #pragma unroll
-  for (int i = 0; i < ND_THR; ++i) {
-    const int d = tile * ND_CTA + dg * ND_THR + i;
-    if (d >= a.ndm) continue;
-    int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
+    for (int blk = 0; blk < ND_THR / 2; ++blk) {
+      uint32_t v[16];
+      if (drained) {
+        tmem_ld16(taddr + 16u * blk, v);
+      } else {
 #pragma unroll
-    for (int j = 0; j < kTimesPerThread; ++j) {
-      const int64_t t = t_cta + my_word + 32 * j;
-      if (t < a.nsamp_out) orow[t] = acc[i][j];
+        for (int m = 0; m < 16; ++m) v[m] = 0;
+      }
+#pragma unroll
+      for (int ii = 0; ii < 2; ++ii) {
+        const int i = 2 * blk + ii;
+        const int d = tile * ND_CTA + dg * ND_THR + i;
+        if (d >= a.ndm) continue;
+        int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
+#pragma unroll
+        for (int j = 0; j < kPairsPerThread; ++j) {
+          const uint32_t w = acc[i][j];
+          const int64_t t = t_cta + my_pair + 32 * j;
+          if (t < a.nsamp_out) orow[t] = static_cast<int32_t>(v[8 * ii + 2 * j] + (w & 0xffffu));
+          if (t + kHalf < a.nsamp_out)
+            orow[t + kHalf] = static_cast<int32_t>(v[8 * ii + 2 * j + 1] + (w >> 16));
+        }
+      }
     }
   }
+  // every thread's tensor-memory accesses are complete (waited) before the
+  // allocating warp frees the columns
+  tmem_fence_before();
+  __syncthreads();
+  tmem_fence_after();
+  if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
 }
 
 }  // namespace

@@ -1,24 +1,29 @@
 // dd_quad.h -- shape constants and plan-time tables of the staged quad
 // kernel for u8 input (internal to libdd).
 //
-// CTA tile: kDmGroups x nd_thr DM trials by kTimeTile output samples.
-// 16 warps = kDmGroups DM groups x kTimeGroups time groups; a thread owns
-// nd_thr trials x kTimesPerThread samples (sample = base + lane + 32*j).
-// Channels are processed in chunks of kQuadsPerChunk quads (4 channels each).
+// CTA tile: kDmGroups x nd_thr DM trials by kTimeTile output samples, taken
+// as kHalf sample pairs (t, t + kHalf).  16 warps = kDmGroups DM groups x
+// kTimeGroups time groups; a thread owns nd_thr trials x kPairsPerThread
+// pairs (pair = base + lane + 32*j).  Channels are processed in chunks of
+// kQuadsPerChunk quads (4 channels each).
 //
 // Pattern rows.  For quad q of a DM tile, let b be the smallest channel-0
-// delay over the tile's trials.  Each distinct relative-delay pattern p of
-// the quad has a row of L words (L = kTimeTile + largest channel-0 delay - b,
-// rounded up to 4); word i of row p holds, for channels k = 0..3, the sample
-// at time t_cta + b + e_k(p) + i, e_k(p) being channel k's delay minus channel
-// 0's in that pattern.  The rows of a quad are contiguous.
+// delay over the tile's trials, less a per-quad slack x in 0..3 (chosen so
+// that every channel's byte shifts fit two loaded words, below).  Each
+// distinct relative-delay pattern p of the quad has a row of L words
+// (L = kHalf + largest channel-0 delay - b, rounded up to 4); word i of row p
+// holds two 16-bit sums over the quad's channels k = 0..3:
+//   low half   sum_k I[c_k][t_cta + b + e_k(p) + i]
+//   high half  sum_k I[c_k][t_cta + b + e_k(p) + i + kHalf]
+// e_k(p) being channel k's delay minus channel 0's in that pattern.  The rows
+// of a quad are contiguous.
 //
 // Per (DM tile, chunk) record, int32 words:
 //   [0] unused                   [1] unused
 //   [2] quads in this chunk      [3] number of build units
 //   A[kQuadsPerChunk][nd_cta]    word offset, within the chunk's pattern-row
 //                                area, of the row word that holds output
-//                                sample 0 of the tile for that quad and trial
+//                                pair 0 of the tile for that quad and trial
 //   units[kMaxUnits][8]: one warp-wide build step each -- items first ..
 //     first+31 (item = 4 row words) of every pattern row of one quad; lane l
 //     builds item first+l of each row:
@@ -29,14 +34,15 @@
 //         patterns << 26;
 //     [3] row length L in words;
 //     [4..7] per pattern p (two per word, 12 bits each): for channel k a
-//         3-bit byte shift 0..7 of the pattern's first sample within the
-//         three loaded words.
+//         3-bit byte shift 0..4 of the pattern's first sample within the two
+//         loaded words (the same shift serves the second half, kHalf bytes on).
 //   warp_start[kThreads/32 + 1] (int16 pairs, after the units): the units are
 //     ordered by the warp that builds them (balanced on the host, largest
 //     first onto the least loaded warp); warp w builds units
 //     warp_start[w] .. warp_start[w+1]-1.
 // raw_meta[tile][nchan_pad][2]: {window start relative to the tile's first
-// output sample (a multiple of 16), bytes needed (0 = padding channel)}.
+// output sample (a multiple of 16; -16 where the slack reaches before the
+// first sample), bytes needed (0 = padding channel)}.
 #pragma once
 
 #include <cstdint>
@@ -71,6 +77,11 @@ constexpr int kTimeGroups = DDQ_TIME_GROUPS;
 constexpr int kThreads = 32 * kDmGroups * kTimeGroups;                // 512
 constexpr int kTimesPerThread = DDQ_TIMES_PER_THREAD;
 constexpr int kTimeTile = kTimeGroups * 32 * kTimesPerThread;         // 512
+constexpr int kHalf = kTimeTile / 2;                                  // pair (t, t + kHalf)
+constexpr int kPairsPerThread = kTimesPerThread / 2;
+// A row word half holds at most 4*255; an accumulator half takes 64 quads
+// (64*1020 = 65280 < 65536) before it is drained into 32-bit sums.
+constexpr int kFlushQuads = 64;
 constexpr int kQuadsPerChunk = DDQ_QUADS_PER_CHUNK;
 constexpr int kNdThr = DDQ_ND_THR;  // DM trials per thread of the wide variant
 constexpr int kMaxPatterns = 8;
@@ -101,9 +112,10 @@ struct Tables {
 constexpr int kRawStages = 3;
 constexpr int kRecStages = 4;
 constexpr int kRowStages = 2;
-constexpr int kBarrierBytes = 64;  // the copy mbarriers (3 x 8 bytes) and padding
+constexpr int kBarrierBytes = 64;  // copy mbarriers (3 x 8 bytes), tensor-memory address, padding
+constexpr int kTmemSlot = 32;      // byte offset of the tensor-memory address
 
-// Shared-memory layout: the mbarriers (kBarrierBytes), the tile's raw
+// Shared-memory layout: the mbarriers and tensor-memory address (kBarrierBytes), the tile's raw
 // window table (nchan_pad x 2 int32), kRecStages records, kRawStages raw
 // window buffers (4*kQuadsPerChunk slots of raw_stride bytes), kRowStages
 // pattern-row areas.

@@ -1,20 +1,20 @@
 // dd_quad_plan.cpp -- plan-time tables of the staged quad kernel
 // (dd_dedisp_quad.cu) for u8 input.
 //
-// The kernel sums four channels per instruction (a byte dot product with
-// weights 1,1,1,1).  For that it needs, for each group of four adjacent
-// channels ("quad") and each DM trial of the CTA's tile, a shared-memory row
-// whose 32-bit word i holds the four channels' samples that the trial adds
-// at one output time.  Within a quad the delays of channels 1..3 relative to
-// channel 0 take only a few distinct values over a tile of trials (they are
-// differences of two rounded delays, Sec. 2.1.1), so one interleaved row per
-// distinct relative pattern serves every trial of the tile that has it.
+// The kernel adds eight channel samples per 32-bit shared-memory word: for
+// each group of four adjacent channels ("quad") and each DM trial of the
+// CTA's tile it reads a row whose word i holds the sum of the four channels'
+// samples that the trial adds at output time i (low 16 bits) and at time
+// i + kHalf (high 16 bits).  Within a quad the delays of channels 1..3
+// relative to channel 0 take only a few distinct values over a tile of
+// trials (they are differences of two rounded delays, Sec. 2.1.1), so one
+// row per distinct relative pattern serves every trial of the tile that has
+// it.
 //
 // Everything here is integer bookkeeping on the plan's delay table; no part
 // of the dedispersion sum happens on the host.
 #include <algorithm>
 #include <array>
-#include <cstdint>
 #include <cstdint>
 #include <vector>
 
@@ -60,6 +60,17 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     bool pad[4];
     int32_t raw_off[4];            // byte offset of time b + emin[k] in channel k's window
   };
+  // slack x (row origin b - x) for which every real channel's byte shifts
+  // (b - x + emin) & 3 .. + spread stay within 0..4, i.e. inside two words
+  auto slack_for = [&](int32_t b, const int32_t *emin, const int32_t *emax, const bool *pad) {
+    for (int x = 0; x < 4; ++x) {
+      bool fits = true;
+      for (int k = 0; k < 4; ++k)
+        if (!pad[k] && ((b - x + emin[k]) & 3) + emax[k] - emin[k] > 4) fits = false;
+      if (fits) return x;
+    }
+    return -1;
+  };
   std::vector<std::vector<Quad>> chunk_quads(static_cast<size_t>(t.ntiles) * t.nchunks);
   for (int tile = 0; tile < t.ntiles; ++tile) {
     std::vector<int32_t> start(t.nchan_pad, 0), need(t.nchan_pad, 0);
@@ -89,27 +100,32 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
         if (static_cast<int>(pats.size()) > kMaxPatterns) return 1;
         Quad Q;
         Q.row_off = row_words;
-        Q.L = round_up(kTimeTile + bmax - b, 4);
         Q.npat = static_cast<int32_t>(pats.size());
+        int32_t emax[4];
         for (int k = 0; k < 4; ++k) {
-          const int c = c0 + k;
-          Q.pad[k] = c >= nchan;
-          int32_t emin = INT32_MAX, emax = INT32_MIN;
+          Q.pad[k] = c0 + k >= nchan;
+          Q.emin[k] = INT32_MAX;
+          emax[k] = INT32_MIN;
           for (int p = 0; p < Q.npat; ++p) {
             const int32_t e = k == 0 ? 0 : pats[p][k - 1];
-            emin = std::min(emin, e);
-            emax = std::max(emax, e);
+            Q.emin[k] = std::min(Q.emin[k], e);
+            emax[k] = std::max(emax[k], e);
           }
-          Q.emin[k] = emin;
-          for (int p = 0; p < Q.npat; ++p) Q.shift[p][k] = (k == 0 ? 0 : pats[p][k - 1]) - emin;
-          // the three loaded words hold bytes (first & 3) + shift .. + 3 when
-          // the shift code (first & 3) + e - emin stays within 0..7
-          if (emax - emin > 4) return 1;
+          for (int p = 0; p < Q.npat; ++p)
+            Q.shift[p][k] = (k == 0 ? 0 : pats[p][k - 1]) - Q.emin[k];
+        }
+        const int x = slack_for(b, Q.emin, emax, Q.pad);
+        if (x < 0) return 1;
+        b -= x;  // may reach -3 for the first tile; those row words are never read
+        Q.L = round_up(kHalf + bmax - b, 4);
+        for (int k = 0; k < 4; ++k) {
+          const int c = c0 + k;
           if (!Q.pad[k]) {
-            // channel window: times b + emin .. b + emax + L (+ the over-read)
-            start[c] = (b + emin) & ~15;
-            need[c] = b + emax + Q.L + 12 - start[c];
-            Q.raw_off[k] = b + emin - start[c];
+            // two words per item and half: the last item's words end at
+            // (raw_off & ~3) + L + kHalf + 4 bytes into the window
+            start[c] = (b + Q.emin[k]) & ~15;
+            Q.raw_off[k] = b + Q.emin[k] - start[c];
+            need[c] = (Q.raw_off[k] & ~3) + Q.L + kHalf + 4;
             raw_stride = std::max(raw_stride, round_up(need[c], 16));
           } else {
             Q.raw_off[k] = 0;

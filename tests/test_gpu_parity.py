@@ -312,6 +312,16 @@ STAGED_CASES = [
     ("full_block_u8", 1021, 100, 700, 16),
     ("full_block_u8", 1024, 2048, 3000, 0),
     ("lband_f32", 4096, 96, 1500, 32),
+    ("full_block_u8", 1036, 64, 900, 0),   # last chunk holds 3 quads
+    ("full_block_u8", 68, 64, 300, 0),     # last chunk holds 1 quad
+]
+
+# Geometries whose first DM tile builds rows from before sample 0 (window of
+# the band-top channel starting at -16): (f_top MHz, channel width MHz,
+# t_samp s, first DM, DM step, nchan, ndm)
+SLACK_GEOMETRIES = [
+    (559.74, 0.7752, 51.2e-6, 0.8816, 0.02105, 64, 100),
+    (728.89, 5.5687, 64e-6, 0.917, 0.00745, 16, 40),
 ]
 
 
@@ -341,6 +351,23 @@ def test_staged_kernel_matches_oracle_and_plain_kernel(name, nchan, ndm, extra, 
     rows = sorted(set([0, ndm - 1] + np.random.default_rng(1).integers(0, ndm, 12).tolist()))
     ref = oracle.dedisperse(block, delays[:, rows], nsamp_out=s.shape[1], nsamp_in=nsamp)
     assert np.array_equal(s[rows], ref)
+
+
+@pytest.mark.parametrize("geo", SLACK_GEOMETRIES)
+def test_staged_kernel_row_origin_before_first_sample(geo):
+    f_top, df, ts, dm0, step, nchan, ndm = geo
+    dms = dm0 + step * np.arange(ndm)
+    delays, mx = oracle.delay_table(nchan, f_top, df, ts, dms)
+    nsamp = mx + 1300
+    pitch = (nsamp + 15) // 16 * 16
+    block = synth.random_block(np.random.default_rng(4), nchan, nsamp, "u8", pitch)
+    dblock = _to_dev(block)
+    with dd.Plan(nchan, f_top, df, ts, dms, "u8") as plan:
+        assert dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)["staged"]
+        out = plan.execute(dblock, nsamp_in=nsamp)
+        dd.dd_sync(plan.handle)
+        got = out.cpu().numpy()
+    assert np.array_equal(got, oracle.dedisperse(block, delays, nsamp_in=nsamp))
 
 
 def test_staged_kernel_bounded_wait_reports_timeout_and_recovers():

@@ -1,10 +1,11 @@
 """CPU checks of the staged u8 kernel's plan-time tables.
 
 The tables (dd_quad_plan.cpp) tell the kernel which bytes to bulk-copy,
-how to interleave four channels into pattern rows and where each DM trial
-reads.  A numpy model of the kernel's three phases (copy, build, accumulate)
-runs on them here, asserting every shared-memory and global index against the
-buffer it addresses, and its result must equal the oracle bit for bit.
+how to sum four channels into pattern rows of sample pairs (t, t + 256) and
+where each DM trial reads.  A numpy model of the kernel's three phases (copy,
+build, accumulate) runs on them here, asserting every shared-memory and global
+index against the buffer it addresses and the 16-bit range of every packed
+half between drains, and its result must equal the oracle bit for bit.
 Uncopied / unbuilt bytes hold garbage so that a read of them shows up.
 """
 import ctypes
@@ -17,9 +18,12 @@ import paper_1401_8258_gb300 as dd
 import synth
 
 T_TILE = 512
+HALF = T_TILE // 2
 QUADS_PER_CHUNK = 4
+FLUSH_CHUNKS = 64 // QUADS_PER_CHUNK
 REC_HEADER = 4
 UNIT_WORDS = 8
+NWARPS = 16
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -61,6 +65,7 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
         for tt in range(ntt):
             t_cta = tt * T_TILE
             acc = np.zeros((nd, T_TILE), dtype=np.int64)
+            packed = np.zeros((nd, T_TILE), dtype=np.int64)  # the 16-bit halves
             for ch in range(tb["nchunks"]):
                 rec = tb["recs"][tile, ch]
                 raw = np.full((4 * QUADS_PER_CHUNK, rs), garbage, dtype=np.uint8)
@@ -73,19 +78,21 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                         assert c >= nchan
                         continue
                     off = t_cta + start
-                    n = (need + 15) // 16 * 16
-                    if off + n > pitch:
-                        n = pitch - off
-                    assert off % 16 == 0 and n % 16 == 0 and 0 < n <= rs and off >= 0
-                    raw[s, :n] = block[c, off:off + n]
+                    hi = min(off + (need + 15) // 16 * 16, pitch)
+                    lo = max(off, 0)
+                    assert off % 16 == 0 and off >= -16 and hi > lo
+                    assert (hi - lo) % 16 == 0 and hi - off <= rs
+                    raw[s, lo - off:hi - off] = block[c, lo:hi]
                 nq, nunits = rec[2], rec[3]
                 units_off = REC_HEADER + QUADS_PER_CHUNK * nd
                 units = rec[units_off:units_off + UNIT_WORDS * nunits].reshape(-1, UNIT_WORDS)
-                # per-warp unit ranges (16 warps), int16 pairs after the unit array
-                starts = rec[units_off + UNIT_WORDS * 32:].view(np.uint16)[:17]
-                assert starts[0] == 0 and starts[16] == nunits and np.all(np.diff(starts.astype(int)) >= 0)
+                # per-warp unit ranges, int16 pairs after the unit array
+                starts = rec[units_off + UNIT_WORDS * 32:].view(np.uint16)[:NWARPS + 1]
+                assert starts[0] == 0 and starts[NWARPS] == nunits
+                assert np.all(np.diff(starts.astype(int)) >= 0)
                 raw_flat = raw.reshape(-1)
-                prow = np.full((pw, 4), garbage, dtype=np.uint8)
+                # row words as (low half, high half); unbuilt words hold garbage
+                prow = np.full((pw, 2), 77777, dtype=np.int64)
                 written = np.zeros(pw, dtype=np.int64)
                 for u in units.astype(np.int64) & 0xFFFFFFFF:  # one warp-wide step
                     items = (u[2] >> 20) & 63
@@ -100,25 +107,31 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                         words = (dest0 + p * L + 4 * lanes[:, None] + np.arange(4)[None, :]).reshape(-1)
                         assert words.max() < pw
                         written[words] += 1
+                        prow[words] = 0
                         for k in range(4):
                             if offs[k] == 0xFFFF:
-                                prow[words, k] = 0
                                 continue
                             sh = (code >> (3 * k)) & 7
-                            assert 0 <= sh <= 7
+                            assert 0 <= sh <= 4  # inside the two loaded words
                             base = offs[k] + 4 * lanes
                             slot = offs[k] // rs
-                            # three aligned words, all inside this channel's slot
-                            assert base.min() % 4 == 0 and (base.max() + 11) // rs == slot
-                            byte = (base[:, None] + sh + np.arange(4)[None, :]).reshape(-1)
-                            prow[words, k] = raw_flat[byte]
+                            # two aligned words per half, all inside this channel's slot
+                            assert base.min() % 4 == 0 and (base.max() + HALF + 7) // rs == slot
+                            for h in range(2):
+                                byte = (base[:, None] + h * HALF + sh + np.arange(4)[None, :]).reshape(-1)
+                                prow[words, h] += raw_flat[byte]
                 assert written.max() <= 1  # no row word is built twice
                 A = rec[REC_HEADER:REC_HEADER + QUADS_PER_CHUNK * nd].reshape(QUADS_PER_CHUNK, nd)
                 for q in range(nq):
                     for i in range(nd):
-                        w = A[q, i] + np.arange(T_TILE)
+                        w = A[q, i] + np.arange(HALF)
                         assert w[0] >= 0 and w[-1] < pw
-                        acc[i] += prow[w].astype(np.int64).sum(axis=1)
+                        packed[i, :HALF] += prow[w, 0]
+                        packed[i, HALF:] += prow[w, 1]
+                assert packed.max() < 65536  # 16-bit halves never carry
+                if (ch + 1) % FLUSH_CHUNKS == 0 or ch + 1 == tb["nchunks"]:
+                    acc += packed
+                    packed[:] = 0
             d0 = tile * nd
             dn = min(nd, ndm - d0)
             tn = min(T_TILE, nsamp_out - t_cta)
@@ -131,6 +144,15 @@ CASES = [
     ("full_block_u8", 1024, 128, 1100, 0),
     ("full_block_u8", 1021, 100, 700, 16),
     ("lband_f32", 512, 70, 600, 48),
+    ("full_block_u8", 1036, 64, 900, 0),  # last chunk holds 3 quads
+]
+
+# Geometries whose first DM tile needs a row origin before sample 0 (the
+# window of the band-top channel then starts at -16): (f_top MHz, channel
+# width MHz, t_samp s, first DM, DM step, nchan, ndm)
+SLACK_GEOMETRIES = [
+    (559.74, 0.7752, 51.2e-6, 0.8816, 0.02105, 64, 100),
+    (728.89, 5.5687, 64e-6, 0.917, 0.00745, 16, 40),
 ]
 
 
@@ -151,6 +173,20 @@ def test_quad_kernel_model_matches_oracle(name, nchan, ndm, extra, pad):
     got = emulate(block, nsamp, tb, wl.ndm, nout)
     ref = oracle.dedisperse(block, delays, nsamp_in=nsamp)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("geo", SLACK_GEOMETRIES)
+def test_quad_kernel_model_with_row_origin_before_first_sample(geo):
+    f_top, df, ts, dm0, step, nchan, ndm = geo
+    dms = dm0 + step * np.arange(ndm)
+    delays, mx = oracle.delay_table(nchan, f_top, df, ts, dms)
+    tb = quad_tables(delays, nchan, ndm, 8) or quad_tables(delays, nchan, ndm, 4)
+    assert tb is not None and (tb["meta"][:, :, 0] < 0).any()
+    nsamp = mx + 1300
+    pitch = (nsamp + 15) // 16 * 16
+    block = synth.random_block(np.random.default_rng(4), nchan, nsamp, "u8", pitch)
+    got = emulate(block, nsamp, tb, ndm, nsamp - mx)
+    assert np.array_equal(got, oracle.dedisperse(block, delays, nsamp_in=nsamp))
 
 
 def test_tables_fit_shared_memory_for_the_workloads():
