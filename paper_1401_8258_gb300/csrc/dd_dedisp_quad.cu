@@ -114,6 +114,25 @@ __device__ __forceinline__ uint32_t lds32_off(uint32_t addr) {
   return v;
 }
 
+// N consecutive row offsets of one quad from the (16-byte aligned) record.
+template <int N>
+__device__ __forceinline__ void load_offsets(const int32_t *p, int (&o)[N]) {
+  if constexpr (N % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < N; i += 4) {
+      const int4 v = reinterpret_cast<const int4 *>(p)[i / 4];
+      o[i] = v.x, o[i + 1] = v.y, o[i + 2] = v.z, o[i + 3] = v.w;
+    }
+  } else {
+    static_assert(N % 2 == 0, "offsets are loaded in pairs at least");
+#pragma unroll
+    for (int i = 0; i < N; i += 2) {
+      const int2 v = reinterpret_cast<const int2 *>(p)[i / 2];
+      o[i] = v.x, o[i + 1] = v.y;
+    }
+  }
+}
+
 // acc[j] += word at a + 128 j (+ word at b + 128 j) for j = J..kPairsPerThread-1
 template <int J>
 struct AccPairs {
@@ -248,18 +267,19 @@ __device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, 
 // loads the two aligned words that hold the earliest needed sample and the
 // next 4 bytes, for the first and the second half of the pair (kHalf bytes
 // on) -- enough for every pattern, whose byte shifts stay within 0..4.  For
-// each pattern it funnels out the 4 samples at that pattern's shift and sums
-// the four channels in 16-bit lanes: the odd bytes (prmt) and the whole words
-// are summed, and the even-byte sum is their difference (exact modulo 2^32).
+// each pattern it funnels out the 4 samples at that pattern's shift (prmt
+// with the unit's selector) and sums the four channels in 16-bit lanes: the
+// odd bytes (prmt) and the whole words are summed, and the even-byte sum is
+// their difference (exact modulo 2^32).  Channel 0 has the same shift in
+// every pattern, so its part is formed once per unit.
 __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint32_t prow,
                                            int lane) {
-  const int4 d0 = reinterpret_cast<const int4 *>(ud)[0];
-  const int4 d1 = reinterpret_cast<const int4 *>(ud)[1];
-  const uint32_t items = (static_cast<uint32_t>(d0.z) >> 20) & 63u;
+  const int4 h = reinterpret_cast<const int4 *>(ud)[0];
+  const uint32_t items = (static_cast<uint32_t>(h.z) >> 20) & 63u;
   if (static_cast<uint32_t>(lane) >= items) return;
-  const uint32_t npat = static_cast<uint32_t>(d0.z) >> 26;
-  const uint32_t off[4] = {static_cast<uint32_t>(d0.x) & 0xffffu, static_cast<uint32_t>(d0.x) >> 16,
-                           static_cast<uint32_t>(d0.y) & 0xffffu, static_cast<uint32_t>(d0.y) >> 16};
+  const uint32_t npat = static_cast<uint32_t>(h.z) >> 26;
+  const uint32_t off[4] = {static_cast<uint32_t>(h.x) & 0xffffu, static_cast<uint32_t>(h.x) >> 16,
+                           static_cast<uint32_t>(h.y) & 0xffffu, static_cast<uint32_t>(h.y) >> 16};
   uint32_t a0[4], a1[4], b0[4], b1[4];
 #pragma unroll
   for (int ch = 0; ch < 4; ++ch) {
@@ -270,19 +290,22 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint
     b0[ch] = pad ? 0u : lds32_off<kHalf>(w);
     b1[ch] = pad ? 0u : lds32_off<kHalf + 4>(w);
   }
-  const uint32_t codes[4] = {static_cast<uint32_t>(d1.x), static_cast<uint32_t>(d1.y),
-                             static_cast<uint32_t>(d1.z), static_cast<uint32_t>(d1.w)};
-  uint32_t dst = prow + 4u * (static_cast<uint32_t>(d0.z) & 0xfffffu) + 16u * lane;
-  const uint32_t row_bytes = 4u * static_cast<uint32_t>(d0.w);
+  const uint32_t sel0 = static_cast<uint32_t>(h.w) >> 16;
+  const uint32_t va0 = prmt(a0[0], a1[0], sel0), vb0 = prmt(b0[0], b1[0], sel0);
+  const uint32_t oa0 = prmt(va0, 0u, 0x4341u), ob0 = prmt(vb0, 0u, 0x4341u);
+  uint32_t dst = prow + 4u * (static_cast<uint32_t>(h.z) & 0xfffffu) + 16u * lane;
+  const uint32_t row_bytes = 4u * (static_cast<uint32_t>(h.w) & 0xffffu);
+  const int2 *sels = reinterpret_cast<const int2 *>(ud + 4);
 #pragma unroll
   for (int p = 0; p < kMaxPatterns; ++p) {
     if (static_cast<uint32_t>(p) >= npat) break;
-    const uint32_t code = (codes[p >> 1] >> (12 * (p & 1))) & 0xfffu;
-    uint32_t sa = 0, sb = 0, oa = 0, ob = 0;  // word sums and odd-byte sums
+    const int2 sp = sels[p];
+    const uint32_t sel[4] = {0u, static_cast<uint32_t>(sp.x), static_cast<uint32_t>(sp.x) >> 16,
+                             static_cast<uint32_t>(sp.y)};  // prmt reads bits 0..15
+    uint32_t sa = va0, sb = vb0, oa = oa0, ob = ob0;  // word sums and odd-byte sums
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
-      const uint32_t sel = 0x3210u + 0x1111u * ((code >> (3 * ch)) & 7u);  // shift 0..4
-      const uint32_t va = prmt(a0[ch], a1[ch], sel), vb = prmt(b0[ch], b1[ch], sel);
+    for (int ch = 1; ch < 4; ++ch) {
+      const uint32_t va = prmt(a0[ch], a1[ch], sel[ch]), vb = prmt(b0[ch], b1[ch], sel[ch]);
       sa += va;
       sb += vb;
       oa += prmt(va, 0u, 0x4341u);  // bytes 1, 3 -> 16-bit lanes
@@ -324,30 +347,30 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_
   return ok != 0;
 }
 
-// Drain the packed accumulators into the 32-bit sums in tensor memory
-// (column 8 i + 2 j + h of this thread's lane holds trial i, pair j, half h).
-// FINAL: add the stored sums (if `load`) and write the output instead.
+// Drain the packed accumulators into the 32-bit sums in tensor memory:
+// entry m = i * kPairsPerThread + j (trial i, pair j) sits in columns 2m
+// (first half) and 2m + 1 (second half) of this thread's lane, moved 8
+// entries (16 columns) at a time.  `load`: add to the sums stored so far.
 template <int ND_THR>
 __device__ __forceinline__ void drain(uint32_t (&acc)[ND_THR][kPairsPerThread], uint32_t taddr,
                                       bool load) {
 #pragma unroll
-  for (int blk = 0; blk < ND_THR / 2; ++blk) {
+  for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
     uint32_t v[16];
     if (load) {
       tmem_ld16(taddr + 16u * blk, v);
     } else {
 #pragma unroll
-      for (int m = 0; m < 16; ++m) v[m] = 0;
+      for (int e = 0; e < 16; ++e) v[e] = 0;
     }
 #pragma unroll
-    for (int ii = 0; ii < 2; ++ii)
-#pragma unroll
-      for (int j = 0; j < kPairsPerThread; ++j) {
-        const uint32_t w = acc[2 * blk + ii][j];
-        v[8 * ii + 2 * j] += w & 0xffffu;
-        v[8 * ii + 2 * j + 1] += w >> 16;
-        acc[2 * blk + ii][j] = 0;
-      }
+    for (int e = 0; e < 8; ++e) {
+      const int m = 8 * blk + e;
+      uint32_t &w = acc[m / kPairsPerThread][m % kPairsPerThread];
+      v[2 * e] += w & 0xffffu;
+      v[2 * e + 1] += w >> 16;
+      w = 0;
+    }
     tmem_st16(taddr + 16u * blk, v);
   }
 }
@@ -361,7 +384,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   // keeps 2 * ND_THR * kPairsPerThread sums
   constexpr uint32_t kColsPerThread = 2 * ND_THR * kPairsPerThread;
   constexpr uint32_t kTmemCols = 4 * kColsPerThread;
-  static_assert(kColsPerThread % 16 == 0 && kTmemCols >= 32 && kTmemCols <= 512 &&
+  static_assert(ND_THR * kPairsPerThread % 8 == 0 && kTmemCols >= 32 && kTmemCols <= 512 &&
                     (kTmemCols & (kTmemCols - 1)) == 0,
                 "tensor-memory allocation must be a power of two in 32..512 columns");
   static_assert(kThreads / 32 == 16, "four warps per tensor-memory lane quarter");
@@ -465,48 +488,31 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     const int32_t *rec_n = rec_ptr(k + 1);
     int nseg_w = -1;  // build units of chunk k+1 for this warp, once its copies landed
     int m_done = 0;
-    int4 a_next[2][ND_THR / 4];
+    int a_next[2][ND_THR];
+    load_offsets<ND_THR>(A, a_next[0]);
+    load_offsets<ND_THR>(A + ND_CTA, a_next[1]);
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int i4 = 0; i4 < ND_THR / 4; ++i4)
-        a_next[h][i4] = reinterpret_cast<const int4 *>(A + h * ND_CTA)[i4];
-#pragma unroll 1
     for (int st = 0; st < kSteps; ++st) {
       const int q = 2 * st;
       if (q < nq) {
-        int4 a_cur[2][ND_THR / 4];
+        int a_cur[2][ND_THR];
 #pragma unroll
         for (int h = 0; h < 2; ++h)
 #pragma unroll
-          for (int i4 = 0; i4 < ND_THR / 4; ++i4) a_cur[h][i4] = a_next[h][i4];
+          for (int i = 0; i < ND_THR; ++i) a_cur[h][i] = a_next[h][i];
         if (q + 2 < nq) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int i4 = 0; i4 < ND_THR / 4; ++i4)
-              a_next[h][i4] = reinterpret_cast<const int4 *>(A + (q + 2 + h) * ND_CTA)[i4];
+          load_offsets<ND_THR>(A + (q + 2) * ND_CTA, a_next[0]);
+          load_offsets<ND_THR>(A + (q + 3) * ND_CTA, a_next[1]);
         }
         if (q + 1 < nq) {
 #pragma unroll
-          for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
-            const int o0[4] = {a_cur[0][i4].x, a_cur[0][i4].y, a_cur[0][i4].z, a_cur[0][i4].w};
-            const int o1[4] = {a_cur[1][i4].x, a_cur[1][i4].y, a_cur[1][i4].z, a_cur[1][i4].w};
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
-              AccPairs<0>::two(acc[4 * i4 + ii],
-                               prow + 4u * (static_cast<uint32_t>(o0[ii]) + my_pair),
-                               prow + 4u * (static_cast<uint32_t>(o1[ii]) + my_pair));
-          }
+          for (int i = 0; i < ND_THR; ++i)
+            AccPairs<0>::two(acc[i], prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair),
+                             prow + 4u * (static_cast<uint32_t>(a_cur[1][i]) + my_pair));
         } else {
 #pragma unroll
-          for (int i4 = 0; i4 < ND_THR / 4; ++i4) {
-            const int o0[4] = {a_cur[0][i4].x, a_cur[0][i4].y, a_cur[0][i4].z, a_cur[0][i4].w};
-#pragma unroll
-            for (int ii = 0; ii < 4; ++ii)
-              AccPairs<0>::one(acc[4 * i4 + ii],
-                               prow + 4u * (static_cast<uint32_t>(o0[ii]) + my_pair));
-          }
+          for (int i = 0; i < ND_THR; ++i)
+            AccPairs<0>::one(acc[i], prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair));
         }
       }
       if (next && ok) {
@@ -544,28 +550,26 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     // final sums: stored part (if any) + the packed halves; pair j of trial
     // i covers samples my_pair + 32 j and my_pair + 32 j + kHalf
 #pragma unroll
-    for (int blk = 0; blk < ND_THR / 2; ++blk) {
+    for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
       uint32_t v[16];
       if (drained) {
         tmem_ld16(taddr + 16u * blk, v);
       } else {
 #pragma unroll
-        for (int m = 0; m < 16; ++m) v[m] = 0;
+        for (int e = 0; e < 16; ++e) v[e] = 0;
       }
 #pragma unroll
-      for (int ii = 0; ii < 2; ++ii) {
-        const int i = 2 * blk + ii;
+      for (int e = 0; e < 8; ++e) {
+        const int m = 8 * blk + e;
+        const int i = m / kPairsPerThread, j = m % kPairsPerThread;
         const int d = tile * ND_CTA + dg * ND_THR + i;
         if (d >= a.ndm) continue;
         int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
-#pragma unroll
-        for (int j = 0; j < kPairsPerThread; ++j) {
-          const uint32_t w = acc[i][j];
-          const int64_t t = t_cta + my_pair + 32 * j;
-          if (t < a.nsamp_out) orow[t] = static_cast<int32_t>(v[8 * ii + 2 * j] + (w & 0xffffu));
-          if (t + kHalf < a.nsamp_out)
-            orow[t + kHalf] = static_cast<int32_t>(v[8 * ii + 2 * j + 1] + (w >> 16));
-        }
+        const uint32_t w = acc[i][j];
+        const int64_t t = t_cta + my_pair + 32 * j;
+        if (t < a.nsamp_out) orow[t] = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
+        if (t + kHalf < a.nsamp_out)
+          orow[t + kHalf] = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
       }
     }
   }

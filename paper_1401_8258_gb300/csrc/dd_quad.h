@@ -3,8 +3,8 @@
 //
 // CTA tile: kDmGroups x nd_thr DM trials by kTimeTile output samples, taken
 // as kHalf sample pairs (t, t + kHalf).  16 warps = kDmGroups DM groups x
-// kTimeGroups time groups; a thread owns nd_thr trials x kPairsPerThread
-// pairs (pair = base + lane + 32*j).  Channels are processed in chunks of
+// kTimeGroups time groups (16 x 1); a thread owns nd_thr trials (4) x
+// kPairsPerThread pairs (8; pair = base + lane + 32*j).  Channels are processed in chunks of
 // kQuadsPerChunk quads (4 channels each).
 //
 // Pattern rows.  For quad q of a DM tile, let b be the smallest channel-0
@@ -24,7 +24,7 @@
 //   A[kQuadsPerChunk][nd_cta]    word offset, within the chunk's pattern-row
 //                                area, of the row word that holds output
 //                                pair 0 of the tile for that quad and trial
-//   units[kMaxUnits][8]: one warp-wide build step each -- items first ..
+//   units[kMaxUnits][20]: one warp-wide build step each -- items first ..
 //     first+31 (item = 4 row words) of every pattern row of one quad; lane l
 //     builds item first+l of each row:
 //     [0] raw-buffer byte offsets of channels 0 | 1 << 16, [1] of 2 | 3 << 16:
@@ -32,10 +32,12 @@
 //         quad needs for this item block (0xffff = padding channel, zeros);
 //     [2] row-area word offset of item `first` of row 0 | items << 20 |
 //         patterns << 26;
-//     [3] row length L in words;
-//     [4..7] per pattern p (two per word, 12 bits each): for channel k a
-//         3-bit byte shift 0..4 of the pattern's first sample within the two
-//         loaded words (the same shift serves the second half, kHalf bytes on).
+//     [3] row length L in words | channel 0's byte selector << 16;
+//     [4 + 2p], [5 + 2p] for pattern p: byte selectors (prmt) of channels
+//         1 | 2 << 16, and 3: for a byte shift s (0..4) of the pattern's
+//         first sample within the two loaded words, 0x3210 + 0x1111 s (the
+//         same shift serves the second half, kHalf bytes on).  Channel 0's
+//         shift is the same for every pattern (its relative delay is 0).
 //   warp_start[kThreads/32 + 1] (int16 pairs, after the units): the units are
 //     ordered by the warp that builds them (balanced on the host, largest
 //     first onto the least loaded warp); warp w builds units
@@ -58,19 +60,19 @@ namespace ddq {
 
 // Tile shape; the DDQ_* macros exist only to build shape variants for tuning.
 #ifndef DDQ_DM_GROUPS
-#define DDQ_DM_GROUPS 8
+#define DDQ_DM_GROUPS 16
 #endif
 #ifndef DDQ_TIME_GROUPS
-#define DDQ_TIME_GROUPS 2
+#define DDQ_TIME_GROUPS 1
 #endif
 #ifndef DDQ_TIMES_PER_THREAD
-#define DDQ_TIMES_PER_THREAD 8
+#define DDQ_TIMES_PER_THREAD 16
 #endif
 #ifndef DDQ_QUADS_PER_CHUNK
 #define DDQ_QUADS_PER_CHUNK 4
 #endif
 #ifndef DDQ_ND_THR
-#define DDQ_ND_THR 8
+#define DDQ_ND_THR 4
 #endif
 constexpr int kDmGroups = DDQ_DM_GROUPS;
 constexpr int kTimeGroups = DDQ_TIME_GROUPS;
@@ -86,7 +88,7 @@ constexpr int kQuadsPerChunk = DDQ_QUADS_PER_CHUNK;
 constexpr int kNdThr = DDQ_ND_THR;  // DM trials per thread of the wide variant
 constexpr int kMaxPatterns = 8;
 constexpr int kRecHeader = 4;
-constexpr int kUnitWords = 8;
+constexpr int kUnitWords = 4 + 2 * kMaxPatterns;  // 20 (80 bytes)
 constexpr int kMaxUnits = 32;
 constexpr int kMaxSmem = 227 * 1024;
 

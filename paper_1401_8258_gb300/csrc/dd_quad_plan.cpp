@@ -164,12 +164,14 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
         u[0] = static_cast<int32_t>(addr[0] | (addr[1] << 16));
         u[1] = static_cast<int32_t>(addr[2] | (addr[3] << 16));
         u[2] = (Q.row_off + 4 * first) | (std::min(32, items - first) << 20) | (Q.npat << 26);
-        u[3] = Q.L;
+        // prmt selector of the 4 bytes starting s bytes into two words
+        auto sel = [&](int p, int k) {
+          return 0x3210u + 0x1111u * static_cast<uint32_t>((Q.raw_off[k] & 3) + Q.shift[p][k]);
+        };
+        u[3] = static_cast<int32_t>(static_cast<uint32_t>(Q.L) | (sel(0, 0) << 16));
         for (int p = 0; p < Q.npat; ++p) {
-          uint32_t code = 0;
-          for (int k = 0; k < 4; ++k)
-            code |= static_cast<uint32_t>((Q.raw_off[k] & 3) + Q.shift[p][k]) << (3 * k);
-          u[4 + p / 2] |= static_cast<int32_t>(code << (12 * (p & 1)));
+          u[4 + 2 * p] = static_cast<int32_t>(sel(p, 1) | (sel(p, 2) << 16));
+          u[5 + 2 * p] = static_cast<int32_t>(sel(p, 3));
         }
         list.push_back(u);
       }

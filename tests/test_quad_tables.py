@@ -22,8 +22,9 @@ HALF = T_TILE // 2
 QUADS_PER_CHUNK = 4
 FLUSH_CHUNKS = 64 // QUADS_PER_CHUNK
 REC_HEADER = 4
-UNIT_WORDS = 8
+UNIT_WORDS = 20
 NWARPS = 16
+ND_THR = 4  # DM trials per thread of the 64-trial tile (16 warps x 4); 2 for the 32-trial one
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -98,12 +99,13 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                     items = (u[2] >> 20) & 63
                     npat = u[2] >> 26
                     dest0 = u[2] & 0xFFFFF
-                    L = u[3]
+                    L = u[3] & 0xFFFF
                     assert 1 <= items <= 32 and 1 <= npat <= 8 and dest0 % 4 == 0 and L % 4 == 0
                     offs = [u[0] & 0xFFFF, u[0] >> 16, u[1] & 0xFFFF, u[1] >> 16]
                     lanes = np.arange(items)
                     for p in range(npat):
-                        code = (u[4 + p // 2] >> (12 * (p & 1))) & 0xFFF
+                        sels = [u[3] >> 16, u[4 + 2 * p] & 0xFFFF, u[4 + 2 * p] >> 16,
+                                u[5 + 2 * p] & 0xFFFF]
                         words = (dest0 + p * L + 4 * lanes[:, None] + np.arange(4)[None, :]).reshape(-1)
                         assert words.max() < pw
                         written[words] += 1
@@ -111,8 +113,9 @@ def emulate(block, nsamp_in, tb, ndm, nsamp_out):
                         for k in range(4):
                             if offs[k] == 0xFFFF:
                                 continue
-                            sh = (code >> (3 * k)) & 7
-                            assert 0 <= sh <= 4  # inside the two loaded words
+                            sh = sels[k] & 0xF
+                            # a 4-byte funnel inside the two loaded words
+                            assert sels[k] == 0x3210 + 0x1111 * sh and sh <= 4
                             base = offs[k] + 4 * lanes
                             slot = offs[k] // rs
                             # two aligned words per half, all inside this channel's slot
@@ -162,7 +165,7 @@ def test_quad_kernel_model_matches_oracle(name, nchan, ndm, extra, pad):
     # keep the channel width of the full band so that pattern counts are realistic
     wl.chan_width_mhz = synth.workload(name).chan_width_mhz
     delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
-    tb = quad_tables(delays, wl.nchan, wl.ndm, 8) or quad_tables(delays, wl.nchan, wl.ndm, 4)
+    tb = quad_tables(delays, wl.nchan, wl.ndm, ND_THR) or quad_tables(delays, wl.nchan, wl.ndm, ND_THR // 2)
     assert tb is not None
     nsamp = mx + extra
     pitch = (nsamp + 15) // 16 * 16 + pad
@@ -180,7 +183,7 @@ def test_quad_kernel_model_with_row_origin_before_first_sample(geo):
     f_top, df, ts, dm0, step, nchan, ndm = geo
     dms = dm0 + step * np.arange(ndm)
     delays, mx = oracle.delay_table(nchan, f_top, df, ts, dms)
-    tb = quad_tables(delays, nchan, ndm, 8) or quad_tables(delays, nchan, ndm, 4)
+    tb = quad_tables(delays, nchan, ndm, ND_THR) or quad_tables(delays, nchan, ndm, ND_THR // 2)
     assert tb is not None and (tb["meta"][:, :, 0] < 0).any()
     nsamp = mx + 1300
     pitch = (nsamp + 15) // 16 * 16
@@ -193,7 +196,7 @@ def test_tables_fit_shared_memory_for_the_workloads():
     for name in ("full_block_u8", "lband_f32"):
         wl = synth.workload(name)
         delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
-        tb = quad_tables(delays, wl.nchan, wl.ndm, 8)
+        tb = quad_tables(delays, wl.nchan, wl.ndm, ND_THR)
         assert tb is not None and tb["nd_cta"] == 64, name
         meta = (tb["nchan_pad"] * 8 + 15) // 16 * 16
         smem = 64 + meta + 4 * tb["rec_words"] * 4 + 3 * 16 * tb["raw_stride"] + 2 * tb["prow_words"] * 4
@@ -205,5 +208,5 @@ def test_tables_refuse_geometries_with_too_many_patterns():
     # every trial, so the plan must fall back to the plain-load kernel
     wl = synth.workload("single_beam_f32")
     delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
-    assert quad_tables(delays, wl.nchan, wl.ndm, 8) is None
-    assert quad_tables(delays, wl.nchan, wl.ndm, 4) is None
+    assert quad_tables(delays, wl.nchan, wl.ndm, ND_THR) is None
+    assert quad_tables(delays, wl.nchan, wl.ndm, ND_THR // 2) is None
