@@ -4,23 +4,23 @@
 // exact in integers.
 //
 // Data flow per CTA (one DM tile x one 512-sample time tile, taken as 256
-// sample pairs (t, t + 256)), per chunk of 16 channels:
-//   1. one warp queues bulk copies (cp.async.bulk, the TMA engine) of each
-//      channel's input window -- the "channel vector" of Sec. 2.4, sized by
-//      the largest and smallest delay of the tile -- plus the chunk's plan
-//      record into shared memory, signalling an mbarrier; copies run three
-//      chunks ahead of the accumulation (triple-buffered windows);
-//   2. all threads build pattern rows: word i of a row holds, for one
+// sample pairs (t, t + 256)), per chunk of 16 channels, in two warp roles
+// that hand chunks to each other through named barriers:
+//   1. a building warp queues bulk copies (cp.async.bulk, the TMA engine) of
+//      each channel's input window -- the "channel vector" of Sec. 2.4,
+//      sized by the largest and smallest delay of the tile -- plus the
+//      chunk's plan record into shared memory, signalling an mbarrier, two
+//      chunks ahead (triple-buffered windows);
+//   2. 8 building warps build pattern rows: word i of a row holds, for one
 //      relative-delay pattern of a quad of channels, the four channels' sum
-//      at pair i as two 16-bit halves (dd_quad_plan.cpp); rows of chunk k+1
-//      are built while chunk k is accumulated (double buffer), with one CTA
-//      barrier per chunk;
-//   3. every thread adds, for each of its DM trials and sample pairs, the
-//      row words of two quads to a packed accumulator with one three-input
-//      integer add: 16 channel-samples per instruction and 8 per 32-bit
-//      shared-memory word.  Every 64 quads the 16-bit halves are drained into
-//      32-bit sums kept in tensor memory (tcgen05.st / tcgen05.ld), which
-//      spares the 64 registers per thread they would take.
+//      at pair i as two 16-bit halves (dd_quad_plan.cpp); they build chunk
+//      k+1 while the accumulating warps add chunk k (double-buffered rows);
+//   3. 16 accumulating warps add, for each of their DM trials and sample
+//      pairs, the row words of two quads to a packed accumulator with one
+//      three-input integer add: 16 channel-samples per instruction and 8 per
+//      32-bit shared-memory word.  Every 64 quads the 16-bit halves are
+//      drained into 32-bit sums kept in tensor memory (tcgen05.st /
+//      tcgen05.ld), which spares the 64 registers per thread they would take.
 // Waits on the mbarriers are bounded (globaltimer): on expiry the CTA records
 // DD_ERR_DEVICE_TIMEOUT in the plan's status word, waits (bounded) for its
 // own copies still in flight, frees its tensor memory and returns without
@@ -123,13 +123,15 @@ __device__ __forceinline__ void load_offsets(const int32_t *p, int (&o)[N]) {
       const int4 v = reinterpret_cast<const int4 *>(p)[i / 4];
       o[i] = v.x, o[i + 1] = v.y, o[i + 2] = v.z, o[i + 3] = v.w;
     }
-  } else {
-    static_assert(N % 2 == 0, "offsets are loaded in pairs at least");
+  } else if constexpr (N % 2 == 0) {
 #pragma unroll
     for (int i = 0; i < N; i += 2) {
       const int2 v = reinterpret_cast<const int2 *>(p)[i / 2];
       o[i] = v.x, o[i + 1] = v.y;
     }
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) o[i] = p[i];
   }
 }
 
@@ -351,6 +353,34 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, uint64_
 // entry m = i * kPairsPerThread + j (trial i, pair j) sits in columns 2m
 // (first half) and 2m + 1 (second half) of this thread's lane, moved 8
 // entries (16 columns) at a time.  `load`: add to the sums stored so far.
+// Named CTA barriers (ids 1..5; id 0 is __syncthreads).  `count` threads take
+// part, in whole warps; bar.arrive does not wait, bar.sync waits for the
+// barrier to complete, and the completion orders shared-memory accesses of
+// all participants before it with those after it.
+__device__ __forceinline__ void bar_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int count) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+// bar.sync that also returns the OR of `pred` over the participants.
+__device__ __forceinline__ bool bar_or(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "bar.red.or.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}"
+      : "=r"(r)
+      : "r"(static_cast<uint32_t>(pred)), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+constexpr int kBarFull = 1;   // + stage: rows of the stage's chunk built
+constexpr int kBarEmpty = 3;  // + stage: rows and record of the stage's chunk consumed
+constexpr int kBarBuild = 5;  // building warps among themselves
+constexpr int kBuildThreads = 32 * kBuildWarps;
+
 template <int ND_THR>
 __device__ __forceinline__ void drain(uint32_t (&acc)[ND_THR][kPairsPerThread], uint32_t taddr,
                                       bool load) {
@@ -380,21 +410,20 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   constexpr int ND_CTA = kDmGroups * ND_THR;
   constexpr int kSegsOff = units_offset(ND_CTA);
   constexpr int kStartsOff = warp_start_offset(ND_CTA);
-  // tensor-memory columns: 4 warps share each 32-lane quarter, each thread
-  // keeps 2 * ND_THR * kPairsPerThread sums
+  // tensor-memory columns: accumulating warp w uses lane quarter w % 4 and
+  // column block w / 4 of 2 * ND_THR * kPairsPerThread columns (one per sum)
   constexpr uint32_t kColsPerThread = 2 * ND_THR * kPairsPerThread;
-  constexpr uint32_t kTmemCols = 4 * kColsPerThread;
+  constexpr uint32_t kTmemCols = kAccThreads / 32 / 4 * kColsPerThread;
+  static_assert(kAccThreads % 128 == 0, "whole warp quartets");
   static_assert(ND_THR * kPairsPerThread % 8 == 0 && kTmemCols >= 32 && kTmemCols <= 512 &&
                     (kTmemCols & (kTmemCols - 1)) == 0,
                 "tensor-memory allocation must be a power of two in 32..512 columns");
-  static_assert(kThreads / 32 == 16, "four warps per tensor-memory lane quarter");
   static_assert(kFlushQuads % kQuadsPerChunk == 0, "drain at chunk boundaries");
+  static_assert(kRawStages == 3 && kRecStages == 4 && kRowStages == 2, "pipeline depths");
   constexpr int kFlushChunks = kFlushQuads / kQuadsPerChunk;
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int tg = warp & (kTimeGroups - 1);
-  const int dg = warp / kTimeGroups;
   // DM tiles vary fastest across the grid, so the CTAs resident at any time
   // cover a narrow span of input samples for all DM tiles and share the
   // input windows through L2 instead of re-reading them from HBM.
@@ -405,6 +434,8 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   // address, raw window table, records, raw window buffers, pattern rows
   const uint32_t bar0 = smem_addr(smem);
   auto tma_bar = [&](int m) { return bar0 + 8u * (m % kRawStages); };
+  // chunk at which the building warps stopped after a copy wait ran out
+  volatile int32_t *abort_at = reinterpret_cast<volatile int32_t *>(smem + kTmemSlot + 4);
   int32_t *meta_s = reinterpret_cast<int32_t *>(smem + kBarrierBytes);
   const uint32_t meta_bytes = static_cast<uint32_t>((a.nchan_pad * 8 + 15) / 16 * 16);
   const uint32_t rec_bytes = static_cast<uint32_t>(a.rec_words) * 4;
@@ -424,6 +455,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   for (int i = tid; i < 2 * a.nchan_pad; i += kThreads) meta_s[i] = meta_g[i];
   if (tid == 0) {
     for (int b = 0; b < kRawStages; ++b) mbar_init(tma_bar(b), 1);
+    *abort_at = INT32_MAX;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) tmem_alloc(bar0 + kTmemSlot, kTmemCols);
@@ -431,153 +463,158 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   __syncthreads();
   tmem_fence_after();
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem + kTmemSlot);
-  // this warp's lane quarter (bits 31..16) and column block
-  const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
-                         static_cast<uint32_t>(warp >> 2) * kColsPerThread;
 
-  // Pipeline (chunk m uses raw stage m%3, record stage m%4, row stage m%2):
-  // iteration k starts with a CTA barrier (rows of chunk k built, chunk k-1
-  // consumed); warp 0 then queues the copies of chunk k+3 into the stages of
-  // chunks k (raw) and k-1 (record); every warp waits (bounded) for the copies
-  // of chunk k+1 and builds its share of chunk k+1's rows, spread over the
-  // accumulation of chunk k.  A copy wait that runs out is folded into the
-  // next barrier (barrier-or), so every thread leaves the loop together.
-  int issued = 0;  // chunks queued (warp 0)
-  if (warp == 0 && !a.skip_copies) {
-    const int prefill = a.nchunks < kRawStages ? a.nchunks : kRawStages;
-    for (int m = 0; m < prefill; ++m)
-      issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
-    issued = prefill;
-  }
-
+  // Pipeline (chunk m: raw stage m%3, record stage m%4, row stage m%2).
+  // Building warps, chunk j: wait until the accumulating warps are done with
+  // chunk j-2 (its rows and record stages are reused); wait (bounded) for
+  // the copies of chunk j and agree among themselves that they landed; the
+  // first building warp queues the copies of chunk j+2 (into the stages of
+  // chunks j-1 and j-2); build this warp's units of chunk j's rows; signal
+  // the rows built.  Accumulating warps, chunk k: wait for its rows, add
+  // them, signal the stage consumed.  A copy wait that runs out records its
+  // chunk in abort_at before that chunk's rows signal; both roles leave at
+  // that chunk, and the building warps then wait for the consumed signals
+  // still outstanding, so every barrier phase completes.
+  const bool builder = warp >= kAccThreads / 32;
+  bool aborted = false;
+  int issued = 0;  // chunks queued (first building warp)
   uint32_t acc[ND_THR][kPairsPerThread];
 #pragma unroll
   for (int i = 0; i < ND_THR; ++i)
 #pragma unroll
     for (int j = 0; j < kPairsPerThread; ++j) acc[i][j] = 0;
+  bool drained = false;  // tensor memory holds sums
+  const int dg = warp / kTimeGroups;
+  const int tg = warp & (kTimeGroups - 1);
   const uint32_t my_pair = static_cast<uint32_t>(tg * 32 * kPairsPerThread + lane);
 
-  bool ok = warp_wait(tma_bar(0), 0, a.timeout_ns, lane);
-  if (ok)
-    build_rows(rec_ptr(0), raw_addr(0), prow_addr(0), kSegsOff, warp, lane, 0,
-               warp_segments(rec_ptr(0), warp, kStartsOff), kStartsOff);
-
-  constexpr int kSteps = kQuadsPerChunk / 2;  // two quads per step
-  bool aborted = false;
-  bool drained = false;  // tensor memory holds sums
-  for (int k = 0; k < a.nchunks; ++k) {
-    if (__syncthreads_or(!ok)) {
-      aborted = true;
-      break;
+  if (builder) {
+    const int bw = warp - kAccThreads / 32;
+    const bool issuer = bw == 0 && !a.skip_copies;
+    if (issuer) {
+      const int prefill = a.nchunks < 2 ? a.nchunks : 2;
+      for (int m = 0; m < prefill; ++m)
+        issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
+      issued = prefill;
     }
-    if (warp == 0 && k + kRawStages < a.nchunks && !a.skip_copies) {
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      const int m = k + kRawStages;
-      issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
-      issued = m + 1;
-    }
-    // accumulate chunk k (two quads per step) and build this warp's share of
-    // chunk k+1's rows after each step; the copies of chunk k+1 are waited
-    // for (bounded) just before the first build step, and each step's offset
-    // table is fetched one step ahead
-    const bool next = k + 1 < a.nchunks;
-    const int32_t *rec = rec_ptr(k);
-    const int nq = rec[2];
-    const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
-    const uint32_t prow = prow_addr(k);
-    const int32_t *rec_n = rec_ptr(k + 1);
-    int nseg_w = -1;  // build units of chunk k+1 for this warp, once its copies landed
-    int m_done = 0;
-    int a_next[2][ND_THR];
-    load_offsets<ND_THR>(A, a_next[0]);
-    load_offsets<ND_THR>(A + ND_CTA, a_next[1]);
-#pragma unroll
-    for (int st = 0; st < kSteps; ++st) {
-      const int q = 2 * st;
-      if (q < nq) {
-        int a_cur[2][ND_THR];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int i = 0; i < ND_THR; ++i) a_cur[h][i] = a_next[h][i];
-        if (q + 2 < nq) {
-          load_offsets<ND_THR>(A + (q + 2) * ND_CTA, a_next[0]);
-          load_offsets<ND_THR>(A + (q + 3) * ND_CTA, a_next[1]);
-        }
-        if (q + 1 < nq) {
-#pragma unroll
-          for (int i = 0; i < ND_THR; ++i)
-            AccPairs<0>::two(acc[i], prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair),
-                             prow + 4u * (static_cast<uint32_t>(a_cur[1][i]) + my_pair));
-        } else {
-#pragma unroll
-          for (int i = 0; i < ND_THR; ++i)
-            AccPairs<0>::one(acc[i], prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair));
-        }
+    for (int j = 0; j < a.nchunks; ++j) {
+      if (j >= 2) bar_sync(kBarEmpty + (j & 1), kThreads);
+      const bool ok = warp_wait(tma_bar(j), (j / kRawStages) & 1, a.timeout_ns, lane);
+      if (bar_or(kBarBuild, kBuildThreads, !ok)) {
+        if (bw == 0 && lane == 0) *abort_at = j;
+        aborted = true;
+        bar_arrive(kBarFull + (j & 1), kThreads);
+        if (j >= 1) bar_sync(kBarEmpty + ((j - 1) & 1), kThreads);
+        break;
       }
-      if (next && ok) {
-        if (nseg_w < 0) {
-          ok = warp_wait(tma_bar(k + 1), ((k + 1) / kRawStages) & 1, a.timeout_ns, lane);
-          if (!ok) continue;  // reported at the next barrier
-          nseg_w = warp_segments(rec_n, warp, kStartsOff);
-        }
-        const int m_to = (nseg_w * (st + 1) + kSteps - 1) / kSteps;
-        if (m_to > m_done) {
-          build_rows(rec_n, raw_addr(k + 1), prow_addr(k + 1), kSegsOff, warp, lane, m_done, m_to,
-                     kStartsOff);
-          m_done = m_to;
-        }
+      if (issuer && j + 2 < a.nchunks) {
+        // every building warp is past chunk j-1 (bar_or above) and the
+        // accumulating warps past chunk j-2 (bar_sync): their stages are free
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const int m = j + 2;
+        issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
+        issued = m + 1;
       }
+      const int32_t *rec = rec_ptr(j);
+      build_rows(rec, raw_addr(j), prow_addr(j), kSegsOff, bw, lane, 0,
+                 warp_segments(rec, bw, kStartsOff), kStartsOff);
+      bar_arrive(kBarFull + (j & 1), kThreads);
     }
-    // at most kFlushQuads quads in the 16-bit halves
-    if ((k + 1) % kFlushChunks == 0 && next) {
-      drain<ND_THR>(acc, taddr, drained);
-      drained = true;
-    }
-  }
-  if (!aborted && __syncthreads_or(!ok)) aborted = true;  // last chunk's copy wait
-
-  if (aborted) {
-    // a bounded wait ran out: record it; warp 0 waits, bounded, for the
-    // copies it queued that may still be in flight (the last kRawStages
-    // queued, each on its own barrier) before the CTA leaves
-    if (tid == 0) {
-      atomicExch(a.status, 1);
-      for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
-        mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, a.timeout_ns);
+    if (!aborted) {
+      // consumed signals of the last two chunks
+      if (a.nchunks >= 2) bar_sync(kBarEmpty + ((a.nchunks - 2) & 1), kThreads);
+      bar_sync(kBarEmpty + ((a.nchunks - 1) & 1), kThreads);
     }
   } else {
-    // final sums: stored part (if any) + the packed halves; pair j of trial
-    // i covers samples my_pair + 32 j and my_pair + 32 j + kHalf
-#pragma unroll
-    for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
-      uint32_t v[16];
-      if (drained) {
-        tmem_ld16(taddr + 16u * blk, v);
-      } else {
-#pragma unroll
-        for (int e = 0; e < 16; ++e) v[e] = 0;
+    const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                           static_cast<uint32_t>(warp >> 2) * kColsPerThread;
+    for (int k = 0; k < a.nchunks; ++k) {
+      bar_sync(kBarFull + (k & 1), kThreads);
+      if (*abort_at == k) {  // rows of chunk k were not built
+        aborted = true;
+        break;
       }
+      const int32_t *rec = rec_ptr(k);
+      const int nq = rec[2];
+      const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
+      const uint32_t prow = prow_addr(k);
+      int a_next[2][ND_THR];
+      load_offsets<ND_THR>(A, a_next[0]);
+      load_offsets<ND_THR>(A + ND_CTA, a_next[1]);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int m = 8 * blk + e;
-        const int i = m / kPairsPerThread, j = m % kPairsPerThread;
-        const int d = tile * ND_CTA + dg * ND_THR + i;
-        if (d >= a.ndm) continue;
-        int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
-        const uint32_t w = acc[i][j];
-        const int64_t t = t_cta + my_pair + 32 * j;
-        if (t < a.nsamp_out) orow[t] = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
-        if (t + kHalf < a.nsamp_out)
-          orow[t + kHalf] = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
+      for (int q = 0; q < kQuadsPerChunk; q += 2) {
+        if (q < nq) {
+          int a_cur[2][ND_THR];
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int i = 0; i < ND_THR; ++i) a_cur[h][i] = a_next[h][i];
+          if (q + 2 < nq) {
+            load_offsets<ND_THR>(A + (q + 2) * ND_CTA, a_next[0]);
+            load_offsets<ND_THR>(A + (q + 3) * ND_CTA, a_next[1]);
+          }
+          if (q + 1 < nq) {
+#pragma unroll
+            for (int i = 0; i < ND_THR; ++i)
+              AccPairs<0>::two(acc[i], prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair),
+                               prow + 4u * (static_cast<uint32_t>(a_cur[1][i]) + my_pair));
+          } else {
+#pragma unroll
+            for (int i = 0; i < ND_THR; ++i)
+              AccPairs<0>::one(acc[i],
+                               prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair));
+          }
+        }
+      }
+      bar_arrive(kBarEmpty + (k & 1), kThreads);
+      // at most kFlushQuads quads in the 16-bit halves
+      if ((k + 1) % kFlushChunks == 0 && k + 1 < a.nchunks) {
+        drain<ND_THR>(acc, taddr, drained);
+        drained = true;
+      }
+    }
+    if (!aborted) {
+      // final sums: stored part (if any) + the packed halves; pair j of
+      // trial i covers samples my_pair + 32 j and my_pair + 32 j + kHalf
+#pragma unroll
+      for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
+        uint32_t v[16];
+        if (drained) {
+          tmem_ld16(taddr + 16u * blk, v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = 0;
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int m = 8 * blk + e;
+          const int i = m / kPairsPerThread, j = m % kPairsPerThread;
+          const int d = tile * ND_CTA + dg * ND_THR + i;
+          if (d >= a.ndm) continue;
+          int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
+          const uint32_t w = acc[i][j];
+          const int64_t t = t_cta + my_pair + 32 * j;
+          if (t < a.nsamp_out) orow[t] = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
+          if (t + kHalf < a.nsamp_out)
+            orow[t + kHalf] = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
+        }
       }
     }
   }
+
   // every thread's tensor-memory accesses are complete (waited) before the
   // allocating warp frees the columns
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
+  if (*abort_at != INT32_MAX && builder && warp - kAccThreads / 32 == 0 && lane == 0) {
+    // a bounded wait ran out: record it, and wait (bounded) for the copies
+    // queued by this warp that may still be in flight (the last kRawStages
+    // queued, each on its own barrier) before the CTA leaves
+    atomicExch(a.status, 1);
+    for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
+      mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, a.timeout_ns);
+  }
   if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
 }
 

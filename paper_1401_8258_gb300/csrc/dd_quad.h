@@ -2,9 +2,11 @@
 // kernel for u8 input (internal to libdd).
 //
 // CTA tile: kDmGroups x nd_thr DM trials by kTimeTile output samples, taken
-// as kHalf sample pairs (t, t + kHalf).  16 warps = kDmGroups DM groups x
-// kTimeGroups time groups (16 x 1); a thread owns nd_thr trials (4) x
-// kPairsPerThread pairs (8; pair = base + lane + 32*j).  Channels are processed in chunks of
+// as kHalf sample pairs (t, t + kHalf).  Two warp roles: 16 accumulating
+// warps = kDmGroups DM groups x kTimeGroups time groups (16 x 1), a thread
+// owning nd_thr trials (4) x kPairsPerThread pairs (8; pair = base + lane +
+// 32*j); and kBuildWarps (8) building warps that queue the copies and build
+// the pattern rows one chunk ahead.  Channels are processed in chunks of
 // kQuadsPerChunk quads (4 channels each).
 //
 // Pattern rows.  For quad q of a DM tile, let b be the smallest channel-0
@@ -38,10 +40,10 @@
 //         first sample within the two loaded words, 0x3210 + 0x1111 s (the
 //         same shift serves the second half, kHalf bytes on).  Channel 0's
 //         shift is the same for every pattern (its relative delay is 0).
-//   warp_start[kThreads/32 + 1] (int16 pairs, after the units): the units are
-//     ordered by the warp that builds them (balanced on the host, largest
-//     first onto the least loaded warp); warp w builds units
-//     warp_start[w] .. warp_start[w+1]-1.
+//   warp_start[kBuildWarps + 1] (int16 pairs, after the units): the units
+//     are ordered by the building warp that builds them (balanced on the
+//     host, largest first onto the least loaded warp); building warp w builds
+//     units warp_start[w] .. warp_start[w+1]-1.
 // raw_meta[tile][nchan_pad][2]: {window start relative to the tile's first
 // output sample (a multiple of 16; -16 where the slack reaches before the
 // first sample), bytes needed (0 = padding channel)}.
@@ -76,7 +78,12 @@ namespace ddq {
 #endif
 constexpr int kDmGroups = DDQ_DM_GROUPS;
 constexpr int kTimeGroups = DDQ_TIME_GROUPS;
-constexpr int kThreads = 32 * kDmGroups * kTimeGroups;                // 512
+#ifndef DDQ_BUILD_WARPS
+#define DDQ_BUILD_WARPS 8
+#endif
+constexpr int kAccThreads = 32 * kDmGroups * kTimeGroups;             // 512
+constexpr int kBuildWarps = DDQ_BUILD_WARPS;
+constexpr int kThreads = kAccThreads + 32 * kBuildWarps;              // 768
 constexpr int kTimesPerThread = DDQ_TIMES_PER_THREAD;
 constexpr int kTimeTile = kTimeGroups * 32 * kTimesPerThread;         // 512
 constexpr int kHalf = kTimeTile / 2;                                  // pair (t, t + kHalf)
@@ -95,7 +102,7 @@ constexpr int kMaxSmem = 227 * 1024;
 DDQ_HD constexpr int units_offset(int nd_cta) { return kRecHeader + kQuadsPerChunk * nd_cta; }
 DDQ_HD constexpr int warp_start_offset(int nd_cta) { return units_offset(nd_cta) + kMaxUnits * kUnitWords; }
 DDQ_HD constexpr int rec_words(int nd_cta) {
-  return (warp_start_offset(nd_cta) + (kThreads / 32 + 2) / 2 + 3) / 4 * 4;
+  return (warp_start_offset(nd_cta) + (kBuildWarps + 2) / 2 + 3) / 4 * 4;
 }
 
 struct Tables {

@@ -147,7 +147,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
   }
   // build units (need the final raw_stride for the byte offsets)
   if (4 * kQuadsPerChunk * static_cast<int64_t>(raw_stride) >= 0xffff) return 1;
-  constexpr int kWarps = kThreads / 32;
+  constexpr int kWarps = kBuildWarps;
   for (size_t rc = 0; rc < chunk_quads.size(); ++rc) {
     int32_t *rec = &t.recs[rc * t.rec_words];
     std::vector<std::array<int32_t, kUnitWords>> list;

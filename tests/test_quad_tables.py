@@ -23,7 +23,7 @@ QUADS_PER_CHUNK = 4
 FLUSH_CHUNKS = 64 // QUADS_PER_CHUNK
 REC_HEADER = 4
 UNIT_WORDS = 20
-NWARPS = 16
+NWARPS = 8  # building warps
 ND_THR = 4  # DM trials per thread of the 64-trial tile (16 warps x 4); 2 for the 32-trial one
 
 
