@@ -9,9 +9,9 @@
 //   1. a building warp queues bulk copies (cp.async.bulk, the TMA engine) of
 //      each channel's input window -- the "channel vector" of Sec. 2.4,
 //      sized by the largest and smallest delay of the tile -- plus the
-//      chunk's plan record into shared memory, signalling an mbarrier, two
-//      chunks ahead (triple-buffered windows);
-//   2. 8 building warps build pattern rows: word i of a row holds, for one
+//      chunk's plan record into shared memory, signalling an mbarrier,
+//      kCopyAhead chunks ahead of the chunk being built;
+//   2. 12 building warps build pattern rows: word i of a row holds, for one
 //      relative-delay pattern of a quad of channels, the four channels' sum
 //      at pair i as two 16-bit halves (dd_quad_plan.cpp); they build chunk
 //      k+1 while the accumulating warps add chunk k (double-buffered rows);
@@ -297,14 +297,10 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint
   const uint32_t oa0 = prmt(va0, 0u, 0x4341u), ob0 = prmt(vb0, 0u, 0x4341u);
   uint32_t dst = prow + 4u * (static_cast<uint32_t>(h.z) & 0xfffffu) + 16u * lane;
   const uint32_t row_bytes = 4u * (static_cast<uint32_t>(h.w) & 0xffffu);
-  const int2 *sels = reinterpret_cast<const int2 *>(ud + 4);
-#pragma unroll
-  for (int p = 0; p < kMaxPatterns; ++p) {
-    if (static_cast<uint32_t>(p) >= npat) break;
-    const int2 sp = sels[p];
-    const uint32_t sel[4] = {0u, static_cast<uint32_t>(sp.x), static_cast<uint32_t>(sp.x) >> 16,
-                             static_cast<uint32_t>(sp.y)};  // prmt reads bits 0..15
-    uint32_t sa = va0, sb = vb0, oa = oa0, ob = ob0;  // word sums and odd-byte sums
+  // the 4 row words of one pattern from its selectors of channels 1..3
+  auto pattern = [&](uint32_t s12, uint32_t s3, uint32_t dst_p) {
+    const uint32_t sel[4] = {0u, s12, s12 >> 16, s3};  // prmt reads bits 0..15
+    uint32_t sa = va0, sb = vb0, oa = oa0, ob = ob0;   // word sums and odd-byte sums
 #pragma unroll
     for (int ch = 1; ch < 4; ++ch) {
       const uint32_t va = prmt(a0[ch], a1[ch], sel[ch]), vb = prmt(b0[ch], b1[ch], sel[ch]);
@@ -315,9 +311,22 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t raw, uint
     }
     const uint32_t ea = sa - (oa << 8), eb = sb - (ob << 8);  // bytes 0, 2 sums
     // word w + j: low half = first-half sum at sample j, high half = second
-    sts128(dst, prmt(ea, eb, 0x5410u), prmt(oa, ob, 0x5410u), prmt(ea, eb, 0x7632u),
+    sts128(dst_p, prmt(ea, eb, 0x5410u), prmt(oa, ob, 0x5410u), prmt(ea, eb, 0x7632u),
            prmt(oa, ob, 0x7632u));
-    dst += row_bytes;
+  };
+  // two patterns per step (independent chains for the scheduler)
+  const int4 *sels = reinterpret_cast<const int4 *>(ud + 4);
+#pragma unroll
+  for (int p = 0; p < kMaxPatterns; p += 2) {
+    if (static_cast<uint32_t>(p) >= npat) break;
+    const int4 sp = sels[p / 2];
+    if (static_cast<uint32_t>(p) + 1 < npat) {
+      pattern(static_cast<uint32_t>(sp.x), static_cast<uint32_t>(sp.y), dst);
+      pattern(static_cast<uint32_t>(sp.z), static_cast<uint32_t>(sp.w), dst + row_bytes);
+    } else {
+      pattern(static_cast<uint32_t>(sp.x), static_cast<uint32_t>(sp.y), dst);
+    }
+    dst += 2 * row_bytes;
   }
 }
 
@@ -376,9 +385,10 @@ __device__ __forceinline__ bool bar_or(int id, int count, bool pred) {
       : "memory");
   return r != 0;
 }
-constexpr int kBarFull = 1;   // + stage: rows of the stage's chunk built
-constexpr int kBarEmpty = 3;  // + stage: rows and record of the stage's chunk consumed
-constexpr int kBarBuild = 5;  // building warps among themselves
+constexpr int kBarFull = 1;                           // + row stage: its chunk's rows built
+constexpr int kBarEmpty = kBarFull + kRowStages;       // + row stage: rows, record consumed
+constexpr int kBarBuild = kBarEmpty + kRowStages;      // building warps among themselves
+static_assert(kBarBuild < 16, "named barrier ids");
 constexpr int kBuildThreads = 32 * kBuildWarps;
 
 template <int ND_THR>
@@ -419,7 +429,9 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
                     (kTmemCols & (kTmemCols - 1)) == 0,
                 "tensor-memory allocation must be a power of two in 32..512 columns");
   static_assert(kFlushQuads % kQuadsPerChunk == 0, "drain at chunk boundaries");
-  static_assert(kRawStages == 3 && kRecStages == 4 && kRowStages == 2, "pipeline depths");
+  static_assert(kRawStages == kCopyAhead + 1 && kRecStages == kRowStages + kCopyAhead &&
+                    8 * kRawStages <= kTmemSlot,
+                "pipeline depths");
   constexpr int kFlushChunks = kFlushQuads / kQuadsPerChunk;
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
@@ -464,13 +476,14 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   tmem_fence_after();
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem + kTmemSlot);
 
-  // Pipeline (chunk m: raw stage m%3, record stage m%4, row stage m%2).
-  // Building warps, chunk j: wait until the accumulating warps are done with
-  // chunk j-2 (its rows and record stages are reused); wait (bounded) for
-  // the copies of chunk j and agree among themselves that they landed; the
-  // first building warp queues the copies of chunk j+2 (into the stages of
-  // chunks j-1 and j-2); build this warp's units of chunk j's rows; signal
-  // the rows built.  Accumulating warps, chunk k: wait for its rows, add
+  // Pipeline (chunk m: raw stage m % kRawStages, record stage m % kRecStages, row
+  // stage m % kRowStages).  Building warps, chunk j: wait until the
+  // accumulating warps are done with chunk j - kRowStages (its row stage is
+  // reused, and so are older record stages); wait (bounded) for the copies
+  // of chunk j and agree among themselves that they landed; the first
+  // building warp queues the copies of chunk j+kCopyAhead (into the raw
+  // stage of chunk j-1 and the record stage of chunk j-kRowStages); build this
+  // warp's units of chunk j's rows; signal the rows built.  Accumulating warps, chunk k: wait for its rows, add
   // them, signal the stage consumed.  A copy wait that runs out records its
   // chunk in abort_at before that chunk's rows signal; both roles leave at
   // that chunk, and the building warps then wait for the consumed signals
@@ -492,44 +505,48 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     const int bw = warp - kAccThreads / 32;
     const bool issuer = bw == 0 && !a.skip_copies;
     if (issuer) {
-      const int prefill = a.nchunks < 2 ? a.nchunks : 2;
+      const int prefill = a.nchunks < kCopyAhead ? a.nchunks : kCopyAhead;
       for (int m = 0; m < prefill; ++m)
         issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
       issued = prefill;
     }
     for (int j = 0; j < a.nchunks; ++j) {
-      if (j >= 2) bar_sync(kBarEmpty + (j & 1), kThreads);
+      if (j >= kRowStages) bar_sync(kBarEmpty + j % kRowStages, kThreads);
       const bool ok = warp_wait(tma_bar(j), (j / kRawStages) & 1, a.timeout_ns, lane);
       if (bar_or(kBarBuild, kBuildThreads, !ok)) {
         if (bw == 0 && lane == 0) *abort_at = j;
         aborted = true;
-        bar_arrive(kBarFull + (j & 1), kThreads);
-        if (j >= 1) bar_sync(kBarEmpty + ((j - 1) & 1), kThreads);
+        bar_arrive(kBarFull + j % kRowStages, kThreads);
+        // consumed signals still outstanding: chunks j-kRowStages+1 .. j-1
+        for (int m = j - kRowStages + 1; m < j; ++m)
+          if (m >= 0) bar_sync(kBarEmpty + m % kRowStages, kThreads);
         break;
       }
-      if (issuer && j + 2 < a.nchunks) {
+      if (issuer && j + kCopyAhead < a.nchunks) {
         // every building warp is past chunk j-1 (bar_or above) and the
-        // accumulating warps past chunk j-2 (bar_sync): their stages are free
+        // accumulating warps past chunk j-kRowStages (bar_sync): the raw
+        // stage of chunk j-1 and the record stage of chunk j-kRowStages are
+        // free
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const int m = j + 2;
+        const int m = j + kCopyAhead;
         issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
         issued = m + 1;
       }
       const int32_t *rec = rec_ptr(j);
       build_rows(rec, raw_addr(j), prow_addr(j), kSegsOff, bw, lane, 0,
                  warp_segments(rec, bw, kStartsOff), kStartsOff);
-      bar_arrive(kBarFull + (j & 1), kThreads);
+      bar_arrive(kBarFull + j % kRowStages, kThreads);
     }
     if (!aborted) {
-      // consumed signals of the last two chunks
-      if (a.nchunks >= 2) bar_sync(kBarEmpty + ((a.nchunks - 2) & 1), kThreads);
-      bar_sync(kBarEmpty + ((a.nchunks - 1) & 1), kThreads);
+      // consumed signals of the last kRowStages chunks
+      for (int m = a.nchunks - kRowStages; m < a.nchunks; ++m)
+        if (m >= 0) bar_sync(kBarEmpty + m % kRowStages, kThreads);
     }
   } else {
     const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
                            static_cast<uint32_t>(warp >> 2) * kColsPerThread;
     for (int k = 0; k < a.nchunks; ++k) {
-      bar_sync(kBarFull + (k & 1), kThreads);
+      bar_sync(kBarFull + k % kRowStages, kThreads);
       if (*abort_at == k) {  // rows of chunk k were not built
         aborted = true;
         break;
@@ -566,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
           }
         }
       }
-      bar_arrive(kBarEmpty + (k & 1), kThreads);
+      bar_arrive(kBarEmpty + k % kRowStages, kThreads);
       // at most kFlushQuads quads in the 16-bit halves
       if ((k + 1) % kFlushChunks == 0 && k + 1 < a.nchunks) {
         drain<ND_THR>(acc, taddr, drained);

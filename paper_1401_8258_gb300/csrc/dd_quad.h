@@ -5,7 +5,7 @@
 // as kHalf sample pairs (t, t + kHalf).  Two warp roles: 16 accumulating
 // warps = kDmGroups DM groups x kTimeGroups time groups (16 x 1), a thread
 // owning nd_thr trials (4) x kPairsPerThread pairs (8; pair = base + lane +
-// 32*j); and kBuildWarps (8) building warps that queue the copies and build
+// 32*j); and kBuildWarps (12) building warps that queue the copies and build
 // the pattern rows one chunk ahead.  Channels are processed in chunks of
 // kQuadsPerChunk quads (4 channels each).
 //
@@ -79,11 +79,11 @@ namespace ddq {
 constexpr int kDmGroups = DDQ_DM_GROUPS;
 constexpr int kTimeGroups = DDQ_TIME_GROUPS;
 #ifndef DDQ_BUILD_WARPS
-#define DDQ_BUILD_WARPS 8
+#define DDQ_BUILD_WARPS 12
 #endif
 constexpr int kAccThreads = 32 * kDmGroups * kTimeGroups;             // 512
 constexpr int kBuildWarps = DDQ_BUILD_WARPS;
-constexpr int kThreads = kAccThreads + 32 * kBuildWarps;              // 768
+constexpr int kThreads = kAccThreads + 32 * kBuildWarps;              // 896
 constexpr int kTimesPerThread = DDQ_TIMES_PER_THREAD;
 constexpr int kTimeTile = kTimeGroups * 32 * kTimesPerThread;         // 512
 constexpr int kHalf = kTimeTile / 2;                                  // pair (t, t + kHalf)
@@ -118,10 +118,20 @@ struct Tables {
 
 // Pipeline depth: raw windows of chunks k+1 and k+2 are in flight while
 // chunk k+1 is interleaved and chunk k accumulated.
-constexpr int kRawStages = 3;
-constexpr int kRecStages = 4;
-constexpr int kRowStages = 2;
-constexpr int kBarrierBytes = 64;  // copy mbarriers (3 x 8 bytes), tensor-memory address, padding
+#ifndef DDQ_ROW_STAGES
+#define DDQ_ROW_STAGES 2
+#endif
+#ifndef DDQ_COPY_AHEAD
+#define DDQ_COPY_AHEAD 2
+#endif
+constexpr int kCopyAhead = DDQ_COPY_AHEAD;  // chunks queued ahead of the one being built
+constexpr int kRawStages = kCopyAhead + 1;
+constexpr int kRowStages = DDQ_ROW_STAGES;
+// a record stays in use until the accumulating warps are done with its
+// chunk, up to kRowStages chunks behind the building warps, which queue
+// copies kCopyAhead chunks ahead
+constexpr int kRecStages = kRowStages + kCopyAhead;
+constexpr int kBarrierBytes = 64;  // copy mbarriers (8 bytes each), tensor-memory address, flags
 constexpr int kTmemSlot = 32;      // byte offset of the tensor-memory address
 
 // Shared-memory layout: the mbarriers and tensor-memory address (kBarrierBytes), the tile's raw

@@ -23,7 +23,7 @@ QUADS_PER_CHUNK = 4
 FLUSH_CHUNKS = 64 // QUADS_PER_CHUNK
 REC_HEADER = 4
 UNIT_WORDS = 20
-NWARPS = 8  # building warps
+NWARPS = 12  # building warps
 ND_THR = 4  # DM trials per thread of the 64-trial tile (16 warps x 4); 2 for the 32-trial one
 
 
@@ -200,6 +200,7 @@ def test_tables_fit_shared_memory_for_the_workloads():
         assert tb is not None and tb["nd_cta"] == 64, name
         meta = (tb["nchan_pad"] * 8 + 15) // 16 * 16
         smem = 64 + meta + 4 * tb["rec_words"] * 4 + 3 * 16 * tb["raw_stride"] + 2 * tb["prow_words"] * 4
+        # (2 row stages, 4 record stages, 3 raw stages)
         assert smem == tb["smem"] <= 227 * 1024
 
 
