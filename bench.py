@@ -1,8 +1,9 @@
 """Benchmark of the dedispersion + detection hot path on GB300.
 
 One step = one pass of the whole path over one synthetic filterbank block
-resident in HBM: dd_execute (brute-force dedispersion) then dd_detect
-(per-DM statistics, n-sigma threshold, candidate list, count to host).
+resident in HBM: dd_run -- brute-force dedispersion (which also accumulates
+each DM row's exact sums and per-tile maxima), then per-DM statistics,
+n-sigma threshold, candidate list and the count to the host.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -292,12 +293,13 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        dd.dd_execute(plan.handle, block, wl.nsamp, block.stride(0), out, stream)
-        ev_mid.record(stream)
-        st, total = dd.dd_detect(plan.handle, out, nsamp_out, NSIGMA, cands, cap, stream)
+        # ev_mid is recorded by the library right after the dedispersion kernel
+        st, total = dd.dd_run(plan.handle, block, wl.nsamp, block.stride(0), out, NSIGMA, cands,
+                              cap, stream, ev_mid)
         return total
 
     ev_mid = torch.cuda.Event(enable_timing=True)
+    ev_mid.record(stream)  # creates the event before its handle is passed on
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()
@@ -305,6 +307,8 @@ def run_ours(args):
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     mids = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for e in mids:
+        e.record(stream)
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     clocks = ClockSampler(local)
     if world > 1:

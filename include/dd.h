@@ -137,8 +137,23 @@ int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_el
 int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma, dd_candidate *cands,
               int64_t capacity, int64_t *count, void *stream);
 
-/* Host copies of the per-DM mean and rms computed by the last dd_detect on
- * this plan (double[ndm] each; either pointer may be NULL). */
+/* The whole path on device buffers in one call: dd_execute(block -> out)
+ * followed by dd_detect(out) (Sec. 2.1.1, 3.5, 3.6), with the same results --
+ * every element of out, the same candidates in (dm_idx, t) order, the same
+ * per-DM mean and rms (dd_get_stats), *count and status codes as those two
+ * calls.  Arguments as for dd_execute and dd_detect; `event` is an optional
+ * cudaEvent_t (NULL = none) recorded on `stream` right after the
+ * dedispersion kernel, for timing the phases.  When the staged kernel runs,
+ * it also accumulates each DM row's exact integer sums and the largest value
+ * of each 512-sample time tile as it writes out, so the detection reads out
+ * only in the tiles that can hold a candidate instead of twice in full.
+ * Synchronises `stream` once. */
+int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems, void *out,
+           float nsigma, dd_candidate *cands, int64_t capacity, int64_t *count, void *stream,
+           void *event);
+
+/* Host copies of the per-DM mean and rms computed by the last dd_detect or
+ * dd_run on this plan (double[ndm] each; either pointer may be NULL). */
 int dd_get_stats(const dd_plan *p, double *mean, double *sigma);
 
 /* Synchronise `stream` and return the plan's sticky device status
@@ -147,7 +162,7 @@ int dd_sync(dd_plan *p, void *stream);
 
 /* Whole path on host buffers: copy `host_block` ([nchan][pitch_elems],
  * host memory, pinned for full speed) to plan-owned device memory, dedisperse
- * (dd_execute), detect (dd_detect) and copy the candidates back to
+ * and detect (dd_run) and copy the candidates back to
  * `host_cands` (host, `capacity` slots).  *count as for dd_detect.  The plan
  * grows its device buffers on first use for a given nsamp_in / pitch and keeps
  * them until destroyed.  Synchronises `stream` before returning. */

@@ -16,8 +16,8 @@ from . import _native
 from ._native import (CANDIDATE_DTYPE, DD_ERR_OVERFLOW, DD_F16, DD_F32, DD_OK, DD_U8, DTYPE_CODES,
                       DDError, dd_compute_delays, dd_detect, dd_execute, dd_get_stats,
                       dd_plan_create, dd_plan_delays, dd_plan_destroy, dd_plan_launch_count,
-                      dd_plan_max_delay, dd_plan_nsamp_out, dd_process_host, dd_status_string,
-                      dd_sync)
+                      dd_plan_max_delay, dd_plan_nsamp_out, dd_process_host, dd_run,
+                      dd_status_string, dd_sync)
 from .build import build
 
 __all__ = [
@@ -25,6 +25,7 @@ __all__ = [
     "DD_ERR_OVERFLOW", "DTYPE_CODES", "dd_compute_delays", "dd_plan_create", "dd_plan_destroy",
     "dd_plan_max_delay", "dd_plan_nsamp_out", "dd_plan_delays", "dd_execute", "dd_detect",
     "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
+    "dd_run",
 ]
 
 _TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
@@ -104,6 +105,27 @@ class Plan:
         host = cands[:k].cpu().numpy().view(CANDIDATE_DTYPE).reshape(-1) if k else \
             np.zeros(0, dtype=CANDIDATE_DTYPE)
         return host, total
+
+    def run(self, block, nsigma, out=None, nsamp_in=None, capacity=1 << 16, stream=None):
+        """Dedisperse and detect in one call (dd_run); returns
+        ``(out, candidates numpy array, total)``."""
+        import torch
+        if block.dim() != 2 or block.stride(1) != 1 or block.shape[0] != self.nchan:
+            raise ValueError("block must be [nchan][pitch] with unit time stride")
+        if str(block.dtype).split(".")[-1] != _TORCH_IN[self.dtype]:
+            raise TypeError(f"block dtype {block.dtype} does not match plan dtype {self.dtype}")
+        nsamp_in = block.shape[1] if nsamp_in is None else int(nsamp_in)
+        n_out = self.nsamp_out(nsamp_in)
+        if out is None:
+            out = torch.empty((self.ndm, n_out), dtype=self.out_torch_dtype, device=block.device)
+        capacity = int(capacity)
+        cands = torch.empty((max(capacity, 1), 16), dtype=torch.uint8, device=block.device)
+        st, total = dd_run(self.handle, block, nsamp_in, block.stride(0), out, nsigma,
+                           cands if capacity else None, capacity, stream)
+        k = min(total, capacity)
+        host = cands[:k].cpu().numpy().view(CANDIDATE_DTYPE).reshape(-1) if k else \
+            np.zeros(0, dtype=CANDIDATE_DTYPE)
+        return out, host, total
 
     def stats(self):
         return dd_get_stats(self.handle, self.ndm)

@@ -66,6 +66,7 @@ SIGNATURES = [
     ("dd_plan_inject_fault", ctypes.c_int, [_vp, _i32]),
     ("dd_plan_kernel_info", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     ("dd_detect_noalloc", ctypes.c_int, [_vp, _i32, _i32, _i64, _f32, _vp, _i64, _vp, _vp]),
+    ("dd_run", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _f32, _vp, _i64, _vp, _vp, _vp]),
 ]
 
 PEAK_KINDS = {"fadd": 0, "fadd2": 1, "iadd": 2, "iadd3": 3, "imad": 4, "lop3": 5, "prmt": 6,
@@ -184,6 +185,20 @@ def dd_detect(plan, out, nsamp_out, nsigma, cands, capacity, stream=None) -> tup
     st = load().dd_detect(plan, _addr(out), int(nsamp_out), float(nsigma), _addr(cands),
                           int(capacity), ctypes.addressof(cnt), _stream(stream))
     _check(st, "dd_detect", allow=(DD_ERR_OVERFLOW,))
+    return st, int(cnt.value)
+
+
+def dd_run(plan, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity, stream=None,
+           event=None) -> tuple[int, int]:
+    """Dedispersion + detection in one call; returns ``(status, count)``
+    (DD_OK or DD_ERR_OVERFLOW).  ``event``: optional CUDA event (torch Event
+    or raw handle) recorded after the dedispersion kernel."""
+    cnt = ctypes.c_int64(0)
+    ev = None if event is None else int(getattr(event, "cuda_event", event))
+    st = load().dd_run(plan, _addr(block), int(nsamp_in), int(pitch_elems), _addr(out),
+                       float(nsigma), _addr(cands), int(capacity), ctypes.addressof(cnt),
+                       _stream(stream), ev)
+    _check(st, "dd_run", allow=(DD_ERR_OVERFLOW,))
     return st, int(cnt.value)
 
 

@@ -60,6 +60,33 @@ int ensure_chunk_workspace(dd_plan *p, size_t entries) {
   return DD_OK;
 }
 
+// Grows the fused path's per-(row, time tile) workspace; the per-row arrays
+// are allocated with it on first use.
+int ensure_tile_workspace(dd_plan *p, size_t entries) {
+  if (!p->d_rowsums) {
+    if (cudaMalloc(&p->d_rowsums, 2 * sizeof(int64_t) * p->ndm) != cudaSuccess ||
+        cudaMalloc(&p->d_rowcount, sizeof(int64_t) * p->ndm) != cudaSuccess ||
+        cudaMalloc(&p->d_rowoff, sizeof(int64_t) * p->ndm) != cudaSuccess) {
+      free_device(p->d_rowsums);
+      free_device(p->d_rowcount);
+      free_device(p->d_rowoff);
+      return DD_ERR_OOM;
+    }
+  }
+  if (entries <= p->tile_cap) return DD_OK;
+  free_device(p->d_tilemax);
+  free_device(p->d_tilecount);
+  p->tile_cap = 0;
+  if (cudaMalloc(&p->d_tilemax, entries * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&p->d_tilecount, entries * sizeof(int32_t)) != cudaSuccess) {
+    free_device(p->d_tilemax);
+    free_device(p->d_tilecount);
+    return DD_ERR_OOM;
+  }
+  p->tile_cap = entries;
+  return DD_OK;
+}
+
 // Reads and clears the sticky device status word (caller has synchronised).
 int take_device_status(dd_plan *p) {
   int32_t flag = 0;
@@ -84,6 +111,11 @@ void destroy_plan(dd_plan *p) {
   free_device(p->d_counts);
   free_device(p->d_offsets);
   free_device(p->d_total);
+  free_device(p->d_rowsums);
+  free_device(p->d_rowcount);
+  free_device(p->d_rowoff);
+  free_device(p->d_tilemax);
+  free_device(p->d_tilecount);
   free_device(p->d_block);
   free_device(p->d_out);
   free_device(p->d_cands);
@@ -230,7 +262,8 @@ extern "C" int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64
   cudaError_t err = cudaSuccess;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int n = (p->path == 0 && ddk::quad_supported(p, block, pitch_elems, nsamp_out))
-                    ? ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, s, &err)
+                    ? ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, nullptr,
+                                                  nullptr, s, &err)
                     : ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
@@ -255,6 +288,50 @@ extern "C" int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float n
   if (n < 0) return cuda_status(err);
   p->launches += n;
   n = ddk::launch_candidates(p, out, nsamp_out, nsigma, cands, capacity, s, &err);
+  if (n < 0) return cuda_status(err);
+  p->launches += n;
+  err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_status(err);
+  st = take_device_status(p);
+  if (st != DD_OK) return st;
+  p->stats_valid = true;
+  *count = *p->h_total;
+  return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
+}
+
+extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
+                      void *out, float nsigma, dd_candidate *cands, int64_t capacity,
+                      int64_t *count, void *stream, void *event) {
+  if (!p || !block || !out || !count || capacity < 0 || (capacity > 0 && !cands))
+    return DD_ERR_ARG;
+  if (!std::isfinite(nsigma)) return DD_ERR_ARG;
+  int64_t nsamp_out = 0;
+  int st = validate_execute(p, nsamp_in, pitch_elems, &nsamp_out);
+  if (st != DD_OK) return st;
+  *count = 0;
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaEvent_t ev = static_cast<cudaEvent_t>(event);
+  if (!(p->path == 0 && ddk::quad_supported(p, block, pitch_elems, nsamp_out))) {
+    // plain-load kernel: dedispersion, then the detection passes over out
+    st = dd_execute(p, block, nsamp_in, pitch_elems, out, stream);
+    if (st != DD_OK) return st;
+    if (ev && cudaEventRecord(ev, s) != cudaSuccess) return DD_ERR_CUDA;
+    return dd_detect(p, out, nsamp_out, nsigma, cands, capacity, count, stream);
+  }
+  st = ensure_tile_workspace(p, static_cast<size_t>(ddk::time_tiles(nsamp_out)) * p->ndm);
+  if (st != DD_OK) return st;
+  p->stats_valid = false;
+  cudaError_t err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
+  if (err != cudaSuccess) return cuda_status(err);
+  int n = ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, p->d_rowsums,
+                                      p->d_tilemax, s, &err);
+  if (n < 0) return cuda_status(err);
+  p->launches += n;
+  if (ev && cudaEventRecord(ev, s) != cudaSuccess) return DD_ERR_CUDA;
+  n = ddk::launch_tiled_detect(p, out, nsamp_out, nsigma, cands, capacity, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
   err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
@@ -329,9 +406,8 @@ extern "C" int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp
   }
   cudaError_t e = cudaMemcpyAsync(p->d_block, host_block, in_bytes, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) return cuda_status(e);
-  st = dd_execute(p, p->d_block, nsamp_in, pitch_elems, p->d_out, stream);
-  if (st != DD_OK) return st;
-  const int dst = dd_detect(p, p->d_out, nsamp_out, nsigma, p->d_cands, capacity, count, stream);
+  const int dst = dd_run(p, p->d_block, nsamp_in, pitch_elems, p->d_out, nsigma, p->d_cands,
+                         capacity, count, stream, nullptr);
   if (dst != DD_OK && dst != DD_ERR_OVERFLOW) return dst;
   const int64_t ncopy = *count < capacity ? *count : capacity;
   if (ncopy > 0) {

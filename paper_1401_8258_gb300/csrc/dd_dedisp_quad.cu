@@ -219,6 +219,8 @@ struct QuadArgs {
   int32_t rec_words;
   int32_t raw_stride;
   int32_t prow_words;
+  int64_t *rowsums;  // [ndm][2] += exact sum D, sum D^2 of the stored outputs (null: skip)
+  int32_t *tilemax;  // [ndm][gridDim.y] largest stored output of the CTA's time tile
   int32_t *status;  // plan's sticky device status word
   uint64_t timeout_ns;
   int32_t skip_copies;  // test hook: queue nothing, so the first wait runs out
@@ -429,6 +431,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
                     (kTmemCols & (kTmemCols - 1)) == 0,
                 "tensor-memory allocation must be a power of two in 32..512 columns");
   static_assert(kFlushQuads % kQuadsPerChunk == 0, "drain at chunk boundaries");
+  static_assert(kTimeGroups == 1, "a warp holds whole time tiles of its trials (tile maxima)");
   static_assert(kRawStages == kCopyAhead + 1 && kRecStages == kRowStages + kCopyAhead &&
                     8 * kRawStages <= kTmemSlot,
                 "pipeline depths");
@@ -592,7 +595,13 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
     }
     if (!aborted) {
       // final sums: stored part (if any) + the packed halves; pair j of
-      // trial i covers samples my_pair + 32 j and my_pair + 32 j + kHalf
+      // trial i covers samples my_pair + 32 j and my_pair + 32 j + kHalf.
+      // Per trial, this thread's exact sum, sum of squares and largest value
+      // of the samples it stores (for the statistics of the detection pass).
+      long long s1[ND_THR], s2[ND_THR];
+      int32_t mx[ND_THR];
+#pragma unroll
+      for (int i = 0; i < ND_THR; ++i) s1[i] = 0, s2[i] = 0, mx[i] = INT32_MIN;
 #pragma unroll
       for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
         uint32_t v[16];
@@ -611,9 +620,37 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
           int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
           const uint32_t w = acc[i][j];
           const int64_t t = t_cta + my_pair + 32 * j;
-          if (t < a.nsamp_out) orow[t] = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
-          if (t + kHalf < a.nsamp_out)
-            orow[t + kHalf] = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
+          const int32_t lo = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
+          const int32_t hi = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
+          if (t < a.nsamp_out) {
+            orow[t] = lo;
+            s1[i] += lo, s2[i] += static_cast<long long>(lo) * lo, mx[i] = max(mx[i], lo);
+          }
+          if (t + kHalf < a.nsamp_out) {
+            orow[t + kHalf] = hi;
+            s1[i] += hi, s2[i] += static_cast<long long>(hi) * hi, mx[i] = max(mx[i], hi);
+          }
+        }
+      }
+      if (a.rowsums) {
+        // one warp holds all kTimeTile samples of its trials: reduce over
+        // lanes; integer sums make the row totals independent of order
+#pragma unroll
+        for (int i = 0; i < ND_THR; ++i) {
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            s1[i] += __shfl_xor_sync(0xffffffffu, s1[i], o);
+            s2[i] += __shfl_xor_sync(0xffffffffu, s2[i], o);
+            mx[i] = max(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
+          }
+          const int d = tile * ND_CTA + dg * ND_THR + i;
+          if (lane == 0 && d < a.ndm) {
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d),
+                      static_cast<unsigned long long>(s1[i]));
+            atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d + 1),
+                      static_cast<unsigned long long>(s2[i]));
+            a.tilemax[static_cast<int64_t>(d) * gridDim.y + blockIdx.y] = mx[i];
+          }
         }
       }
     }
@@ -646,7 +683,8 @@ bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t 
 }
 
 int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                           void *out, cudaStream_t stream, cudaError_t *err) {
+                           void *out, int64_t *rowsums, int32_t *tilemax, cudaStream_t stream,
+                           cudaError_t *err) {
   const QuadDevice &q = *p->quad;
   QuadArgs a;
   a.block = static_cast<const uint8_t *>(block);
@@ -661,6 +699,8 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
   a.rec_words = q.tables.rec_words;
   a.raw_stride = q.tables.raw_stride;
   a.prow_words = q.tables.prow_words;
+  a.rowsums = rowsums;
+  a.tilemax = tilemax;
   a.status = p->d_error;
   a.timeout_ns = p->wait_timeout_ns;
   a.skip_copies = p->debug_skip_copies;

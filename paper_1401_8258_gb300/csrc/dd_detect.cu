@@ -14,6 +14,18 @@
 //                      in time order at their prefix offset.
 // The candidate list is therefore ordered by (dm_idx, t) and independent of
 // scheduling.  The predicate is evaluated identically in passes 2 and 4.
+//
+// Tiled variant (after the staged u8 kernel, which already added each row's
+// exact sums and recorded the largest output of each 512-sample time tile):
+//   1. dd_tile_count   one CTA per row: mean, rms and threshold from the sums
+//                      (the same finaliser as dd_stats_i32); counts the
+//                      candidates of the tiles whose maximum reaches the
+//                      threshold -- the only tiles that can hold one -- and
+//                      the row total;
+//   2. dd_scan         exclusive prefix over the row totals;
+//   3. dd_tile_write   rows with candidates write them tile by tile in time
+//                      order at their prefix offset.
+// Same statistics, predicate and (dm_idx, t) order as the passes above.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -85,9 +97,26 @@ __device__ float float_threshold(double mean, double sigma, double thr) {
   return order_float(hi);
 }
 
-// One CTA per row: S1 = sum D, S2 = sum D^2 exactly, then
-//   mean = S1 / N,  rms = sqrt((double)(N*S2 - S1^2)) / N,
-// and the row's integer candidate threshold.
+// Statistics of an integer row from its exact sums S1 = sum D, S2 = sum D^2
+// over N samples:
+//   mean = S1 / N,  rms = sqrt((double)(N*S2 - S1^2)) / N
+// (numerator exact in 128 bits, one rounding to double), and the row's
+// integer candidate threshold.
+__device__ dd_row_stats finish_i32(long long s1, unsigned __int128 s2, int64_t n, double thr) {
+  const __int128 S1 = s1;
+  const __int128 S2 = static_cast<__int128>(s2);
+  const __int128 num = static_cast<__int128>(n) * S2 - S1 * S1;  // >= 0
+  const double dn = __ll2double_rn(n);
+  dd_row_stats st;
+  st.mean = __ddiv_rn(__ll2double_rn(s1), dn);
+  st.sigma = __ddiv_rn(__dsqrt_rn(u128_to_double_rn(static_cast<unsigned __int128>(num))), dn);
+  st.any = st.sigma > 0.0;
+  st.ithr = st.any ? int_threshold(st.mean, st.sigma, thr) : static_cast<int64_t>(INT32_MAX) + 1;
+  st.fthr = INFINITY;
+  return st;
+}
+
+// One CTA per row: S1 = sum D, S2 = sum D^2 exactly, then finish_i32.
 __global__ void __launch_bounds__(kStatsThreads)
 dd_stats_i32(const int32_t *__restrict__ D, int64_t n, double thr,
              dd_row_stats *__restrict__ stats) {
@@ -119,19 +148,7 @@ dd_stats_i32(const int32_t *__restrict__ D, int64_t n, double thr,
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    const __int128 S1 = s_s1[0];
-    const __int128 S2 = static_cast<__int128>(s_s2[0]);
-    const __int128 num = static_cast<__int128>(n) * S2 - S1 * S1;  // >= 0
-    const double dn = __ll2double_rn(n);
-    dd_row_stats st;
-    st.mean = __ddiv_rn(__ll2double_rn(s_s1[0]), dn);
-    st.sigma = __ddiv_rn(__dsqrt_rn(u128_to_double_rn(static_cast<unsigned __int128>(num))), dn);
-    st.any = st.sigma > 0.0;
-    st.ithr = st.any ? int_threshold(st.mean, st.sigma, thr) : static_cast<int64_t>(INT32_MAX) + 1;
-    st.fthr = INFINITY;
-    stats[blockIdx.x] = st;
-  }
+  if (threadIdx.x == 0) stats[blockIdx.x] = finish_i32(s_s1[0], s_s2[0], n, thr);
 }
 
 // One CTA per row of f32 values: double sums of (x - K) with K the row's
@@ -286,6 +303,140 @@ dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__
   }
 }
 
+// ---- tiled detection after the staged kernel ----
+
+constexpr int kTileThreads = 256;
+constexpr int kTileSamp = ddk::kTileSamples;          // 512 samples per tile
+constexpr int kTilePer = kTileSamp / kTileThreads;   // 2 consecutive samples per thread
+constexpr int kTileList = 1024;                       // tiles examined per round
+
+// Exclusive prefix of v over the CTA (kTileThreads threads); *total gets the sum.
+__device__ __forceinline__ int block_exclusive(int v, int *total) {
+  __shared__ int s_warp[kTileThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  __syncthreads();  // s_warp free from any previous call
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  int before = 0, all = 0;
+#pragma unroll
+  for (int k = 0; k < kTileThreads / 32; ++k) {
+    const int x = s_warp[k];
+    before += k < w ? x : 0;
+    all += x;
+  }
+  *total = all;
+  return before + inc - v;
+}
+
+// One CTA per row d: statistics from rowsums[d], then the candidates of each
+// tile whose maximum reaches the threshold; tilecount[d][*] and rowcount[d].
+__global__ void __launch_bounds__(kTileThreads)
+dd_tile_count(const int32_t *__restrict__ D, int64_t n, int ntiles, double thr,
+              const long long *__restrict__ rowsums, const int32_t *__restrict__ tilemax,
+              dd_row_stats *__restrict__ stats, int32_t *__restrict__ tilecount,
+              int64_t *__restrict__ rowcount) {
+  __shared__ dd_row_stats s_st;
+  __shared__ int s_list[kTileList];
+  __shared__ int s_nlist;
+  const int d = blockIdx.x;
+  if (threadIdx.x == 0) {
+    const unsigned long long s2 = static_cast<unsigned long long>(rowsums[2 * d + 1]);
+    s_st = finish_i32(rowsums[2 * d], static_cast<unsigned __int128>(s2), n, thr);
+    stats[d] = s_st;
+  }
+  __syncthreads();
+  const dd_row_stats st = s_st;
+  const int32_t *row = D + static_cast<int64_t>(d) * n;
+  const int32_t *tmax = tilemax + static_cast<int64_t>(d) * ntiles;
+  int32_t *tcnt = tilecount + static_cast<int64_t>(d) * ntiles;
+  int64_t total = 0;  // thread 0
+  for (int base = 0; base < ntiles; base += kTileList) {
+    if (threadIdx.x == 0) s_nlist = 0;
+    __syncthreads();
+    for (int k = threadIdx.x; k < kTileList && base + k < ntiles; k += kTileThreads) {
+      const int tt = base + k;
+      if (st.any && static_cast<int64_t>(tmax[tt]) >= st.ithr) {
+        s_list[atomicAdd(&s_nlist, 1)] = tt;  // order irrelevant: counts go by tile
+      } else {
+        tcnt[tt] = 0;
+      }
+    }
+    __syncthreads();
+    const int nl = s_nlist;
+    for (int k = 0; k < nl; ++k) {
+      const int tt = s_list[k];
+      const int64_t t0 = static_cast<int64_t>(tt) * kTileSamp + threadIdx.x * kTilePer;
+      int mine = 0;
+#pragma unroll
+      for (int u = 0; u < kTilePer; ++u)
+        mine += (t0 + u < n && is_candidate(row[t0 + u], st)) ? 1 : 0;
+      int tile_total = 0;
+      block_exclusive(mine, &tile_total);
+      if (threadIdx.x == 0) {
+        tcnt[tt] = tile_total;
+        total += tile_total;
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) rowcount[d] = total;
+}
+
+// One CTA per row with candidates: tiles in time order, each tile's
+// candidates in time order, at rowoff[d] + (candidates of earlier tiles).
+__global__ void __launch_bounds__(kTileThreads)
+dd_tile_write(const int32_t *__restrict__ D, int64_t n, int ntiles,
+              const dd_row_stats *__restrict__ stats, const int32_t *__restrict__ tilecount,
+              const int64_t *__restrict__ rowcount, const int64_t *__restrict__ rowoff,
+              dd_candidate *__restrict__ cands, int64_t capacity) {
+  const int d = blockIdx.x;
+  if (rowcount[d] == 0) return;  // uniform across the CTA
+  int64_t run = rowoff[d];
+  if (run >= capacity) return;
+  const dd_row_stats st = stats[d];
+  const int32_t *row = D + static_cast<int64_t>(d) * n;
+  const int32_t *tcnt = tilecount + static_cast<int64_t>(d) * ntiles;
+  __shared__ int s_cnt[kTileList];
+  for (int base = 0; base < ntiles && run < capacity; base += kTileList) {
+    __syncthreads();  // s_cnt free from the previous round
+    for (int k = threadIdx.x; k < kTileList && base + k < ntiles; k += kTileThreads)
+      s_cnt[k] = tcnt[base + k];
+    __syncthreads();
+    const int lim = ntiles - base < kTileList ? ntiles - base : kTileList;
+    for (int k = 0; k < lim && run < capacity; ++k) {
+      if (s_cnt[k] == 0) continue;  // same in every thread
+      const int64_t t0 = static_cast<int64_t>(base + k) * kTileSamp + threadIdx.x * kTilePer;
+      unsigned mask = 0;
+#pragma unroll
+      for (int u = 0; u < kTilePer; ++u)
+        if (t0 + u < n && is_candidate(row[t0 + u], st)) mask |= 1u << u;
+      int tile_total = 0;
+      int64_t idx = run + block_exclusive(__popc(mask), &tile_total);
+      while (mask) {
+        const int u = __ffs(mask) - 1;
+        mask &= mask - 1;
+        if (idx < capacity) {
+          const double v = static_cast<double>(row[t0 + u]);
+          dd_candidate cd;
+          cd.dm_idx = d;
+          cd.t = static_cast<int32_t>(t0 + u);
+          cd.value = static_cast<float>(v);
+          cd.snr = static_cast<float>(snr_of(v, st.mean, st.sigma));
+          cands[idx] = cd;
+        }
+        ++idx;
+      }
+      run += tile_total;
+    }
+  }
+}
+
 }  // namespace
 
 namespace ddk {
@@ -330,6 +481,27 @@ int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsig
       dd_write<float><<<grid, kCountThreads, 0, stream>>>(
           static_cast<const float *>(out), nsamp_out, nchunks, p->d_stats, p->d_counts,
           p->d_offsets, cands, capacity);
+    ++n;
+  }
+  *err = cudaGetLastError();
+  return *err == cudaSuccess ? n : -1;
+}
+
+int launch_tiled_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                        dd_candidate *cands, int64_t capacity, cudaStream_t stream,
+                        cudaError_t *err) {
+  const int ntiles = static_cast<int>(time_tiles(nsamp_out));
+  const int32_t *D = static_cast<const int32_t *>(out);
+  dd_tile_count<<<p->ndm, kTileThreads, 0, stream>>>(
+      D, nsamp_out, ntiles, static_cast<double>(nsigma),
+      reinterpret_cast<const long long *>(p->d_rowsums), p->d_tilemax, p->d_stats,
+      p->d_tilecount, p->d_rowcount);
+  dd_scan<<<1, kScanThreads, 0, stream>>>(p->d_rowcount, p->ndm, p->d_rowoff, p->d_total);
+  int n = 2;
+  if (capacity > 0) {
+    dd_tile_write<<<p->ndm, kTileThreads, 0, stream>>>(D, nsamp_out, ntiles, p->d_stats,
+                                                       p->d_tilecount, p->d_rowcount,
+                                                       p->d_rowoff, cands, capacity);
     ++n;
   }
   *err = cudaGetLastError();

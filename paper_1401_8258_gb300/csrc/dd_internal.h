@@ -55,6 +55,14 @@ struct dd_plan {
   std::vector<double> h_mean, h_sigma;
   bool stats_valid = false;
 
+  // workspace of the fused path (dd_run with the staged kernel)
+  int64_t *d_rowsums = nullptr;     // [ndm][2] exact S1, S2 from the dedispersion kernel
+  int64_t *d_rowcount = nullptr;    // [ndm] candidates per row
+  int64_t *d_rowoff = nullptr;      // [ndm] exclusive prefix of d_rowcount
+  int32_t *d_tilemax = nullptr;     // [ndm * ntiles] largest output of each time tile
+  int32_t *d_tilecount = nullptr;   // [ndm * ntiles] candidates per time tile
+  size_t tile_cap = 0;              // entries allocated in d_tilemax / d_tilecount
+
   // buffers owned for dd_process_host
   void *d_block = nullptr;
   size_t d_block_bytes = 0;
@@ -84,8 +92,15 @@ int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64
 // Staged quad kernel (u8): needs the plan's quad tables, a 16-byte aligned
 // block, a pitch that is a multiple of 16 bytes and at most 65535 time tiles.
 bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
+// With rowsums / tilemax non-null it also adds each row's exact sums
+// (rowsums[2d] += sum D, rowsums[2d+1] += sum D^2; the caller zeroes them
+// first) and writes the largest output of every (row, kTileSamples-sample
+// time tile) to tilemax[d * ntiles + tile].
 int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                           void *out, cudaStream_t stream, cudaError_t *err);
+                           void *out, int64_t *rowsums, int32_t *tilemax, cudaStream_t stream,
+                           cudaError_t *err);
+constexpr int kTileSamples = ddq::kTimeTile;
+inline int64_t time_tiles(int64_t nsamp_out) { return (nsamp_out + kTileSamples - 1) / kTileSamples; }
 
 // Detection passes over out[ndm][nsamp_out]; see dd_detect in dd.h.
 constexpr int kDetectChunk = 4096;  // samples per (row, chunk) work unit
@@ -94,5 +109,11 @@ int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
 int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
                       dd_candidate *cands, int64_t capacity, cudaStream_t stream,
                       cudaError_t *err);
+// Detection from the sums and tile maxima of the staged kernel (int32 rows):
+// same statistics, thresholds and candidate list as launch_stats +
+// launch_candidates, reading only the tiles that can hold a candidate.
+int launch_tiled_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                        dd_candidate *cands, int64_t capacity, cudaStream_t stream,
+                        cudaError_t *err);
 
 }  // namespace ddk

@@ -3,8 +3,10 @@
 //
 // Each probe runs, in every thread, eight independent dependency chains of
 // one instruction form, so that issue rate rather than latency bounds it.
-// Cycles are read with clock64() inside the kernel, so the result in
-// operations per clock per SM does not depend on the clock the GPU ran at.
+// Cycles are read with clock64() inside the kernel (a per-SM counter), and
+// each SM's busy span runs from the earliest start to the latest end of the
+// blocks it ran, so the result in operations per clock per SM does not depend
+// on the clock the GPU ran at nor on blocks starting at different times.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -57,6 +59,13 @@ constexpr int ops_per_chain() {
   return (KIND == DD_PEAK_IADD3) ? 2 : (KIND == DD_PEAK_FADD2 ? 2 : 1);
 }
 
+__device__ __forceinline__ uint32_t sm_id() {
+  uint32_t id;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(id));
+  return id;
+}
+
+// cycles[3 * block .. +3) = {SM id, start, end}
 template <int KIND>
 __global__ void __launch_bounds__(kThreads) peak_kernel(uint32_t *sink, long long *cycles) {
   uint32_t a[kChains];
@@ -85,7 +94,11 @@ __global__ void __launch_bounds__(kThreads) peak_kernel(uint32_t *sink, long lon
 #pragma unroll
   for (int i = 0; i < kChains; ++i) x ^= a[i];
   if (x == 0x9e3779b9u) sink[blockIdx.x] = x;  // keeps the chains live
-  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  if (threadIdx.x == 0) {
+    cycles[3 * blockIdx.x] = sm_id();
+    cycles[3 * blockIdx.x + 1] = t0;
+    cycles[3 * blockIdx.x + 2] = t1;
+  }
 }
 
 template <int KIND>
@@ -100,7 +113,7 @@ int run(int device, double *ops_per_s, double *ops_per_clk_sm) {
   uint32_t *sink = nullptr;
   long long *cyc = nullptr;
   if (cudaMalloc(&sink, blocks * sizeof(uint32_t)) != cudaSuccess) return DD_PEAK_ERR;
-  if (cudaMalloc(&cyc, blocks * sizeof(long long)) != cudaSuccess) {
+  if (cudaMalloc(&cyc, 3 * blocks * sizeof(long long)) != cudaSuccess) {
     cudaFree(sink);
     return DD_PEAK_ERR;
   }
@@ -115,11 +128,23 @@ int run(int device, double *ops_per_s, double *ops_per_clk_sm) {
   cudaError_t err = cudaEventSynchronize(e1);
   float ms = 0.f;
   cudaEventElapsedTime(&ms, e0, e1);
-  long long *h = new long long[blocks];
-  cudaMemcpy(h, cyc, blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+  // busy span of each SM over the last launch: earliest start to latest end
+  long long *h = new long long[3 * blocks];
+  cudaMemcpy(h, cyc, 3 * blocks * sizeof(long long), cudaMemcpyDeviceToHost);
+  long long *lo = new long long[sms], *hi = new long long[sms];
+  for (int i = 0; i < sms; ++i) lo[i] = -1, hi[i] = -1;
+  for (int b = 0; b < blocks; ++b) {
+    const long long id = h[3 * b], t0 = h[3 * b + 1], t1 = h[3 * b + 2];
+    if (id < 0 || id >= sms) continue;
+    if (lo[id] < 0 || t0 < lo[id]) lo[id] = t0;
+    if (hi[id] < 0 || t1 > hi[id]) hi[id] = t1;
+  }
   long long mx = 0;
-  for (int i = 0; i < blocks; ++i) mx = h[i] > mx ? h[i] : mx;
+  for (int i = 0; i < sms; ++i)
+    if (lo[i] >= 0 && hi[i] - lo[i] > mx) mx = hi[i] - lo[i];
   delete[] h;
+  delete[] lo;
+  delete[] hi;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(sink);

@@ -1,0 +1,163 @@
+"""GPU: dd_run (dedispersion + detection in one call) against the separate
+dd_execute + dd_detect calls, which the parity tests pin to the oracle, and
+directly against the oracle on reduced shapes.
+
+With the staged u8 kernel, dd_run takes each row's sums and tile maxima from
+the dedispersion kernel and reads the output only in tiles that can hold a
+candidate; everything it returns must still be bit-identical.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1401_8258_gb300 as dd
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    dd.build()
+    oracle.build()
+
+
+def both_paths(wl, block, nsigma, capacity=1 << 16, nsamp_in=None, expect_staged=True):
+    """(separate calls, dd_run) results for the same device block."""
+    nchan, pitch = block.shape
+    nsamp_in = pitch if nsamp_in is None else nsamp_in
+    dblock = torch.from_numpy(np.ascontiguousarray(block)).to(DEV)
+    res = []
+    with dd.Plan(nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, wl.dtype) as plan:
+        info = dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)
+        assert bool(info["staged"]) == expect_staged, info
+        n_out = plan.nsamp_out(nsamp_in)
+        cap = max(capacity, 1)
+        for fused in (False, True):
+            out = torch.full((wl.ndm, n_out), -7, dtype=plan.out_torch_dtype, device=DEV)
+            cands = torch.zeros((cap, 16), dtype=torch.uint8, device=DEV)
+            if fused:
+                st, total = dd.dd_run(plan.handle, dblock, nsamp_in, pitch, out, nsigma,
+                                      cands if capacity else None, capacity)
+            else:
+                dd.dd_execute(plan.handle, dblock, nsamp_in, pitch, out)
+                st, total = dd.dd_detect(plan.handle, out, n_out, nsigma,
+                                         cands if capacity else None, capacity)
+            mean, sigma = plan.stats()
+            k = min(total, capacity)
+            c = cands[:k].cpu().numpy().view(dd.CANDIDATE_DTYPE).reshape(-1)
+            res.append({"st": st, "total": total, "out": out, "cands": c, "mean": mean,
+                        "sigma": sigma})
+    return res
+
+
+def assert_same(a, b):
+    assert a["st"] == b["st"] and a["total"] == b["total"]
+    assert torch.equal(a["out"], b["out"])
+    assert np.array_equal(a["cands"], b["cands"])
+    assert np.array_equal(a["mean"], b["mean"]) and np.array_equal(a["sigma"], b["sigma"])
+
+
+def test_run_full_block_u8_full_size_matches_separate_calls():
+    wl = synth.workload("full_block_u8")
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, pulses = synth.make_block(wl, seed=1, delays=delays)
+    sep, run = both_paths(wl, block, 6.0, capacity=1 << 20)
+    assert_same(sep, run)
+    assert run["total"] > 0
+    for p in pulses:
+        hit = (run["cands"]["dm_idx"] == p.dm_idx) & (run["cands"]["t"] >= p.t0) & \
+            (run["cands"]["t"] < p.t0 + p.width)
+        assert hit.any(), p
+
+
+CASES = [
+    # (nchan, ndm, samples past maxshift, pitch pad, nsigma)
+    (1024, 128, 3000, 0, 6.0),
+    (1021, 100, 1700, 16, 3.0),     # ragged channels, pitch padding, ragged last tile
+    (512, 70, 513, 0, -1.0),        # every tile holds candidates
+    (256, 64, 900, 32, 1e9),        # none
+    (68, 64, 600, 0, 2.5),          # last chunk holds one quad
+]
+
+
+@pytest.mark.parametrize("nchan,ndm,extra,pad,nsigma", CASES)
+def test_run_matches_oracle_and_separate_calls(nchan, ndm, extra, pad, nsigma):
+    base = synth.workload("full_block_u8")
+    wl = synth.scaled(base, nchan=nchan, ndm=ndm)
+    wl.chan_width_mhz = base.chan_width_mhz
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    wl.nsamp = mx + extra
+    block, _ = synth.make_block(wl, seed=9, delays=delays)
+    pitch = (wl.nsamp + 15) // 16 * 16 + pad
+    padded = np.zeros((nchan, pitch), dtype=np.uint8)
+    padded[:, :wl.nsamp] = block
+    padded[:, wl.nsamp:] = 0xEE  # row padding must never reach a stored output
+    sep, run = both_paths(wl, padded, nsigma, capacity=1 << 20, nsamp_in=wl.nsamp)
+    assert_same(sep, run)
+    ref = oracle.dedisperse(block, delays)
+    assert np.array_equal(run["out"].cpu().numpy(), ref)
+    mean, sigma = oracle.stats(ref)
+    assert np.array_equal(run["mean"], mean) and np.array_equal(run["sigma"], sigma)
+    cands, total = oracle.detect(ref, mean, sigma, nsigma)
+    assert run["total"] == total
+    assert np.array_equal(run["cands"], cands)
+
+
+def narrow(nchan, nsamp, ndm):
+    """The top nchan channels of the 400-416 MHz band (staged-kernel geometry)."""
+    base = synth.workload("full_block_u8")
+    wl = synth.scaled(base, nchan=nchan, nsamp=nsamp, ndm=ndm)
+    wl.chan_width_mhz = base.chan_width_mhz
+    return wl
+
+
+def test_run_capacity_overflow_keeps_first_candidates_in_order():
+    wl = narrow(64, 8000, 32)
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, _ = synth.make_block(wl, seed=4, delays=delays)
+    sep, run = both_paths(wl, block, 1.0, capacity=100)
+    assert_same(sep, run)
+    assert run["st"] == dd.DD_ERR_OVERFLOW and run["total"] > 100
+    _, full = both_paths(wl, block, 1.0, capacity=1 << 20)
+    assert np.array_equal(run["cands"], full["cands"][:100])
+    _, none = both_paths(wl, block, 1.0, capacity=0)
+    assert none["total"] == full["total"] and none["st"] == dd.DD_ERR_OVERFLOW
+
+
+def test_run_constant_rows_have_no_candidates():
+    wl = narrow(128, 6000, 64)
+    block = np.full((wl.nchan, wl.nsamp), 77, dtype=np.uint8)
+    sep, run = both_paths(wl, block, 0.0)
+    assert_same(sep, run)
+    assert run["total"] == 0 and np.all(run["sigma"] == 0.0)
+
+
+def test_run_float_plan_takes_the_plain_kernel_with_identical_results():
+    wl = synth.workload("single_beam_f32")
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, _ = synth.make_block(wl, seed=2, delays=delays)
+    sep, run = both_paths(wl, block, 5.0, expect_staged=False)
+    assert_same(sep, run)
+
+
+def test_run_records_the_phase_event():
+    wl = narrow(256, 9000, 128)
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, _ = synth.make_block(wl, seed=3, delays=delays)
+    dblock = torch.from_numpy(block).to(DEV)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as plan:
+        out = torch.empty((wl.ndm, plan.nsamp_out(wl.nsamp)), dtype=torch.int32, device=DEV)
+        cands = torch.empty((1 << 12, 16), dtype=torch.uint8, device=DEV)
+        start, mid = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        mid.record()  # creates the event
+        start.record()
+        dd.dd_run(plan.handle, dblock, wl.nsamp, wl.nsamp, out, 6.0, cands, 1 << 12,
+                  torch.cuda.current_stream(), mid)
+        end = torch.cuda.Event(enable_timing=True)
+        end.record()
+        torch.cuda.synchronize()
+        assert 0.0 < start.elapsed_time(mid) <= start.elapsed_time(end)
