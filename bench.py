@@ -143,8 +143,11 @@ def kernel_source_sha() -> str:
     """Hash of the dedispersion kernels' code (comments and blank lines
     dropped), to tell whether a recorded ncu traffic figure still applies."""
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1401_8258_gb300", "csrc", "dd_dedisp*.cu")) +
-                    glob.glob(os.path.join(ROOT, "paper_1401_8258_gb300", "csrc", "dd_quad*"))):
+    csrc = os.path.join(ROOT, "paper_1401_8258_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "dd_dedisp*.cu")) +
+                    glob.glob(os.path.join(csrc, "dd_quad*")) +
+                    glob.glob(os.path.join(csrc, "dd_octet*")) +
+                    glob.glob(os.path.join(csrc, "dd_device.cuh"))):
         with open(f) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].strip()

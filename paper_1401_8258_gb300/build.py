@@ -33,7 +33,8 @@ def sources() -> list[str]:
 
 
 def _inputs() -> list[str]:
-    return sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__]
+    return (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh")) +
+            glob.glob(os.path.join(INCLUDE, "*.h")) + [__file__])
 
 
 def up_to_date() -> bool:

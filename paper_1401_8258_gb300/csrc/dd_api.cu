@@ -105,6 +105,12 @@ void destroy_plan(dd_plan *p) {
     delete p->quad;
     p->quad = nullptr;
   }
+  if (p->octet) {
+    free_device(p->octet->d_recs);
+    free_device(p->octet->d_raw_meta);
+    delete p->octet;
+    p->octet = nullptr;
+  }
   free_device(p->d_delays);
   free_device(p->d_error);
   free_device(p->d_stats);
@@ -141,6 +147,28 @@ int setup_quad(dd_plan *p) {
   if (e == cudaSuccess)
     e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
   p->quad = q;  // freed with the plan on error
+  return cuda_status(e);
+}
+
+// Plan-time tables of the staged f16/f32 kernel: 64 DM trials per CTA where
+// the delay patterns allow, else 32; none if neither fits (plain-load kernel).
+int setup_octet(dd_plan *p) {
+  const int esize = p->dtype == DD_F16 ? 2 : 4;
+  ddo::Tables t;
+  int rc = ddo::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddo::kNdThr, esize, &t);
+  if (rc != 0) rc = ddo::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddo::kNdThr / 2, esize, &t);
+  if (rc != 0) return DD_OK;
+  OctetDevice *q = new (std::nothrow) OctetDevice();
+  if (!q) return DD_ERR_OOM;
+  q->tables = std::move(t);
+  const size_t rb = q->tables.recs.size() * sizeof(int32_t);
+  const size_t mb = q->tables.raw_meta.size() * sizeof(int32_t);
+  cudaError_t e = cudaMalloc(&q->d_recs, rb);
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_raw_meta, mb);
+  if (e == cudaSuccess) e = cudaMemcpy(q->d_recs, q->tables.recs.data(), rb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
+  p->octet = q;  // freed with the plan on error
   return cuda_status(e);
 }
 
@@ -207,12 +235,10 @@ extern "C" int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz,
     destroy_plan(p);
     return cuda_status(e);
   }
-  if (in_dtype == DD_U8) {
-    st = setup_quad(p);
-    if (st != DD_OK) {
-      destroy_plan(p);
-      return st;
-    }
+  st = in_dtype == DD_U8 ? setup_quad(p) : setup_octet(p);
+  if (st != DD_OK) {
+    destroy_plan(p);
+    return st;
   }
   *out = p;
   return DD_OK;
@@ -261,10 +287,14 @@ extern "C" int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64
   if (!scope.ok()) return DD_ERR_CUDA;
   cudaError_t err = cudaSuccess;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const int n = (p->path == 0 && ddk::quad_supported(p, block, pitch_elems, nsamp_out))
-                    ? ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, nullptr,
-                                                  nullptr, s, &err)
-                    : ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, s, &err);
+  int n;
+  if (p->path == 0 && ddk::quad_supported(p, block, pitch_elems, nsamp_out))
+    n = ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, nullptr, nullptr, s,
+                                    &err);
+  else if (p->path == 0 && ddk::octet_supported(p, block, pitch_elems, nsamp_out))
+    n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, s, &err);
+  else
+    n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
   return DD_OK;
@@ -440,9 +470,13 @@ extern "C" int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies) {
 extern "C" int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems,
                                    int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes) {
   if (!p || !staged) return DD_ERR_ARG;
-  const bool q = p->path == 0 && block && ddk::quad_supported(p, block, pitch_elems, p->maxshift + 1);
+  const bool q = p->path == 0 && block &&
+                 (ddk::quad_supported(p, block, pitch_elems, p->maxshift + 1) ||
+                  ddk::octet_supported(p, block, pitch_elems, p->maxshift + 1));
   *staged = q ? 1 : 0;
-  if (dms_per_cta) *dms_per_cta = p->quad ? p->quad->tables.nd_cta : 0;
-  if (smem_bytes) *smem_bytes = p->quad ? p->quad->tables.smem_bytes : 0;
+  const int nd = p->quad ? p->quad->tables.nd_cta : (p->octet ? p->octet->tables.nd_cta : 0);
+  const int sm = p->quad ? p->quad->tables.smem_bytes : (p->octet ? p->octet->tables.smem_bytes : 0);
+  if (dms_per_cta) *dms_per_cta = nd;
+  if (smem_bytes) *smem_bytes = sm;
   return DD_OK;
 }

@@ -8,11 +8,19 @@
 #include <vector>
 
 #include "dd.h"
+#include "dd_octet.h"
 #include "dd_quad.h"
 
 // Device copies of the staged quad kernel's plan-time tables.
 struct QuadDevice {
   ddq::Tables tables;
+  int32_t *d_recs = nullptr;
+  int32_t *d_raw_meta = nullptr;
+};
+
+// Device copies of the staged octet kernel's plan-time tables.
+struct OctetDevice {
+  ddo::Tables tables;
   int32_t *d_recs = nullptr;
   int32_t *d_raw_meta = nullptr;
 };
@@ -72,6 +80,7 @@ struct dd_plan {
   size_t d_cands_cap = 0;
 
   QuadDevice *quad = nullptr;       // staged u8 kernel tables (null: not applicable)
+  OctetDevice *octet = nullptr;     // staged f16/f32 kernel tables (null: not applicable)
   int32_t path = 0;                 // 0 = automatic, 1 = plain-load kernel only
   uint64_t wait_timeout_ns = 2000000000ull;  // bound on every device-side wait
   int32_t debug_skip_copies = 0;    // fault injection: staged kernel queues no copies
@@ -100,6 +109,12 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
                            void *out, int64_t *rowsums, int32_t *tilemax, cudaStream_t stream,
                            cudaError_t *err);
 constexpr int kTileSamples = ddq::kTimeTile;
+// Staged octet kernel (f16 / f32): needs the plan's octet tables, a 16-byte
+// aligned block, a pitch of a whole number of 16-byte units and at most
+// 65535 time tiles.
+bool octet_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
+int launch_dedisperse_octet(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
+                            void *out, cudaStream_t stream, cudaError_t *err);
 inline int64_t time_tiles(int64_t nsamp_out) { return (nsamp_out + kTileSamples - 1) / kTileSamples; }
 
 // Detection passes over out[ndm][nsamp_out]; see dd_detect in dd.h.

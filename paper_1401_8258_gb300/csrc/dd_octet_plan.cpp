@@ -1,0 +1,217 @@
+// dd_octet_plan.cpp -- plan-time tables of the staged octet kernel
+// (dd_dedisp_octet.cu) for f16 and f32 input.
+//
+// The kernel adds eight channels per shared-memory word: for each group of
+// eight adjacent channels ("octet") and each DM trial of the CTA's tile it
+// reads a row whose word i holds the sum of the eight channels' samples that
+// the trial adds at output time i.  Within an octet the delays of channels
+// 1..7 relative to channel 0 take only a few distinct values over a tile of
+// trials (differences of two rounded delays, Sec. 2.1.1), so one row per
+// distinct relative pattern serves every trial of the tile that has it.
+//
+// Everything here is integer bookkeeping on the plan's delay table; no part
+// of the dedispersion sum happens on the host.
+#include <algorithm>
+#include <array>
+#include <cstdint>
+#include <vector>
+
+#include "dd_octet.h"
+
+namespace {
+
+inline int32_t round_up(int32_t v, int32_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+namespace ddo {
+
+int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, int esize,
+                 Tables *tb) {
+  if (esize != 2 && esize != 4) return 1;
+  const int nd_cta = kDmGroups * nd_thr;
+  const int align = 16 / esize;  // elements per 16 bytes
+  Tables t;
+  t.nd_thr = nd_thr;
+  t.nd_cta = nd_cta;
+  t.esize = esize;
+  t.opc = esize == 4 ? 1 : 2;
+  t.ntiles = (ndm + nd_cta - 1) / nd_cta;
+  t.noctets = (nchan + kGroup - 1) / kGroup;
+  t.nchan_pad = t.noctets * kGroup;
+  t.nchunks = (t.noctets + t.opc - 1) / t.opc;
+  t.rec_words = rec_words(nd_cta);
+  t.recs.assign(static_cast<size_t>(t.ntiles) * t.nchunks * t.rec_words, 0);
+  t.raw_meta.assign(static_cast<size_t>(t.ntiles) * t.nchan_pad * 2, 0);
+
+  // delay of (channel c, i-th trial of tile); padded trials reuse the last
+  auto delay = [&](int tile, int c, int i) -> int32_t {
+    const int d = std::min(tile * nd_cta + i, ndm - 1);
+    return delays[static_cast<int64_t>(c) * ndm + d];
+  };
+
+  struct Octet {
+    int32_t row_off, L, npat;
+    int32_t shift[kMaxPatterns][kGroup];  // e_k(p) - emin[k]
+    bool pad[kGroup];
+    int32_t raw_off[kGroup];               // element offset of time b + emin[k] in its window
+  };
+  std::vector<std::vector<Octet>> chunk_octets(static_cast<size_t>(t.ntiles) * t.nchunks);
+  int32_t raw_stride = align;
+  int32_t prow_words = 4;
+  for (int tile = 0; tile < t.ntiles; ++tile) {
+    std::vector<int32_t> start(t.nchan_pad, 0), need(t.nchan_pad, 0);
+    for (int ch = 0; ch < t.nchunks; ++ch) {
+      int32_t *rec = &t.recs[(static_cast<size_t>(tile) * t.nchunks + ch) * t.rec_words];
+      int32_t *A = rec + kRecHeader;
+      std::vector<Octet> &octs = chunk_octets[static_cast<size_t>(tile) * t.nchunks + ch];
+      int row_words = 0;
+      const int o_lo = ch * t.opc;
+      const int no = std::min(t.opc, t.noctets - o_lo);
+      for (int o = 0; o < no; ++o) {
+        const int c0 = kGroup * (o_lo + o);
+        const int nreal = std::min(kGroup, nchan - c0);
+        // distinct relative patterns of the real channels
+        std::vector<std::array<int32_t, kGroup>> pats;
+        std::vector<int> pid(nd_cta);
+        int32_t b = INT32_MAX, bmax = INT32_MIN;
+        for (int i = 0; i < nd_cta; ++i) {
+          const int32_t d0 = delay(tile, c0, i);
+          b = std::min(b, d0);
+          bmax = std::max(bmax, d0);
+          std::array<int32_t, kGroup> rel{};
+          for (int k = 1; k < nreal; ++k) rel[k] = delay(tile, c0 + k, i) - d0;
+          auto it = std::find(pats.begin(), pats.end(), rel);
+          pid[i] = static_cast<int>(it - pats.begin());
+          if (it == pats.end()) pats.push_back(rel);
+        }
+        if (static_cast<int>(pats.size()) > kMaxPatterns) return 1;
+        Octet O;
+        O.row_off = row_words;
+        O.npat = static_cast<int32_t>(pats.size());
+        O.L = round_up(kTimeTile + bmax - b, 4);
+        for (int k = 0; k < kGroup; ++k) {
+          const int c = c0 + k;
+          O.pad[k] = k >= nreal;
+          int32_t emin = INT32_MAX, emax = INT32_MIN;
+          for (int p = 0; p < O.npat; ++p) {
+            emin = std::min(emin, pats[p][k]);
+            emax = std::max(emax, pats[p][k]);
+          }
+          if (emax - emin > kMaxShift) return 1;
+          for (int p = 0; p < O.npat; ++p) O.shift[p][k] = pats[p][k] - emin;
+          if (!O.pad[k]) {
+            // window: times b + emin .. b + emax + L - 1
+            start[c] = (b + emin) / align * align;
+            O.raw_off[k] = b + emin - start[c];
+            need[c] = O.raw_off[k] + (emax - emin) + O.L;
+            raw_stride = std::max(raw_stride, round_up(need[c], align));
+          } else {
+            O.raw_off[k] = 0;
+          }
+        }
+        for (int i = 0; i < nd_cta; ++i)
+          A[o * nd_cta + i] = row_words + pid[i] * O.L + delay(tile, c0, i) - b;
+        row_words += O.npat * O.L;
+        octs.push_back(O);
+      }
+      rec[2] = no;
+      prow_words = std::max(prow_words, row_words);
+    }
+    for (int c = 0; c < t.nchan_pad; ++c) {
+      int32_t *m = &t.raw_meta[(static_cast<size_t>(tile) * t.nchan_pad + c) * 2];
+      m[0] = start[c];
+      m[1] = c < nchan ? need[c] : 0;
+    }
+  }
+  // raw-buffer element offsets must fit 16 bits (zero area first)
+  const int64_t raw_elems = static_cast<int64_t>(kGroup) * t.opc * raw_stride;
+  if (kZeroElems + raw_elems + 32 + kMaxShift >= 0xffff) return 1;
+  constexpr int kWarps = kThreads / 32;
+  for (size_t rc = 0; rc < chunk_octets.size(); ++rc) {
+    int32_t *rec = &t.recs[rc * t.rec_words];
+    std::vector<std::array<int32_t, kUnitWords>> list;
+    for (size_t o = 0; o < chunk_octets[rc].size(); ++o) {
+      const Octet &O = chunk_octets[rc][o];
+      for (int first = 0; first < O.L; first += 32) {
+        std::array<int32_t, kUnitWords> u{};
+        u[0] = (O.row_off + first) | (std::min(32, O.L - first) << 20);
+        u[1] = O.npat | (O.L << 8);
+        for (int k = 0; k < kGroup; ++k) {
+          // element offsets from the start of the zero area; the raw buffer
+          // follows it (kZeroElems elements)
+          const uint32_t e =
+              O.pad[k] ? 0u
+                       : static_cast<uint32_t>(kZeroElems +
+                                               (kGroup * static_cast<int>(o) + k) * raw_stride +
+                                               O.raw_off[k] + first);
+          u[2 + k / 2] |= static_cast<int32_t>(e << (16 * (k & 1)));
+        }
+        for (int p = 0; p < O.npat; ++p) {
+          uint32_t code = 0;
+          for (int k = 0; k < kGroup; ++k)
+            code |= static_cast<uint32_t>(O.pad[k] ? 0 : O.shift[p][k]) << (2 * k);
+          u[6 + p / 2] |= static_cast<int32_t>(code << (16 * (p & 1)));
+        }
+        list.push_back(u);
+      }
+    }
+    if (static_cast<int>(list.size()) > kMaxUnits) return 1;
+    // balance: costliest unit first onto the least loaded warp
+    std::vector<int> order(list.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
+    auto cost = [&](int i) { return 1 + (list[i][1] & 0xff); };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    std::vector<int> load(kWarps, 0);
+    std::vector<std::vector<int>> per_warp(kWarps);
+    for (int i : order) {
+      const int w = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+      load[w] += cost(i);
+      per_warp[w].push_back(i);
+    }
+    int32_t *units = rec + units_offset(nd_cta);
+    uint16_t *starts = reinterpret_cast<uint16_t *>(rec + warp_start_offset(nd_cta));
+    int n = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      starts[w] = static_cast<uint16_t>(n);
+      for (int i : per_warp[w]) {
+        for (int j = 0; j < kUnitWords; ++j) units[n * kUnitWords + j] = list[i][j];
+        ++n;
+      }
+    }
+    starts[kWarps] = static_cast<uint16_t>(n);
+    rec[3] = n;
+  }
+  t.raw_stride = raw_stride;
+  t.prow_words = prow_words;
+  t.smem_bytes = smem_bytes(t);
+  if (t.smem_bytes > kMaxSmem) return 1;
+  *tb = std::move(t);
+  return 0;
+}
+
+}  // namespace ddo
+
+// Host-side access to the tables for the CPU tests (not part of dd.h).
+// info[0..11) = {ok, nd_cta, ntiles, nchunks, nchan_pad, rec_words, raw_stride,
+// prow_words, smem_bytes, opc, esize}; recs / raw_meta may be NULL.
+extern "C" int ddi_octet_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int32_t nd_thr,
+                                int32_t esize, int32_t *info, int32_t *recs, int32_t *raw_meta) {
+  ddo::Tables t;
+  const int rc = ddo::build_tables(delays, nchan, ndm, nd_thr, esize, &t);
+  info[0] = rc == 0;
+  if (rc != 0) return 0;
+  info[1] = t.nd_cta;
+  info[2] = t.ntiles;
+  info[3] = t.nchunks;
+  info[4] = t.nchan_pad;
+  info[5] = t.rec_words;
+  info[6] = t.raw_stride;
+  info[7] = t.prow_words;
+  info[8] = t.smem_bytes;
+  info[9] = t.opc;
+  info[10] = t.esize;
+  if (recs) std::copy(t.recs.begin(), t.recs.end(), recs);
+  if (raw_meta) std::copy(t.raw_meta.begin(), t.raw_meta.end(), raw_meta);
+  return 0;
+}

@@ -395,3 +395,65 @@ def test_staged_kernel_bounded_wait_reports_timeout_and_recovers():
         dd.dd_sync(plan.handle)
         got = out.cpu().numpy()
     assert np.array_equal(got, oracle.dedisperse(block, delays, nsamp_in=nsamp))
+
+
+# ----------------------------------------------------- staged f16/f32 kernel
+
+FLOAT_STAGED_CASES = [
+    # (workload, nchan, ndm, samples past maxshift, pitch pad, dtype)
+    ("lband_f32", 1024, 96, 1500, 0, "f32"),
+    ("lband_f32", 1021, 70, 700, 8, "f16"),     # padding channels, pitch padding
+    ("lband_f32", 4096, 128, 900, 0, "f16"),
+    ("full_block_u8", 512, 64, 1000, 16, "f32"),
+]
+
+
+@pytest.mark.parametrize("name,nchan,ndm,extra,pad,dtype", FLOAT_STAGED_CASES)
+def test_staged_float_kernel_matches_oracle_and_plain_kernel(name, nchan, ndm, extra, pad, dtype):
+    base = synth.workload(name)
+    wl = synth.scaled(base, nchan=nchan, ndm=ndm)
+    wl.chan_width_mhz = base.chan_width_mhz
+    wl.dtype = dtype
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    nsamp = mx + extra
+    pitch = (nsamp + 7) // 8 * 8 + pad
+    block = synth.random_block(np.random.default_rng(21), wl.nchan, nsamp, dtype, pitch)
+    block[:, nsamp:] = 1e4  # row padding must never reach a stored output
+    dblock = _to_dev(block)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, dtype) as plan:
+        assert dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)["staged"]
+        staged = plan.execute(dblock, nsamp_in=nsamp)
+        dd._native.dd_plan_set_path(plan.handle, 1)
+        plain = plan.execute(dblock, nsamp_in=nsamp)
+        dd.dd_sync(plan.handle)
+        s, p = staged.cpu().numpy(), plain.cpu().numpy()
+    ref = oracle.dedisperse(block[:, :nsamp], delays)
+    err_s = float_rel_err(block[:, :nsamp], delays, s, ref)
+    err_p = float_rel_err(block[:, :nsamp], delays, p, ref)
+    print(f"{name} {dtype} {nchan}x{ndm}: staged {err_s:.2e}, plain {err_p:.2e}")
+    assert err_s <= FLOAT_RTOL and err_p <= FLOAT_RTOL
+
+
+def test_staged_float_kernel_bounded_wait_reports_timeout_and_recovers():
+    base = synth.workload("lband_f32")
+    wl = synth.scaled(base, nchan=256, ndm=64)
+    wl.chan_width_mhz = base.chan_width_mhz
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    nsamp = mx + 2000
+    pitch = (nsamp + 7) // 8 * 8
+    block = synth.random_block(np.random.default_rng(3), wl.nchan, nsamp, "f32", pitch)
+    dblock = _to_dev(block)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "f32") as plan:
+        assert dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)["staged"]
+        dd._native.dd_plan_set_wait_timeout(plan.handle, 50_000_000)
+        dd._native.dd_plan_inject_fault(plan.handle, 1)
+        plan.execute(dblock, nsamp_in=nsamp)
+        with pytest.raises(dd.DDError) as e:
+            dd.dd_sync(plan.handle)
+        assert e.value.status == -7
+        dd._native.dd_plan_inject_fault(plan.handle, 0)
+        out = plan.execute(dblock, nsamp_in=nsamp)
+        dd.dd_sync(plan.handle)
+        got = out.cpu().numpy()
+    ref = oracle.dedisperse(block[:, :nsamp], delays)
+    assert float_rel_err(block[:, :nsamp], delays, got, ref) <= FLOAT_RTOL
