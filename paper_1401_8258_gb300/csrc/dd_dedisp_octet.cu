@@ -4,8 +4,8 @@
 // D[d][t] = sum_c I[c][t + delay(c,d)]   (Sec. 2.1.1, brute-force equation),
 // summed in FP32.
 //
-// Data flow per CTA (one DM tile x one 512-sample time tile), per chunk of
-// 8 (f32) or 16 (f16) channels:
+// Data flow per CTA (one 128-trial DM tile x one 256-sample time tile), per
+// chunk of 16 channels:
 //   1. one warp queues bulk copies (cp.async.bulk, the TMA engine) of each
 //      channel's input window -- the "channel vector" of Sec. 2.4, sized by
 //      the largest and smallest delay of the tile -- plus the chunk's plan
@@ -143,7 +143,10 @@ __device__ void issue_chunk(const OctetArgs &a, int opc, int esize, int tile, in
 // Build all pattern rows of an octet, one build unit (dd_octet.h) at a
 // time: lane l builds row word first+l of every row -- per pattern the sum
 // over the eight channels of the sample at that channel's shift.  Channel 0
-// has the same sample in every pattern.
+// has the same sample in every pattern.  When every shift of the unit is 0
+// or 1 (the common case), each lane loads both candidate samples of every
+// channel once and selects per pattern; otherwise it loads each pattern's
+// samples directly.
 template <typename T>
 __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t zero, uint32_t prow,
                                            int lane) {
@@ -154,7 +157,7 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t zero, uin
   const int4 h2 = reinterpret_cast<const int4 *>(ud)[2];
   const int4 h3 = reinterpret_cast<const int4 *>(ud)[3];
   const uint32_t npat = static_cast<uint32_t>(h0.y) & 0xffu;
-  const uint32_t row_bytes = 4u * (static_cast<uint32_t>(h0.y) >> 8);
+  const uint32_t row_bytes = 4u * ((static_cast<uint32_t>(h0.y) >> 8) & 0xffffu);
   const uint32_t offw[4] = {static_cast<uint32_t>(h0.z), static_cast<uint32_t>(h0.w),
                             static_cast<uint32_t>(h1.x), static_cast<uint32_t>(h1.y)};
   const uint32_t codes[8] = {static_cast<uint32_t>(h1.z), static_cast<uint32_t>(h1.w),
@@ -168,6 +171,23 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t zero, uin
     addr[k] = zero + es * (((offw[k / 2] >> (16 * (k & 1))) & 0xffffu) + lane);
   const float v0 = Elem<T>::load(addr[0]);
   uint32_t dst = prow + 4u * ((static_cast<uint32_t>(h0.x) & 0xfffffu) + lane);
+  if ((static_cast<uint32_t>(h0.y) >> 30) & 1u) {
+    float r0[kGroup], r1[kGroup];
+#pragma unroll
+    for (int k = 1; k < kGroup; ++k)
+      r0[k] = Elem<T>::load(addr[k]), r1[k] = Elem<T>::load(addr[k] + es);
+#pragma unroll
+    for (int p = 0; p < kMaxPatterns; ++p) {
+      if (static_cast<uint32_t>(p) >= npat) break;
+      const uint32_t code = codes[p >> 1] >> (16 * (p & 1));
+      float v = v0;
+#pragma unroll
+      for (int k = 1; k < kGroup; ++k) v += ((code >> (2 * k)) & 1u) ? r1[k] : r0[k];
+      stsf(dst, v);
+      dst += row_bytes;
+    }
+    return;
+  }
 #pragma unroll
   for (int p = 0; p < kMaxPatterns; ++p) {
     if (static_cast<uint32_t>(p) >= npat) break;
@@ -196,7 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_octet(OctetArgs a) 
   constexpr int kUnitsOff = units_offset(ND_CTA);
   constexpr int kStartsOff = warp_start_offset(ND_CTA);
   constexpr int kEs = sizeof(T);
-  constexpr int kOpc = kEs == 4 ? 1 : 2;  // octets per chunk
+  constexpr int kOpc = kEs == 4 ? kOpcF32 : 2;  // octets per chunk
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;

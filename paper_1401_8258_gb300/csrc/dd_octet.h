@@ -1,12 +1,11 @@
 // dd_octet.h -- shape constants and plan-time tables of the staged octet
 // kernel for f16 and f32 input (internal to libdd).
 //
-// CTA tile: kDmGroups x nd_thr DM trials (16 x 4 = 64, or 16 x 2 = 32) by
-// kTimeTile output samples.  16 warps = 16 DM groups; a thread owns nd_thr
-// trials x kTimesPerThread samples (sample = lane + 32*j).  Channels are taken
-// in groups of kGroup = 8 adjacent channels ("octets"), `opc` octets per
-// chunk (1 for f32 input, 2 for f16: a chunk's input windows then take the
-// same shared memory).
+// CTA tile: kDmGroups x nd_thr DM trials (16 x 8 = 128, or 16 x 4 = 64) by
+// kTimeTile (256) output samples.  16 warps = 16 DM groups; a thread owns
+// nd_thr trials x kTimesPerThread samples (sample = lane + 32*j).  Channels
+// are taken in groups of kGroup = 8 adjacent channels ("octets"), `opc` (2)
+// octets per chunk.
 //
 // Pattern rows.  For octet o of a DM tile, let b be the smallest channel-0
 // delay over the tile's trials.  Each distinct relative-delay pattern p of
@@ -26,7 +25,7 @@
 //     first+31 (item = one row word) of every pattern row of one octet; lane
 //     l builds item first+l:
 //     [0] row-area word offset of item `first` of row 0 | items << 20
-//     [1] patterns | L << 8
+//     [1] patterns | L << 8 | fast << 30 (fast: every shift is 0 or 1)
 //     [2..5] element offsets, from the raw stage's zero area, of channels
 //         0..7 (16 bits each, two per word): the earliest sample any pattern
 //         needs for item `first`; padding channels point into the zero area
@@ -50,12 +49,23 @@
 
 namespace ddo {
 
+// Tile shape; the DDO_* macros exist only to build shape variants for tuning.
+#ifndef DDO_TIMES_PER_THREAD
+#define DDO_TIMES_PER_THREAD 8
+#endif
+#ifndef DDO_ND_THR
+#define DDO_ND_THR 8
+#endif
+#ifndef DDO_OPC_F32
+#define DDO_OPC_F32 2
+#endif
 constexpr int kGroup = 8;
 constexpr int kDmGroups = 16;
 constexpr int kThreads = 32 * kDmGroups;                 // 512
-constexpr int kTimesPerThread = 16;
-constexpr int kTimeTile = 32 * kTimesPerThread;          // 512
-constexpr int kNdThr = 4;                                // trials per thread (64 per CTA)
+constexpr int kTimesPerThread = DDO_TIMES_PER_THREAD;
+constexpr int kTimeTile = 32 * kTimesPerThread;          // 256
+constexpr int kNdThr = DDO_ND_THR;                       // trials per thread (128 per CTA)
+constexpr int kOpcF32 = DDO_OPC_F32;                     // octets per chunk for f32 input
 constexpr int kMaxOctetsPerChunk = 2;
 constexpr int kMaxPatterns = 16;
 constexpr int kMaxShift = 3;                             // element shifts 0..3 within a unit

@@ -35,7 +35,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
   t.nd_thr = nd_thr;
   t.nd_cta = nd_cta;
   t.esize = esize;
-  t.opc = esize == 4 ? 1 : 2;
+  t.opc = esize == 4 ? kOpcF32 : 2;
   t.ntiles = (ndm + nd_cta - 1) / nd_cta;
   t.noctets = (nchan + kGroup - 1) / kGroup;
   t.nchan_pad = t.noctets * kGroup;
@@ -136,7 +136,12 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
       for (int first = 0; first < O.L; first += 32) {
         std::array<int32_t, kUnitWords> u{};
         u[0] = (O.row_off + first) | (std::min(32, O.L - first) << 20);
-        u[1] = O.npat | (O.L << 8);
+        // fast: every channel's shift is 0 or 1 in every pattern
+        bool fast = true;
+        for (int p = 0; p < O.npat; ++p)
+          for (int k = 0; k < kGroup; ++k)
+            if (!O.pad[k] && O.shift[p][k] > 1) fast = false;
+        u[1] = O.npat | (O.L << 8) | (fast ? 1 << 30 : 0);
         for (int k = 0; k < kGroup; ++k) {
           // element offsets from the start of the zero area; the raw buffer
           // follows it (kZeroElems elements)
@@ -160,7 +165,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     // balance: costliest unit first onto the least loaded warp
     std::vector<int> order(list.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
-    auto cost = [&](int i) { return 1 + (list[i][1] & 0xff); };
+    auto cost = [&](int i) { return 1 + (list[i][1] & 0xff); };  // loads ~ one pattern
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
     std::vector<int> load(kWarps, 0);
     std::vector<std::vector<int>> per_warp(kWarps);

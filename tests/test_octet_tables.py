@@ -18,14 +18,14 @@ import paper_1401_8258_gb300 as dd
 import synth
 
 GROUP = 8
-T_TILE = 512
+T_TILE = 256
 REC_HEADER = 4
 UNIT_WORDS = 16
 MAX_OCTETS_PER_CHUNK = 2
 MAX_UNITS = 64
 ZERO_ELEMS = 64
 NWARPS = 16
-ND_THR = 4  # DM trials per thread of the 64-trial tile (16 warps x 4); 2 for 32
+ND_THR = 8  # DM trials per thread of the 128-trial tile (16 warps x 8); 4 for 64
 SENTINEL = 1e30
 
 
@@ -96,7 +96,7 @@ def emulate(block, tb, ndm, nsamp_out):
                 written = np.zeros(pw, dtype=np.int64)
                 for u in units.astype(np.int64) & 0xFFFFFFFF:
                     dest0, items = u[0] & 0xFFFFF, (u[0] >> 20) & 63
-                    npat, L = u[1] & 0xFF, u[1] >> 8
+                    npat, L, fast = u[1] & 0xFF, (u[1] >> 8) & 0xFFFF, (u[1] >> 30) & 1
                     assert 1 <= items <= 32 and 1 <= npat <= 16 and L % 4 == 0
                     offs = [(u[2 + k // 2] >> (16 * (k & 1))) & 0xFFFF for k in range(GROUP)]
                     lanes = np.arange(items)
@@ -110,6 +110,8 @@ def emulate(block, tb, ndm, nsamp_out):
                             sh = (code >> (2 * k)) & 3
                             if k == 0:
                                 assert sh == 0
+                            if fast:  # the kernel then only loads shifts 0 and 1
+                                assert sh <= 1
                             idx = offs[k] + lanes + sh
                             if offs[k] < ZERO_ELEMS:  # padding channel: inside the zero area
                                 assert idx.max() < ZERO_ELEMS
@@ -167,7 +169,7 @@ def test_octet_tables_fit_shared_memory_for_lband():
     delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
     for esize in (4, 2):
         tb = octet_tables(delays, wl.nchan, wl.ndm, ND_THR, esize)
-        assert tb is not None and tb["nd_cta"] == 64, esize
+        assert tb is not None and tb["nd_cta"] == 128, esize
         stage = ZERO_ELEMS * esize + GROUP * tb["opc"] * tb["raw_stride"] * esize
         smem = 64 + 4 * tb["rec_words"] * 4 + 3 * stage + 2 * tb["prow_words"] * 4
         assert smem == tb["smem"] <= 227 * 1024
