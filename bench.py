@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-probes", action="store_true", help="skip the add-pipe probes")
+    ap.add_argument("--nsamp", type=int, default=None,
+                    help="input samples per channel (default: the workload's); a shorter "
+                         "block for profiling captures")
     return ap.parse_args()
 
 
@@ -218,11 +221,18 @@ def cpu_model() -> str:
 
 # ------------------------------------------------------------- reference arm
 
+def load_workload(args):
+    wl = synth.workload(args.workload)
+    if args.nsamp is not None:
+        wl = synth.scaled(wl, nsamp=args.nsamp)
+    return wl
+
+
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    wl = synth.workload(args.workload)
+    wl = load_workload(args)
     delays, mx, nsamp_out = geometry_oracle(wl)
     block, _ = synth.make_block(wl, args.seed, delays)
     per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
@@ -283,7 +293,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     dd.build()
 
-    wl = synth.workload(args.workload)
+    wl = load_workload(args)
     plan = dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, wl.dtype, local)
     delays = plan.delays()
     nsamp_out = plan.nsamp_out(wl.nsamp)
