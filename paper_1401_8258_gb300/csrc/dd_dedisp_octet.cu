@@ -57,22 +57,37 @@ struct OctetArgs {
   int32_t skip_copies;  // test hook: queue nothing, so the first wait runs out
 };
 
+// Input elements in shared memory: `raw` is the stored sample, `add` sums it
+// into an FP32 value (f16 samples enter the sum exactly: add.f32.f16 widens
+// the half before the single rounding of the add).
 template <typename T>
 struct Elem;
 template <>
 struct Elem<float> {
+  using raw = float;
   static __device__ __forceinline__ float load(uint32_t addr) {
     float v;
     asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
     return v;
   }
+  static __device__ __forceinline__ float widen(float x) { return x; }
+  static __device__ __forceinline__ float add(float v, float x) { return v + x; }
 };
 template <>
 struct Elem<__half> {
-  static __device__ __forceinline__ float load(uint32_t addr) {
+  using raw = unsigned short;
+  static __device__ __forceinline__ unsigned short load(uint32_t addr) {
     unsigned short v;
     asm volatile("ld.shared.u16 %0, [%1];" : "=h"(v) : "r"(addr));
-    return __half2float(__ushort_as_half(v));
+    return v;
+  }
+  static __device__ __forceinline__ float widen(unsigned short x) {
+    return __half2float(__ushort_as_half(x));
+  }
+  static __device__ __forceinline__ float add(float v, unsigned short x) {
+    float r;
+    asm("add.rn.f32.f16 %0, %1, %2;" : "=f"(r) : "h"(x), "f"(v));
+    return r;
   }
 };
 
@@ -169,20 +184,21 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t zero, uin
 #pragma unroll
   for (int k = 0; k < kGroup; ++k)
     addr[k] = zero + es * (((offw[k / 2] >> (16 * (k & 1))) & 0xffffu) + lane);
-  const float v0 = Elem<T>::load(addr[0]);
+  using E = Elem<T>;
+  const float v0 = E::widen(E::load(addr[0]));
   uint32_t dst = prow + 4u * ((static_cast<uint32_t>(h0.x) & 0xfffffu) + lane);
   if ((static_cast<uint32_t>(h0.y) >> 30) & 1u) {
-    float r0[kGroup], r1[kGroup];
+    typename E::raw r0[kGroup], r1[kGroup];
 #pragma unroll
     for (int k = 1; k < kGroup; ++k)
-      r0[k] = Elem<T>::load(addr[k]), r1[k] = Elem<T>::load(addr[k] + es);
+      r0[k] = E::load(addr[k]), r1[k] = E::load(addr[k] + es);
 #pragma unroll
     for (int p = 0; p < kMaxPatterns; ++p) {
       if (static_cast<uint32_t>(p) >= npat) break;
       const uint32_t code = codes[p >> 1] >> (16 * (p & 1));
       float v = v0;
 #pragma unroll
-      for (int k = 1; k < kGroup; ++k) v += ((code >> (2 * k)) & 1u) ? r1[k] : r0[k];
+      for (int k = 1; k < kGroup; ++k) v = E::add(v, ((code >> (2 * k)) & 1u) ? r1[k] : r0[k]);
       stsf(dst, v);
       dst += row_bytes;
     }
@@ -194,7 +210,7 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t zero, uin
     const uint32_t code = codes[p >> 1] >> (16 * (p & 1));
     float v = v0;
 #pragma unroll
-    for (int k = 1; k < kGroup; ++k) v += Elem<T>::load(addr[k] + es * ((code >> (2 * k)) & 3u));
+    for (int k = 1; k < kGroup; ++k) v = E::add(v, E::load(addr[k] + es * ((code >> (2 * k)) & 3u)));
     stsf(dst, v);
     dst += row_bytes;
   }
