@@ -111,6 +111,7 @@ void destroy_plan(dd_plan *p) {
     delete p->octet;
     p->octet = nullptr;
   }
+  free_device(p->d_next_item);
   free_device(p->d_delays);
   free_device(p->d_error);
   free_device(p->d_stats);
@@ -147,6 +148,7 @@ int setup_quad(dd_plan *p) {
   if (e == cudaSuccess)
     e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
   p->quad = q;  // freed with the plan on error
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_next_item, sizeof(unsigned long long));
   return cuda_status(e);
 }
 

@@ -28,6 +28,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <cstring>
 
 #include "dd_device.cuh"
 #include "dd_internal.h"
@@ -117,30 +118,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
       : "memory");
 }
 
-struct QuadArgs {
-  const uint8_t *block;
-  int64_t pitch;  // bytes per channel row (multiple of 16)
-  int32_t ndm;
-  int64_t nsamp_out;
-  int32_t *out;
-  const int32_t *recs;
-  const int32_t *raw_meta;
-  int32_t nchunks;
-  int32_t nchan_pad;
-  int32_t rec_words;
-  int32_t raw_stride;
-  int32_t prow_words;
-  int64_t *rowsums;  // [ndm][2] += exact sum D, sum D^2 of the stored outputs (null: skip)
-  int32_t *tilemax;  // [ndm][gridDim.y] largest stored output of the CTA's time tile
-  int32_t *status;  // plan's sticky device status word
+// Kernel parameters of one launch: the beams' descriptors (dd_quad.h) and
+// the shared work queue.
+struct QuadLaunch {
+  Beam beams[kMaxBeams];
+  int32_t nbeams;
+  int64_t total_items;
+  unsigned long long *next_item;  // work-queue head (zero at launch)
+  int32_t *status;                // sticky device status word
   uint64_t timeout_ns;
-  int32_t skip_copies;  // test hook: queue nothing, so the first wait runs out
+  int32_t skip_copies;            // test hook: queue nothing, so the first wait runs out
 };
 
 // Queue the bulk copies of chunk `ch` (its record and the raw windows of its
 // 4*kQuadsPerChunk channels) on mbarrier `bar`.  Called by all 32 lanes of
 // one warp: lane s < 16 owns channel slot s; lane 0 posts the byte count.
-__device__ void issue_chunk(const QuadArgs &a, const int32_t *meta_s, int tile, int64_t t_cta,
+__device__ void issue_chunk(const Beam &a, const int32_t *meta_s, int tile, int64_t t_cta,
                             int ch, uint32_t bar, uint32_t rec_dst, uint32_t raw_dst, int lane) {
   constexpr int kSlots = 4 * kQuadsPerChunk;
   uint32_t len = 0, skip = 0;
@@ -293,8 +286,14 @@ __device__ __forceinline__ void drain(uint32_t (&acc)[ND_THR][kPairsPerThread], 
   }
 }
 
+// Persistent kernel: each CTA takes work items (one DM tile x one time tile
+// of one beam) from the launch's queue until it is empty.  Per item every
+// warp role runs the chunk pipeline below from a clean state (mbarriers
+// re-initialised, every named-barrier phase of the previous item complete);
+// tensor memory is allocated once per CTA.
 template <int ND_THR>
-__global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a) {
+__global__ void __launch_bounds__(kThreads, 1)
+dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
   constexpr int ND_CTA = kDmGroups * ND_THR;
   constexpr int kSegsOff = units_offset(ND_CTA);
   constexpr int kStartsOff = warp_start_offset(ND_CTA);
@@ -309,242 +308,267 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_quad_u8(QuadArgs a)
   static_assert(kFlushQuads % kQuadsPerChunk == 0, "drain at chunk boundaries");
   static_assert(kTimeGroups == 1, "a warp holds whole time tiles of its trials (tile maxima)");
   static_assert(kRawStages == kCopyAhead + 1 && kRecStages == kRowStages + kCopyAhead &&
-                    8 * kRawStages <= kTmemSlot,
+                    8 * kRawStages <= kTmemSlot && kItemSlot + 8 <= kBarrierBytes,
                 "pipeline depths");
   constexpr int kFlushChunks = kFlushQuads / kQuadsPerChunk;
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  // DM tiles vary fastest across the grid, so the CTAs resident at any time
-  // cover a narrow span of input samples for all DM tiles and share the
-  // input windows through L2 instead of re-reading them from HBM.
-  const int tile = blockIdx.x;
-  const int64_t t_cta = static_cast<int64_t>(blockIdx.y) * kTimeTile;
-
-  // shared-memory layout (dd_quad.h): copy mbarriers and tensor-memory
-  // address, raw window table, records, raw window buffers, pattern rows
   const uint32_t bar0 = smem_addr(smem);
   auto tma_bar = [&](int m) { return bar0 + 8u * (m % kRawStages); };
   // chunk at which the building warps stopped after a copy wait ran out
-  volatile int32_t *abort_at = reinterpret_cast<volatile int32_t *>(smem + kTmemSlot + 4);
+  volatile int32_t *abort_at = reinterpret_cast<volatile int32_t *>(smem + kAbortSlot);
+  volatile long long *item_s = reinterpret_cast<volatile long long *>(smem + kItemSlot);
   int32_t *meta_s = reinterpret_cast<int32_t *>(smem + kBarrierBytes);
-  const uint32_t meta_bytes = static_cast<uint32_t>((a.nchan_pad * 8 + 15) / 16 * 16);
-  const uint32_t rec_bytes = static_cast<uint32_t>(a.rec_words) * 4;
-  const uint32_t rec_off = kBarrierBytes + meta_bytes;
-  const uint32_t raw_off = rec_off + kRecStages * rec_bytes;
-  const uint32_t raw_bytes = 4u * kQuadsPerChunk * static_cast<uint32_t>(a.raw_stride);
-  const uint32_t prow_off = raw_off + kRawStages * raw_bytes;
-  const uint32_t prow_bytes = static_cast<uint32_t>(a.prow_words) * 4;
-  auto rec_ptr = [&](int m) {
-    return reinterpret_cast<const int32_t *>(smem + rec_off + (m % kRecStages) * rec_bytes);
-  };
-  auto rec_addr = [&](int m) { return bar0 + rec_off + (m % kRecStages) * rec_bytes; };
-  auto raw_addr = [&](int m) { return bar0 + raw_off + (m % kRawStages) * raw_bytes; };
-  auto prow_addr = [&](int m) { return bar0 + prow_off + (m % kRowStages) * prow_bytes; };
 
-  const int32_t *meta_g = a.raw_meta + static_cast<int64_t>(tile) * a.nchan_pad * 2;
-  for (int i = tid; i < 2 * a.nchan_pad; i += kThreads) meta_s[i] = meta_g[i];
-  if (tid == 0) {
-    for (int b = 0; b < kRawStages; ++b) mbar_init(tma_bar(b), 1);
-    *abort_at = INT32_MAX;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
   if (warp == 0) tmem_alloc(bar0 + kTmemSlot, kTmemCols);
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
   const uint32_t tmem_base = *reinterpret_cast<volatile uint32_t *>(smem + kTmemSlot);
-
-  // Pipeline (chunk m: raw stage m % kRawStages, record stage m % kRecStages, row
-  // stage m % kRowStages).  Building warps, chunk j: wait until the
-  // accumulating warps are done with chunk j - kRowStages (its row stage is
-  // reused, and so are older record stages); wait (bounded) for the copies
-  // of chunk j and agree among themselves that they landed; the first
-  // building warp queues the copies of chunk j+kCopyAhead (into the raw
-  // stage of chunk j-1 and the record stage of chunk j-kRowStages); build this
-  // warp's units of chunk j's rows; signal the rows built.  Accumulating warps, chunk k: wait for its rows, add
-  // them, signal the stage consumed.  A copy wait that runs out records its
-  // chunk in abort_at before that chunk's rows signal; both roles leave at
-  // that chunk, and the building warps then wait for the consumed signals
-  // still outstanding, so every barrier phase completes.
   const bool builder = warp >= kAccThreads / 32;
-  bool aborted = false;
-  int issued = 0;  // chunks queued (first building warp)
-  uint32_t acc[ND_THR][kPairsPerThread];
-#pragma unroll
-  for (int i = 0; i < ND_THR; ++i)
-#pragma unroll
-    for (int j = 0; j < kPairsPerThread; ++j) acc[i][j] = 0;
-  bool drained = false;  // tensor memory holds sums
   const int dg = warp / kTimeGroups;
   const int tg = warp & (kTimeGroups - 1);
   const uint32_t my_pair = static_cast<uint32_t>(tg * 32 * kPairsPerThread + lane);
 
-  if (builder) {
-    const int bw = warp - kAccThreads / 32;
-    const bool issuer = bw == 0 && !a.skip_copies;
-    if (issuer) {
-      const int prefill = a.nchunks < kCopyAhead ? a.nchunks : kCopyAhead;
-      for (int m = 0; m < prefill; ++m)
-        issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
-      issued = prefill;
+  for (;;) {
+    if (tid == 0) *item_s = static_cast<long long>(atomicAdd(L.next_item, 1ull));
+    __syncthreads();
+    const long long item = *item_s;
+    if (item >= L.total_items) break;
+    int b = 0;
+    while (b + 1 < L.nbeams && item >= L.beams[b + 1].item_begin) ++b;
+    const Beam &a = L.beams[b];
+    // DM tiles vary fastest along the queue, so the items in flight at any
+    // time cover a narrow span of input samples for all DM tiles and share
+    // the input windows through L2 instead of re-reading them from HBM.
+    const long long local = item - a.item_begin;
+    const int tile = static_cast<int>(local % a.ntiles_dm);
+    const int ttile = static_cast<int>(local / a.ntiles_dm);
+    const int64_t t_cta = static_cast<int64_t>(ttile) * kTimeTile;
+
+    // shared-memory layout (dd_quad.h): copy mbarriers, tensor-memory
+    // address and flags, raw window table, records, raw window buffers,
+    // pattern rows
+    const uint32_t meta_bytes = static_cast<uint32_t>((a.nchan_pad * 8 + 15) / 16 * 16);
+    const uint32_t rec_bytes = static_cast<uint32_t>(a.rec_words) * 4;
+    const uint32_t rec_off = kBarrierBytes + meta_bytes;
+    const uint32_t raw_off = rec_off + kRecStages * rec_bytes;
+    const uint32_t raw_bytes = 4u * kQuadsPerChunk * static_cast<uint32_t>(a.raw_stride);
+    const uint32_t prow_off = raw_off + kRawStages * raw_bytes;
+    const uint32_t prow_bytes = static_cast<uint32_t>(a.prow_words) * 4;
+    auto rec_ptr = [&](int m) {
+      return reinterpret_cast<const int32_t *>(smem + rec_off + (m % kRecStages) * rec_bytes);
+    };
+    auto rec_addr = [&](int m) { return bar0 + rec_off + (m % kRecStages) * rec_bytes; };
+    auto raw_addr = [&](int m) { return bar0 + raw_off + (m % kRawStages) * raw_bytes; };
+    auto prow_addr = [&](int m) { return bar0 + prow_off + (m % kRowStages) * prow_bytes; };
+
+    const int32_t *meta_g = a.raw_meta + static_cast<int64_t>(tile) * a.nchan_pad * 2;
+    for (int i = tid; i < 2 * a.nchan_pad; i += kThreads) meta_s[i] = meta_g[i];
+    if (tid == 0) {
+      for (int s = 0; s < kRawStages; ++s) mbar_init(tma_bar(s), 1);
+      *abort_at = INT32_MAX;
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int j = 0; j < a.nchunks; ++j) {
-      if (j >= kRowStages) bar_sync(kBarEmpty + j % kRowStages, kThreads);
-      const bool ok = warp_wait(tma_bar(j), (j / kRawStages) & 1, a.timeout_ns, lane);
-      if (bar_or(kBarBuild, kBuildThreads, !ok)) {
-        if (bw == 0 && lane == 0) *abort_at = j;
-        aborted = true;
+    __syncthreads();
+
+    // Pipeline (chunk m: raw stage m % kRawStages, record stage m %
+    // kRecStages, row stage m % kRowStages).  Building warps, chunk j: wait
+    // until the accumulating warps are done with chunk j - kRowStages (its
+    // row stage is reused, and so are older record stages); wait (bounded)
+    // for the copies of chunk j and agree among themselves that they landed;
+    // the first building warp queues the copies of chunk j + kCopyAhead (into
+    // the raw stage of chunk j-1 and the record stage of chunk j-kRowStages);
+    // build this warp's units of chunk j's rows; signal the rows built.
+    // Accumulating warps, chunk k: wait for its rows, add them, signal the
+    // stage consumed.  A copy wait that runs out records its chunk in
+    // abort_at before that chunk's rows signal; both roles leave at that
+    // chunk, and the building warps then wait for the consumed signals still
+    // outstanding, so every barrier phase completes.
+    bool aborted = false;
+    int issued = 0;  // chunks queued (first building warp)
+    if (builder) {
+      const int bw = warp - kAccThreads / 32;
+      const bool issuer = bw == 0 && !L.skip_copies;
+      if (issuer) {
+        const int prefill = a.nchunks < kCopyAhead ? a.nchunks : kCopyAhead;
+        for (int m = 0; m < prefill; ++m)
+          issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
+        issued = prefill;
+      }
+      for (int j = 0; j < a.nchunks; ++j) {
+        if (j >= kRowStages) bar_sync(kBarEmpty + j % kRowStages, kThreads);
+        const bool ok = warp_wait(tma_bar(j), (j / kRawStages) & 1, L.timeout_ns, lane);
+        if (bar_or(kBarBuild, kBuildThreads, !ok)) {
+          if (bw == 0 && lane == 0) *abort_at = j;
+          aborted = true;
+          bar_arrive(kBarFull + j % kRowStages, kThreads);
+          // consumed signals still outstanding: chunks j-kRowStages+1 .. j-1
+          for (int m = j - kRowStages + 1; m < j; ++m)
+            if (m >= 0) bar_sync(kBarEmpty + m % kRowStages, kThreads);
+          break;
+        }
+        if (issuer && j + kCopyAhead < a.nchunks) {
+          // every building warp is past chunk j-1 (bar_or above) and the
+          // accumulating warps past chunk j-kRowStages (bar_sync): the raw
+          // stage of chunk j-1 and the record stage of chunk j-kRowStages are
+          // free
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const int m = j + kCopyAhead;
+          issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
+          issued = m + 1;
+        }
+        const int32_t *rec = rec_ptr(j);
+        build_rows(rec, raw_addr(j), prow_addr(j), kSegsOff, bw, lane, 0,
+                   warp_segments(rec, bw, kStartsOff), kStartsOff);
         bar_arrive(kBarFull + j % kRowStages, kThreads);
-        // consumed signals still outstanding: chunks j-kRowStages+1 .. j-1
-        for (int m = j - kRowStages + 1; m < j; ++m)
+      }
+      if (!aborted) {
+        // consumed signals of the last kRowStages chunks
+        for (int m = a.nchunks - kRowStages; m < a.nchunks; ++m)
           if (m >= 0) bar_sync(kBarEmpty + m % kRowStages, kThreads);
-        break;
       }
-      if (issuer && j + kCopyAhead < a.nchunks) {
-        // every building warp is past chunk j-1 (bar_or above) and the
-        // accumulating warps past chunk j-kRowStages (bar_sync): the raw
-        // stage of chunk j-1 and the record stage of chunk j-kRowStages are
-        // free
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const int m = j + kCopyAhead;
-        issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
-        issued = m + 1;
-      }
-      const int32_t *rec = rec_ptr(j);
-      build_rows(rec, raw_addr(j), prow_addr(j), kSegsOff, bw, lane, 0,
-                 warp_segments(rec, bw, kStartsOff), kStartsOff);
-      bar_arrive(kBarFull + j % kRowStages, kThreads);
-    }
-    if (!aborted) {
-      // consumed signals of the last kRowStages chunks
-      for (int m = a.nchunks - kRowStages; m < a.nchunks; ++m)
-        if (m >= 0) bar_sync(kBarEmpty + m % kRowStages, kThreads);
-    }
-  } else {
-    const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
-                           static_cast<uint32_t>(warp >> 2) * kColsPerThread;
-    for (int k = 0; k < a.nchunks; ++k) {
-      bar_sync(kBarFull + k % kRowStages, kThreads);
-      if (*abort_at == k) {  // rows of chunk k were not built
-        aborted = true;
-        break;
-      }
-      const int32_t *rec = rec_ptr(k);
-      const int nq = rec[2];
-      const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
-      const uint32_t prow = prow_addr(k);
-      int a_next[2][ND_THR];
-      load_offsets<ND_THR>(A, a_next[0]);
-      load_offsets<ND_THR>(A + ND_CTA, a_next[1]);
+    } else {
+      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                             static_cast<uint32_t>(warp >> 2) * kColsPerThread;
+      uint32_t acc[ND_THR][kPairsPerThread];
 #pragma unroll
-      for (int q = 0; q < kQuadsPerChunk; q += 2) {
-        if (q < nq) {
-          int a_cur[2][ND_THR];
+      for (int i = 0; i < ND_THR; ++i)
 #pragma unroll
-          for (int h = 0; h < 2; ++h)
+        for (int j = 0; j < kPairsPerThread; ++j) acc[i][j] = 0;
+      bool drained = false;  // tensor memory holds sums of this item
+      for (int k = 0; k < a.nchunks; ++k) {
+        bar_sync(kBarFull + k % kRowStages, kThreads);
+        if (*abort_at == k) {  // rows of chunk k were not built
+          aborted = true;
+          break;
+        }
+        const int32_t *rec = rec_ptr(k);
+        const int nq = rec[2];
+        const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
+        const uint32_t prow = prow_addr(k);
+        int a_next[2][ND_THR];
+        load_offsets<ND_THR>(A, a_next[0]);
+        load_offsets<ND_THR>(A + ND_CTA, a_next[1]);
 #pragma unroll
-            for (int i = 0; i < ND_THR; ++i) a_cur[h][i] = a_next[h][i];
-          if (q + 2 < nq) {
-            load_offsets<ND_THR>(A + (q + 2) * ND_CTA, a_next[0]);
-            load_offsets<ND_THR>(A + (q + 3) * ND_CTA, a_next[1]);
+        for (int q = 0; q < kQuadsPerChunk; q += 2) {
+          if (q < nq) {
+            int a_cur[2][ND_THR];
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+#pragma unroll
+              for (int i = 0; i < ND_THR; ++i) a_cur[h][i] = a_next[h][i];
+            if (q + 2 < nq) {
+              load_offsets<ND_THR>(A + (q + 2) * ND_CTA, a_next[0]);
+              load_offsets<ND_THR>(A + (q + 3) * ND_CTA, a_next[1]);
+            }
+            if (q + 1 < nq) {
+#pragma unroll
+              for (int i = 0; i < ND_THR; ++i)
+                AccPairs<0>::two(acc[i],
+                                 prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair),
+                                 prow + 4u * (static_cast<uint32_t>(a_cur[1][i]) + my_pair));
+            } else {
+#pragma unroll
+              for (int i = 0; i < ND_THR; ++i)
+                AccPairs<0>::one(acc[i],
+                                 prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair));
+            }
           }
-          if (q + 1 < nq) {
+        }
+        bar_arrive(kBarEmpty + k % kRowStages, kThreads);
+        // at most kFlushQuads quads in the 16-bit halves
+        if ((k + 1) % kFlushChunks == 0 && k + 1 < a.nchunks) {
+          drain<ND_THR>(acc, taddr, drained);
+          drained = true;
+        }
+      }
+      if (!aborted) {
+        // final sums: stored part (if any) + the packed halves; pair j of
+        // trial i covers samples my_pair + 32 j and my_pair + 32 j + kHalf.
+        // Per trial, this thread's exact sum, sum of squares and largest
+        // value of the samples it stores (for the detection statistics).
+        long long s1[ND_THR], s2[ND_THR];
+        int32_t mx[ND_THR];
 #pragma unroll
-            for (int i = 0; i < ND_THR; ++i)
-              AccPairs<0>::two(acc[i], prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair),
-                               prow + 4u * (static_cast<uint32_t>(a_cur[1][i]) + my_pair));
+        for (int i = 0; i < ND_THR; ++i) s1[i] = 0, s2[i] = 0, mx[i] = INT32_MIN;
+#pragma unroll
+        for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
+          uint32_t v[16];
+          if (drained) {
+            tmem_ld16(taddr + 16u * blk, v);
           } else {
 #pragma unroll
-            for (int i = 0; i < ND_THR; ++i)
-              AccPairs<0>::one(acc[i],
-                               prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair));
+            for (int e = 0; e < 16; ++e) v[e] = 0;
+          }
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int m = 8 * blk + e;
+            const int i = m / kPairsPerThread, j = m % kPairsPerThread;
+            const int d = tile * ND_CTA + dg * ND_THR + i;
+            if (d >= a.ndm) continue;
+            int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
+            const uint32_t w = acc[i][j];
+            const int64_t t = t_cta + my_pair + 32 * j;
+            const int32_t lo = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
+            const int32_t hi = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
+            if (t < a.nsamp_out) {
+              orow[t] = lo;
+              s1[i] += lo, s2[i] += static_cast<long long>(lo) * lo, mx[i] = max(mx[i], lo);
+            }
+            if (t + kHalf < a.nsamp_out) {
+              orow[t + kHalf] = hi;
+              s1[i] += hi, s2[i] += static_cast<long long>(hi) * hi, mx[i] = max(mx[i], hi);
+            }
           }
         }
-      }
-      bar_arrive(kBarEmpty + k % kRowStages, kThreads);
-      // at most kFlushQuads quads in the 16-bit halves
-      if ((k + 1) % kFlushChunks == 0 && k + 1 < a.nchunks) {
-        drain<ND_THR>(acc, taddr, drained);
-        drained = true;
+        if (a.rowsums) {
+          // one warp holds all kTimeTile samples of its trials: reduce over
+          // lanes; integer sums make the row totals independent of order
+#pragma unroll
+          for (int i = 0; i < ND_THR; ++i) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+              s1[i] += __shfl_xor_sync(0xffffffffu, s1[i], o);
+              s2[i] += __shfl_xor_sync(0xffffffffu, s2[i], o);
+              mx[i] = max(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
+            }
+            const int d = tile * ND_CTA + dg * ND_THR + i;
+            if (lane == 0 && d < a.ndm) {
+              atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d),
+                        static_cast<unsigned long long>(s1[i]));
+              atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d + 1),
+                        static_cast<unsigned long long>(s2[i]));
+              a.tilemax[static_cast<int64_t>(d) * a.ntiles_t + ttile] = mx[i];
+            }
+          }
+        }
       }
     }
-    if (!aborted) {
-      // final sums: stored part (if any) + the packed halves; pair j of
-      // trial i covers samples my_pair + 32 j and my_pair + 32 j + kHalf.
-      // Per trial, this thread's exact sum, sum of squares and largest value
-      // of the samples it stores (for the statistics of the detection pass).
-      long long s1[ND_THR], s2[ND_THR];
-      int32_t mx[ND_THR];
-#pragma unroll
-      for (int i = 0; i < ND_THR; ++i) s1[i] = 0, s2[i] = 0, mx[i] = INT32_MIN;
-#pragma unroll
-      for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
-        uint32_t v[16];
-        if (drained) {
-          tmem_ld16(taddr + 16u * blk, v);
-        } else {
-#pragma unroll
-          for (int e = 0; e < 16; ++e) v[e] = 0;
-        }
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int m = 8 * blk + e;
-          const int i = m / kPairsPerThread, j = m % kPairsPerThread;
-          const int d = tile * ND_CTA + dg * ND_THR + i;
-          if (d >= a.ndm) continue;
-          int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
-          const uint32_t w = acc[i][j];
-          const int64_t t = t_cta + my_pair + 32 * j;
-          const int32_t lo = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
-          const int32_t hi = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
-          if (t < a.nsamp_out) {
-            orow[t] = lo;
-            s1[i] += lo, s2[i] += static_cast<long long>(lo) * lo, mx[i] = max(mx[i], lo);
-          }
-          if (t + kHalf < a.nsamp_out) {
-            orow[t + kHalf] = hi;
-            s1[i] += hi, s2[i] += static_cast<long long>(hi) * hi, mx[i] = max(mx[i], hi);
-          }
-        }
+
+    // the item is complete in every warp (tensor-memory accesses waited)
+    tmem_fence_before();
+    __syncthreads();
+    tmem_fence_after();
+    if (*abort_at != INT32_MAX) {
+      if (builder && warp - kAccThreads / 32 == 0 && lane == 0) {
+        // a bounded wait ran out: record it, and wait (bounded) for the
+        // copies this warp queued that may still be in flight (the last
+        // kRawStages queued, each on its own barrier) before leaving
+        atomicExch(L.status, 1);
+        for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
+          mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, L.timeout_ns);
       }
-      if (a.rowsums) {
-        // one warp holds all kTimeTile samples of its trials: reduce over
-        // lanes; integer sums make the row totals independent of order
-#pragma unroll
-        for (int i = 0; i < ND_THR; ++i) {
-#pragma unroll
-          for (int o = 16; o > 0; o >>= 1) {
-            s1[i] += __shfl_xor_sync(0xffffffffu, s1[i], o);
-            s2[i] += __shfl_xor_sync(0xffffffffu, s2[i], o);
-            mx[i] = max(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
-          }
-          const int d = tile * ND_CTA + dg * ND_THR + i;
-          if (lane == 0 && d < a.ndm) {
-            atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d),
-                      static_cast<unsigned long long>(s1[i]));
-            atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d + 1),
-                      static_cast<unsigned long long>(s2[i]));
-            a.tilemax[static_cast<int64_t>(d) * gridDim.y + blockIdx.y] = mx[i];
-          }
-        }
-      }
+      __syncthreads();
+      break;
     }
   }
-
-  // every thread's tensor-memory accesses are complete (waited) before the
+  // every thread's tensor-memory accesses are complete before the
   // allocating warp frees the columns
   tmem_fence_before();
   __syncthreads();
   tmem_fence_after();
-  if (*abort_at != INT32_MAX && builder && warp - kAccThreads / 32 == 0 && lane == 0) {
-    // a bounded wait ran out: record it, and wait (bounded) for the copies
-    // queued by this warp that may still be in flight (the last kRawStages
-    // queued, each on its own barrier) before the CTA leaves
-    atomicExch(a.status, 1);
-    for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
-      mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, a.timeout_ns);
-  }
   if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
 }
 
@@ -554,46 +578,76 @@ namespace ddk {
 
 bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out) {
   if (!p->quad || p->dtype != DD_U8) return false;
-  if ((nsamp_out + kTimeTile - 1) / kTimeTile > 65535) return false;  // grid.y limit
   return (reinterpret_cast<uintptr_t>(block) & 15) == 0 && (pitch & 15) == 0;
+}
+
+int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int smem, int device_sms,
+                      unsigned long long *next_item, int32_t *status, uint64_t timeout_ns,
+                      int32_t skip_copies, cudaStream_t stream, cudaError_t *err) {
+  if (nbeams < 1 || nbeams > kMaxBeams) {
+    *err = cudaErrorInvalidValue;
+    return -1;
+  }
+  QuadLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  int64_t items = 0;
+  for (int i = 0; i < nbeams; ++i) {
+    L.beams[i] = beams[i];
+    L.beams[i].item_begin = items;
+    items += static_cast<int64_t>(beams[i].ntiles_dm) * beams[i].ntiles_t;
+  }
+  L.nbeams = nbeams;
+  L.total_items = items;
+  L.next_item = next_item;
+  L.status = status;
+  L.timeout_ns = timeout_ns;
+  L.skip_copies = skip_copies;
+  auto kern = nd_thr == kNdThr ? dd_dedisperse_quad_u8<kNdThr> : dd_dedisperse_quad_u8<kNdThr / 2>;
+  *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int per_sm = 0;
+  if (*err == cudaSuccess)
+    *err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem);
+  if (*err == cudaSuccess) *err = cudaMemsetAsync(next_item, 0, sizeof(unsigned long long), stream);
+  if (*err == cudaSuccess) {
+    int64_t grid = static_cast<int64_t>(device_sms) * (per_sm > 0 ? per_sm : 1);
+    if (grid > items) grid = items;
+    if (grid > 0) kern<<<static_cast<unsigned>(grid), kThreads, smem, stream>>>(L);
+    *err = cudaGetLastError();
+  }
+  return *err == cudaSuccess ? 1 : -1;
+}
+
+Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out, void *out,
+               int64_t *rowsums, int32_t *tilemax) {
+  const QuadDevice &q = *p->quad;
+  Beam b;
+  std::memset(&b, 0, sizeof(b));
+  b.block = static_cast<const uint8_t *>(block);
+  b.out = static_cast<int32_t *>(out);
+  b.recs = q.d_recs;
+  b.raw_meta = q.d_raw_meta;
+  b.rowsums = rowsums;
+  b.tilemax = tilemax;
+  b.pitch = pitch;
+  b.nsamp_out = nsamp_out;
+  b.ndm = p->ndm;
+  b.nchunks = q.tables.nchunks;
+  b.nchan_pad = q.tables.nchan_pad;
+  b.rec_words = q.tables.rec_words;
+  b.raw_stride = q.tables.raw_stride;
+  b.prow_words = q.tables.prow_words;
+  b.ntiles_dm = q.tables.ntiles;
+  b.ntiles_t = static_cast<int32_t>((nsamp_out + kTimeTile - 1) / kTimeTile);
+  return b;
 }
 
 int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                            void *out, int64_t *rowsums, int32_t *tilemax, cudaStream_t stream,
                            cudaError_t *err) {
-  const QuadDevice &q = *p->quad;
-  QuadArgs a;
-  a.block = static_cast<const uint8_t *>(block);
-  a.pitch = pitch;
-  a.ndm = p->ndm;
-  a.nsamp_out = nsamp_out;
-  a.out = static_cast<int32_t *>(out);
-  a.recs = q.d_recs;
-  a.raw_meta = q.d_raw_meta;
-  a.nchunks = q.tables.nchunks;
-  a.nchan_pad = q.tables.nchan_pad;
-  a.rec_words = q.tables.rec_words;
-  a.raw_stride = q.tables.raw_stride;
-  a.prow_words = q.tables.prow_words;
-  a.rowsums = rowsums;
-  a.tilemax = tilemax;
-  a.status = p->d_error;
-  a.timeout_ns = p->wait_timeout_ns;
-  a.skip_copies = p->debug_skip_copies;
-  const dim3 grid(static_cast<unsigned>(q.tables.ntiles),
-                  static_cast<unsigned>((nsamp_out + kTimeTile - 1) / kTimeTile));
-  const int smem = q.tables.smem_bytes;
-  if (q.tables.nd_thr == kNdThr) {
-    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<kNdThr>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (*err == cudaSuccess) dd_dedisperse_quad_u8<kNdThr><<<grid, kThreads, smem, stream>>>(a);
-  } else {
-    *err = cudaFuncSetAttribute(dd_dedisperse_quad_u8<kNdThr / 2>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (*err == cudaSuccess) dd_dedisperse_quad_u8<kNdThr / 2><<<grid, kThreads, smem, stream>>>(a);
-  }
-  if (*err == cudaSuccess) *err = cudaGetLastError();
-  return *err == cudaSuccess ? 1 : -1;
+  const Beam b = quad_beam(p, block, pitch, nsamp_out, out, rowsums, tilemax);
+  return launch_quad_beams(&b, 1, p->quad->tables.nd_thr, p->quad->tables.smem_bytes, p->sm_count,
+                           p->d_next_item, p->d_error, p->wait_timeout_ns,
+                           p->debug_skip_copies, stream, err);
 }
 
 }  // namespace ddk

@@ -80,6 +80,7 @@ struct dd_plan {
   size_t d_cands_cap = 0;
 
   QuadDevice *quad = nullptr;       // staged u8 kernel tables (null: not applicable)
+  unsigned long long *d_next_item = nullptr;  // work-queue head of the staged u8 kernel
   OctetDevice *octet = nullptr;     // staged f16/f32 kernel tables (null: not applicable)
   int32_t path = 0;                 // 0 = automatic, 1 = plain-load kernel only
   uint64_t wait_timeout_ns = 2000000000ull;  // bound on every device-side wait
@@ -108,6 +109,14 @@ bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t 
 int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                            void *out, int64_t *rowsums, int32_t *tilemax, cudaStream_t stream,
                            cudaError_t *err);
+// The staged kernel is persistent: one launch drains a queue of (beam, DM
+// tile, time tile) items over up to ddq::kMaxBeams beams, which must share
+// nd_thr; smem is the largest of the beams' shared-memory sizes.
+ddq::Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
+                    void *out, int64_t *rowsums, int32_t *tilemax);
+int launch_quad_beams(const ddq::Beam *beams, int nbeams, int nd_thr, int smem, int device_sms,
+                      unsigned long long *next_item, int32_t *status, uint64_t timeout_ns,
+                      int32_t skip_copies, cudaStream_t stream, cudaError_t *err);
 constexpr int kTileSamples = ddq::kTimeTile;
 // Staged octet kernel (f16 / f32): needs the plan's octet tables, a 16-byte
 // aligned block, a pitch of a whole number of 16-byte units and at most

@@ -133,6 +133,8 @@ constexpr int kRowStages = DDQ_ROW_STAGES;
 constexpr int kRecStages = kRowStages + kCopyAhead;
 constexpr int kBarrierBytes = 64;  // copy mbarriers (8 bytes each), tensor-memory address, flags
 constexpr int kTmemSlot = 32;      // byte offset of the tensor-memory address
+constexpr int kAbortSlot = 36;     // chunk at which a copy wait ran out
+constexpr int kItemSlot = 40;      // current work item (int64)
 
 // Shared-memory layout: the mbarriers and tensor-memory address (kBarrierBytes), the tile's raw
 // window table (nchan_pad x 2 int32), kRecStages records, kRawStages raw
@@ -149,5 +151,23 @@ inline int32_t smem_bytes(const Tables &t) {
 // Returns 0 and fills *tb, or 1 if this geometry needs more than
 // kMaxPatterns patterns per quad and tile or more shared memory than a CTA has.
 int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, Tables *tb);
+
+// One beam of a launch of the (persistent) staged kernel: its block, output,
+// tables and work items.  Work item i of the launch belongs to the last beam
+// with item_begin <= i; within the beam, item (i - item_begin) is DM tile
+// (i - item_begin) % ntiles_dm of time tile (i - item_begin) / ntiles_dm.
+struct Beam {
+  const uint8_t *block;
+  int32_t *out;
+  const int32_t *recs;
+  const int32_t *raw_meta;
+  int64_t *rowsums;  // [ndm][2] += exact sum D, sum D^2 (null: no statistics)
+  int32_t *tilemax;  // [ndm][ntiles_t] largest output of each time tile
+  int64_t pitch;     // bytes per channel row (multiple of 16)
+  int64_t nsamp_out;
+  int64_t item_begin;
+  int32_t ndm, nchunks, nchan_pad, rec_words, raw_stride, prow_words, ntiles_dm, ntiles_t;
+};
+constexpr int kMaxBeams = 64;  // beams per launch (the descriptors travel as kernel parameters)
 
 }  // namespace ddq
