@@ -152,8 +152,32 @@ int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
            float nsigma, dd_candidate *cands, int64_t capacity, int64_t *count, void *stream,
            void *event);
 
-/* Host copies of the per-DM mean and rms computed by the last dd_detect or
- * dd_run on this plan (double[ndm] each; either pointer may be NULL). */
+/* Batches: several beams, each with its own plan (geometry, DM list, dtype),
+ * processed together.  The thesis runs one beam per GPU kernel (Sec. 2.4) and
+ * several beams per GPU (Sec. 3.4, Ch. 6); here the staged u8 kernel is
+ * persistent, so one launch drains the work items (DM tile x time tile) of
+ * up to 64 beams, with the costliest beams queued first, and small or
+ * uneven beams no longer leave most of the GPU idle.
+ *
+ * dd_batch_create: `plans` (host array of nplans >= 1 plan pointers, all on
+ * one device) must outlive the batch; a plan may appear once.
+ * dd_batch_run: for beam i, block[i], nsamp_in[i], pitch_elems[i], out[i],
+ * cands[i] (device, capacity[i] slots, NULL when capacity[i] == 0) as for
+ * dd_run with plans[i]; counts[i] (host) receives beam i's total.  Results
+ * per beam are identical to dd_run.  Synchronises `stream` once.  Returns the
+ * first error, else DD_ERR_OVERFLOW if any count exceeds its capacity (every
+ * beam's first capacity[i] candidates are still written), else DD_OK. */
+typedef struct dd_batch dd_batch;
+int dd_batch_create(dd_batch **out, dd_plan *const *plans, int32_t nplans);
+int dd_batch_destroy(dd_batch *b);
+int dd_batch_run(dd_batch *b, const void *const *block, const int64_t *nsamp_in,
+                 const int64_t *pitch_elems, void *const *out, float nsigma,
+                 dd_candidate *const *cands, const int64_t *capacity, int64_t *counts,
+                 void *stream);
+
+/* Host copies of the per-DM mean and rms computed by the last dd_detect,
+ * dd_run or dd_batch_run on this plan (double[ndm] each; either pointer may
+ * be NULL). */
 int dd_get_stats(const dd_plan *p, double *mean, double *sigma);
 
 /* Synchronise `stream` and return the plan's sticky device status

@@ -17,7 +17,7 @@ from ._native import (CANDIDATE_DTYPE, DD_ERR_OVERFLOW, DD_F16, DD_F32, DD_OK, D
                       DDError, dd_compute_delays, dd_detect, dd_execute, dd_get_stats,
                       dd_plan_create, dd_plan_delays, dd_plan_destroy, dd_plan_launch_count,
                       dd_plan_max_delay, dd_plan_nsamp_out, dd_process_host, dd_run,
-                      dd_status_string, dd_sync)
+                      dd_batch_create, dd_batch_destroy, dd_batch_run, dd_status_string, dd_sync)
 from .build import build
 
 __all__ = [
@@ -25,7 +25,7 @@ __all__ = [
     "DD_ERR_OVERFLOW", "DTYPE_CODES", "dd_compute_delays", "dd_plan_create", "dd_plan_destroy",
     "dd_plan_max_delay", "dd_plan_nsamp_out", "dd_plan_delays", "dd_execute", "dd_detect",
     "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
-    "dd_run",
+    "dd_run", "Batch", "dd_batch_create", "dd_batch_destroy", "dd_batch_run",
 ]
 
 _TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
@@ -132,3 +132,50 @@ class Plan:
 
     def launch_count(self) -> int:
         return dd_plan_launch_count(self.handle)
+
+
+class Batch:
+    """Several plans run together (dd_batch_*); keeps the plans alive."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        self.handle = dd_batch_create([p.handle for p in self.plans])
+
+    def run(self, blocks, nsigma, outs=None, nsamp_in=None, capacity=1 << 16, stream=None):
+        """Dedisperse and detect every beam; returns ``(outs, candidate arrays,
+        totals)``, one entry per plan."""
+        import torch
+        n = len(self.plans)
+        nsamp_in = [b.shape[1] for b in blocks] if nsamp_in is None else list(nsamp_in)
+        if outs is None:
+            outs = [torch.empty((p.ndm, p.nsamp_out(ns)), dtype=p.out_torch_dtype,
+                                device=b.device) for p, b, ns in zip(self.plans, blocks, nsamp_in)]
+        caps = [int(capacity)] * n if np.isscalar(capacity) else [int(c) for c in capacity]
+        cands = [torch.empty((max(c, 1), 16), dtype=torch.uint8, device=b.device)
+                 for c, b in zip(caps, blocks)]
+        st, totals = dd_batch_run(self.handle, blocks, nsamp_in, [b.stride(0) for b in blocks],
+                                  outs, nsigma, [c if k else None for c, k in zip(cands, caps)],
+                                  caps, stream)
+        hosts = []
+        for c, k, t in zip(cands, caps, totals):
+            m = min(t, k)
+            hosts.append(c[:m].cpu().numpy().view(CANDIDATE_DTYPE).reshape(-1) if m else
+                         np.zeros(0, dtype=CANDIDATE_DTYPE))
+        return outs, hosts, totals
+
+    def close(self):
+        if self.handle:
+            dd_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -67,6 +67,9 @@ SIGNATURES = [
     ("dd_plan_kernel_info", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     ("dd_detect_noalloc", ctypes.c_int, [_vp, _i32, _i32, _i64, _f32, _vp, _i64, _vp, _vp]),
     ("dd_run", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _f32, _vp, _i64, _vp, _vp, _vp]),
+    ("dd_batch_create", ctypes.c_int, [_vp, _vp, _i32]),
+    ("dd_batch_destroy", ctypes.c_int, [_vp]),
+    ("dd_batch_run", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp]),
 ]
 
 PEAK_KINDS = {"fadd": 0, "fadd2": 1, "iadd": 2, "iadd3": 3, "imad": 4, "lop3": 5, "prmt": 6,
@@ -200,6 +203,36 @@ def dd_run(plan, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity, str
                        _stream(stream), ev)
     _check(st, "dd_run", allow=(DD_ERR_OVERFLOW,))
     return st, int(cnt.value)
+
+
+def dd_batch_create(plans) -> int:
+    """Handle of a batch over the given plan handles."""
+    arr = (ctypes.c_void_p * len(plans))(*[int(p) for p in plans])
+    h = ctypes.c_void_p()
+    _check(load().dd_batch_create(ctypes.addressof(h), arr, len(plans)), "dd_batch_create")
+    return h.value
+
+
+def dd_batch_destroy(batch) -> None:
+    _check(load().dd_batch_destroy(batch), "dd_batch_destroy")
+
+
+def dd_batch_run(batch, blocks, nsamp_in, pitch_elems, outs, nsigma, cands, capacity,
+                 stream=None) -> tuple[int, list[int]]:
+    """Per-beam lists; returns ``(status, counts)`` (DD_OK or DD_ERR_OVERFLOW)."""
+    n = len(blocks)
+    vp_arr = ctypes.c_void_p * n
+    i64_arr = ctypes.c_int64 * n
+    b_ = vp_arr(*[_addr(x) for x in blocks])
+    o_ = vp_arr(*[_addr(x) for x in outs])
+    c_ = vp_arr(*[_addr(x) if x is not None else None for x in cands])
+    ns = i64_arr(*[int(x) for x in nsamp_in])
+    pe = i64_arr(*[int(x) for x in pitch_elems])
+    cap = i64_arr(*[int(x) for x in capacity])
+    cnt = i64_arr()
+    st = load().dd_batch_run(batch, b_, ns, pe, o_, float(nsigma), c_, cap, cnt, _stream(stream))
+    _check(st, "dd_batch_run", allow=(DD_ERR_OVERFLOW,))
+    return st, [int(x) for x in cnt]
 
 
 def dd_get_stats(plan, ndm) -> tuple[np.ndarray, np.ndarray]:

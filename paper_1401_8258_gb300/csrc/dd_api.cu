@@ -6,8 +6,10 @@
 
 #include <cmath>
 #include <cstdint>
+#include <algorithm>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "dd.h"
 #include "dd_internal.h"
@@ -374,6 +376,168 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   p->stats_valid = true;
   *count = *p->h_total;
   return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
+}
+
+struct dd_batch {
+  int device = 0;
+  int sm_count = 0;
+  std::vector<dd_plan *> plans;
+  unsigned long long *d_next_item = nullptr;  // work-queue head of the shared launches
+  int32_t *d_error = nullptr;                 // status word of the shared launches
+  int64_t launches = 0;
+};
+
+extern "C" int dd_batch_create(dd_batch **out, dd_plan *const *plans, int32_t nplans) {
+  if (!out) return DD_ERR_ARG;
+  *out = nullptr;
+  if (!plans || nplans < 1) return DD_ERR_ARG;
+  for (int32_t i = 0; i < nplans; ++i) {
+    if (!plans[i] || plans[i]->device != plans[0]->device) return DD_ERR_ARG;
+    for (int32_t j = 0; j < i; ++j)
+      if (plans[j] == plans[i]) return DD_ERR_ARG;
+  }
+  dd_batch *b = new (std::nothrow) dd_batch();
+  if (!b) return DD_ERR_OOM;
+  b->device = plans[0]->device;
+  b->sm_count = plans[0]->sm_count;
+  try {
+    b->plans.assign(plans, plans + nplans);
+  } catch (...) {
+    delete b;
+    return DD_ERR_OOM;
+  }
+  DeviceScope scope(b->device);
+  cudaError_t e = scope.ok() ? cudaSuccess : cudaErrorInvalidDevice;
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_next_item, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&b->d_error, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(b->d_error, 0, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    free_device(b->d_next_item);
+    free_device(b->d_error);
+    delete b;
+    return cuda_status(e);
+  }
+  *out = b;
+  return DD_OK;
+}
+
+extern "C" int dd_batch_destroy(dd_batch *b) {
+  if (!b) return DD_OK;
+  DeviceScope scope(b->device);
+  if (scope.ok()) cudaDeviceSynchronize();
+  free_device(b->d_next_item);
+  free_device(b->d_error);
+  delete b;
+  return DD_OK;
+}
+
+extern "C" int dd_batch_run(dd_batch *b, const void *const *block, const int64_t *nsamp_in,
+                            const int64_t *pitch_elems, void *const *out, float nsigma,
+                            dd_candidate *const *cands, const int64_t *capacity, int64_t *counts,
+                            void *stream) {
+  if (!b || !block || !nsamp_in || !pitch_elems || !out || !cands || !capacity || !counts)
+    return DD_ERR_ARG;
+  if (!std::isfinite(nsigma)) return DD_ERR_ARG;
+  const int n = static_cast<int>(b->plans.size());
+  std::vector<int64_t> nout(n);
+  for (int i = 0; i < n; ++i) {
+    counts[i] = 0;
+    if (!block[i] || !out[i] || capacity[i] < 0 || (capacity[i] > 0 && !cands[i]))
+      return DD_ERR_ARG;
+    const int st = validate_execute(b->plans[i], nsamp_in[i], pitch_elems[i], &nout[i]);
+    if (st != DD_OK) return st;
+  }
+  DeviceScope scope(b->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t err = cudaSuccess;
+  // staged u8 beams, by DM-tile width; the rest take their own kernels
+  std::vector<int> staged[2];
+  std::vector<char> is_staged(n, 0);
+  for (int i = 0; i < n; ++i) {
+    dd_plan *p = b->plans[i];
+    p->stats_valid = false;
+    if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
+      const int st = ensure_tile_workspace(p, static_cast<size_t>(ddk::time_tiles(nout[i])) * p->ndm);
+      if (st != DD_OK) return st;
+      err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
+      if (err != cudaSuccess) return cuda_status(err);
+      staged[p->quad->tables.nd_thr == ddq::kNdThr ? 0 : 1].push_back(i);
+      is_staged[i] = 1;
+    } else {
+      const int st = dd_execute(p, block[i], nsamp_in[i], pitch_elems[i], out[i], stream);
+      if (st != DD_OK) return st;
+    }
+  }
+  for (int g = 0; g < 2; ++g) {
+    std::vector<int> &idx = staged[g];
+    // costliest beams first (a work item costs about nchan): the queue's
+    // tail then holds the cheap items
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+      return b->plans[x]->nchan > b->plans[y]->nchan;
+    });
+    for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
+      const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
+      std::vector<ddq::Beam> beams;
+      int smem = 0;
+      for (size_t k = lo; k < hi; ++k) {
+        dd_plan *p = b->plans[idx[k]];
+        beams.push_back(ddk::quad_beam(p, block[idx[k]], pitch_elems[idx[k]], nout[idx[k]],
+                                       out[idx[k]], p->d_rowsums, p->d_tilemax));
+        smem = std::max(smem, static_cast<int>(p->quad->tables.smem_bytes));
+      }
+      dd_plan *p0 = b->plans[idx[lo]];
+      const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
+                                            g == 0 ? ddq::kNdThr : ddq::kNdThr / 2, smem,
+                                            b->sm_count, b->d_next_item, b->d_error,
+                                            p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
+      if (nl < 0) return cuda_status(err);
+      b->launches += nl;
+    }
+  }
+  // detection per beam, then one synchronisation for every count
+  for (int i = 0; i < n; ++i) {
+    dd_plan *p = b->plans[i];
+    int nl;
+    if (is_staged[i]) {
+      nl = ddk::launch_tiled_detect(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
+    } else {
+      const int64_t nchunks = (nout[i] + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
+      const int st = ensure_chunk_workspace(p, static_cast<size_t>(nchunks) * p->ndm);
+      if (st != DD_OK) return st;
+      nl = ddk::launch_stats(p, out[i], nout[i], nsigma, s, &err);
+      if (nl >= 0) {
+        p->launches += nl;
+        nl = ddk::launch_candidates(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
+      }
+    }
+    if (nl < 0) return cuda_status(err);
+    p->launches += nl;
+    // each beam has its own plan, hence its own pinned count slot
+    err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (err != cudaSuccess) return cuda_status(err);
+  }
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_status(err);
+  int result = DD_OK;
+  int32_t flag = 0;
+  if (cudaMemcpy(&flag, b->d_error, sizeof(flag), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DD_ERR_CUDA;
+  if (flag != 0) {
+    cudaMemset(b->d_error, 0, sizeof(int32_t));
+    result = DD_ERR_DEVICE_TIMEOUT;
+  }
+  for (int i = 0; i < n; ++i) {
+    dd_plan *p = b->plans[i];
+    const int st = take_device_status(p);
+    if (st != DD_OK && result == DD_OK) result = st;
+    counts[i] = *p->h_total;
+    p->stats_valid = true;
+  }
+  if (result != DD_OK) return result;
+  for (int i = 0; i < n; ++i)
+    if (counts[i] > capacity[i]) return DD_ERR_OVERFLOW;
+  return DD_OK;
 }
 
 extern "C" int dd_get_stats(const dd_plan *p, double *mean, double *sigma) {

@@ -80,6 +80,36 @@ def workload(name: str) -> Workload:
     raise KeyError(name)
 
 
+def batch_workloads(seed: int, maxshift_of, n: int = 32, nchan_choices=(256, 512, 1024, 4096),
+                    nsamp_range=(16384, 131072), ndm_range=(128, 4096)) -> list[Workload]:
+    """A batch of uneven u8 beams (config 4 of the batching row).
+
+    Per beam, drawn with ``default_rng(seed)``: nchan from ``nchan_choices``;
+    nsamp uniform over multiples of 1024 in ``nsamp_range``; ndm uniform over
+    multiples of 128 in ``ndm_range``; band A (416 MHz top, 16 MHz wide,
+    51.2 us) or band B (1500 MHz top, 300 MHz wide, 64 us), channel width =
+    bandwidth / nchan; DM trials 0, 0.1, ...; data and pulses as
+    ``full_block_u8``.  A beam whose largest delay (``maxshift_of(beam)``,
+    supplied by the caller) reaches nsamp / 2 is drawn again.
+    """
+    rng = np.random.default_rng(seed)
+    beams = []
+    while len(beams) < n:
+        nchan = int(rng.choice(nchan_choices))
+        nsamp = 1024 * int(rng.integers(nsamp_range[0] // 1024, nsamp_range[1] // 1024 + 1))
+        ndm = 128 * int(rng.integers(ndm_range[0] // 128, ndm_range[1] // 128 + 1))
+        if rng.integers(0, 2) == 0:
+            f_top, bw, ts = 416.0, 16.0, 51.2e-6
+        else:
+            f_top, bw, ts = 1500.0, 300.0, 64e-6
+        wl = Workload(f"beam{len(beams)}", nchan, nsamp, f_top, bw / nchan, ts,
+                      dm_grid(0.0, 0.1, ndm), "u8", n_pulses=8, pulse_amp=16.0,
+                      pulse_width=(1, 32))
+        if maxshift_of(wl) < nsamp // 2:
+            beams.append(wl)
+    return beams
+
+
 def scaled(wl: Workload, nchan: int | None = None, nsamp: int | None = None,
            ndm: int | None = None) -> Workload:
     """Same band and DM step, smaller sizes (for tests)."""

@@ -1,0 +1,150 @@
+"""GPU: dd_batch_run over uneven beams against dd_run on each beam alone
+(which the other GPU tests pin to the oracle), and directly against the
+oracle on small beams.
+
+The staged u8 beams of a batch share persistent launches (one per DM-tile
+width) whose work queue interleaves the beams; each beam's output, statistics
+and candidates must still be bit-identical to a run of that beam alone.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_1401_8258_gb300 as dd
+import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    dd.build()
+    oracle.build()
+
+
+def maxshift(wl):
+    _, m = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    return m
+
+
+def small_batch(seed, n):
+    return synth.batch_workloads(seed, maxshift, n=n, nchan_choices=(256, 512, 1024),
+                                 nsamp_range=(16384, 24576), ndm_range=(128, 384))
+
+
+def make_beams(workloads, seed):
+    blocks, delays = [], []
+    for i, wl in enumerate(workloads):
+        d, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+        b, _ = synth.make_block(wl, seed + i, d)
+        blocks.append(b)
+        delays.append(d)
+    return blocks, delays
+
+
+def plan_of(wl):
+    return dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, wl.dtype)
+
+
+def run_alone(plan, dblock, nsigma, capacity):
+    out, cands, total = plan.run(dblock, nsigma, capacity=capacity)
+    mean, sigma = plan.stats()
+    return out, cands, total, mean, sigma
+
+
+def assert_batch_matches_alone(workloads, blocks, nsigma, capacity=1 << 16):
+    dblocks = [torch.from_numpy(np.ascontiguousarray(b)).to(DEV) for b in blocks]
+    plans = [plan_of(wl) for wl in workloads]
+    alone = [run_alone(p, b, nsigma, capacity) for p, b in zip(plans, dblocks)]
+    with dd.Batch(plans) as batch:
+        for _ in range(2):  # a second run reuses every buffer
+            outs, cands, totals = batch.run(dblocks, nsigma, capacity=capacity)
+            for i, p in enumerate(plans):
+                out_a, c_a, t_a, m_a, s_a = alone[i]
+                assert totals[i] == t_a, i
+                assert torch.equal(outs[i], out_a), i
+                assert np.array_equal(cands[i], c_a), i
+                mean, sigma = p.stats()
+                assert np.array_equal(mean, m_a) and np.array_equal(sigma, s_a), i
+    staged = [dd._native.dd_plan_kernel_info(p.handle, b, b.stride(0))["staged"]
+              for p, b in zip(plans, dblocks)]
+    for p in plans:
+        p.close()
+    return outs, cands, totals, staged
+
+
+def test_batch_of_uneven_u8_beams_matches_each_beam_alone_and_the_oracle():
+    workloads = small_batch(seed=3, n=7)
+    blocks, delays = make_beams(workloads, seed=40)
+    outs, cands, totals, staged = assert_batch_matches_alone(workloads, blocks, 5.0)
+    assert sum(staged) >= 4  # the shared persistent launches carry most beams
+    for i in (0, len(workloads) - 1):
+        ref = oracle.dedisperse(blocks[i], delays[i])
+        assert np.array_equal(outs[i].cpu().numpy(), ref)
+        mean, sigma = oracle.stats(ref)
+        c, t = oracle.detect(ref, mean, sigma, 5.0)
+        assert totals[i] == t and np.array_equal(cands[i], c)
+
+
+def test_mixed_batch_with_float_and_plain_kernel_beams():
+    wls = small_batch(seed=5, n=3)
+    f32 = synth.scaled(synth.workload("lband_f32"), nchan=512, nsamp=12000, ndm=96)
+    f32.chan_width_mhz = synth.workload("lband_f32").chan_width_mhz
+    wide = synth.scaled(synth.workload("single_beam_f32"), nsamp=4096)
+    wide.dtype = "u8"  # 64 wide channels: no staged tables, plain-load kernel
+    workloads = wls + [f32, wide]
+    blocks, _ = make_beams(workloads, seed=70)
+    _, _, _, staged = assert_batch_matches_alone(workloads, blocks, 4.0)
+    assert staged[-1] == 0 and sum(staged) >= 3
+
+
+def test_batch_capacity_overflow_keeps_each_beams_first_candidates():
+    workloads = small_batch(seed=7, n=4)
+    blocks, _ = make_beams(workloads, seed=90)
+    dblocks = [torch.from_numpy(b).to(DEV) for b in blocks]
+    plans = [plan_of(wl) for wl in workloads]
+    full = [p.run(b, 1.5, capacity=1 << 20) for p, b in zip(plans, dblocks)]
+    with dd.Batch(plans) as batch:
+        outs = [torch.empty_like(f[0]) for f in full]
+        cands = [torch.empty((50, 16), dtype=torch.uint8, device=DEV) for _ in plans]
+        st, totals = dd.dd_batch_run(batch.handle, dblocks, [b.shape[1] for b in blocks],
+                                     [b.shape[1] for b in blocks], outs, 1.5, cands,
+                                     [50] * len(plans))
+        assert st == dd.DD_ERR_OVERFLOW
+        for i, f in enumerate(full):
+            assert totals[i] == f[2] > 50
+            got = cands[i].cpu().numpy().view(dd.CANDIDATE_DTYPE).reshape(-1)
+            assert np.array_equal(got, f[1][:50])
+    for p in plans:
+        p.close()
+
+
+def test_batch_bounded_wait_reports_timeout_and_recovers():
+    """Fault injection on the host: the shared launch queues no copies, its
+    first bounded wait (50 ms) runs out, the batch reports
+    DD_ERR_DEVICE_TIMEOUT, and the next run is exact."""
+    workloads = small_batch(seed=9, n=3)
+    blocks, _ = make_beams(workloads, seed=110)
+    dblocks = [torch.from_numpy(b).to(DEV) for b in blocks]
+    plans = [plan_of(wl) for wl in workloads]
+    alone = [p.run(b, 5.0) for p, b in zip(plans, dblocks)]
+    # the shared launch takes its timeout and fault switch from the costliest
+    # beam's plan (queued first); set them on every plan
+    for p in plans:
+        dd._native.dd_plan_set_wait_timeout(p.handle, 50_000_000)
+        dd._native.dd_plan_inject_fault(p.handle, 1)
+    with dd.Batch(plans) as batch:
+        with pytest.raises(dd.DDError) as e:
+            batch.run(dblocks, 5.0)
+        assert e.value.status == -7
+        for p in plans:
+            dd._native.dd_plan_inject_fault(p.handle, 0)
+        outs, cands, totals = batch.run(dblocks, 5.0)
+        for i, a in enumerate(alone):
+            assert torch.equal(outs[i], a[0]) and totals[i] == a[2]
+            assert np.array_equal(cands[i], a[1])
+    for p in plans:
+        p.close()
