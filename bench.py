@@ -232,7 +232,11 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    wl = load_workload(args)
+    if args.workload == BATCH:
+        # the oracle on the batch's first beam (its rate stands for the batch)
+        wl = synth.batch_workloads(args.seed, lambda w: geometry_oracle(w)[1], n=32)[0]
+    else:
+        wl = load_workload(args)
     delays, mx, nsamp_out = geometry_oracle(wl)
     block, _ = synth.make_block(wl, args.seed, delays)
     per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
@@ -435,10 +439,164 @@ def run_ours(args):
     plan.close()
 
 
+# ------------------------------------------------------------- batch
+
+BATCH = "batch32_u8"  # 32 uneven u8 beams (the batching row's configuration)
+
+
+def batch_workloads(seed):
+    from paper_1401_8258_gb300 import dd_compute_delays
+
+    def maxshift(wl):
+        return dd_compute_delays(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)[1]
+    return synth.batch_workloads(seed, maxshift, n=32)
+
+
+def run_batch(args):
+    """One step = dd_batch_run over 32 uneven beams resident in HBM."""
+    import torch
+
+    import paper_1401_8258_gb300 as dd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dd.build()
+    wls = batch_workloads(args.seed)
+    plans = [dd.Plan(w.nchan, w.f_top_mhz, w.chan_width_mhz, w.t_samp_s, w.dms, "u8", local)
+             for w in wls]
+    host_blocks, blocks, outs, nouts = [], [], [], []
+    for i, (w, p) in enumerate(zip(wls, plans)):
+        b, _ = synth.make_block(w, args.seed + 1000 * (rank + 1) + i, p.delays())
+        host_blocks.append(b)
+        blocks.append(torch.from_numpy(b).to(dev))
+        nouts.append(p.nsamp_out(w.nsamp))
+        outs.append(torch.empty((w.ndm, nouts[-1]), dtype=torch.int32, device=dev))
+    cap = 1 << 16
+    cands = [torch.empty((cap, 16), dtype=torch.uint8, device=dev) for _ in wls]
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    nsamp = [w.nsamp for w in wls]
+    batch = dd.Batch(plans)
+
+    def step():
+        st, totals = dd.dd_batch_run(batch.handle, blocks, nsamp, nsamp, outs, NSIGMA, cands,
+                                     [cap] * len(wls), stream)
+        return sum(totals)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sum(p.launch_count() for p in plans)
+    totals = []
+    for i in range(args.steps):
+        flush.fill_(1.0)
+        starts[i].record(stream)
+        totals.append(step())
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    launches = sum(p.launch_count() for p in plans) - launches0
+    clock = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    t_total = sum(step_ms) / 1e3
+    units = sum(w.ndm * n for w, n in zip(wls, nouts))
+    value = units * args.steps / t_total
+
+    # the same beams one dd_run after another (the per-beam launch baseline)
+    cands1 = torch.empty((cap, 16), dtype=torch.uint8, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for rep in range(2):
+        flush.fill_(1.0)
+        ev0.record(stream)
+        for p, b, o, n in zip(plans, blocks, outs, nsamp):
+            dd.dd_run(p.handle, b, n, n, o, NSIGMA, cands1, cap, stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    per_beam_ms = ev0.elapsed_time(ev1)
+
+    e2e = None
+    if not args.no_e2e:
+        pinned = [torch.from_numpy(b).pin_memory() for b in host_blocks]
+        host_cands = [torch.empty((cap, 16), dtype=torch.uint8).pin_memory() for _ in wls]
+        counts = []
+
+        def e2e_step():
+            for hb, db in zip(pinned, blocks):
+                db.copy_(hb, non_blocking=True)
+            st, tot = dd.dd_batch_run(batch.handle, blocks, nsamp, nsamp, outs, NSIGMA, cands,
+                                      [cap] * len(wls), stream)
+            for hc, c, t in zip(host_cands, cands, tot):
+                if t:
+                    hc[:min(t, cap)].copy_(c[:min(t, cap)], non_blocking=True)
+            torch.cuda.synchronize()
+            counts.append(sum(min(t, cap) for t in tot))
+        e2e_step()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            e2e_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t_e2e = ev0.elapsed_time(ev1) / 1e3
+        e2e = {"value": units * args.steps / t_e2e, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(b.nbytes for b in host_blocks)),
+               "d2h_bytes_per_step": int(8 * len(wls) + 16 * statistics.mean(counts[1:]))}
+
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    adds = float(sum(w.ndm * n * w.nchan for w, n in zip(wls, nouts)))
+    t_step = t_total / args.steps
+    achieved = adds / t_step / 1e12
+    peak = sms * LANES_PER_SM * smax * 1e6 / 1e12
+    staged = sum(dd._native.dd_plan_kernel_info(p.handle, b, n)["staged"]
+                 for p, b, n in zip(plans, blocks, nsamp))
+    algo_bytes = sum(b.nbytes for b in host_blocks) + sum(4 * w.ndm * n for w, n in zip(wls, nouts))
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "whole batch step (shared persistent launches, other beams' kernels, "
+                      "detection)", "kernel_ms": t_step * 1e3,
+            "peak_basis": f"{sms} SMs x {LANES_PER_SM} add lanes x {smax:.0f} MHz (max clock)",
+            "algorithmic_bytes": algo_bytes,
+            "hbm_frac_of_measured": (algo_bytes / t_step / 1e9) / float(peaks.get("hbm_gbs", 6784.5))}
+    cpu = None
+    if not args.no_cpu_baseline:
+        w0 = wls[0]
+        cpu = time_oracle_sample(w0, host_blocks[0], plans[0].delays(), nouts[0], args.cpu_seconds)
+        cpu["sample"] = "beam 0 of the batch: " + cpu["sample"]
+        cpu["cpu_model"] = cpu_model()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": BATCH, "beams": len(wls), "staged_beams": int(staged),
+                   "nchan": [w.nchan for w in wls], "ndm": [w.ndm for w in wls],
+                   "nsamp_in": nsamp, "input_dtype": "u8", "nsigma": NSIGMA,
+                   "parallelism": "replicas1",
+                   "l2": "L2 flushed (256 MiB write) before every timed step"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clock,
+        "gpu_launches": int(launches),
+        "per_beam_dd_run_ms": per_beam_ms,
+        "candidates_per_step": int(statistics.median(totals)),
+    }
+    print(json.dumps(line), flush=True)
+    batch.close()
+    for p in plans:
+        p.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == BATCH:
+        run_batch(args)
     else:
         run_ours(args)
 

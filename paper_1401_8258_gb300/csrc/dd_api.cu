@@ -133,11 +133,13 @@ void destroy_plan(dd_plan *p) {
 }
 
 // Plan-time tables of the staged u8 kernel: 64 DM trials per CTA where the
-// delay patterns allow, else 32; none if neither fits (plain-load kernel).
+// delay patterns allow, else 32, else 16 (wide channels); none if no width
+// fits (plain-load kernel).
 int setup_quad(dd_plan *p) {
   ddq::Tables t;
-  int rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddq::kNdThr, &t);
-  if (rc != 0) rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddq::kNdThr / 2, &t);
+  int rc = 1;
+  for (int nd_thr = ddq::kNdThr; rc != 0 && nd_thr >= ddq::kNdThr / 4; nd_thr /= 2)
+    rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, nd_thr, &t);
   if (rc != 0) return DD_OK;
   QuadDevice *q = new (std::nothrow) QuadDevice();
   if (!q) return DD_ERR_OOM;
@@ -451,8 +453,10 @@ extern "C" int dd_batch_run(dd_batch *b, const void *const *block, const int64_t
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t err = cudaSuccess;
-  // staged u8 beams, by DM-tile width; the rest take their own kernels
-  std::vector<int> staged[2];
+  // staged u8 beams, by DM-tile width (64, 32, 16 trials); the rest take
+  // their own kernels
+  constexpr int kWidths = 3;
+  std::vector<int> staged[kWidths];
   std::vector<char> is_staged(n, 0);
   for (int i = 0; i < n; ++i) {
     dd_plan *p = b->plans[i];
@@ -462,14 +466,15 @@ extern "C" int dd_batch_run(dd_batch *b, const void *const *block, const int64_t
       if (st != DD_OK) return st;
       err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
       if (err != cudaSuccess) return cuda_status(err);
-      staged[p->quad->tables.nd_thr == ddq::kNdThr ? 0 : 1].push_back(i);
+      const int nd_thr = p->quad->tables.nd_thr;
+      staged[nd_thr == ddq::kNdThr ? 0 : (nd_thr == ddq::kNdThr / 2 ? 1 : 2)].push_back(i);
       is_staged[i] = 1;
     } else {
       const int st = dd_execute(p, block[i], nsamp_in[i], pitch_elems[i], out[i], stream);
       if (st != DD_OK) return st;
     }
   }
-  for (int g = 0; g < 2; ++g) {
+  for (int g = 0; g < kWidths; ++g) {
     std::vector<int> &idx = staged[g];
     // costliest beams first (a work item costs about nchan): the queue's
     // tail then holds the cheap items
@@ -488,11 +493,12 @@ extern "C" int dd_batch_run(dd_batch *b, const void *const *block, const int64_t
       }
       dd_plan *p0 = b->plans[idx[lo]];
       const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
-                                            g == 0 ? ddq::kNdThr : ddq::kNdThr / 2, smem,
+                                            ddq::kNdThr >> g, smem,
                                             b->sm_count, b->d_next_item, b->d_error,
                                             p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
       if (nl < 0) return cuda_status(err);
       b->launches += nl;
+      p0->launches += nl;  // counted on the first beam's plan
     }
   }
   // detection per beam, then one synchronisation for every count

@@ -602,7 +602,9 @@ int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int smem, int d
   L.status = status;
   L.timeout_ns = timeout_ns;
   L.skip_copies = skip_copies;
-  auto kern = nd_thr == kNdThr ? dd_dedisperse_quad_u8<kNdThr> : dd_dedisperse_quad_u8<kNdThr / 2>;
+  auto kern = nd_thr == kNdThr       ? dd_dedisperse_quad_u8<kNdThr>
+              : nd_thr == kNdThr / 2 ? dd_dedisperse_quad_u8<kNdThr / 2>
+                                     : dd_dedisperse_quad_u8<kNdThr / 4>;
   *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
   if (*err == cudaSuccess)

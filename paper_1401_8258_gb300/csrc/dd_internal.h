@@ -111,7 +111,8 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
                            cudaError_t *err);
 // The staged kernel is persistent: one launch drains a queue of (beam, DM
 // tile, time tile) items over up to ddq::kMaxBeams beams, which must share
-// nd_thr; smem is the largest of the beams' shared-memory sizes.
+// nd_thr (kNdThr, kNdThr/2 or kNdThr/4); smem is the largest of the beams'
+// shared-memory sizes.
 ddq::Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                     void *out, int64_t *rowsums, int32_t *tilemax);
 int launch_quad_beams(const ddq::Beam *beams, int nbeams, int nd_thr, int smem, int device_sms,

@@ -370,6 +370,29 @@ def test_staged_kernel_row_origin_before_first_sample(geo):
     assert np.array_equal(got, oracle.dedisperse(block, delays, nsamp_in=nsamp))
 
 
+def test_staged_kernel_16_trial_tiles_on_wide_channels():
+    """256 channels of 62.5 kHz in the 400-416 MHz band: relative delays vary
+    too much for 64- or 32-trial tiles, so the plan takes 16-trial tiles."""
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=256, ndm=300)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    nsamp = mx + 1500
+    pitch = (nsamp + 15) // 16 * 16
+    block = synth.random_block(np.random.default_rng(8), wl.nchan, nsamp, "u8", pitch)
+    dblock = _to_dev(block)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as plan:
+        info = dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)
+        assert info["staged"] and info["dms_per_cta"] == 16, info
+        out, cands, total = plan.run(dblock, 3.0, nsamp_in=nsamp)
+        mean, sigma = plan.stats()
+        got = out.cpu().numpy()
+    ref = oracle.dedisperse(block, delays, nsamp_in=nsamp)
+    assert np.array_equal(got, ref)
+    m, s = oracle.stats(ref)
+    assert np.array_equal(mean, m) and np.array_equal(sigma, s)
+    c, t = oracle.detect(ref, m, s, 3.0)
+    assert total == t and np.array_equal(cands, c)
+
+
 def test_staged_kernel_bounded_wait_reports_timeout_and_recovers():
     """Fault injection: the staged kernel queues no copies, so its first
     bounded wait (50 ms) runs out; the launch reports DD_ERR_DEVICE_TIMEOUT
