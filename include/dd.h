@@ -198,6 +198,19 @@ int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp_in, int64_
  * points); used to account for device work. */
 int dd_plan_launch_count(const dd_plan *p, int64_t *launches);
 
+/* Autotuning (plan time).  The thesis sets the accumulators per thread and
+ * threads per block by a hand sweep for its GPU (Sec. 2.4); here each staged
+ * kernel is compiled for several tile widths (u8: 64, 32 or 16 DM trials per
+ * CTA; f16/f32: 128 or 64), and the plan takes the widest whose delay
+ * patterns fit.  dd_plan_autotune instead times every width that fits, on a
+ * scratch block of nsamp_in samples of the plan's geometry (allocated and
+ * freed here; the choice depends on the channel / DM geometry, so a shorter
+ * block tunes faster), and keeps the fastest.  *dms_per_cta receives the
+ * chosen width (0: no staged width fits; the plain-load kernel stays), and
+ * *ms_per_launch (may be NULL) its median time.  Results of dd_execute /
+ * dd_run do not depend on the width.  Synchronous. */
+int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_cta, float *ms_per_launch);
+
 /* Kernel selection: path 0 (default) lets dd_execute take the staged kernel
  * whenever the plan and the block's layout allow it; path 1 forces the
  * plain-load kernel (same results; used to cross-check the two). */

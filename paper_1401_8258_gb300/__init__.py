@@ -127,6 +127,11 @@ class Plan:
             np.zeros(0, dtype=CANDIDATE_DTYPE)
         return out, host, total
 
+    def autotune(self, nsamp_in):
+        """Time every staged tile width that fits and keep the fastest;
+        returns (DM trials per CTA, ms per launch)."""
+        return _native.dd_plan_autotune(self.handle, nsamp_in)
+
     def stats(self):
         return dd_get_stats(self.handle, self.ndm)
 

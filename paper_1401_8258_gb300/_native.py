@@ -67,6 +67,7 @@ SIGNATURES = [
     ("dd_plan_kernel_info", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
     ("dd_detect_noalloc", ctypes.c_int, [_vp, _i32, _i32, _i64, _f32, _vp, _i64, _vp, _vp]),
     ("dd_run", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _f32, _vp, _i64, _vp, _vp, _vp]),
+    ("dd_plan_autotune", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("dd_batch_create", ctypes.c_int, [_vp, _vp, _i32]),
     ("dd_batch_destroy", ctypes.c_int, [_vp]),
     ("dd_batch_run", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp]),
@@ -203,6 +204,14 @@ def dd_run(plan, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity, str
                        _stream(stream), ev)
     _check(st, "dd_run", allow=(DD_ERR_OVERFLOW,))
     return st, int(cnt.value)
+
+
+def dd_plan_autotune(plan, nsamp_in) -> tuple[int, float]:
+    """(DM trials per CTA chosen, its median ms per launch)."""
+    nd, ms = ctypes.c_int32(0), ctypes.c_float(0)
+    _check(load().dd_plan_autotune(plan, int(nsamp_in), ctypes.addressof(nd), ctypes.addressof(ms)),
+           "dd_plan_autotune")
+    return nd.value, ms.value
 
 
 def dd_batch_create(plans) -> int:

@@ -99,20 +99,26 @@ int take_device_status(dd_plan *p) {
   return DD_ERR_DEVICE_TIMEOUT;
 }
 
+void free_quad(QuadDevice *&q) {
+  if (!q) return;
+  free_device(q->d_recs);
+  free_device(q->d_raw_meta);
+  delete q;
+  q = nullptr;
+}
+
+void free_octet(OctetDevice *&q) {
+  if (!q) return;
+  free_device(q->d_recs);
+  free_device(q->d_raw_meta);
+  delete q;
+  q = nullptr;
+}
+
 void destroy_plan(dd_plan *p) {
   if (!p) return;
-  if (p->quad) {
-    free_device(p->quad->d_recs);
-    free_device(p->quad->d_raw_meta);
-    delete p->quad;
-    p->quad = nullptr;
-  }
-  if (p->octet) {
-    free_device(p->octet->d_recs);
-    free_device(p->octet->d_raw_meta);
-    delete p->octet;
-    p->octet = nullptr;
-  }
+  free_quad(p->quad);
+  free_octet(p->octet);
   free_device(p->d_next_item);
   free_device(p->d_delays);
   free_device(p->d_error);
@@ -132,17 +138,17 @@ void destroy_plan(dd_plan *p) {
   delete p;
 }
 
-// Plan-time tables of the staged u8 kernel: 64 DM trials per CTA where the
-// delay patterns allow, else 32, else 16 (wide channels); none if no width
-// fits (plain-load kernel).
-int setup_quad(dd_plan *p) {
+// Tables of the staged u8 kernel for nd_thr trials per thread, on the device;
+// *st = DD_OK and nullptr if the geometry does not fit that width.
+QuadDevice *make_quad(const dd_plan *p, int nd_thr, int *st) {
+  *st = DD_OK;
   ddq::Tables t;
-  int rc = 1;
-  for (int nd_thr = ddq::kNdThr; rc != 0 && nd_thr >= ddq::kNdThr / 4; nd_thr /= 2)
-    rc = ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, nd_thr, &t);
-  if (rc != 0) return DD_OK;
+  if (ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, nd_thr, &t) != 0) return nullptr;
   QuadDevice *q = new (std::nothrow) QuadDevice();
-  if (!q) return DD_ERR_OOM;
+  if (!q) {
+    *st = DD_ERR_OOM;
+    return nullptr;
+  }
   q->tables = std::move(t);
   const size_t rb = q->tables.recs.size() * sizeof(int32_t);
   const size_t mb = q->tables.raw_meta.size() * sizeof(int32_t);
@@ -151,21 +157,25 @@ int setup_quad(dd_plan *p) {
   if (e == cudaSuccess) e = cudaMemcpy(q->d_recs, q->tables.recs.data(), rb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
-  p->quad = q;  // freed with the plan on error
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_next_item, sizeof(unsigned long long));
-  return cuda_status(e);
+  if (e != cudaSuccess) {
+    free_quad(q);
+    *st = cuda_status(e);
+  }
+  return q;
 }
 
-// Plan-time tables of the staged f16/f32 kernel: 64 DM trials per CTA where
-// the delay patterns allow, else 32; none if neither fits (plain-load kernel).
-int setup_octet(dd_plan *p) {
-  const int esize = p->dtype == DD_F16 ? 2 : 4;
+// Same for the staged f16/f32 kernel.
+OctetDevice *make_octet(const dd_plan *p, int nd_thr, int *st) {
+  *st = DD_OK;
   ddo::Tables t;
-  int rc = ddo::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddo::kNdThr, esize, &t);
-  if (rc != 0) rc = ddo::build_tables(p->h_delays.data(), p->nchan, p->ndm, ddo::kNdThr / 2, esize, &t);
-  if (rc != 0) return DD_OK;
+  const int esize = p->dtype == DD_F16 ? 2 : 4;
+  if (ddo::build_tables(p->h_delays.data(), p->nchan, p->ndm, nd_thr, esize, &t) != 0)
+    return nullptr;
   OctetDevice *q = new (std::nothrow) OctetDevice();
-  if (!q) return DD_ERR_OOM;
+  if (!q) {
+    *st = DD_ERR_OOM;
+    return nullptr;
+  }
   q->tables = std::move(t);
   const size_t rb = q->tables.recs.size() * sizeof(int32_t);
   const size_t mb = q->tables.raw_meta.size() * sizeof(int32_t);
@@ -174,8 +184,40 @@ int setup_octet(dd_plan *p) {
   if (e == cudaSuccess) e = cudaMemcpy(q->d_recs, q->tables.recs.data(), rb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
-  p->octet = q;  // freed with the plan on error
-  return cuda_status(e);
+  if (e != cudaSuccess) {
+    free_octet(q);
+    *st = cuda_status(e);
+  }
+  return q;
+}
+
+// Widths (trials per thread) a staged kernel of this plan may take, widest
+// first: u8 64 / 32 / 16 trials per CTA, f16/f32 128 / 64.
+std::vector<int> staged_widths(const dd_plan *p) {
+  if (p->dtype == DD_U8) return {ddq::kNdThr, ddq::kNdThr / 2, ddq::kNdThr / 4};
+  return {ddo::kNdThr, ddo::kNdThr / 2};
+}
+
+// Plan-time tables of the staged kernels: the widest width whose delay
+// patterns fit; none if no width fits (plain-load kernel).
+int setup_quad(dd_plan *p) {
+  int st = DD_OK;
+  for (int w : staged_widths(p)) {
+    p->quad = make_quad(p, w, &st);
+    if (p->quad || st != DD_OK) break;
+  }
+  if (st == DD_OK && p->quad && cudaMalloc(&p->d_next_item, sizeof(unsigned long long)) != cudaSuccess)
+    st = DD_ERR_OOM;
+  return st;
+}
+
+int setup_octet(dd_plan *p) {
+  int st = DD_OK;
+  for (int w : staged_widths(p)) {
+    p->octet = make_octet(p, w, &st);
+    if (p->octet || st != DD_OK) break;
+  }
+  return st;
 }
 
 int validate_execute(const dd_plan *p, int64_t nsamp_in, int64_t pitch, int64_t *nsamp_out) {
@@ -619,6 +661,94 @@ extern "C" int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp
     if (e != cudaSuccess) return cuda_status(e);
   }
   return dst;
+}
+
+extern "C" int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_cta,
+                                float *ms_per_launch) {
+  if (!p || !dms_per_cta) return DD_ERR_ARG;
+  *dms_per_cta = 0;
+  if (ms_per_launch) *ms_per_launch = 0.f;
+  if (nsamp_in <= p->maxshift) return DD_ERR_SIZE;
+  const int64_t nsamp_out = nsamp_in - p->maxshift;
+  if (nsamp_out > INT32_MAX) return DD_ERR_SIZE;
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const int es = ddk::elem_size(p->dtype);
+  const int64_t pitch = (nsamp_in * es + 15) / 16 * 16 / es;
+  const size_t in_bytes = static_cast<size_t>(p->nchan) * pitch * es;
+  const size_t out_bytes = static_cast<size_t>(p->ndm) * nsamp_out * 4;
+  void *blk = nullptr, *out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e = cudaMalloc(&blk, in_bytes);
+  if (e == cudaSuccess) e = cudaMalloc(&out, out_bytes);
+  if (e == cudaSuccess) e = cudaMemset(blk, 0x3c, in_bytes);  // any finite data times alike
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  const bool u8 = p->dtype == DD_U8;
+  QuadDevice *best_q = nullptr;
+  OctetDevice *best_o = nullptr;
+  float best_ms = 0.f;
+  int st = cuda_status(e);
+  for (int w : staged_widths(p)) {
+    if (st != DD_OK) break;
+    QuadDevice *q = u8 ? make_quad(p, w, &st) : nullptr;
+    OctetDevice *o = u8 ? nullptr : make_octet(p, w, &st);
+    if (!q && !o) continue;
+    QuadDevice *keep_q = p->quad;
+    OctetDevice *keep_o = p->octet;
+    p->quad = q ? q : p->quad;
+    p->octet = o ? o : p->octet;
+    float times[4] = {0, 0, 0, 0};
+    for (int r = 0; r < 4 && st == DD_OK; ++r) {  // one warm-up, three timed
+      cudaError_t le = cudaSuccess;
+      e = cudaEventRecord(e0, s);
+      const int n = u8 ? ddk::launch_dedisperse_quad(p, blk, pitch, nsamp_out, out, nullptr,
+                                                     nullptr, s, &le)
+                       : ddk::launch_dedisperse_octet(p, blk, pitch, nsamp_out, out, s, &le);
+      if (n < 0) e = le;
+      if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+      if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&times[r], e0, e1);
+      st = cuda_status(e);
+    }
+    p->quad = keep_q;
+    p->octet = keep_o;
+    std::sort(times + 1, times + 4);
+    if (st == DD_OK && (!(best_q || best_o) || times[2] < best_ms)) {
+      free_quad(best_q);
+      free_octet(best_o);
+      best_q = q;
+      best_o = o;
+      best_ms = times[2];
+    } else {
+      free_quad(q);
+      free_octet(o);
+    }
+  }
+  if (st == DD_OK && take_device_status(p) != DD_OK) st = DD_ERR_DEVICE_TIMEOUT;
+  if (st == DD_OK && (best_q || best_o)) {
+    if (best_q) {
+      free_quad(p->quad);
+      p->quad = best_q;
+      *dms_per_cta = best_q->tables.nd_cta;
+    } else {
+      free_octet(p->octet);
+      p->octet = best_o;
+      *dms_per_cta = best_o->tables.nd_cta;
+    }
+    if (ms_per_launch) *ms_per_launch = best_ms;
+  } else {
+    free_quad(best_q);
+    free_octet(best_o);
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  free_device(blk);
+  free_device(out);
+  return st;
 }
 
 extern "C" int dd_plan_set_path(dd_plan *p, int32_t path) {

@@ -161,3 +161,34 @@ def test_run_records_the_phase_event():
         end.record()
         torch.cuda.synchronize()
         assert 0.0 < start.elapsed_time(mid) <= start.elapsed_time(end)
+
+
+@pytest.mark.parametrize("name,nchan,ndm,dtype", [
+    ("full_block_u8", 1024, 256, "u8"),
+    ("lband_f32", 1024, 256, "f32"),
+    ("lband_f32", 512, 192, "f16"),
+])
+def test_autotune_keeps_results_identical(name, nchan, ndm, dtype):
+    """The plan's tile width is chosen by timing; no width changes a result
+    (integer sums are exact, and the float kernel's summation order per output
+    does not depend on the tiling)."""
+    base = synth.workload(name)
+    wl = synth.scaled(base, nchan=nchan, ndm=ndm)
+    wl.chan_width_mhz = base.chan_width_mhz
+    wl.dtype = dtype
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    wl.nsamp = mx + 3000
+    pitch = (wl.nsamp + 15) // 16 * 16
+    block, _ = synth.make_block(wl, seed=6, delays=delays, pitch=pitch)
+    dblock = torch.from_numpy(block).to(DEV)
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, dtype) as plan:
+        assert dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)["staged"]
+        before = plan.run(dblock, 4.0, nsamp_in=wl.nsamp)
+        nd, ms = plan.autotune(wl.nsamp)
+        assert nd in ((64, 32, 16) if dtype == "u8" else (128, 64)) and ms > 0
+        print(f"{name} {dtype}: autotune chose {nd} trials per CTA ({ms:.3f} ms)")
+        info = dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)
+        assert info["staged"] and info["dms_per_cta"] == nd
+        after = plan.run(dblock, 4.0, nsamp_in=wl.nsamp)
+    assert torch.equal(before[0], after[0])
+    assert before[2] == after[2] and np.array_equal(before[1], after[1])
