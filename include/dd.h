@@ -175,6 +175,31 @@ int dd_batch_run(dd_batch *b, const void *const *block, const int64_t *nsamp_in,
                  dd_candidate *const *cands, const int64_t *capacity, int64_t *counts,
                  void *stream);
 
+/* Streams (Sec. 3.4: each block is dedispersed together with the previous
+ * block's last maxshift samples, kept on the device, so that the output runs
+ * on without gaps).  A stream belongs to one plan and takes blocks of
+ * `block_samples` samples per channel; before its first block the history is
+ * zeros.  Push k of a stream writes out[ndm][block_samples] = the dedispersed
+ * samples k*block_samples - maxshift .. (k+1)*block_samples - maxshift - 1 of
+ * the stream (zeros before sample 0), with detection as in dd_run.
+ *
+ * dd_stream_bytes: device bytes one stream of this plan and block length
+ * needs (its double buffer, one output block, detection workspace), for
+ * admission against free memory.
+ * dd_streams_push: one block for each of n streams (distinct plans, one
+ * device) in one wave -- block[i] a device array [nchan][pitch_elems[i]] of
+ * the plan's dtype, out[i], cands[i], capacity[i], counts[i] as for
+ * dd_batch_run; the staged u8 beams of the wave share persistent launches.
+ * Synchronises `stream` once; status codes as for dd_batch_run. */
+typedef struct dd_stream dd_stream;
+int dd_stream_bytes(const dd_plan *p, int64_t block_samples, int64_t *bytes);
+int dd_stream_create(dd_stream **out, dd_plan *p, int64_t block_samples);
+int dd_stream_destroy(dd_stream *s);
+int dd_streams_push(dd_stream *const *streams, int32_t n, const void *const *block,
+                    const int64_t *pitch_elems, void *const *out, float nsigma,
+                    dd_candidate *const *cands, const int64_t *capacity, int64_t *counts,
+                    void *stream);
+
 /* Host copies of the per-DM mean and rms computed by the last dd_detect,
  * dd_run or dd_batch_run on this plan (double[ndm] each; either pointer may
  * be NULL). */

@@ -25,7 +25,8 @@ __all__ = [
     "DD_ERR_OVERFLOW", "DTYPE_CODES", "dd_compute_delays", "dd_plan_create", "dd_plan_destroy",
     "dd_plan_max_delay", "dd_plan_nsamp_out", "dd_plan_delays", "dd_execute", "dd_detect",
     "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
-    "dd_run", "Batch", "dd_batch_create", "dd_batch_destroy", "dd_batch_run",
+    "dd_run", "Batch", "dd_batch_create", "dd_batch_destroy", "dd_batch_run", "Stream",
+    "push_streams",
 ]
 
 _TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
@@ -184,3 +185,63 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+class Stream:
+    """Block-by-block dedispersion of one beam with its overlap tail kept on
+    the device (dd_stream_*); keeps its plan alive."""
+
+    def __init__(self, plan, block_samples):
+        self.plan = plan
+        self.block_samples = int(block_samples)
+        self.handle = _native.dd_stream_create(plan.handle, self.block_samples)
+
+    @staticmethod
+    def bytes_needed(plan, block_samples) -> int:
+        return _native.dd_stream_bytes(plan.handle, block_samples)
+
+    def push(self, block, nsigma, capacity=1 << 16, out=None, stream=None):
+        """One block [nchan][>= block_samples]; returns (out, candidates, total)."""
+        outs, cands, totals = push_streams([self], [block], nsigma, capacity,
+                                           None if out is None else [out], stream)
+        return outs[0], cands[0], totals[0]
+
+    def close(self):
+        if self.handle:
+            _native.dd_stream_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def push_streams(streams, blocks, nsigma, capacity=1 << 16, outs=None, stream=None):
+    """One wave: a block for each stream (distinct plans); returns
+    ``(outs, candidate arrays, totals)``."""
+    import torch
+    n = len(streams)
+    if outs is None:
+        outs = [torch.empty((s.plan.ndm, s.block_samples), dtype=s.plan.out_torch_dtype,
+                            device=b.device) for s, b in zip(streams, blocks)]
+    caps = [int(capacity)] * n if np.isscalar(capacity) else [int(c) for c in capacity]
+    cands = [torch.empty((max(c, 1), 16), dtype=torch.uint8, device=b.device)
+             for c, b in zip(caps, blocks)]
+    st, totals = _native.dd_streams_push([s.handle for s in streams], blocks,
+                                         [b.stride(0) for b in blocks], outs, nsigma,
+                                         [c if k else None for c, k in zip(cands, caps)], caps,
+                                         stream)
+    hosts = []
+    for c, k, t in zip(cands, caps, totals):
+        m = min(t, k)
+        hosts.append(c[:m].cpu().numpy().view(CANDIDATE_DTYPE).reshape(-1) if m else
+                     np.zeros(0, dtype=CANDIDATE_DTYPE))
+    return outs, hosts, totals

@@ -68,6 +68,10 @@ SIGNATURES = [
     ("dd_detect_noalloc", ctypes.c_int, [_vp, _i32, _i32, _i64, _f32, _vp, _i64, _vp, _vp]),
     ("dd_run", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _f32, _vp, _i64, _vp, _vp, _vp]),
     ("dd_plan_autotune", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("dd_stream_bytes", ctypes.c_int, [_vp, _i64, _vp]),
+    ("dd_stream_create", ctypes.c_int, [_vp, _vp, _i64]),
+    ("dd_stream_destroy", ctypes.c_int, [_vp]),
+    ("dd_streams_push", ctypes.c_int, [_vp, _i32, _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp]),
     ("dd_batch_create", ctypes.c_int, [_vp, _vp, _i32]),
     ("dd_batch_destroy", ctypes.c_int, [_vp]),
     ("dd_batch_run", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp]),
@@ -212,6 +216,40 @@ def dd_plan_autotune(plan, nsamp_in) -> tuple[int, float]:
     _check(load().dd_plan_autotune(plan, int(nsamp_in), ctypes.addressof(nd), ctypes.addressof(ms)),
            "dd_plan_autotune")
     return nd.value, ms.value
+
+
+def dd_stream_bytes(plan, block_samples) -> int:
+    v = ctypes.c_int64(0)
+    _check(load().dd_stream_bytes(plan, int(block_samples), ctypes.addressof(v)), "dd_stream_bytes")
+    return int(v.value)
+
+
+def dd_stream_create(plan, block_samples) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dd_stream_create(ctypes.addressof(h), plan, int(block_samples)),
+           "dd_stream_create")
+    return h.value
+
+
+def dd_stream_destroy(stream_handle) -> None:
+    _check(load().dd_stream_destroy(stream_handle), "dd_stream_destroy")
+
+
+def dd_streams_push(streams, blocks, pitch_elems, outs, nsigma, cands, capacity,
+                    stream=None) -> tuple[int, list[int]]:
+    """One wave: a block per stream handle; returns ``(status, counts)``."""
+    n = len(streams)
+    vp_arr, i64_arr = ctypes.c_void_p * n, ctypes.c_int64 * n
+    st_ = vp_arr(*[int(x) for x in streams])
+    b_ = vp_arr(*[_addr(x) for x in blocks])
+    o_ = vp_arr(*[_addr(x) for x in outs])
+    c_ = vp_arr(*[_addr(x) if x is not None else None for x in cands])
+    pe = i64_arr(*[int(x) for x in pitch_elems])
+    cap = i64_arr(*[int(x) for x in capacity])
+    cnt = i64_arr()
+    st = load().dd_streams_push(st_, n, b_, pe, o_, float(nsigma), c_, cap, cnt, _stream(stream))
+    _check(st, "dd_streams_push", allow=(DD_ERR_OVERFLOW,))
+    return st, [int(x) for x in cnt]
 
 
 def dd_batch_create(plans) -> int:

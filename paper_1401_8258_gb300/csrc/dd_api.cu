@@ -422,6 +422,122 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
 }
 
+// The body of dd_batch_run and dd_streams_push: n beams (distinct plans on
+// `device`), staged u8 beams through shared persistent launches that use
+// the work-queue head `next_item` and status word `status`, the rest through
+// their own kernels; detection per beam; one synchronisation.
+int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
+              unsigned long long *next_item, int32_t *status, const void *const *block,
+              const int64_t *nsamp_in, const int64_t *pitch_elems, void *const *out, float nsigma,
+              dd_candidate *const *cands, const int64_t *capacity, int64_t *counts, void *stream) {
+  if (!block || !nsamp_in || !pitch_elems || !out || !cands || !capacity || !counts)
+    return DD_ERR_ARG;
+  if (!std::isfinite(nsigma)) return DD_ERR_ARG;
+  std::vector<int64_t> nout(n);
+  for (int i = 0; i < n; ++i) {
+    counts[i] = 0;
+    if (!block[i] || !out[i] || capacity[i] < 0 || (capacity[i] > 0 && !cands[i]))
+      return DD_ERR_ARG;
+    const int st = validate_execute(plans[i], nsamp_in[i], pitch_elems[i], &nout[i]);
+    if (st != DD_OK) return st;
+  }
+  DeviceScope scope(device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t err = cudaSuccess;
+  // staged u8 beams, by DM-tile width (64, 32, 16 trials); the rest take
+  // their own kernels
+  constexpr int kWidths = 3;
+  std::vector<int> staged[kWidths];
+  std::vector<char> is_staged(n, 0);
+  for (int i = 0; i < n; ++i) {
+    dd_plan *p = plans[i];
+    p->stats_valid = false;
+    if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
+      const int st = ensure_tile_workspace(p, static_cast<size_t>(ddk::time_tiles(nout[i])) * p->ndm);
+      if (st != DD_OK) return st;
+      err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
+      if (err != cudaSuccess) return cuda_status(err);
+      const int nd_thr = p->quad->tables.nd_thr;
+      staged[nd_thr == ddq::kNdThr ? 0 : (nd_thr == ddq::kNdThr / 2 ? 1 : 2)].push_back(i);
+      is_staged[i] = 1;
+    } else {
+      const int st = dd_execute(p, block[i], nsamp_in[i], pitch_elems[i], out[i], stream);
+      if (st != DD_OK) return st;
+    }
+  }
+  for (int g = 0; g < kWidths; ++g) {
+    std::vector<int> &idx = staged[g];
+    // costliest beams first (a work item costs about nchan): the queue's
+    // tail then holds the cheap items
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+      return plans[x]->nchan > plans[y]->nchan;
+    });
+    for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
+      const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
+      std::vector<ddq::Beam> beams;
+      int smem = 0;
+      for (size_t k = lo; k < hi; ++k) {
+        dd_plan *p = plans[idx[k]];
+        beams.push_back(ddk::quad_beam(p, block[idx[k]], pitch_elems[idx[k]], nout[idx[k]],
+                                       out[idx[k]], p->d_rowsums, p->d_tilemax));
+        smem = std::max(smem, static_cast<int>(p->quad->tables.smem_bytes));
+      }
+      dd_plan *p0 = plans[idx[lo]];
+      const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
+                                            ddq::kNdThr >> g, smem,
+                                            sm_count, next_item, status,
+                                            p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
+      if (nl < 0) return cuda_status(err);
+            p0->launches += nl;  // counted on the first beam's plan
+    }
+  }
+  // detection per beam, then one synchronisation for every count
+  for (int i = 0; i < n; ++i) {
+    dd_plan *p = plans[i];
+    int nl;
+    if (is_staged[i]) {
+      nl = ddk::launch_tiled_detect(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
+    } else {
+      const int64_t nchunks = (nout[i] + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
+      const int st = ensure_chunk_workspace(p, static_cast<size_t>(nchunks) * p->ndm);
+      if (st != DD_OK) return st;
+      nl = ddk::launch_stats(p, out[i], nout[i], nsigma, s, &err);
+      if (nl >= 0) {
+        p->launches += nl;
+        nl = ddk::launch_candidates(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
+      }
+    }
+    if (nl < 0) return cuda_status(err);
+    p->launches += nl;
+    // each beam has its own plan, hence its own pinned count slot
+    err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (err != cudaSuccess) return cuda_status(err);
+  }
+  err = cudaStreamSynchronize(s);
+  if (err != cudaSuccess) return cuda_status(err);
+  int result = DD_OK;
+  int32_t flag = 0;
+  if (cudaMemcpy(&flag, status, sizeof(flag), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return DD_ERR_CUDA;
+  if (flag != 0) {
+    cudaMemset(status, 0, sizeof(int32_t));
+    result = DD_ERR_DEVICE_TIMEOUT;
+  }
+  for (int i = 0; i < n; ++i) {
+    dd_plan *p = plans[i];
+    const int st = take_device_status(p);
+    if (st != DD_OK && result == DD_OK) result = st;
+    counts[i] = *p->h_total;
+    p->stats_valid = true;
+  }
+  if (result != DD_OK) return result;
+  for (int i = 0; i < n; ++i)
+    if (counts[i] > capacity[i]) return DD_ERR_OVERFLOW;
+  return DD_OK;
+}
+
+
 struct dd_batch {
   int device = 0;
   int sm_count = 0;
@@ -479,113 +595,148 @@ extern "C" int dd_batch_run(dd_batch *b, const void *const *block, const int64_t
                             const int64_t *pitch_elems, void *const *out, float nsigma,
                             dd_candidate *const *cands, const int64_t *capacity, int64_t *counts,
                             void *stream) {
-  if (!b || !block || !nsamp_in || !pitch_elems || !out || !cands || !capacity || !counts)
-    return DD_ERR_ARG;
-  if (!std::isfinite(nsigma)) return DD_ERR_ARG;
-  const int n = static_cast<int>(b->plans.size());
-  std::vector<int64_t> nout(n);
-  for (int i = 0; i < n; ++i) {
-    counts[i] = 0;
-    if (!block[i] || !out[i] || capacity[i] < 0 || (capacity[i] > 0 && !cands[i]))
-      return DD_ERR_ARG;
-    const int st = validate_execute(b->plans[i], nsamp_in[i], pitch_elems[i], &nout[i]);
-    if (st != DD_OK) return st;
-  }
-  DeviceScope scope(b->device);
-  if (!scope.ok()) return DD_ERR_CUDA;
-  const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  cudaError_t err = cudaSuccess;
-  // staged u8 beams, by DM-tile width (64, 32, 16 trials); the rest take
-  // their own kernels
-  constexpr int kWidths = 3;
-  std::vector<int> staged[kWidths];
-  std::vector<char> is_staged(n, 0);
-  for (int i = 0; i < n; ++i) {
-    dd_plan *p = b->plans[i];
-    p->stats_valid = false;
-    if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
-      const int st = ensure_tile_workspace(p, static_cast<size_t>(ddk::time_tiles(nout[i])) * p->ndm);
-      if (st != DD_OK) return st;
-      err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
-      if (err != cudaSuccess) return cuda_status(err);
-      const int nd_thr = p->quad->tables.nd_thr;
-      staged[nd_thr == ddq::kNdThr ? 0 : (nd_thr == ddq::kNdThr / 2 ? 1 : 2)].push_back(i);
-      is_staged[i] = 1;
-    } else {
-      const int st = dd_execute(p, block[i], nsamp_in[i], pitch_elems[i], out[i], stream);
-      if (st != DD_OK) return st;
-    }
-  }
-  for (int g = 0; g < kWidths; ++g) {
-    std::vector<int> &idx = staged[g];
-    // costliest beams first (a work item costs about nchan): the queue's
-    // tail then holds the cheap items
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-      return b->plans[x]->nchan > b->plans[y]->nchan;
-    });
-    for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
-      const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
-      std::vector<ddq::Beam> beams;
-      int smem = 0;
-      for (size_t k = lo; k < hi; ++k) {
-        dd_plan *p = b->plans[idx[k]];
-        beams.push_back(ddk::quad_beam(p, block[idx[k]], pitch_elems[idx[k]], nout[idx[k]],
-                                       out[idx[k]], p->d_rowsums, p->d_tilemax));
-        smem = std::max(smem, static_cast<int>(p->quad->tables.smem_bytes));
-      }
-      dd_plan *p0 = b->plans[idx[lo]];
-      const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
-                                            ddq::kNdThr >> g, smem,
-                                            b->sm_count, b->d_next_item, b->d_error,
-                                            p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
-      if (nl < 0) return cuda_status(err);
-      b->launches += nl;
-      p0->launches += nl;  // counted on the first beam's plan
-    }
-  }
-  // detection per beam, then one synchronisation for every count
-  for (int i = 0; i < n; ++i) {
-    dd_plan *p = b->plans[i];
-    int nl;
-    if (is_staged[i]) {
-      nl = ddk::launch_tiled_detect(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
-    } else {
-      const int64_t nchunks = (nout[i] + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
-      const int st = ensure_chunk_workspace(p, static_cast<size_t>(nchunks) * p->ndm);
-      if (st != DD_OK) return st;
-      nl = ddk::launch_stats(p, out[i], nout[i], nsigma, s, &err);
-      if (nl >= 0) {
-        p->launches += nl;
-        nl = ddk::launch_candidates(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
-      }
-    }
-    if (nl < 0) return cuda_status(err);
-    p->launches += nl;
-    // each beam has its own plan, hence its own pinned count slot
-    err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
-    if (err != cudaSuccess) return cuda_status(err);
-  }
-  err = cudaStreamSynchronize(s);
-  if (err != cudaSuccess) return cuda_status(err);
-  int result = DD_OK;
-  int32_t flag = 0;
-  if (cudaMemcpy(&flag, b->d_error, sizeof(flag), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return DD_ERR_CUDA;
-  if (flag != 0) {
-    cudaMemset(b->d_error, 0, sizeof(int32_t));
-    result = DD_ERR_DEVICE_TIMEOUT;
-  }
-  for (int i = 0; i < n; ++i) {
-    dd_plan *p = b->plans[i];
-    const int st = take_device_status(p);
-    if (st != DD_OK && result == DD_OK) result = st;
-    counts[i] = *p->h_total;
-    p->stats_valid = true;
-  }
-  if (result != DD_OK) return result;
-  for (int i = 0; i < n; ++i)
-    if (counts[i] > capacity[i]) return DD_ERR_OVERFLOW;
+  if (!b) return DD_ERR_ARG;
+  return run_beams(b->plans.data(), static_cast<int>(b->plans.size()), b->device, b->sm_count,
+                   b->d_next_item, b->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands,
+                   capacity, counts, stream);
+}
+
+// Streaming (Sec. 3.4): each push dedisperses the previous push's last
+// maxshift samples followed by the new block, so consecutive pushes give
+// consecutive output samples.
+struct dd_stream {
+  dd_plan *plan = nullptr;
+  int64_t block = 0;   // samples per push
+  int64_t pitch = 0;   // elements per channel row of each buffer (16-byte multiple)
+  void *buf[2] = {nullptr, nullptr};  // [nchan][pitch]: tail (maxshift samples), then the block
+  int cur = 0;                        // buffer whose first maxshift samples hold the tail
+  unsigned long long *d_next_item = nullptr;
+  int32_t *d_error = nullptr;
+};
+
+namespace {
+
+int64_t stream_pitch(const dd_plan *p, int64_t block) {
+  const int64_t per16 = 16 / ddk::elem_size(p->dtype);
+  return (p->maxshift + block + per16 - 1) / per16 * per16;
+}
+
+void free_stream(dd_stream *s) {
+  if (!s) return;
+  free_device(s->buf[0]);
+  free_device(s->buf[1]);
+  free_device(s->d_next_item);
+  free_device(s->d_error);
+  delete s;
+}
+
+}  // namespace
+
+extern "C" int dd_stream_bytes(const dd_plan *p, int64_t block_samples, int64_t *bytes) {
+  if (!p || !bytes || block_samples < 1) return DD_ERR_ARG;
+  const int64_t es = ddk::elem_size(p->dtype);
+  const int64_t pitch = stream_pitch(p, block_samples);
+  const int64_t tiles = ddk::time_tiles(block_samples);
+  const int64_t chunks = (block_samples + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
+  *bytes = 2 * static_cast<int64_t>(p->nchan) * pitch * es          // double buffer
+           + static_cast<int64_t>(p->ndm) * block_samples * 4        // output
+           + static_cast<int64_t>(p->ndm) * (2 * tiles * 4 + 4 * 8)  // tile maxima, counts, rows
+           + static_cast<int64_t>(p->ndm) * chunks * 16              // chunk counts (plain path)
+           + static_cast<int64_t>(p->ndm) * static_cast<int64_t>(sizeof(dd_row_stats));
   return DD_OK;
+}
+
+extern "C" int dd_stream_create(dd_stream **out, dd_plan *p, int64_t block_samples) {
+  if (!out) return DD_ERR_ARG;
+  *out = nullptr;
+  if (!p || block_samples < 1) return DD_ERR_ARG;
+  if (p->maxshift + block_samples > INT32_MAX) return DD_ERR_SIZE;
+  dd_stream *s = new (std::nothrow) dd_stream();
+  if (!s) return DD_ERR_OOM;
+  s->plan = p;
+  s->block = block_samples;
+  s->pitch = stream_pitch(p, block_samples);
+  DeviceScope scope(p->device);
+  if (!scope.ok()) {
+    delete s;
+    return DD_ERR_CUDA;
+  }
+  const size_t bytes = static_cast<size_t>(p->nchan) * s->pitch * ddk::elem_size(p->dtype);
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&s->buf[k], bytes);
+    if (e == cudaSuccess) e = cudaMemset(s->buf[k], 0, bytes);  // no samples before the first block
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_next_item, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&s->d_error, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMemset(s->d_error, 0, sizeof(int32_t));
+  if (e != cudaSuccess) {
+    free_stream(s);
+    return cuda_status(e);
+  }
+  *out = s;
+  return DD_OK;
+}
+
+extern "C" int dd_stream_destroy(dd_stream *s) {
+  if (!s) return DD_OK;
+  DeviceScope scope(s->plan->device);
+  if (scope.ok()) cudaDeviceSynchronize();
+  free_stream(s);
+  return DD_OK;
+}
+
+extern "C" int dd_streams_push(dd_stream *const *streams, int32_t n, const void *const *block,
+                               const int64_t *pitch_elems, void *const *out, float nsigma,
+                               dd_candidate *const *cands, const int64_t *capacity,
+                               int64_t *counts, void *stream) {
+  if (!streams || n < 1 || !block || !pitch_elems) return DD_ERR_ARG;
+  std::vector<dd_plan *> plans(n);
+  std::vector<const void *> bufs(n);
+  std::vector<int64_t> nin(n), pitch(n);
+  for (int i = 0; i < n; ++i) {
+    dd_stream *st = streams[i];
+    if (!st || !block[i] || pitch_elems[i] < st->block) return DD_ERR_ARG;
+    if (st->plan->device != streams[0]->plan->device) return DD_ERR_ARG;
+    for (int j = 0; j < i; ++j)
+      if (streams[j]->plan == st->plan) return DD_ERR_ARG;  // one stream per plan in a wave
+    plans[i] = st->plan;
+    bufs[i] = st->buf[st->cur];
+    nin[i] = st->plan->maxshift + st->block;
+    pitch[i] = st->pitch;
+  }
+  DeviceScope scope(plans[0]->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t cs = static_cast<cudaStream_t>(stream);
+  // the new block behind each tail
+  for (int i = 0; i < n; ++i) {
+    dd_stream *st = streams[i];
+    const size_t es = ddk::elem_size(st->plan->dtype);
+    uint8_t *dst = static_cast<uint8_t *>(st->buf[st->cur]) + st->plan->maxshift * es;
+    const cudaError_t e = cudaMemcpy2DAsync(dst, st->pitch * es, block[i], pitch_elems[i] * es,
+                                            st->block * es, st->plan->nchan,
+                                            cudaMemcpyDeviceToDevice, cs);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  const int rc = run_beams(plans.data(), n, plans[0]->device, plans[0]->sm_count,
+                           streams[0]->d_next_item, streams[0]->d_error, bufs.data(), nin.data(),
+                           pitch.data(), out, nsigma, cands, capacity, counts, stream);
+  if (rc != DD_OK && rc != DD_ERR_OVERFLOW) return rc;
+  // the last maxshift samples become the next push's tail, in the other buffer
+  for (int i = 0; i < n; ++i) {
+    dd_stream *st = streams[i];
+    const size_t es = ddk::elem_size(st->plan->dtype);
+    const int64_t tail = st->plan->maxshift;
+    if (tail > 0) {
+      const uint8_t *src = static_cast<const uint8_t *>(st->buf[st->cur]) + st->block * es;
+      const cudaError_t e = cudaMemcpy2DAsync(st->buf[1 - st->cur], st->pitch * es, src,
+                                              st->pitch * es, tail * es, st->plan->nchan,
+                                              cudaMemcpyDeviceToDevice, cs);
+      if (e != cudaSuccess) return cuda_status(e);
+    }
+    st->cur = 1 - st->cur;
+  }
+  return rc;
 }
 
 extern "C" int dd_get_stats(const dd_plan *p, double *mean, double *sigma) {
