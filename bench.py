@@ -232,9 +232,10 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    if args.workload == BATCH:
-        # the oracle on the batch's first beam (its rate stands for the batch)
-        wl = synth.batch_workloads(args.seed, lambda w: geometry_oracle(w)[1], n=32)[0]
+    if args.workload in (BATCH, SERVE):
+        # the oracle on the first beam (its rate stands for the set)
+        gen = synth.batch_workloads if args.workload == BATCH else synth.serving_workloads
+        wl = gen(args.seed, lambda w: geometry_oracle(w)[1])[0]
     else:
         wl = load_workload(args)
     delays, mx, nsamp_out = geometry_oracle(wl)
@@ -591,12 +592,160 @@ def run_batch(args):
         p.close()
 
 
+# ----------------------------------------------------------- serving
+
+SERVE = "serve64_u8"  # 64 beams streaming 1 s blocks (the serving row's configuration)
+
+
+def serving_workloads(seed):
+    from paper_1401_8258_gb300 import dd_compute_delays
+
+    def maxshift(wl):
+        return dd_compute_delays(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)[1]
+    return synth.serving_workloads(seed, maxshift, n=64)
+
+
+def run_serve(args):
+    """Streaming service over 64 beams with 1 s blocks.
+
+    Beams are admitted while their bytes (dd_stream_bytes + candidate and
+    input buffers) fit 80% of free HBM.  Block k of beam b arrives at
+    phase_b + k seconds (phases uniform in [0, 1)).  A wave starts as soon as
+    the previous one ends and takes the oldest waiting block of every beam
+    that has one (continuous batching: new blocks join the next wave); the
+    clock advances by each wave's measured GPU time, so latency = wave end -
+    arrival under real-time arrivals.  The same arrivals are replayed with
+    one push (launch set) per beam for comparison, and both again with
+    aligned arrivals (every beam's block at the same instant: the load under
+    which waves carry many beams).  ``value`` is the staggered-arrival wave
+    throughput."""
+    import torch
+
+    import paper_1401_8258_gb300 as dd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dd.build()
+    wls = serving_workloads(args.seed)
+    plans = [dd.Plan(w.nchan, w.f_top_mhz, w.chan_width_mhz, w.t_samp_s, w.dms, "u8", local)
+             for w in wls]
+    cap = 1 << 14
+    free, _ = torch.cuda.mem_get_info(dev)
+    budget, used, admitted = 0.8 * free, 0, []
+    for i, (w, p) in enumerate(zip(wls, plans)):
+        need = dd.Stream.bytes_needed(p, w.nsamp) + 16 * cap + w.nchan * w.nsamp
+        if used + need <= budget:
+            admitted.append(i)
+            used += need
+    wls = [wls[i] for i in admitted]
+    plans = [plans[i] for i in admitted]
+    n = len(wls)
+    streams = [dd.Stream(p, w.nsamp) for p, w in zip(plans, wls)]
+    rng = np.random.default_rng(args.seed)
+    blocks = [torch.from_numpy(synth.random_block(rng, w.nchan, w.nsamp, "u8")).to(dev)
+              for w in wls]
+    outs = [torch.empty((w.ndm, w.nsamp), dtype=torch.int32, device=dev) for w in wls]
+    cands = [torch.empty((cap, 16), dtype=torch.uint8, device=dev) for _ in wls]
+    phases = rng.uniform(0.0, 1.0, n)  # staggered arrivals
+    rounds = max(2, args.steps)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def push(idx):
+        dd._native.dd_streams_push([streams[b].handle for b in idx], [blocks[b] for b in idx],
+                                   [blocks[b].stride(0) for b in idx], [outs[b] for b in idx],
+                                   NSIGMA, [cands[b] for b in idx], [cap] * len(idx), stream)
+
+    def simulate(per_beam, phases):
+        t, busy, waves, sizes = 0.0, 0.0, 0, []
+        done = [0] * n
+        lat = []
+        while min(done) < rounds:
+            ready = [b for b in range(n) if done[b] < rounds and phases[b] + done[b] <= t]
+            if not ready:
+                t = min(phases[b] + done[b] for b in range(n) if done[b] < rounds)
+                continue
+            ev0.record(stream)
+            if per_beam:
+                for b in ready:
+                    push([b])
+            else:
+                push(ready)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            w = ev0.elapsed_time(ev1) / 1e3
+            t += w
+            busy += w
+            waves += 1
+            sizes.append(len(ready))
+            for b in ready:
+                lat.append(t - (phases[b] + done[b]))
+                done[b] += 1
+        return {"p50_latency_s": float(np.percentile(lat, 50)),
+                "p99_latency_s": float(np.percentile(lat, 99)),
+                "busy_s": busy, "waves": waves, "beams_per_wave": float(np.mean(sizes)),
+                # beam-seconds of data per GPU-second: the number of beams of
+                # this mix the GPU keeps up with in real time
+                "max_realtime_beams": n * rounds * 1.0 / busy,
+                "realtime_factor": rounds * 1.0 / busy}
+
+    for _ in range(max(1, args.warmup)):  # warm-up waves of every beam
+        push(list(range(n)))
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = sum(p.launch_count() for p in plans)
+    wave = simulate(False, phases)
+    launches = sum(p.launch_count() for p in plans) - launches0
+    aligned = np.zeros(n)  # every beam's block lands at the same instant
+    wave_aligned = simulate(False, aligned)
+    clock = clocks.stop()
+    per_beam = simulate(True, phases)
+    per_beam_aligned = simulate(True, aligned)
+    units = sum(w.ndm * w.nsamp for w in wls) * rounds
+    value = units / wave["busy_s"]
+    adds = float(sum(w.ndm * w.nsamp * w.nchan for w in wls)) * rounds
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+    peaks = measured_peaks()
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = sms * LANES_PER_SM * smax * 1e6 / 1e12
+    achieved = adds / wave["busy_s"] / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": rounds,
+        "warmup": args.warmup, "ms_per_step": 1e3 * wave["busy_s"] / wave["waves"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": SERVE, "beams_drawn": 64, "beams_admitted": n,
+                   "block_s": 1.0, "rounds": rounds, "nchan": [w.nchan for w in wls],
+                   "ndm": [w.ndm for w in wls], "t_samp_s": [w.t_samp_s for w in wls],
+                   "admission_bytes": int(used), "input_dtype": "u8", "nsigma": NSIGMA,
+                   "parallelism": "replicas1"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "whole waves (copies, shared persistent launches, detection)",
+                     "kernel_ms": 1e3 * wave["busy_s"] / wave["waves"]},
+        "serving": {"staggered_arrivals": {"waves": wave, "per_beam_launches": per_beam},
+                    "aligned_arrivals": {"waves": wave_aligned,
+                                         "per_beam_launches": per_beam_aligned}},
+        "cpu_baseline": None, "e2e": None, "clocks": clock, "gpu_launches": int(launches),
+    }
+    print(json.dumps(line), flush=True)
+    for st in streams:
+        st.close()
+    for p in plans:
+        p.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == BATCH:
         run_batch(args)
+    elif args.workload == SERVE:
+        run_serve(args)
     else:
         run_ours(args)
 

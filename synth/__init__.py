@@ -82,7 +82,7 @@ def workload(name: str) -> Workload:
 
 def batch_workloads(seed: int, maxshift_of, n: int = 32, nchan_choices=(256, 512, 1024, 4096),
                     nsamp_range=(16384, 131072), ndm_range=(128, 4096)) -> list[Workload]:
-    """A batch of uneven u8 beams (config 4 of the batching row).
+    """A batch of 32 uneven u8 beams of varied geometry (multi-beam batching).
 
     Per beam, drawn with ``default_rng(seed)``: nchan from ``nchan_choices``;
     nsamp uniform over multiples of 1024 in ``nsamp_range``; ndm uniform over
@@ -106,6 +106,34 @@ def batch_workloads(seed: int, maxshift_of, n: int = 32, nchan_choices=(256, 512
                       dm_grid(0.0, 0.1, ndm), "u8", n_pulses=8, pulse_amp=16.0,
                       pulse_width=(1, 32))
         if maxshift_of(wl) < nsamp // 2:
+            beams.append(wl)
+    return beams
+
+
+def serving_workloads(seed: int, maxshift_of, n: int = 64) -> list[Workload]:
+    """64 streaming beams with 1 s blocks (real-time serving).
+
+    Per beam, drawn with ``default_rng(seed)``: sampling time 51.2, 64, 128
+    or 256 us (n/4 beams each); nchan from {512, 1024, 2048, 4096}; ndm
+    uniform over multiples of 128 in [512, 4096]; band A (416 MHz top,
+    16 MHz wide) or band B (1500 MHz top, 300 MHz wide), channel width =
+    bandwidth / nchan; DM trials 0, 0.1, ...  ``nsamp`` is the block length,
+    1 s of samples rounded half away from zero (19531, 15625, 7813, 3906).
+    A beam whose largest delay (``maxshift_of(beam)``, supplied by the
+    caller) reaches half a block is drawn again.
+    """
+    rng = np.random.default_rng(seed)
+    tsamps = (51.2e-6, 64e-6, 128e-6, 256e-6)
+    blocks = {51.2e-6: 19531, 64e-6: 15625, 128e-6: 7813, 256e-6: 3906}
+    beams = []
+    while len(beams) < n:
+        ts = tsamps[len(beams) * len(tsamps) // n]
+        nchan = int(rng.choice((512, 1024, 2048, 4096)))
+        ndm = 128 * int(rng.integers(4, 33))
+        f_top, bw = (416.0, 16.0) if rng.integers(0, 2) == 0 else (1500.0, 300.0)
+        wl = Workload(f"serve{len(beams)}", nchan, blocks[ts], f_top, bw / nchan, ts,
+                      dm_grid(0.0, 0.1, ndm), "u8")
+        if maxshift_of(wl) < wl.nsamp // 2:
             beams.append(wl)
     return beams
 
