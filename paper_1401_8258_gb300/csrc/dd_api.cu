@@ -489,7 +489,7 @@ int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
                                             sm_count, next_item, status,
                                             p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
       if (nl < 0) return cuda_status(err);
-            p0->launches += nl;  // counted on the first beam's plan
+      p0->launches += nl;  // counted on the first beam's plan
     }
   }
   // detection per beam, then one synchronisation for every count
