@@ -17,6 +17,11 @@ compiled with ``-ffp-contract=off``), written from the thesis:
 Each function is pinned by ``tests/test_oracle_pins.py`` to facts that do not
 come from the oracle itself (exact rational delays, library sums, impulse
 responses, injected pulses, closed forms printed in the thesis).
+
+``oracle.post`` (numpy) holds the post-processing of the dedispersed series
+(Sec. 3.5 median filtering, detrending and normalisation; Sec. 1.5.1 boxcar
+smoothing and single-pulse thresholding), pinned by
+``tests/test_oracle_post_pins.py``.
 """
 from __future__ import annotations
 
