@@ -126,7 +126,8 @@ def boxcar_detect(x: np.ndarray, mean: np.ndarray | None, sigma: np.ndarray | No
     """Single-pulse search over boxcar widths (Sec. 1.5.1).
 
     ``mean`` / ``sigma``: float64 per row (None: 0 and 1, as after
-    ``detrend``).  Rows whose sigma is not finite and positive give nothing.
+    ``detrend``).  Rows whose sigma is not finite and positive, or whose mean
+    is not finite, give nothing.
     Returns PULSE_DTYPE records ordered by (dm_idx, t): for each (row, t) with
     some width w (t + w <= n) whose S/N exceeds ``nsigma``, the width with the
     largest S/N (smallest on ties), that S/N (rounded to float32) and S_w."""
@@ -139,7 +140,7 @@ def boxcar_detect(x: np.ndarray, mean: np.ndarray | None, sigma: np.ndarray | No
     best = np.full((nrows, n), -np.inf)
     best_w = np.zeros((nrows, n), dtype=np.int32)
     best_v = np.zeros((nrows, n))
-    ok = np.isfinite(sigma) & (sigma > 0)
+    ok = np.isfinite(sigma) & (sigma > 0) & np.isfinite(mean)
     with np.errstate(divide="ignore", invalid="ignore"):
         for j, s in enumerate(sums):
             w = 1 << j
