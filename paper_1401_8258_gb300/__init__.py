@@ -6,7 +6,9 @@ the C ABI of ``include/dd.h``).  This package is the thin Python side:
 * :mod:`._native` -- one ctypes function per C entry point (same names);
 * :class:`Plan`   -- a small owner of a plan handle that passes torch device
   tensors and streams to those functions (PyTorch supplies memory and
-  streams only).
+  streams only);
+* :func:`median_filter`, :func:`detrend`, :func:`boxcar_detect` -- the
+  post-processing of ``include/dd_post.h`` on torch device rows.
 """
 from __future__ import annotations
 
@@ -18,6 +20,7 @@ from ._native import (CANDIDATE_DTYPE, DD_ERR_OVERFLOW, DD_F16, DD_F32, DD_OK, D
                       dd_plan_create, dd_plan_delays, dd_plan_destroy, dd_plan_launch_count,
                       dd_plan_max_delay, dd_plan_nsamp_out, dd_process_host, dd_run,
                       dd_batch_create, dd_batch_destroy, dd_batch_run, dd_status_string, dd_sync)
+from ._native import DD_ROWS_F32, DD_ROWS_I32, PULSE_DTYPE
 from .build import build
 
 __all__ = [
@@ -26,7 +29,7 @@ __all__ = [
     "dd_plan_max_delay", "dd_plan_nsamp_out", "dd_plan_delays", "dd_execute", "dd_detect",
     "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
     "dd_run", "Batch", "dd_batch_create", "dd_batch_destroy", "dd_batch_run", "Stream",
-    "push_streams",
+    "push_streams", "median_filter", "detrend", "boxcar_detect", "PULSE_DTYPE",
 ]
 
 _TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
@@ -245,3 +248,58 @@ def push_streams(streams, blocks, nsigma, capacity=1 << 16, outs=None, stream=No
         hosts.append(c[:m].cpu().numpy().view(CANDIDATE_DTYPE).reshape(-1) if m else
                      np.zeros(0, dtype=CANDIDATE_DTYPE))
     return outs, hosts, totals
+
+
+def _rows_type(rows) -> int:
+    import torch
+    if rows.dim() != 2 or rows.stride(1) != 1:
+        raise ValueError("rows must be a 2-D tensor with contiguous rows")
+    if rows.dtype == torch.int32:
+        return DD_ROWS_I32
+    if rows.dtype == torch.float32:
+        return DD_ROWS_F32
+    raise ValueError("rows must be int32 or float32")
+
+
+def median_filter(rows, width, out=None, stream=None):
+    """Windowed median of each row (dd_median_filter); returns ``out``."""
+    import torch
+    rt = _rows_type(rows)
+    if out is None:
+        out = torch.empty(rows.shape, dtype=rows.dtype, device=rows.device)
+    _native.dd_median_filter(rows, rows.stride(0), rt, rows.shape[0], rows.shape[1], width, out,
+                             out.stride(0), stream)
+    return out
+
+
+def detrend(rows, out=None, coef=False, stream=None):
+    """Detrended, normalised float rows (dd_detrend); with ``coef`` also the
+    per-row (a, b, s) as a float64 device tensor."""
+    import torch
+    rt = _rows_type(rows)
+    if out is None:
+        out = torch.empty(rows.shape, dtype=torch.float32, device=rows.device)
+    c = torch.empty((rows.shape[0], 3), dtype=torch.float64, device=rows.device) if coef else None
+    _native.dd_detrend(rows, rows.stride(0), rt, rows.shape[0], rows.shape[1], out, out.stride(0),
+                       c, stream)
+    return (out, c) if coef else out
+
+
+def boxcar_detect(rows, nwidths, nsigma, mean=None, sigma=None, capacity=1 << 16,
+                  workspace=None, stream=None):
+    """Boxcar single-pulse search (dd_boxcar_detect).  ``mean`` / ``sigma``:
+    float64 device tensors per row or None (0 and 1).  Returns (pulses as a
+    PULSE_DTYPE numpy array, total found)."""
+    import torch
+    rt = _rows_type(rows)
+    nrows, ncols = rows.shape
+    need = _native.dd_boxcar_workspace_bytes(nrows, ncols)
+    if workspace is None or workspace.numel() < need:
+        workspace = torch.empty(need, dtype=torch.uint8, device=rows.device)
+    pulses = torch.empty((max(capacity, 1), PULSE_DTYPE.itemsize), dtype=torch.uint8,
+                         device=rows.device)
+    _, total = _native.dd_boxcar_detect(rows, rows.stride(0), rt, nrows, ncols, mean, sigma,
+                                        nwidths, nsigma, workspace, workspace.numel(), pulses,
+                                        capacity, stream)
+    got = pulses[:min(total, capacity)].cpu().numpy().view(PULSE_DTYPE).reshape(-1)
+    return got, total

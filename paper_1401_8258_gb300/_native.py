@@ -33,6 +33,10 @@ CANDIDATE_DTYPE = np.dtype(
     [("dm_idx", np.int32), ("t", np.int32), ("value", np.float32), ("snr", np.float32)]
 )
 
+DD_ROWS_I32, DD_ROWS_F32 = 0, 1
+PULSE_DTYPE = np.dtype([("dm_idx", np.int32), ("t", np.int32), ("width", np.int32),
+                        ("snr", np.float32), ("value", np.float64)])
+
 
 class DDError(RuntimeError):
     def __init__(self, status: int, what: str):
@@ -75,6 +79,12 @@ SIGNATURES = [
     ("dd_batch_create", ctypes.c_int, [_vp, _vp, _i32]),
     ("dd_batch_destroy", ctypes.c_int, [_vp]),
     ("dd_batch_run", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp]),
+    # dd_post.h
+    ("dd_median_filter", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _i32, _vp, _i64, _vp]),
+    ("dd_detrend", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _vp, _i64, _vp, _vp]),
+    ("dd_boxcar_workspace_bytes", ctypes.c_int, [_i32, _i64, _vp]),
+    ("dd_boxcar_detect", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _vp, _vp, _i32, _f32, _vp,
+                                        _i64, _vp, _i64, _vp, _vp]),
 ]
 
 PEAK_KINDS = {"fadd": 0, "fadd2": 1, "iadd": 2, "iadd3": 3, "imad": 4, "lop3": 5, "prmt": 6,
@@ -340,4 +350,35 @@ def dd_detect_noalloc(out, dtype, ndm, nsamp_out, nsigma, cands, capacity, strea
                                   _addr(cands), int(capacity), ctypes.addressof(cnt),
                                   _stream(stream))
     _check(st, "dd_detect_noalloc", allow=(DD_ERR_OVERFLOW,))
+    return st, int(cnt.value)
+
+
+def dd_median_filter(rows, in_pitch, rows_type, nrows, ncols, width, out, out_pitch, stream=None):
+    _check(load().dd_median_filter(_addr(rows), int(in_pitch), int(rows_type), int(nrows),
+                                   int(ncols), int(width), _addr(out), int(out_pitch),
+                                   _stream(stream)), "dd_median_filter")
+
+
+def dd_detrend(rows, in_pitch, rows_type, nrows, ncols, out, out_pitch, coef=None, stream=None):
+    _check(load().dd_detrend(_addr(rows), int(in_pitch), int(rows_type), int(nrows), int(ncols),
+                             _addr(out), int(out_pitch), _addr(coef), _stream(stream)),
+           "dd_detrend")
+
+
+def dd_boxcar_workspace_bytes(nrows, ncols) -> int:
+    b = ctypes.c_int64(0)
+    _check(load().dd_boxcar_workspace_bytes(int(nrows), int(ncols), ctypes.addressof(b)),
+           "dd_boxcar_workspace_bytes")
+    return int(b.value)
+
+
+def dd_boxcar_detect(rows, pitch, rows_type, nrows, ncols, mean, sigma, nwidths, nsigma,
+                     workspace, workspace_bytes, pulses, capacity, stream=None):
+    """Returns ``(status, count)``; status is DD_OK or DD_ERR_OVERFLOW."""
+    cnt = ctypes.c_int64(0)
+    st = load().dd_boxcar_detect(_addr(rows), int(pitch), int(rows_type), int(nrows), int(ncols),
+                                 _addr(mean), _addr(sigma), int(nwidths), float(nsigma),
+                                 _addr(workspace), int(workspace_bytes), _addr(pulses),
+                                 int(capacity), ctypes.addressof(cnt), _stream(stream))
+    _check(st, "dd_boxcar_detect", allow=(DD_ERR_OVERFLOW,))
     return st, int(cnt.value)

@@ -1,0 +1,787 @@
+// dd_post.cu -- post-processing of dedispersed series on the GPU:
+//   dd_median_filter   windowed median (Sec. 3.5, median filtering);
+//   dd_detrend         least-squares line removal and normalisation
+//                      (Sec. 3.5, detrending and normalisation);
+//   dd_boxcar_detect   boxcar smoothing by successive adjacent sums and n-sigma
+//                      thresholding of every width (Sec. 1.5.1).
+// All three are bound by HBM: each reads its rows about once (the median's
+// window halo and the boxcar's width halo come from L2) and the arithmetic
+// per sample is a handful of integer or float operations.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <type_traits>
+
+#include "dd_post.h"
+
+namespace {
+
+inline int cuda_status(cudaError_t e) { return e == cudaSuccess ? DD_OK : DD_ERR_CUDA; }
+
+inline bool overlap(const void *a, size_t na, const void *b, size_t nb) {
+  const uintptr_t x = reinterpret_cast<uintptr_t>(a), y = reinterpret_cast<uintptr_t>(b);
+  return x < y + nb && y < x + na;
+}
+
+inline size_t row_span(int32_t nrows, int64_t pitch, int64_t ncols, size_t esize) {
+  return (static_cast<size_t>(nrows - 1) * static_cast<size_t>(pitch) + static_cast<size_t>(ncols)) *
+         esize;
+}
+
+template <typename T> __device__ __forceinline__ T vmin(T a, T b);
+template <typename T> __device__ __forceinline__ T vmax(T a, T b);
+template <> __device__ __forceinline__ int32_t vmin<int32_t>(int32_t a, int32_t b) { return min(a, b); }
+template <> __device__ __forceinline__ int32_t vmax<int32_t>(int32_t a, int32_t b) { return max(a, b); }
+template <> __device__ __forceinline__ float vmin<float>(float a, float b) { return fminf(a, b); }
+template <> __device__ __forceinline__ float vmax<float>(float a, float b) { return fmaxf(a, b); }
+
+// ------------------------------------------------------------------ median
+//
+// CTA = one tile of kMedTile outputs of one row.  The tile's samples and a
+// halo of H on each side (clamped to the row: the window repeats the end
+// sample) are staged in shared memory.  A thread takes output pairs
+// (t, t + 1): their windows share the 2H samples t-H+1 .. t+H, whose two
+// middle order statistics lo <= hi come from one sorting network; the median
+// of a window is then its remaining sample clamped to [lo, hi].
+
+constexpr int kMedThreads = 256;
+constexpr int kMedTile = 4096;
+
+// Ascending sort of s[0..N) by odd-even transposition (N rounds).
+template <typename T, int N>
+__device__ __forceinline__ void sort_network(T (&s)[N]) {
+#pragma unroll
+  for (int r = 0; r < N; ++r) {
+#pragma unroll
+    for (int i = r & 1; i + 1 < N; i += 2) {
+      const T a = s[i], b = s[i + 1];
+      s[i] = vmin(a, b);
+      s[i + 1] = vmax(a, b);
+    }
+  }
+}
+
+template <typename T> struct Pair;
+template <> struct Pair<int32_t> { using type = int2; };
+template <> struct Pair<float> { using type = float2; };
+
+template <typename T, int H>
+__global__ void __launch_bounds__(kMedThreads)
+dd_median(const T *__restrict__ in, int64_t in_pitch, int64_t ncols, int ntiles,
+          T *__restrict__ out, int64_t out_pitch, int pair_store) {
+  using P2 = typename Pair<T>::type;
+  __shared__ __align__(16) T s[kMedTile + 2 * H];
+  const int64_t row = blockIdx.x / ntiles;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x % ntiles) * kMedTile;
+  const T *x = in + row * in_pitch;
+  T *y = out + row * out_pitch;
+  // s[i] = sample t0 - H + i, clamped to the row
+  for (int i = threadIdx.x; i < kMedTile + 2 * H; i += kMedThreads) {
+    int64_t g = t0 - H + i;
+    g = g < 0 ? 0 : (g >= ncols ? ncols - 1 : g);
+    s[i] = x[g];
+  }
+  __syncthreads();
+  const P2 *s2 = reinterpret_cast<const P2 *>(s);
+  for (int p = threadIdx.x; p < kMedTile / 2; p += kMedThreads) {
+    const int64_t t = t0 + 2 * p;
+    if (t >= ncols) break;
+    // v[k] = sample t - H + k, k = 0 .. 2H+1 (window of t: v[0..2H], of t+1: v[1..2H+1])
+    T v[2 * H + 2];
+#pragma unroll
+    for (int k = 0; k < H + 1; ++k) {
+      const P2 q = s2[p + k];
+      v[2 * k] = q.x;
+      v[2 * k + 1] = q.y;
+    }
+    T m0, m1;
+    if constexpr (H == 0) {
+      m0 = v[0];
+      m1 = v[1];
+    } else {
+      T c[2 * H];
+#pragma unroll
+      for (int k = 0; k < 2 * H; ++k) c[k] = v[k + 1];
+      sort_network(c);
+      const T lo = c[H - 1], hi = c[H];
+      m0 = vmin(vmax(v[0], lo), hi);
+      m1 = vmin(vmax(v[2 * H + 1], lo), hi);
+    }
+    if (pair_store && t + 1 < ncols) {
+      P2 q;
+      q.x = m0;
+      q.y = m1;
+      *reinterpret_cast<P2 *>(y + t) = q;
+    } else {
+      y[t] = m0;
+      if (t + 1 < ncols) y[t + 1] = m1;
+    }
+  }
+}
+
+template <typename T>
+int launch_median(const T *in, int64_t in_pitch, int32_t nrows, int64_t ncols, int width, T *out,
+                  int64_t out_pitch, cudaStream_t s) {
+  const int64_t ntiles = (ncols + kMedTile - 1) / kMedTile;
+  if (ntiles * nrows > INT32_MAX) return DD_ERR_SIZE;
+  const int grid = static_cast<int>(ntiles * nrows);
+  // 8-byte pair stores when every row start is 8-byte aligned (t is even)
+  const int pair_store = (reinterpret_cast<uintptr_t>(out) % 8 == 0) && (out_pitch % 2 == 0);
+  const int nt = static_cast<int>(ntiles);
+  switch (width / 2) {
+    case 0: dd_median<T, 0><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    case 1: dd_median<T, 1><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    case 2: dd_median<T, 2><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    case 3: dd_median<T, 3><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    case 4: dd_median<T, 4><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    case 5: dd_median<T, 5><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    case 6: dd_median<T, 6><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    case 7: dd_median<T, 7><<<grid, kMedThreads, 0, s>>>(in, in_pitch, ncols, nt, out, out_pitch, pair_store); break;
+    default: return DD_ERR_ARG;
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+// ----------------------------------------------------------------- detrend
+//
+// CTA = one row.  Pass 1 sums the row: exactly in 128-bit integers for int32
+// rows (Sy = sum y, Sty = sum t y, Syy = sum y^2), in float chunks of 16
+// consecutive samples about the row's first value, added in double, for
+// float rows.  Thread 0 solves the least-squares line from the centred sums
+//   Sxx = n St2 - St^2,  Sxy = n Sty - St Sy,  Syyc = n Syy - Sy^2
+// (St, St2: sums of t and t^2, closed forms).  Int rows: the residual sum of
+// squares is n RSS = Syyc - Sxy^2 / Sxx, exactly zero when Syyc Sxx == Sxy^2
+// (tested in 256 bits).  Float rows take the thesis's second pass instead,
+// summing the squared residual itself.  The last pass writes (y - a - b t)/s
+// in float: a + b t is formed in double once per 16 samples and split into
+// an integer part (subtracted exactly from int rows) and a small float part.
+
+constexpr int kDtThreads = 1024;
+constexpr int kDtChunk = 16;
+
+using i128 = __int128;
+using u128 = unsigned __int128;
+
+__device__ double u128_to_double(u128 v) {
+  const unsigned long long hi = static_cast<unsigned long long>(v >> 64);
+  const unsigned long long lo = static_cast<unsigned long long>(v);
+  if (hi == 0) return __ull2double_rn(lo);
+  // top 64 bits with a sticky bit for everything below: one rounding
+  const int drop = 64 - __clzll(static_cast<long long>(hi));
+  const u128 mask = (static_cast<u128>(1) << drop) - 1;
+  const unsigned long long top =
+      static_cast<unsigned long long>(v >> drop) | static_cast<unsigned long long>((v & mask) != 0);
+  return scalbn(__ull2double_rn(top), drop);
+}
+
+__device__ double i128_to_double(i128 v) {
+  return v < 0 ? -u128_to_double(static_cast<u128>(-v)) : u128_to_double(static_cast<u128>(v));
+}
+
+// 256-bit product of two unsigned 128-bit values as (hi, lo).
+__device__ void mul_u128(u128 a, u128 b, u128 *hi, u128 *lo) {
+  const unsigned long long a0 = static_cast<unsigned long long>(a), a1 = static_cast<unsigned long long>(a >> 64);
+  const unsigned long long b0 = static_cast<unsigned long long>(b), b1 = static_cast<unsigned long long>(b >> 64);
+  const u128 p00 = static_cast<u128>(a0) * b0, p01 = static_cast<u128>(a0) * b1;
+  const u128 p10 = static_cast<u128>(a1) * b0, p11 = static_cast<u128>(a1) * b1;
+  const u128 mid = (p00 >> 64) + static_cast<unsigned long long>(p01) + static_cast<unsigned long long>(p10);
+  *lo = (p00 & ~static_cast<unsigned long long>(0)) | (mid << 64);
+  *hi = p11 + (p01 >> 64) + (p10 >> 64) + (mid >> 64);
+}
+
+__device__ __forceinline__ i128 shfl_down_i128(i128 v, int o) {
+  long long lo = static_cast<long long>(static_cast<unsigned long long>(v));
+  long long hi = static_cast<long long>(v >> 64);
+  lo = __shfl_down_sync(0xffffffffu, lo, o);
+  hi = __shfl_down_sync(0xffffffffu, hi, o);
+  return (static_cast<i128>(hi) << 64) | static_cast<unsigned long long>(lo);
+}
+
+// Sum of v over the CTA, valid in thread 0.
+template <typename V>
+__device__ V block_sum(V v, V *scratch) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    if constexpr (sizeof(V) == 16) {
+      v += shfl_down_i128(v, o);
+    } else {
+      v += __shfl_down_sync(0xffffffffu, v, o);
+    }
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) scratch[w] = v;
+  __syncthreads();
+  V total = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kDtThreads / 32; ++k) total += scratch[k];
+  return total;
+}
+
+template <typename X, bool VEC>
+__device__ __forceinline__ void load16(const X *x, int64_t t, int64_t n, X (&v)[kDtChunk]) {
+  if (VEC && t + kDtChunk <= n) {
+    const int4 *p = reinterpret_cast<const int4 *>(x + t);
+#pragma unroll
+    for (int q = 0; q < kDtChunk / 4; ++q) {
+      const int4 u = p[q];
+      v[4 * q] = *reinterpret_cast<const X *>(&u.x);
+      v[4 * q + 1] = *reinterpret_cast<const X *>(&u.y);
+      v[4 * q + 2] = *reinterpret_cast<const X *>(&u.z);
+      v[4 * q + 3] = *reinterpret_cast<const X *>(&u.w);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kDtChunk; ++k) v[k] = t + k < n ? x[t + k] : X(0);
+  }
+}
+
+// Pairwise (tree) sum of 16 floats.
+__device__ __forceinline__ float tree16(const float (&v)[kDtChunk]) {
+  float a[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = v[2 * k] + v[2 * k + 1];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) a[k] = a[2 * k] + a[2 * k + 1];
+  a[0] = a[0] + a[1];
+  a[2] = a[2] + a[3];
+  return a[0] + a[2];
+}
+
+// Least-squares line and residual rms of an int32 row from its exact sums
+// (thread 0 only; kept out of line so that the sweep loops keep their
+// registers).  line[0..3) = a, b, s.
+__device__ __noinline__ void line_i32(i128 sy, i128 sty, i128 syy, int64_t n, double *line) {
+  const i128 N = n, St = N * (N - 1) / 2, St2 = (N - 1) * N * (2 * N - 1) / 6;
+  const i128 Sxx = N * St2 - St * St;  // 0 only for n == 1
+  double a, b, s;
+  if (Sxx == 0) {
+    a = i128_to_double(sy);  // n == 1: the line is the sample
+    b = 0.0;
+    s = 0.0;
+  } else {
+    const i128 Sxy = N * sty - St * sy;
+    const i128 Syyc = N * syy - sy * sy;  // >= 0
+    const i128 An = sy * St2 - St * sty;  // a Sxx, exact
+    const double dSxx = i128_to_double(Sxx);
+    b = i128_to_double(Sxy) / dSxx;
+    a = i128_to_double(An) / dSxx;
+    u128 l_hi, l_lo, r_hi, r_lo;
+    const u128 aSxy = static_cast<u128>(Sxy < 0 ? -Sxy : Sxy);
+    mul_u128(static_cast<u128>(Syyc), static_cast<u128>(Sxx), &l_hi, &l_lo);
+    mul_u128(aSxy, aSxy, &r_hi, &r_lo);
+    if (l_hi == r_hi && l_lo == r_lo) {
+      s = 0.0;
+    } else {
+      const double dSxy = i128_to_double(Sxy);
+      const double rss_n = i128_to_double(Syyc) - dSxy * (dSxy / dSxx);
+      s = rss_n > 0 ? sqrt(rss_n) / static_cast<double>(n) : 0.0;
+    }
+  }
+  line[0] = a;
+  line[1] = b;
+  line[2] = s;
+}
+
+// Least-squares line of a float row from double sums of d = y - y0 and t d
+// (thread 0 only).  line[0] = a, line[1] = b.
+__device__ __noinline__ void line_f32(double sy, double sty, float y0, int64_t n, double *line) {
+  const i128 N = n, St = N * (N - 1) / 2, St2 = (N - 1) * N * (2 * N - 1) / 6;
+  const i128 Sxx = N * St2 - St * St;
+  double a, b;
+  if (Sxx == 0) {
+    a = y0;
+    b = 0.0;
+  } else {
+    const double dN = static_cast<double>(n), dSt = i128_to_double(St);
+    const double dSt2 = i128_to_double(St2), dSxx = i128_to_double(Sxx);
+    b = (dN * sty - dSt * sy) / dSxx;
+    a = (sy * dSt2 - dSt * sty) / dSxx + static_cast<double>(y0);
+  }
+  line[0] = a;
+  line[1] = b;
+}
+
+template <typename X, bool VEC>
+__global__ void __launch_bounds__(kDtThreads, 1)
+dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t out_pitch,
+                double *coef) {  // no __restrict__: out may be in (float rows, in place)
+  __shared__ i128 s_i[kDtThreads / 32];
+  __shared__ double s_d[kDtThreads / 32];
+  __shared__ double s_line[3];  // a, b, s
+  const int64_t row = blockIdx.x;
+  const X *x = in + row * in_pitch;
+  float *z = out + row * out_pitch;
+  const int64_t step = static_cast<int64_t>(kDtThreads) * kDtChunk;
+
+  if constexpr (std::is_integral<X>::value) {  // int32 rows: exact sums
+    i128 sy = 0, sty = 0, syy = 0;
+    for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+      X v[kDtChunk];
+      load16<X, VEC>(x, t, n, v);
+      long long c1 = 0, c2 = 0;  // chunk sums of y and of k y, k = 0..15
+      u128 c3 = 0;
+#pragma unroll
+      for (int k = 0; k < kDtChunk; ++k) {
+        const long long y = v[k];
+        c1 += y;
+        c2 += static_cast<long long>(k) * y;
+        c3 += static_cast<u128>(static_cast<unsigned long long>(y * y));
+      }
+      sy += c1;
+      sty += static_cast<i128>(t) * c1 + c2;
+      syy += static_cast<i128>(c3);
+    }
+    sy = block_sum(sy, s_i);
+    sty = block_sum(sty, s_i);
+    syy = block_sum(syy, s_i);
+    if (threadIdx.x == 0) line_i32(sy, sty, syy, n, s_line);
+  } else {  // float rows: three passes in the thesis's order
+    const float y0 = x[0];
+    double sy = 0, sty = 0;
+    for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+      X v[kDtChunk];
+      load16<X, VEC>(x, t, n, v);
+      float d[kDtChunk], kd[kDtChunk];
+#pragma unroll
+      for (int k = 0; k < kDtChunk; ++k) {
+        d[k] = t + k < n ? v[k] - y0 : 0.0f;
+        kd[k] = static_cast<float>(k) * d[k];
+      }
+      const double c1 = tree16(d), c2 = tree16(kd);
+      sy += c1;
+      sty += static_cast<double>(t) * c1 + c2;
+    }
+    sy = block_sum(sy, s_d);
+    sty = block_sum(sty, s_d);
+    if (threadIdx.x == 0) line_f32(sy, sty, y0, n, s_line);
+    __syncthreads();
+    const double a = s_line[0], b = s_line[1];
+    const float bf = static_cast<float>(b);
+    double rss = 0;
+    for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+      X v[kDtChunk];
+      load16<X, VEC>(x, t, n, v);
+      const double base = fma(b, static_cast<double>(t), a);
+      const double hi = floor(base);
+      const float lo = static_cast<float>(base - hi), hf = static_cast<float>(hi);
+      float r2[kDtChunk];
+#pragma unroll
+      for (int k = 0; k < kDtChunk; ++k) {
+        const float r = (v[k] - hf) - fmaf(bf, static_cast<float>(k), lo);
+        r2[k] = t + k < n ? r * r : 0.0f;
+      }
+      rss += tree16(r2);
+    }
+    rss = block_sum(rss, s_d);
+    if (threadIdx.x == 0) s_line[2] = rss > 0 ? sqrt(rss / static_cast<double>(n)) : 0.0;
+  }
+  __syncthreads();
+  const double a = s_line[0], b = s_line[1], s = s_line[2];
+  if (coef && threadIdx.x == 0) {
+    coef[3 * row] = a;
+    coef[3 * row + 1] = b;
+    coef[3 * row + 2] = s;
+  }
+  const float inv = s > 0 ? static_cast<float>(1.0 / s) : 0.0f;
+  const float bf = static_cast<float>(b);
+  for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+    X v[kDtChunk];
+    load16<X, VEC>(x, t, n, v);
+    const double base = fma(b, static_cast<double>(t), a);
+    const double hi = floor(base);
+    const float lo = static_cast<float>(base - hi);
+    float r[kDtChunk];
+#pragma unroll
+    for (int k = 0; k < kDtChunk; ++k) {
+      const float line = fmaf(bf, static_cast<float>(k), lo);
+      if constexpr (std::is_integral<X>::value) {
+        r[k] = static_cast<float>(static_cast<long long>(v[k]) - static_cast<long long>(hi)) - line;
+      } else {
+        r[k] = (v[k] - static_cast<float>(hi)) - line;
+      }
+      r[k] *= inv;
+    }
+    if (VEC && t + kDtChunk <= n) {
+      float4 *p = reinterpret_cast<float4 *>(z + t);
+#pragma unroll
+      for (int q = 0; q < kDtChunk / 4; ++q)
+        p[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int k = 0; k < kDtChunk; ++k)
+        if (t + k < n) z[t + k] = r[k];
+    }
+  }
+}
+
+// ------------------------------------------------------------------ boxcar
+//
+// Thresholds: for each (row, width) the smallest sum that passes the double
+// S/N test (a bisection over int64 sums or over floats in order; the test is
+// monotone in the sum), so the sweep compares sums only.
+// Sweep (count pass, then write pass for tiles with pulses): CTA = one tile
+// of kBoxTile start samples of one row; the tile plus a halo of
+// 2^(nwidths-1) - 1 samples sits in shared memory and is replaced, width by
+// width, by S_2w[i] = S_w[i] + S_w[i + w]; thread k owns elements
+// k + 256 m in registers.  Pulses of a tile are ranked by start sample
+// through a bitmap, after an exclusive scan of the per-tile counts in
+// (row, tile) order, so the list is ordered by (row, t).
+
+constexpr int kBoxThreads = 256;
+constexpr int kBoxTile = 4096;
+constexpr int kBoxOwn = kBoxTile / kBoxThreads;  // 16 outputs per thread
+constexpr int kMaxWidths = 12;
+constexpr int kBoxPer = (kBoxTile + (1 << (kMaxWidths - 1)) - 1 + kBoxThreads - 1) / kBoxThreads;
+constexpr int kScanThreads = 1024;
+
+__device__ __forceinline__ double boxcar_snr(double sum, int w, double mean, double sigma) {
+  const double dw = static_cast<double>(w);
+  return __ddiv_rn(__dsub_rn(sum, __dmul_rn(dw, mean)), __dmul_rn(sigma, __dsqrt_rn(dw)));
+}
+
+__device__ __forceinline__ uint32_t float_key(float x) {
+  const uint32_t u = __float_as_uint(x);
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float key_float(uint32_t k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7fffffffu) : ~k);
+}
+
+// thr[row][j]: int rows -> smallest passing int64 sum (INT64_MAX: none);
+// float rows -> bits of the smallest passing float (a NaN: none).
+__global__ void dd_boxcar_thresholds(int32_t rows_type, int32_t nrows, int nwidths,
+                                     const double *mean, const double *sigma, double nsigma,
+                                     int64_t *thr) {
+  const int64_t idx = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (idx >= static_cast<int64_t>(nrows) * kMaxWidths) return;
+  const int64_t row = idx / kMaxWidths;
+  const int j = static_cast<int>(idx % kMaxWidths);
+  const double mu = mean ? mean[row] : 0.0, sg = sigma ? sigma[row] : 1.0;
+  const bool ok = j < nwidths && isfinite(mu) && isfinite(sg) && sg > 0.0;
+  const int w = 1 << j;
+  if (rows_type == DD_ROWS_I32) {
+    int64_t res = INT64_MAX;
+    if (ok) {
+      // |sums| < 2^43, so [-2^53, 2^53] brackets every decision
+      int64_t lo = -(static_cast<int64_t>(1) << 53), hi = static_cast<int64_t>(1) << 53;
+      if (boxcar_snr(static_cast<double>(lo), w, mu, sg) > nsigma) {
+        res = lo;
+      } else if (boxcar_snr(static_cast<double>(hi), w, mu, sg) > nsigma) {
+        while (hi - lo > 1) {  // pass(lo) false, pass(hi) true
+          const int64_t mid = lo + (hi - lo) / 2;
+          if (boxcar_snr(static_cast<double>(mid), w, mu, sg) > nsigma) hi = mid; else lo = mid;
+        }
+        res = hi;
+      }
+    }
+    thr[idx] = res;
+  } else {
+    uint32_t bits = 0x7fc00000u;  // NaN: no sum passes
+    if (ok) {
+      uint32_t lo = float_key(-INFINITY), hi = float_key(INFINITY);
+      if (boxcar_snr(-static_cast<double>(INFINITY), w, mu, sg) > nsigma) {
+        bits = __float_as_uint(-INFINITY);
+      } else if (boxcar_snr(static_cast<double>(INFINITY), w, mu, sg) > nsigma) {
+        while (hi - lo > 1) {
+          const uint32_t mid = lo + (hi - lo) / 2;
+          if (boxcar_snr(static_cast<double>(key_float(mid)), w, mu, sg) > nsigma) hi = mid; else lo = mid;
+        }
+        bits = __float_as_uint(key_float(hi));
+      }
+    }
+    thr[idx] = static_cast<int64_t>(bits);
+  }
+}
+
+template <typename V>
+__device__ __forceinline__ bool passes(V s, int64_t thr);
+template <> __device__ __forceinline__ bool passes<long long>(long long s, int64_t thr) { return s >= thr; }
+template <> __device__ __forceinline__ bool passes<float>(float s, int64_t thr) {
+  return s >= __uint_as_float(static_cast<uint32_t>(thr));
+}
+
+template <typename X, typename V, bool WRITE>
+__global__ void __launch_bounds__(kBoxThreads)
+dd_boxcar_sweep(const X *__restrict__ rows, int64_t pitch, int64_t ncols, int ntiles, int nwidths,
+                const int64_t *__restrict__ thr_all, const double *mean, const double *sigma,
+                int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
+                dd_pulse *__restrict__ pulses, int64_t capacity) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  V *S = reinterpret_cast<V *>(smem_raw);
+  __shared__ int64_t s_thr[kMaxWidths];
+  __shared__ uint32_t s_bits[kBoxTile / 32];
+  __shared__ int s_pre[kBoxTile / 32];
+  __shared__ int s_cnt[kBoxThreads / 32];
+  if (WRITE && counts[blockIdx.x] == 0) return;
+  const int64_t row = blockIdx.x / ntiles;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x % ntiles) * kBoxTile;
+  const X *x = rows + row * pitch;
+  const int E = kBoxTile + (1 << (nwidths - 1)) - 1;
+  if (threadIdx.x < kMaxWidths) s_thr[threadIdx.x] = thr_all[row * kMaxWidths + threadIdx.x];
+  V reg[kBoxPer];
+#pragma unroll
+  for (int m = 0; m < kBoxPer; ++m) {
+    const int i = threadIdx.x + kBoxThreads * m;
+    const int64_t g = t0 + i;
+    reg[m] = (i < E && g < ncols) ? static_cast<V>(x[g]) : V(0);
+    if (i < E) S[i] = reg[m];
+  }
+  __syncthreads();
+  uint32_t mask = 0;  // bit m: element threadIdx.x + 256 m is a pulse start
+  double bsnr[WRITE ? kBoxOwn : 1];
+  int bw[WRITE ? kBoxOwn : 1];
+  V bval[WRITE ? kBoxOwn : 1];
+  if constexpr (WRITE) {
+#pragma unroll
+    for (int m = 0; m < kBoxOwn; ++m) {
+      bsnr[m] = -INFINITY;
+      bw[m] = 0;
+      bval[m] = V(0);
+    }
+  }
+  const double mu = mean ? mean[row] : 0.0, sg = sigma ? sigma[row] : 1.0;
+  for (int j = 0; j < nwidths; ++j) {
+    const int w = 1 << j;
+    if (j > 0) {
+      const int half = w >> 1, lim = E - w + 1;
+#pragma unroll
+      for (int m = 0; m < kBoxPer; ++m) {
+        const int i = threadIdx.x + kBoxThreads * m;
+        if (i < lim) reg[m] = reg[m] + S[i + half];
+      }
+      __syncthreads();
+#pragma unroll
+      for (int m = 0; m < kBoxPer; ++m) {
+        const int i = threadIdx.x + kBoxThreads * m;
+        if (i < lim) S[i] = reg[m];
+      }
+    }
+    const int64_t thr = s_thr[j];
+#pragma unroll
+    for (int m = 0; m < kBoxOwn; ++m) {
+      const int64_t t = t0 + threadIdx.x + kBoxThreads * m;
+      if (t + w <= ncols && passes<V>(reg[m], thr)) {
+        mask |= 1u << m;
+        if constexpr (WRITE) {
+          const double snr = boxcar_snr(static_cast<double>(reg[m]), w, mu, sg);
+          if (snr > bsnr[m]) {
+            bsnr[m] = snr;
+            bw[m] = w;
+            bval[m] = reg[m];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if constexpr (!WRITE) {
+    int c = __popc(mask);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) s_cnt[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int total = 0;
+      for (int k = 0; k < kBoxThreads / 32; ++k) total += s_cnt[k];
+      counts[blockIdx.x] = total;
+    }
+  } else {
+    // element i = threadIdx.x + 256 m lies in word (i >> 5) = warp + 8 m, bit lane
+#pragma unroll
+    for (int m = 0; m < kBoxOwn; ++m) {
+      const uint32_t b = __ballot_sync(0xffffffffu, (mask >> m) & 1u);
+      if (lane == 0) s_bits[warp + (kBoxThreads / 32) * m] = b;
+    }
+    __syncthreads();
+    if (threadIdx.x < kBoxTile / 32) {  // exclusive prefix of the word counts (4 warps)
+      const int c = __popc(s_bits[threadIdx.x]);
+      int inc = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+      }
+      if (lane == 31) s_cnt[warp] = inc;
+      s_pre[threadIdx.x] = inc - c;
+    }
+    __syncthreads();
+    if (threadIdx.x < kBoxTile / 32) {
+      int add = 0;
+      for (int k = 0; k < warp; ++k) add += s_cnt[k];
+      s_pre[threadIdx.x] += add;
+    }
+    __syncthreads();
+    const int64_t base = offsets[blockIdx.x];
+#pragma unroll
+    for (int m = 0; m < kBoxOwn; ++m) {
+      if (!((mask >> m) & 1u)) continue;
+      const int i = threadIdx.x + kBoxThreads * m;
+      const int word = i >> 5;
+      const int64_t pos =
+          base + s_pre[word] + __popc(s_bits[word] & ((1u << (i & 31)) - 1u));
+      if (pos < capacity) {
+        dd_pulse p;
+        p.dm_idx = static_cast<int32_t>(row);
+        p.t = static_cast<int32_t>(t0 + i);
+        p.width = bw[m];
+        p.snr = __double2float_rn(bsnr[m]);
+        p.value = static_cast<double>(bval[m]);
+        pulses[pos] = p;
+      }
+    }
+  }
+}
+
+// Single-CTA exclusive scan of m counts; *total gets their sum.
+__global__ void __launch_bounds__(kScanThreads)
+dd_boxcar_scan(const int64_t *__restrict__ counts, int64_t m, int64_t *__restrict__ offsets,
+               int64_t *__restrict__ total) {
+  __shared__ int64_t s_part[kScanThreads];
+  const int64_t per = (m + kScanThreads - 1) / kScanThreads;
+  const int64_t lo = threadIdx.x * per;
+  const int64_t hi = lo + per < m ? lo + per : m;
+  int64_t sum = 0;
+  for (int64_t i = lo; i < hi; ++i) sum += counts[i];
+  s_part[threadIdx.x] = sum;
+  __syncthreads();
+  for (int o = 1; o < kScanThreads; o <<= 1) {
+    const int64_t add = threadIdx.x >= o ? s_part[threadIdx.x - o] : 0;
+    __syncthreads();
+    s_part[threadIdx.x] += add;
+    __syncthreads();
+  }
+  int64_t run = s_part[threadIdx.x] - sum;
+  for (int64_t i = lo; i < hi; ++i) {
+    offsets[i] = run;
+    run += counts[i];
+  }
+  if (threadIdx.x == kScanThreads - 1) *total = s_part[kScanThreads - 1];
+}
+
+inline int64_t box_tiles(int64_t ncols) { return (ncols + kBoxTile - 1) / kBoxTile; }
+
+inline int64_t box_workspace(int32_t nrows, int64_t ncols) {
+  const int64_t m = static_cast<int64_t>(nrows) * box_tiles(ncols);
+  return 8 * (static_cast<int64_t>(nrows) * kMaxWidths + 2 * m + 2);
+}
+
+template <typename X, typename V>
+int launch_boxcar(const X *rows, int64_t pitch, int32_t nrows, int64_t ncols, const double *mean,
+                  const double *sigma, int nwidths, float nsigma, unsigned char *ws, dd_pulse *pulses,
+                  int64_t capacity, int64_t *count, cudaStream_t s) {
+  const int64_t ntiles = box_tiles(ncols);
+  const int64_t m = ntiles * nrows;
+  int64_t *thr = reinterpret_cast<int64_t *>(ws);
+  int64_t *counts = thr + static_cast<int64_t>(nrows) * kMaxWidths;
+  int64_t *offsets = counts + m;
+  int64_t *total = offsets + m;
+  const int rows_type = sizeof(V) == 8 ? DD_ROWS_I32 : DD_ROWS_F32;
+  const int64_t nthr = static_cast<int64_t>(nrows) * kMaxWidths;
+  dd_boxcar_thresholds<<<static_cast<unsigned>((nthr + 255) / 256), 256, 0, s>>>(
+      rows_type, nrows, nwidths, mean, sigma, static_cast<double>(nsigma), thr);
+  const int E = kBoxTile + (1 << (nwidths - 1)) - 1;
+  const size_t smem = static_cast<size_t>(E) * sizeof(V);
+  cudaError_t e = cudaFuncSetAttribute(dd_boxcar_sweep<X, V, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dd_boxcar_sweep<X, V, true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return DD_ERR_CUDA;
+  const unsigned grid = static_cast<unsigned>(m);
+  dd_boxcar_sweep<X, V, false><<<grid, kBoxThreads, smem, s>>>(
+      rows, pitch, ncols, static_cast<int>(ntiles), nwidths, thr, mean, sigma, counts, offsets,
+      pulses, capacity);
+  dd_boxcar_scan<<<1, kScanThreads, 0, s>>>(counts, m, offsets, total);
+  if (capacity > 0)
+    dd_boxcar_sweep<X, V, true><<<grid, kBoxThreads, smem, s>>>(
+        rows, pitch, ncols, static_cast<int>(ntiles), nwidths, thr, mean, sigma, counts, offsets,
+        pulses, capacity);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return DD_ERR_CUDA;
+  int64_t found = 0;
+  e = cudaMemcpyAsync(&found, total, sizeof(found), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return DD_ERR_CUDA;
+  *count = found;
+  return found > capacity ? DD_ERR_OVERFLOW : DD_OK;
+}
+
+}  // namespace
+
+extern "C" int dd_median_filter(const void *in, int64_t in_pitch, int32_t rows_type, int32_t nrows,
+                                int64_t ncols, int32_t width, void *out, int64_t out_pitch,
+                                void *stream) {
+  if (rows_type != DD_ROWS_I32 && rows_type != DD_ROWS_F32) return DD_ERR_DTYPE;
+  if (!in || !out) return DD_ERR_ARG;
+  if (nrows < 1 || ncols < 1 || ncols > INT32_MAX) return DD_ERR_SIZE;
+  if (width < 1 || width > 15 || width % 2 == 0) return DD_ERR_ARG;
+  if (in_pitch < ncols || out_pitch < ncols) return DD_ERR_ARG;
+  if (overlap(in, row_span(nrows, in_pitch, ncols, 4), out, row_span(nrows, out_pitch, ncols, 4)))
+    return DD_ERR_ARG;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (rows_type == DD_ROWS_I32)
+    return launch_median(static_cast<const int32_t *>(in), in_pitch, nrows, ncols, width,
+                         static_cast<int32_t *>(out), out_pitch, s);
+  return launch_median(static_cast<const float *>(in), in_pitch, nrows, ncols, width,
+                       static_cast<float *>(out), out_pitch, s);
+}
+
+extern "C" int dd_detrend(const void *in, int64_t in_pitch, int32_t rows_type, int32_t nrows,
+                          int64_t ncols, float *out, int64_t out_pitch, double *coef, void *stream) {
+  if (rows_type != DD_ROWS_I32 && rows_type != DD_ROWS_F32) return DD_ERR_DTYPE;
+  if (!in || !out) return DD_ERR_ARG;
+  if (nrows < 1 || ncols < 1 || ncols > (static_cast<int64_t>(1) << 24)) return DD_ERR_SIZE;
+  if (in_pitch < ncols || out_pitch < ncols) return DD_ERR_ARG;
+  const bool same = static_cast<const void *>(out) == in && out_pitch == in_pitch;
+  if (!(same && rows_type == DD_ROWS_F32) &&
+      overlap(in, row_span(nrows, in_pitch, ncols, 4), out, row_span(nrows, out_pitch, ncols, 4)))
+    return DD_ERR_ARG;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bool vec = reinterpret_cast<uintptr_t>(in) % 16 == 0 && in_pitch % 4 == 0 &&
+                   reinterpret_cast<uintptr_t>(out) % 16 == 0 && out_pitch % 4 == 0;
+  if (rows_type == DD_ROWS_I32) {
+    const int32_t *x = static_cast<const int32_t *>(in);
+    if (vec) dd_detrend_rows<int32_t, true><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
+    else dd_detrend_rows<int32_t, false><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
+  } else {
+    const float *x = static_cast<const float *>(in);
+    if (vec) dd_detrend_rows<float, true><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
+    else dd_detrend_rows<float, false><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
+  }
+  return cuda_status(cudaGetLastError());
+}
+
+extern "C" int dd_boxcar_workspace_bytes(int32_t nrows, int64_t ncols, int64_t *bytes) {
+  if (!bytes) return DD_ERR_ARG;
+  if (nrows < 1 || ncols < 1 || ncols > INT32_MAX) return DD_ERR_SIZE;
+  *bytes = box_workspace(nrows, ncols);
+  return DD_OK;
+}
+
+extern "C" int dd_boxcar_detect(const void *rows, int64_t pitch, int32_t rows_type, int32_t nrows,
+                                int64_t ncols, const double *mean, const double *sigma,
+                                int32_t nwidths, float nsigma, void *workspace,
+                                int64_t workspace_bytes, dd_pulse *pulses, int64_t capacity,
+                                int64_t *count, void *stream) {
+  if (rows_type != DD_ROWS_I32 && rows_type != DD_ROWS_F32) return DD_ERR_DTYPE;
+  if (!rows || !count || !workspace || capacity < 0 || (capacity > 0 && !pulses)) return DD_ERR_ARG;
+  if (nrows < 1 || ncols < 1 || ncols > INT32_MAX) return DD_ERR_SIZE;
+  if (nwidths < 1 || nwidths > kMaxWidths || !std::isfinite(nsigma) || pitch < ncols)
+    return DD_ERR_ARG;
+  if (box_tiles(ncols) * nrows > INT32_MAX) return DD_ERR_SIZE;
+  if (workspace_bytes < box_workspace(nrows, ncols) ||
+      reinterpret_cast<uintptr_t>(workspace) % 16 != 0)
+    return DD_ERR_ARG;
+  *count = 0;
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (rows_type == DD_ROWS_I32)
+    return launch_boxcar<int32_t, long long>(static_cast<const int32_t *>(rows), pitch, nrows, ncols,
+                                             mean, sigma, nwidths, nsigma, ws, pulses, capacity,
+                                             count, s);
+  return launch_boxcar<float, float>(static_cast<const float *>(rows), pitch, nrows, ncols, mean,
+                                     sigma, nwidths, nsigma, ws, pulses, capacity, count, s);
+}

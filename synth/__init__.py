@@ -241,3 +241,33 @@ def random_block(rng: np.random.Generator, nchan: int, nsamp: int, dtype: str,
     if pitch > nsamp:
         b[:, nsamp:] = 0
     return b
+
+
+def series_rows(rng: np.random.Generator, nrows: int, ncols: int, dtype: str,
+                level: float = 0.0, noise: float = 1.0, slope: float = 0.0,
+                pulses: int = 0, pulse_amp: float = 0.0, pulse_width=(1, 64),
+                pitch: int | None = None) -> np.ndarray:
+    """Rows shaped like dedispersed series, for the post-processing tests.
+
+    Per row: ``level`` + a linear drift of ``slope`` per sample with a
+    random sign + N(0, noise^2) noise + ``pulses`` top-hat pulses of height
+    ``pulse_amp`` x noise, widths uniform in ``pulse_width``, at uniform
+    start samples.  ``dtype`` "i32" rounds half away from zero to int32,
+    "f32" keeps float32.  Columns past ncols (pitch > ncols) hold a large
+    sentinel that no result may read."""
+    pitch = ncols if pitch is None else pitch
+    t = np.arange(ncols, dtype=np.float64)
+    y = level + np.outer(rng.choice((-1.0, 1.0), nrows) * slope, t)
+    y = y + noise * rng.standard_normal((nrows, ncols))
+    for r in range(nrows):
+        for _ in range(pulses):
+            w = int(rng.integers(pulse_width[0], pulse_width[1] + 1))
+            t0 = int(rng.integers(0, max(1, ncols - w)))
+            y[r, t0:t0 + w] += pulse_amp * noise
+    out_dtype = np.int32 if dtype == "i32" else np.float32
+    rows = np.full((nrows, pitch), 1 << 30, dtype=out_dtype)
+    if dtype == "i32":
+        rows[:, :ncols] = (np.sign(y) * np.floor(np.abs(y) + 0.5)).astype(np.int32)
+    else:
+        rows[:, :ncols] = y.astype(np.float32)
+    return rows
