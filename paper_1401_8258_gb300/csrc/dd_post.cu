@@ -219,9 +219,11 @@ __device__ V block_sum(V v, V *scratch) {
   return total;
 }
 
-template <typename X, bool VEC>
-__device__ __forceinline__ void load16(const X *x, int64_t t, int64_t n, X (&v)[kDtChunk]) {
-  if (VEC && t + kDtChunk <= n) {
+// v[k] = x[t + k] for t + k < lim, else 0; one 16-byte load per four
+// samples when the chunk is whole (x + t is then 16-byte aligned).
+template <typename X>
+__device__ __forceinline__ void load16(const X *x, int64_t t, int64_t lim, X (&v)[kDtChunk]) {
+  if (t + kDtChunk <= lim) {
     const int4 *p = reinterpret_cast<const int4 *>(x + t);
 #pragma unroll
     for (int q = 0; q < kDtChunk / 4; ++q) {
@@ -233,7 +235,7 @@ __device__ __forceinline__ void load16(const X *x, int64_t t, int64_t n, X (&v)[
     }
   } else {
 #pragma unroll
-    for (int k = 0; k < kDtChunk; ++k) v[k] = t + k < n ? x[t + k] : X(0);
+    for (int k = 0; k < kDtChunk; ++k) v[k] = t + k < lim ? x[t + k] : X(0);
   }
 }
 
@@ -303,7 +305,18 @@ __device__ __noinline__ void line_f32(double sy, double sty, float y0, int64_t n
   line[1] = b;
 }
 
-template <typename X, bool VEC>
+// Chunks of a row: the head [0, head) up to the first 16-byte boundary of the
+// row (thread 0), then whole 16-sample chunks from `head`, one per thread
+// in turn; `head` < 4.
+template <typename F>
+__device__ __forceinline__ void for_chunks(int64_t n, int head, F &&f) {
+  if (threadIdx.x == 0 && head > 0) f(static_cast<int64_t>(0), static_cast<int64_t>(head));
+  const int64_t step = static_cast<int64_t>(kDtThreads) * kDtChunk;
+  for (int64_t t = head + static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step)
+    f(t, n);
+}
+
+template <typename X>
 __global__ void __launch_bounds__(kDtThreads, 1)
 dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t out_pitch,
                 double *coef) {  // no __restrict__: out may be in (float rows, in place)
@@ -313,13 +326,16 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
   const int64_t row = blockIdx.x;
   const X *x = in + row * in_pitch;
   float *z = out + row * out_pitch;
-  const int64_t step = static_cast<int64_t>(kDtThreads) * kDtChunk;
+  const int head = static_cast<int>(
+      min(n, static_cast<int64_t>(((16 - reinterpret_cast<uintptr_t>(x) % 16) % 16) / 4)));
+  // 16-byte stores when the output row has the input row's alignment phase
+  const bool zvec = (reinterpret_cast<uintptr_t>(z + head) % 16) == 0;
 
   if constexpr (std::is_integral<X>::value) {  // int32 rows: exact sums
     i128 sy = 0, sty = 0, syy = 0;
-    for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+    for_chunks(n, head, [&](int64_t t, int64_t lim) {
       X v[kDtChunk];
-      load16<X, VEC>(x, t, n, v);
+      load16<X>(x, t, lim, v);
       long long c1 = 0, c2 = 0;  // chunk sums of y and of k y, k = 0..15
       u128 c3 = 0;
 #pragma unroll
@@ -332,7 +348,7 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
       sy += c1;
       sty += static_cast<i128>(t) * c1 + c2;
       syy += static_cast<i128>(c3);
-    }
+    });
     sy = block_sum(sy, s_i);
     sty = block_sum(sty, s_i);
     syy = block_sum(syy, s_i);
@@ -340,19 +356,19 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
   } else {  // float rows: three passes in the thesis's order
     const float y0 = x[0];
     double sy = 0, sty = 0;
-    for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+    for_chunks(n, head, [&](int64_t t, int64_t lim) {
       X v[kDtChunk];
-      load16<X, VEC>(x, t, n, v);
+      load16<X>(x, t, lim, v);
       float d[kDtChunk], kd[kDtChunk];
 #pragma unroll
       for (int k = 0; k < kDtChunk; ++k) {
-        d[k] = t + k < n ? v[k] - y0 : 0.0f;
+        d[k] = t + k < lim ? v[k] - y0 : 0.0f;
         kd[k] = static_cast<float>(k) * d[k];
       }
       const double c1 = tree16(d), c2 = tree16(kd);
       sy += c1;
       sty += static_cast<double>(t) * c1 + c2;
-    }
+    });
     sy = block_sum(sy, s_d);
     sty = block_sum(sty, s_d);
     if (threadIdx.x == 0) line_f32(sy, sty, y0, n, s_line);
@@ -360,9 +376,9 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
     const double a = s_line[0], b = s_line[1];
     const float bf = static_cast<float>(b);
     double rss = 0;
-    for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+    for_chunks(n, head, [&](int64_t t, int64_t lim) {
       X v[kDtChunk];
-      load16<X, VEC>(x, t, n, v);
+      load16<X>(x, t, lim, v);
       const double base = fma(b, static_cast<double>(t), a);
       const double hi = floor(base);
       const float lo = static_cast<float>(base - hi), hf = static_cast<float>(hi);
@@ -370,10 +386,10 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
 #pragma unroll
       for (int k = 0; k < kDtChunk; ++k) {
         const float r = (v[k] - hf) - fmaf(bf, static_cast<float>(k), lo);
-        r2[k] = t + k < n ? r * r : 0.0f;
+        r2[k] = t + k < lim ? r * r : 0.0f;
       }
       rss += tree16(r2);
-    }
+    });
     rss = block_sum(rss, s_d);
     if (threadIdx.x == 0) s_line[2] = rss > 0 ? sqrt(rss / static_cast<double>(n)) : 0.0;
   }
@@ -386,9 +402,9 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
   }
   const float inv = s > 0 ? static_cast<float>(1.0 / s) : 0.0f;
   const float bf = static_cast<float>(b);
-  for (int64_t t = static_cast<int64_t>(threadIdx.x) * kDtChunk; t < n; t += step) {
+  for_chunks(n, head, [&](int64_t t, int64_t lim) {
     X v[kDtChunk];
-    load16<X, VEC>(x, t, n, v);
+    load16<X>(x, t, lim, v);
     const double base = fma(b, static_cast<double>(t), a);
     const double hi = floor(base);
     const float lo = static_cast<float>(base - hi);
@@ -403,7 +419,7 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
       }
       r[k] *= inv;
     }
-    if (VEC && t + kDtChunk <= n) {
+    if (zvec && t + kDtChunk <= lim) {
       float4 *p = reinterpret_cast<float4 *>(z + t);
 #pragma unroll
       for (int q = 0; q < kDtChunk / 4; ++q)
@@ -411,9 +427,9 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
     } else {
 #pragma unroll
       for (int k = 0; k < kDtChunk; ++k)
-        if (t + k < n) z[t + k] = r[k];
+        if (t + k < lim) z[t + k] = r[k];
     }
-  }
+  });
 }
 
 // ------------------------------------------------------------------ boxcar
@@ -434,6 +450,9 @@ constexpr int kBoxTile = 4096;
 constexpr int kBoxOwn = kBoxTile / kBoxThreads;  // 16 outputs per thread
 constexpr int kMaxWidths = 12;
 constexpr int kBoxPer = (kBoxTile + (1 << (kMaxWidths - 1)) - 1 + kBoxThreads - 1) / kBoxThreads;
+constexpr int kSmallWidths = 8;  // up to 128 samples: fewer registers per thread
+constexpr int kBoxPerSmall =
+    (kBoxTile + (1 << (kSmallWidths - 1)) - 1 + kBoxThreads - 1) / kBoxThreads;
 constexpr int kScanThreads = 1024;
 
 __device__ __forceinline__ double boxcar_snr(double sum, int w, double mean, double sigma) {
@@ -502,15 +521,17 @@ template <> __device__ __forceinline__ bool passes<float>(float s, int64_t thr) 
   return s >= __uint_as_float(static_cast<uint32_t>(thr));
 }
 
-template <typename X, typename V, bool WRITE>
+template <typename X, typename V, bool WRITE, int PER>
 __global__ void __launch_bounds__(kBoxThreads)
 dd_boxcar_sweep(const X *__restrict__ rows, int64_t pitch, int64_t ncols, int ntiles, int nwidths,
                 const int64_t *__restrict__ thr_all, const double *mean, const double *sigma,
                 int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
                 dd_pulse *__restrict__ pulses, int64_t capacity) {
+  // two buffers of E sums: width w reads buffer (j-1)&1 and writes j&1, so
+  // one barrier per width separates every read from the next overwrite
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V *S = reinterpret_cast<V *>(smem_raw);
   __shared__ int64_t s_thr[kMaxWidths];
+  __shared__ double s_wmu[kMaxWidths], s_den[kMaxWidths], s_rden[kMaxWidths];
   __shared__ uint32_t s_bits[kBoxTile / 32];
   __shared__ int s_pre[kBoxTile / 32];
   __shared__ int s_cnt[kBoxThreads / 32];
@@ -519,43 +540,57 @@ dd_boxcar_sweep(const X *__restrict__ rows, int64_t pitch, int64_t ncols, int nt
   const int64_t t0 = static_cast<int64_t>(blockIdx.x % ntiles) * kBoxTile;
   const X *x = rows + row * pitch;
   const int E = kBoxTile + (1 << (nwidths - 1)) - 1;
-  if (threadIdx.x < kMaxWidths) s_thr[threadIdx.x] = thr_all[row * kMaxWidths + threadIdx.x];
-  V reg[kBoxPer];
+  V *buf0 = reinterpret_cast<V *>(smem_raw);
+  V *buf1 = buf0 + E;
+  if (threadIdx.x < kMaxWidths) {
+    const int j = threadIdx.x;
+    s_thr[j] = thr_all[row * kMaxWidths + j];
+    if (WRITE) {
+      // the S/N's constant parts, rounded exactly as in the S/N itself
+      const double mu = mean ? mean[row] : 0.0, sg = sigma ? sigma[row] : 1.0;
+      const double dw = static_cast<double>(1 << j);
+      s_wmu[j] = __dmul_rn(dw, mu);
+      s_den[j] = __dmul_rn(sg, __dsqrt_rn(dw));
+      s_rden[j] = 1.0 / s_den[j];
+    }
+  }
+  V reg[PER];
 #pragma unroll
-  for (int m = 0; m < kBoxPer; ++m) {
+  for (int m = 0; m < PER; ++m) {
     const int i = threadIdx.x + kBoxThreads * m;
     const int64_t g = t0 + i;
     reg[m] = (i < E && g < ncols) ? static_cast<V>(x[g]) : V(0);
-    if (i < E) S[i] = reg[m];
+    if (i < E) buf0[i] = reg[m];
   }
   __syncthreads();
   uint32_t mask = 0;  // bit m: element threadIdx.x + 256 m is a pulse start
-  double bsnr[WRITE ? kBoxOwn : 1];
-  int bw[WRITE ? kBoxOwn : 1];
+  // write pass: per owned element the best width so far, its sum and an
+  // approximate S/N (num / den through a rounded reciprocal: within a few
+  // units in the last place of the exact quotient)
+  double ba[WRITE ? kBoxOwn : 1];
+  int bj[WRITE ? kBoxOwn : 1];
   V bval[WRITE ? kBoxOwn : 1];
   if constexpr (WRITE) {
 #pragma unroll
     for (int m = 0; m < kBoxOwn; ++m) {
-      bsnr[m] = -INFINITY;
-      bw[m] = 0;
+      ba[m] = -INFINITY;
+      bj[m] = -1;
       bval[m] = V(0);
     }
   }
-  const double mu = mean ? mean[row] : 0.0, sg = sigma ? sigma[row] : 1.0;
   for (int j = 0; j < nwidths; ++j) {
     const int w = 1 << j;
     if (j > 0) {
       const int half = w >> 1, lim = E - w + 1;
+      const V *src = (j & 1) ? buf0 : buf1;
+      V *dst = (j & 1) ? buf1 : buf0;
 #pragma unroll
-      for (int m = 0; m < kBoxPer; ++m) {
+      for (int m = 0; m < PER; ++m) {
         const int i = threadIdx.x + kBoxThreads * m;
-        if (i < lim) reg[m] = reg[m] + S[i + half];
-      }
-      __syncthreads();
-#pragma unroll
-      for (int m = 0; m < kBoxPer; ++m) {
-        const int i = threadIdx.x + kBoxThreads * m;
-        if (i < lim) S[i] = reg[m];
+        if (i < lim) {
+          reg[m] = reg[m] + src[i + half];
+          dst[i] = reg[m];
+        }
       }
     }
     const int64_t thr = s_thr[j];
@@ -565,10 +600,24 @@ dd_boxcar_sweep(const X *__restrict__ rows, int64_t pitch, int64_t ncols, int nt
       if (t + w <= ncols && passes<V>(reg[m], thr)) {
         mask |= 1u << m;
         if constexpr (WRITE) {
-          const double snr = boxcar_snr(static_cast<double>(reg[m]), w, mu, sg);
-          if (snr > bsnr[m]) {
-            bsnr[m] = snr;
-            bw[m] = w;
+          // the oracle keeps the first width with the largest exact S/N;
+          // the approximation decides unless two widths are within 2^-40
+          const double num = __dsub_rn(static_cast<double>(reg[m]), s_wmu[j]);
+          const double a = num * s_rden[j];
+          bool take;
+          if (bj[m] < 0) {
+            take = true;
+          } else if (fabs(a - ba[m]) > 0x1p-40 * fmax(fabs(a), fabs(ba[m]))) {
+            take = a > ba[m];
+          } else {
+            const int k = bj[m];
+            const double e_old =
+                __ddiv_rn(__dsub_rn(static_cast<double>(bval[m]), s_wmu[k]), s_den[k]);
+            take = __ddiv_rn(num, s_den[j]) > e_old;
+          }
+          if (take) {
+            ba[m] = a;
+            bj[m] = j;
             bval[m] = reg[m];
           }
         }
@@ -626,8 +675,10 @@ dd_boxcar_sweep(const X *__restrict__ rows, int64_t pitch, int64_t ncols, int nt
         dd_pulse p;
         p.dm_idx = static_cast<int32_t>(row);
         p.t = static_cast<int32_t>(t0 + i);
-        p.width = bw[m];
-        p.snr = __double2float_rn(bsnr[m]);
+        const int k = bj[m];
+        p.width = 1 << k;
+        p.snr = __double2float_rn(
+            __ddiv_rn(__dsub_rn(static_cast<double>(bval[m]), s_wmu[k]), s_den[k]));
         p.value = static_cast<double>(bval[m]);
         pulses[pos] = p;
       }
@@ -668,6 +719,28 @@ inline int64_t box_workspace(int32_t nrows, int64_t ncols) {
   return 8 * (static_cast<int64_t>(nrows) * kMaxWidths + 2 * m + 2);
 }
 
+template <typename X, typename V, int PER>
+cudaError_t sweep_launches(const X *rows, int64_t pitch, int64_t ncols, int ntiles, int nwidths,
+                           const int64_t *thr, const double *mean, const double *sigma,
+                           int64_t *counts, int64_t *offsets, int64_t *total, int64_t m,
+                           dd_pulse *pulses, int64_t capacity, unsigned grid, size_t smem,
+                           cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(dd_boxcar_sweep<X, V, false, PER>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(dd_boxcar_sweep<X, V, true, PER>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  dd_boxcar_sweep<X, V, false, PER><<<grid, kBoxThreads, smem, s>>>(
+      rows, pitch, ncols, ntiles, nwidths, thr, mean, sigma, counts, offsets, pulses, capacity);
+  dd_boxcar_scan<<<1, kScanThreads, 0, s>>>(counts, m, offsets, total);
+  if (capacity > 0)
+    dd_boxcar_sweep<X, V, true, PER><<<grid, kBoxThreads, smem, s>>>(
+        rows, pitch, ncols, ntiles, nwidths, thr, mean, sigma, counts, offsets, pulses, capacity);
+  return cudaGetLastError();
+}
+
 template <typename X, typename V>
 int launch_boxcar(const X *rows, int64_t pitch, int32_t nrows, int64_t ncols, const double *mean,
                   const double *sigma, int nwidths, float nsigma, unsigned char *ws, dd_pulse *pulses,
@@ -683,22 +756,18 @@ int launch_boxcar(const X *rows, int64_t pitch, int32_t nrows, int64_t ncols, co
   dd_boxcar_thresholds<<<static_cast<unsigned>((nthr + 255) / 256), 256, 0, s>>>(
       rows_type, nrows, nwidths, mean, sigma, static_cast<double>(nsigma), thr);
   const int E = kBoxTile + (1 << (nwidths - 1)) - 1;
-  const size_t smem = static_cast<size_t>(E) * sizeof(V);
-  cudaError_t e = cudaFuncSetAttribute(dd_boxcar_sweep<X, V, false>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(dd_boxcar_sweep<X, V, true>,
-                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (e != cudaSuccess) return DD_ERR_CUDA;
+  const size_t smem = 2 * static_cast<size_t>(E) * sizeof(V);
   const unsigned grid = static_cast<unsigned>(m);
-  dd_boxcar_sweep<X, V, false><<<grid, kBoxThreads, smem, s>>>(
-      rows, pitch, ncols, static_cast<int>(ntiles), nwidths, thr, mean, sigma, counts, offsets,
-      pulses, capacity);
-  dd_boxcar_scan<<<1, kScanThreads, 0, s>>>(counts, m, offsets, total);
-  if (capacity > 0)
-    dd_boxcar_sweep<X, V, true><<<grid, kBoxThreads, smem, s>>>(
-        rows, pitch, ncols, static_cast<int>(ntiles), nwidths, thr, mean, sigma, counts, offsets,
-        pulses, capacity);
+  const int nt = static_cast<int>(ntiles);
+  cudaError_t e;
+  if (nwidths <= kSmallWidths)
+    e = sweep_launches<X, V, kBoxPerSmall>(rows, pitch, ncols, nt, nwidths, thr, mean, sigma,
+                                           counts, offsets, total, m, pulses, capacity, grid,
+                                           smem, s);
+  else
+    e = sweep_launches<X, V, kBoxPer>(rows, pitch, ncols, nt, nwidths, thr, mean, sigma, counts,
+                                      offsets, total, m, pulses, capacity, grid, smem, s);
+  if (e != cudaSuccess) return DD_ERR_CUDA;
   e = cudaGetLastError();
   if (e != cudaSuccess) return DD_ERR_CUDA;
   int64_t found = 0;
@@ -740,17 +809,14 @@ extern "C" int dd_detrend(const void *in, int64_t in_pitch, int32_t rows_type, i
       overlap(in, row_span(nrows, in_pitch, ncols, 4), out, row_span(nrows, out_pitch, ncols, 4)))
     return DD_ERR_ARG;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  const bool vec = reinterpret_cast<uintptr_t>(in) % 16 == 0 && in_pitch % 4 == 0 &&
-                   reinterpret_cast<uintptr_t>(out) % 16 == 0 && out_pitch % 4 == 0;
-  if (rows_type == DD_ROWS_I32) {
-    const int32_t *x = static_cast<const int32_t *>(in);
-    if (vec) dd_detrend_rows<int32_t, true><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
-    else dd_detrend_rows<int32_t, false><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
-  } else {
-    const float *x = static_cast<const float *>(in);
-    if (vec) dd_detrend_rows<float, true><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
-    else dd_detrend_rows<float, false><<<nrows, kDtThreads, 0, s>>>(x, in_pitch, ncols, out, out_pitch, coef);
-  }
+  if (reinterpret_cast<uintptr_t>(in) % 4 != 0 || reinterpret_cast<uintptr_t>(out) % 4 != 0)
+    return DD_ERR_ARG;
+  if (rows_type == DD_ROWS_I32)
+    dd_detrend_rows<int32_t><<<nrows, kDtThreads, 0, s>>>(static_cast<const int32_t *>(in),
+                                                          in_pitch, ncols, out, out_pitch, coef);
+  else
+    dd_detrend_rows<float><<<nrows, kDtThreads, 0, s>>>(static_cast<const float *>(in), in_pitch,
+                                                        ncols, out, out_pitch, coef);
   return cuda_status(cudaGetLastError());
 }
 
