@@ -1,0 +1,130 @@
+"""Pins of the subband oracle (``oracle/approx.py``) and of the analytic S/N
+loss curve it is checked with.
+
+* The thesis's incorrect-dedispersion curve (Sec. 3.6) against the brute-force
+  oracle on a Gaussian pulse dispersed with exact (unrounded) delays: a pin
+  of the curve's transcription and of the brute-force sum at once.
+* Subband dedispersion (Sec. 2.1.3) equals the brute-force sum exactly at the
+  nominal trials, for one channel per subband and for one trial per group.
+* Away from the nominal trials its peak loss follows the same curve applied
+  to each subband (bandwidth of the subband, DM error = trial - nominal).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import approx
+import synth
+
+K_DM = 4.148808e3  # MHz^2 pc^-1 cm^3 s (Sec. 1.2.1)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    oracle.build()
+
+
+def gaussian_pulse_block(nchan, f_top, df, t_samp, dm, fwhm_ms, nsamp, t0_s):
+    """Unit-height Gaussian pulse dispersed with the exact cold-plasma delay."""
+    t = np.arange(nsamp) * t_samp
+    f = f_top - np.arange(nchan) * df
+    tau = K_DM * dm * (f ** -2 - f_top ** -2)
+    sig = fwhm_ms * 1e-3 / (2 * math.sqrt(2 * math.log(2)))
+    return np.exp(-0.5 * ((t[None, :] - t0_s - tau[:, None]) / sig) ** 2).astype(np.float32)
+
+
+BAND = dict(nchan=256, f_top=416.0, bw=16.0, t_samp=51.2e-6)
+
+
+def test_curve_limits():
+    assert approx.smearing_peak_ratio(0.0, 16, 0.4, 1.0) == 1.0
+    # small zeta: 1 - zeta^2 / 3; large zeta: sqrt(pi) / (2 zeta)
+    z = 1e-3
+    ddm = z * 1.0 * 0.4 ** 3 / (6.91e-3 * 16)
+    assert approx.smearing_peak_ratio(ddm, 16, 0.4, 1.0) == pytest.approx(1 - z * z / 3, rel=1e-9)
+    ddm = 50 * 1.0 * 0.4 ** 3 / (6.91e-3 * 16)
+    assert approx.smearing_peak_ratio(ddm, 16, 0.4, 1.0) == pytest.approx(
+        math.sqrt(math.pi) / 100, rel=1e-9)
+
+
+@pytest.mark.parametrize("ddm,width_ms", [(0.5, 5.0), (1.0, 5.0), (3.0, 5.0), (5.0, 5.0),
+                                          (1.0, 2.0), (2.0, 2.0)])
+def test_brute_force_smearing_matches_analytic_curve(ddm, width_ms):
+    b = BAND
+    df = b["bw"] / b["nchan"]
+    dm = 50.0
+    blk = gaussian_pulse_block(b["nchan"], b["f_top"], df, b["t_samp"], dm, width_ms, 6000, 0.05)
+    delays, _ = oracle.delay_table(b["nchan"], b["f_top"], df, b["t_samp"],
+                                   np.array([dm, dm + ddm]))
+    D = oracle.dedisperse(blk, delays)
+    measured = D[1].max() / D[0].max()
+    f_centre = (b["f_top"] - b["bw"] / 2 + df / 2) / 1000
+    predicted = approx.smearing_peak_ratio(ddm, b["bw"], f_centre, width_ms)
+    assert measured == pytest.approx(predicted, abs=0.01)
+
+
+def geometry(nchan=256, ndm=96, step=0.5):
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=nchan, ndm=ndm)
+    wl.chan_width_mhz = 16.0 / nchan
+    wl.dms = synth.dm_grid(0.0, step, ndm)
+    return wl
+
+
+def test_subband_exact_at_nominal_trials_and_degenerate_sizes():
+    wl = geometry()
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s,
+                                    wl.dms)
+    rng = np.random.default_rng(4)
+    block = synth.random_block(rng, wl.nchan, mx + 3000, "u8")
+    brute = oracle.dedisperse(block, delays)
+    for cps, dpg in ((32, 16), (16, 7), (64, 32)):
+        tb = approx.SubbandTables(delays, cps, dpg)
+        out = approx.subband_dedisperse(block, delays, cps, dpg)
+        # the step delays reach at most the nominal trials' span, so the
+        # output may run a little longer than the brute-force one
+        assert out.shape[1] == block.shape[1] - tb.maxshift
+        n = min(out.shape[1], brute.shape[1])
+        assert np.array_equal(out[tb.nominal, :n], brute[tb.nominal, :n])
+        assert not np.array_equal(out[:, :n], brute[:, :n])  # other trials are approximate
+    for cps, dpg in ((1, 16), (32, 1)):
+        out = approx.subband_dedisperse(block, delays, cps, dpg)
+        n = min(out.shape[1], brute.shape[1])
+        assert np.array_equal(out[:, :n], brute[:, :n])
+
+
+def test_subband_tables():
+    wl = geometry(nchan=100, ndm=50)
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s,
+                                   wl.dms)
+    tb = approx.SubbandTables(delays, 32, 16)
+    assert tb.first == [0, 32, 64, 96] and [t.shape[0] for t in tb.d1] == [32, 32, 32, 4]
+    assert tb.groups == [(0, 16), (16, 32), (32, 48), (48, 50)]
+    assert tb.nominal == [7, 23, 39, 48]
+    for s, c0 in enumerate(tb.first):
+        assert np.all(tb.d1[s][0] == 0) and np.all(np.diff(tb.d1[s], axis=0) >= 0)
+    assert np.array_equal(tb.d2[1], delays[tb.first][:, 16:32])
+
+
+@pytest.mark.parametrize("offset", [-6, -3, 3, 6])
+def test_subband_loss_follows_analytic_curve_per_subband(offset):
+    """A pulse at trial nominal + offset: the subband sum spreads each
+    subband by the DM error (offset trials) over the subband's bandwidth."""
+    b = BAND
+    nchan, cps, dpg, width = b["nchan"], 32, 16, 0.5
+    df = b["bw"] / nchan
+    dms = synth.dm_grid(40.0, 0.5, 48)
+    tb_probe = approx.SubbandTables(np.zeros((nchan, 48), dtype=np.int32), cps, dpg)
+    nominal = tb_probe.nominal[1]
+    d = nominal + offset
+    blk = gaussian_pulse_block(nchan, b["f_top"], df, b["t_samp"], dms[d], width, 9000, 0.08)
+    delays, _ = oracle.delay_table(nchan, b["f_top"], df, b["t_samp"], dms)
+    brute = oracle.dedisperse(blk, delays)
+    sub = approx.subband_dedisperse(blk, delays, cps, dpg)
+    measured = sub[d].max() / brute[d].max()
+    ddm = dms[d] - dms[nominal]
+    f_centres = [(b["f_top"] - (c0 + cps / 2 - 0.5) * df) / 1000 for c0 in tb_probe.first]
+    predicted = np.mean([approx.smearing_peak_ratio(ddm, cps * df, f, width) for f in f_centres])
+    assert predicted < 0.97  # a visible loss
+    assert measured == pytest.approx(predicted, abs=0.03)
