@@ -96,6 +96,16 @@ int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz, double chan_w
  * plan's device first. */
 int dd_plan_destroy(dd_plan *p);
 
+/* A plan for an explicit delay table instead of the dispersion law: host
+ * int32 delays[nchan][ndm] (channel-major, copied), every entry in
+ * 0 .. 2^30; out[d][t] = sum_c block[c][t + delays[c][d]] with the same
+ * kernels, layouts and detection as dd_plan_create.  The thesis's two-step
+ * approximations (subband and tree dedispersion, Sec. 2.1) are brute-force
+ * sums over such tables.  DD_ERR_ARG for a null table or a negative or
+ * larger entry. */
+int dd_plan_create_from_delays(dd_plan **out, int32_t nchan, int32_t ndm, const int32_t *delays,
+                               int32_t in_dtype, int32_t device);
+
 /* Largest delay of the plan (maxshift, Sec. 3.4). */
 int dd_plan_max_delay(const dd_plan *p, int32_t *maxshift);
 
@@ -120,6 +130,14 @@ int dd_plan_delays(const dd_plan *p, int32_t *host_out);
  * results. */
 int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
                void *out, void *stream);
+
+/* dd_execute with output rows `out_pitch` elements apart (out_pitch >=
+ * nsamp_out; DD_ERR_ARG otherwise): row d starts at out + d * out_pitch, and
+ * only its first nsamp_out elements are written.  Lets a caller place the
+ * rows of several plans into one interleaved array (the subband variant,
+ * dd_subband.h, does this). */
+int dd_execute_pitched(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
+                       void *out, int64_t out_pitch, void *stream);
 
 /* Normalise and threshold a dedispersed block (Sec. 3.5, 3.6) on `stream`.
  *   out:   device pointer to [ndm][nsamp_out] as written by dd_execute;

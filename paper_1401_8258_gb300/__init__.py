@@ -29,7 +29,7 @@ __all__ = [
     "dd_plan_max_delay", "dd_plan_nsamp_out", "dd_plan_delays", "dd_execute", "dd_detect",
     "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
     "dd_run", "Batch", "dd_batch_create", "dd_batch_destroy", "dd_batch_run", "Stream",
-    "push_streams", "median_filter", "detrend", "boxcar_detect", "PULSE_DTYPE",
+    "push_streams", "median_filter", "detrend", "boxcar_detect", "PULSE_DTYPE", "Subband",
 ]
 
 _TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
@@ -303,3 +303,50 @@ def boxcar_detect(rows, nwidths, nsigma, mean=None, sigma=None, capacity=1 << 16
                                         capacity, stream)
     got = pulses[:min(total, capacity)].cpu().numpy().view(PULSE_DTYPE).reshape(-1)
     return got, total
+
+
+class Subband:
+    """Owner of a dd_subband handle (two-step subband dedispersion,
+    include/dd_subband.h) working on torch device tensors."""
+
+    def __init__(self, nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype,
+                 chans_per_subband, dms_per_group, device=0):
+        self.nchan, self.ndm, self.dtype = int(nchan), len(dms), dtype
+        self.device = device
+        self.handle = _native.dd_subband_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms,
+                                                dtype, chans_per_subband, dms_per_group, device)
+        self.maxshift = _native.dd_subband_max_delay(self.handle)
+        self.nominal = _native.dd_subband_nominal(self.handle)
+
+    def nsamp_out(self, nsamp_in):
+        return int(nsamp_in) - self.maxshift
+
+    def execute(self, block, nsamp_in=None, out=None, stream=None):
+        import torch
+        nsamp_in = block.shape[1] if nsamp_in is None else nsamp_in
+        n = self.nsamp_out(nsamp_in)
+        if out is None:
+            dt = torch.int32 if self.dtype == "u8" else torch.float32
+            out = torch.empty((self.ndm, n), dtype=dt, device=block.device)
+        _native.dd_subband_execute(self.handle, block, nsamp_in, block.stride(0), out, stream)
+        return out
+
+    def launch_count(self):
+        return _native.dd_subband_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            _native.dd_subband_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

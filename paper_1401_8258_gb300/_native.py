@@ -79,6 +79,16 @@ SIGNATURES = [
     ("dd_batch_create", ctypes.c_int, [_vp, _vp, _i32]),
     ("dd_batch_destroy", ctypes.c_int, [_vp]),
     ("dd_batch_run", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp]),
+    ("dd_plan_create_from_delays", ctypes.c_int, [_vp, _i32, _i32, _vp, _i32, _i32]),
+    ("dd_execute_pitched", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp]),
+    # dd_subband.h
+    ("dd_subband_create", ctypes.c_int, [_vp, _i32, _f64, _f64, _f64, _vp, _i32, _i32, _i32, _i32,
+                                         _i32]),
+    ("dd_subband_destroy", ctypes.c_int, [_vp]),
+    ("dd_subband_max_delay", ctypes.c_int, [_vp, _vp]),
+    ("dd_subband_nominal", ctypes.c_int, [_vp, _vp, _vp]),
+    ("dd_subband_execute", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp]),
+    ("dd_subband_launch_count", ctypes.c_int, [_vp, _vp]),
     # dd_post.h
     ("dd_median_filter", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _i32, _vp, _i64, _vp]),
     ("dd_detrend", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _vp, _i64, _vp, _vp]),
@@ -382,3 +392,60 @@ def dd_boxcar_detect(rows, pitch, rows_type, nrows, ncols, mean, sigma, nwidths,
                                  int(capacity), ctypes.addressof(cnt), _stream(stream))
     _check(st, "dd_boxcar_detect", allow=(DD_ERR_OVERFLOW,))
     return st, int(cnt.value)
+
+
+def dd_plan_create_from_delays(delays, dtype, device=0) -> int:
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    d = np.ascontiguousarray(delays, dtype=np.int32)
+    h = ctypes.c_void_p()
+    _check(load().dd_plan_create_from_delays(ctypes.addressof(h), int(d.shape[0]),
+                                             int(d.shape[1]), d.ctypes.data, code, int(device)),
+           "dd_plan_create_from_delays")
+    return h.value
+
+
+def dd_execute_pitched(plan, block, nsamp_in, pitch_elems, out, out_pitch, stream=None) -> None:
+    _check(load().dd_execute_pitched(plan, _addr(block), int(nsamp_in), int(pitch_elems),
+                                     _addr(out), int(out_pitch), _stream(stream)),
+           "dd_execute_pitched")
+
+
+def dd_subband_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype, chans_per_subband,
+                      dms_per_group, device=0) -> int:
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    dms = np.ascontiguousarray(dms, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load().dd_subband_create(ctypes.addressof(h), int(nchan), float(f_top_mhz),
+                                    float(chan_width_mhz), float(t_samp_s), dms.ctypes.data,
+                                    int(dms.size), code, int(chans_per_subband),
+                                    int(dms_per_group), int(device)), "dd_subband_create")
+    return h.value
+
+
+def dd_subband_destroy(sub) -> None:
+    _check(load().dd_subband_destroy(sub), "dd_subband_destroy")
+
+
+def dd_subband_max_delay(sub) -> int:
+    m = ctypes.c_int32(0)
+    _check(load().dd_subband_max_delay(sub, ctypes.addressof(m)), "dd_subband_max_delay")
+    return int(m.value)
+
+
+def dd_subband_nominal(sub) -> np.ndarray:
+    n = ctypes.c_int32(0)
+    _check(load().dd_subband_nominal(sub, None, ctypes.addressof(n)), "dd_subband_nominal")
+    nom = np.zeros(n.value, dtype=np.int32)
+    _check(load().dd_subband_nominal(sub, nom.ctypes.data, None), "dd_subband_nominal")
+    return nom
+
+
+def dd_subband_execute(sub, block, nsamp_in, pitch_elems, out, stream=None) -> None:
+    _check(load().dd_subband_execute(sub, _addr(block), int(nsamp_in), int(pitch_elems),
+                                     _addr(out), _stream(stream)), "dd_subband_execute")
+
+
+def dd_subband_launch_count(sub) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().dd_subband_launch_count(sub, ctypes.addressof(n)), "dd_subband_launch_count")
+    return int(n.value)

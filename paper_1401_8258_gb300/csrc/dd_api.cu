@@ -230,60 +230,106 @@ int validate_execute(const dd_plan *p, int64_t nsamp_in, int64_t pitch, int64_t 
 
 }  // namespace
 
-extern "C" int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz,
-                              double chan_width_mhz, double t_samp_s, const double *dm_list,
-                              int32_t ndm, int32_t in_dtype, int32_t device) {
-  if (!out) return DD_ERR_ARG;
-  *out = nullptr;
-  if (in_dtype != DD_U8 && in_dtype != DD_F16 && in_dtype != DD_F32) return DD_ERR_DTYPE;
-  if (nchan < 1 || ndm < 1 || !dm_list || device < 0) return DD_ERR_ARG;
-  if (ndm > 65535) return DD_ERR_SIZE;  // one grid row per trial in the detection passes
-  if (in_dtype == DD_U8 && static_cast<int64_t>(nchan) * 255 > INT32_MAX) return DD_ERR_RANGE;
+namespace {
 
-  dd_plan *p = new (std::nothrow) dd_plan();
-  if (!p) return DD_ERR_OOM;
-  p->device = device;
-  p->nchan = nchan;
-  p->ndm = ndm;
-  p->dtype = in_dtype;
-  p->f_top = f_top_mhz;
-  p->df = chan_width_mhz;
-  p->t_samp = t_samp_s;
-  try {
-    p->dms.assign(dm_list, dm_list + ndm);
-    p->h_delays.resize(static_cast<size_t>(nchan) * ndm);
-    p->h_mean.resize(ndm);
-    p->h_sigma.resize(ndm);
-  } catch (...) {
-    delete p;
-    return DD_ERR_OOM;
-  }
-  int st = dd_compute_delays(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dm_list, ndm,
-                             p->h_delays.data(), &p->maxshift);
-  if (st != DD_OK) {
-    delete p;
-    return st;
-  }
-  DeviceScope scope(device);
-  if (!scope.ok()) {
-    delete p;
-    return DD_ERR_CUDA;
-  }
-  cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, device);
+// Device buffers and staged-kernel tables of a plan whose host delay table
+// and maxshift are set.
+int finish_plan(dd_plan *p) {
+  DeviceScope scope(p->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
   const size_t table_bytes = p->h_delays.size() * sizeof(int32_t);
   cudaError_t e = cudaMalloc(&p->d_delays, table_bytes);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_error, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_stats, sizeof(dd_row_stats) * ndm);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_stats, sizeof(dd_row_stats) * p->ndm);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_total, sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_total, sizeof(int64_t));
   if (e == cudaSuccess)
     e = cudaMemcpy(p->d_delays, p->h_delays.data(), table_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
-  if (e != cudaSuccess) {
-    destroy_plan(p);
-    return cuda_status(e);
+  if (e != cudaSuccess) return cuda_status(e);
+  return p->dtype == DD_U8 ? setup_quad(p) : setup_octet(p);
+}
+
+int check_plan_args(dd_plan **out, int32_t nchan, int32_t ndm, int32_t in_dtype, int32_t device) {
+  if (!out) return DD_ERR_ARG;
+  *out = nullptr;
+  if (in_dtype != DD_U8 && in_dtype != DD_F16 && in_dtype != DD_F32) return DD_ERR_DTYPE;
+  if (nchan < 1 || ndm < 1 || device < 0) return DD_ERR_ARG;
+  if (ndm > 65535) return DD_ERR_SIZE;  // one grid row per trial in the detection passes
+  if (in_dtype == DD_U8 && static_cast<int64_t>(nchan) * 255 > INT32_MAX) return DD_ERR_RANGE;
+  return DD_OK;
+}
+
+dd_plan *new_plan(int32_t nchan, int32_t ndm, int32_t in_dtype, int32_t device) {
+  dd_plan *p = new (std::nothrow) dd_plan();
+  if (!p) return nullptr;
+  p->device = device;
+  p->nchan = nchan;
+  p->ndm = ndm;
+  p->dtype = in_dtype;
+  try {
+    p->h_delays.resize(static_cast<size_t>(nchan) * ndm);
+    p->h_mean.resize(ndm);
+    p->h_sigma.resize(ndm);
+  } catch (...) {
+    delete p;
+    return nullptr;
   }
-  st = in_dtype == DD_U8 ? setup_quad(p) : setup_octet(p);
+  return p;
+}
+
+}  // namespace
+
+extern "C" int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz,
+                              double chan_width_mhz, double t_samp_s, const double *dm_list,
+                              int32_t ndm, int32_t in_dtype, int32_t device) {
+  int st = check_plan_args(out, nchan, ndm, in_dtype, device);
+  if (st != DD_OK) return st;
+  if (!dm_list) return DD_ERR_ARG;
+  dd_plan *p = new_plan(nchan, ndm, in_dtype, device);
+  if (!p) return DD_ERR_OOM;
+  p->f_top = f_top_mhz;
+  p->df = chan_width_mhz;
+  p->t_samp = t_samp_s;
+  try {
+    p->dms.assign(dm_list, dm_list + ndm);
+  } catch (...) {
+    delete p;
+    return DD_ERR_OOM;
+  }
+  st = dd_compute_delays(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dm_list, ndm,
+                         p->h_delays.data(), &p->maxshift);
+  if (st != DD_OK) {
+    delete p;
+    return st;
+  }
+  st = finish_plan(p);
+  if (st != DD_OK) {
+    destroy_plan(p);
+    return st;
+  }
+  *out = p;
+  return DD_OK;
+}
+
+extern "C" int dd_plan_create_from_delays(dd_plan **out, int32_t nchan, int32_t ndm,
+                                          const int32_t *delays, int32_t in_dtype,
+                                          int32_t device) {
+  int st = check_plan_args(out, nchan, ndm, in_dtype, device);
+  if (st != DD_OK) return st;
+  if (!delays) return DD_ERR_ARG;
+  const size_t n = static_cast<size_t>(nchan) * ndm;
+  int32_t mx = 0;
+  for (size_t i = 0; i < n; ++i) {
+    if (delays[i] < 0 || delays[i] > (1 << 30)) return DD_ERR_ARG;
+    mx = std::max(mx, delays[i]);
+  }
+  dd_plan *p = new_plan(nchan, ndm, in_dtype, device);
+  if (!p) return DD_ERR_OOM;
+  std::copy(delays, delays + n, p->h_delays.begin());
+  p->maxshift = mx;
+  st = finish_plan(p);
   if (st != DD_OK) {
     destroy_plan(p);
     return st;
@@ -327,22 +373,33 @@ extern "C" int dd_plan_launch_count(const dd_plan *p, int64_t *launches) {
 
 extern "C" int dd_execute(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
                           void *out, void *stream) {
+  if (!p) return DD_ERR_ARG;
+  int64_t nsamp_out = 0;
+  const int st = validate_execute(p, nsamp_in, pitch_elems, &nsamp_out);
+  if (st != DD_OK) return st;
+  return dd_execute_pitched(p, block, nsamp_in, pitch_elems, out, nsamp_out, stream);
+}
+
+extern "C" int dd_execute_pitched(dd_plan *p, const void *block, int64_t nsamp_in,
+                                  int64_t pitch_elems, void *out, int64_t out_pitch,
+                                  void *stream) {
   if (!p || !block || !out) return DD_ERR_ARG;
   int64_t nsamp_out = 0;
   int st = validate_execute(p, nsamp_in, pitch_elems, &nsamp_out);
   if (st != DD_OK) return st;
+  if (out_pitch < nsamp_out) return DD_ERR_ARG;
   DeviceScope scope(p->device);
   if (!scope.ok()) return DD_ERR_CUDA;
   cudaError_t err = cudaSuccess;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   int n;
   if (p->path == 0 && ddk::quad_supported(p, block, pitch_elems, nsamp_out))
-    n = ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, nullptr, nullptr, s,
-                                    &err);
+    n = ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, out_pitch, nullptr,
+                                    nullptr, s, &err);
   else if (p->path == 0 && ddk::octet_supported(p, block, pitch_elems, nsamp_out))
-    n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, s, &err);
+    n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, out_pitch, s, &err);
   else
-    n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, s, &err);
+    n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, out_pitch, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
   return DD_OK;
@@ -404,8 +461,8 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   p->stats_valid = false;
   cudaError_t err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
   if (err != cudaSuccess) return cuda_status(err);
-  int n = ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, p->d_rowsums,
-                                      p->d_tilemax, s, &err);
+  int n = ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, nsamp_out,
+                                      p->d_rowsums, p->d_tilemax, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
   if (ev && cudaEventRecord(ev, s) != cudaSuccess) return DD_ERR_CUDA;
@@ -480,7 +537,7 @@ int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
       for (size_t k = lo; k < hi; ++k) {
         dd_plan *p = plans[idx[k]];
         beams.push_back(ddk::quad_beam(p, block[idx[k]], pitch_elems[idx[k]], nout[idx[k]],
-                                       out[idx[k]], p->d_rowsums, p->d_tilemax));
+                                       out[idx[k]], nout[idx[k]], p->d_rowsums, p->d_tilemax));
         smem = std::max(smem, static_cast<int>(p->quad->tables.smem_bytes));
       }
       dd_plan *p0 = plans[idx[lo]];
@@ -855,9 +912,10 @@ extern "C" int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_c
     for (int r = 0; r < 4 && st == DD_OK; ++r) {  // one warm-up, three timed
       cudaError_t le = cudaSuccess;
       e = cudaEventRecord(e0, s);
-      const int n = u8 ? ddk::launch_dedisperse_quad(p, blk, pitch, nsamp_out, out, nullptr,
-                                                     nullptr, s, &le)
-                       : ddk::launch_dedisperse_octet(p, blk, pitch, nsamp_out, out, s, &le);
+      const int n = u8 ? ddk::launch_dedisperse_quad(p, blk, pitch, nsamp_out, out, nsamp_out,
+                                                     nullptr, nullptr, s, &le)
+                       : ddk::launch_dedisperse_octet(p, blk, pitch, nsamp_out, out, nsamp_out,
+                                                      s, &le);
       if (n < 0) e = le;
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);

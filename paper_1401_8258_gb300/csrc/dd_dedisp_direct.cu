@@ -45,7 +45,7 @@ template <typename T>
 __global__ void __launch_bounds__(kDirectThreads)
 dd_dedisperse_direct(const T *__restrict__ in, int64_t pitch, const int32_t *__restrict__ delays,
                      int32_t nchan, int32_t ndm, int64_t nsamp_out,
-                     typename DirectTraits<T>::acc_t *__restrict__ out) {
+                     typename DirectTraits<T>::acc_t *__restrict__ out, int64_t out_pitch) {
   using acc_t = typename DirectTraits<T>::acc_t;
   __shared__ int32_t s_delay[kDelayChans][kDirectDms];
   const int64_t t = static_cast<int64_t>(blockIdx.x) * kDirectThreads + threadIdx.x;
@@ -77,7 +77,7 @@ dd_dedisperse_direct(const T *__restrict__ in, int64_t pitch, const int32_t *__r
   if (live) {
 #pragma unroll
     for (int j = 0; j < kDirectDms; ++j)
-      if (d0 + j < ndm) out[static_cast<int64_t>(d0 + j) * nsamp_out + t] = acc[j];
+      if (d0 + j < ndm) out[static_cast<int64_t>(d0 + j) * out_pitch + t] = acc[j];
   }
 }
 
@@ -86,24 +86,24 @@ dd_dedisperse_direct(const T *__restrict__ in, int64_t pitch, const int32_t *__r
 namespace ddk {
 
 int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                             void *out, cudaStream_t stream, cudaError_t *err) {
+                             void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err) {
   const dim3 grid(static_cast<unsigned>((nsamp_out + kDirectThreads - 1) / kDirectThreads),
                   static_cast<unsigned>((p->ndm + kDirectDms - 1) / kDirectDms));
   switch (p->dtype) {
     case DD_U8:
       dd_dedisperse_direct<uint8_t><<<grid, kDirectThreads, 0, stream>>>(
           static_cast<const uint8_t *>(block), pitch, p->d_delays, p->nchan, p->ndm, nsamp_out,
-          static_cast<int32_t *>(out));
+          static_cast<int32_t *>(out), out_pitch);
       break;
     case DD_F16:
       dd_dedisperse_direct<uint16_t><<<grid, kDirectThreads, 0, stream>>>(
           static_cast<const uint16_t *>(block), pitch, p->d_delays, p->nchan, p->ndm, nsamp_out,
-          static_cast<float *>(out));
+          static_cast<float *>(out), out_pitch);
       break;
     default:
       dd_dedisperse_direct<float><<<grid, kDirectThreads, 0, stream>>>(
           static_cast<const float *>(block), pitch, p->d_delays, p->nchan, p->ndm, nsamp_out,
-          static_cast<float *>(out));
+          static_cast<float *>(out), out_pitch);
       break;
   }
   *err = cudaGetLastError();

@@ -45,6 +45,7 @@ struct OctetArgs {
   int32_t ndm;
   int64_t nsamp_out;
   float *out;
+  int64_t out_pitch;  // elements between output rows (>= nsamp_out)
   const int32_t *recs;
   const int32_t *raw_meta;
   int32_t nchunks;
@@ -355,7 +356,7 @@ __global__ void __launch_bounds__(kThreads, 1) dd_dedisperse_octet(OctetArgs a) 
   for (int i = 0; i < ND_THR; ++i) {
     const int d = tile * ND_CTA + warp * ND_THR + i;
     if (d >= a.ndm) continue;
-    float *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
+    float *orow = a.out + static_cast<int64_t>(d) * a.out_pitch;
 #pragma unroll
     for (int j = 0; j < kTimesPerThread; ++j) {
       const int64_t t = t_cta + lane + 32 * j;
@@ -389,7 +390,7 @@ bool octet_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t
 }
 
 int launch_dedisperse_octet(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                            void *out, cudaStream_t stream, cudaError_t *err) {
+                            void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err) {
   const OctetDevice &q = *p->octet;
   OctetArgs a;
   a.block = static_cast<const uint8_t *>(block);
@@ -397,6 +398,7 @@ int launch_dedisperse_octet(dd_plan *p, const void *block, int64_t pitch, int64_
   a.ndm = p->ndm;
   a.nsamp_out = nsamp_out;
   a.out = static_cast<float *>(out);
+  a.out_pitch = out_pitch;
   a.recs = q.d_recs;
   a.raw_meta = q.d_raw_meta;
   a.nchunks = q.tables.nchunks;

@@ -508,7 +508,7 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
             const int i = m / kPairsPerThread, j = m % kPairsPerThread;
             const int d = tile * ND_CTA + dg * ND_THR + i;
             if (d >= a.ndm) continue;
-            int32_t *orow = a.out + static_cast<int64_t>(d) * a.nsamp_out;
+            int32_t *orow = a.out + static_cast<int64_t>(d) * a.out_pitch;
             const uint32_t w = acc[i][j];
             const int64_t t = t_cta + my_pair + 32 * j;
             const int32_t lo = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
@@ -620,7 +620,7 @@ int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int smem, int d
 }
 
 Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out, void *out,
-               int64_t *rowsums, int32_t *tilemax) {
+               int64_t out_pitch, int64_t *rowsums, int32_t *tilemax) {
   const QuadDevice &q = *p->quad;
   Beam b;
   std::memset(&b, 0, sizeof(b));
@@ -632,6 +632,7 @@ Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp
   b.tilemax = tilemax;
   b.pitch = pitch;
   b.nsamp_out = nsamp_out;
+  b.out_pitch = out_pitch;
   b.ndm = p->ndm;
   b.nchunks = q.tables.nchunks;
   b.nchan_pad = q.tables.nchan_pad;
@@ -644,9 +645,9 @@ Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp
 }
 
 int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                           void *out, int64_t *rowsums, int32_t *tilemax, cudaStream_t stream,
-                           cudaError_t *err) {
-  const Beam b = quad_beam(p, block, pitch, nsamp_out, out, rowsums, tilemax);
+                           void *out, int64_t out_pitch, int64_t *rowsums, int32_t *tilemax,
+                           cudaStream_t stream, cudaError_t *err) {
+  const Beam b = quad_beam(p, block, pitch, nsamp_out, out, out_pitch, rowsums, tilemax);
   return launch_quad_beams(&b, 1, p->quad->tables.nd_thr, p->quad->tables.smem_bytes, p->sm_count,
                            p->d_next_item, p->d_error, p->wait_timeout_ns,
                            p->debug_skip_copies, stream, err);

@@ -98,7 +98,7 @@ inline int elem_size(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F
 // Each launcher returns the number of kernels queued, or -1 with the CUDA
 // error in *err.
 int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                             void *out, cudaStream_t stream, cudaError_t *err);
+                             void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err);
 // Staged quad kernel (u8): needs the plan's quad tables, a 16-byte aligned
 // block, a pitch that is a multiple of 16 bytes and at most 65535 time tiles.
 bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
@@ -107,14 +107,14 @@ bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t 
 // first) and writes the largest output of every (row, kTileSamples-sample
 // time tile) to tilemax[d * ntiles + tile].
 int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                           void *out, int64_t *rowsums, int32_t *tilemax, cudaStream_t stream,
-                           cudaError_t *err);
+                           void *out, int64_t out_pitch, int64_t *rowsums, int32_t *tilemax,
+                           cudaStream_t stream, cudaError_t *err);
 // The staged kernel is persistent: one launch drains a queue of (beam, DM
 // tile, time tile) items over up to ddq::kMaxBeams beams, which must share
 // nd_thr (kNdThr, kNdThr/2 or kNdThr/4); smem is the largest of the beams'
 // shared-memory sizes.
 ddq::Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                    void *out, int64_t *rowsums, int32_t *tilemax);
+                    void *out, int64_t out_pitch, int64_t *rowsums, int32_t *tilemax);
 int launch_quad_beams(const ddq::Beam *beams, int nbeams, int nd_thr, int smem, int device_sms,
                       unsigned long long *next_item, int32_t *status, uint64_t timeout_ns,
                       int32_t skip_copies, cudaStream_t stream, cudaError_t *err);
@@ -124,7 +124,7 @@ constexpr int kTileSamples = ddq::kTimeTile;
 // 65535 time tiles.
 bool octet_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
 int launch_dedisperse_octet(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                            void *out, cudaStream_t stream, cudaError_t *err);
+                            void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err);
 inline int64_t time_tiles(int64_t nsamp_out) { return (nsamp_out + kTileSamples - 1) / kTileSamples; }
 
 // Detection passes over out[ndm][nsamp_out]; see dd_detect in dd.h.

@@ -165,6 +165,7 @@ struct Beam {
   int32_t *tilemax;  // [ndm][ntiles_t] largest output of each time tile
   int64_t pitch;     // bytes per channel row (multiple of 16)
   int64_t nsamp_out;
+  int64_t out_pitch;  // elements between output rows (>= nsamp_out)
   int64_t item_begin;
   int32_t ndm, nchunks, nchan_pad, rec_words, raw_stride, prow_words, ntiles_dm, ntiles_t;
 };
