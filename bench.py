@@ -271,6 +271,30 @@ def run_reference(args):
     if args.workload == POST:
         run_reference_post(args)
         return
+    if args.workload == SUBBAND:
+        wl = synth.workload("full_block_u8")
+        delays, _, _ = geometry_oracle(wl)
+        block, _ = synth.make_block(wl, args.seed, delays)
+        per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+        vals, secs, sample = [], 0.0, ""
+        for _ in range(args.steps):
+            r = time_oracle_subband(wl, block, delays, per_step)
+            vals.append(r["value"])
+            secs += r["seconds"]
+            sample = r["sample"]
+        value = statistics.median(vals)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": SUBBAND, "chans_per_subband": SUB_CHANS,
+                       "dms_per_group": SUB_DMS, "parallelism": "replicas1"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"],
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}), flush=True)
+        return
     if args.workload in (BATCH, SERVE):
         # the oracle on the first beam (its rate stands for the set)
         gen = synth.batch_workloads if args.workload == BATCH else synth.serving_workloads
@@ -895,6 +919,131 @@ def run_post(args):
     plan.close()
 
 
+# ------------------------------------------------------------ subband
+
+SUBBAND = "subband_full_block_u8"  # full_block_u8 by subband dedispersion
+SUB_CHANS, SUB_DMS = 32, 64        # channels per subband, trials per DM group
+
+
+def time_oracle_subband(wl, block, delays, seconds):
+    """The subband oracle on whole DM groups of the block (a bounded sample)."""
+    from oracle import approx
+
+    ngroups_all = (wl.ndm + SUB_DMS - 1) // SUB_DMS
+    t0 = time.perf_counter()
+    approx.subband_dedisperse(block, np.ascontiguousarray(delays[:, :SUB_DMS]), SUB_CHANS,
+                              SUB_DMS)
+    one = time.perf_counter() - t0
+    groups = int(max(1, min(ngroups_all, seconds / max(one, 1e-6))))
+    sub = np.ascontiguousarray(delays[:, :groups * SUB_DMS])
+    t0 = time.perf_counter()
+    out = approx.subband_dedisperse(block, sub, SUB_CHANS, SUB_DMS)
+    dt = time.perf_counter() - t0
+    import oracle
+    return {"value": out.size / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "seconds": dt,
+            "sample": f"{groups} of {ngroups_all} DM groups ({out.shape[0]} trials) x "
+                      f"{out.shape[1]} samples, {wl.nchan} channels in subbands of {SUB_CHANS}"}
+
+
+def run_subband(args):
+    """One step = dd_subband_execute over full_block_u8 (resident in HBM);
+    the brute-force kernel on the same block is timed beside it."""
+    import torch
+
+    import paper_1401_8258_gb300 as dd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dd.build()
+    wl = load_workload(argparse.Namespace(workload="full_block_u8", nsamp=args.nsamp))
+    sub = dd.Subband(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8",
+                     SUB_CHANS, SUB_DMS, local)
+    plan = dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8", local)
+    delays = plan.delays()
+    block, _ = synth.make_block(wl, args.seed + 1000 * (rank + 1), delays)
+    dblock = torch.from_numpy(block).to(dev)
+    n_out = sub.nsamp_out(wl.nsamp)
+    out = torch.empty((wl.ndm, n_out), dtype=torch.int32, device=dev)
+    n_bf = plan.nsamp_out(wl.nsamp)
+    out_bf = torch.empty((wl.ndm, n_bf), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    run_sub = lambda: sub.execute(dblock, out=out, stream=stream)  # noqa: E731
+    run_bf = lambda: dd.dd_execute(plan.handle, dblock, wl.nsamp, wl.nsamp, out_bf,  # noqa: E731
+                                   stream)
+    timed(run_sub, args.warmup)
+    timed(run_bf, args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = sub.launch_count()
+    sub_ms = timed(run_sub, args.steps)
+    launches = sub.launch_count() - l0
+    clock = clocks.stop()
+    bf_ms = timed(run_bf, max(3, args.steps // 2))
+    t_step = statistics.mean(sub_ms) / 1e3
+    units = wl.ndm * n_out
+    nnom = len(sub.nominal)
+    nsub = (wl.nchan + SUB_CHANS - 1) // SUB_CHANS
+    # step-1 series run nsamp_in - D1 samples, D1 = the largest delay inside a
+    # subband at a nominal trial (from the plan's delay table)
+    tn = delays[:, sub.nominal].astype(np.int64)
+    d1 = max(int((tn[c0:c0 + SUB_CHANS] - tn[c0]).max()) for c0 in range(0, wl.nchan, SUB_CHANS))
+    adds = float(wl.nchan) * nnom * (wl.nsamp - d1) + float(nsub) * wl.ndm * n_out
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * LANES_PER_SM * smax * 1e6 / 1e12
+    achieved = adds / t_step / 1e12
+    dm_step = float(wl.dms[1] - wl.dms[0])
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "whole subband step (step-1 plans, conversions, step-2 plans)",
+            "kernel_ms": 1e3 * t_step,
+            "peak_basis": f"{props.multi_processor_count} SMs x {LANES_PER_SM} add lanes x "
+                          f"{smax:.0f} MHz (max clock)",
+            "algorithmic_adds_per_step": adds,
+            "brute_force_adds_per_step": float(wl.nchan) * wl.ndm * n_bf}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = time_oracle_subband(wl, block, delays, args.cpu_seconds)
+        cpu["cpu_model"] = cpu_model()
+    line = {
+        "metric": METRIC, "value": units / t_step, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": SUBBAND, "nchan": wl.nchan, "nsamp_in": wl.nsamp,
+                   "nsamp_out": n_out, "ndm": wl.ndm, "chans_per_subband": SUB_CHANS,
+                   "dms_per_group": SUB_DMS, "nominal_trials": nnom,
+                   "max_dm_error": dm_step * (SUB_DMS // 2), "input_dtype": "u8",
+                   "parallelism": "replicas1",
+                   "l2": "L2 flushed (256 MiB write) before every timed step"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None, "clocks": clock,
+        "gpu_launches": int(launches / max(args.steps, 1)) * args.steps,
+        "brute_force": {"ms": statistics.mean(bf_ms),
+                        "value": wl.ndm * n_bf / (statistics.mean(bf_ms) / 1e3)},
+        "speedup_vs_brute_force": statistics.mean(bf_ms) / (1e3 * t_step),
+    }
+    print(json.dumps(line), flush=True)
+    sub.close()
+    plan.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -905,6 +1054,8 @@ def main():
         run_serve(args)
     elif args.workload == POST:
         run_post(args)
+    elif args.workload == SUBBAND:
+        run_subband(args)
     else:
         run_ours(args)
 

@@ -1,13 +1,15 @@
-// dd_subband.cu -- subband dedispersion (Sec. 2.1.3) as two brute-force
-// passes over derived delay tables, each run by the library's dedispersion
-// kernels through plans built with dd_plan_create_from_delays:
-//   step 1: one plan per subband (its channels x the nominal trials), rows
-//           written interleaved as SB[n][s][t] (dd_execute_pitched);
-//   step 2: one plan per DM group (the subbands as channels x the group's
-//           trials), reading SB[n] as a float block.
-// For u8 input the step-1 sums (int32) are converted to float in place
-// before step 2 and the float result back to int32 after it; both
-// conversions are exact (|values| < 2^24).
+// dd_subband.cu -- subband dedispersion (Sec. 2.1.3): two brute-force
+// passes over delay tables derived from the brute-force table, each one
+// launch of a grouped kernel:
+//   step 1: groups = subbands, channels = the subband's channels, trials =
+//           the nominal trials; rows written interleaved as SB[n][s][t];
+//   step 2: groups = DM groups, channels = the subbands (SB[n(g)] as a
+//           float block), trials = the group's trials.
+// The grouped kernel stages, per CTA (group, 16 trials, time tile), each
+// channel's input window in shared memory and adds from there.  u8 input:
+// step 1 adds in int32 and stores float (exact below 2^24), step 2 adds the
+// integer-valued floats exactly and stores int32.
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,12 +29,172 @@ struct dd_subband {
   std::vector<dd_plan *> step2;  // per group
   std::vector<int32_t> shift1, shift2;
   int32_t D1 = 0, D2 = 0;
+  // stacked tables for the grouped kernel: step 1 [nsub][cps][nnom] (rows
+  // past a narrow last subband unused), step 2 [ngroups][nsub][dpg] (trials
+  // past a short last group repeat its last trial)
+  int32_t *d_tab1 = nullptr, *d_tab2 = nullptr;
+  int32_t span1 = 0, span2 = 0;  // largest delay spread over kGroupTrials trials of a channel
   void *d_sb = nullptr;  // step-1 series [ngroups][nsub][L1pad], 4-byte elements
   size_t sb_bytes = 0;
   int64_t launches = 0;
 };
 
 namespace {
+
+constexpr int kGroupThreads = 256;
+constexpr int kGroupTrials = 16;   // trials per CTA (one accumulator each per thread)
+constexpr int kGroupTile = 512;    // output samples per CTA (two per thread)
+
+template <typename T> struct GroupIn;
+template <> struct GroupIn<uint8_t> {
+  using acc = int32_t;
+  static __device__ __forceinline__ int32_t add(int32_t a, uint8_t x) { return a + x; }
+};
+template <> struct GroupIn<__half> {
+  using acc = float;
+  static __device__ __forceinline__ float add(float a, __half x) { return a + __half2float(x); }
+};
+template <> struct GroupIn<float> {
+  using acc = float;
+  static __device__ __forceinline__ float add(float a, float x) { return a + x; }
+};
+
+template <typename A, typename O> __device__ __forceinline__ O store_as(A v);
+template <> __device__ __forceinline__ float store_as<int32_t, float>(int32_t v) {
+  return static_cast<float>(v);  // exact below 2^24
+}
+template <> __device__ __forceinline__ float store_as<float, float>(float v) { return v; }
+template <> __device__ __forceinline__ int32_t store_as<float, int32_t>(float v) {
+  return __float2int_rn(v);  // integer-valued sums below 2^24
+}
+
+// Grouped brute-force sum: for group g, trial j < ntr and t < nsamp_out,
+//   out[g * og + j * oj + t] = sum_{c < nch(g)} in[g * ig + c * pitch + t + tab[g][c][j]]
+// tab: [ngroups][tab_ch][ntr]; nch(g) = min(tab_ch, nch_total - g * tab_ch)
+// (the last group of channels may be narrower); trials j >= ntr_g(g) are not
+// stored.  Input samples at or past n_valid in a row are never read (they
+// could only reach outputs t >= nsamp_out, which are not stored).  Grid:
+// (time tiles, ceil(ntr / 16), ngroups).  Dynamic shared memory:
+// min(tab_ch, 64) rows of kGroupTile + span elements.
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kGroupThreads)
+dd_grouped(const TI *__restrict__ in, int64_t pitch, int64_t ig, const int32_t *__restrict__ tab,
+           int tab_ch, int nch_total, int ntr, int ntr_last, int span, int64_t n_valid,
+           TO *__restrict__ out, int64_t og, int64_t oj, int64_t nsamp_out) {
+  using A = typename GroupIn<TI>::acc;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TI *win = reinterpret_cast<TI *>(smem_raw);
+  __shared__ int32_t s_del[64][kGroupTrials];  // delay relative to the window start
+  __shared__ int32_t s_lo[64];
+  const int g = blockIdx.z;
+  const int j0 = blockIdx.y * kGroupTrials;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * kGroupTile;
+  const int nch = min(tab_ch, nch_total - g * tab_ch);
+  const int ntr_g = g == gridDim.z - 1 ? ntr_last : ntr;
+  const int W = kGroupTile + span;
+  const TI *x = in + g * ig;
+  const int32_t *tg = tab + static_cast<int64_t>(g) * tab_ch * ntr;
+  A acc0[kGroupTrials], acc1[kGroupTrials];
+#pragma unroll
+  for (int j = 0; j < kGroupTrials; ++j) acc0[j] = acc1[j] = A(0);
+  for (int c0 = 0; c0 < nch; c0 += 64) {
+    const int nc = min(64, nch - c0);
+    __syncthreads();
+    if (threadIdx.x < nc) {  // window start of each channel = its smallest delay here
+      const int c = c0 + threadIdx.x;
+      int lo = INT32_MAX;
+      for (int j = 0; j < kGroupTrials; ++j) {
+        const int jj = min(j0 + j, ntr_g - 1);
+        lo = min(lo, tg[static_cast<int64_t>(c) * ntr + jj]);
+      }
+      s_lo[threadIdx.x] = lo;
+      for (int j = 0; j < kGroupTrials; ++j) {
+        const int jj = min(j0 + j, ntr_g - 1);
+        s_del[threadIdx.x][j] = tg[static_cast<int64_t>(c) * ntr + jj] - lo;
+      }
+    }
+    __syncthreads();
+    // windows: channel c, samples t0 + lo_c .. t0 + lo_c + W - 1; the loads
+    // of several channels are issued before their shared-memory stores
+    constexpr int kUnroll = 4;
+    for (int cb = 0; cb < nc; cb += kUnroll) {
+      for (int k = threadIdx.x; k < W; k += kGroupThreads) {
+        TI v[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const int c = cb + u;
+          const int64_t tt = t0 + (c < nc ? s_lo[c] : 0) + k;
+          v[u] = (c < nc && tt < n_valid) ? x[static_cast<int64_t>(c0 + c) * pitch + tt] : TI(0);
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+          if (cb + u < nc) win[(cb + u) * W + k] = v[u];
+      }
+    }
+    __syncthreads();
+    for (int c = 0; c < nc; ++c) {
+      const TI *w = win + c * W + threadIdx.x;
+#pragma unroll
+      for (int j = 0; j < kGroupTrials; ++j) {
+        const int dl = s_del[c][j];
+        acc0[j] = GroupIn<TI>::add(acc0[j], w[dl]);
+        acc1[j] = GroupIn<TI>::add(acc1[j], w[dl + kGroupThreads]);
+      }
+    }
+  }
+  const int64_t ta = t0 + threadIdx.x, tb = ta + kGroupThreads;
+#pragma unroll
+  for (int j = 0; j < kGroupTrials; ++j) {
+    if (j0 + j >= ntr_g) break;
+    TO *o = out + g * og + static_cast<int64_t>(j0 + j) * oj;
+    if (ta < nsamp_out) o[ta] = store_as<A, TO>(acc0[j]);
+    if (tb < nsamp_out) o[tb] = store_as<A, TO>(acc1[j]);
+  }
+}
+
+constexpr size_t kGroupSmemMax = 200 * 1024;
+
+inline size_t grouped_smem(int tab_ch, int span, size_t esize) {
+  return static_cast<size_t>(std::min(tab_ch, 64)) * (kGroupTile + span) * esize;
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_grouped(const TI *in, int64_t pitch, int64_t ig, const int32_t *tab, int tab_ch,
+                           int nch_total, int ngroups, int ntr, int ntr_last, int span,
+                           int64_t n_valid, TO *out, int64_t og, int64_t oj, int64_t nsamp_out,
+                           cudaStream_t s) {
+  const size_t smem = grouped_smem(tab_ch, span, sizeof(TI));
+  cudaError_t e = cudaFuncSetAttribute(dd_grouped<TI, TO>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const dim3 grid(static_cast<unsigned>((nsamp_out + kGroupTile - 1) / kGroupTile),
+                  static_cast<unsigned>((ntr + kGroupTrials - 1) / kGroupTrials),
+                  static_cast<unsigned>(ngroups));
+  dd_grouped<TI, TO><<<grid, kGroupThreads, smem, s>>>(in, pitch, ig, tab, tab_ch, nch_total, ntr,
+                                                       ntr_last, span, n_valid, out, og, oj,
+                                                       nsamp_out);
+  return cudaGetLastError();
+}
+
+// Largest spread (max - min) of a channel's delays over any kGroupTrials
+// consecutive trials of a group (the chunks the kernel stages together).
+int32_t chunk_span(const std::vector<int32_t> &tab, int ngroups, int tab_ch, int ntr,
+                   const std::vector<int32_t> &ntr_of) {
+  int32_t span = 0;
+  for (int g = 0; g < ngroups; ++g)
+    for (int c = 0; c < tab_ch; ++c)
+      for (int j0 = 0; j0 < ntr_of[g]; j0 += kGroupTrials) {
+        int32_t lo = INT32_MAX, hi = INT32_MIN;
+        for (int j = j0; j < std::min(ntr_of[g], j0 + kGroupTrials); ++j) {
+          const int32_t v = tab[(static_cast<size_t>(g) * tab_ch + c) * ntr + j];
+          lo = std::min(lo, v);
+          hi = std::max(hi, v);
+        }
+        span = std::max(span, hi - lo);
+      }
+  return span;
+}
 
 constexpr int kConvThreads = 256;
 
@@ -64,11 +226,13 @@ int elem_bytes(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F16 ? 2
 void destroy(dd_subband *s) {
   for (dd_plan *p : s->step1) dd_plan_destroy(p);
   for (dd_plan *p : s->step2) dd_plan_destroy(p);
-  if (s->d_sb) {
+  if (s->d_sb || s->d_tab1 || s->d_tab2) {
     int prev = 0;
     cudaGetDevice(&prev);
     cudaSetDevice(s->device);
     cudaFree(s->d_sb);
+    cudaFree(s->d_tab1);
+    cudaFree(s->d_tab2);
     cudaSetDevice(prev);
   }
   delete s;
@@ -151,6 +315,46 @@ extern "C" int dd_subband_create(dd_subband **out, int32_t nchan, double f_top_m
   } catch (...) {
     st = DD_ERR_OOM;
   }
+  // stacked tables and spans for the grouped kernel (one launch per step)
+  if (st == DD_OK) {
+    try {
+      const int32_t nnom = s->ngroups;
+      std::vector<int32_t> t1(static_cast<size_t>(s->nsub) * chans_per_subband * nnom, 0);
+      for (int32_t k = 0; k < s->nsub; ++k) {
+        const int32_t c0 = s->first[k], nc = std::min(chans_per_subband, nchan - c0);
+        for (int32_t c = 0; c < nc; ++c)
+          for (int32_t n = 0; n < nnom; ++n)
+            t1[(static_cast<size_t>(k) * chans_per_subband + c) * nnom + n] =
+                at(c0 + c, s->nominal[n]) - at(c0, s->nominal[n]);
+      }
+      std::vector<int32_t> t2(static_cast<size_t>(s->ngroups) * s->nsub * dms_per_group, 0);
+      std::vector<int32_t> ntr2(s->ngroups);
+      for (int32_t g = 0; g < s->ngroups; ++g) {
+        const int32_t g0 = g * dms_per_group, gn = std::min(dms_per_group, ndm - g0);
+        ntr2[g] = gn;
+        for (int32_t k = 0; k < s->nsub; ++k)
+          for (int32_t d = 0; d < dms_per_group; ++d)  // past a short group: its last trial
+            t2[(static_cast<size_t>(g) * s->nsub + k) * dms_per_group + d] =
+                at(s->first[k], g0 + std::min(d, gn - 1));
+      }
+      std::vector<int32_t> ntr1(s->nsub, nnom);
+      s->span1 = chunk_span(t1, s->nsub, chans_per_subband, nnom, ntr1);
+      s->span2 = chunk_span(t2, s->ngroups, s->nsub, dms_per_group, ntr2);
+      int prev = 0;
+      cudaGetDevice(&prev);
+      cudaSetDevice(device);
+      cudaError_t e = cudaMalloc(&s->d_tab1, t1.size() * sizeof(int32_t));
+      if (e == cudaSuccess) e = cudaMalloc(&s->d_tab2, t2.size() * sizeof(int32_t));
+      if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_tab1, t1.data(), t1.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy(s->d_tab2, t2.data(), t2.size() * sizeof(int32_t), cudaMemcpyHostToDevice);
+      cudaSetDevice(prev);
+      if (e != cudaSuccess) st = DD_ERR_OOM;
+    } catch (...) {
+      st = DD_ERR_OOM;
+    }
+  }
   if (st != DD_OK) {
     destroy(s);
     return st;
@@ -223,11 +427,46 @@ extern "C" int dd_subband_execute(dd_subband *s, const void *block, int64_t nsam
   const unsigned char *blk = static_cast<const unsigned char *>(block);
   const int eb = elem_bytes(s->dtype);
   int32_t *sb = static_cast<int32_t *>(s->d_sb);
-  // step 1: subband k at the nominal trials, rows (n, k) of SB
+  float *sbf = reinterpret_cast<float *>(sb);
+  const int64_t ldsb = static_cast<int64_t>(s->nsub) * L1pad;  // SB row pitch per nominal
+  const int last = s->ndm - (s->ngroups - 1) * s->dpg;
+  if (grouped_smem(s->cps, s->span1, eb) <= kGroupSmemMax &&
+      grouped_smem(s->nsub, s->span2, 4) <= kGroupSmemMax) {
+    cudaError_t e;
+    // step 1: group = subband k, rows (n, k) of SB, float
+    const int64_t ig = static_cast<int64_t>(s->cps) * pitch_elems;
+    if (s->dtype == DD_U8)
+      e = launch_grouped(static_cast<const uint8_t *>(block), pitch_elems, ig, s->d_tab1, s->cps,
+                         s->nchan, s->nsub, s->ngroups, s->ngroups, s->span1, nsamp_in, sbf,
+                         L1pad, ldsb, L1, st);
+    else if (s->dtype == DD_F16)
+      e = launch_grouped(static_cast<const __half *>(block), pitch_elems, ig, s->d_tab1, s->cps,
+                         s->nchan, s->nsub, s->ngroups, s->ngroups, s->span1, nsamp_in, sbf,
+                         L1pad, ldsb, L1, st);
+    else
+      e = launch_grouped(static_cast<const float *>(block), pitch_elems, ig, s->d_tab1, s->cps,
+                         s->nchan, s->nsub, s->ngroups, s->ngroups, s->span1, nsamp_in, sbf,
+                         L1pad, ldsb, L1, st);
+    // step 2: group g reads SB[g] ([nsub][L1pad]), rows g * dpg + j of out
+    if (e == cudaSuccess) {
+      const int64_t og = static_cast<int64_t>(s->dpg) * nsamp_out;
+      if (s->dtype == DD_U8)
+        e = launch_grouped(static_cast<const float *>(sbf), L1pad, ldsb, s->d_tab2, s->nsub,
+                           s->nsub * s->ngroups, s->ngroups, s->dpg, last, s->span2, L1,
+                           static_cast<int32_t *>(out), og, nsamp_out, nsamp_out, st);
+      else
+        e = launch_grouped(static_cast<const float *>(sbf), L1pad, ldsb, s->d_tab2, s->nsub,
+                           s->nsub * s->ngroups, s->ngroups, s->dpg, last, s->span2, L1,
+                           static_cast<float *>(out), og, nsamp_out, nsamp_out, st);
+    }
+    s->launches += 2;
+    return e == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+  }
+  // windows too wide for shared memory: one plan per subband and per group
   for (int32_t k = 0; k < s->nsub; ++k) {
     const void *bk = blk + static_cast<size_t>(s->first[k]) * pitch_elems * eb;
     const int r = dd_execute_pitched(s->step1[k], bk, L1 + s->shift1[k], pitch_elems,
-                                     sb + k * L1pad, static_cast<int64_t>(s->nsub) * L1pad, stream);
+                                     sb + k * L1pad, ldsb, stream);
     if (r != DD_OK) return r;
   }
   if (s->dtype == DD_U8) {
@@ -235,10 +474,8 @@ extern "C" int dd_subband_execute(dd_subband *s, const void *block, int64_t nsam
     to_float_rows<<<conv_grid(rows * L1), kConvThreads, 0, st>>>(sb, rows, L1, L1pad);
     ++s->launches;
   }
-  // step 2: group g from its nominal's SB block, rows g0 .. of out
-  const float *sbf = reinterpret_cast<const float *>(sb);
   for (int32_t g = 0; g < s->ngroups; ++g) {
-    const float *bg = sbf + static_cast<size_t>(g) * s->nsub * L1pad;
+    const float *bg = sbf + static_cast<size_t>(g) * ldsb;
     float *og = static_cast<float *>(out) + static_cast<size_t>(g) * s->dpg * nsamp_out;
     const int r = dd_execute_pitched(s->step2[g], bg, nsamp_out + s->shift2[g], L1pad, og,
                                      nsamp_out, stream);
