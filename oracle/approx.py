@@ -1,7 +1,8 @@
 """CPU oracle for subband dedispersion, the thesis's two-step approximation of
-the brute-force sum (Sec. 2.1.3, subband dedispersion), and the analytic S/N
-loss of a pulse dedispersed at a wrong DM (Sec. 3.6, candidate classification
-after Cordes & McLaughlin).
+the brute-force sum (Sec. 2.1.3, subband dedispersion), for time binning past
+the diagonal DM (Sec. 2.1.1 and the downfactoring procedure of Sec. 2.1.2),
+and the analytic S/N loss of a pulse dedispersed at a wrong DM (Sec. 3.6,
+candidate classification after Cordes & McLaughlin).
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle``.  Both steps are plain
 brute-force sums over delay tables, so each runs through ``oracle.dedisperse``
@@ -99,3 +100,77 @@ def smearing_peak_ratio(ddm: float, bandwidth_mhz: float, f_centre_ghz: float,
     if zeta == 0:
         return 1.0
     return math.sqrt(math.pi) / 2 * math.erf(zeta) / zeta
+
+
+# ---------------------------------------------------------------- time binning
+#
+# Above the diagonal DM a channel's dispersion sweep is wider than a sample, so
+# the thesis dedisperses the higher DM ranges from a time series downfactored
+# by 2 (adjacent samples summed), 4, ...: trials below twice the diagonal DM
+# at full resolution, trials in [2^k, 2^(k+1)) x DM_diag from the series
+# binned by 2^k (capped at max_factor), with delays at 2^k sampling times.
+
+
+def diagonal_dm(nchan: int, f_top_mhz: float, chan_width_mhz: float, t_samp_s: float,
+                k_dm: float = 4.148808e3) -> float:
+    """DM at which the dispersion delay across one channel at the bottom of the
+    band equals one sample: d/dc [K DM (f_c^-2 - f_top^-2)] = t_samp with
+    f_c = f_top - c df, i.e. DM_diag = t_samp f_bot^3 / (2 K df)."""
+    f_bot = f_top_mhz - (nchan - 1) * chan_width_mhz
+    return t_samp_s * f_bot ** 3 / (2.0 * k_dm * chan_width_mhz)
+
+
+def binning_factors(dms: np.ndarray, dm_diag: float, max_factor: int) -> np.ndarray:
+    """Downfactor per trial: 1 below 2 DM_diag, else 2^floor(log2(DM/DM_diag)),
+    at most max_factor (a power of two)."""
+    f = np.ones(len(dms), dtype=np.int32)
+    for i, dm in enumerate(np.asarray(dms, dtype=np.float64)):
+        k = 1
+        while 2 * k <= max_factor and dm >= 2 * k * dm_diag:
+            k *= 2
+        f[i] = k
+    return f
+
+
+def decimate(block: np.ndarray, nsamp_in: int, factor: int) -> np.ndarray:
+    """Sum adjacent samples pairwise, log2(factor) times: b[c][t] = a[c][2t] +
+    a[c][2t+1].  Integers for uint8 input (exact), float32 otherwise (in this
+    order).  Length nsamp_in // factor."""
+    x = block[:, :nsamp_in].astype(np.int64 if block.dtype == np.uint8 else np.float32)
+    while factor > 1:
+        n = x.shape[1] // 2
+        x = x[:, 0:2 * n:2] + x[:, 1:2 * n:2]
+        factor //= 2
+    return x
+
+
+def binned_dedisperse(block: np.ndarray, nchan: int, f_top_mhz: float, chan_width_mhz: float,
+                      t_samp_s: float, dms: np.ndarray, max_factor: int,
+                      nsamp_in: int | None = None):
+    """Time-binned dedispersion.  Returns (rows, factors, lengths): rows[d] is
+    the dedispersed series of trial d at 1/factor[d] of the sampling rate,
+    lengths[d] its length (nsamp_in // f - maxshift of its factor's trials at
+    f t_samp); int32 for uint8 input, float64 otherwise."""
+    from . import delay_table
+
+    dms = np.asarray(dms, dtype=np.float64)
+    if nsamp_in is None:
+        nsamp_in = block.shape[1]
+    fac = binning_factors(dms, diagonal_dm(nchan, f_top_mhz, chan_width_mhz, t_samp_s),
+                          max_factor)
+    rows = [None] * len(dms)
+    for f in sorted(set(fac.tolist())):
+        idx = np.nonzero(fac == f)[0]
+        delays, _ = delay_table(nchan, f_top_mhz, chan_width_mhz, t_samp_s * f, dms[idx])
+        if f == 1:
+            src, n_in = block, nsamp_in
+        else:
+            d = decimate(block, nsamp_in, f)
+            src = d.astype(np.float32)  # exact for the integer sums of uint8 input
+            n_in = d.shape[1]
+        D = dedisperse(np.ascontiguousarray(src), delays, nsamp_in=n_in)
+        if block.dtype == np.uint8 and D.dtype != np.int32:
+            D = np.rint(D).astype(np.int32)
+        for j, i in enumerate(idx):
+            rows[i] = D[j]
+    return rows, fac, np.array([len(r) for r in rows])

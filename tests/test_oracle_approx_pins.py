@@ -128,3 +128,78 @@ def test_subband_loss_follows_analytic_curve_per_subband(offset):
     predicted = np.mean([approx.smearing_peak_ratio(ddm, cps * df, f, width) for f in f_centres])
     assert predicted < 0.97  # a visible loss
     assert measured == pytest.approx(predicted, abs=0.03)
+
+
+# ---------------------------------------------------------------- time binning
+
+def test_diagonal_dm_is_one_sample_per_channel_at_the_band_bottom():
+    for name in ("full_block_u8", "lband_f32", "single_beam_f32"):
+        wl = synth.workload(name)
+        dd = approx.diagonal_dm(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s)
+        for m in (1, 2, 4):
+            delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz,
+                                           wl.t_samp_s, np.array([m * dd]))
+            step = int(delays[-1, 0] - delays[-2, 0])
+            assert abs(step - m) <= 1, (name, m, step)
+
+
+def test_binning_factors_follow_the_doubling_ranges():
+    f = approx.binning_factors(np.array([0, 10, 19.9, 20, 39.9, 40, 79, 80, 1000.0]), 10.0, 8)
+    assert f.tolist() == [1, 1, 1, 2, 2, 4, 4, 8, 8]
+
+
+def test_decimate_sums_adjacent_samples():
+    rng = np.random.default_rng(8)
+    b = rng.integers(0, 256, size=(3, 1000), dtype=np.uint8)
+    for f in (1, 2, 4, 16):
+        d = approx.decimate(b, 1000, f)
+        n = 1000 // f
+        assert np.array_equal(d, b[:, :n * f].astype(np.int64).reshape(3, n, f).sum(axis=2))
+    x = rng.standard_normal((2, 999)).astype(np.float32)
+    d = approx.decimate(x, 999, 4)
+    ref = x[:, :996].astype(np.float64).reshape(2, 249, 4).sum(axis=2)
+    assert d.dtype == np.float32 and np.allclose(d, ref, rtol=0, atol=1e-5)
+
+
+def test_binned_rows_full_rate_exact_and_flux_conserved():
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=128, ndm=160)
+    wl.dms = synth.dm_grid(0.0, 1.0, 160)
+    dd = approx.diagonal_dm(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s,
+                                    wl.dms)
+    nsamp = (2 * mx + 4096) // 64 * 64
+    rng = np.random.default_rng(3)
+    block = np.zeros((wl.nchan, nsamp), dtype=np.uint8)
+    block[:, mx + 64:nsamp - mx - 64] = rng.integers(0, 256, size=(wl.nchan, nsamp - 2 * mx - 128))
+    rows, fac, lens = approx.binned_dedisperse(block, wl.nchan, wl.f_top_mhz, wl.chan_width_mhz,
+                                               wl.t_samp_s, wl.dms, 8)
+    assert set(fac.tolist()) == {1, 2, 4, 8} and dd * 2 <= wl.dms[-1]
+    brute = oracle.dedisperse(block, delays)
+    for d in range(wl.ndm):
+        if fac[d] == 1:  # the full-rate trials' own maxshift: rows may run longer
+            n = min(lens[d], brute.shape[1])
+            assert np.array_equal(rows[d][:n], brute[d, :n])
+        # every sample of the signal is added exactly once at any rate
+        assert int(rows[d].astype(np.int64).sum()) == int(brute[d].astype(np.int64).sum()), d
+        assert lens[d] >= nsamp // fac[d] - (mx // fac[d] + 1)
+
+
+def test_binned_rows_gather_a_dispersed_pulse():
+    """A 16-sample pulse on trial d's track: at any rate the row's peak
+    collects most of it (f samples per bin), which a wrong delay scale (f)
+    or a misaligned bin would spread over many bins."""
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=128, ndm=160)
+    wl.dms = synth.dm_grid(0.0, 1.0, 160)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s,
+                                    wl.dms)
+    nsamp = (2 * mx + 4096) // 64 * 64
+    for d in (10, 70, 120, 159):
+        block = np.zeros((wl.nchan, nsamp), dtype=np.uint8)
+        for c in range(wl.nchan):  # amplitude 3 on the track (uint8 block)
+            block[c, mx + 500 + delays[c, d]:mx + 516 + delays[c, d]] = 3
+        rows, fac, _ = approx.binned_dedisperse(block, wl.nchan, wl.f_top_mhz,
+                                                wl.chan_width_mhz, wl.t_samp_s, wl.dms, 8)
+        total = int(block.astype(np.int64).sum())  # the pulse: 16 samples x nchan x 3
+        assert total == 16 * wl.nchan * 3
+        peak = int(rows[d].max())
+        assert peak >= 0.75 * wl.nchan * 3 * min(fac[d], 16), (d, fac[d], peak)
