@@ -1,0 +1,67 @@
+/*
+ * dd_binned.h -- C ABI of libdd's time-binned dedispersion: past the
+ * diagonal DM the higher DM ranges are dedispersed from the series
+ * downfactored by 2, 4, ... (A. Magro 2013, Sec. 2.1.1 on the diagonal DM
+ * and the downfactoring procedure of Sec. 2.1.2).
+ *
+ * Diagonal DM (the DM whose sweep across one channel at the bottom of the
+ * band is one sample): DM_diag = t_samp f_bot^3 / (2 K df), f_bot = f_top -
+ * (nchan - 1) df, K = 4.148808e3, in double, f_bot^3 as f_bot*f_bot*f_bot.
+ * Trial d gets the downfactor 1 below 2 DM_diag, else the largest power of
+ * two f <= max_factor with DM_d >= f DM_diag.  A trial with downfactor f is
+ * dedispersed from the block binned by f -- adjacent samples summed in pairs,
+ * log2(f) times: b[c][t] = a[c][2t] + a[c][2t+1] -- with the delays of
+ * dd_plan_create at sampling time f t_samp, over the trials that share f:
+ *   out[d][t] = sum_c B_f[c][t + delay_f(c, d)],  t < nsamp_out(d),
+ *   nsamp_out(d) = floor(nsamp_in / f) - (largest delay_f of those trials).
+ * Each output sample of such a row covers f input samples.  u8 input: the
+ * binned series are integer sums carried in float (exact below 2^24, hence
+ * DD_ERR_RANGE when nchan * 255 * max_factor >= 2^24) and every row is int32;
+ * f16/f32 input: float rows (float pair sums, float accumulation).
+ */
+#ifndef DD_BINNED_H
+#define DD_BINNED_H
+
+#include <stdint.h>
+
+#include "dd.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_binned dd_binned; /* opaque; owns one plan per downfactor and the binned series */
+
+/* Geometry and DM list as for dd_plan_create, with the DM list
+ * non-decreasing (so each downfactor covers consecutive trials; DD_ERR_ARG
+ * otherwise); max_factor a power of two in 1..64. */
+int dd_binned_create(dd_binned **out, int32_t nchan, double f_top_mhz, double chan_width_mhz,
+                     double t_samp_s, const double *dm_list, int32_t ndm, int32_t in_dtype,
+                     int32_t max_factor, int32_t device);
+int dd_binned_destroy(dd_binned *b);
+
+int dd_binned_diagonal_dm(const dd_binned *b, double *dm_diag);
+
+/* Per trial, host arrays of ndm entries (either may be NULL): its downfactor
+ * and its output length for a block of nsamp_in samples (DD_ERR_SIZE when
+ * some trial would have no output). */
+int dd_binned_rows(const dd_binned *b, int64_t nsamp_in, int32_t *factor, int64_t *nsamp_out);
+
+/* Dedisperse one block (device, [nchan][pitch_elems] of the dtype, first
+ * nsamp_in samples of each row read) on `stream`: row d of out (device,
+ * [ndm][out_pitch], int32 for u8 input, float otherwise) gets its
+ * nsamp_out(d) samples; the rest of the row is not written.  out_pitch must
+ * cover the longest row (DD_ERR_ARG).  The first call for a given nsamp_in
+ * grows the binned-series workspace (about nchan x nsamp_in x 4 bytes) and
+ * synchronises the device; later calls are asynchronous. */
+int dd_binned_execute(dd_binned *b, const void *block, int64_t nsamp_in, int64_t pitch_elems,
+                      void *out, int64_t out_pitch, void *stream);
+
+/* Kernel launches queued by this object since creation. */
+int dd_binned_launch_count(const dd_binned *b, int64_t *launches);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_BINNED_H */

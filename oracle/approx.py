@@ -117,7 +117,7 @@ def diagonal_dm(nchan: int, f_top_mhz: float, chan_width_mhz: float, t_samp_s: f
     band equals one sample: d/dc [K DM (f_c^-2 - f_top^-2)] = t_samp with
     f_c = f_top - c df, i.e. DM_diag = t_samp f_bot^3 / (2 K df)."""
     f_bot = f_top_mhz - (nchan - 1) * chan_width_mhz
-    return t_samp_s * f_bot ** 3 / (2.0 * k_dm * chan_width_mhz)
+    return t_samp_s * (f_bot * f_bot * f_bot) / (2.0 * k_dm * chan_width_mhz)
 
 
 def binning_factors(dms: np.ndarray, dm_diag: float, max_factor: int) -> np.ndarray:

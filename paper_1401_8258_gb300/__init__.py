@@ -30,6 +30,7 @@ __all__ = [
     "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
     "dd_run", "Batch", "dd_batch_create", "dd_batch_destroy", "dd_batch_run", "Stream",
     "push_streams", "median_filter", "detrend", "boxcar_detect", "PULSE_DTYPE", "Subband",
+    "Binned",
 ]
 
 _TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
@@ -337,6 +338,53 @@ class Subband:
     def close(self):
         if self.handle:
             _native.dd_subband_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Binned:
+    """Owner of a dd_binned handle (time-binned dedispersion past the
+    diagonal DM, include/dd_binned.h) working on torch device tensors."""
+
+    def __init__(self, nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype, max_factor,
+                 device=0):
+        self.ndm, self.dtype = len(dms), dtype
+        self.handle = _native.dd_binned_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms,
+                                               dtype, max_factor, device)
+        self.dm_diag = _native.dd_binned_diagonal_dm(self.handle)
+
+    def rows(self, nsamp_in):
+        """(downfactor, output length) per trial for nsamp_in input samples."""
+        return _native.dd_binned_rows(self.handle, self.ndm, nsamp_in)
+
+    def execute(self, block, nsamp_in=None, out=None, stream=None):
+        import torch
+        nsamp_in = block.shape[1] if nsamp_in is None else nsamp_in
+        _, lens = self.rows(nsamp_in)
+        if out is None:
+            dt = torch.int32 if self.dtype == "u8" else torch.float32
+            out = torch.zeros((self.ndm, int(lens.max())), dtype=dt, device=block.device)
+        _native.dd_binned_execute(self.handle, block, nsamp_in, block.stride(0), out,
+                                  out.stride(0), stream)
+        return out
+
+    def launch_count(self):
+        return _native.dd_binned_launch_count(self.handle)
+
+    def close(self):
+        if self.handle:
+            _native.dd_binned_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -89,6 +89,13 @@ SIGNATURES = [
     ("dd_subband_nominal", ctypes.c_int, [_vp, _vp, _vp]),
     ("dd_subband_execute", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp]),
     ("dd_subband_launch_count", ctypes.c_int, [_vp, _vp]),
+    # dd_binned.h
+    ("dd_binned_create", ctypes.c_int, [_vp, _i32, _f64, _f64, _f64, _vp, _i32, _i32, _i32, _i32]),
+    ("dd_binned_destroy", ctypes.c_int, [_vp]),
+    ("dd_binned_diagonal_dm", ctypes.c_int, [_vp, _vp]),
+    ("dd_binned_rows", ctypes.c_int, [_vp, _i64, _vp, _vp]),
+    ("dd_binned_execute", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp]),
+    ("dd_binned_launch_count", ctypes.c_int, [_vp, _vp]),
     # dd_post.h
     ("dd_median_filter", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _i32, _vp, _i64, _vp]),
     ("dd_detrend", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _vp, _i64, _vp, _vp]),
@@ -448,4 +455,45 @@ def dd_subband_execute(sub, block, nsamp_in, pitch_elems, out, stream=None) -> N
 def dd_subband_launch_count(sub) -> int:
     n = ctypes.c_int64(0)
     _check(load().dd_subband_launch_count(sub, ctypes.addressof(n)), "dd_subband_launch_count")
+    return int(n.value)
+
+
+def dd_binned_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype, max_factor,
+                     device=0) -> int:
+    code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    dms = np.ascontiguousarray(dms, dtype=np.float64)
+    h = ctypes.c_void_p()
+    _check(load().dd_binned_create(ctypes.addressof(h), int(nchan), float(f_top_mhz),
+                                   float(chan_width_mhz), float(t_samp_s), dms.ctypes.data,
+                                   int(dms.size), code, int(max_factor), int(device)),
+           "dd_binned_create")
+    return h.value
+
+
+def dd_binned_destroy(b) -> None:
+    _check(load().dd_binned_destroy(b), "dd_binned_destroy")
+
+
+def dd_binned_diagonal_dm(b) -> float:
+    v = ctypes.c_double(0)
+    _check(load().dd_binned_diagonal_dm(b, ctypes.addressof(v)), "dd_binned_diagonal_dm")
+    return float(v.value)
+
+
+def dd_binned_rows(b, ndm, nsamp_in) -> tuple[np.ndarray, np.ndarray]:
+    fac = np.zeros(ndm, dtype=np.int32)
+    n = np.zeros(ndm, dtype=np.int64)
+    _check(load().dd_binned_rows(b, int(nsamp_in), fac.ctypes.data, n.ctypes.data),
+           "dd_binned_rows")
+    return fac, n
+
+
+def dd_binned_execute(b, block, nsamp_in, pitch_elems, out, out_pitch, stream=None) -> None:
+    _check(load().dd_binned_execute(b, _addr(block), int(nsamp_in), int(pitch_elems), _addr(out),
+                                    int(out_pitch), _stream(stream)), "dd_binned_execute")
+
+
+def dd_binned_launch_count(b) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().dd_binned_launch_count(b, ctypes.addressof(n)), "dd_binned_launch_count")
     return int(n.value)
