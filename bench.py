@@ -271,6 +271,30 @@ def run_reference(args):
     if args.workload == POST:
         run_reference_post(args)
         return
+    if args.workload == BINNED:
+        wl = synth.workload("full_block_u8")
+        delays, _, _ = geometry_oracle(wl)
+        block, _ = synth.make_block(wl, args.seed, delays)
+        per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
+        vals, secs, sample = [], 0.0, ""
+        for _ in range(args.steps):
+            r = time_oracle_binned(wl, block, per_step)
+            vals.append(r["value"])
+            secs += r["seconds"]
+            sample = r["sample"]
+        value = statistics.median(vals)
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": BINNED, "max_factor": BIN_MAX_FACTOR,
+                       "parallelism": "replicas1"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"],
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}), flush=True)
+        return
     if args.workload == SUBBAND:
         wl = synth.workload("full_block_u8")
         delays, _, _ = geometry_oracle(wl)
@@ -1044,6 +1068,127 @@ def run_subband(args):
     plan.close()
 
 
+# --------------------------------------------------------- time binning
+
+BINNED = "binned_full_block_u8"  # full_block_u8 with downfactors past the diagonal DM
+BIN_MAX_FACTOR = 8
+
+
+def time_oracle_binned(wl, block, seconds):
+    """The binning oracle on evenly spaced trials (each at its own rate)."""
+    from oracle import approx
+    import oracle
+
+    n = 8
+    while True:
+        idx = np.linspace(0, wl.ndm - 1, n).astype(np.int64)
+        t0 = time.perf_counter()
+        rows, fac, lens = approx.binned_dedisperse(block, wl.nchan, wl.f_top_mhz,
+                                                   wl.chan_width_mhz, wl.t_samp_s, wl.dms[idx],
+                                                   BIN_MAX_FACTOR)
+        dt = time.perf_counter() - t0
+        if dt * 2 > seconds or n >= wl.ndm:
+            break
+        n = min(wl.ndm, n * 2)
+    covered = float(np.sum(lens * fac))
+    return {"value": covered / dt, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+            "seconds": dt,
+            "sample": f"{n} of {wl.ndm} evenly spaced trials (downfactors "
+                      f"{sorted(set(fac.tolist()))}), full block"}
+
+
+def run_binned(args):
+    """One step = dd_binned_execute over full_block_u8 (resident); the
+    brute-force kernel on the same block is timed beside it.  value counts
+    each trial's output samples times its downfactor (input samples covered)."""
+    import torch
+
+    import paper_1401_8258_gb300 as dd
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dd.build()
+    wl = load_workload(argparse.Namespace(workload="full_block_u8", nsamp=args.nsamp))
+    b = dd.Binned(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8",
+                  BIN_MAX_FACTOR, local)
+    plan = dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8", local)
+    block, _ = synth.make_block(wl, args.seed + 1000 * (rank + 1), plan.delays())
+    dblock = torch.from_numpy(block).to(dev)
+    fac, lens = b.rows(wl.nsamp)
+    out = torch.empty((wl.ndm, int(lens.max())), dtype=torch.int32, device=dev)
+    n_bf = plan.nsamp_out(wl.nsamp)
+    out_bf = torch.empty((wl.ndm, n_bf), dtype=torch.int32, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn, steps):
+        ms = []
+        for _ in range(steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms
+
+    run_b = lambda: b.execute(dblock, out=out, stream=stream)  # noqa: E731
+    run_bf = lambda: dd.dd_execute(plan.handle, dblock, wl.nsamp, wl.nsamp, out_bf,  # noqa: E731
+                                   stream)
+    timed(run_b, args.warmup)
+    timed(run_bf, args.warmup)
+    clocks = ClockSampler(local)
+    clocks.start()
+    l0 = b.launch_count()
+    b_ms = timed(run_b, args.steps)
+    launches = b.launch_count() - l0
+    clock = clocks.stop()
+    bf_ms = timed(run_bf, max(3, args.steps // 2))
+    t_step = statistics.mean(b_ms) / 1e3
+    covered = float(np.sum(lens * fac))
+    adds = float(np.sum(lens)) * wl.nchan
+    peaks = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    smax = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * LANES_PER_SM * smax * 1e6 / 1e12
+    achieved = adds / t_step / 1e12
+    counts = {int(k): int((fac == k).sum()) for k in sorted(set(fac.tolist()))}
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
+            "frac": achieved / peak, "traffic": None,
+            "kernel": "whole binned step (binning passes, one plan per downfactor)",
+            "kernel_ms": 1e3 * t_step,
+            "peak_basis": f"{props.multi_processor_count} SMs x {LANES_PER_SM} add lanes x "
+                          f"{smax:.0f} MHz (max clock)",
+            "algorithmic_adds_per_step": adds,
+            "brute_force_adds_per_step": float(wl.nchan) * wl.ndm * n_bf}
+    cpu = None
+    if not args.no_cpu_baseline:
+        cpu = time_oracle_binned(wl, block, args.cpu_seconds)
+        cpu["cpu_model"] = cpu_model()
+    line = {
+        "metric": METRIC, "value": covered / t_step, "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "int32", "data": "synthetic",
+        "config": {"workload": BINNED, "nchan": wl.nchan, "nsamp_in": wl.nsamp, "ndm": wl.ndm,
+                   "max_factor": BIN_MAX_FACTOR, "diagonal_dm": b.dm_diag,
+                   "trials_per_downfactor": counts, "input_dtype": "u8",
+                   "value_counts": "output samples x downfactor (input samples covered)",
+                   "parallelism": "replicas1",
+                   "l2": "L2 flushed (256 MiB write) before every timed step"},
+        "roofline": roof, "cpu_baseline": cpu, "e2e": None, "clocks": clock,
+        "gpu_launches": int(launches),
+        "brute_force": {"ms": statistics.mean(bf_ms),
+                        "value": wl.ndm * n_bf / (statistics.mean(bf_ms) / 1e3)},
+        "speedup_vs_brute_force": statistics.mean(bf_ms) / (1e3 * t_step),
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    plan.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -1056,6 +1201,8 @@ def main():
         run_post(args)
     elif args.workload == SUBBAND:
         run_subband(args)
+    elif args.workload == BINNED:
+        run_binned(args)
     else:
         run_ours(args)
 
