@@ -187,6 +187,12 @@ int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems,
  * beam's first capacity[i] candidates are still written), else DD_OK. */
 typedef struct dd_batch dd_batch;
 int dd_batch_create(dd_batch **out, dd_plan *const *plans, int32_t nplans);
+/* The batch's launch sequence is captured into a CUDA graph after the first
+ * run of an argument set and replayed (one graph launch on `stream`) while
+ * the arguments, the plans' workspaces and their kernel settings (path,
+ * wait timeout, fault injection) stay the same; anything else runs directly
+ * and re-captures.  dd_batch_graph_replays: runs served by the graph. */
+int dd_batch_graph_replays(const dd_batch *b, int64_t *replays);
 int dd_batch_destroy(dd_batch *b);
 int dd_batch_run(dd_batch *b, const void *const *block, const int64_t *nsamp_in,
                  const int64_t *pitch_elems, void *const *out, float nsigma,

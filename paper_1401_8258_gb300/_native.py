@@ -79,6 +79,7 @@ SIGNATURES = [
     ("dd_batch_create", ctypes.c_int, [_vp, _vp, _i32]),
     ("dd_batch_destroy", ctypes.c_int, [_vp]),
     ("dd_batch_run", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _f32, _vp, _vp, _vp, _vp]),
+    ("dd_batch_graph_replays", ctypes.c_int, [_vp, _vp]),
     ("dd_plan_create_from_delays", ctypes.c_int, [_vp, _i32, _i32, _vp, _i32, _i32]),
     ("dd_execute_pitched", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp]),
     # dd_subband.h
@@ -496,4 +497,10 @@ def dd_binned_execute(b, block, nsamp_in, pitch_elems, out, out_pitch, stream=No
 def dd_binned_launch_count(b) -> int:
     n = ctypes.c_int64(0)
     _check(load().dd_binned_launch_count(b, ctypes.addressof(n)), "dd_binned_launch_count")
+    return int(n.value)
+
+
+def dd_batch_graph_replays(batch) -> int:
+    n = ctypes.c_int64(0)
+    _check(load().dd_batch_graph_replays(batch, ctypes.addressof(n)), "dd_batch_graph_replays")
     return int(n.value)

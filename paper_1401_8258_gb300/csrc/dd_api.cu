@@ -52,6 +52,7 @@ int ensure_chunk_workspace(dd_plan *p, size_t entries) {
   free_device(p->d_counts);
   free_device(p->d_offsets);
   p->chunk_cap = 0;
+  ++p->ws_gen;
   if (cudaMalloc(&p->d_counts, entries * sizeof(int64_t)) != cudaSuccess ||
       cudaMalloc(&p->d_offsets, entries * sizeof(int64_t)) != cudaSuccess) {
     free_device(p->d_counts);
@@ -66,6 +67,7 @@ int ensure_chunk_workspace(dd_plan *p, size_t entries) {
 // are allocated with it on first use.
 int ensure_tile_workspace(dd_plan *p, size_t entries) {
   if (!p->d_rowsums) {
+    ++p->ws_gen;
     if (cudaMalloc(&p->d_rowsums, 2 * sizeof(int64_t) * p->ndm) != cudaSuccess ||
         cudaMalloc(&p->d_rowcount, sizeof(int64_t) * p->ndm) != cudaSuccess ||
         cudaMalloc(&p->d_rowoff, sizeof(int64_t) * p->ndm) != cudaSuccess) {
@@ -79,6 +81,7 @@ int ensure_tile_workspace(dd_plan *p, size_t entries) {
   free_device(p->d_tilemax);
   free_device(p->d_tilecount);
   p->tile_cap = 0;
+  ++p->ws_gen;
   if (cudaMalloc(&p->d_tilemax, entries * sizeof(int32_t)) != cudaSuccess ||
       cudaMalloc(&p->d_tilecount, entries * sizeof(int32_t)) != cudaSuccess) {
     free_device(p->d_tilemax);
@@ -479,14 +482,18 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
 }
 
-// The body of dd_batch_run and dd_streams_push: n beams (distinct plans on
-// `device`), staged u8 beams through shared persistent launches that use
-// the work-queue head `next_item` and status word `status`, the rest through
-// their own kernels; detection per beam; one synchronisation.
-int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
-              unsigned long long *next_item, int32_t *status, const void *const *block,
-              const int64_t *nsamp_in, const int64_t *pitch_elems, void *const *out, float nsigma,
-              dd_candidate *const *cands, const int64_t *capacity, int64_t *counts, void *stream) {
+// Queues the work of dd_batch_run and dd_streams_push on `stream`: n beams
+// (distinct plans on `device`), staged u8 beams through shared persistent
+// launches that use the work-queue head `next_item` and status word
+// `status`, the rest through their own kernels; detection per beam; each
+// beam's count copied to its plan's pinned slot.  Queues only (no
+// synchronisation, no allocation once the workspaces fit), so the same
+// sequence can be captured into a CUDA graph.
+int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
+                unsigned long long *next_item, int32_t *status, const void *const *block,
+                const int64_t *nsamp_in, const int64_t *pitch_elems, void *const *out,
+                float nsigma, dd_candidate *const *cands, const int64_t *capacity,
+                int64_t *counts, void *stream) {
   if (!block || !nsamp_in || !pitch_elems || !out || !cands || !capacity || !counts)
     return DD_ERR_ARG;
   if (!std::isfinite(nsigma)) return DD_ERR_ARG;
@@ -571,7 +578,16 @@ int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
     err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
     if (err != cudaSuccess) return cuda_status(err);
   }
-  err = cudaStreamSynchronize(s);
+  return DD_OK;
+}
+
+// Waits for queued beams and collects their status and counts.
+int finish_beams(dd_plan *const *plans, int n, int device, int32_t *status,
+                 const int64_t *capacity, int64_t *counts, void *stream) {
+  DeviceScope scope(device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return cuda_status(err);
   int result = DD_OK;
   int32_t flag = 0;
@@ -594,7 +610,23 @@ int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
   return DD_OK;
 }
 
+// queue_beams then finish_beams on the same stream.
+int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
+              unsigned long long *next_item, int32_t *status, const void *const *block,
+              const int64_t *nsamp_in, const int64_t *pitch_elems, void *const *out, float nsigma,
+              dd_candidate *const *cands, const int64_t *capacity, int64_t *counts, void *stream) {
+  const int st = queue_beams(plans, n, device, sm_count, next_item, status, block, nsamp_in,
+                             pitch_elems, out, nsigma, cands, capacity, counts, stream);
+  if (st != DD_OK) return st;
+  return finish_beams(plans, n, device, status, capacity, counts, stream);
+}
 
+
+// A batch replays its launch sequence as a CUDA graph while the arguments,
+// the plans' workspaces (ws_gen) and their kernel settings stay the same:
+// the first run of an argument set runs directly (and sizes the
+// workspaces), the sequence is then captured on a private stream, and later
+// runs launch the graph on the caller's stream.
 struct dd_batch {
   int device = 0;
   int sm_count = 0;
@@ -602,6 +634,11 @@ struct dd_batch {
   unsigned long long *d_next_item = nullptr;  // work-queue head of the shared launches
   int32_t *d_error = nullptr;                 // status word of the shared launches
   int64_t launches = 0;
+  cudaStream_t capture = nullptr;       // private stream for graph capture
+  cudaGraphExec_t exec = nullptr;       // captured launch sequence (null: none)
+  std::vector<uint64_t> key;            // what the graph was captured for
+  std::vector<int64_t> graph_launches;  // kernels per replay, per plan
+  int64_t replays = 0;
 };
 
 extern "C" int dd_batch_create(dd_batch **out, dd_plan *const *plans, int32_t nplans) {
@@ -628,9 +665,11 @@ extern "C" int dd_batch_create(dd_batch **out, dd_plan *const *plans, int32_t np
   if (e == cudaSuccess) e = cudaMalloc(&b->d_next_item, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMalloc(&b->d_error, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMemset(b->d_error, 0, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_device(b->d_next_item);
     free_device(b->d_error);
+    if (b->capture) cudaStreamDestroy(b->capture);
     delete b;
     return cuda_status(e);
   }
@@ -644,18 +683,132 @@ extern "C" int dd_batch_destroy(dd_batch *b) {
   if (scope.ok()) cudaDeviceSynchronize();
   free_device(b->d_next_item);
   free_device(b->d_error);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
   return DD_OK;
 }
+
+namespace {
+
+// Everything a captured batch sequence depends on.
+std::vector<uint64_t> batch_key(const dd_batch *b, const void *const *block,
+                                const int64_t *nsamp_in, const int64_t *pitch_elems,
+                                void *const *out, float nsigma, dd_candidate *const *cands,
+                                const int64_t *capacity) {
+  std::vector<uint64_t> k;
+  uint32_t ns = 0;
+  std::memcpy(&ns, &nsigma, sizeof(ns));
+  k.push_back(ns);
+  for (size_t i = 0; i < b->plans.size(); ++i) {
+    const dd_plan *p = b->plans[i];
+    k.push_back(reinterpret_cast<uintptr_t>(block[i]));
+    k.push_back(static_cast<uint64_t>(nsamp_in[i]));
+    k.push_back(static_cast<uint64_t>(pitch_elems[i]));
+    k.push_back(reinterpret_cast<uintptr_t>(out[i]));
+    k.push_back(reinterpret_cast<uintptr_t>(cands[i]));
+    k.push_back(static_cast<uint64_t>(capacity[i]));
+    k.push_back(p->ws_gen);
+    k.push_back(static_cast<uint64_t>(p->path));
+    k.push_back(p->wait_timeout_ns);
+    k.push_back(static_cast<uint64_t>(p->debug_skip_copies));
+  }
+  return k;
+}
+
+// Captures the batch's launch sequence for these arguments into b->exec
+// (after a direct run sized every workspace).  Returns false when capture
+// is unavailable; the batch then keeps running directly.
+bool capture_batch(dd_batch *b, std::vector<uint64_t> key, const void *const *block,
+                   const int64_t *nsamp_in, const int64_t *pitch_elems, void *const *out,
+                   float nsigma, dd_candidate *const *cands, const int64_t *capacity,
+                   int64_t *counts) {
+  if (b->exec) {
+    cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+  }
+  const int n = static_cast<int>(b->plans.size());
+  std::vector<int64_t> before(n);
+  std::vector<uint64_t> gens(n);
+  std::vector<char> valid(n);
+  for (int i = 0; i < n; ++i) {
+    before[i] = b->plans[i]->launches;
+    gens[i] = b->plans[i]->ws_gen;
+    valid[i] = b->plans[i]->stats_valid;
+  }
+  if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) return false;
+  const int st = queue_beams(b->plans.data(), n, b->device, b->sm_count, b->d_next_item,
+                             b->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands,
+                             capacity, counts, b->capture);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(b->capture, &graph);
+  bool ok = st == DD_OK && e == cudaSuccess && graph != nullptr;
+  for (int i = 0; i < n; ++i) ok = ok && b->plans[i]->ws_gen == gens[i];  // nothing reallocated
+  if (ok) ok = cudaGraphInstantiate(&b->exec, graph, 0) == cudaSuccess;
+  if (graph) cudaGraphDestroy(graph);
+  cudaGetLastError();  // a failed capture leaves no sticky error behind
+  b->graph_launches.assign(n, 0);
+  for (int i = 0; i < n; ++i) {  // nothing ran during capture: restore the plans' state
+    b->graph_launches[i] = b->plans[i]->launches - before[i];
+    b->plans[i]->launches = before[i];
+    b->plans[i]->stats_valid = valid[i];
+  }
+  if (!ok) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+    return false;
+  }
+  b->key = std::move(key);
+  return true;
+}
+
+}  // namespace
 
 extern "C" int dd_batch_run(dd_batch *b, const void *const *block, const int64_t *nsamp_in,
                             const int64_t *pitch_elems, void *const *out, float nsigma,
                             dd_candidate *const *cands, const int64_t *capacity, int64_t *counts,
                             void *stream) {
   if (!b) return DD_ERR_ARG;
-  return run_beams(b->plans.data(), static_cast<int>(b->plans.size()), b->device, b->sm_count,
-                   b->d_next_item, b->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands,
-                   capacity, counts, stream);
+  if (!block || !nsamp_in || !pitch_elems || !out || !cands || !capacity || !counts)
+    return DD_ERR_ARG;
+  const int n = static_cast<int>(b->plans.size());
+  std::vector<uint64_t> key;
+  try {
+    key = batch_key(b, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity);
+  } catch (...) {
+    return DD_ERR_OOM;
+  }
+  if (b->exec && key == b->key) {
+    DeviceScope scope(b->device);
+    if (!scope.ok()) return DD_ERR_CUDA;
+    for (int i = 0; i < n; ++i) {
+      counts[i] = 0;
+      b->plans[i]->stats_valid = false;
+    }
+    if (cudaGraphLaunch(b->exec, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+      return DD_ERR_CUDA;
+    ++b->replays;
+    for (int i = 0; i < n; ++i) b->plans[i]->launches += b->graph_launches[i];
+    return finish_beams(b->plans.data(), n, b->device, b->d_error, capacity, counts, stream);
+  }
+  const int st = run_beams(b->plans.data(), n, b->device, b->sm_count, b->d_next_item,
+                           b->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity,
+                           counts, stream);
+  if (st == DD_OK || st == DD_ERR_OVERFLOW) {
+    DeviceScope scope(b->device);
+    std::vector<int64_t> keep(counts, counts + n);
+    if (scope.ok())
+      capture_batch(b, std::move(key), block, nsamp_in, pitch_elems, out, nsigma, cands, capacity,
+                    counts);
+    std::copy(keep.begin(), keep.end(), counts);  // capture resets them; the run's stand
+  }
+  return st;
+}
+
+extern "C" int dd_batch_graph_replays(const dd_batch *b, int64_t *replays) {
+  if (!b || !replays) return DD_ERR_ARG;
+  *replays = b->replays;
+  return DD_OK;
 }
 
 // Streaming (Sec. 3.4): each push dedisperses the previous push's last

@@ -87,6 +87,7 @@ struct dd_plan {
   int32_t debug_skip_copies = 0;    // fault injection: staged kernel queues no copies
 
   int64_t launches = 0;
+  uint64_t ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
 };
 
 namespace ddk {

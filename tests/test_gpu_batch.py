@@ -148,3 +148,38 @@ def test_batch_bounded_wait_reports_timeout_and_recovers():
             assert np.array_equal(cands[i], a[1])
     for p in plans:
         p.close()
+
+
+def test_batch_replays_its_captured_graph_and_recaptures_on_change():
+    workloads = small_batch(seed=13, n=5)
+    blocks, _ = make_beams(workloads, seed=150)
+    dblocks = [torch.from_numpy(np.ascontiguousarray(b)).to(DEV) for b in blocks]
+    plans = [plan_of(wl) for wl in workloads]
+    alone = [run_alone(p, b, 5.0, 1 << 16) for p, b in zip(plans, dblocks)]
+    outs = [torch.empty_like(a[0]) for a in alone]
+    with dd.Batch(plans) as batch:
+        for rep in range(4):  # run, capture, then replays
+            for o in outs:
+                o.fill_(-1)
+            got, cands, totals = batch.run(dblocks, 5.0, outs=outs)
+            for i, a in enumerate(alone):
+                assert torch.equal(got[i], a[0]) and totals[i] == a[2], (rep, i)
+                assert np.array_equal(cands[i], a[1])
+                mean, sigma = plans[i].stats()
+                assert np.array_equal(mean, a[3]) and np.array_equal(sigma, a[4])
+        assert batch.graph_replays() == 3
+        # a new output array: run directly and capture again
+        outs[0] = torch.empty_like(outs[0])
+        got, _, totals = batch.run(dblocks, 5.0, outs=outs)
+        assert torch.equal(got[0], alone[0][0]) and batch.graph_replays() == 3
+        got, _, totals = batch.run(dblocks, 5.0, outs=outs)
+        assert torch.equal(got[0], alone[0][0]) and batch.graph_replays() == 4
+        # a plan's workspace reallocated by a longer block elsewhere: no stale replay
+        big = torch.from_numpy(np.ascontiguousarray(
+            np.tile(blocks[1], (1, 2)))).to(DEV)
+        plans[1].run(big, 5.0)
+        got, _, totals = batch.run(dblocks, 5.0, outs=outs)
+        assert torch.equal(got[1], alone[1][0]) and totals[1] == alone[1][2]
+        assert batch.graph_replays() == 4
+    for p in plans:
+        p.close()
