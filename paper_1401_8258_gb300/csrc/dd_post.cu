@@ -686,6 +686,239 @@ dd_boxcar_sweep(const X *__restrict__ rows, int64_t pitch, int64_t ncols, int nt
   }
 }
 
+// Count and write passes for up to kSmallWidths widths, in registers: CTA =
+// the same 4096-sample tile as dd_boxcar_sweep, split between its warps.
+// Lane l of a warp holds K consecutive samples of the warp's window (32 K >=
+// the warp's start samples + 127, the largest width's reach), staged through
+// shared memory so that the global loads are coalesced; each width's sums
+// S_2w[k] = S_w[k] + S_w[k + w] take the partner from the lane's own
+// registers or, past its K samples, from the next lanes by shuffle (fetched
+// before the in-place update, so every partner is still a width-w sum).
+// Lanes past the warp's start samples only feed others; a start sample's sums
+// never reach past the window, so values shuffled in from beyond the warp
+// never reach a counted sum.
+// Two shapes: the count pass keeps 36 samples per lane (1024 start samples
+// per warp, 4 warps: the fewest halo samples); the write pass keeps 20 per
+// lane (512 per warp, 8 warps: twice the warps per SM for the same shared
+// memory, which its per-sample state fills).
+template <bool WRITE> struct RegShape;
+template <> struct RegShape<false> { static constexpr int K = 36, OWN = 1024; };
+template <> struct RegShape<true> { static constexpr int K = 20, OWN = 512; };
+
+// Per start sample of a warp, the best width so far (write pass), and a
+// queue of the samples that pass at the current width: their S/N work runs
+// on all 32 lanes instead of on the few lanes a pulse lights up.
+template <typename V, int OWN>
+struct BestState {
+  float a[OWN];          // S/N through the rounded reciprocal (float)
+  V val[OWN];            // its sum
+  V qval[OWN];           // queue: sums
+  short qpos[OWN];       // queue: positions in the warp's range
+  unsigned char j[OWN];  // its width index (0xff: none yet)
+};
+
+// Dynamic shared memory of dd_boxcar_regs: the staging area, which the
+// write pass then reuses for the best-width state.
+template <typename V, bool WRITE>
+constexpr size_t reg_smem_bytes() {
+  constexpr int K = RegShape<WRITE>::K, OWN = RegShape<WRITE>::OWN, W = kBoxTile / OWN;
+  constexpr size_t stage = sizeof(V) * W * 32 * (K + 1);
+  constexpr size_t best = sizeof(BestState<V, OWN>) * W;
+  return (!WRITE || stage > best) ? stage : best;
+}
+
+template <typename X, typename V, bool WRITE>
+__global__ void __launch_bounds__(kBoxTile / RegShape<WRITE>::OWN * 32)
+dd_boxcar_regs(const X *__restrict__ rows, int64_t pitch, int64_t ncols, int ntiles, int nwidths,
+               const int64_t *__restrict__ thr_all, const double *mean, const double *sigma,
+               int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
+               dd_pulse *__restrict__ pulses, int64_t capacity) {
+  // the staging area is reused for the write pass's best-width state
+  constexpr int kLaneK = RegShape<WRITE>::K, kWarpOwn = RegShape<WRITE>::OWN;
+  constexpr int kRegWarps = kBoxTile / kWarpOwn;
+  static_assert(32 * kLaneK >= kWarpOwn + (1 << (kSmallWidths - 1)) - 1, "window too short");
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int64_t s_thr[kMaxWidths];
+  __shared__ double s_wmu[kMaxWidths], s_den[kMaxWidths], s_rden[kMaxWidths];
+  __shared__ int s_cnt[kRegWarps];
+  if (WRITE && counts[blockIdx.x] == 0) return;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t row = blockIdx.x / ntiles;
+  const int64_t seg = static_cast<int64_t>(blockIdx.x % ntiles) * kBoxTile +
+                      static_cast<int64_t>(warp) * kWarpOwn;
+  const X *x = rows + row * pitch;
+  if (threadIdx.x < kMaxWidths) {
+    const int j = threadIdx.x;
+    s_thr[j] = thr_all[row * kMaxWidths + j];
+    if (WRITE) {
+      const double mu = mean ? mean[row] : 0.0, sg = sigma ? sigma[row] : 1.0;
+      const double dw = static_cast<double>(1 << j);
+      s_wmu[j] = __dmul_rn(dw, mu);
+      s_den[j] = __dmul_rn(sg, __dsqrt_rn(dw));
+      s_rden[j] = 1.0 / s_den[j];
+    }
+  }
+  V *st = reinterpret_cast<V *>(smem_raw) + warp * 32 * (kLaneK + 1);
+#pragma unroll 4
+  for (int q = 0; q < kLaneK; ++q) {
+    const int p = lane + 32 * q;  // position in the warp's window
+    const int64_t g = seg + p;
+    st[(p / kLaneK) * (kLaneK + 1) + p % kLaneK] = g < ncols ? static_cast<V>(x[g]) : V(0);
+  }
+  __syncthreads();
+  V v[kLaneK];
+#pragma unroll
+  for (int k = 0; k < kLaneK; ++k) v[k] = st[lane * (kLaneK + 1) + k];
+  if (WRITE) __syncthreads();  // staging read: the area now holds the best-width state
+  BestState<V, kWarpOwn> *bs = reinterpret_cast<BestState<V, kWarpOwn> *>(smem_raw) + warp;
+  const int base = lane * kLaneK;        // first position of this lane
+  const int64_t t_lane = seg + base;
+  if (WRITE) {
+    for (int k = lane; k < kWarpOwn; k += 32) bs->j[k] = 0xff;
+    __syncwarp();
+  }
+  // a warp whose every counted sum ends inside the row needs no per-sample
+  // length test; lane ownership (positions below 1024) is applied at the end
+  const bool interior = seg + kWarpOwn - 1 + (1 << (nwidths - 1)) <= ncols;
+  uint64_t mask = 0;
+#pragma unroll
+  for (int j = 0; j < kSmallWidths; ++j) {
+    if (j >= nwidths) break;
+    if (j > 0) {
+      const int h = 1 << (j - 1);
+      V part[kLaneK];
+#pragma unroll
+      for (int k = 0; k < kLaneK; ++k) {
+        if (k + h >= kLaneK) {
+          const int idx = k + h;
+          part[k] = __shfl_down_sync(0xffffffffu, v[idx % kLaneK], idx / kLaneK);
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kLaneK; ++k) v[k] = v[k] + (k + h < kLaneK ? v[k + h] : part[k]);
+    }
+    const int w = 1 << j;
+    const int64_t thr = s_thr[j];
+    uint64_t hit = 0;
+    if (interior) {
+#pragma unroll
+      for (int k = 0; k < kLaneK; ++k)
+        if (passes<V>(v[k], thr)) hit |= 1ull << k;
+    } else {
+#pragma unroll
+      for (int k = 0; k < kLaneK; ++k)
+        if (t_lane + k + w <= ncols && passes<V>(v[k], thr)) hit |= 1ull << k;
+    }
+    if constexpr (WRITE) {
+      // queue this width's passing owned samples in position order
+      const int own_k = kWarpOwn - base;
+      const uint64_t q = own_k <= 0 ? 0 : (own_k >= kLaneK ? hit : hit & ((1ull << own_k) - 1));
+      const int nq = __popcll(q);
+      int inc = nq;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+      }
+      const int total = __shfl_sync(0xffffffffu, inc, 31);
+      if (total > 0) {
+        int e = inc - nq;
+#pragma unroll
+        for (int k = 0; k < kLaneK; ++k) {
+          if ((q >> k) & 1) {
+            bs->qpos[e] = static_cast<short>(base + k);
+            bs->qval[e] = v[k];
+            ++e;
+          }
+        }
+        __syncwarp();
+        // the oracle keeps the first width with the largest exact S/N; the
+        // float approximation decides unless two widths are within 2^-20
+        for (int e2 = lane; e2 < total; e2 += 32) {
+          const int i = bs->qpos[e2];
+          const V val = bs->qval[e2];
+          const double num = __dsub_rn(static_cast<double>(val), s_wmu[j]);
+          const float a = static_cast<float>(num * s_rden[j]);
+          const int oj = bs->j[i];
+          bool take;
+          if (oj == 0xff) {
+            take = true;
+          } else if (fabsf(a - bs->a[i]) > 0x1p-20f * fmaxf(fabsf(a), fabsf(bs->a[i]))) {
+            take = a > bs->a[i];
+          } else {
+            const double e_old =
+                __ddiv_rn(__dsub_rn(static_cast<double>(bs->val[i]), s_wmu[oj]), s_den[oj]);
+            take = __ddiv_rn(num, s_den[j]) > e_old;
+          }
+          if (take) {
+            bs->a[i] = a;
+            bs->j[i] = static_cast<unsigned char>(j);
+            bs->val[i] = val;
+          }
+        }
+        __syncwarp();
+      }
+    }
+    mask |= hit;
+  }
+  // positions at or past the warp's 1024 belong to the next warp
+  const int own = kWarpOwn - base;  // <= 0: none, >= kLaneK: all
+  if (own <= 0) mask = 0;
+  else if (own < kLaneK) mask &= (1ull << own) - 1;
+  const int mine = __popcll(mask);
+  if constexpr (!WRITE) {
+    int c = mine;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xffffffffu, c, o);
+    if (lane == 0) s_cnt[warp] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int total = 0;
+      for (int k = 0; k < kRegWarps; ++k) total += s_cnt[k];
+      counts[blockIdx.x] = total;
+    }
+  } else {
+    // lanes' segments are in time order: rank = pulses of earlier warps and
+    // lanes + earlier pulses of this lane
+    int inc = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (lane == 31) s_cnt[warp] = inc;
+    __syncthreads();
+    int warp_before = 0;
+    for (int k = 0; k < warp; ++k) warp_before += s_cnt[k];
+    const int total = s_cnt[warp];
+    // the warp's pulses in position order, then written by all lanes
+    int e = inc - mine;
+#pragma unroll
+    for (int k = 0; k < kLaneK; ++k) {
+      if ((mask >> k) & 1) {
+        bs->qpos[e] = static_cast<short>(base + k);
+        ++e;
+      }
+    }
+    __syncwarp();
+    const int64_t pos0 = offsets[blockIdx.x] + warp_before;
+    for (int e2 = lane; e2 < total; e2 += 32) {
+      const int64_t pos = pos0 + e2;
+      if (pos >= capacity) break;
+      const int i = bs->qpos[e2];
+      const int bj = bs->j[i];
+      dd_pulse p;
+      p.dm_idx = static_cast<int32_t>(row);
+      p.t = static_cast<int32_t>(seg + i);
+      p.width = 1 << bj;
+      p.snr = __double2float_rn(
+          __ddiv_rn(__dsub_rn(static_cast<double>(bs->val[i]), s_wmu[bj]), s_den[bj]));
+      p.value = static_cast<double>(bs->val[i]);
+      pulses[pos] = p;
+    }
+  }
+}
+
 // Single-CTA exclusive scan of m counts; *total gets their sum.
 __global__ void __launch_bounds__(kScanThreads)
 dd_boxcar_scan(const int64_t *__restrict__ counts, int64_t m, int64_t *__restrict__ offsets,
@@ -732,6 +965,23 @@ cudaError_t sweep_launches(const X *rows, int64_t pitch, int64_t ncols, int ntil
     e = cudaFuncSetAttribute(dd_boxcar_sweep<X, V, true, PER>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   if (e != cudaSuccess) return e;
+  if (PER == kBoxPerSmall) {  // up to kSmallWidths widths: the register passes
+    const size_t rc = reg_smem_bytes<V, false>(), rw = reg_smem_bytes<V, true>();
+    e = cudaFuncSetAttribute(dd_boxcar_regs<X, V, false>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(rc));
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(dd_boxcar_regs<X, V, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(rw));
+    if (e != cudaSuccess) return e;
+    dd_boxcar_regs<X, V, false><<<grid, kBoxTile / RegShape<false>::OWN * 32, rc, s>>>(
+        rows, pitch, ncols, ntiles, nwidths, thr, mean, sigma, counts, offsets, pulses, capacity);
+    dd_boxcar_scan<<<1, kScanThreads, 0, s>>>(counts, m, offsets, total);
+    if (capacity > 0)
+      dd_boxcar_regs<X, V, true><<<grid, kBoxTile / RegShape<true>::OWN * 32, rw, s>>>(
+          rows, pitch, ncols, ntiles, nwidths, thr, mean, sigma, counts, offsets, pulses,
+          capacity);
+    return cudaGetLastError();
+  }
   dd_boxcar_sweep<X, V, false, PER><<<grid, kBoxThreads, smem, s>>>(
       rows, pitch, ncols, ntiles, nwidths, thr, mean, sigma, counts, offsets, pulses, capacity);
   dd_boxcar_scan<<<1, kScanThreads, 0, s>>>(counts, m, offsets, total);
