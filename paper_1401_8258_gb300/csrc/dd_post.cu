@@ -76,11 +76,21 @@ dd_median(const T *__restrict__ in, int64_t in_pitch, int64_t ncols, int ntiles,
   const int64_t t0 = static_cast<int64_t>(blockIdx.x % ntiles) * kMedTile;
   const T *x = in + row * in_pitch;
   T *y = out + row * out_pitch;
-  // s[i] = sample t0 - H + i, clamped to the row
-  for (int i = threadIdx.x; i < kMedTile + 2 * H; i += kMedThreads) {
+  // s[i] = sample t0 - H + i, clamped to the row; several loads in flight
+  // per thread before their stores
+  constexpr int kLoads = (kMedTile + 2 * H + kMedThreads - 1) / kMedThreads;
+  T v[kLoads];
+#pragma unroll
+  for (int r = 0; r < kLoads; ++r) {
+    const int i = threadIdx.x + r * kMedThreads;
     int64_t g = t0 - H + i;
     g = g < 0 ? 0 : (g >= ncols ? ncols - 1 : g);
-    s[i] = x[g];
+    v[r] = i < kMedTile + 2 * H ? x[g] : T(0);
+  }
+#pragma unroll
+  for (int r = 0; r < kLoads; ++r) {
+    const int i = threadIdx.x + r * kMedThreads;
+    if (i < kMedTile + 2 * H) s[i] = v[r];
   }
   __syncthreads();
   const P2 *s2 = reinterpret_cast<const P2 *>(s);
@@ -157,7 +167,7 @@ int launch_median(const T *in, int64_t in_pitch, int32_t nrows, int64_t ncols, i
 // in float: a + b t is formed in double once per 16 samples and split into
 // an integer part (subtracted exactly from int rows) and a small float part.
 
-constexpr int kDtThreads = 1024;
+constexpr int kDtThreads = 256;
 constexpr int kDtChunk = 16;
 
 using i128 = __int128;
@@ -317,7 +327,7 @@ __device__ __forceinline__ void for_chunks(int64_t n, int head, F &&f) {
 }
 
 template <typename X>
-__global__ void __launch_bounds__(kDtThreads, 1)
+__global__ void __launch_bounds__(kDtThreads, 4)  // four rows in flight per SM
 dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t out_pitch,
                 double *coef) {  // no __restrict__: out may be in (float rows, in place)
   __shared__ i128 s_i[kDtThreads / 32];
