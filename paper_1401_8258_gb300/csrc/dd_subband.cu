@@ -114,21 +114,36 @@ dd_grouped(const TI *__restrict__ in, int64_t pitch, int64_t ig, const int32_t *
       }
     }
     __syncthreads();
-    // windows: channel c, samples t0 + lo_c .. t0 + lo_c + W - 1; the loads
-    // of several channels are issued before their shared-memory stores
-    constexpr int kUnroll = 4;
+    // windows: channel c, samples t0 + lo_c .. t0 + lo_c + W - 1; a thread
+    // issues the loads of 8 channels x 3 samples before their shared-memory
+    // stores (24 loads in flight), then covers any rest of a wide window
+    constexpr int kUnroll = 8, kReach = 3;
     for (int cb = 0; cb < nc; cb += kUnroll) {
-      for (int k = threadIdx.x; k < W; k += kGroupThreads) {
-        TI v[kUnroll];
+      TI v[kUnroll][kReach];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const int c = cb + u;
+      for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+        for (int r = 0; r < kReach; ++r) {
+          const int c = cb + u, k = threadIdx.x + r * kGroupThreads;
           const int64_t tt = t0 + (c < nc ? s_lo[c] : 0) + k;
-          v[u] = (c < nc && tt < n_valid) ? x[static_cast<int64_t>(c0 + c) * pitch + tt] : TI(0);
+          v[u][r] = (c < nc && k < W && tt < n_valid)
+                        ? x[static_cast<int64_t>(c0 + c) * pitch + tt] : TI(0);
         }
+      }
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u)
-          if (cb + u < nc) win[(cb + u) * W + k] = v[u];
+      for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+        for (int r = 0; r < kReach; ++r) {
+          const int k = threadIdx.x + r * kGroupThreads;
+          if (cb + u < nc && k < W) win[(cb + u) * W + k] = v[u][r];
+        }
+      }
+      for (int u = 0; u < kUnroll && cb + u < nc; ++u) {
+        const int c = cb + u;
+        for (int k = threadIdx.x + kReach * kGroupThreads; k < W; k += kGroupThreads) {
+          const int64_t tt = t0 + s_lo[c] + k;
+          win[c * W + k] = tt < n_valid ? x[static_cast<int64_t>(c0 + c) * pitch + tt] : TI(0);
+        }
       }
     }
     __syncthreads();
