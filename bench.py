@@ -70,6 +70,32 @@ def dist_env():
     return rank, world, local
 
 
+# Replicas: with N ranks each dedisperses its own beam (no data-path
+# collective); the job's time is the slowest rank's and its rate counts the
+# units every rank processed.
+
+def replica_seed(seed, rank):
+    """Seed of rank `rank`'s beam (each replica gets its own data)."""
+    return seed + rank
+
+
+def max_over_ranks(value, world, device=None):
+    """The largest `value` over all ranks (all_reduce MAX; needs an initialised
+    process group when world > 1)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, units_per_step, steps, seconds):
+    """Units all ranks processed per second of the slowest rank."""
+    return world * units_per_step * steps / seconds
+
+
 # ------------------------------------------------------------------ clocks
 
 class ClockSampler:
@@ -389,7 +415,7 @@ def run_ours(args):
     plan = dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, wl.dtype, local)
     delays = plan.delays()
     nsamp_out = plan.nsamp_out(wl.nsamp)
-    block_np, pulses = synth.make_block(wl, args.seed + rank, delays)
+    block_np, pulses = synth.make_block(wl, replica_seed(args.seed, rank), delays)
     block = torch.from_numpy(block_np).to(dev)
     out = torch.empty((wl.ndm, nsamp_out), dtype=plan.out_torch_dtype, device=dev)
     cap = 1 << 20
@@ -437,12 +463,9 @@ def run_ours(args):
     kern_ms = [s.elapsed_time(m) for s, m in zip(starts, mids)]
     t_total = sum(step_ms) / 1e3
     t_kernel = sum(kern_ms) / len(kern_ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = max_over_ranks(t_total, world, dev)
     units_per_step = wl.ndm * nsamp_out
-    value = world * units_per_step * args.steps / t_total
+    value = whole_job_rate(world, units_per_step, args.steps, t_total)
 
     # end to end through the C ABI on pinned host buffers
     e2e = None
@@ -463,11 +486,8 @@ def run_ours(args):
         ev1.record(stream)
         torch.cuda.synchronize()
         t_e2e = ev0.elapsed_time(ev1) / 1e3
-        if world > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * units_per_step * args.steps / t_e2e, "unit": UNIT,
+        t_e2e = max_over_ranks(t_e2e, world, dev)
+        e2e = {"value": whole_job_rate(world, units_per_step, args.steps, t_e2e), "unit": UNIT,
                "h2d_bytes_per_step": int(block_np.nbytes),
                "d2h_bytes_per_step": int(8 + 16 * statistics.mean(min(c, cap) for c in counts))}
 
