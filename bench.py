@@ -797,6 +797,63 @@ def run_serve(args):
                 "max_realtime_beams": n * rounds * 1.0 / busy,
                 "realtime_factor": rounds * 1.0 / busy}
 
+    def saturate(per_beam, factor, rounds_sat):
+        """Load sweep: each admitted stream stands for `factor` beams of the
+        same geometry whose 1 s blocks arrive at phases (phase_b + r /
+        factor) + k, so n * factor blocks arrive per second.  The GPU work of
+        a block is that of its stream's push (timing only: the replicas
+        share the stream's buffers); a wave takes at most one waiting block
+        per stream, oldest first.  Returns the p99 latency, the GPU's busy
+        time per second of data (utilisation) and whether the load is
+        sustained: utilisation below 1 (the backlog does not grow) and every
+        block finished, at p99 within one block duration of its arrival."""
+        arr = sorted((phases[b] + r / factor + k, b) for b in range(n) for r in range(factor)
+                     for k in range(rounds_sat))
+        waiting = [[] for _ in range(n)]  # per stream, arrival times (sorted)
+        i, t, lat, busy = 0, 0.0, [], 0.0
+        left = len(arr)
+        while left:
+            while i < len(arr) and arr[i][0] <= t:
+                waiting[arr[i][1]].append(arr[i][0])
+                i += 1
+            ready = [b for b in range(n) if waiting[b]]
+            if not ready:
+                t = arr[i][0]
+                continue
+            ev0.record(stream)
+            if per_beam:
+                for b in ready:
+                    push([b])
+            else:
+                push(ready)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            w = ev0.elapsed_time(ev1) / 1e3
+            t += w
+            busy += w
+            for b in ready:
+                lat.append(t - waiting[b].pop(0))
+                left -= 1
+            if lat and lat[-1] > 4.0:
+                break  # far past the block duration: the queue grows without bound
+        p99 = float(np.percentile(lat, 99))
+        util = busy / rounds_sat
+        return p99, util, bool(left == 0 and p99 < 1.0 and util < 1.0)
+
+    def max_beams(per_beam):
+        """Largest load (beams of this mix) kept within one block duration at
+        p99, over a sweep of stream multiplicities."""
+        best, p99_best, tried = 0, None, []
+        for factor in (4, 8, 10, 11, 12, 13, 14, 15, 16, 18, 20):
+            p99, util, ok = saturate(per_beam, factor, 4)
+            tried.append({"beams": n * factor, "p99_latency_s": p99, "utilisation": util,
+                          "sustained": ok})
+            if not ok:
+                break
+            best, p99_best = n * factor, p99
+        return {"max_realtime_beams_at_p99_below_block": best, "p99_latency_s": p99_best,
+                "sweep": tried}
+
     for _ in range(max(1, args.warmup)):  # warm-up waves of every beam
         push(list(range(n)))
     torch.cuda.synchronize()
@@ -810,6 +867,8 @@ def run_serve(args):
     clock = clocks.stop()
     per_beam = simulate(True, phases)
     per_beam_aligned = simulate(True, aligned)
+    sat_waves = max_beams(False)
+    sat_plain = max_beams(True)
     units = sum(w.ndm * w.nsamp for w in wls) * rounds
     value = units / wave["busy_s"]
     adds = float(sum(w.ndm * w.nsamp * w.nchan for w in wls)) * rounds
@@ -835,7 +894,9 @@ def run_serve(args):
                      "kernel_ms": 1e3 * wave["busy_s"] / wave["waves"]},
         "serving": {"staggered_arrivals": {"waves": wave, "per_beam_launches": per_beam},
                     "aligned_arrivals": {"waves": wave_aligned,
-                                         "per_beam_launches": per_beam_aligned}},
+                                         "per_beam_launches": per_beam_aligned},
+                    "saturation": {"waves": sat_waves, "per_beam_launches": sat_plain,
+                                   "block_s": 1.0}},
         "cpu_baseline": None, "e2e": None, "clocks": clock, "gpu_launches": int(launches),
     }
     print(json.dumps(line), flush=True)
