@@ -183,3 +183,42 @@ def test_batch_replays_its_captured_graph_and_recaptures_on_change():
         assert batch.graph_replays() == 4
     for p in plans:
         p.close()
+
+
+def test_full_size_batch_of_32_beams_sampled_rows():
+    """The 32-beam batch the bench times (same generator and seed), every
+    beam checked on two sampled DM rows against the oracle: outputs exactly,
+    and the candidates of those rows with the rows' own statistics."""
+    import bench
+    workloads = bench.batch_workloads(1)
+    assert len(workloads) == 32
+    plans = [plan_of(wl) for wl in workloads]
+    rng = np.random.default_rng(77)
+    blocks, dblocks, delays = [], [], []
+    for i, (wl, p) in enumerate(zip(workloads, plans)):
+        d = p.delays()
+        b, _ = synth.make_block(wl, 1000 + i, d)
+        blocks.append(b)
+        dblocks.append(torch.from_numpy(b).to(DEV))
+        delays.append(d)
+    with dd.Batch(plans) as batch:
+        outs, cands, totals = batch.run(dblocks, 6.0, capacity=1 << 20)
+        assert max(totals) <= 1 << 20
+        for i, wl in enumerate(workloads):
+            rows = rng.choice(wl.ndm, 2, replace=False)
+            ref = oracle.dedisperse(blocks[i], np.ascontiguousarray(delays[i][:, rows]),
+                                    nsamp_out=outs[i].shape[1])
+            got = outs[i][torch.as_tensor(rows, device=DEV)].cpu().numpy()
+            assert np.array_equal(got, ref), i
+            mean, sigma = oracle.stats(ref)
+            c_ref, _ = oracle.detect(ref, mean, sigma, 6.0)
+            g_mean, g_sigma = plans[i].stats()
+            assert np.array_equal(g_mean[rows], mean) and np.array_equal(g_sigma[rows], sigma)
+            for k, r in enumerate(rows):
+                mine = cands[i][cands[i]["dm_idx"] == r]
+                theirs = c_ref[c_ref["dm_idx"] == k]
+                assert np.array_equal(mine["t"], theirs["t"]), (i, r)
+                assert np.array_equal(mine["value"], theirs["value"]), (i, r)
+    del outs, dblocks
+    for p in plans:
+        p.close()

@@ -131,3 +131,38 @@ def test_stream_memory_model_covers_its_buffers():
         # output and the plan's workspace, also in the model)
         assert 0 < free0 - free1 <= need
         assert need >= 2 * wl.nchan * (plan.maxshift + block)
+
+
+def test_full_size_serving_mix_sampled_rows():
+    """The 64-beam serving mix the bench runs (same generator and seed), two
+    consecutive 1 s blocks pushed as one wave each; every beam checked on two
+    sampled DM rows against the oracle over its whole signal (maxshift zeros,
+    then both blocks)."""
+    import bench
+    wls = bench.serving_workloads(1)
+    assert len(wls) == 64
+    plans = [plan_of(w) for w in wls]
+    streams = [dd.Stream(p, w.nsamp) for p, w in zip(plans, wls)]
+    rng = np.random.default_rng(5)
+    sigs = [synth.random_block(rng, w.nchan, 2 * w.nsamp, "u8") for w in wls]
+    results = [[] for _ in wls]
+    for k in range(2):
+        blks = [torch.from_numpy(np.ascontiguousarray(s[:, k * w.nsamp:(k + 1) * w.nsamp]))
+                .to(DEV) for s, w in zip(sigs, wls)]
+        outs, _, _ = dd.push_streams(streams, blks, 6.0, capacity=1 << 18)
+        for i in range(len(wls)):
+            results[i].append(outs[i])
+    for i, (w, p) in enumerate(zip(wls, plans)):
+        mx = p.maxshift
+        full = np.zeros((w.nchan, mx + 2 * w.nsamp), dtype=np.uint8)
+        full[:, mx:] = sigs[i]
+        rows = rng.choice(w.ndm, 2, replace=False)
+        ref = oracle.dedisperse(full, np.ascontiguousarray(p.delays()[:, rows]),
+                                nsamp_out=2 * w.nsamp)
+        got = torch.cat([r[torch.as_tensor(rows, device=DEV)] for r in results[i]],
+                        dim=1).cpu().numpy()
+        assert got.shape == ref.shape and np.array_equal(got, ref), i
+    for st in streams:
+        st.close()
+    for p in plans:
+        p.close()
