@@ -92,11 +92,6 @@ struct Elem<__half> {
   }
 };
 
-__device__ __forceinline__ float ldsf(uint32_t addr) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(addr));
-  return v;
-}
 template <int OFF>
 __device__ __forceinline__ float ldsf_off(uint32_t addr) {
   float v;

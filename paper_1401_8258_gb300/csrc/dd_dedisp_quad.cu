@@ -576,8 +576,8 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
 
 namespace ddk {
 
-bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out) {
-  if (!p->quad || p->dtype != DD_U8) return false;
+bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t /*nsamp_out*/) {
+  if (!p->quad || p->dtype != DD_U8) return false;  // the work queue has no tile-count limit
   return (reinterpret_cast<uintptr_t>(block) & 15) == 0 && (pitch & 15) == 0;
 }
 
