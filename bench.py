@@ -573,6 +573,10 @@ def run_batch(args):
     wls = batch_workloads(args.seed)
     plans = [dd.Plan(w.nchan, w.f_top_mhz, w.chan_width_mhz, w.t_samp_s, w.dms, "u8", local)
              for w in wls]
+    # plan time, outside the timed region: the autotuner times every staged
+    # tile width on each beam's geometry and keeps the fastest (a shorter
+    # scratch block suffices: the choice depends on the geometry)
+    tuned = [p.autotune(min(w.nsamp, p.maxshift + 32768)) for p, w in zip(plans, wls)]
     host_blocks, blocks, outs, nouts = [], [], [], []
     for i, (w, p) in enumerate(zip(wls, plans)):
         b, _ = synth.make_block(w, args.seed + 1000 * (rank + 1) + i, p.delays())
@@ -684,6 +688,7 @@ def run_batch(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": BATCH, "beams": len(wls), "staged_beams": int(staged),
+                   "autotuned_dms_per_cta": [int(t[0]) for t in tuned],
                    "nchan": [w.nchan for w in wls], "ndm": [w.ndm for w in wls],
                    "nsamp_in": nsamp, "input_dtype": "u8", "nsigma": NSIGMA,
                    "parallelism": "replicas1",
