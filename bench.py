@@ -228,8 +228,18 @@ def time_oracle_sample(wl, block, delays, nsamp_out, target_s: float) -> dict:
     m, s = oracle.stats(D)
     oracle.detect(D, m, s, NSIGMA, capacity=0)
     dt = time.perf_counter() - t0
+    # the same work on one core, on a few trials (about a tenth of the time)
+    n1 = max(1, min(n, int(0.1 * target_s / max(per_dm * oracle.max_threads(), 1e-9))))
+    idx1 = np.linspace(0, ndm_total - 1, n1).astype(int)
+    t0 = time.perf_counter()
+    D1 = oracle.dedisperse(block, delays[:, idx1], nsamp_out=nsamp_out, nsamp_in=wl.nsamp,
+                           nthreads=1)
+    m1, s1 = oracle.stats(D1)
+    oracle.detect(D1, m1, s1, NSIGMA, capacity=0)
+    dt1 = time.perf_counter() - t0
     return {"value": n * nsamp_out / dt, "unit": UNIT, "cores": oracle.max_threads(),
             "kind": "oracle", "seconds": dt,
+            "single_core": {"value": n1 * nsamp_out / dt1, "trials": n1, "seconds": dt1},
             "sample": f"{n} of {ndm_total} DM trials (evenly spaced) x {nsamp_out} samples x "
                       f"{wl.nchan} channels of the same block; dedispersion + stats + detection"}
 
@@ -372,7 +382,8 @@ def run_reference(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "int64" if wl.dtype == "u8" else "f64",
         "data": "synthetic", "config": workload_config(wl, nsamp_out, args.gpus),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
-                         "kind": "oracle", "sample": samples[-1], "cpu_model": cpu_model()},
+                         "kind": "oracle", "sample": samples[-1], "cpu_model": cpu_model(),
+                         "single_core": r["single_core"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -462,7 +473,7 @@ def run_ours(args):
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     kern_ms = [s.elapsed_time(m) for s, m in zip(starts, mids)]
     t_total = sum(step_ms) / 1e3
-    t_kernel = sum(kern_ms) / len(kern_ms) / 1e3
+    t_kernel = statistics.median(kern_ms) / 1e3  # median of the timed launches
     t_total = max_over_ranks(t_total, world, dev)
     units_per_step = wl.ndm * nsamp_out
     value = whole_job_rate(world, units_per_step, args.steps, t_total)
@@ -523,6 +534,9 @@ def run_ours(args):
                                        if clock.get("sm_mhz") else None),
             "algorithmic_bytes": algo_bytes,
             "hbm_frac_of_measured": (algo_bytes / t_kernel / 1e9) / float(peaks.get("hbm_gbs", 6784.5)),
+            # the ncu DRAM bytes of one launch over this run's kernel time
+            "hbm_frac_from_traffic": ((traffic / t_kernel / 1e9) / float(peaks.get("hbm_gbs", 6784.5))
+                                      if traffic else None),
             "traffic_source": prof, "add_pipe_probes": probes}
 
     cpu = None
