@@ -264,96 +264,70 @@ def load_workload(args):
     return wl
 
 
-def run_reference_post(args):
-    """Reference arm of the post-processing workload: the oracle's chain on
-    a bounded sample of rows, each row dedispersed by the oracle first
-    (outside the timing)."""
-    import oracle
-
-    wl = synth.workload("full_block_u8")
-    delays, mx, nsamp_out = geometry_oracle(wl)
-    block, _ = synth.make_block(wl, args.seed, delays)
+def reference_steps(args, timed):
+    """Runs the oracle sample `timed(seconds)` for the reference arm's warm-up
+    and timed steps (each sized so the whole run ends within about a
+    minute); returns the median rate, the seconds spent and the last
+    sample's record."""
     per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
-    rows = np.linspace(0, wl.ndm - 1, 64).astype(np.int64)
-    D = oracle.dedisperse(block, np.ascontiguousarray(delays[:, rows]), nsamp_out=nsamp_out)
     for _ in range(args.warmup):
-        time_oracle_post(D, min(per_step, 2.0))
-    vals, secs, sample = [], 0.0, ""
+        timed(min(per_step, 2.0))
+    vals, secs, last = [], 0.0, None
     for _ in range(args.steps):
-        r = time_oracle_post(D, per_step)
-        vals.append(r["value"])
-        secs += r["seconds"]
-        sample = r["sample"]
-    value = statistics.median(vals)
-    line = {
+        last = timed(per_step)
+        vals.append(last["value"])
+        secs += last["seconds"]
+    return statistics.median(vals), secs, last
+
+
+def print_reference(args, value, secs, last, dtype, config):
+    """The reference arm's JSON line (the oracle's rate on the host cores)."""
+    cpu = {"value": value, "unit": UNIT, "cores": last["cores"], "kind": "oracle",
+           "sample": last["sample"]}
+    for k in ("single_core", "cpu_model"):
+        if k in last:
+            cpu[k] = last[k]
+    print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": POST, "rows": wl.ndm, "samples": nsamp_out,
-                   "median_width": POST_MEDIAN_WIDTH, "boxcar_widths": POST_WIDTHS,
-                   "nsigma": NSIGMA, "parallelism": "replicas1"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": "evenly spaced DM rows of the block: " + sample},
+        "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+        "config": config, "cpu_baseline": cpu,
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    }), flush=True)
 
 
 def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    if args.workload == POST:
-        run_reference_post(args)
-        return
-    if args.workload == BINNED:
+    if args.workload in (POST, BINNED, SUBBAND):
+        import oracle
         wl = synth.workload("full_block_u8")
-        delays, _, _ = geometry_oracle(wl)
+        delays, _, nsamp_out = geometry_oracle(wl)
         block, _ = synth.make_block(wl, args.seed, delays)
-        per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
-        vals, secs, sample = [], 0.0, ""
-        for _ in range(args.steps):
-            r = time_oracle_binned(wl, block, per_step)
-            vals.append(r["value"])
-            secs += r["seconds"]
-            sample = r["sample"]
-        value = statistics.median(vals)
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": BINNED, "max_factor": BIN_MAX_FACTOR,
-                       "parallelism": "replicas1"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"],
-                             "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}), flush=True)
-        return
-    if args.workload == SUBBAND:
-        wl = synth.workload("full_block_u8")
-        delays, _, _ = geometry_oracle(wl)
-        block, _ = synth.make_block(wl, args.seed, delays)
-        per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
-        vals, secs, sample = [], 0.0, ""
-        for _ in range(args.steps):
-            r = time_oracle_subband(wl, block, delays, per_step)
-            vals.append(r["value"])
-            secs += r["seconds"]
-            sample = r["sample"]
-        value = statistics.median(vals)
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
-            "config": {"workload": SUBBAND, "chans_per_subband": SUB_CHANS,
-                       "dms_per_group": SUB_DMS, "parallelism": "replicas1"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": r["cores"],
-                             "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": 0}}), flush=True)
+        if args.workload == POST:
+            # the chain on evenly spaced rows, dedispersed by the oracle first
+            rows = np.linspace(0, wl.ndm - 1, 64).astype(np.int64)
+            D = oracle.dedisperse(block, np.ascontiguousarray(delays[:, rows]),
+                                  nsamp_out=nsamp_out)
+            value, secs, last = reference_steps(args, lambda t: time_oracle_post(D, t))
+            last["sample"] = "evenly spaced DM rows of the block: " + last["sample"]
+            config = {"workload": POST, "rows": wl.ndm, "samples": nsamp_out,
+                      "median_width": POST_MEDIAN_WIDTH, "boxcar_widths": POST_WIDTHS,
+                      "nsigma": NSIGMA, "parallelism": "replicas1"}
+            print_reference(args, value, secs, last, "f64", config)
+        elif args.workload == BINNED:
+            value, secs, last = reference_steps(args, lambda t: time_oracle_binned(wl, block, t))
+            config = {"workload": BINNED, "max_factor": BIN_MAX_FACTOR,
+                      "parallelism": "replicas1"}
+            print_reference(args, value, secs, last, "int32", config)
+        else:
+            value, secs, last = reference_steps(
+                args, lambda t: time_oracle_subband(wl, block, delays, t))
+            config = {"workload": SUBBAND, "chans_per_subband": SUB_CHANS,
+                      "dms_per_group": SUB_DMS, "parallelism": "replicas1"}
+            print_reference(args, value, secs, last, "int32", config)
         return
     if args.workload in (BATCH, SERVE):
         # the oracle on the first beam (its rate stands for the set)
@@ -363,30 +337,15 @@ def run_reference(args):
         wl = load_workload(args)
     delays, mx, nsamp_out = geometry_oracle(wl)
     block, _ = synth.make_block(wl, args.seed, delays)
-    per_step = max(1.0, 60.0 / max(args.steps + args.warmup, 1))
-    for _ in range(args.warmup):
-        time_oracle_sample(wl, block, delays, nsamp_out, min(per_step, 2.0))
-    vals, secs = [], 0.0
-    samples = []
-    for _ in range(args.steps):
-        r = time_oracle_sample(wl, block, delays, nsamp_out, per_step)
-        vals.append(r["value"])
-        secs += r["seconds"]
-        samples.append(r["sample"])
-    value = statistics.median(vals)
-    import oracle
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1e3 * secs / max(args.steps, 1), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "int64" if wl.dtype == "u8" else "f64",
-        "data": "synthetic", "config": workload_config(wl, nsamp_out, args.gpus),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
-                         "kind": "oracle", "sample": samples[-1], "cpu_model": cpu_model(),
-                         "single_core": r["single_core"]},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    value, secs, last = reference_steps(
+        args, lambda t: time_oracle_sample(wl, block, delays, nsamp_out, t))
+    last["cpu_model"] = cpu_model()
+    config = workload_config(wl, nsamp_out, args.gpus)
+    if args.workload in (BATCH, SERVE):
+        config = {"workload": args.workload, "sampled_beam": config,
+                  "note": "the oracle's rate on the set's first beam stands for the set"}
+        last["sample"] = "first beam of the set: " + last["sample"]
+    print_reference(args, value, secs, last, "int64" if wl.dtype == "u8" else "f64", config)
 
 
 def geometry_oracle(wl):
