@@ -109,6 +109,9 @@ def smearing_peak_ratio(ddm: float, bandwidth_mhz: float, f_centre_ghz: float,
 # by 2 (adjacent samples summed), 4, ...: trials below twice the diagonal DM
 # at full resolution, trials in [2^k, 2^(k+1)) x DM_diag from the series
 # binned by 2^k (capped at max_factor), with delays at 2^k sampling times.
+# The 8-bit variant keeps uint8 binned series (rounded means instead of sums,
+# which need 9 or more bits), at the cost of a rounding error of at most half
+# a count per halving; it is not in the thesis.
 
 
 def diagonal_dm(nchan: int, f_top_mhz: float, chan_width_mhz: float, t_samp_s: float,
@@ -144,15 +147,36 @@ def decimate(block: np.ndarray, nsamp_in: int, factor: int) -> np.ndarray:
     return x
 
 
+def decimate_mean8(block: np.ndarray, nsamp_in: int, factor: int) -> np.ndarray:
+    """8-bit binned series of uint8 input (a variant; the thesis sums): each
+    halving takes the mean of two adjacent samples rounded half up,
+    b[c][t] = floor((a[c][2t] + a[c][2t+1] + 1) / 2), log2(factor) times.
+    Length nsamp_in // factor, uint8."""
+    if block.dtype != np.uint8:
+        raise ValueError("8-bit means need uint8 input")
+    x = block[:, :nsamp_in].astype(np.int64)
+    while factor > 1:
+        n = x.shape[1] // 2
+        x = (x[:, 0:2 * n:2] + x[:, 1:2 * n:2] + 1) // 2
+        factor //= 2
+    return x.astype(np.uint8)
+
+
 def binned_dedisperse(block: np.ndarray, nchan: int, f_top_mhz: float, chan_width_mhz: float,
                       t_samp_s: float, dms: np.ndarray, max_factor: int,
-                      nsamp_in: int | None = None):
+                      nsamp_in: int | None = None, mode: str = "sum"):
     """Time-binned dedispersion.  Returns (rows, factors, lengths): rows[d] is
     the dedispersed series of trial d at 1/factor[d] of the sampling rate,
     lengths[d] its length (nsamp_in // f - maxshift of its factor's trials at
-    f t_samp); int32 for uint8 input, float64 otherwise."""
+    f t_samp); int32 for uint8 input, float64 otherwise.  mode "sum" bins by
+    summing (the thesis's downfactoring); "mean8" (uint8 input only) bins
+    into 8-bit rounded means (decimate_mean8) and dedisperses those."""
     from . import delay_table
 
+    if mode not in ("sum", "mean8"):
+        raise ValueError(f"unknown binning mode {mode!r}")
+    if mode == "mean8" and block.dtype != np.uint8:
+        raise ValueError("8-bit means need uint8 input")
     dms = np.asarray(dms, dtype=np.float64)
     if nsamp_in is None:
         nsamp_in = block.shape[1]
@@ -164,6 +188,9 @@ def binned_dedisperse(block: np.ndarray, nchan: int, f_top_mhz: float, chan_widt
         delays, _ = delay_table(nchan, f_top_mhz, chan_width_mhz, t_samp_s * f, dms[idx])
         if f == 1:
             src, n_in = block, nsamp_in
+        elif mode == "mean8":
+            src = decimate_mean8(block, nsamp_in, f)
+            n_in = src.shape[1]
         else:
             d = decimate(block, nsamp_in, f)
             src = d.astype(np.float32)  # exact for the integer sums of uint8 input

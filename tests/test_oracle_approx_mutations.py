@@ -33,6 +33,12 @@ MUTANTS = {
         "while 2 * k <= max_factor and dm >= k * dm_diag:"),
     "binning averages instead of summing": ("x = x[:, 0:2 * n:2] + x[:, 1:2 * n:2]",
                                             "x = (x[:, 0:2 * n:2] + x[:, 1:2 * n:2]) // 2"),
+    "8-bit binning rounds down": ("x = (x[:, 0:2 * n:2] + x[:, 1:2 * n:2] + 1) // 2",
+                                  "x = (x[:, 0:2 * n:2] + x[:, 1:2 * n:2]) // 2"),
+    "8-bit binning keeps the even samples": (
+        "x = (x[:, 0:2 * n:2] + x[:, 1:2 * n:2] + 1) // 2", "x = x[:, 0:2 * n:2]"),
+    "8-bit binned rows from the full-rate block": (
+        "src = decimate_mean8(block, nsamp_in, f)", "src = block[:, :nsamp_in // f]"),
     "binned delays at the full-rate sampling time": (
         "delay_table(nchan, f_top_mhz, chan_width_mhz, t_samp_s * f, dms[idx])",
         "delay_table(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms[idx])"),
@@ -61,6 +67,8 @@ def _pin_calls():
              pins.test_diagonal_dm_is_one_sample_per_channel_at_the_band_bottom,
              pins.test_binning_factors_follow_the_doubling_ranges,
              pins.test_decimate_sums_adjacent_samples,
+             pins.test_decimate_mean8_rounds_half_up_within_half_a_count_per_level,
+             pins.test_mean8_binned_rows_keep_the_pulse_snr_of_summed_binning,
              pins.test_binned_rows_full_rate_exact_and_flux_conserved,
              pins.test_binned_rows_gather_a_dispersed_pulse]
     calls += [lambda d=d, w=w: pins.test_brute_force_smearing_matches_analytic_curve(d, w)

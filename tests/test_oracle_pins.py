@@ -393,3 +393,39 @@ def test_realtime_op_rate_accounting_matches_thesis():
     ops = r["n_beams"] * r["samples_per_s"] * r["nchan"] * r["n_dm"]
     assert abs(ops / r["ops_per_s"] - 1) < 0.01
     assert r["samples_per_s"] == 1 / 51.2e-6
+
+
+# -------------------------------------------------------- f16 storage error
+
+@pytest.mark.parametrize("name,nsamp,rows", [
+    ("single_beam_f32", None, None),
+    ("lband_f32", 2048, [0, 1, 2048, 4094, 4095]),
+])
+def test_f16_storage_error_within_half_precision_bound(name, nsamp, rows):
+    """Storing the input in f16 (round to nearest even, unit roundoff 2^-11)
+    moves each sum by at most sum_c |f16(I) - I| <= 2^-11 sum_c |I| plus
+    2^-25 per channel for values in the subnormal range.  Both sides run
+    through the FP64 oracle, so this is the storage error alone, apart from
+    any accumulation error of a kernel; its max and 99th percentile (relative
+    to sum_c |I|) are printed for the record."""
+    wl = synth.workload(name)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    if nsamp is not None:
+        wl = synth.scaled(wl, nsamp=mx + nsamp)
+    block32, _ = synth.make_block(wl, seed=1, delays=delays)
+    block16 = block32.astype(np.float16)
+    d = delays if rows is None else delays[:, rows]
+    nout = wl.nsamp - mx
+    D32 = oracle.dedisperse(block32, d, nsamp_out=nout)
+    D16 = oracle.dedisperse(block16, d, nsamp_out=nout)
+    # f16 -> f32 widening is exact, so the oracle must read both forms alike
+    assert np.array_equal(D16, oracle.dedisperse(block16.astype(np.float32), d, nsamp_out=nout))
+    scale = oracle.dedisperse(np.abs(block32), d, nsamp_out=nout)
+    cast_err = oracle.dedisperse(np.abs(block16.astype(np.float32) - block32), d, nsamp_out=nout)
+    diff = np.abs(D16 - D32)
+    assert np.all(diff <= cast_err * (1 + 1e-12))
+    assert np.all(cast_err <= 2.0 ** -11 * scale + wl.nchan * 2.0 ** -25)
+    rel = diff / scale
+    print(f"\n{name} f16 storage: relative error max {rel.max():.3e} "
+          f"p99 {np.percentile(rel, 99):.3e}")
+    assert rel.max() > 0  # the cast does move the sums
