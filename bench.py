@@ -301,7 +301,7 @@ def run_reference(args):
     rank, world, local = dist_env()
     if rank != 0:
         return
-    if args.workload in (POST, BINNED, SUBBAND):
+    if args.workload in (POST, BINNED, BINNED8, SUBBAND):
         import oracle
         wl = synth.workload("full_block_u8")
         delays, _, nsamp_out = geometry_oracle(wl)
@@ -317,9 +317,11 @@ def run_reference(args):
                       "median_width": POST_MEDIAN_WIDTH, "boxcar_widths": POST_WIDTHS,
                       "nsigma": NSIGMA, "parallelism": "replicas1"}
             print_reference(args, value, secs, last, "f64", config)
-        elif args.workload == BINNED:
-            value, secs, last = reference_steps(args, lambda t: time_oracle_binned(wl, block, t))
-            config = {"workload": BINNED, "max_factor": BIN_MAX_FACTOR,
+        elif args.workload in (BINNED, BINNED8):
+            mode = bin_mode(args.workload)
+            value, secs, last = reference_steps(
+                args, lambda t: time_oracle_binned(wl, block, t, mode))
+            config = {"workload": args.workload, "max_factor": BIN_MAX_FACTOR, "binning": mode,
                       "parallelism": "replicas1"}
             print_reference(args, value, secs, last, "int32", config)
         else:
@@ -1130,10 +1132,15 @@ def run_subband(args):
 # --------------------------------------------------------- time binning
 
 BINNED = "binned_full_block_u8"  # full_block_u8 with downfactors past the diagonal DM
+BINNED8 = "binned8_full_block_u8"  # the same, binned series kept as 8-bit rounded means
 BIN_MAX_FACTOR = 8
 
 
-def time_oracle_binned(wl, block, seconds):
+def bin_mode(workload):
+    return "mean8" if workload == BINNED8 else "sum"
+
+
+def time_oracle_binned(wl, block, seconds, mode="sum"):
     """The binning oracle on evenly spaced trials (each at its own rate)."""
     from oracle import approx
     import oracle
@@ -1144,7 +1151,7 @@ def time_oracle_binned(wl, block, seconds):
         t0 = time.perf_counter()
         rows, fac, lens = approx.binned_dedisperse(block, wl.nchan, wl.f_top_mhz,
                                                    wl.chan_width_mhz, wl.t_samp_s, wl.dms[idx],
-                                                   BIN_MAX_FACTOR)
+                                                   BIN_MAX_FACTOR, mode=mode)
         dt = time.perf_counter() - t0
         if dt * 2 > seconds or n >= wl.ndm:
             break
@@ -1157,9 +1164,10 @@ def time_oracle_binned(wl, block, seconds):
 
 
 def run_binned(args):
-    """One step = dd_binned_execute over full_block_u8 (resident); the
-    brute-force kernel on the same block is timed beside it.  value counts
-    each trial's output samples times its downfactor (input samples covered)."""
+    """One step = dd_binned_execute over full_block_u8 (resident), binned by
+    pair sums or (binned8_full_block_u8) by 8-bit pair means; the brute-force
+    kernel on the same block is timed beside it.  value counts each trial's
+    output samples times its downfactor (input samples covered)."""
     import torch
 
     import paper_1401_8258_gb300 as dd
@@ -1169,8 +1177,9 @@ def run_binned(args):
     dev = torch.device("cuda", local)
     dd.build()
     wl = load_workload(argparse.Namespace(workload="full_block_u8", nsamp=args.nsamp))
+    mode = bin_mode(args.workload)
     b = dd.Binned(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8",
-                  BIN_MAX_FACTOR, local)
+                  BIN_MAX_FACTOR, mode=mode, device=local)
     plan = dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8", local)
     block, _ = synth.make_block(wl, args.seed + 1000 * (rank + 1), plan.delays())
     dblock = torch.from_numpy(block).to(dev)
@@ -1224,15 +1233,16 @@ def run_binned(args):
             "brute_force_adds_per_step": float(wl.nchan) * wl.ndm * n_bf}
     cpu = None
     if not args.no_cpu_baseline:
-        cpu = time_oracle_binned(wl, block, args.cpu_seconds)
+        cpu = time_oracle_binned(wl, block, args.cpu_seconds, mode)
         cpu["cpu_model"] = cpu_model()
     line = {
         "metric": METRIC, "value": covered / t_step, "unit": UNIT, "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": BINNED, "nchan": wl.nchan, "nsamp_in": wl.nsamp, "ndm": wl.ndm,
-                   "max_factor": BIN_MAX_FACTOR, "diagonal_dm": b.dm_diag,
+        "config": {"workload": args.workload, "nchan": wl.nchan, "nsamp_in": wl.nsamp,
+                   "ndm": wl.ndm, "max_factor": BIN_MAX_FACTOR, "binning": mode,
+                   "diagonal_dm": b.dm_diag,
                    "trials_per_downfactor": counts, "input_dtype": "u8",
                    "value_counts": "output samples x downfactor (input samples covered)",
                    "parallelism": "replicas1",
@@ -1260,7 +1270,7 @@ def main():
         run_post(args)
     elif args.workload == SUBBAND:
         run_subband(args)
-    elif args.workload == BINNED:
+    elif args.workload in (BINNED, BINNED8):
         run_binned(args)
     else:
         run_ours(args)

@@ -365,13 +365,15 @@ class Subband:
 
 class Binned:
     """Owner of a dd_binned handle (time-binned dedispersion past the
-    diagonal DM, include/dd_binned.h) working on torch device tensors."""
+    diagonal DM, include/dd_binned.h) working on torch device tensors.
+    mode "sum" bins by pair sums (the thesis's downfactoring), "mean8" (u8
+    input) by 8-bit pair means rounded half up."""
 
     def __init__(self, nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype, max_factor,
-                 device=0):
-        self.ndm, self.dtype = len(dms), dtype
+                 mode="sum", device=0):
+        self.ndm, self.dtype, self.mode = len(dms), dtype, mode
         self.handle = _native.dd_binned_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms,
-                                               dtype, max_factor, device)
+                                               dtype, max_factor, mode, device)
         self.dm_diag = _native.dd_binned_diagonal_dm(self.handle)
 
     def rows(self, nsamp_in):

@@ -91,7 +91,8 @@ SIGNATURES = [
     ("dd_subband_execute", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp]),
     ("dd_subband_launch_count", ctypes.c_int, [_vp, _vp]),
     # dd_binned.h
-    ("dd_binned_create", ctypes.c_int, [_vp, _i32, _f64, _f64, _f64, _vp, _i32, _i32, _i32, _i32]),
+    ("dd_binned_create", ctypes.c_int,
+     [_vp, _i32, _f64, _f64, _f64, _vp, _i32, _i32, _i32, _i32, _i32]),
     ("dd_binned_destroy", ctypes.c_int, [_vp]),
     ("dd_binned_diagonal_dm", ctypes.c_int, [_vp, _vp]),
     ("dd_binned_rows", ctypes.c_int, [_vp, _i64, _vp, _vp]),
@@ -459,14 +460,18 @@ def dd_subband_launch_count(sub) -> int:
     return int(n.value)
 
 
+BIN_MODES = {"sum": 0, "mean8": 1}  # dd_bin_mode
+
+
 def dd_binned_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype, max_factor,
-                     device=0) -> int:
+                     mode="sum", device=0) -> int:
     code = DTYPE_CODES[dtype] if isinstance(dtype, str) else int(dtype)
+    mcode = BIN_MODES[mode] if isinstance(mode, str) else int(mode)
     dms = np.ascontiguousarray(dms, dtype=np.float64)
     h = ctypes.c_void_p()
     _check(load().dd_binned_create(ctypes.addressof(h), int(nchan), float(f_top_mhz),
                                    float(chan_width_mhz), float(t_samp_s), dms.ctypes.data,
-                                   int(dms.size), code, int(max_factor), int(device)),
+                                   int(dms.size), code, int(max_factor), mcode, int(device)),
            "dd_binned_create")
     return h.value
 

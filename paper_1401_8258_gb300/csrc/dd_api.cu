@@ -408,6 +408,62 @@ extern "C" int dd_execute_pitched(dd_plan *p, const void *block, int64_t nsamp_i
   return DD_OK;
 }
 
+int execute_plans_pitched(dd_plan *const *plans, int n, const void *const *block,
+                          const int64_t *nsamp_in, const int64_t *pitch_elems, void *const *out,
+                          const int64_t *out_pitch, void *stream) {
+  if (n < 1 || !plans || !block || !nsamp_in || !pitch_elems || !out || !out_pitch)
+    return DD_ERR_ARG;
+  std::vector<int64_t> nout(n);
+  for (int i = 0; i < n; ++i) {
+    if (!plans[i] || !block[i] || !out[i]) return DD_ERR_ARG;
+    const int st = validate_execute(plans[i], nsamp_in[i], pitch_elems[i], &nout[i]);
+    if (st != DD_OK) return st;
+    if (out_pitch[i] < nout[i]) return DD_ERR_ARG;
+    if (plans[i]->device != plans[0]->device) return DD_ERR_ARG;
+  }
+  DeviceScope scope(plans[0]->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // staged u8 work by DM-tile width (64, 32, 16 trials), in the given order
+  constexpr int kWidths = 3;
+  std::vector<int> staged[kWidths];
+  for (int i = 0; i < n; ++i) {
+    dd_plan *p = plans[i];
+    if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
+      const int nd_thr = p->quad->tables.nd_thr;
+      staged[nd_thr == ddq::kNdThr ? 0 : (nd_thr == ddq::kNdThr / 2 ? 1 : 2)].push_back(i);
+    } else {
+      const int st =
+          dd_execute_pitched(p, block[i], nsamp_in[i], pitch_elems[i], out[i], out_pitch[i], stream);
+      if (st != DD_OK) return st;
+    }
+  }
+  for (int g = 0; g < kWidths; ++g) {
+    const std::vector<int> &idx = staged[g];
+    for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
+      const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
+      std::vector<ddq::Beam> beams;
+      int smem = 0;
+      for (size_t k = lo; k < hi; ++k) {
+        dd_plan *p = plans[idx[k]];
+        beams.push_back(ddk::quad_beam(p, block[idx[k]], pitch_elems[idx[k]], nout[idx[k]],
+                                       out[idx[k]], out_pitch[idx[k]], nullptr, nullptr));
+        smem = std::max(smem, static_cast<int>(p->quad->tables.smem_bytes));
+      }
+      // the first plan's work-queue head and status word serve the launch
+      dd_plan *p0 = plans[idx[lo]];
+      cudaError_t err = cudaSuccess;
+      const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
+                                            ddq::kNdThr >> g, smem, p0->sm_count,
+                                            p0->d_next_item, p0->d_error, p0->wait_timeout_ns,
+                                            p0->debug_skip_copies, s, &err);
+      if (nl < 0) return cuda_status(err);
+      p0->launches += nl;
+    }
+  }
+  return DD_OK;
+}
+
 extern "C" int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
                          dd_candidate *cands, int64_t capacity, int64_t *count, void *stream) {
   if (!p || !out || !count || capacity < 0 || (capacity > 0 && !cands)) return DD_ERR_ARG;

@@ -4,7 +4,9 @@
 // by f.  The binned series are built level by level on the device (pairs of
 // adjacent samples summed; u8 sums are exact integers held in float), the
 // full-rate trials run on the block itself, and for u8 input the float rows
-// of the binned trials are turned back into int32 in place (exact).
+// of the binned trials are turned back into int32 in place (exact).  In the
+// 8-bit mode the levels hold rounded pair means as bytes instead, and every
+// downfactor runs through the 8-bit kernel.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -15,6 +17,7 @@
 
 #include "dd.h"
 #include "dd_binned.h"
+#include "dd_internal.h"
 
 namespace {
 
@@ -31,11 +34,11 @@ struct Range {
 }  // namespace
 
 struct dd_binned {
-  int32_t device = 0, nchan = 0, ndm = 0, dtype = 0, max_factor = 1;
+  int32_t device = 0, nchan = 0, ndm = 0, dtype = 0, max_factor = 1, mode = DD_BIN_SUM;
   double dm_diag = 0.0;
   std::vector<int32_t> factor;  // per trial
   std::vector<Range> ranges;    // ascending factor
-  void *d_bins = nullptr;       // binned series, levels 1.. back to back (float)
+  void *d_bins = nullptr;       // binned series, levels 1.. back to back (float, or u8)
   size_t bins_bytes = 0;
   int64_t launches = 0;
 };
@@ -65,6 +68,56 @@ __global__ void bin_pairs(const T *__restrict__ in, int64_t in_pitch, int32_t nc
   }
 }
 
+// out[c][t] = (in[c][2t] + in[c][2t+1] + 1) >> 1 for t < n_out: the pair's
+// mean rounded half up, which stays in 0..255.
+__global__ void bin_mean_u8(const uint8_t *__restrict__ in, int64_t in_pitch, int32_t nchan,
+                            int64_t n_out, uint8_t *__restrict__ out, int64_t out_pitch) {
+  for (int64_t c = blockIdx.y; c < nchan; c += gridDim.y) {
+    const uint8_t *p = in + c * in_pitch;
+    uint8_t *q = out + c * out_pitch;
+    for (int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; t < n_out;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      const uint32_t a = p[2 * t], b = p[2 * t + 1];
+      q[t] = static_cast<uint8_t>((a + b + 1u) >> 1);
+    }
+  }
+}
+
+// The same with 16-byte loads: thread v of row c makes outputs 8v .. 8v+7
+// from input bytes 16v .. 16v+15; thread nvec makes the row's last n_out % 8
+// outputs one by one.  Rows of `in` and `out` start on 16-byte boundaries.
+// In each 32-bit word the even and odd bytes are added in 16-bit lanes
+// (at most 511), halved, and the two results of a pair of words packed.
+__global__ void bin_mean_u8_vec(const uint8_t *__restrict__ in, int64_t in_pitch, int32_t nchan,
+                                int64_t n_out, uint8_t *__restrict__ out, int64_t out_pitch) {
+  const int64_t nvec = n_out / 8;
+  for (int64_t c = blockIdx.y; c < nchan; c += gridDim.y) {
+    const uint8_t *p = in + c * in_pitch;
+    uint8_t *q = out + c * out_pitch;
+    for (int64_t v = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; v <= nvec;
+         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+      if (v < nvec) {
+        const uint4 w = *reinterpret_cast<const uint4 *>(p + 16 * v);
+        const uint32_t x[4] = {w.x, w.y, w.z, w.w};
+        uint32_t m[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+          m[i] = (((x[i] & 0x00ff00ffu) + ((x[i] >> 8) & 0x00ff00ffu) + 0x00010001u) >> 1) &
+                 0x00ff00ffu;
+        uint2 r;
+        r.x = __byte_perm(m[0], m[1], 0x6420);
+        r.y = __byte_perm(m[2], m[3], 0x6420);
+        *reinterpret_cast<uint2 *>(q + 8 * v) = r;
+      } else {
+        for (int64_t t = 8 * nvec; t < n_out; ++t) {
+          const uint32_t a = p[2 * t], b = p[2 * t + 1];
+          q[t] = static_cast<uint8_t>((a + b + 1u) >> 1);
+        }
+      }
+    }
+  }
+}
+
 // In-place float -> int32 over rows [nrows][pitch] (first ncols of each);
 // the values are integers below 2^24.
 __global__ void rows_to_int(float *p, int64_t nrows, int64_t ncols, int64_t pitch) {
@@ -87,9 +140,13 @@ int level_of(int32_t f) {
   return k;
 }
 
-// Length and 16-byte-padded pitch of binning level k (k >= 1).
+// Length and 16-byte-padded pitch (in elements of esize bytes) of binning
+// level k (k >= 1).
 inline int64_t level_len(int64_t nsamp_in, int k) { return nsamp_in >> k; }
-inline int64_t level_pitch(int64_t nsamp_in, int k) { return (level_len(nsamp_in, k) + 3) / 4 * 4; }
+inline int64_t level_pitch(int64_t nsamp_in, int k, int esize) {
+  const int64_t per = 16 / esize;
+  return (level_len(nsamp_in, k) + per - 1) / per * per;
+}
 
 void destroy(dd_binned *b) {
   for (Range &r : b->ranges) dd_plan_destroy(r.plan);
@@ -108,10 +165,12 @@ void destroy(dd_binned *b) {
 extern "C" int dd_binned_create(dd_binned **out, int32_t nchan, double f_top_mhz,
                                 double chan_width_mhz, double t_samp_s, const double *dm_list,
                                 int32_t ndm, int32_t in_dtype, int32_t max_factor,
-                                int32_t device) {
+                                int32_t mode, int32_t device) {
   if (!out) return DD_ERR_ARG;
   *out = nullptr;
   if (in_dtype != DD_U8 && in_dtype != DD_F16 && in_dtype != DD_F32) return DD_ERR_DTYPE;
+  if (mode != DD_BIN_SUM && mode != DD_BIN_MEAN_U8) return DD_ERR_ARG;
+  if (mode == DD_BIN_MEAN_U8 && in_dtype != DD_U8) return DD_ERR_DTYPE;
   if (nchan < 1 || ndm < 1 || !dm_list || device < 0 || !(chan_width_mhz > 0) ||
       !(t_samp_s > 0))
     return DD_ERR_ARG;
@@ -119,7 +178,8 @@ extern "C" int dd_binned_create(dd_binned **out, int32_t nchan, double f_top_mhz
     return DD_ERR_ARG;
   for (int32_t d = 1; d < ndm; ++d)
     if (!(dm_list[d] >= dm_list[d - 1])) return DD_ERR_ARG;
-  if (in_dtype == DD_U8 && static_cast<int64_t>(nchan) * 255 * max_factor >= (1 << 24))
+  if (mode == DD_BIN_SUM && in_dtype == DD_U8 &&
+      static_cast<int64_t>(nchan) * 255 * max_factor >= (1 << 24))
     return DD_ERR_RANGE;
   dd_binned *b = new (std::nothrow) dd_binned();
   if (!b) return DD_ERR_OOM;
@@ -128,6 +188,7 @@ extern "C" int dd_binned_create(dd_binned **out, int32_t nchan, double f_top_mhz
   b->ndm = ndm;
   b->dtype = in_dtype;
   b->max_factor = max_factor;
+  b->mode = mode;
   const double f_bot = f_top_mhz - (nchan - 1) * chan_width_mhz;
   b->dm_diag = t_samp_s * (f_bot * f_bot * f_bot) / (2.0 * kDispersion * chan_width_mhz);
   int st = DD_OK;
@@ -147,8 +208,9 @@ extern "C" int dd_binned_create(dd_binned **out, int32_t nchan, double f_top_mhz
       b->ranges.push_back(r);
     }
     for (Range &r : b->ranges) {
+      const int32_t level_dtype = mode == DD_BIN_MEAN_U8 ? DD_U8 : DD_F32;
       st = dd_plan_create(&r.plan, nchan, f_top_mhz, chan_width_mhz, t_samp_s * r.factor,
-                          dm_list + r.d0, r.n, r.factor == 1 ? in_dtype : DD_F32, device);
+                          dm_list + r.d0, r.n, r.factor == 1 ? in_dtype : level_dtype, device);
       if (st != DD_OK) break;
       dd_plan_max_delay(r.plan, &r.maxshift);
     }
@@ -211,10 +273,13 @@ extern "C" int dd_binned_execute(dd_binned *b, const void *block, int64_t nsamp_
     longest = std::max(longest, n);
   }
   if (out_pitch < longest) return DD_ERR_ARG;
+  const bool mean8 = b->mode == DD_BIN_MEAN_U8;
+  const int es = mean8 ? 1 : 4;  // bytes per binned sample
   const int top = level_of(b->ranges.back().factor);
-  // workspace: levels 1 .. top back to back
+  // workspace: levels 1 .. top back to back, each a multiple of 16 bytes
   size_t need = 0;
-  for (int k = 1; k <= top; ++k) need += static_cast<size_t>(b->nchan) * level_pitch(nsamp_in, k) * 4;
+  for (int k = 1; k <= top; ++k)
+    need += static_cast<size_t>(b->nchan) * level_pitch(nsamp_in, k, es) * es;
   int prev = 0;
   if (cudaGetDevice(&prev) != cudaSuccess || cudaSetDevice(b->device) != cudaSuccess)
     return DD_ERR_CUDA;
@@ -231,51 +296,84 @@ extern "C" int dd_binned_execute(dd_binned *b, const void *block, int64_t nsamp_
     b->bins_bytes = need;
   }
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
-  float *level[kMaxLevels] = {};
+  char *level[kMaxLevels] = {};
   {
-    float *p = static_cast<float *>(b->d_bins);
+    char *p = static_cast<char *>(b->d_bins);
     for (int k = 1; k <= top; ++k) {
       level[k] = p;
-      p += static_cast<size_t>(b->nchan) * level_pitch(nsamp_in, k);
+      p += static_cast<size_t>(b->nchan) * level_pitch(nsamp_in, k, es) * es;
     }
   }
   // binned series, level by level
   for (int k = 1; k <= top; ++k) {
     const int64_t n = level_len(nsamp_in, k);
-    const int64_t np = level_pitch(nsamp_in, k);
-    const unsigned g = grid_for(static_cast<int64_t>(b->nchan) * n);
-    if (k > 1) {
-      bin_pairs<float><<<g, kThreads, 0, st>>>(level[k - 1], level_pitch(nsamp_in, k - 1),
-                                               b->nchan, n, level[k], np);
-    } else if (b->dtype == DD_U8) {
-      bin_pairs<uint8_t><<<g, kThreads, 0, st>>>(static_cast<const uint8_t *>(block), pitch_elems,
-                                                 b->nchan, n, level[k], np);
-    } else if (b->dtype == DD_F16) {
-      bin_pairs<__half><<<g, kThreads, 0, st>>>(static_cast<const __half *>(block), pitch_elems,
-                                                b->nchan, n, level[k], np);
+    const int64_t np = level_pitch(nsamp_in, k, es);
+    if (mean8) {
+      const uint8_t *src = k > 1 ? reinterpret_cast<const uint8_t *>(level[k - 1])
+                                 : static_cast<const uint8_t *>(block);
+      const int64_t sp = k > 1 ? level_pitch(nsamp_in, k - 1, es) : pitch_elems;
+      uint8_t *dst = reinterpret_cast<uint8_t *>(level[k]);
+      const unsigned gy = static_cast<unsigned>(std::min<int32_t>(b->nchan, 65535));
+      if ((reinterpret_cast<uintptr_t>(src) & 15) == 0 && (sp & 15) == 0) {
+        const int64_t nvec = n / 8 + 1;  // the last thread of a row takes the ragged end
+        const dim3 g(static_cast<unsigned>(std::min<int64_t>((nvec + kThreads - 1) / kThreads, 64)),
+                     gy);
+        bin_mean_u8_vec<<<g, kThreads, 0, st>>>(src, sp, b->nchan, n, dst, np);
+      } else {
+        const dim3 g(static_cast<unsigned>(std::min<int64_t>((n + kThreads - 1) / kThreads, 64)),
+                     gy);
+        bin_mean_u8<<<g, kThreads, 0, st>>>(src, sp, b->nchan, n, dst, np);
+      }
     } else {
-      bin_pairs<float><<<g, kThreads, 0, st>>>(static_cast<const float *>(block), pitch_elems,
-                                               b->nchan, n, level[k], np);
+      float *dst = reinterpret_cast<float *>(level[k]);
+      const unsigned g = grid_for(static_cast<int64_t>(b->nchan) * n);
+      if (k > 1) {
+        bin_pairs<float><<<g, kThreads, 0, st>>>(reinterpret_cast<const float *>(level[k - 1]),
+                                                 level_pitch(nsamp_in, k - 1, es), b->nchan, n,
+                                                 dst, np);
+      } else if (b->dtype == DD_U8) {
+        bin_pairs<uint8_t><<<g, kThreads, 0, st>>>(static_cast<const uint8_t *>(block),
+                                                   pitch_elems, b->nchan, n, dst, np);
+      } else if (b->dtype == DD_F16) {
+        bin_pairs<__half><<<g, kThreads, 0, st>>>(static_cast<const __half *>(block),
+                                                  pitch_elems, b->nchan, n, dst, np);
+      } else {
+        bin_pairs<float><<<g, kThreads, 0, st>>>(static_cast<const float *>(block), pitch_elems,
+                                                 b->nchan, n, dst, np);
+      }
     }
     ++b->launches;
   }
-  for (const Range &r : b->ranges) {
-    char *orow = static_cast<char *>(out) + static_cast<size_t>(r.d0) * out_pitch * 4;
-    const int64_t n_out = nsamp_in / r.factor - r.maxshift;
-    int rc;
+  // every downfactor's plan at once: the staged 8-bit ones share persistent
+  // launches (all of them in the 8-bit mode)
+  const int nr = static_cast<int>(b->ranges.size());
+  std::vector<dd_plan *> plans(nr);
+  std::vector<const void *> src(nr);
+  std::vector<void *> dst(nr);
+  std::vector<int64_t> len(nr), pitch(nr), opitch(nr, out_pitch);
+  for (int i = 0; i < nr; ++i) {
+    const Range &r = b->ranges[i];
+    plans[i] = r.plan;
+    dst[i] = static_cast<char *>(out) + static_cast<size_t>(r.d0) * out_pitch * 4;
     if (r.factor == 1) {
-      rc = dd_execute_pitched(r.plan, block, nsamp_in, pitch_elems, orow, out_pitch, stream);
+      src[i] = block, len[i] = nsamp_in, pitch[i] = pitch_elems;
     } else {
       const int k = level_of(r.factor);
-      rc = dd_execute_pitched(r.plan, level[k], level_len(nsamp_in, k), level_pitch(nsamp_in, k),
-                              orow, out_pitch, stream);
-      if (rc == DD_OK && b->dtype == DD_U8) {
-        rows_to_int<<<grid_for(static_cast<int64_t>(r.n) * n_out), kThreads, 0, st>>>(
-            reinterpret_cast<float *>(orow), r.n, n_out, out_pitch);
-        ++b->launches;
-      }
+      src[i] = level[k], len[i] = level_len(nsamp_in, k), pitch[i] = level_pitch(nsamp_in, k, es);
     }
-    if (rc != DD_OK) return rc;
+  }
+  const int rc = execute_plans_pitched(plans.data(), nr, src.data(), len.data(), pitch.data(),
+                                       dst.data(), opitch.data(), stream);
+  if (rc != DD_OK) return rc;
+  if (b->dtype == DD_U8 && !mean8) {
+    for (int i = 0; i < nr; ++i) {
+      const Range &r = b->ranges[i];
+      if (r.factor == 1) continue;
+      const int64_t n_out = nsamp_in / r.factor - r.maxshift;
+      rows_to_int<<<grid_for(static_cast<int64_t>(r.n) * n_out), kThreads, 0, st>>>(
+          static_cast<float *>(dst[i]), r.n, n_out, out_pitch);
+      ++b->launches;
+    }
   }
   return cudaGetLastError() == cudaSuccess ? DD_OK : DD_ERR_CUDA;
 }

@@ -90,7 +90,18 @@ struct dd_plan {
   uint64_t ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
 };
 
+// dd_execute_pitched for n plans on one device at once, on `stream`: the
+// staged u8 work of plans with the same DM-tile width shares persistent
+// launches (no row statistics), the rest runs as dd_execute_pitched would.
+// Arguments per plan as for dd_execute_pitched; a timeout of a shared launch
+// is recorded in the status word of its first plan.  Queues only.
+int execute_plans_pitched(dd_plan *const *plans, int n, const void *const *block,
+                          const int64_t *nsamp_in, const int64_t *pitch_elems, void *const *out,
+                          const int64_t *out_pitch, void *stream);
+
 namespace ddk {
+
+// Element size of a dd_dtype.namespace ddk {
 
 // Element size of a dd_dtype.
 inline int elem_size(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F16 ? 2 : 4); }

@@ -75,12 +75,19 @@ def test_subband_and_binned_creation_errors(lib):
               0) == DD_ERR_RANGE
     bc = lib.dd_binned_create
     rev = dms[::-1].copy()
-    assert bc(ctypes.addressof(h), 64, 416.0, 0.25, 1e-4, rev.ctypes.data, 16, 0, 4, 0) == DD_ERR_ARG
+    assert bc(ctypes.addressof(h), 64, 416.0, 0.25, 1e-4, rev.ctypes.data, 16, 0, 4, 0,
+              0) == DD_ERR_ARG
     for mf in (0, 3, 6, 128):
-        assert bc(ctypes.addressof(h), 64, 416.0, 0.25, 1e-4, dms.ctypes.data, 16, 0, mf,
+        assert bc(ctypes.addressof(h), 64, 416.0, 0.25, 1e-4, dms.ctypes.data, 16, 0, mf, 0,
                   0) == DD_ERR_ARG
-    assert bc(ctypes.addressof(h), 4096, 1500.0, 0.07, 64e-6, dms.ctypes.data, 16, 0, 64,
+    assert bc(ctypes.addressof(h), 4096, 1500.0, 0.07, 64e-6, dms.ctypes.data, 16, 0, 64, 0,
               0) == DD_ERR_RANGE
+    for mode in (-1, 2):  # no such binning mode
+        assert bc(ctypes.addressof(h), 64, 416.0, 0.25, 1e-4, dms.ctypes.data, 16, 0, 4, mode,
+                  0) == DD_ERR_ARG
+    for dtype in (1, 2):  # 8-bit means need u8 input
+        assert bc(ctypes.addressof(h), 64, 416.0, 0.25, 1e-4, dms.ctypes.data, 16, dtype, 4, 1,
+                  0) == DD_ERR_DTYPE
     assert h.value is None  # nothing was created
 
 
