@@ -243,6 +243,37 @@ int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp_in, int64_
                     float nsigma, dd_candidate *host_cands, int64_t capacity, int64_t *count,
                     void *stream);
 
+/* Host pipes: dd_process_host over a sequence of host blocks with the copy
+ * of each block overlapped with the previous block's dedispersion (the
+ * thesis's double-buffered input, filled while the GPU works on the previous
+ * buffer, Sec. 4.2).  A pipe belongs to one plan and
+ * takes blocks of one shape ([nchan][pitch_elems] host memory, the first
+ * nsamp_in samples of each row used; pinned memory lets the copies run
+ * asynchronously) and owns two device input buffers, one output and a
+ * candidate buffer of `capacity` slots, and its own copy stream.
+ *
+ * dd_host_pipe_push queues the copy of `host_block` on the copy stream, then,
+ * if an earlier block's result is still due, runs dd_run with `nsigma` on
+ * that block on `stream` while the new copy is in flight and copies its
+ * candidates to `host_cands` (host, `capacity` slots): *has_result = 1 and
+ * *count = its total; otherwise *has_result = 0.  dd_host_pipe_flush returns
+ * the last pushed block's result the same way (*has_result = 0 when none is
+ * due).  So push k returns block k-1's result, and one flush after the last
+ * push returns the last block's.  host_block must stay unchanged until the
+ * next push or flush returns.  Each result equals dd_process_host of its
+ * block; status codes as for dd_process_host (DD_ERR_OVERFLOW when the total
+ * exceeds capacity; the first capacity candidates are still returned).
+ * Synchronises `stream` before returning.  Not thread-safe; the plan must
+ * not be used elsewhere while the pipe runs, and must outlive it. */
+typedef struct dd_host_pipe dd_host_pipe;
+int dd_host_pipe_create(dd_host_pipe **out, dd_plan *p, int64_t nsamp_in, int64_t pitch_elems,
+                        float nsigma, int64_t capacity);
+int dd_host_pipe_destroy(dd_host_pipe *q);
+int dd_host_pipe_push(dd_host_pipe *q, const void *host_block, dd_candidate *host_cands,
+                      int64_t *count, int32_t *has_result, void *stream);
+int dd_host_pipe_flush(dd_host_pipe *q, dd_candidate *host_cands, int64_t *count,
+                       int32_t *has_result, void *stream);
+
 /* Number of kernel launches queued by this plan since creation (all entry
  * points); used to account for device work. */
 int dd_plan_launch_count(const dd_plan *p, int64_t *launches);

@@ -30,7 +30,7 @@ __all__ = [
     "dd_get_stats", "dd_sync", "dd_process_host", "dd_plan_launch_count", "dd_status_string",
     "dd_run", "Batch", "dd_batch_create", "dd_batch_destroy", "dd_batch_run", "Stream",
     "push_streams", "median_filter", "detrend", "boxcar_detect", "PULSE_DTYPE", "Subband",
-    "Binned",
+    "Binned", "HostPipe",
 ]
 
 _TORCH_IN = {"u8": "uint8", "f16": "float16", "f32": "float32"}
@@ -348,6 +348,50 @@ class Subband:
     def close(self):
         if self.handle:
             _native.dd_subband_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class HostPipe:
+    """Owner of a dd_host_pipe handle: host blocks of one shape through a
+    plan, each block's copy overlapped with the previous block's work
+    (include/dd.h).  ``push`` returns the previous block's candidates,
+    ``flush`` the last block's; both return None when no result is due."""
+
+    def __init__(self, plan, nsamp_in, pitch_elems, nsigma, capacity=1 << 16):
+        self.plan, self.capacity = plan, int(capacity)
+        self.handle = _native.dd_host_pipe_create(plan.handle, nsamp_in, pitch_elems, nsigma,
+                                                  capacity)
+        self._cands = np.zeros(max(1, self.capacity), dtype=CANDIDATE_DTYPE)
+
+    def _result(self, st, total, has):
+        if not has:
+            return None
+        return self._cands[:min(total, self.capacity)].copy(), total
+
+    def push(self, host_block, stream=None):
+        """host_block: host numpy array or (pinned) torch tensor [nchan][pitch],
+        unchanged until the next push or flush returns."""
+        return self._result(*_native.dd_host_pipe_push(self.handle, host_block, self._cands,
+                                                       stream))
+
+    def flush(self, stream=None):
+        return self._result(*_native.dd_host_pipe_flush(self.handle, self._cands, stream))
+
+    def close(self):
+        if self.handle:
+            _native.dd_host_pipe_destroy(self.handle)
             self.handle = None
 
     def __enter__(self):

@@ -62,6 +62,10 @@ SIGNATURES = [
     ("dd_get_stats", ctypes.c_int, [_vp, _vp, _vp]),
     ("dd_sync", ctypes.c_int, [_vp, _vp]),
     ("dd_process_host", ctypes.c_int, [_vp, _vp, _i64, _i64, _f32, _vp, _i64, _vp, _vp]),
+    ("dd_host_pipe_create", ctypes.c_int, [_vp, _vp, _i64, _i64, _f32, _i64]),
+    ("dd_host_pipe_destroy", ctypes.c_int, [_vp]),
+    ("dd_host_pipe_push", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp, _vp]),
+    ("dd_host_pipe_flush", ctypes.c_int, [_vp, _vp, _vp, _vp, _vp]),
     ("dd_plan_launch_count", ctypes.c_int, [_vp, _vp]),
     ("dd_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("dd_measure_add_peak", ctypes.c_int, [_i32, _i32, _vp, _vp]),
@@ -330,6 +334,35 @@ def dd_process_host(plan, host_block, nsamp_in, pitch_elems, nsigma, host_cands,
                                 ctypes.addressof(cnt), _stream(stream))
     _check(st, "dd_process_host", allow=(DD_ERR_OVERFLOW,))
     return st, int(cnt.value)
+
+
+def dd_host_pipe_create(plan, nsamp_in, pitch_elems, nsigma, capacity) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dd_host_pipe_create(ctypes.addressof(h), plan, int(nsamp_in), int(pitch_elems),
+                                      float(nsigma), int(capacity)), "dd_host_pipe_create")
+    return h.value
+
+
+def dd_host_pipe_destroy(pipe) -> None:
+    _check(load().dd_host_pipe_destroy(pipe), "dd_host_pipe_destroy")
+
+
+def dd_host_pipe_push(pipe, host_block, host_cands, stream=None) -> tuple[int, int, bool]:
+    """(status, count, has_result) of the block pushed before this one."""
+    cnt, has = ctypes.c_int64(0), ctypes.c_int32(0)
+    st = load().dd_host_pipe_push(pipe, _addr(host_block), _addr(host_cands),
+                                  ctypes.addressof(cnt), ctypes.addressof(has), _stream(stream))
+    _check(st, "dd_host_pipe_push", allow=(DD_ERR_OVERFLOW,))
+    return st, int(cnt.value), bool(has.value)
+
+
+def dd_host_pipe_flush(pipe, host_cands, stream=None) -> tuple[int, int, bool]:
+    """(status, count, has_result) of the last pushed block."""
+    cnt, has = ctypes.c_int64(0), ctypes.c_int32(0)
+    st = load().dd_host_pipe_flush(pipe, _addr(host_cands), ctypes.addressof(cnt),
+                                   ctypes.addressof(has), _stream(stream))
+    _check(st, "dd_host_pipe_flush", allow=(DD_ERR_OVERFLOW,))
+    return st, int(cnt.value), bool(has.value)
 
 
 def dd_measure_add_peak(kind, device=0) -> tuple[float, float]:

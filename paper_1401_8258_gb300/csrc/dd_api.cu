@@ -1080,6 +1080,137 @@ extern "C" int dd_process_host(dd_plan *p, const void *host_block, int64_t nsamp
   return dst;
 }
 
+struct dd_host_pipe {
+  dd_plan *plan = nullptr;
+  int64_t nsamp_in = 0, pitch = 0, nsamp_out = 0, capacity = 0;
+  float nsigma = 0.f;
+  size_t in_bytes = 0;
+  void *buf[2] = {nullptr, nullptr};  // device input buffers, block k in buf[k & 1]
+  void *d_out = nullptr;
+  dd_candidate *d_cands = nullptr;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  int64_t pushed = 0;  // blocks queued
+  int64_t done = 0;    // blocks whose result was returned
+};
+
+namespace {
+
+void free_pipe(dd_host_pipe *q) {
+  if (!q) return;
+  for (int k = 0; k < 2; ++k) {
+    free_device(q->buf[k]);
+    if (q->copied[k]) cudaEventDestroy(q->copied[k]);
+  }
+  free_device(q->d_out);
+  free_device(q->d_cands);
+  if (q->copy) cudaStreamDestroy(q->copy);
+  delete q;
+}
+
+// dd_run on block m (already queued for copy) on `stream`, candidates back.
+int pipe_result(dd_host_pipe *q, int64_t m, dd_candidate *host_cands, int64_t *count,
+                void *stream) {
+  const cudaStream_t s = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamWaitEvent(s, q->copied[m & 1], 0);
+  if (e != cudaSuccess) return cuda_status(e);
+  const int st = dd_run(q->plan, q->buf[m & 1], q->nsamp_in, q->pitch, q->d_out, q->nsigma,
+                        q->d_cands, q->capacity, count, stream, nullptr);
+  q->done = m + 1;
+  if (st != DD_OK && st != DD_ERR_OVERFLOW) return st;
+  const int64_t ncopy = *count < q->capacity ? *count : q->capacity;
+  if (ncopy > 0) {
+    e = cudaMemcpyAsync(host_cands, q->d_cands, sizeof(dd_candidate) * ncopy,
+                        cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_status(e);
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" int dd_host_pipe_create(dd_host_pipe **out, dd_plan *p, int64_t nsamp_in,
+                                   int64_t pitch_elems, float nsigma, int64_t capacity) {
+  if (!out) return DD_ERR_ARG;
+  *out = nullptr;
+  if (!p || capacity < 0 || !std::isfinite(nsigma)) return DD_ERR_ARG;
+  int64_t nsamp_out = 0;
+  const int st = validate_execute(p, nsamp_in, pitch_elems, &nsamp_out);
+  if (st != DD_OK) return st;
+  dd_host_pipe *q = new (std::nothrow) dd_host_pipe();
+  if (!q) return DD_ERR_OOM;
+  q->plan = p;
+  q->nsamp_in = nsamp_in;
+  q->pitch = pitch_elems;
+  q->nsamp_out = nsamp_out;
+  q->capacity = capacity;
+  q->nsigma = nsigma;
+  q->in_bytes = static_cast<size_t>(p->nchan) * pitch_elems * ddk::elem_size(p->dtype);
+  DeviceScope scope(p->device);
+  if (!scope.ok()) {
+    delete q;
+    return DD_ERR_CUDA;
+  }
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+    e = cudaMalloc(&q->buf[k], q->in_bytes);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&q->copied[k], cudaEventDisableTiming);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_out, static_cast<size_t>(p->ndm) * nsamp_out * 4);
+  if (e == cudaSuccess && capacity > 0)
+    e = cudaMalloc(reinterpret_cast<void **>(&q->d_cands), sizeof(dd_candidate) * capacity);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&q->copy, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    free_pipe(q);
+    return e == cudaErrorMemoryAllocation ? DD_ERR_OOM : cuda_status(e);
+  }
+  *out = q;
+  return DD_OK;
+}
+
+extern "C" int dd_host_pipe_destroy(dd_host_pipe *q) {
+  if (!q) return DD_OK;
+  DeviceScope scope(q->plan->device);
+  if (q->copy) cudaStreamSynchronize(q->copy);  // no copy may still target the buffers
+  free_pipe(q);
+  return DD_OK;
+}
+
+extern "C" int dd_host_pipe_push(dd_host_pipe *q, const void *host_block,
+                                 dd_candidate *host_cands, int64_t *count, int32_t *has_result,
+                                 void *stream) {
+  if (!q || !host_block || !count || !has_result || (q->capacity > 0 && !host_cands))
+    return DD_ERR_ARG;
+  *count = 0;
+  *has_result = 0;
+  DeviceScope scope(q->plan->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  // block k goes to buf[k & 1]: its last user, block k - 2, finished its
+  // dd_run (which synchronises) before push k - 1 returned
+  const int64_t k = q->pushed;
+  cudaError_t e = cudaMemcpyAsync(q->buf[k & 1], host_block, q->in_bytes,
+                                  cudaMemcpyHostToDevice, q->copy);
+  if (e == cudaSuccess) e = cudaEventRecord(q->copied[k & 1], q->copy);
+  if (e != cudaSuccess) return cuda_status(e);
+  q->pushed = k + 1;
+  if (q->done >= k) return DD_OK;  // nothing due: the first push, or right after a flush
+  *has_result = 1;
+  return pipe_result(q, k - 1, host_cands, count, stream);
+}
+
+extern "C" int dd_host_pipe_flush(dd_host_pipe *q, dd_candidate *host_cands, int64_t *count,
+                                  int32_t *has_result, void *stream) {
+  if (!q || !count || !has_result || (q->capacity > 0 && !host_cands)) return DD_ERR_ARG;
+  *count = 0;
+  *has_result = 0;
+  if (q->done >= q->pushed) return DD_OK;
+  DeviceScope scope(q->plan->device);
+  if (!scope.ok()) return DD_ERR_CUDA;
+  *has_result = 1;
+  return pipe_result(q, q->pushed - 1, host_cands, count, stream);
+}
+
 extern "C" int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_cta,
                                 float *ms_per_launch) {
   if (!p || !dms_per_cta) return DD_ERR_ARG;

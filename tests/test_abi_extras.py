@@ -99,3 +99,19 @@ def test_plan_from_delays_rejects_bad_tables(lib):
     assert lib.dd_plan_create_from_delays(ctypes.addressof(h), 2, 2, big.ctypes.data, 0, 0) == DD_ERR_ARG
     assert lib.dd_plan_create_from_delays(ctypes.addressof(h), 2, 2, None, 0, 0) == DD_ERR_ARG
     assert lib.dd_plan_create_from_delays(ctypes.addressof(h), 2, 2, bad.ctypes.data, 7, 0) == DD_ERR_DTYPE
+
+
+def test_host_pipe_argument_errors(lib):
+    """dd_host_pipe_*: null handles and outputs are refused before any device
+    work; destroying a null pipe is a no-op."""
+    h = ctypes.c_void_p()
+    cnt, has = ctypes.c_int64(0), ctypes.c_int32(0)
+    assert lib.dd_host_pipe_create(None, FAKE, 100, 100, ctypes.c_float(5.0), 10) == DD_ERR_ARG
+    assert lib.dd_host_pipe_create(ctypes.addressof(h), None, 100, 100, ctypes.c_float(5.0),
+                                   10) == DD_ERR_ARG
+    assert h.value is None
+    assert lib.dd_host_pipe_push(None, FAKE, FAKE, ctypes.addressof(cnt), ctypes.addressof(has),
+                                 None) == DD_ERR_ARG
+    assert lib.dd_host_pipe_flush(None, FAKE, ctypes.addressof(cnt), ctypes.addressof(has),
+                                  None) == DD_ERR_ARG
+    assert lib.dd_host_pipe_destroy(None) == 0

@@ -65,7 +65,10 @@ def test_float_kernel_time_tile_limit(extra):
     block = synth.random_block(np.random.default_rng(21), nchan, nsamp, "f32", pitch=pitch)
     with dd.Plan(nchan, f_top, df, ts, dms, "f32") as plan:
         assert plan.maxshift == mx and plan.nsamp_out(nsamp) == n_out
-        out = plan.execute(torch.from_numpy(block).to(DEV), nsamp_in=nsamp)
+        dblock = torch.from_numpy(block).to(DEV)
+        # the staged tables exist, so the time-tile count alone picks the kernel
+        assert dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)["staged"]
+        out = plan.execute(dblock, nsamp_in=nsamp)
         got = out.cpu().numpy()
     assert got.shape == (4, n_out)
     check_ranges(block, delays, got, n_out, "f32")

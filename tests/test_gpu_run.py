@@ -192,3 +192,36 @@ def test_autotune_keeps_results_identical(name, nchan, ndm, dtype):
         after = plan.run(dblock, 4.0, nsamp_in=wl.nsamp)
     assert torch.equal(before[0], after[0])
     assert before[2] == after[2] and np.array_equal(before[1], after[1])
+
+
+@pytest.mark.parametrize("dtype,capacity", [("u8", 1 << 14), ("f32", 1 << 14), ("u8", 5)])
+def test_host_pipe_results_equal_process_host_per_block(dtype, capacity):
+    """dd_host_pipe: push k returns block k-1's candidates, flush the last
+    block's; each equals dd_process_host of that block (candidates, total,
+    statistics), also after a flush and with a capacity below the total."""
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=256, nsamp=24000, ndm=160)
+    wl.dtype = dtype
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    blocks = [torch.from_numpy(synth.make_block(wl, seed=s, delays=delays)[0]).pin_memory()
+              for s in (1, 2, 3)]
+    nsigma = 4.0
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, dtype) as plan:
+        want = []
+        host = np.zeros(max(capacity, 1), dtype=dd.CANDIDATE_DTYPE)
+        for b in blocks:
+            st, total = dd.dd_process_host(plan.handle, b, wl.nsamp, wl.nsamp, nsigma, host,
+                                           capacity)
+            want.append((host[:min(total, capacity)].copy(), total, plan.stats()))
+        assert want[0][1] > capacity or capacity > 5
+        with dd.HostPipe(plan, wl.nsamp, wl.nsamp, nsigma, capacity) as pipe:
+            got = [pipe.push(blocks[0])]
+            got.append((pipe.push(blocks[1]), plan.stats()))
+            got.append((pipe.push(blocks[2]), plan.stats()))
+            got.append((pipe.flush(), plan.stats()))
+            assert got[0] is None and pipe.flush() is None
+            assert pipe.push(blocks[0]) is None  # the previous result went out with the flush
+            got.append((pipe.flush(), plan.stats()))
+    for (res, stats), (c, total, wstats) in zip(got[1:], want + [want[0]]):
+        assert res is not None and res[1] == total
+        assert np.array_equal(res[0], c)
+        assert np.array_equal(stats[0], wstats[0]) and np.array_equal(stats[1], wstats[1])
