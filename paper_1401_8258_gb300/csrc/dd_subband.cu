@@ -77,7 +77,7 @@ template <> __device__ __forceinline__ int32_t store_as<float, int32_t>(float v)
 // (time tiles, ceil(ntr / 16), ngroups).  Dynamic shared memory:
 // min(tab_ch, 64) rows of kGroupTile + span elements.
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(kGroupThreads)
+__global__ void __launch_bounds__(kGroupThreads, 2)  // two CTAs per SM: at most 128 registers
 dd_grouped(const TI *__restrict__ in, int64_t pitch, int64_t ig, const int32_t *__restrict__ tab,
            int tab_ch, int nch_total, int ntr, int ntr_last, int span, int64_t n_valid,
            TO *__restrict__ out, int64_t og, int64_t oj, int64_t nsamp_out) {
@@ -114,12 +114,14 @@ dd_grouped(const TI *__restrict__ in, int64_t pitch, int64_t ig, const int32_t *
       }
     }
     __syncthreads();
-    // windows: channel c, samples t0 + lo_c .. t0 + lo_c + W - 1; a thread
-    // issues the loads of 8 channels x 3 samples before their shared-memory
-    // stores (24 loads in flight), then covers any rest of a wide window
+    // windows: channel c, samples t0 + lo_c .. t0 + lo_c + W - 1, in blocks
+    // of 8 channels; a thread issues the loads of a block (8 channels x 3
+    // samples in flight) before adding the previous block from shared memory,
+    // and stores them after, so each block's loads overlap the adds of the
+    // one before; any rest of a wide window is copied directly
     constexpr int kUnroll = 8, kReach = 3;
-    for (int cb = 0; cb < nc; cb += kUnroll) {
-      TI v[kUnroll][kReach];
+    TI v[kUnroll][kReach];
+    auto load_block = [&](int cb) {
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
@@ -130,6 +132,8 @@ dd_grouped(const TI *__restrict__ in, int64_t pitch, int64_t ig, const int32_t *
                         ? x[static_cast<int64_t>(c0 + c) * pitch + tt] : TI(0);
         }
       }
+    };
+    auto store_block = [&](int cb) {
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
@@ -145,16 +149,24 @@ dd_grouped(const TI *__restrict__ in, int64_t pitch, int64_t ig, const int32_t *
           win[c * W + k] = tt < n_valid ? x[static_cast<int64_t>(c0 + c) * pitch + tt] : TI(0);
         }
       }
-    }
-    __syncthreads();
-    for (int c = 0; c < nc; ++c) {
-      const TI *w = win + c * W + threadIdx.x;
+    };
+    load_block(0);
+    store_block(0);
+    for (int cb = 0; cb < nc; cb += kUnroll) {
+      const bool more = cb + kUnroll < nc;
+      if (more) load_block(cb + kUnroll);  // in flight during the adds below
+      __syncthreads();                     // block cb stored by every thread
+      const int ce = min(cb + kUnroll, nc);
+      for (int c = cb; c < ce; ++c) {
+        const TI *w = win + c * W + threadIdx.x;
 #pragma unroll
-      for (int j = 0; j < kGroupTrials; ++j) {
-        const int dl = s_del[c][j];
-        acc0[j] = GroupIn<TI>::add(acc0[j], w[dl]);
-        acc1[j] = GroupIn<TI>::add(acc1[j], w[dl + kGroupThreads]);
+        for (int j = 0; j < kGroupTrials; ++j) {
+          const int dl = s_del[c][j];
+          acc0[j] = GroupIn<TI>::add(acc0[j], w[dl]);
+          acc1[j] = GroupIn<TI>::add(acc1[j], w[dl + kGroupThreads]);
+        }
       }
+      if (more) store_block(cb + kUnroll);  // read only after the next barrier
     }
   }
   const int64_t ta = t0 + threadIdx.x, tb = ta + kGroupThreads;
