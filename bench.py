@@ -170,15 +170,18 @@ def measured_peaks() -> dict:
     return {}
 
 
-def kernel_source_sha() -> str:
-    """Hash of the dedispersion kernels' code (comments and blank lines
-    dropped), to tell whether a recorded ncu traffic figure still applies."""
+def kernel_source_sha(workload: str) -> str:
+    """Hash of the code of the dedispersion kernel that dominates `workload`
+    (the 8-bit kernel for u8 workloads, the float kernel otherwise; comments
+    and blank lines dropped), to tell whether a recorded ncu traffic figure
+    still applies."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1401_8258_gb300", "csrc")
-    for f in sorted(glob.glob(os.path.join(csrc, "dd_dedisp*.cu")) +
-                    glob.glob(os.path.join(csrc, "dd_quad*")) +
-                    glob.glob(os.path.join(csrc, "dd_octet*")) +
-                    glob.glob(os.path.join(csrc, "dd_device.cuh"))):
+    kind = "quad" if workload.endswith("u8") else "octet"
+    files = {"quad": ["dd_dedisp_quad.cu"], "octet": ["dd_dedisp_octet.cu"]}[kind]
+    for f in sorted([os.path.join(csrc, n) for n in files] +
+                    glob.glob(os.path.join(csrc, f"dd_{kind}*")) +
+                    [os.path.join(csrc, "dd_device.cuh")]):
         with open(f) as fh:
             for line in fh:
                 code = line.split("//", 1)[0].strip()
@@ -196,7 +199,7 @@ def recorded_traffic(workload: str) -> tuple[float | None, str | None]:
     text = open(path).read()
     m_b = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", text)
     m_s = re.search(r"source_sha:\s*([0-9a-f]+)", text)
-    if not (m_b and m_s) or m_s.group(1) != kernel_source_sha():
+    if not (m_b and m_s) or m_s.group(1) != kernel_source_sha(workload):
         return None, os.path.relpath(path, ROOT)
     return float(m_b.group(1)), os.path.relpath(path, ROOT)
 
@@ -571,9 +574,11 @@ def run_batch(args):
     plans = [dd.Plan(w.nchan, w.f_top_mhz, w.chan_width_mhz, w.t_samp_s, w.dms, "u8", local)
              for w in wls]
     # plan time, outside the timed region: the autotuner times every staged
-    # tile width on each beam's geometry and keeps the fastest (a shorter
-    # scratch block suffices: the choice depends on the geometry)
+    # tile width and staging depth on each beam's geometry and keeps the
+    # fastest (a shorter scratch block suffices: the choice depends on the
+    # geometry)
     tuned = [p.autotune(min(w.nsamp, p.maxshift + 32768)) for p, w in zip(plans, wls)]
+    depths = [dd._native.dd_plan_kernel_info(p.handle, None, 0)["copy_ahead"] for p in plans]
     host_blocks, blocks, outs, nouts = [], [], [], []
     for i, (w, p) in enumerate(zip(wls, plans)):
         b, _ = synth.make_block(w, args.seed + 1000 * (rank + 1) + i, p.delays())
@@ -686,6 +691,7 @@ def run_batch(args):
         "dtype": "int32", "data": "synthetic",
         "config": {"workload": BATCH, "beams": len(wls), "staged_beams": int(staged),
                    "autotuned_dms_per_cta": [int(t[0]) for t in tuned],
+                   "autotuned_staging_depth": depths,
                    "nchan": [w.nchan for w in wls], "ndm": [w.ndm for w in wls],
                    "nsamp_in": nsamp, "input_dtype": "u8", "nsigma": NSIGMA,
                    "parallelism": "replicas1",

@@ -281,14 +281,17 @@ int dd_plan_launch_count(const dd_plan *p, int64_t *launches);
 /* Autotuning (plan time).  The thesis sets the accumulators per thread and
  * threads per block by a hand sweep for its GPU (Sec. 2.4); here each staged
  * kernel is compiled for several tile widths (u8: 64, 32 or 16 DM trials per
- * CTA; f16/f32: 128 or 64), and the plan takes the widest whose delay
- * patterns fit.  dd_plan_autotune instead times every width that fits, on a
- * scratch block of nsamp_in samples of the plan's geometry (allocated and
- * freed here; the choice depends on the channel / DM geometry, so a shorter
- * block tunes faster), and keeps the fastest.  *dms_per_cta receives the
- * chosen width (0: no staged width fits; the plain-load kernel stays), and
+ * CTA; f16/f32: 128 or 64) and the u8 kernel also for staging depths 1, 2
+ * and 3 (input windows queued that many channel chunks ahead of the chunk
+ * being built), and the plan takes the widest width whose delay patterns
+ * fit, at depth 2.  dd_plan_autotune instead times every width (and, for
+ * u8, every depth) that fits, on a scratch block of nsamp_in samples of the
+ * plan's geometry (allocated and freed here; the choice depends on the
+ * channel / DM geometry, so a shorter block tunes faster), and keeps the
+ * fastest.  *dms_per_cta receives the chosen width (0: no staged width fits;
+ * the plain-load kernel stays; dd_plan_kernel_info reports the depth), and
  * *ms_per_launch (may be NULL) its median time.  Results of dd_execute /
- * dd_run do not depend on the width.  Synchronous. */
+ * dd_run do not depend on the width or depth.  Synchronous. */
 int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_cta, float *ms_per_launch);
 
 /* Kernel selection: path 0 (default) lets dd_execute take the staged kernel
@@ -302,6 +305,14 @@ int dd_plan_set_path(dd_plan *p, int32_t path);
  * its output unwritten.  DD_ERR_ARG below 1000 ns. */
 int dd_plan_set_wait_timeout(dd_plan *p, int64_t timeout_ns);
 
+/* Staging depth of the staged u8 kernel (1..3 channel chunks of input
+ * windows queued ahead of the chunk being built; 2 by default, else what
+ * dd_plan_autotune picked).  DD_ERR_ARG for a depth outside 1..3 or a plan
+ * without the staged u8 kernel; DD_ERR_SIZE if that depth's buffers exceed
+ * a CTA's shared memory (the depth is then unchanged).  Results do not
+ * depend on it. */
+int dd_plan_set_staging_depth(dd_plan *p, int32_t copy_ahead);
+
 /* Fault injection for tests of the timeout path: with skip_copies != 0 the
  * staged kernel queues none of its bulk copies, so its first bounded wait
  * runs out (no device fault, no hang).  0 restores normal operation. */
@@ -309,10 +320,13 @@ int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies);
 
 /* Which kernel dd_execute would use for `block` / `pitch_elems`:
  * *staged = 1 for the staged (bulk-copy) kernel, 0 for the plain-load one;
- * *dms_per_cta and *smem_bytes describe the staged kernel's tiling (0 when
- * the plan has none).  Either of the last two may be NULL. */
+ * *dms_per_cta, *smem_bytes and *copy_ahead describe the staged kernel's
+ * tiling and staging depth (0 when the plan has none; the depth is 0 for the
+ * f16/f32 kernel, whose depth is fixed).  Any of the last three may be
+ * NULL. */
 int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems,
-                        int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes);
+                        int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes,
+                        int32_t *copy_ahead);
 
 /* dd_detect without allocation.  The thesis has no counterpart: this entry
  * point exists for callers that must not allocate device memory at run time

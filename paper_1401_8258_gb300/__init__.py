@@ -133,8 +133,8 @@ class Plan:
         return out, host, total
 
     def autotune(self, nsamp_in):
-        """Time every staged tile width that fits and keep the fastest;
-        returns (DM trials per CTA, ms per launch)."""
+        """Time every staged tile width (and, for u8, staging depth) that fits
+        and keep the fastest; returns (DM trials per CTA, ms per launch)."""
         return _native.dd_plan_autotune(self.handle, nsamp_in)
 
     def stats(self):

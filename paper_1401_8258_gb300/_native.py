@@ -70,9 +70,10 @@ SIGNATURES = [
     ("dd_status_string", ctypes.c_char_p, [ctypes.c_int]),
     ("dd_measure_add_peak", ctypes.c_int, [_i32, _i32, _vp, _vp]),
     ("dd_plan_set_path", ctypes.c_int, [_vp, _i32]),
+    ("dd_plan_set_staging_depth", ctypes.c_int, [_vp, _i32]),
     ("dd_plan_set_wait_timeout", ctypes.c_int, [_vp, _i64]),
     ("dd_plan_inject_fault", ctypes.c_int, [_vp, _i32]),
-    ("dd_plan_kernel_info", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp]),
+    ("dd_plan_kernel_info", ctypes.c_int, [_vp, _vp, _i64, _vp, _vp, _vp, _vp]),
     ("dd_detect_noalloc", ctypes.c_int, [_vp, _i32, _i32, _i64, _f32, _vp, _i64, _vp, _vp]),
     ("dd_run", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _f32, _vp, _i64, _vp, _vp, _vp]),
     ("dd_plan_autotune", ctypes.c_int, [_vp, _i64, _vp, _vp]),
@@ -386,12 +387,18 @@ def dd_plan_inject_fault(plan, skip_copies) -> None:
     _check(load().dd_plan_inject_fault(plan, int(skip_copies)), "dd_plan_inject_fault")
 
 
+def dd_plan_set_staging_depth(plan, copy_ahead) -> None:
+    _check(load().dd_plan_set_staging_depth(plan, int(copy_ahead)), "dd_plan_set_staging_depth")
+
+
 def dd_plan_kernel_info(plan, block, pitch_elems) -> dict:
-    st, nd, sm = ctypes.c_int32(0), ctypes.c_int32(0), ctypes.c_int32(0)
+    st, nd, sm, ca = (ctypes.c_int32(0) for _ in range(4))
     _check(load().dd_plan_kernel_info(plan, _addr(block), int(pitch_elems), ctypes.addressof(st),
-                                      ctypes.addressof(nd), ctypes.addressof(sm)),
+                                      ctypes.addressof(nd), ctypes.addressof(sm),
+                                      ctypes.addressof(ca)),
            "dd_plan_kernel_info")
-    return {"staged": bool(st.value), "dms_per_cta": nd.value, "smem_bytes": sm.value}
+    return {"staged": bool(st.value), "dms_per_cta": nd.value, "smem_bytes": sm.value,
+            "copy_ahead": ca.value}
 
 
 def dd_detect_noalloc(out, dtype, ndm, nsamp_out, nsigma, cands, capacity, stream=None):

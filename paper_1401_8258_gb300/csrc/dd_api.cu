@@ -201,6 +201,19 @@ std::vector<int> staged_widths(const dd_plan *p) {
   return {ddo::kNdThr, ddo::kNdThr / 2};
 }
 
+// Shared persistent launches take staged u8 plans of one DM-tile width and
+// one staging depth: group = width index (64, 32, 16 trials) x kDepths +
+// depth - kMinCopyAhead.
+constexpr int kDepths = ddq::kMaxCopyAhead - ddq::kMinCopyAhead + 1;
+constexpr int kQuadGroups = 3 * kDepths;
+int quad_group(const dd_plan *p) {
+  const int nd = p->quad->tables.nd_thr;
+  const int wi = nd == ddq::kNdThr ? 0 : (nd == ddq::kNdThr / 2 ? 1 : 2);
+  return wi * kDepths + p->quad->tables.copy_ahead - ddq::kMinCopyAhead;
+}
+int group_nd_thr(int g) { return ddq::kNdThr >> (g / kDepths); }
+int group_copy_ahead(int g) { return ddq::kMinCopyAhead + g % kDepths; }
+
 // Plan-time tables of the staged kernels: the widest width whose delay
 // patterns fit; none if no width fits (plain-load kernel).
 int setup_quad(dd_plan *p) {
@@ -424,21 +437,19 @@ int execute_plans_pitched(dd_plan *const *plans, int n, const void *const *block
   DeviceScope scope(plans[0]->device);
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // staged u8 work by DM-tile width (64, 32, 16 trials), in the given order
-  constexpr int kWidths = 3;
-  std::vector<int> staged[kWidths];
+  // staged u8 work by DM-tile width and staging depth, in the given order
+  std::vector<int> staged[kQuadGroups];
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
     if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
-      const int nd_thr = p->quad->tables.nd_thr;
-      staged[nd_thr == ddq::kNdThr ? 0 : (nd_thr == ddq::kNdThr / 2 ? 1 : 2)].push_back(i);
+      staged[quad_group(p)].push_back(i);
     } else {
       const int st =
           dd_execute_pitched(p, block[i], nsamp_in[i], pitch_elems[i], out[i], out_pitch[i], stream);
       if (st != DD_OK) return st;
     }
   }
-  for (int g = 0; g < kWidths; ++g) {
+  for (int g = 0; g < kQuadGroups; ++g) {
     const std::vector<int> &idx = staged[g];
     for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
       const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
@@ -454,7 +465,8 @@ int execute_plans_pitched(dd_plan *const *plans, int n, const void *const *block
       dd_plan *p0 = plans[idx[lo]];
       cudaError_t err = cudaSuccess;
       const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
-                                            ddq::kNdThr >> g, smem, p0->sm_count,
+                                            group_nd_thr(g), group_copy_ahead(g), smem,
+                                            p0->sm_count,
                                             p0->d_next_item, p0->d_error, p0->wait_timeout_ns,
                                             p0->debug_skip_copies, s, &err);
       if (nl < 0) return cuda_status(err);
@@ -565,10 +577,9 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t err = cudaSuccess;
-  // staged u8 beams, by DM-tile width (64, 32, 16 trials); the rest take
-  // their own kernels
-  constexpr int kWidths = 3;
-  std::vector<int> staged[kWidths];
+  // staged u8 beams, by DM-tile width (64, 32, 16 trials) and staging
+  // depth; the rest take their own kernels
+  std::vector<int> staged[kQuadGroups];
   std::vector<char> is_staged(n, 0);
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
@@ -578,15 +589,14 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
       if (st != DD_OK) return st;
       err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
       if (err != cudaSuccess) return cuda_status(err);
-      const int nd_thr = p->quad->tables.nd_thr;
-      staged[nd_thr == ddq::kNdThr ? 0 : (nd_thr == ddq::kNdThr / 2 ? 1 : 2)].push_back(i);
+      staged[quad_group(p)].push_back(i);
       is_staged[i] = 1;
     } else {
       const int st = dd_execute(p, block[i], nsamp_in[i], pitch_elems[i], out[i], stream);
       if (st != DD_OK) return st;
     }
   }
-  for (int g = 0; g < kWidths; ++g) {
+  for (int g = 0; g < kQuadGroups; ++g) {
     std::vector<int> &idx = staged[g];
     // costliest beams first (a work item costs about nchan): the queue's
     // tail then holds the cheap items
@@ -605,7 +615,7 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
       }
       dd_plan *p0 = plans[idx[lo]];
       const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
-                                            ddq::kNdThr >> g, smem,
+                                            group_nd_thr(g), group_copy_ahead(g), smem,
                                             sm_count, next_item, status,
                                             p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
       if (nl < 0) return cuda_status(err);
@@ -1239,17 +1249,11 @@ extern "C" int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_c
   OctetDevice *best_o = nullptr;
   float best_ms = 0.f;
   int st = cuda_status(e);
-  for (int w : staged_widths(p)) {
-    if (st != DD_OK) break;
-    QuadDevice *q = u8 ? make_quad(p, w, &st) : nullptr;
-    OctetDevice *o = u8 ? nullptr : make_octet(p, w, &st);
-    if (!q && !o) continue;
-    QuadDevice *keep_q = p->quad;
-    OctetDevice *keep_o = p->octet;
-    p->quad = q ? q : p->quad;
-    p->octet = o ? o : p->octet;
+  // median of three timed launches (after one untimed) of the plan's
+  // current staged kernel on the scratch block
+  auto time_current = [&](float *ms) {
     float times[4] = {0, 0, 0, 0};
-    for (int r = 0; r < 4 && st == DD_OK; ++r) {  // one warm-up, three timed
+    for (int r = 0; r < 4 && st == DD_OK; ++r) {
       cudaError_t le = cudaSuccess;
       e = cudaEventRecord(e0, s);
       const int n = u8 ? ddk::launch_dedisperse_quad(p, blk, pitch, nsamp_out, out, nsamp_out,
@@ -1262,15 +1266,41 @@ extern "C" int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_c
       if (e == cudaSuccess) e = cudaEventElapsedTime(&times[r], e0, e1);
       st = cuda_status(e);
     }
+    std::sort(times + 1, times + 4);
+    *ms = times[2];
+  };
+  for (int w : staged_widths(p)) {
+    if (st != DD_OK) break;
+    QuadDevice *q = u8 ? make_quad(p, w, &st) : nullptr;
+    OctetDevice *o = u8 ? nullptr : make_octet(p, w, &st);
+    if (!q && !o) continue;
+    QuadDevice *keep_q = p->quad;
+    OctetDevice *keep_o = p->octet;
+    p->quad = q ? q : p->quad;
+    p->octet = o ? o : p->octet;
+    // u8: every staging depth that fits at this width; floats: one kernel
+    float w_ms = 0.f;
+    int w_ca = 0;
+    if (q) {
+      for (int ca = ddq::kMinCopyAhead; ca <= ddq::kMaxCopyAhead && st == DD_OK; ++ca) {
+        if (!ddq::set_copy_ahead(q->tables, ca)) continue;
+        float ms = 0.f;
+        time_current(&ms);
+        if (st == DD_OK && (w_ca == 0 || ms < w_ms)) w_ms = ms, w_ca = ca;
+      }
+      if (w_ca != 0) ddq::set_copy_ahead(q->tables, w_ca);
+    } else {
+      time_current(&w_ms);
+    }
     p->quad = keep_q;
     p->octet = keep_o;
-    std::sort(times + 1, times + 4);
-    if (st == DD_OK && (!(best_q || best_o) || times[2] < best_ms)) {
+    const bool timed = o || w_ca != 0;
+    if (st == DD_OK && timed && (!(best_q || best_o) || w_ms < best_ms)) {
       free_quad(best_q);
       free_octet(best_o);
       best_q = q;
       best_o = o;
-      best_ms = times[2];
+      best_ms = w_ms;
     } else {
       free_quad(q);
       free_octet(o);
@@ -1300,6 +1330,17 @@ extern "C" int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_c
   return st;
 }
 
+extern "C" int dd_plan_set_staging_depth(dd_plan *p, int32_t copy_ahead) {
+  if (!p || !p->quad || copy_ahead < ddq::kMinCopyAhead || copy_ahead > ddq::kMaxCopyAhead)
+    return DD_ERR_ARG;
+  const int keep = p->quad->tables.copy_ahead;
+  if (!ddq::set_copy_ahead(p->quad->tables, copy_ahead)) {
+    ddq::set_copy_ahead(p->quad->tables, keep);
+    return DD_ERR_SIZE;
+  }
+  return DD_OK;
+}
+
 extern "C" int dd_plan_set_path(dd_plan *p, int32_t path) {
   if (!p || path < 0 || path > 1) return DD_ERR_ARG;
   p->path = path;
@@ -1319,7 +1360,8 @@ extern "C" int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies) {
 }
 
 extern "C" int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems,
-                                   int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes) {
+                                   int32_t *staged, int32_t *dms_per_cta, int32_t *smem_bytes,
+                                   int32_t *copy_ahead) {
   if (!p || !staged) return DD_ERR_ARG;
   const bool q = p->path == 0 && block &&
                  (ddk::quad_supported(p, block, pitch_elems, p->maxshift + 1) ||
@@ -1329,5 +1371,6 @@ extern "C" int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t 
   const int sm = p->quad ? p->quad->tables.smem_bytes : (p->octet ? p->octet->tables.smem_bytes : 0);
   if (dms_per_cta) *dms_per_cta = nd;
   if (smem_bytes) *smem_bytes = sm;
+  if (copy_ahead) *copy_ahead = p->quad ? p->quad->tables.copy_ahead : 0;
   return DD_OK;
 }

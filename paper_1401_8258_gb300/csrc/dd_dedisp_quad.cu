@@ -10,7 +10,8 @@
 //      each channel's input window -- the "channel vector" of Sec. 2.4,
 //      sized by the largest and smallest delay of the tile -- plus the
 //      chunk's plan record into shared memory, signalling an mbarrier,
-//      kCopyAhead chunks ahead of the chunk being built;
+//      1 to 3 chunks ahead of the chunk being built (the staging depth, a
+//      template parameter picked per plan by the autotuner);
 //   2. 12 building warps build pattern rows: word i of a row holds, for one
 //      relative-delay pattern of a quad of channels, the four channels' sum
 //      at pair i as two 16-bit halves (dd_quad_plan.cpp); they build chunk
@@ -291,9 +292,12 @@ __device__ __forceinline__ void drain(uint32_t (&acc)[ND_THR][kPairsPerThread], 
 // warp role runs the chunk pipeline below from a clean state (mbarriers
 // re-initialised, every named-barrier phase of the previous item complete);
 // tensor memory is allocated once per CTA.
-template <int ND_THR>
+template <int ND_THR, int CA>
 __global__ void __launch_bounds__(kThreads, 1)
 dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
+  // staging depth: copies queued CA chunks ahead, kRaw raw window buffers,
+  // kRec records
+  constexpr int kRaw = raw_stages(CA), kRec = rec_stages(CA);
   constexpr int ND_CTA = kDmGroups * ND_THR;
   constexpr int kSegsOff = units_offset(ND_CTA);
   constexpr int kStartsOff = warp_start_offset(ND_CTA);
@@ -307,15 +311,15 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
                 "tensor-memory allocation must be a power of two in 32..512 columns");
   static_assert(kFlushQuads % kQuadsPerChunk == 0, "drain at chunk boundaries");
   static_assert(kTimeGroups == 1, "a warp holds whole time tiles of its trials (tile maxima)");
-  static_assert(kRawStages == kCopyAhead + 1 && kRecStages == kRowStages + kCopyAhead &&
-                    8 * kRawStages <= kTmemSlot && kItemSlot + 8 <= kBarrierBytes,
+  static_assert(CA >= kMinCopyAhead && CA <= kMaxCopyAhead && 8 * kRaw <= kTmemSlot &&
+                    kItemSlot + 8 <= kBarrierBytes,
                 "pipeline depths");
   constexpr int kFlushChunks = kFlushQuads / kQuadsPerChunk;
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const uint32_t bar0 = smem_addr(smem);
-  auto tma_bar = [&](int m) { return bar0 + 8u * (m % kRawStages); };
+  auto tma_bar = [&](int m) { return bar0 + 8u * (m % kRaw); };
   // chunk at which the building warps stopped after a copy wait ran out
   volatile int32_t *abort_at = reinterpret_cast<volatile int32_t *>(smem + kAbortSlot);
   volatile long long *item_s = reinterpret_cast<volatile long long *>(smem + kItemSlot);
@@ -353,32 +357,32 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
     const uint32_t meta_bytes = static_cast<uint32_t>((a.nchan_pad * 8 + 15) / 16 * 16);
     const uint32_t rec_bytes = static_cast<uint32_t>(a.rec_words) * 4;
     const uint32_t rec_off = kBarrierBytes + meta_bytes;
-    const uint32_t raw_off = rec_off + kRecStages * rec_bytes;
+    const uint32_t raw_off = rec_off + kRec * rec_bytes;
     const uint32_t raw_bytes = 4u * kQuadsPerChunk * static_cast<uint32_t>(a.raw_stride);
-    const uint32_t prow_off = raw_off + kRawStages * raw_bytes;
+    const uint32_t prow_off = raw_off + kRaw * raw_bytes;
     const uint32_t prow_bytes = static_cast<uint32_t>(a.prow_words) * 4;
     auto rec_ptr = [&](int m) {
-      return reinterpret_cast<const int32_t *>(smem + rec_off + (m % kRecStages) * rec_bytes);
+      return reinterpret_cast<const int32_t *>(smem + rec_off + (m % kRec) * rec_bytes);
     };
-    auto rec_addr = [&](int m) { return bar0 + rec_off + (m % kRecStages) * rec_bytes; };
-    auto raw_addr = [&](int m) { return bar0 + raw_off + (m % kRawStages) * raw_bytes; };
+    auto rec_addr = [&](int m) { return bar0 + rec_off + (m % kRec) * rec_bytes; };
+    auto raw_addr = [&](int m) { return bar0 + raw_off + (m % kRaw) * raw_bytes; };
     auto prow_addr = [&](int m) { return bar0 + prow_off + (m % kRowStages) * prow_bytes; };
 
     const int32_t *meta_g = a.raw_meta + static_cast<int64_t>(tile) * a.nchan_pad * 2;
     for (int i = tid; i < 2 * a.nchan_pad; i += kThreads) meta_s[i] = meta_g[i];
     if (tid == 0) {
-      for (int s = 0; s < kRawStages; ++s) mbar_init(tma_bar(s), 1);
+      for (int s = 0; s < kRaw; ++s) mbar_init(tma_bar(s), 1);
       *abort_at = INT32_MAX;
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // Pipeline (chunk m: raw stage m % kRawStages, record stage m %
-    // kRecStages, row stage m % kRowStages).  Building warps, chunk j: wait
+    // Pipeline (chunk m: raw stage m % kRaw, record stage m %
+    // kRec, row stage m % kRowStages).  Building warps, chunk j: wait
     // until the accumulating warps are done with chunk j - kRowStages (its
     // row stage is reused, and so are older record stages); wait (bounded)
     // for the copies of chunk j and agree among themselves that they landed;
-    // the first building warp queues the copies of chunk j + kCopyAhead (into
+    // the first building warp queues the copies of chunk j + CA (into
     // the raw stage of chunk j-1 and the record stage of chunk j-kRowStages);
     // build this warp's units of chunk j's rows; signal the rows built.
     // Accumulating warps, chunk k: wait for its rows, add them, signal the
@@ -392,14 +396,14 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
       const int bw = warp - kAccThreads / 32;
       const bool issuer = bw == 0 && !L.skip_copies;
       if (issuer) {
-        const int prefill = a.nchunks < kCopyAhead ? a.nchunks : kCopyAhead;
+        const int prefill = a.nchunks < CA ? a.nchunks : CA;
         for (int m = 0; m < prefill; ++m)
           issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
         issued = prefill;
       }
       for (int j = 0; j < a.nchunks; ++j) {
         if (j >= kRowStages) bar_sync(kBarEmpty + j % kRowStages, kThreads);
-        const bool ok = warp_wait(tma_bar(j), (j / kRawStages) & 1, L.timeout_ns, lane);
+        const bool ok = warp_wait(tma_bar(j), (j / kRaw) & 1, L.timeout_ns, lane);
         if (bar_or(kBarBuild, kBuildThreads, !ok)) {
           if (bw == 0 && lane == 0) *abort_at = j;
           aborted = true;
@@ -409,13 +413,13 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
             if (m >= 0) bar_sync(kBarEmpty + m % kRowStages, kThreads);
           break;
         }
-        if (issuer && j + kCopyAhead < a.nchunks) {
+        if (issuer && j + CA < a.nchunks) {
           // every building warp is past chunk j-1 (bar_or above) and the
           // accumulating warps past chunk j-kRowStages (bar_sync): the raw
           // stage of chunk j-1 and the record stage of chunk j-kRowStages are
           // free
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          const int m = j + kCopyAhead;
+          const int m = j + CA;
           issue_chunk(a, meta_s, tile, t_cta, m, tma_bar(m), rec_addr(m), raw_addr(m), lane);
           issued = m + 1;
         }
@@ -555,10 +559,10 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
       if (builder && warp - kAccThreads / 32 == 0 && lane == 0) {
         // a bounded wait ran out: record it, and wait (bounded) for the
         // copies this warp queued that may still be in flight (the last
-        // kRawStages queued, each on its own barrier) before leaving
+        // kRaw queued, each on its own barrier) before leaving
         atomicExch(L.status, 1);
-        for (int m = issued > kRawStages ? issued - kRawStages : 0; m < issued; ++m)
-          mbar_wait_bounded(tma_bar(m), (m / kRawStages) & 1, L.timeout_ns);
+        for (int m = issued > kRaw ? issued - kRaw : 0; m < issued; ++m)
+          mbar_wait_bounded(tma_bar(m), (m / kRaw) & 1, L.timeout_ns);
       }
       __syncthreads();
       break;
@@ -572,6 +576,14 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
   if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
 }
 
+// The kernel of ND_THR trials per thread at staging depth copy_ahead.
+template <int ND_THR>
+auto pick_depth(int copy_ahead) {
+  return copy_ahead == 1   ? dd_dedisperse_quad_u8<ND_THR, 1>
+         : copy_ahead == 3 ? dd_dedisperse_quad_u8<ND_THR, 3>
+                           : dd_dedisperse_quad_u8<ND_THR, 2>;
+}
+
 }  // namespace
 
 namespace ddk {
@@ -581,7 +593,8 @@ bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t 
   return (reinterpret_cast<uintptr_t>(block) & 15) == 0 && (pitch & 15) == 0;
 }
 
-int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int smem, int device_sms,
+int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int copy_ahead, int smem,
+                      int device_sms,
                       unsigned long long *next_item, int32_t *status, uint64_t timeout_ns,
                       int32_t skip_copies, cudaStream_t stream, cudaError_t *err) {
   if (nbeams < 1 || nbeams > kMaxBeams) {
@@ -602,9 +615,13 @@ int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int smem, int d
   L.status = status;
   L.timeout_ns = timeout_ns;
   L.skip_copies = skip_copies;
-  auto kern = nd_thr == kNdThr       ? dd_dedisperse_quad_u8<kNdThr>
-              : nd_thr == kNdThr / 2 ? dd_dedisperse_quad_u8<kNdThr / 2>
-                                     : dd_dedisperse_quad_u8<kNdThr / 4>;
+  if (copy_ahead < kMinCopyAhead || copy_ahead > kMaxCopyAhead) {
+    *err = cudaErrorInvalidValue;
+    return -1;
+  }
+  auto kern = nd_thr == kNdThr       ? pick_depth<kNdThr>(copy_ahead)
+              : nd_thr == kNdThr / 2 ? pick_depth<kNdThr / 2>(copy_ahead)
+                                     : pick_depth<kNdThr / 4>(copy_ahead);
   *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
   if (*err == cudaSuccess)
@@ -648,7 +665,8 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
                            void *out, int64_t out_pitch, int64_t *rowsums, int32_t *tilemax,
                            cudaStream_t stream, cudaError_t *err) {
   const Beam b = quad_beam(p, block, pitch, nsamp_out, out, out_pitch, rowsums, tilemax);
-  return launch_quad_beams(&b, 1, p->quad->tables.nd_thr, p->quad->tables.smem_bytes, p->sm_count,
+  return launch_quad_beams(&b, 1, p->quad->tables.nd_thr, p->quad->tables.copy_ahead,
+                           p->quad->tables.smem_bytes, p->sm_count,
                            p->d_next_item, p->d_error, p->wait_timeout_ns,
                            p->debug_skip_copies, stream, err);
 }

@@ -123,11 +123,13 @@ int launch_dedisperse_quad(dd_plan *p, const void *block, int64_t pitch, int64_t
                            cudaStream_t stream, cudaError_t *err);
 // The staged kernel is persistent: one launch drains a queue of (beam, DM
 // tile, time tile) items over up to ddq::kMaxBeams beams, which must share
-// nd_thr (kNdThr, kNdThr/2 or kNdThr/4); smem is the largest of the beams'
-// shared-memory sizes.
+// nd_thr (kNdThr, kNdThr/2 or kNdThr/4) and the staging depth copy_ahead
+// (ddq::kMinCopyAhead .. kMaxCopyAhead); smem is the largest of the beams'
+// shared-memory sizes at that depth.
 ddq::Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                     void *out, int64_t out_pitch, int64_t *rowsums, int32_t *tilemax);
-int launch_quad_beams(const ddq::Beam *beams, int nbeams, int nd_thr, int smem, int device_sms,
+int launch_quad_beams(const ddq::Beam *beams, int nbeams, int nd_thr, int copy_ahead, int smem,
+                      int device_sms,
                       unsigned long long *next_item, int32_t *status, uint64_t timeout_ns,
                       int32_t skip_copies, cudaStream_t stream, cudaError_t *err);
 constexpr int kTileSamples = ddq::kTimeTile;

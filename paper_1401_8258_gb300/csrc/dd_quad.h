@@ -105,8 +105,14 @@ DDQ_HD constexpr int rec_words(int nd_cta) {
   return (warp_start_offset(nd_cta) + (kBuildWarps + 2) / 2 + 3) / 4 * 4;
 }
 
+#ifndef DDQ_COPY_AHEAD
+#define DDQ_COPY_AHEAD 2
+#endif
+constexpr int kCopyAhead = DDQ_COPY_AHEAD;  // default staging depth (chunks queued ahead)
+
 struct Tables {
   int nd_thr = 0, nd_cta = 0;
+  int copy_ahead = kCopyAhead;  // staging depth that smem_bytes is computed for
   int ntiles = 0, nquads = 0, nchan_pad = 0, nchunks = 0;
   int rec_words = 0;
   int32_t raw_stride = 0;   // bytes per channel window slot (multiple of 16)
@@ -116,36 +122,44 @@ struct Tables {
   std::vector<int32_t> raw_meta;  // [ntiles][nchan_pad][2]
 };
 
-// Pipeline depth: raw windows of chunks k+1 and k+2 are in flight while
-// chunk k+1 is interleaved and chunk k accumulated.
+// Pipeline depth: the building warps queue the copies of a chunk copy_ahead
+// chunks ahead of the one they build (the staging depth, kMinCopyAhead ..
+// kMaxCopyAhead, compiled for each and picked by the autotuner; kCopyAhead by
+// default), and the rows of chunk k+1 are built while chunk k is
+// accumulated (kRowStages row areas).
 #ifndef DDQ_ROW_STAGES
 #define DDQ_ROW_STAGES 2
 #endif
-#ifndef DDQ_COPY_AHEAD
-#define DDQ_COPY_AHEAD 2
-#endif
-constexpr int kCopyAhead = DDQ_COPY_AHEAD;  // chunks queued ahead of the one being built
-constexpr int kRawStages = kCopyAhead + 1;
 constexpr int kRowStages = DDQ_ROW_STAGES;
+constexpr int kMinCopyAhead = 1, kMaxCopyAhead = 3;
+// raw window buffers: the chunk being built and the copy_ahead queued after it
+DDQ_HD constexpr int raw_stages(int copy_ahead) { return copy_ahead + 1; }
 // a record stays in use until the accumulating warps are done with its
 // chunk, up to kRowStages chunks behind the building warps, which queue
-// copies kCopyAhead chunks ahead
-constexpr int kRecStages = kRowStages + kCopyAhead;
+// copies copy_ahead chunks ahead
+DDQ_HD constexpr int rec_stages(int copy_ahead) { return kRowStages + copy_ahead; }
 constexpr int kBarrierBytes = 64;  // copy mbarriers (8 bytes each), tensor-memory address, flags
 constexpr int kTmemSlot = 32;      // byte offset of the tensor-memory address
 constexpr int kAbortSlot = 36;     // chunk at which a copy wait ran out
 constexpr int kItemSlot = 40;      // current work item (int64)
 
 // Shared-memory layout: the mbarriers and tensor-memory address (kBarrierBytes), the tile's raw
-// window table (nchan_pad x 2 int32), kRecStages records, kRawStages raw
+// window table (nchan_pad x 2 int32), rec_stages records, raw_stages raw
 // window buffers (4*kQuadsPerChunk slots of raw_stride bytes), kRowStages
 // pattern-row areas.
 inline int32_t rec_bytes(const Tables &t) { return t.rec_words * 4; }
 inline int32_t raw_buf_bytes(const Tables &t) { return 4 * kQuadsPerChunk * t.raw_stride; }
 inline int32_t meta_bytes(const Tables &t) { return (t.nchan_pad * 8 + 15) / 16 * 16; }
 inline int32_t smem_bytes(const Tables &t) {
-  return kBarrierBytes + meta_bytes(t) + kRecStages * rec_bytes(t) + kRawStages * raw_buf_bytes(t) +
-         kRowStages * t.prow_words * 4;
+  return kBarrierBytes + meta_bytes(t) + rec_stages(t.copy_ahead) * rec_bytes(t) +
+         raw_stages(t.copy_ahead) * raw_buf_bytes(t) + kRowStages * t.prow_words * 4;
+}
+// Staging depth of the tables (the records and windows do not depend on it,
+// only the shared-memory size); false if that depth does not fit a CTA.
+inline bool set_copy_ahead(Tables &t, int copy_ahead) {
+  t.copy_ahead = copy_ahead;
+  t.smem_bytes = smem_bytes(t);
+  return copy_ahead >= kMinCopyAhead && copy_ahead <= kMaxCopyAhead && t.smem_bytes <= kMaxSmem;
 }
 
 // Returns 0 and fills *tb, or 1 if this geometry needs more than

@@ -189,6 +189,8 @@ def test_autotune_keeps_results_identical(name, nchan, ndm, dtype):
         print(f"{name} {dtype}: autotune chose {nd} trials per CTA ({ms:.3f} ms)")
         info = dd._native.dd_plan_kernel_info(plan.handle, dblock, pitch)
         assert info["staged"] and info["dms_per_cta"] == nd
+        assert info["copy_ahead"] in ((1, 2, 3) if dtype == "u8" else (0,))
+        print(f"  staging depth {info['copy_ahead']}")
         after = plan.run(dblock, 4.0, nsamp_in=wl.nsamp)
     assert torch.equal(before[0], after[0])
     assert before[2] == after[2] and np.array_equal(before[1], after[1])
@@ -225,3 +227,45 @@ def test_host_pipe_results_equal_process_host_per_block(dtype, capacity):
         assert res is not None and res[1] == total
         assert np.array_equal(res[0], c)
         assert np.array_equal(stats[0], wstats[0]) and np.array_equal(stats[1], wstats[1])
+
+
+@pytest.mark.parametrize("depth", [1, 2, 3])
+def test_staging_depths_give_identical_results(depth):
+    """Each staging depth of the u8 kernel (input windows queued 1, 2 or 3
+    chunks ahead) gives the oracle's output, statistics and candidates, alone
+    and in a batch that mixes depths (one shared launch per depth)."""
+    wl = synth.scaled(synth.workload("full_block_u8"), nchan=512, nsamp=30000, ndm=192)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    block, _ = synth.make_block(wl, seed=8, delays=delays)
+    dblock = torch.from_numpy(block).to(DEV)
+    ref = oracle.dedisperse(block, delays)
+    m, sd = oracle.stats(ref)
+    c_ref, tot = oracle.detect(ref, m, sd, 4.0)
+    other = 1 + depth % 3
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as p1, \
+            dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, "u8") as p2:
+        dd._native.dd_plan_set_staging_depth(p1.handle, depth)
+        dd._native.dd_plan_set_staging_depth(p2.handle, other)
+        assert dd._native.dd_plan_kernel_info(p1.handle, dblock, wl.nsamp)["copy_ahead"] == depth
+        out, cands, total = p1.run(dblock, 4.0)
+        assert np.array_equal(out.cpu().numpy(), ref)
+        assert total == tot and np.array_equal(cands, c_ref)
+        mean, sigma = p1.stats()
+        assert np.array_equal(mean, m) and np.array_equal(sigma, sd)
+        batch = dd.Batch([p1, p2])
+        outs, bc, totals = batch.run([dblock, dblock], 4.0)
+        batch.close()
+        for o, c, t in zip(outs, bc, totals):
+            assert np.array_equal(o.cpu().numpy(), ref)
+            assert t == tot and np.array_equal(c, c_ref)
+        with pytest.raises(dd.DDError):
+            dd._native.dd_plan_set_staging_depth(p1.handle, 4)
+        # the timeout path at this depth: no copies queued, the wait runs out
+        dd._native.dd_plan_set_wait_timeout(p1.handle, 50_000_000)
+        dd._native.dd_plan_inject_fault(p1.handle, 1)
+        with pytest.raises(dd.DDError) as e:
+            p1.run(dblock, 4.0)
+        assert e.value.status == -7
+        dd._native.dd_plan_inject_fault(p1.handle, 0)
+        out, cands, total = p1.run(dblock, 4.0)
+        assert np.array_equal(out.cpu().numpy(), ref) and total == tot
