@@ -76,6 +76,11 @@ int dd_binned_execute(dd_binned *b, const void *block, int64_t nsamp_in, int64_t
 /* Kernel launches queued by this object since creation. */
 int dd_binned_launch_count(const dd_binned *b, int64_t *launches);
 
+/* Synchronise `stream` and return DD_ERR_DEVICE_TIMEOUT if a bounded wait
+ * of any launch of this object ran out since the last call (clearing it),
+ * else DD_OK -- dd_sync for the plans inside. */
+int dd_binned_sync(dd_binned *b, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

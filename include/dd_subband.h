@@ -68,6 +68,11 @@ int dd_subband_execute(dd_subband *s, const void *block, int64_t nsamp_in, int64
 /* Kernel launches queued by this object since creation. */
 int dd_subband_launch_count(const dd_subband *s, int64_t *launches);
 
+/* Synchronise `stream` and return DD_ERR_DEVICE_TIMEOUT if a bounded wait
+ * of any launch of this object ran out since the last call (clearing it),
+ * else DD_OK -- dd_sync for the step plans inside. */
+int dd_subband_sync(dd_subband *s, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

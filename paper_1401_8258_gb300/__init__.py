@@ -345,6 +345,11 @@ class Subband:
     def launch_count(self):
         return _native.dd_subband_launch_count(self.handle)
 
+    def sync(self, stream=None):
+        """Wait for this object's work on `stream`; raises DDError if a
+        bounded device wait of one of its launches ran out."""
+        _native.dd_subband_sync(self.handle, stream)
+
     def close(self):
         if self.handle:
             _native.dd_subband_destroy(self.handle)
@@ -437,6 +442,11 @@ class Binned:
 
     def launch_count(self):
         return _native.dd_binned_launch_count(self.handle)
+
+    def sync(self, stream=None):
+        """Wait for this object's work on `stream`; raises DDError if a
+        bounded device wait of one of its launches ran out."""
+        _native.dd_binned_sync(self.handle, stream)
 
     def close(self):
         if self.handle:

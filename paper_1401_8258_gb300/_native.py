@@ -95,6 +95,7 @@ SIGNATURES = [
     ("dd_subband_nominal", ctypes.c_int, [_vp, _vp, _vp]),
     ("dd_subband_execute", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _vp]),
     ("dd_subband_launch_count", ctypes.c_int, [_vp, _vp]),
+    ("dd_subband_sync", ctypes.c_int, [_vp, _vp]),
     # dd_binned.h
     ("dd_binned_create", ctypes.c_int,
      [_vp, _i32, _f64, _f64, _f64, _vp, _i32, _i32, _i32, _i32, _i32]),
@@ -103,6 +104,7 @@ SIGNATURES = [
     ("dd_binned_rows", ctypes.c_int, [_vp, _i64, _vp, _vp]),
     ("dd_binned_execute", ctypes.c_int, [_vp, _vp, _i64, _i64, _vp, _i64, _vp]),
     ("dd_binned_launch_count", ctypes.c_int, [_vp, _vp]),
+    ("dd_binned_sync", ctypes.c_int, [_vp, _vp]),
     # dd_post.h
     ("dd_median_filter", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _i32, _vp, _i64, _vp]),
     ("dd_detrend", ctypes.c_int, [_vp, _i64, _i32, _i32, _i64, _vp, _i64, _vp, _vp]),
@@ -492,6 +494,14 @@ def dd_subband_nominal(sub) -> np.ndarray:
 def dd_subband_execute(sub, block, nsamp_in, pitch_elems, out, stream=None) -> None:
     _check(load().dd_subband_execute(sub, _addr(block), int(nsamp_in), int(pitch_elems),
                                      _addr(out), _stream(stream)), "dd_subband_execute")
+
+
+def dd_subband_sync(sub, stream=None) -> None:
+    _check(load().dd_subband_sync(sub, _stream(stream)), "dd_subband_sync")
+
+
+def dd_binned_sync(b, stream=None) -> None:
+    _check(load().dd_binned_sync(b, _stream(stream)), "dd_binned_sync")
 
 
 def dd_subband_launch_count(sub) -> int:

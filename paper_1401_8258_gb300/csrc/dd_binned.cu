@@ -262,6 +262,16 @@ extern "C" int dd_binned_launch_count(const dd_binned *b, int64_t *launches) {
   return DD_OK;
 }
 
+extern "C" int dd_binned_sync(dd_binned *b, void *stream) {
+  if (!b) return DD_ERR_ARG;
+  int result = DD_OK;
+  for (const Range &r : b->ranges) {
+    const int st = dd_sync(r.plan, stream);
+    if (st != DD_OK && result == DD_OK) result = st;
+  }
+  return result;
+}
+
 extern "C" int dd_binned_execute(dd_binned *b, const void *block, int64_t nsamp_in,
                                  int64_t pitch_elems, void *out, int64_t out_pitch, void *stream) {
   if (!b || !block || !out) return DD_ERR_ARG;

@@ -425,6 +425,20 @@ extern "C" int dd_subband_launch_count(const dd_subband *s, int64_t *launches) {
   return DD_OK;
 }
 
+extern "C" int dd_subband_sync(dd_subband *s, void *stream) {
+  if (!s) return DD_ERR_ARG;
+  int result = DD_OK;
+  for (dd_plan *p : s->step1) {
+    const int st = dd_sync(p, stream);
+    if (st != DD_OK && result == DD_OK) result = st;
+  }
+  for (dd_plan *p : s->step2) {
+    const int st = dd_sync(p, stream);
+    if (st != DD_OK && result == DD_OK) result = st;
+  }
+  return result;
+}
+
 extern "C" int dd_subband_execute(dd_subband *s, const void *block, int64_t nsamp_in,
                                   int64_t pitch_elems, void *out, void *stream) {
   if (!s || !block || !out) return DD_ERR_ARG;

@@ -115,3 +115,8 @@ def test_host_pipe_argument_errors(lib):
     assert lib.dd_host_pipe_flush(None, FAKE, ctypes.addressof(cnt), ctypes.addressof(has),
                                   None) == DD_ERR_ARG
     assert lib.dd_host_pipe_destroy(None) == 0
+
+
+def test_subband_and_binned_sync_reject_null(lib):
+    assert lib.dd_subband_sync(None, None) == DD_ERR_ARG
+    assert lib.dd_binned_sync(None, None) == DD_ERR_ARG

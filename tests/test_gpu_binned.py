@@ -60,6 +60,7 @@ def test_binned_u8_matches_oracle_exactly(nchan, ndm, step, max_factor, extra, p
         assert np.array_equal(gf, fac) and np.array_equal(gl, lens)
         out = b.execute(torch.from_numpy(block).to(DEV), nsamp_in=nsamp).cpu().numpy()
         assert b.launch_count() > 0
+        b.sync()  # no bounded wait ran out
     if max_factor > 1:
         assert fac.max() > 1  # the geometry reaches past twice the diagonal DM
     for d in range(wl.ndm):
