@@ -23,7 +23,8 @@
  * D1 the largest step-1 delay and D2 the largest step-2 delay (it can be
  * slightly below the brute-force maxshift: the step-1 delays reach only the
  * nominal trials).  Types as for dd_execute: u8 input gives int32 output
- * (exact integer sums: step 1 in int32, carried through float, which is
+ * (exact integer sums: the step-1 series kept as 16-bit integers when
+ * chans_per_subband * 255 <= 65535, else carried through float, which is
  * exact below 2^24, hence DD_ERR_RANGE when nchan * 255 >= 2^24), f16/f32
  * input gives float (step-1 series kept in float).
  */

@@ -4,11 +4,13 @@
 //   step 1: groups = subbands, channels = the subband's channels, trials =
 //           the nominal trials; rows written interleaved as SB[n][s][t];
 //   step 2: groups = DM groups, channels = the subbands (SB[n(g)] as a
-//           float block), trials = the group's trials.
-// The grouped kernel stages, per CTA (group, 16 trials, time tile), each
-// channel's input window in shared memory and adds from there.  u8 input:
-// step 1 adds in int32 and stores float (exact below 2^24), step 2 adds the
-// integer-valued floats exactly and stores int32.
+//           block), trials = the group's trials.
+// The grouped kernels stage, per CTA (group, 16 trials, time tile), each
+// channel's input window in shared memory and add from there.  u8 input
+// (chans_per_subband x 255 <= 65535): both steps on packed pairs of 16-bit
+// sums, SB kept as uint16, output int32 (exact).  Float input, or u8 with
+// wider subbands: step 1 stores float (exact for u8 below 2^24), step 2 adds
+// the floats (u8: integer-valued, exact) and stores float or int32.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
@@ -44,6 +46,7 @@ namespace {
 constexpr int kGroupThreads = 256;
 constexpr int kGroupTrials = 16;   // trials per CTA (one accumulator each per thread)
 constexpr int kGroupTile = 512;    // output samples per CTA (two per thread)
+static_assert(kGroupTile == 2 * kGroupThreads, "a thread owns samples t and t + kGroupThreads");
 
 template <typename T> struct GroupIn;
 template <> struct GroupIn<uint8_t> {
@@ -201,6 +204,151 @@ cudaError_t launch_grouped(const TI *in, int64_t pitch, int64_t ig, const int32_
   dd_grouped<TI, TO><<<grid, kGroupThreads, smem, s>>>(in, pitch, ig, tab, tab_ch, nch_total, ntr,
                                                        ntr_last, span, n_valid, out, og, oj,
                                                        nsamp_out);
+  return cudaGetLastError();
+}
+
+// The grouped sum for integer input (u8 blocks, u16 subband series) with
+// packed pairs: each channel's window is staged as pair words, word i
+// holding the window's samples i and i + kGroupThreads in its low and high
+// 16 bits, so one shared load and one add serve both outputs (t and t + 256)
+// of a thread for one trial.  The 16-bit halves are drained into 32-bit sums
+// every `drain` channels (drain x the largest input sample <= 65535).  Same
+// grid, tables, n_valid rule and stores as dd_grouped; dynamic shared memory
+// min(tab_ch, 64) rows of kGroupThreads + span words.
+template <typename TI, typename TO>
+__global__ void __launch_bounds__(kGroupThreads, 2)
+dd_grouped_pairs(const TI *__restrict__ in, int64_t pitch, int64_t ig,
+                 const int32_t *__restrict__ tab, int tab_ch, int nch_total, int ntr, int ntr_last,
+                 int span, int64_t n_valid, int drain, TO *__restrict__ out, int64_t og,
+                 int64_t oj, int64_t nsamp_out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  uint32_t *win = reinterpret_cast<uint32_t *>(smem_raw);
+  __shared__ int32_t s_del[64][kGroupTrials];  // delay relative to the window start
+  __shared__ int32_t s_lo[64];
+  const int g = blockIdx.z;
+  const int j0 = blockIdx.y * kGroupTrials;
+  const int64_t t0 = static_cast<int64_t>(blockIdx.x) * kGroupTile;
+  const int nch = min(tab_ch, nch_total - g * tab_ch);
+  const int ntr_g = g == gridDim.z - 1 ? ntr_last : ntr;
+  const int P = kGroupThreads + span;  // pair words per channel
+  const TI *x = in + g * ig;
+  const int32_t *tg = tab + static_cast<int64_t>(g) * tab_ch * ntr;
+  uint32_t pk[kGroupTrials], lo32[kGroupTrials], hi32[kGroupTrials];
+#pragma unroll
+  for (int j = 0; j < kGroupTrials; ++j) pk[j] = lo32[j] = hi32[j] = 0u;
+  int since = 0;  // channels added into pk since the last drain
+  for (int c0 = 0; c0 < nch; c0 += 64) {
+    const int nc = min(64, nch - c0);
+    __syncthreads();
+    if (threadIdx.x < nc) {  // window start of each channel = its smallest delay here
+      const int c = c0 + threadIdx.x;
+      int lo = INT32_MAX;
+      for (int j = 0; j < kGroupTrials; ++j) {
+        const int jj = min(j0 + j, ntr_g - 1);
+        lo = min(lo, tg[static_cast<int64_t>(c) * ntr + jj]);
+      }
+      s_lo[threadIdx.x] = lo;
+      for (int j = 0; j < kGroupTrials; ++j) {
+        const int jj = min(j0 + j, ntr_g - 1);
+        s_del[threadIdx.x][j] = tg[static_cast<int64_t>(c) * ntr + jj] - lo;
+      }
+    }
+    __syncthreads();
+    // pair words in blocks of 4 channels: a block's 16 loads are issued
+    // before the previous block is added from shared memory and stored after
+    // it, so the loads overlap the adds; any rest of a wide window is copied
+    // directly
+    constexpr int kU = 4;
+    uint32_t va[kU][2], vb[kU][2];
+    auto load_block = [&](int cb) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int c = cb + u, i = threadIdx.x + r * kGroupThreads;
+          const bool live = c < nc && i < P;
+          const TI *row = x + static_cast<int64_t>(c0 + (live ? c : 0)) * pitch;
+          const int64_t ta = t0 + (live ? s_lo[c] : 0) + i, tb = ta + kGroupThreads;
+          va[u][r] = live && ta < n_valid ? static_cast<uint32_t>(row[ta]) : 0u;
+          vb[u][r] = live && tb < n_valid ? static_cast<uint32_t>(row[tb]) : 0u;
+        }
+      }
+    };
+    auto store_block = [&](int cb) {
+#pragma unroll
+      for (int u = 0; u < kU; ++u) {
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          const int i = threadIdx.x + r * kGroupThreads;
+          if (cb + u < nc && i < P) win[(cb + u) * P + i] = va[u][r] | (vb[u][r] << 16);
+        }
+      }
+      for (int u = 0; u < kU && cb + u < nc; ++u) {
+        const int c = cb + u;
+        const TI *row = x + static_cast<int64_t>(c0 + c) * pitch;
+        for (int i = threadIdx.x + 2 * kGroupThreads; i < P; i += kGroupThreads) {
+          const int64_t ta = t0 + s_lo[c] + i, tb = ta + kGroupThreads;
+          const uint32_t a = ta < n_valid ? static_cast<uint32_t>(row[ta]) : 0u;
+          const uint32_t b = tb < n_valid ? static_cast<uint32_t>(row[tb]) : 0u;
+          win[c * P + i] = a | (b << 16);
+        }
+      }
+    };
+    load_block(0);
+    store_block(0);
+    for (int cb = 0; cb < nc; cb += kU) {
+      const bool more = cb + kU < nc;
+      if (more) load_block(cb + kU);  // in flight during the adds below
+      __syncthreads();                // block cb stored by every thread
+      const int ce = min(cb + kU, nc);
+      for (int c = cb; c < ce; ++c) {
+        const uint32_t *w = win + c * P + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < kGroupTrials; ++j) pk[j] += w[s_del[c][j]];
+        if (++since == drain) {
+#pragma unroll
+          for (int j = 0; j < kGroupTrials; ++j) {
+            lo32[j] += pk[j] & 0xffffu;
+            hi32[j] += pk[j] >> 16;
+            pk[j] = 0u;
+          }
+          since = 0;
+        }
+      }
+      if (more) store_block(cb + kU);  // read only after the next barrier
+    }
+  }
+  const int64_t ta = t0 + threadIdx.x, tb = ta + kGroupThreads;
+#pragma unroll
+  for (int j = 0; j < kGroupTrials; ++j) {
+    if (j0 + j >= ntr_g) break;
+    TO *o = out + g * og + static_cast<int64_t>(j0 + j) * oj;
+    if (ta < nsamp_out) o[ta] = static_cast<TO>(lo32[j] + (pk[j] & 0xffffu));
+    if (tb < nsamp_out) o[tb] = static_cast<TO>(hi32[j] + (pk[j] >> 16));
+  }
+}
+
+inline size_t pairs_smem(int tab_ch, int span) {
+  return static_cast<size_t>(std::min(tab_ch, 64)) * (kGroupThreads + span) * 4;
+}
+
+template <typename TI, typename TO>
+cudaError_t launch_pairs(const TI *in, int64_t pitch, int64_t ig, const int32_t *tab, int tab_ch,
+                         int nch_total, int ngroups, int ntr, int ntr_last, int span,
+                         int64_t n_valid, int drain, TO *out, int64_t og, int64_t oj,
+                         int64_t nsamp_out, cudaStream_t s) {
+  const size_t smem = pairs_smem(tab_ch, span);
+  cudaError_t e = cudaFuncSetAttribute(dd_grouped_pairs<TI, TO>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       static_cast<int>(smem));
+  if (e != cudaSuccess) return e;
+  const dim3 grid(static_cast<unsigned>((nsamp_out + kGroupTile - 1) / kGroupTile),
+                  static_cast<unsigned>((ntr + kGroupTrials - 1) / kGroupTrials),
+                  static_cast<unsigned>(ngroups));
+  dd_grouped_pairs<TI, TO><<<grid, kGroupThreads, smem, s>>>(in, pitch, ig, tab, tab_ch,
+                                                             nch_total, ntr, ntr_last, span,
+                                                             n_valid, drain, out, og, oj,
+                                                             nsamp_out);
   return cudaGetLastError();
 }
 
@@ -471,6 +619,25 @@ extern "C" int dd_subband_execute(dd_subband *s, const void *block, int64_t nsam
   float *sbf = reinterpret_cast<float *>(sb);
   const int64_t ldsb = static_cast<int64_t>(s->nsub) * L1pad;  // SB row pitch per nominal
   const int last = s->ndm - (s->ngroups - 1) * s->dpg;
+  const int64_t max_sb = static_cast<int64_t>(s->cps) * 255;  // largest step-1 sum (u8)
+  if (s->dtype == DD_U8 && max_sb <= 65535 && pairs_smem(s->cps, s->span1) <= kGroupSmemMax &&
+      pairs_smem(s->nsub, s->span2) <= kGroupSmemMax) {
+    // u8: both steps on packed pairs, the step-1 series kept as uint16
+    uint16_t *sb16 = static_cast<uint16_t *>(s->d_sb);
+    const int64_t ig = static_cast<int64_t>(s->cps) * pitch_elems;
+    cudaError_t e = launch_pairs(static_cast<const uint8_t *>(block), pitch_elems, ig, s->d_tab1,
+                                 s->cps, s->nchan, s->nsub, s->ngroups, s->ngroups, s->span1,
+                                 nsamp_in, 65535 / 255, sb16, L1pad, ldsb, L1, st);
+    if (e == cudaSuccess) {
+      const int64_t og = static_cast<int64_t>(s->dpg) * nsamp_out;
+      e = launch_pairs(static_cast<const uint16_t *>(sb16), L1pad, ldsb, s->d_tab2, s->nsub,
+                       s->nsub * s->ngroups, s->ngroups, s->dpg, last, s->span2, L1,
+                       static_cast<int>(65535 / max_sb), static_cast<int32_t *>(out), og,
+                       nsamp_out, nsamp_out, st);
+    }
+    s->launches += 2;
+    return e == cudaSuccess ? DD_OK : DD_ERR_CUDA;
+  }
   if (grouped_smem(s->cps, s->span1, eb) <= kGroupSmemMax &&
       grouped_smem(s->nsub, s->span2, 4) <= kGroupSmemMax) {
     cudaError_t e;
