@@ -1,8 +1,9 @@
 """GPU: subband dedispersion (include/dd_subband.h) against the subband oracle
 (oracle/approx.py), and at the nominal trials against the brute-force sum.
 
-u8 input: integer sums throughout (step-1 series carried as float below
-2^24), so the comparison is exact.  Float input: step 1 and step 2 each
+u8 input: integer sums throughout (step-1 series as 16-bit integers, or
+carried as float below 2^24 for subbands wider than 257 channels), so the
+comparison is exact.  Float input: step 1 and step 2 each
 accumulate in float on the device and in double in the oracle; with the
 step-1 series rounded to float on both sides, each output agrees within
 1e-5 of the sum of |I| over the channels it adds (the bound of the
@@ -46,6 +47,7 @@ def make(wl, dtype, cps, dpg):
     (300, 70, 32, 16, 5),    # unaligned pitch: plain-load kernels in both steps
     (512, 128, 64, 32, 0),
     (256, 64, 1, 8, 0),      # one channel per subband: the brute-force sum
+    (600, 64, 300, 16, 0),   # subbands too wide for 16-bit sums: float step-1 series
 ])
 def test_subband_u8_matches_oracle_exactly(nchan, ndm, cps, dpg, pitch_pad):
     wl = geometry(nchan, ndm)
