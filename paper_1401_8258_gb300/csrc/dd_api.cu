@@ -1374,3 +1374,15 @@ extern "C" int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t 
   if (copy_ahead) *copy_ahead = p->quad ? p->quad->tables.copy_ahead : 0;
   return DD_OK;
 }
+
+// Shared memory of the staged u8 kernel's tables at staging depth
+// copy_ahead, for the CPU tests: *smem = bytes, or -1 when the tables do not
+// fit the width or the depth does not fit a CTA.
+extern "C" int ddi_quad_smem(const int32_t *delays, int32_t nchan, int32_t ndm, int32_t nd_thr,
+                             int32_t copy_ahead, int32_t *smem) {
+  ddq::Tables t;
+  *smem = -1;
+  if (ddq::build_tables(delays, nchan, ndm, nd_thr, &t) != 0) return 0;
+  if (ddq::set_copy_ahead(t, copy_ahead)) *smem = t.smem_bytes;
+  return 0;
+}

@@ -211,3 +211,34 @@ def test_tables_refuse_geometries_with_too_many_patterns():
     delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
     assert quad_tables(delays, wl.nchan, wl.ndm, ND_THR) is None
     assert quad_tables(delays, wl.nchan, wl.ndm, ND_THR // 2) is None
+
+
+@pytest.mark.parametrize("name", ["full_block_u8", "single_beam_f32"])
+def test_shared_memory_per_staging_depth(name):
+    """The kernel keeps copy_ahead + 1 window buffers and 2 + copy_ahead
+    records (plus the barrier area, the window table and two pattern-row
+    areas); depths outside 1..3 are refused."""
+    wl = synth.scaled(synth.workload(name), nchan=256, ndm=128)
+    wl.dtype = "u8"
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    lib = ctypes.CDLL(dd._native.library_path())
+    fn = lib.ddi_quad_smem
+    fn.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                   ctypes.c_int32, ctypes.c_void_p]
+    d = np.ascontiguousarray(delays, dtype=np.int32)
+    for nd_thr in (4, 2, 1):
+        tb = quad_tables(d, wl.nchan, wl.ndm, nd_thr)
+        if tb is None:
+            continue
+        meta = (tb["nchan_pad"] * 8 + 15) // 16 * 16
+        for ca in (0, 1, 2, 3, 4):
+            out = np.zeros(1, dtype=np.int32)
+            fn(d.ctypes.data, wl.nchan, wl.ndm, nd_thr, ca, out.ctypes.data)
+            want = (64 + meta + (2 + ca) * tb["rec_words"] * 4 + (ca + 1) * 16 * tb["raw_stride"]
+                    + 2 * tb["prow_words"] * 4)
+            if 1 <= ca <= 3 and want <= 227 * 1024:
+                assert out[0] == want, (nd_thr, ca)
+            else:
+                assert out[0] == -1, (nd_thr, ca)
+            if ca == 2:
+                assert out[0] == tb["smem"]
