@@ -10,6 +10,7 @@ import os
 import socket
 
 import numpy as np
+import pytest
 import torch.multiprocessing as mp
 
 
@@ -82,3 +83,32 @@ def test_single_rank_helpers_need_no_process_group():
     assert bench.max_over_ranks(2.5, 1) == 2.5
     assert bench.whole_job_rate(1, 10, 4, 2.0) == 20.0
     assert bench.replica_seed(5, 0) != bench.replica_seed(5, 1)
+
+
+@pytest.mark.parametrize("workload", ["full_block_u8", "binned8_full_block_u8"])
+def test_reference_arm_line_carries_the_contract_keys(monkeypatch, capsys, workload):
+    """Rank 0 of the reference arm prints one JSON line with the keys the
+    bench contract asks for, the oracle's rate as value, cpu_baseline and
+    e2e describing that run (a short sample)."""
+    import json
+
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    args = bench.argparse.Namespace(workload=workload, impl="reference", gpus=1, steps=1,
+                                    warmup=0, seed=1, cpu_seconds=0.2, nsamp=None)
+    bench.run_reference(args)
+    lines = [l for l in capsys.readouterr().out.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    line = json.loads(lines[0])
+    for k in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["n_gpus"] == 1
+    assert line["config"]["workload"] == workload
+    cpu = line["cpu_baseline"]
+    assert cpu["kind"] == "oracle" and cpu["cores"] >= 1 and cpu["value"] == line["value"]
+    assert cpu["sample"] and cpu["unit"] == line["unit"]
+    e2e = line["e2e"]
+    assert e2e["value"] == line["value"] and e2e["h2d_bytes_per_step"] == 0
