@@ -1,9 +1,13 @@
 """Benchmark of the dedispersion + detection hot path on GB300.
 
 One step = one pass of the whole path over one synthetic filterbank block
-resident in HBM: dd_run -- brute-force dedispersion (which also accumulates
-each DM row's exact sums and per-tile maxima), then per-DM statistics,
-n-sigma threshold, candidate list and the count to the host.
+resident in HBM: dd_run -- brute-force dedispersion, then per-DM statistics,
+n-sigma threshold, candidate list and the count to the host.  The default
+workload is the largest single-GPU configuration, ``lband_f32``: 4096
+channels x 131072 f32 samples (1200-1500 MHz, 64 us), 4096 DM trials
+0..409.5; ``--workload full_block_u8`` times the 8-bit block (1024 channels x
+65536, 2048 trials), whose dedispersion kernel also accumulates each DM row's
+exact sums and per-tile maxima.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
 
@@ -51,7 +55,7 @@ def parse():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="full_block_u8")
+    ap.add_argument("--workload", default="lband_f32")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,

@@ -349,8 +349,9 @@ int dd_plan_kernel_info(const dd_plan *p, const void *block, int64_t pitch_elems
  * before anything is queued.  The call makes no cudaMalloc, cudaFree or other
  * allocating call; it runs on the calling thread's current device.  Its first
  * call on a device looks up the array's device address
- * (cudaGetSymbolAddress), so make that first call before any stream capture.
- * Every call uses the same array and leaves its contents behind (nothing in
+ * (cudaGetSymbolAddress), and so does the first call after that device's
+ * context has been re-created (for example by cudaDeviceReset): make those
+ * first calls before any stream capture.  Every call uses the same array and leaves its contents behind (nothing in
  * it needs to start at zero): calls whose work overlaps on the GPU -- on
  * different streams, or from different host threads -- race and must be
  * serialised by the caller.  Synchronises `stream` once (to return *count). */

@@ -244,7 +244,30 @@ int validate_execute(const dd_plan *p, int64_t nsamp_in, int64_t pitch, int64_t 
   return DD_OK;
 }
 
+// The fused path (staged u8 kernel + tiled detection) totals each row's
+// S2 = sum D^2 in one 64-bit word (an unsigned atomic add per warp); with
+// |D| <= 255 * nchan the total fits when (255 * nchan)^2 * nsamp_out < 2^64.
+// Larger blocks take the unfused passes, which keep S2 in 128 bits.
+bool fused_sums_fit(int32_t nchan, int64_t nsamp_out) {
+  if (nchan < 1 || nsamp_out < 1) return false;
+  const unsigned __int128 m = static_cast<unsigned __int128>(255) * static_cast<uint32_t>(nchan);
+  const unsigned __int128 worst = m * m * static_cast<uint64_t>(nsamp_out);
+  return (worst >> 64) == 0;
+}
+
+// Whether dd_run (and a batch or stream wave) takes the fused path for a beam.
+bool fused_path(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out) {
+  return p->path == 0 && ddk::quad_supported(p, block, pitch, nsamp_out) &&
+         fused_sums_fit(p->nchan, nsamp_out);
+}
+
 }  // namespace
+
+// Host-side check of the fused path's 64-bit S2 limit, for the CPU tests (not
+// part of dd.h): 1 if (255 * nchan)^2 * nsamp_out < 2^64.
+extern "C" int ddi_fused_sums_fit(int32_t nchan, int64_t nsamp_out) {
+  return fused_sums_fit(nchan, nsamp_out) ? 1 : 0;
+}
 
 namespace {
 
@@ -520,8 +543,9 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   const cudaEvent_t ev = static_cast<cudaEvent_t>(event);
-  if (!(p->path == 0 && ddk::quad_supported(p, block, pitch_elems, nsamp_out))) {
-    // plain-load kernel: dedispersion, then the detection passes over out
+  if (!fused_path(p, block, pitch_elems, nsamp_out)) {
+    // other kernels (or S2 beyond 64 bits): dedispersion, then the
+    // detection passes over out
     st = dd_execute(p, block, nsamp_in, pitch_elems, out, stream);
     if (st != DD_OK) return st;
     if (ev && cudaEventRecord(ev, s) != cudaSuccess) return DD_ERR_CUDA;
@@ -584,7 +608,7 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
     p->stats_valid = false;
-    if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
+    if (fused_path(p, block[i], pitch_elems[i], nout[i])) {
       const int st = ensure_tile_workspace(p, static_cast<size_t>(ddk::time_tiles(nout[i])) * p->ndm);
       if (st != DD_OK) return st;
       err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);

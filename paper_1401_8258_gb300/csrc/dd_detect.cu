@@ -528,20 +528,57 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 constexpr int kNoAllocMaxDevices = 64;
 std::mutex g_noalloc_mutex;
-void *g_noalloc_addr[kNoAllocMaxDevices] = {};
+struct NoAllocSlot {
+  unsigned long long ctx_id = 0;  // context the address belongs to (0: none yet)
+  void *addr = nullptr;
+};
+NoAllocSlot g_noalloc_slot[kNoAllocMaxDevices];
 
-// Device address of the scratch array on the current device, looked up once
-// per device (cudaGetSymbolAddress; the host-side symbol is not a device
-// address).  Returns nullptr on failure.
+// Unique id of the calling thread's current context (cuCtxGetCurrent +
+// cuCtxGetId through the runtime's driver entry points, so that the library
+// needs no link against the driver library); 0 if it cannot be read.
+unsigned long long current_context_id() {
+  using GetCurrent = int (*)(void **);
+  using GetId = int (*)(void *, unsigned long long *);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  void *ctx = nullptr;
+  unsigned long long id = 0;
+  if (!get_current || !get_id || get_current(&ctx) != 0 || !ctx || get_id(ctx, &id) != 0) return 0;
+  return id;
+}
+
+// Device address of the scratch array on the current device (the host-side
+// symbol is only a stand-in, not a device address).  It is looked up with
+// cudaGetSymbolAddress on the first call on a device and again whenever the
+// device's context has been re-created since (e.g. by cudaDeviceReset), or on
+// every call if the context id cannot be read.  Returns nullptr on failure.
 void *noalloc_scratch(int device) {
   if (device < 0 || device >= kNoAllocMaxDevices) return nullptr;
+  // no context may be current yet on this thread (id 0): the lookup below
+  // makes the device's primary context current, and its id is read after it
+  const unsigned long long ctx = current_context_id();
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[device]) {
+  NoAllocSlot &slot = g_noalloc_slot[device];
+  if (ctx == 0 || slot.ctx_id != ctx || !slot.addr) {
     void *ptr = nullptr;
     if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess) return nullptr;
-    g_noalloc_addr[device] = ptr;
+    slot.addr = ptr;
+    slot.ctx_id = current_context_id();
   }
-  return g_noalloc_addr[device];
+  return slot.addr;
 }
 
 }  // namespace

@@ -120,3 +120,30 @@ def test_host_pipe_argument_errors(lib):
 def test_subband_and_binned_sync_reject_null(lib):
     assert lib.dd_subband_sync(None, None) == DD_ERR_ARG
     assert lib.dd_binned_sync(None, None) == DD_ERR_ARG
+
+
+def fused_sums_fit(nchan, nsamp_out) -> bool:
+    """The library's decision (ddi_fused_sums_fit, a host-only test hook) of
+    whether dd_run's fused path may total a row's sum of squares in 64 bits."""
+    f = _native.load().ddi_fused_sums_fit
+    f.argtypes = [ctypes.c_int32, ctypes.c_int64]
+    return bool(f(nchan, nsamp_out))
+
+
+@pytest.mark.parametrize("nchan", [1, 64, 1024, 4096, 16384, 1 << 20])
+def test_fused_sum_limit_is_exact(lib, nchan):
+    """The fused path is taken exactly while (255 nchan)^2 nsamp_out < 2^64,
+    the range of its 64-bit sum of squares; the largest such nsamp_out is
+    (2^64 - 1) // (255 nchan)^2, computed here in Python's exact integers."""
+    m2 = (255 * nchan) ** 2
+    last = (2 ** 64 - 1) // m2
+    for n in (1, 1000, last - 1, last):
+        if 1 <= n <= min(last, 2 ** 62):
+            assert fused_sums_fit(nchan, n), (nchan, n)
+    if last + 1 <= 2 ** 62:
+        assert not fused_sums_fit(nchan, last + 1)
+    assert not fused_sums_fit(nchan, 0)
+    # 16384 channels: the limit lies near 1.06 M outputs, within a block that
+    # fits GB300 memory
+    if nchan == 16384:
+        assert last == 1056816

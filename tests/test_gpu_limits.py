@@ -9,6 +9,8 @@ the block it reads).
   sample block runs through it.
 * 16384 channels: 64 drains of the u8 kernel's 16-bit partial sums into its
   32-bit sums, and exact int32 sums up to 16384 x 255.
+* Past the 64-bit limit of dd_run's fused row sums of squares, dd_run keeps
+  the statistics exact through the 128-bit passes.
 """
 import numpy as np
 import pytest
@@ -17,6 +19,7 @@ import torch
 import oracle
 import paper_1401_8258_gb300 as dd
 import synth
+from tests.test_abi_extras import fused_sums_fit
 
 pytestmark = pytest.mark.gpu
 
@@ -105,3 +108,30 @@ def test_u8_kernel_sixteen_thousand_channels():
     assert np.array_equal(mean, m) and np.array_equal(sigma, s)
     c_ref, tot = oracle.detect(ref, m, s, 3.0)
     assert total == tot and np.array_equal(cands, c_ref)
+
+
+def test_u8_run_past_the_fused_sum_limit_keeps_exact_statistics():
+    """dd_run totals each row's sum of squares in 64 bits only while
+    (255 nchan)^2 nsamp_out < 2^64; 16384 saturated channels x 1.1 M outputs
+    are past that, so dd_run must take the passes that keep it in 128 bits and
+    still give the oracle's statistics and candidates exactly.  Both trials
+    are DM 0, so each row is the plain channel sum (a pinned identity of the
+    oracle) and the block can be checked at this size in seconds."""
+    nchan, nsamp = 16384, 1_100_000
+    assert not fused_sums_fit(nchan, nsamp)
+    dms = np.zeros(2)
+    block = np.full((nchan, nsamp), 255, dtype=np.uint8)
+    rng = np.random.default_rng(24)
+    block[rng.integers(0, nchan, 40000), rng.integers(0, nsamp, 40000)] = 0
+    with dd.Plan(nchan, 1500.0, 300.0 / nchan, 64e-6, dms, "u8") as plan:
+        assert plan.maxshift == 0
+        out, cands, total = plan.run(torch.from_numpy(block).to(DEV), 0.5, capacity=0)
+        got = out.cpu().numpy()
+        mean, sigma = plan.stats()
+    row = (255 * nchan - 255 * np.count_nonzero(block == 0, axis=0)).astype(np.int32)
+    ref = np.stack([row, row])
+    assert np.array_equal(got, ref)
+    m, s = oracle.stats(ref)
+    assert np.array_equal(mean, m) and np.array_equal(sigma, s) and s[0] > 0
+    _, tot = oracle.detect(ref, m, s, 0.5, capacity=0)
+    assert total == tot > 0

@@ -93,7 +93,30 @@ def assert_parity(wl, block, res, nsamp_in=None):
     return ref
 
 
-def assert_detection(wl, ref, res, nsigma):
+def assert_float_candidates(got, D, ref, scale, mean, sigma, ref_mean, ref_sigma):
+    """Every float candidate (Sec. 3.6 triplet: DM index, time, intensity,
+    plus its S/N) against the FP64 oracle.
+
+    value: the GPU output at (d, t) itself, hence within the stated bound
+      1e-5 * sum_c |I| of the oracle's D.
+    snr: computed from the GPU's D, mean and rms; against the oracle's
+      (D - mean) / rms its error is at most
+        (|dD| + |dmean|) / rms_gpu + |snr_oracle| * |d rms| / rms_gpu
+      with |dD| <= 1e-5 * sum_c |I| and the measured differences of the row
+      statistics, plus the rounding of snr to float (2^-24 relative)."""
+    d, t = got["dm_idx"].astype(np.int64), got["t"].astype(np.int64)
+    assert np.array_equal(got["value"], D[d, t].astype(np.float32))
+    dv = np.abs(got["value"].astype(np.float64) - ref[d, t])
+    assert np.all(dv <= FLOAT_RTOL * scale[d, t]), float(np.max(dv / scale[d, t]))
+    snr_ref = (ref[d, t] - ref_mean[d]) / ref_sigma[d]
+    bound = ((FLOAT_RTOL * scale[d, t] + np.abs(mean[d] - ref_mean[d])) / sigma[d] +
+             np.abs(snr_ref) * np.abs(sigma[d] - ref_sigma[d]) / sigma[d] +
+             2.0 ** -23 * np.abs(snr_ref) + 1e-9)
+    err = np.abs(got["snr"].astype(np.float64) - snr_ref)
+    assert np.all(err <= bound), float(np.max(err - bound))
+
+
+def assert_detection(wl, ref, res, nsigma, block=None, delays=None, nsamp_in=None):
     if wl.dtype == "u8":
         mean, sigma = oracle.stats(ref)
         assert np.array_equal(res["mean"], mean)
@@ -115,6 +138,13 @@ def assert_detection(wl, ref, res, nsigma):
         assert sure <= got <= maybe
         order = list(zip(res["cands"]["dm_idx"].tolist(), res["cands"]["t"].tolist()))
         assert order == sorted(order)
+        assert res["total"] == res["cands"].size
+        if res["cands"].size:
+            assert block is not None, "float candidates need the block for their bounds"
+            scale = oracle.dedisperse(np.abs(block.astype(np.float32)), delays,
+                                      nsamp_out=ref.shape[1], nsamp_in=nsamp_in)
+            assert_float_candidates(res["cands"], res["D"], ref, scale, res["mean"],
+                                    res["sigma"], mean, sigma)
 
 
 # ------------------------------------------------------------------ tiny
@@ -137,7 +167,7 @@ def test_tiny_random_shapes(dtype, seed):
     offset = int(rng.integers(0, 5))
     res = run_plan(wl, block, nsamp_in=nsamp, offset=offset, nsigma=1.5)
     ref = assert_parity(wl, block, res, nsamp_in=nsamp)
-    assert_detection(wl, ref, res, 1.5)
+    assert_detection(wl, ref, res, 1.5, block, res["delays"], nsamp)
 
 
 @pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
@@ -183,7 +213,7 @@ def test_single_beam_full_config(dtype):
     block, pulses = synth.make_block(wl, seed=1, delays=delays)
     res = run_plan(wl, block, nsigma=6.0)
     ref = assert_parity(wl, block, res)
-    assert_detection(wl, ref, res, 6.0)
+    assert_detection(wl, ref, res, 6.0, block, delays)
     if dtype != "u8":
         report_errs(f"single_beam {dtype}", float_rel_errs(block, delays, res["D"], ref))
     p = pulses[0]
@@ -201,7 +231,7 @@ def test_full_block_geometry_reduced_size(pitch_pad, offset):
     block, _ = synth.make_block(wl, seed=2, delays=delays, pitch=wl.nsamp + pitch_pad)
     res = run_plan(wl, block, nsamp_in=wl.nsamp, offset=offset, nsigma=4.0)
     ref = assert_parity(wl, block, res, nsamp_in=wl.nsamp)
-    assert_detection(wl, ref, res, 4.0)
+    assert_detection(wl, ref, res, 4.0, block, delays, wl.nsamp)
 
 
 def test_full_block_u8_full_size_sampled_rows():
@@ -235,17 +265,46 @@ def test_full_block_u8_full_size_sampled_rows():
 
 @pytest.mark.parametrize("dtype", ["f32", "f16"])
 def test_lband_full_size_sampled_rows(dtype):
-    """4096 ch x 131072, 4096 trials DM 0..409.5 with narrowband RFI: sampled
-    rows within 1e-5 of the FP64 oracle (relative to the sum of |I|)."""
+    """4096 ch x 131072, 4096 trials DM 0..409.5 with narrowband RFI, detected
+    at 6 sigma in the launch configuration the bench times: sampled rows
+    within 1e-5 of the FP64 oracle (relative to the sum of |I|), their
+    statistics within 1e-5, and their candidates (set, order, value, snr)
+    against the oracle's; the pulse is found at its trial and time."""
     wl = synth.workload("lband_" + dtype)
     delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
     block, pulses = synth.make_block(wl, seed=1, delays=delays)
-    res = run_plan(wl, block)
-    rows = [0, 1, 2048, 4094, 4095, pulses[0].dm_idx]
-    ref = oracle.dedisperse(block, delays[:, rows], nsamp_out=res["D"].shape[1])
-    errs = float_rel_errs(block, delays, res["D"][rows], ref, rows=rows)
+    nsigma = 6.0
+    with dd.Plan(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms, wl.dtype) as plan:
+        out, cands, total = plan.run(_to_dev(block), nsigma)
+        mean_g, sigma_g = plan.stats()
+        D = out.cpu().numpy()
+    del out
+    assert total == cands.size
+    p = pulses[0]
+    rows = [0, 1, 2048, 4094, 4095, p.dm_idx]
+    ref = oracle.dedisperse(block, delays[:, rows], nsamp_out=D.shape[1])
+    errs = float_rel_errs(block, delays, D[rows], ref, rows=rows)
     report_errs(f"lband {dtype} (rows {rows})", errs)
     assert errs.max() <= FLOAT_RTOL
+    mean, sigma = oracle.stats(ref)
+    np.testing.assert_allclose(mean_g[rows], mean, rtol=1e-5, atol=1e-4 * np.sqrt(wl.nchan))
+    np.testing.assert_allclose(sigma_g[rows], sigma, rtol=1e-5)
+    scale = oracle.dedisperse(np.abs(block.astype(np.float32)), delays[:, rows],
+                              nsamp_out=D.shape[1])
+    band = BAND * max(1.0, abs(nsigma))
+    for i, r in enumerate(rows):
+        snr = (ref[i] - mean[i]) / sigma[i]
+        mine = cands[cands["dm_idx"] == r]
+        got = set(mine["t"].tolist())
+        assert set(np.flatnonzero(snr > nsigma + band).tolist()) <= got
+        assert got <= set(np.flatnonzero(snr > nsigma - band).tolist())
+        assert np.all(np.diff(mine["t"]) > 0)
+        sub = mine.copy()
+        sub["dm_idx"] = i
+        assert_float_candidates(sub, D[rows], ref, scale, mean_g[rows], sigma_g[rows],
+                                mean, sigma)
+    hit = (cands["dm_idx"] == p.dm_idx) & (cands["t"] >= p.t0) & (cands["t"] < p.t0 + p.width)
+    assert hit.any()
 
 
 # ------------------------------------------------------------ error paths
