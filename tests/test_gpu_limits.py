@@ -125,7 +125,8 @@ def test_u8_run_past_the_fused_sum_limit_keeps_exact_statistics():
     block[rng.integers(0, nchan, 40000), rng.integers(0, nsamp, 40000)] = 0
     with dd.Plan(nchan, 1500.0, 300.0 / nchan, 64e-6, dms, "u8") as plan:
         assert plan.maxshift == 0
-        out, cands, total = plan.run(torch.from_numpy(block).to(DEV), 0.5, capacity=0)
+        # the full columns sit about 0.19 sigma above the mean
+        out, cands, total = plan.run(torch.from_numpy(block).to(DEV), 0.1, capacity=0)
         got = out.cpu().numpy()
         mean, sigma = plan.stats()
     row = (255 * nchan - 255 * np.count_nonzero(block == 0, axis=0)).astype(np.int32)
@@ -133,5 +134,5 @@ def test_u8_run_past_the_fused_sum_limit_keeps_exact_statistics():
     assert np.array_equal(got, ref)
     m, s = oracle.stats(ref)
     assert np.array_equal(mean, m) and np.array_equal(sigma, s) and s[0] > 0
-    _, tot = oracle.detect(ref, m, s, 0.5, capacity=0)
+    _, tot = oracle.detect(ref, m, s, 0.1, capacity=0)
     assert total == tot > 0
