@@ -233,6 +233,8 @@ int setup_octet(dd_plan *p) {
     p->octet = make_octet(p, w, &st);
     if (p->octet || st != DD_OK) break;
   }
+  if (st == DD_OK && p->octet && cudaMalloc(&p->d_next_item, sizeof(unsigned long long)) != cudaSuccess)
+    st = DD_ERR_OOM;
   return st;
 }
 

@@ -80,7 +80,7 @@ struct dd_plan {
   size_t d_cands_cap = 0;
 
   QuadDevice *quad = nullptr;       // staged u8 kernel tables (null: not applicable)
-  unsigned long long *d_next_item = nullptr;  // work-queue head of the staged u8 kernel
+  unsigned long long *d_next_item = nullptr;  // work-queue head of the staged kernels
   OctetDevice *octet = nullptr;     // staged f16/f32 kernel tables (null: not applicable)
   int32_t path = 0;                 // 0 = automatic, 1 = plain-load kernel only
   uint64_t wait_timeout_ns = 2000000000ull;  // bound on every device-side wait
@@ -134,11 +134,20 @@ int launch_quad_beams(const ddq::Beam *beams, int nbeams, int nd_thr, int copy_a
                       int32_t skip_copies, cudaStream_t stream, cudaError_t *err);
 constexpr int kTileSamples = ddq::kTimeTile;
 // Staged octet kernel (f16 / f32): needs the plan's octet tables, a 16-byte
-// aligned block, a pitch of a whole number of 16-byte units and at most
-// 65535 time tiles.
+// aligned block and a pitch of a whole number of 16-byte units.
 bool octet_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
 int launch_dedisperse_octet(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                             void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err);
+// The staged octet kernel is persistent too: one launch drains a queue of
+// (beam, DM tile, time tile) items over up to ddo::kMaxBeams beams of one
+// input dtype and one nd_thr (kNdThr or kNdThr/2); smem is the largest of
+// the beams' shared-memory sizes.
+ddo::Beam octet_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
+                     void *out, int64_t out_pitch);
+int launch_octet_beams(const ddo::Beam *beams, int nbeams, int32_t dtype, int nd_thr, int smem,
+                       int device_sms, unsigned long long *next_item, int32_t *status,
+                       uint64_t timeout_ns, int32_t skip_copies, cudaStream_t stream,
+                       cudaError_t *err);
 inline int64_t time_tiles(int64_t nsamp_out) { return (nsamp_out + kTileSamples - 1) / kTileSamples; }
 
 // Detection passes over out[ndm][nsamp_out]; see dd_detect in dd.h.

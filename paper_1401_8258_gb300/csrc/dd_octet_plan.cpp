@@ -21,6 +21,8 @@
 namespace {
 
 inline int32_t round_up(int32_t v, int32_t m) { return (v + m - 1) / m * m; }
+// largest multiple of m not above v (v may be negative)
+inline int32_t floor_to(int32_t v, int32_t m) { return (v >= 0 ? v / m : -((-v + m - 1) / m)) * m; }
 
 }  // namespace
 
@@ -71,16 +73,21 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
       for (int o = 0; o < no; ++o) {
         const int c0 = kGroup * (o_lo + o);
         const int nreal = std::min(kGroup, nchan - c0);
+        // the reference channel whose delay every pattern is relative to:
+        // channel kRefChan of the octet (the middle, which keeps the other
+        // channels' relative delays small), or its last real channel when
+        // the octet has fewer; padding channels read zeros at any shift
+        const int cref = c0 + std::min(kRefChan, nreal - 1);
         // distinct relative patterns of the real channels
         std::vector<std::array<int32_t, kGroup>> pats;
         std::vector<int> pid(nd_cta);
         int32_t b = INT32_MAX, bmax = INT32_MIN;
         for (int i = 0; i < nd_cta; ++i) {
-          const int32_t d0 = delay(tile, c0, i);
+          const int32_t d0 = delay(tile, cref, i);
           b = std::min(b, d0);
           bmax = std::max(bmax, d0);
           std::array<int32_t, kGroup> rel{};
-          for (int k = 1; k < nreal; ++k) rel[k] = delay(tile, c0 + k, i) - d0;
+          for (int k = 0; k < nreal; ++k) rel[k] = delay(tile, c0 + k, i) - d0;
           auto it = std::find(pats.begin(), pats.end(), rel);
           pid[i] = static_cast<int>(it - pats.begin());
           if (it == pats.end()) pats.push_back(rel);
@@ -101,8 +108,10 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
           if (emax - emin > kMaxShift) return 1;
           for (int p = 0; p < O.npat; ++p) O.shift[p][k] = pats[p][k] - emin;
           if (!O.pad[k]) {
-            // window: times b + emin .. b + emax + L - 1
-            start[c] = (b + emin) / align * align;
+            // window: times b + emin .. b + emax + L - 1; for channels below
+            // the reference it may start before the first time tile's first
+            // sample (the kernel then clips the copy: no output reads there)
+            start[c] = floor_to(b + emin, align);
             O.raw_off[k] = b + emin - start[c];
             need[c] = O.raw_off[k] + (emax - emin) + O.L;
             raw_stride = std::max(raw_stride, round_up(need[c], align));
@@ -111,7 +120,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
           }
         }
         for (int i = 0; i < nd_cta; ++i)
-          A[o * nd_cta + i] = row_words + pid[i] * O.L + delay(tile, c0, i) - b;
+          A[o * nd_cta + i] = row_words + pid[i] * O.L + delay(tile, cref, i) - b;
         row_words += O.npat * O.L;
         octs.push_back(O);
       }
@@ -127,7 +136,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
   // raw-buffer element offsets must fit 16 bits (zero area first)
   const int64_t raw_elems = static_cast<int64_t>(kGroup) * t.opc * raw_stride;
   if (kZeroElems + raw_elems + 32 + kMaxShift >= 0xffff) return 1;
-  constexpr int kWarps = kThreads / 32;
+  constexpr int kWarps = kBuildWarps;
   for (size_t rc = 0; rc < chunk_octets.size(); ++rc) {
     int32_t *rec = &t.recs[rc * t.rec_words];
     std::vector<std::array<int32_t, kUnitWords>> list;
@@ -136,12 +145,21 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
       for (int first = 0; first < O.L; first += 32) {
         std::array<int32_t, kUnitWords> u{};
         u[0] = (O.row_off + first) | (std::min(32, O.L - first) << 20);
-        // fast: every channel's shift is 0 or 1 in every pattern
-        bool fast = true;
-        for (int p = 0; p < O.npat; ++p)
-          for (int k = 0; k < kGroup; ++k)
-            if (!O.pad[k] && O.shift[p][k] > 1) fast = false;
-        u[1] = O.npat | (O.L << 8) | (fast ? 1 << 30 : 0);
+        // per channel, the largest shift over the patterns; the unit's bound
+        // is the largest over its channels if at most 2 (the kernel then
+        // loads each channel's candidate samples once and selects per
+        // pattern), 0 otherwise (it loads each pattern's samples)
+        int32_t smax = 0;
+        uint32_t chan_bounds = 0;
+        for (int k = 0; k < kGroup; ++k) {
+          int32_t b = 0;
+          for (int p = 0; p < O.npat; ++p)
+            if (!O.pad[k]) b = std::max(b, O.shift[p][k]);
+          chan_bounds |= static_cast<uint32_t>(b) << (2 * k);
+          smax = std::max(smax, b);
+        }
+        const int32_t bound = smax <= 2 ? std::max(smax, 1) : 0;
+        u[1] = O.npat | (O.L << 8) | (bound << 29);
         for (int k = 0; k < kGroup; ++k) {
           // element offsets from the start of the zero area; the raw buffer
           // follows it (kZeroElems elements)
@@ -152,12 +170,16 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
                                                O.raw_off[k] + first);
           u[2 + k / 2] |= static_cast<int32_t>(e << (16 * (k & 1)));
         }
+        // pattern-major shift codes: word kCodesWord + p/2, 16 bits per
+        // pattern (two patterns per word), channel k's shift at bits 2k ..
+        // 2k+1 of its half; the reference channel's shift is 0
         for (int p = 0; p < O.npat; ++p) {
           uint32_t code = 0;
           for (int k = 0; k < kGroup; ++k)
             code |= static_cast<uint32_t>(O.pad[k] ? 0 : O.shift[p][k]) << (2 * k);
-          u[6 + p / 2] |= static_cast<int32_t>(code << (16 * (p & 1)));
+          u[kCodesWord + p / 2] |= static_cast<int32_t>(code << (16 * (p & 1)));
         }
+        u[kBoundsWord] = static_cast<int32_t>(chan_bounds);
         list.push_back(u);
       }
     }
@@ -165,12 +187,19 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     // balance: costliest unit first onto the least loaded warp
     std::vector<int> order(list.size());
     for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
-    auto cost = [&](int i) { return 1 + (list[i][1] & 0xff); };  // loads ~ one pattern
+    // instructions of a unit, roughly: per pattern and channel a select per
+    // candidate past the first and an add, plus the candidate loads (or, on
+    // the general path, 8 loads and adds per pattern)
+    auto cost = [&](int i) {
+      const int32_t npat = list[i][1] & 0xff, bound = (list[i][1] >> 29) & 3;
+      return bound ? 8 * (bound + 1) + npat * (7 * (1 + 2 * bound) + 3) : 4 + 24 * npat;
+    };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
     std::vector<int> load(kWarps, 0);
     std::vector<std::vector<int>> per_warp(kWarps);
     for (int i : order) {
-      const int w = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+      const int w = static_cast<int>(
+          std::min_element(load.begin() + kFirstBuilder, load.end()) - load.begin());
       load[w] += cost(i);
       per_warp[w].push_back(i);
     }

@@ -2,9 +2,9 @@
 sampled output ranges (each range computed by the oracle from the slice of
 the block it reads).
 
-* The staged float kernel takes at most 65535 time tiles of 256 samples; a
-  block one output past that runs on the plain-load kernel.  Both sides of
-  the limit must give the oracle's sums.
+* The staged float kernel is persistent, so its time tiles have no grid
+  limit: 65535 x 256 outputs and one more (the old grid-row limit) both run
+  on it and must give the oracle's sums.
 * The staged u8 kernel's work queue has no tile-count limit: a 20-million-
   sample block runs through it.
 * 16384 channels: 64 drains of the u8 kernel's 16-bit partial sums into its
@@ -54,8 +54,7 @@ def check_ranges(block, delays, got, n_out, dtype):
 
 @pytest.mark.parametrize("extra", [0, 1])
 def test_float_kernel_time_tile_limit(extra):
-    """nsamp_out = 65535 x 256 (+1): the last staged size and the first that
-    falls back to the plain-load kernel."""
+    """nsamp_out = 65535 x 256 (+1): both sizes on the staged kernel."""
     # L-band channel spacing, trials far enough apart for non-zero delays and
     # close enough for the staged kernel's tables
     nchan, f_top, df, ts = 8, 1500.0, 300.0 / 4096, 64e-6

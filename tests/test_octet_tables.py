@@ -21,10 +21,13 @@ GROUP = 8
 T_TILE = 256
 REC_HEADER = 4
 UNIT_WORDS = 16
+CODES_WORD = 8  # shift codes within a unit, two patterns per word
+BOUNDS_WORD = 6
+REF_CHAN = 3
 MAX_OCTETS_PER_CHUNK = 2
 MAX_UNITS = 64
 ZERO_ELEMS = 64
-NWARPS = 16
+NWARPS = 12  # building warps
 ND_THR = 8  # DM trials per thread of the 128-trial tile (16 warps x 8); 4 for 64
 SENTINEL = 1e30
 
@@ -80,38 +83,49 @@ def emulate(block, tb, ndm, nsamp_out):
                     if need <= 0:
                         assert c >= nchan
                         continue
+                    # the window, clipped to the row: a channel below the
+                    # reference may start before the first sample
                     off = t_cta + start
-                    n = (need * es + 15) // 16 * 16 // es
-                    if off + n > pitch:
-                        n = pitch - off
-                    assert off >= 0 and off % align == 0 and n % align == 0 and 0 < n <= rs
+                    hi = min(off + (need * es + 15) // 16 * 16 // es, pitch)
+                    lo = max(off, 0)
+                    assert off % align == 0 and hi % align == 0 and 0 < hi - off <= rs
+                    assert off >= -rs
                     base = ZERO_ELEMS + s * rs
-                    stage[base:base + n] = block[c, off:off + n]
+                    stage[base + lo - off:base + hi - off] = block[c, lo:hi]
                 no, nunits = rec[2], rec[3]
+                # the kernel reads each unit's header (words 0..7) as two
+                # 16-byte vectors; the record sits 16-byte aligned in shared
+                # memory
+                assert (units_off * 4) % 16 == 0 and (UNIT_WORDS * 4) % 16 == 0
+                assert CODES_WORD + 8 <= UNIT_WORDS
+                assert (REC_HEADER * 4) % 16 == 0 and (tb["rec_words"] * 4) % 16 == 0
                 units = rec[units_off:units_off + UNIT_WORDS * nunits].reshape(-1, UNIT_WORDS)
                 starts = rec[units_off + UNIT_WORDS * MAX_UNITS:].view(np.uint16)[:NWARPS + 1]
                 assert starts[0] == 0 and starts[NWARPS] == nunits
                 assert np.all(np.diff(starts.astype(int)) >= 0)
+                assert starts[1] == 0  # building warp 0 queues the copies and builds nothing
                 prow = np.full(pw, SENTINEL)
                 written = np.zeros(pw, dtype=np.int64)
                 for u in units.astype(np.int64) & 0xFFFFFFFF:
                     dest0, items = u[0] & 0xFFFFF, (u[0] >> 20) & 63
-                    npat, L, fast = u[1] & 0xFF, (u[1] >> 8) & 0xFFFF, (u[1] >> 30) & 1
+                    npat, L, bound = u[1] & 0xFF, (u[1] >> 8) & 0x1FFFFF, (u[1] >> 29) & 3
                     assert 1 <= items <= 32 and 1 <= npat <= 16 and L % 4 == 0
                     offs = [(u[2 + k // 2] >> (16 * (k & 1))) & 0xFFFF for k in range(GROUP)]
+                    chan_bound = [(u[BOUNDS_WORD] >> (2 * k)) & 3 for k in range(GROUP)]
                     lanes = np.arange(items)
                     for p in range(npat):
-                        code = (u[6 + p // 2] >> (16 * (p & 1))) & 0xFFFF
                         words = dest0 + p * L + lanes
                         assert words.max() < pw
                         written[words] += 1
                         v = np.zeros(items)
+                        code = (u[CODES_WORD + p // 2] >> (16 * (p & 1))) & 0xFFFF
                         for k in range(GROUP):
                             sh = (code >> (2 * k)) & 3
-                            if k == 0:
+                            if k == REF_CHAN:  # the patterns' delay origin
                                 assert sh == 0
-                            if fast:  # the kernel then only loads shifts 0 and 1
-                                assert sh <= 1
+                            if bound:  # the kernel then only loads shifts 0 .. bound
+                                assert sh <= bound
+                            assert sh <= chan_bound[k]  # and per channel 0 .. its bound
                             idx = offs[k] + lanes + sh
                             if offs[k] < ZERO_ELEMS:  # padding channel: inside the zero area
                                 assert idx.max() < ZERO_ELEMS
@@ -139,6 +153,7 @@ CASES = [
     # (workload, nchan, ndm, samples past maxshift, pitch pad in elements, esize)
     ("lband_f32", 512, 70, 600, 8, 4),
     ("lband_f32", 509, 64, 900, 0, 2),    # padding channels in the last octet, f16 layout
+    ("lband_f32", 515, 66, 800, 4, 4),    # last octet of 3 channels: its reference is channel 2
     ("lband_f32", 1024, 130, 700, 0, 2),
     ("full_block_u8", 256, 64, 800, 4, 4),
 ]
@@ -159,6 +174,10 @@ def test_octet_kernel_model_matches_oracle(name, nchan, ndm, extra, pad, esize):
     rng = np.random.default_rng(5)
     block = rng.integers(-8, 9, size=(nchan, pitch)).astype(np.float64)
     block[:, nsamp:] = 1e6  # row padding must never reach a stored output
+    # the first DM tile starts at DM 0, where the reference channel's delay is
+    # 0 while channels below it have negative relative delays at the tile's
+    # larger DMs: their windows start before the first sample (clipped)
+    assert (tb["meta"][0, :nchan, 0] < 0).any()
     got = emulate(block, tb, ndm, nsamp - mx)
     ref = oracle.dedisperse(block[:, :nsamp].astype(np.float32), delays, nsamp_in=nsamp)
     assert np.array_equal(got, ref)
