@@ -182,11 +182,16 @@ OctetDevice *make_octet(const dd_plan *p, int nd_thr, int *st) {
   q->tables = std::move(t);
   const size_t rb = q->tables.recs.size() * sizeof(int32_t);
   const size_t mb = q->tables.raw_meta.size() * sizeof(int32_t);
+  const size_t sb = q->tables.skew.size() * sizeof(int32_t);
   cudaError_t e = cudaMalloc(&q->d_recs, rb);
-  if (e == cudaSuccess) e = cudaMalloc(&q->d_raw_meta, mb);
+  // the queue skews follow the window table in the same allocation
+  if (e == cudaSuccess) e = cudaMalloc(&q->d_raw_meta, mb + sb);
   if (e == cudaSuccess) e = cudaMemcpy(q->d_recs, q->tables.recs.data(), rb, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(q->d_raw_meta + q->tables.raw_meta.size(), q->tables.skew.data(), sb,
+                   cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_octet(q);
     *st = cuda_status(e);

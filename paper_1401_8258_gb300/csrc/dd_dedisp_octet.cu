@@ -12,14 +12,13 @@
 //      by the largest and smallest delay of the tile -- plus the chunk's plan
 //      record into shared memory, signalling an mbarrier, two chunks ahead of
 //      the chunk being built;
-//   2. 8 building warps build pattern rows: word i of a row holds, for one
+//   2. 11 building warps build pattern rows: word i of a row holds, for one
 //      relative-delay pattern of an octet of channels, the eight channels'
 //      FP32 sum at output time i (dd_octet_plan.cpp); they build chunk k+1
 //      while the accumulating warps add chunk k (double-buffered rows);
 //   3. 16 accumulating warps add, for each of their DM trials and output
-//      samples, one row word per octet into FP32 register accumulators (two
-//      samples per packed add.f32x2): eight channel-samples per add and per
-//      shared-memory word.
+//      samples, one row word per octet into FP32 register accumulators:
+//      eight channel-samples per add and per shared-memory word.
 // The two roles split the launch's registers (setmaxnreg): the accumulating
 // warps hold 64 accumulators per thread, the building warps need few.
 // The kernel is persistent: each CTA takes work items (beam, DM tile, time
@@ -97,62 +96,24 @@ __device__ __forceinline__ void stsf(uint32_t addr, float v) {
   asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
 }
 
-// acc += {word at a + OFF0, word at a + OFF1}: two row words of one trial
-// (output samples 32 apart) added to a packed pair of accumulators.
-template <int OFF0, int OFF1>
-__device__ __forceinline__ void acc_pair(unsigned long long &acc, uint32_t a) {
-  asm volatile(
-      "{\n\t.reg .f32 x, y;\n\t.reg .b64 p;\n\t"
-      "ld.shared.f32 x, [%1+%2];\n\t"
-      "ld.shared.f32 y, [%1+%3];\n\t"
-      "mov.b64 p, {x, y};\n\t"
-      "add.rn.f32x2 %0, %0, p;\n\t}"
-      : "+l"(acc)
-      : "r"(a), "n"(OFF0), "n"(OFF1));
+// acc[j] += row word at a + 128 j (output sample lane + 32 j of one trial),
+// j = J .. kTimesPerThread-1, each load at a compile-time offset
+template <int OFF>
+__device__ __forceinline__ float ldsf_off(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+  return v;
 }
-
-// acc += word at a + OFF: one row word of one trial added to one accumulator
-// (kept in one half of a 64-bit pair, so that both forms share a layout).
-template <int OFF, int HALF>
-__device__ __forceinline__ void acc_one(unsigned long long &acc, uint32_t a) {
-  if (HALF == 0)
-    asm volatile(
-        "{\n\t.reg .f32 x, lo, hi;\n\t"
-        "ld.shared.f32 x, [%1+%2];\n\t"
-        "mov.b64 {lo, hi}, %0;\n\t"
-        "add.rn.f32 lo, lo, x;\n\t"
-        "mov.b64 %0, {lo, hi};\n\t}"
-        : "+l"(acc)
-        : "r"(a), "n"(OFF));
-  else
-    asm volatile(
-        "{\n\t.reg .f32 x, lo, hi;\n\t"
-        "ld.shared.f32 x, [%1+%2];\n\t"
-        "mov.b64 {lo, hi}, %0;\n\t"
-        "add.rn.f32 hi, hi, x;\n\t"
-        "mov.b64 %0, {lo, hi};\n\t}"
-        : "+l"(acc)
-        : "r"(a), "n"(OFF));
-}
-
-// acc[J/2] += row words J, J+1 of one trial, J = 0, 2, .., kTimesPerThread-2
 template <int J>
 struct AccRow {
-  static __device__ __forceinline__ void run(unsigned long long (&acc)[kTimesPerThread / 2],
-                                             uint32_t a) {
-    if (kAccPairs) {
-      acc_pair<128 * J, 128 * (J + 1)>(acc[J / 2], a);
-    } else {
-      acc_one<128 * J, 0>(acc[J / 2], a);
-      acc_one<128 * (J + 1), 1>(acc[J / 2], a);
-    }
-    AccRow<J + 2>::run(acc, a);
+  static __device__ __forceinline__ void run(float (&acc)[kTimesPerThread], uint32_t a) {
+    acc[J] += ldsf_off<128 * J>(a);
+    AccRow<J + 1>::run(acc, a);
   }
 };
 template <>
 struct AccRow<kTimesPerThread> {
-  static __device__ __forceinline__ void run(unsigned long long (&)[kTimesPerThread / 2],
-                                             uint32_t) {}
+  static __device__ __forceinline__ void run(float (&)[kTimesPerThread], uint32_t) {}
 };
 
 __device__ __forceinline__ void setmaxnreg_inc_acc() {
@@ -291,9 +252,10 @@ __device__ __forceinline__ void build_unit(const int32_t *ud, uint32_t zero, uin
 #pragma unroll 1
     for (uint32_t p = 0; p < npat; ++p) {
       const uint32_t code = codes[p >> 1] >> (16 * (p & 1));
-      float v = E::widen(E::load(addr[0] + es * (code & 3u)));
+      auto shift = [&](int k) { return (code >> (2 * k)) & 3u; };
+      float v = E::widen(E::load(addr[0] + es * shift(0)));
 #pragma unroll
-      for (int k = 1; k < kGroup; ++k) v = E::add(v, E::load(addr[k] + es * ((code >> (2 * k)) & 3u)));
+      for (int k = 1; k < kGroup; ++k) v = E::add(v, E::load(addr[k] + es * shift(k)));
       stsf(dst + p * row_bytes, v);
     }
   }
@@ -335,15 +297,35 @@ struct Item {
   int beam, tile;
   int64_t t_cta;
 };
+// Queue slot `item` as (beam, DM tile, time tile); false for an empty slot
+// (the DM tile's time tile, after its skew, outside the beam's block).
+__device__ __forceinline__ bool decode_item(const OctetLaunch &L, long long item, Item *it) {
+  int b = 0;
+  while (b + 1 < L.nbeams && item >= L.beams[b + 1].item_begin) ++b;
+  const Beam &a = L.beams[b];
+  const long long local = item - a.item_begin;
+  const int tile = static_cast<int>(local % a.ntiles_dm);
+  const long long ttile = local / a.ntiles_dm - __ldg(a.skew + tile);
+  it->beam = b;
+  it->tile = tile;
+  it->t_cta = ttile * kTimeTile;
+  return ttile >= 0 && ttile < a.ntiles_t;
+}
+
+// Next non-empty queue slot (one thread per CTA): the slot number, or
+// total_items when the queue is drained.
+__device__ __forceinline__ long long fetch_item(const OctetLaunch &L) {
+  for (;;) {
+    const long long item = static_cast<long long>(atomicAdd(L.next_item, 1ull));
+    Item it;
+    if (item >= L.total_items || decode_item(L, item, &it)) return item;
+  }
+}
+
 __device__ __forceinline__ bool next_item(const OctetLaunch &L, const uint8_t *smem, Item *it) {
   const long long item = *reinterpret_cast<const volatile long long *>(smem + kItemSlot);
   if (item >= L.total_items) return false;
-  int b = 0;
-  while (b + 1 < L.nbeams && item >= L.beams[b + 1].item_begin) ++b;
-  const long long local = item - L.beams[b].item_begin;
-  it->beam = b;
-  it->tile = static_cast<int>(local % L.beams[b].ntiles_dm);
-  it->t_cta = static_cast<int64_t>(local / L.beams[b].ntiles_dm) * kTimeTile;
+  decode_item(L, item, it);
   return true;
 }
 
@@ -375,8 +357,7 @@ __device__ __forceinline__ void build_role(const OctetLaunch &L, uint8_t *smem, 
   volatile int32_t *abort_at = reinterpret_cast<volatile int32_t *>(smem + kAbortSlot);
   for (;;) {
     if (btid == 0) {
-      *reinterpret_cast<volatile long long *>(smem + kItemSlot) =
-          static_cast<long long>(atomicAdd(L.next_item, 1ull));
+      *reinterpret_cast<volatile long long *>(smem + kItemSlot) = fetch_item(L);
       *abort_at = INT32_MAX;
     }
     bar_sync(kBarItem, kThreads);
@@ -473,11 +454,11 @@ __device__ __forceinline__ void acc_role(const OctetLaunch &L, uint8_t *smem, in
     if (!next_item(L, smem, &it)) return;
     const Beam &a = L.beams[it.beam];
     const Lay lay(bar0, a);
-    unsigned long long acc[ND_THR][kTimesPerThread / 2];
+    float acc[ND_THR][kTimesPerThread];
 #pragma unroll
     for (int i = 0; i < ND_THR; ++i)
 #pragma unroll
-      for (int j = 0; j < kTimesPerThread / 2; ++j) acc[i][j] = 0ull;
+      for (int j = 0; j < kTimesPerThread; ++j) acc[i][j] = 0.f;
     bool aborted = false;
     for (int k = 0; k < a.nchunks; ++k) {
       bar_sync(kBarFull + k % kRowStages, kThreads);
@@ -512,12 +493,9 @@ __device__ __forceinline__ void acc_role(const OctetLaunch &L, uint8_t *smem, in
         if (d >= a.ndm) continue;
         float *orow = a.out + static_cast<int64_t>(d) * a.out_pitch;
 #pragma unroll
-        for (int j = 0; j < kTimesPerThread; j += 2) {
-          float lo, hi;
-          asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(acc[i][j / 2]));
+        for (int j = 0; j < kTimesPerThread; ++j) {
           const int64_t t = it.t_cta + lane + 32 * j;
-          if (t < a.nsamp_out) orow[t] = lo;
-          if (t + 32 < a.nsamp_out) orow[t + 32] = hi;
+          if (t < a.nsamp_out) orow[t] = acc[i][j];
         }
       }
     }
@@ -583,6 +561,8 @@ ddo::Beam octet_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t
   b.out = static_cast<float *>(out);
   b.recs = q.d_recs;
   b.raw_meta = q.d_raw_meta;
+  b.skew = q.d_raw_meta + q.tables.raw_meta.size();
+  b.max_skew = q.tables.max_skew;
   b.pitch_bytes = pitch * elem_size(p->dtype);
   b.nsamp_out = nsamp_out;
   b.out_pitch = out_pitch;
@@ -612,7 +592,7 @@ int launch_octet_beams(const ddo::Beam *beams, int nbeams, int32_t dtype, int nd
   for (int i = 0; i < nbeams; ++i) {
     L.beams[i] = beams[i];
     L.beams[i].item_begin = items;
-    items += static_cast<int64_t>(beams[i].ntiles_dm) * beams[i].ntiles_t;
+    items += static_cast<int64_t>(beams[i].ntiles_dm) * (beams[i].ntiles_t + beams[i].max_skew);
   }
   L.nbeams = nbeams;
   L.total_items = items;

@@ -78,9 +78,6 @@ constexpr int kAccThreads = 32 * kDmGroups;              // 512 accumulating thr
 #ifndef DDO_ACC_REGS
 #define DDO_ACC_REGS 80
 #endif
-#ifndef DDO_ACC_PAIRS
-#define DDO_ACC_PAIRS 0
-#endif
 #ifndef DDO_DEDICATED_ISSUER
 #define DDO_DEDICATED_ISSUER 1
 #endif
@@ -88,9 +85,6 @@ constexpr int kBuildWarps = DDO_BUILD_WARPS;
 // Building warp 0 queues the copies; with kFirstBuilder = 1 it builds no
 // rows (its share of the build units goes to the other building warps).
 constexpr int kFirstBuilder = DDO_DEDICATED_ISSUER ? 1 : 0;
-// Accumulation: two output samples per packed add.f32x2 (1), or one FADD per
-// sample (0).
-constexpr bool kAccPairs = DDO_ACC_PAIRS != 0;
 constexpr int kBuildThreads = 32 * kBuildWarps;          // 384 building threads
 constexpr int kThreads = kAccThreads + kBuildThreads;    // 896
 // Register split of the two roles (setmaxnreg): the launch gives every
@@ -158,6 +152,12 @@ struct Tables {
   int32_t smem_bytes = 0;
   std::vector<int32_t> recs;      // [ntiles][nchunks][rec_words]
   std::vector<int32_t> raw_meta;  // [ntiles][nchan_pad][2]
+  // Work-queue order: DM tile T runs its time tiles skew[T] places later in
+  // the queue, skew[T] = the tile's smallest delay of the channel whose
+  // largest delay is nearest half the plan's largest, in time tiles; so the
+  // items in flight together read nearby input samples at every DM.
+  std::vector<int32_t> skew;      // [ntiles]
+  int32_t max_skew = 0;
 };
 
 // Shared-memory layout: mbarriers (kBarrierBytes), kRecStages records,
@@ -176,18 +176,21 @@ inline int32_t smem_bytes(const Tables &t) {
 
 // One beam of a launch of the (persistent) staged kernel: its block, output,
 // tables and work items.  Work item i of the launch belongs to the last beam
-// with item_begin <= i; within the beam, item (i - item_begin) is DM tile
-// (i - item_begin) % ntiles_dm of time tile (i - item_begin) / ntiles_dm.
+// with item_begin <= i; within the beam, slot j = i - item_begin is DM tile
+// T = j % ntiles_dm of time tile j / ntiles_dm - skew[T], an empty slot when
+// that is outside 0 .. ntiles_t-1 (ntiles_dm * (ntiles_t + max_skew) slots).
 struct Beam {
   const uint8_t *block;
   float *out;
   const int32_t *recs;
   const int32_t *raw_meta;
+  const int32_t *skew;  // [ntiles_dm] time-tile offset of each DM tile in the queue
   int64_t pitch_bytes;  // bytes per channel row (multiple of 16)
   int64_t nsamp_out;
   int64_t out_pitch;    // elements between output rows (>= nsamp_out)
   int64_t item_begin;
   int32_t ndm, nchunks, nchan_pad, rec_words, raw_stride, prow_words, ntiles_dm, ntiles_t;
+  int32_t max_skew;
 };
 constexpr int kMaxBeams = 64;  // beams per launch (the descriptors travel as kernel parameters)
 

@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <array>
 #include <cstdint>
+#include <cstdlib>
 #include <vector>
 
 #include "dd_octet.h"
@@ -215,6 +216,27 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     }
     starts[kWarps] = static_cast<uint16_t>(n);
     rec[3] = n;
+  }
+  // queue skew: the reference channel of the order is the one whose largest
+  // delay is nearest half the largest of any channel
+  {
+    int32_t maxd = 0;
+    for (int64_t i = 0; i < static_cast<int64_t>(nchan) * ndm; ++i) maxd = std::max(maxd, delays[i]);
+    int cmid = 0;
+    int64_t best = INT64_MAX;
+    for (int c = 0; c < nchan; ++c) {
+      int32_t dc = 0;
+      for (int d = 0; d < ndm; ++d) dc = std::max(dc, delays[static_cast<int64_t>(c) * ndm + d]);
+      const int64_t gap = std::llabs(2 * static_cast<int64_t>(dc) - maxd);
+      if (gap < best) best = gap, cmid = c;
+    }
+    t.skew.assign(t.ntiles, 0);
+    for (int tile = 0; tile < t.ntiles; ++tile) {
+      int32_t b = INT32_MAX;
+      for (int i = 0; i < nd_cta; ++i) b = std::min(b, delay(tile, cmid, i));
+      t.skew[tile] = b / kTimeTile;
+      t.max_skew = std::max(t.max_skew, t.skew[tile]);
+    }
   }
   t.raw_stride = raw_stride;
   t.prow_words = prow_words;
