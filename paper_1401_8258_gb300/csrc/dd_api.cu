@@ -64,8 +64,9 @@ int ensure_chunk_workspace(dd_plan *p, size_t entries) {
 }
 
 // Grows the fused path's per-(row, time tile) workspace; the per-row arrays
-// are allocated with it on first use.
-int ensure_tile_workspace(dd_plan *p, size_t entries) {
+// are allocated with it on first use.  Integer rows keep each tile's maximum
+// (int32), float rows each tile's partial statistics (float4).
+int ensure_tile_workspace(dd_plan *p, size_t entries, bool float_rows = false) {
   if (!p->d_rowsums) {
     ++p->ws_gen;
     if (cudaMalloc(&p->d_rowsums, 2 * sizeof(int64_t) * p->ndm) != cudaSuccess ||
@@ -77,18 +78,27 @@ int ensure_tile_workspace(dd_plan *p, size_t entries) {
       return DD_ERR_OOM;
     }
   }
-  if (entries <= p->tile_cap) return DD_OK;
-  free_device(p->d_tilemax);
-  free_device(p->d_tilecount);
-  p->tile_cap = 0;
-  ++p->ws_gen;
-  if (cudaMalloc(&p->d_tilemax, entries * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&p->d_tilecount, entries * sizeof(int32_t)) != cudaSuccess) {
+  if (entries > p->tile_cap || (!float_rows && !p->d_tilemax)) {
     free_device(p->d_tilemax);
     free_device(p->d_tilecount);
-    return DD_ERR_OOM;
+    p->tile_cap = 0;
+    ++p->ws_gen;
+    const size_t cap = std::max(entries, p->tile_cap);
+    if ((!float_rows && cudaMalloc(&p->d_tilemax, cap * sizeof(int32_t)) != cudaSuccess) ||
+        cudaMalloc(&p->d_tilecount, cap * sizeof(int32_t)) != cudaSuccess) {
+      free_device(p->d_tilemax);
+      free_device(p->d_tilecount);
+      return DD_ERR_OOM;
+    }
+    p->tile_cap = cap;
   }
-  p->tile_cap = entries;
+  if (float_rows && entries > p->tilestats_cap) {
+    free_device(p->d_tilestats);
+    p->tilestats_cap = 0;
+    ++p->ws_gen;
+    if (cudaMalloc(&p->d_tilestats, entries * sizeof(float4)) != cudaSuccess) return DD_ERR_OOM;
+    p->tilestats_cap = entries;
+  }
   return DD_OK;
 }
 
@@ -134,6 +144,7 @@ void destroy_plan(dd_plan *p) {
   free_device(p->d_rowoff);
   free_device(p->d_tilemax);
   free_device(p->d_tilecount);
+  free_device(p->d_tilestats);
   free_device(p->d_block);
   free_device(p->d_out);
   free_device(p->d_cands);
@@ -443,7 +454,8 @@ extern "C" int dd_execute_pitched(dd_plan *p, const void *block, int64_t nsamp_i
     n = ddk::launch_dedisperse_quad(p, block, pitch_elems, nsamp_out, out, out_pitch, nullptr,
                                     nullptr, s, &err);
   else if (p->path == 0 && ddk::octet_supported(p, block, pitch_elems, nsamp_out))
-    n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, out_pitch, s, &err);
+    n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, out_pitch, nullptr, s,
+                                     &err);
   else
     n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, out_pitch, s, &err);
   if (n < 0) return cuda_status(err);
@@ -550,6 +562,31 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   const cudaEvent_t ev = static_cast<cudaEvent_t>(event);
+  if (p->path == 0 && ddk::octet_supported(p, block, pitch_elems, nsamp_out)) {
+    // staged float kernel with per-tile partial statistics, then the tiled
+    // detection passes
+    st = ensure_tile_workspace(p, static_cast<size_t>(ddk::octet_tiles(nsamp_out)) * p->ndm,
+                               true);
+    if (st != DD_OK) return st;
+    p->stats_valid = false;
+    cudaError_t err = cudaSuccess;
+    int n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, nsamp_out,
+                                         p->d_tilestats, s, &err);
+    if (n < 0) return cuda_status(err);
+    p->launches += n;
+    if (ev && cudaEventRecord(ev, s) != cudaSuccess) return DD_ERR_CUDA;
+    n = ddk::launch_tiled_detect_f32(p, out, nsamp_out, nsigma, cands, capacity, s, &err);
+    if (n < 0) return cuda_status(err);
+    p->launches += n;
+    err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    if (err != cudaSuccess) return cuda_status(err);
+    st = take_device_status(p);
+    if (st != DD_OK) return st;
+    p->stats_valid = true;
+    *count = *p->h_total;
+    return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
+  }
   if (!fused_path(p, block, pitch_elems, nsamp_out)) {
     // other kernels (or S2 beyond 64 bits): dedispersion, then the
     // detection passes over out
@@ -611,7 +648,7 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
   // staged u8 beams, by DM-tile width (64, 32, 16 trials) and staging
   // depth; the rest take their own kernels
   std::vector<int> staged[kQuadGroups];
-  std::vector<char> is_staged(n, 0);
+  std::vector<char> is_staged(n, 0);  // 1: staged u8 (fused), 2: staged float (fused)
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
     p->stats_valid = false;
@@ -622,6 +659,16 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
       if (err != cudaSuccess) return cuda_status(err);
       staged[quad_group(p)].push_back(i);
       is_staged[i] = 1;
+    } else if (p->path == 0 && ddk::octet_supported(p, block[i], pitch_elems[i], nout[i])) {
+      // staged float kernel with per-tile statistics, as dd_run
+      const int st = ensure_tile_workspace(
+          p, static_cast<size_t>(ddk::octet_tiles(nout[i])) * p->ndm, true);
+      if (st != DD_OK) return st;
+      const int nl = ddk::launch_dedisperse_octet(p, block[i], pitch_elems[i], nout[i], out[i],
+                                                  nout[i], p->d_tilestats, s, &err);
+      if (nl < 0) return cuda_status(err);
+      p->launches += nl;
+      is_staged[i] = 2;
     } else {
       const int st = dd_execute(p, block[i], nsamp_in[i], pitch_elems[i], out[i], stream);
       if (st != DD_OK) return st;
@@ -657,8 +704,11 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
     int nl;
-    if (is_staged[i]) {
+    if (is_staged[i] == 1) {
       nl = ddk::launch_tiled_detect(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
+    } else if (is_staged[i] == 2) {
+      nl = ddk::launch_tiled_detect_f32(p, out[i], nout[i], nsigma, cands[i], capacity[i], s,
+                                        &err);
     } else {
       const int64_t nchunks = (nout[i] + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
       const int st = ensure_chunk_workspace(p, static_cast<size_t>(nchunks) * p->ndm);
@@ -1290,7 +1340,7 @@ extern "C" int dd_plan_autotune(dd_plan *p, int64_t nsamp_in, int32_t *dms_per_c
       const int n = u8 ? ddk::launch_dedisperse_quad(p, blk, pitch, nsamp_out, out, nsamp_out,
                                                      nullptr, nullptr, s, &le)
                        : ddk::launch_dedisperse_octet(p, blk, pitch, nsamp_out, out, nsamp_out,
-                                                      s, &le);
+                                                      nullptr, s, &le);
       if (n < 0) e = le;
       if (e == cudaSuccess) e = cudaEventRecord(e1, s);
       if (e == cudaSuccess) e = cudaEventSynchronize(e1);

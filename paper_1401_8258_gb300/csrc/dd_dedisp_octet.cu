@@ -490,12 +490,37 @@ __device__ __forceinline__ void acc_role(const OctetLaunch &L, uint8_t *smem, in
 #pragma unroll
       for (int i = 0; i < ND_THR; ++i) {
         const int d = it.tile * ND_CTA + warp * ND_THR + i;
-        if (d >= a.ndm) continue;
+        if (d >= a.ndm) continue;  // the same for the whole warp
         float *orow = a.out + static_cast<int64_t>(d) * a.out_pitch;
 #pragma unroll
         for (int j = 0; j < kTimesPerThread; ++j) {
           const int64_t t = it.t_cta + lane + 32 * j;
           if (t < a.nsamp_out) orow[t] = acc[i][j];
+        }
+        if (a.tilestats) {
+          // this trial's partial statistics over the tile (one warp holds
+          // all its samples): sums of y = x - K about the tile's first
+          // output K, of y^2, and the largest output, in a fixed order
+          const float K = __shfl_sync(0xffffffffu, acc[i][0], 0);
+          float s1 = 0.f, s2 = 0.f, mx = -INFINITY;
+#pragma unroll
+          for (int j = 0; j < kTimesPerThread; ++j) {
+            if (it.t_cta + lane + 32 * j < a.nsamp_out) {
+              const float y = acc[i][j] - K;
+              s1 += y;
+              s2 = fmaf(y, y, s2);
+              mx = fmaxf(mx, acc[i][j]);
+            }
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) {
+            s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+            s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+          }
+          if (lane == 0)
+            a.tilestats[static_cast<int64_t>(d) * a.ntiles_t + it.t_cta / kTimeTile] =
+                make_float4(K, s1, s2, mx);
         }
       }
     }
@@ -553,7 +578,7 @@ bool octet_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t
 }
 
 ddo::Beam octet_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                     void *out, int64_t out_pitch) {
+                     void *out, int64_t out_pitch, float4 *tilestats) {
   const OctetDevice &q = *p->octet;
   Beam b;
   std::memset(&b, 0, sizeof(b));
@@ -562,6 +587,7 @@ ddo::Beam octet_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t
   b.recs = q.d_recs;
   b.raw_meta = q.d_raw_meta;
   b.skew = q.d_raw_meta + q.tables.raw_meta.size();
+  b.tilestats = tilestats;
   b.max_skew = q.tables.max_skew;
   b.pitch_bytes = pitch * elem_size(p->dtype);
   b.nsamp_out = nsamp_out;
@@ -609,8 +635,9 @@ int launch_octet_beams(const ddo::Beam *beams, int nbeams, int32_t dtype, int nd
 }
 
 int launch_dedisperse_octet(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                            void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err) {
-  const Beam b = octet_beam(p, block, pitch, nsamp_out, out, out_pitch);
+                            void *out, int64_t out_pitch, float4 *tilestats, cudaStream_t stream,
+                            cudaError_t *err) {
+  const Beam b = octet_beam(p, block, pitch, nsamp_out, out, out_pitch, tilestats);
   return launch_octet_beams(&b, 1, p->dtype, p->octet->tables.nd_thr, p->octet->tables.smem_bytes,
                             p->sm_count, p->d_next_item, p->d_error, p->wait_timeout_ns,
                             p->debug_skip_copies, stream, err);

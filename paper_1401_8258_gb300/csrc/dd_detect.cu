@@ -303,11 +303,9 @@ dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__
   }
 }
 
-// ---- tiled detection after the staged kernel ----
+// ---- tiled detection after the staged kernels ----
 
 constexpr int kTileThreads = 256;
-constexpr int kTileSamp = ddk::kTileSamples;          // 512 samples per tile
-constexpr int kTilePer = kTileSamp / kTileThreads;   // 2 consecutive samples per thread
 constexpr int kTileList = 1024;                       // tiles examined per round
 
 // Exclusive prefix of v over the CTA (kTileThreads threads); *total gets the sum.
@@ -334,34 +332,25 @@ __device__ __forceinline__ int block_exclusive(int v, int *total) {
   return before + inc - v;
 }
 
-// One CTA per row d: statistics from rowsums[d], then the candidates of each
-// tile whose maximum reaches the threshold; tilecount[d][*] and rowcount[d].
-__global__ void __launch_bounds__(kTileThreads)
-dd_tile_count(const int32_t *__restrict__ D, int64_t n, int ntiles, double thr,
-              const long long *__restrict__ rowsums, const int32_t *__restrict__ tilemax,
-              dd_row_stats *__restrict__ stats, int32_t *__restrict__ tilecount,
-              int64_t *__restrict__ rowcount) {
-  __shared__ dd_row_stats s_st;
+// Row d's candidates per tile of TILE samples: the tiles that `reaches(tt)`
+// admits (their largest value passes the threshold; no other tile can hold a
+// candidate) are read and counted into tcnt[tt], the others get 0; the row
+// total goes to *rowcount.  Called by the whole CTA after st is final.
+template <typename T, int TILE, typename Reaches>
+__device__ void count_row_tiles(const T *__restrict__ row, int64_t n, int ntiles,
+                                const dd_row_stats &st, Reaches reaches,
+                                int32_t *__restrict__ tcnt, int64_t *__restrict__ rowcount) {
+  constexpr int kPer = TILE / kTileThreads;  // consecutive samples per thread
+  static_assert(TILE % kTileThreads == 0, "whole samples per thread");
   __shared__ int s_list[kTileList];
   __shared__ int s_nlist;
-  const int d = blockIdx.x;
-  if (threadIdx.x == 0) {
-    const unsigned long long s2 = static_cast<unsigned long long>(rowsums[2 * d + 1]);
-    s_st = finish_i32(rowsums[2 * d], static_cast<unsigned __int128>(s2), n, thr);
-    stats[d] = s_st;
-  }
-  __syncthreads();
-  const dd_row_stats st = s_st;
-  const int32_t *row = D + static_cast<int64_t>(d) * n;
-  const int32_t *tmax = tilemax + static_cast<int64_t>(d) * ntiles;
-  int32_t *tcnt = tilecount + static_cast<int64_t>(d) * ntiles;
   int64_t total = 0;  // thread 0
   for (int base = 0; base < ntiles; base += kTileList) {
     if (threadIdx.x == 0) s_nlist = 0;
     __syncthreads();
     for (int k = threadIdx.x; k < kTileList && base + k < ntiles; k += kTileThreads) {
       const int tt = base + k;
-      if (st.any && static_cast<int64_t>(tmax[tt]) >= st.ithr) {
+      if (st.any && reaches(tt)) {
         s_list[atomicAdd(&s_nlist, 1)] = tt;  // order irrelevant: counts go by tile
       } else {
         tcnt[tt] = 0;
@@ -371,11 +360,10 @@ dd_tile_count(const int32_t *__restrict__ D, int64_t n, int ntiles, double thr,
     const int nl = s_nlist;
     for (int k = 0; k < nl; ++k) {
       const int tt = s_list[k];
-      const int64_t t0 = static_cast<int64_t>(tt) * kTileSamp + threadIdx.x * kTilePer;
+      const int64_t t0 = static_cast<int64_t>(tt) * TILE + threadIdx.x * kPer;
       int mine = 0;
 #pragma unroll
-      for (int u = 0; u < kTilePer; ++u)
-        mine += (t0 + u < n && is_candidate(row[t0 + u], st)) ? 1 : 0;
+      for (int u = 0; u < kPer; ++u) mine += (t0 + u < n && is_candidate(row[t0 + u], st)) ? 1 : 0;
       int tile_total = 0;
       block_exclusive(mine, &tile_total);
       if (threadIdx.x == 0) {
@@ -385,22 +373,118 @@ dd_tile_count(const int32_t *__restrict__ D, int64_t n, int ntiles, double thr,
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) rowcount[d] = total;
+  if (threadIdx.x == 0) *rowcount = total;
 }
 
-// One CTA per row with candidates: tiles in time order, each tile's
-// candidates in time order, at rowoff[d] + (candidates of earlier tiles).
+// One CTA per row d (int32 rows after the staged u8 kernel): statistics from
+// rowsums[d], then the candidates of each tile whose maximum reaches the
+// threshold; tilecount[d][*] and rowcount[d].
 __global__ void __launch_bounds__(kTileThreads)
-dd_tile_write(const int32_t *__restrict__ D, int64_t n, int ntiles,
+dd_tile_count(const int32_t *__restrict__ D, int64_t n, int ntiles, double thr,
+              const long long *__restrict__ rowsums, const int32_t *__restrict__ tilemax,
+              dd_row_stats *__restrict__ stats, int32_t *__restrict__ tilecount,
+              int64_t *__restrict__ rowcount) {
+  __shared__ dd_row_stats s_st;
+  const int d = blockIdx.x;
+  if (threadIdx.x == 0) {
+    const unsigned long long s2 = static_cast<unsigned long long>(rowsums[2 * d + 1]);
+    s_st = finish_i32(rowsums[2 * d], static_cast<unsigned __int128>(s2), n, thr);
+    stats[d] = s_st;
+  }
+  __syncthreads();
+  const dd_row_stats st = s_st;
+  const int32_t *tmax = tilemax + static_cast<int64_t>(d) * ntiles;
+  count_row_tiles<int32_t, ddk::kTileSamples>(
+      D + static_cast<int64_t>(d) * n, n, ntiles, st,
+      [&](int tt) { return static_cast<int64_t>(tmax[tt]) >= st.ithr; },
+      tilecount + static_cast<int64_t>(d) * ntiles, rowcount + d);
+}
+
+// Running (count, mean, sum of squared deviations) of float samples, merged
+// pairwise by the parallel-variance update (Chan, Golub and LeVeque): exact
+// in real arithmetic for any split, evaluated in FP64 in a fixed order.
+struct Moments {
+  double n, mean, m2;
+};
+__device__ __forceinline__ Moments merge(const Moments &a, const Moments &b) {
+  if (a.n == 0.0) return b;
+  if (b.n == 0.0) return a;
+  const double n = a.n + b.n;
+  const double dl = b.mean - a.mean;
+  return {n, a.mean + dl * (b.n / n), a.m2 + b.m2 + dl * dl * (a.n * b.n / n)};
+}
+
+// One CTA per row d (float rows after the staged float kernel): each tile's
+// partials {K, S1 = sum (D - K), S2 = sum (D - K)^2, max} give its moments
+// (mean K + S1/n_t, m2 = S2 - S1^2/n_t, in FP64); thread t merges a
+// contiguous run of tiles in order, then the threads' moments are merged in
+// a fixed tree.  mean and the population rms sqrt(m2 / n) then give the row's
+// float threshold (the same bisection as dd_stats_f32), and the tiles whose
+// maximum reaches it are counted.
+template <int TILE>
+__global__ void __launch_bounds__(kTileThreads)
+dd_tile_count_f32(const float *__restrict__ D, int64_t n, int ntiles, double thr,
+                  const float4 *__restrict__ tilestats, dd_row_stats *__restrict__ stats,
+                  int32_t *__restrict__ tilecount, int64_t *__restrict__ rowcount) {
+  __shared__ double s_m[3][kTileThreads];
+  __shared__ dd_row_stats s_st;
+  const int d = blockIdx.x;
+  const float4 *ts = tilestats + static_cast<int64_t>(d) * ntiles;
+  const int per = (ntiles + kTileThreads - 1) / kTileThreads;
+  Moments m = {0.0, 0.0, 0.0};
+  for (int tt = threadIdx.x * per; tt < (threadIdx.x + 1) * per && tt < ntiles; ++tt) {
+    const float4 v = ts[tt];
+    const int64_t rest = n - static_cast<int64_t>(tt) * TILE;
+    const double nt = static_cast<double>(rest < TILE ? rest : TILE);
+    const double s1 = v.y, s2 = v.z;
+    const double m2 = s2 - s1 * (s1 / nt);
+    m = merge(m, {nt, static_cast<double>(v.x) + s1 / nt, m2 > 0.0 ? m2 : 0.0});
+  }
+  s_m[0][threadIdx.x] = m.n, s_m[1][threadIdx.x] = m.mean, s_m[2][threadIdx.x] = m.m2;
+  __syncthreads();
+  for (int w = kTileThreads / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      const Moments a = {s_m[0][threadIdx.x], s_m[1][threadIdx.x], s_m[2][threadIdx.x]};
+      const Moments b = {s_m[0][threadIdx.x + w], s_m[1][threadIdx.x + w],
+                         s_m[2][threadIdx.x + w]};
+      const Moments c = merge(a, b);
+      s_m[0][threadIdx.x] = c.n, s_m[1][threadIdx.x] = c.mean, s_m[2][threadIdx.x] = c.m2;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    dd_row_stats st;
+    st.mean = s_m[1][0];
+    st.sigma = sqrt(s_m[2][0] / static_cast<double>(n));
+    st.any = st.sigma > 0.0;
+    st.fthr = st.any ? float_threshold(st.mean, st.sigma, thr) : INFINITY;
+    st.ithr = static_cast<int64_t>(INT32_MAX) + 1;
+    s_st = st;
+    stats[d] = st;
+  }
+  __syncthreads();
+  const dd_row_stats st = s_st;
+  count_row_tiles<float, TILE>(
+      D + static_cast<int64_t>(d) * n, n, ntiles, st, [&](int tt) { return ts[tt].w >= st.fthr; },
+      tilecount + static_cast<int64_t>(d) * ntiles, rowcount + d);
+}
+
+// One CTA per row with candidates: tiles of TILE samples in time order, each
+// tile's candidates in time order, at rowoff[d] + (candidates of earlier
+// tiles).
+template <typename T, int TILE>
+__global__ void __launch_bounds__(kTileThreads)
+dd_tile_write(const T *__restrict__ D, int64_t n, int ntiles,
               const dd_row_stats *__restrict__ stats, const int32_t *__restrict__ tilecount,
               const int64_t *__restrict__ rowcount, const int64_t *__restrict__ rowoff,
               dd_candidate *__restrict__ cands, int64_t capacity) {
+  constexpr int kPer = TILE / kTileThreads;
   const int d = blockIdx.x;
   if (rowcount[d] == 0) return;  // uniform across the CTA
   int64_t run = rowoff[d];
   if (run >= capacity) return;
   const dd_row_stats st = stats[d];
-  const int32_t *row = D + static_cast<int64_t>(d) * n;
+  const T *row = D + static_cast<int64_t>(d) * n;
   const int32_t *tcnt = tilecount + static_cast<int64_t>(d) * ntiles;
   __shared__ int s_cnt[kTileList];
   for (int base = 0; base < ntiles && run < capacity; base += kTileList) {
@@ -411,10 +495,10 @@ dd_tile_write(const int32_t *__restrict__ D, int64_t n, int ntiles,
     const int lim = ntiles - base < kTileList ? ntiles - base : kTileList;
     for (int k = 0; k < lim && run < capacity; ++k) {
       if (s_cnt[k] == 0) continue;  // same in every thread
-      const int64_t t0 = static_cast<int64_t>(base + k) * kTileSamp + threadIdx.x * kTilePer;
+      const int64_t t0 = static_cast<int64_t>(base + k) * TILE + threadIdx.x * kPer;
       unsigned mask = 0;
 #pragma unroll
-      for (int u = 0; u < kTilePer; ++u)
+      for (int u = 0; u < kPer; ++u)
         if (t0 + u < n && is_candidate(row[t0 + u], st)) mask |= 1u << u;
       int tile_total = 0;
       int64_t idx = run + block_exclusive(__popc(mask), &tile_total);
@@ -499,9 +583,29 @@ int launch_tiled_detect(dd_plan *p, const void *out, int64_t nsamp_out, float ns
   dd_scan<<<1, kScanThreads, 0, stream>>>(p->d_rowcount, p->ndm, p->d_rowoff, p->d_total);
   int n = 2;
   if (capacity > 0) {
-    dd_tile_write<<<p->ndm, kTileThreads, 0, stream>>>(D, nsamp_out, ntiles, p->d_stats,
-                                                       p->d_tilecount, p->d_rowcount,
-                                                       p->d_rowoff, cands, capacity);
+    dd_tile_write<int32_t, kTileSamples><<<p->ndm, kTileThreads, 0, stream>>>(
+        D, nsamp_out, ntiles, p->d_stats, p->d_tilecount, p->d_rowcount, p->d_rowoff, cands,
+        capacity);
+    ++n;
+  }
+  *err = cudaGetLastError();
+  return *err == cudaSuccess ? n : -1;
+}
+
+int launch_tiled_detect_f32(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                            dd_candidate *cands, int64_t capacity, cudaStream_t stream,
+                            cudaError_t *err) {
+  const int ntiles = static_cast<int>(octet_tiles(nsamp_out));
+  const float *D = static_cast<const float *>(out);
+  dd_tile_count_f32<kOctetTileSamples><<<p->ndm, kTileThreads, 0, stream>>>(
+      D, nsamp_out, ntiles, static_cast<double>(nsigma), p->d_tilestats, p->d_stats,
+      p->d_tilecount, p->d_rowcount);
+  dd_scan<<<1, kScanThreads, 0, stream>>>(p->d_rowcount, p->ndm, p->d_rowoff, p->d_total);
+  int n = 2;
+  if (capacity > 0) {
+    dd_tile_write<float, kOctetTileSamples><<<p->ndm, kTileThreads, 0, stream>>>(
+        D, nsamp_out, ntiles, p->d_stats, p->d_tilecount, p->d_rowcount, p->d_rowoff, cands,
+        capacity);
     ++n;
   }
   *err = cudaGetLastError();

@@ -70,6 +70,8 @@ struct dd_plan {
   int32_t *d_tilemax = nullptr;     // [ndm * ntiles] largest output of each time tile
   int32_t *d_tilecount = nullptr;   // [ndm * ntiles] candidates per time tile
   size_t tile_cap = 0;              // entries allocated in d_tilemax / d_tilecount
+  float4 *d_tilestats = nullptr;    // [ndm * ntiles] float rows: per-tile partial statistics
+  size_t tilestats_cap = 0;         // entries allocated in d_tilestats
 
   // buffers owned for dd_process_host
   void *d_block = nullptr;
@@ -136,14 +138,23 @@ constexpr int kTileSamples = ddq::kTimeTile;
 // Staged octet kernel (f16 / f32): needs the plan's octet tables, a 16-byte
 // aligned block and a pitch of a whole number of 16-byte units.
 bool octet_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
+// With tilestats non-null it also writes each (row, 256-sample time tile)'s
+// partial statistics {K, sum (D - K), sum (D - K)^2, max D} (K the tile's
+// first output) to tilestats[d * ntiles + tile] (octet_tiles(nsamp_out)
+// tiles per row), for launch_tiled_detect_f32.
 int launch_dedisperse_octet(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                            void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err);
+                            void *out, int64_t out_pitch, float4 *tilestats, cudaStream_t stream,
+                            cudaError_t *err);
+constexpr int kOctetTileSamples = ddo::kTimeTile;
+inline int64_t octet_tiles(int64_t nsamp_out) {
+  return (nsamp_out + kOctetTileSamples - 1) / kOctetTileSamples;
+}
 // The staged octet kernel is persistent too: one launch drains a queue of
 // (beam, DM tile, time tile) items over up to ddo::kMaxBeams beams of one
 // input dtype and one nd_thr (kNdThr or kNdThr/2); smem is the largest of
 // the beams' shared-memory sizes.
 ddo::Beam octet_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                     void *out, int64_t out_pitch);
+                     void *out, int64_t out_pitch, float4 *tilestats);
 int launch_octet_beams(const ddo::Beam *beams, int nbeams, int32_t dtype, int nd_thr, int smem,
                        int device_sms, unsigned long long *next_item, int32_t *status,
                        uint64_t timeout_ns, int32_t skip_copies, cudaStream_t stream,
@@ -163,5 +174,11 @@ int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsig
 int launch_tiled_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
                         dd_candidate *cands, int64_t capacity, cudaStream_t stream,
                         cudaError_t *err);
+// The same from the staged float kernel's per-tile partial statistics
+// (float rows): each row's mean and rms combine its tiles' partials in a
+// fixed order in FP64; candidates as launch_candidates.
+int launch_tiled_detect_f32(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
+                            dd_candidate *cands, int64_t capacity, cudaStream_t stream,
+                            cudaError_t *err);
 
 }  // namespace ddk

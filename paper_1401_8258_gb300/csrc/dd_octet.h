@@ -47,6 +47,8 @@
 // reference channel), elements needed (0 = padding channel)}.
 #pragma once
 
+#include <cuda_runtime.h>
+
 #include <cstdint>
 #include <vector>
 
@@ -185,6 +187,9 @@ struct Beam {
   const int32_t *recs;
   const int32_t *raw_meta;
   const int32_t *skew;  // [ntiles_dm] time-tile offset of each DM tile in the queue
+  // [ndm][ntiles_t] per (trial, time tile): {K, sum (D - K), sum (D - K)^2,
+  // max D} over the tile's outputs, K its first output (null: none kept)
+  float4 *tilestats;
   int64_t pitch_bytes;  // bytes per channel row (multiple of 16)
   int64_t nsamp_out;
   int64_t out_pitch;    // elements between output rows (>= nsamp_out)

@@ -269,3 +269,44 @@ def test_staging_depths_give_identical_results(depth):
         dd._native.dd_plan_inject_fault(p1.handle, 0)
         out, cands, total = p1.run(dblock, 4.0)
         assert np.array_equal(out.cpu().numpy(), ref) and total == tot
+
+
+FLOAT_CASES = [
+    # (nchan, ndm, samples past maxshift, pitch pad, dtype, nsigma)
+    (1024, 128, 1500, 0, "f32", 4.0),
+    (1021, 70, 700, 8, "f16", 3.0),    # padding channels and trials, pitch padding, ragged tail
+    (512, 64, 257, 0, "f32", -1.0),    # nearly every tile holds candidates
+    (256, 64, 900, 0, "f32", 1e9),     # none
+]
+
+
+@pytest.mark.parametrize("nchan,ndm,extra,pad,dtype,nsigma", FLOAT_CASES)
+def test_run_float_fused_statistics_and_candidates(nchan, ndm, extra, pad, dtype, nsigma):
+    """dd_run on the staged float kernel keeps per-tile partial statistics in
+    its epilogue and reads the output only in tiles that can hold a
+    candidate.  Its output is dd_execute's bit for bit; its statistics agree
+    with the separate statistics pass to 1e-6 (both FP64 evaluations of the
+    same rows); statistics and candidates (set, order, value, snr) against the
+    FP64 oracle as in the parity tests (Sec. 3.5, 3.6)."""
+    from tests.test_gpu_parity import assert_detection
+    base = synth.workload("lband_f32")
+    wl = synth.scaled(base, nchan=nchan, ndm=ndm)
+    wl.chan_width_mhz = base.chan_width_mhz
+    wl.dtype = dtype
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    nsamp = mx + extra
+    pitch = (nsamp + 7) // 8 * 8 + pad
+    block = synth.random_block(np.random.default_rng(31), nchan, nsamp, dtype, pitch)
+    block[:, nsamp:] = 1e4  # row padding must never reach an output or a statistic
+    sep, run = both_paths(wl, block, nsigma, capacity=1 << 20, nsamp_in=nsamp)
+    assert torch.equal(sep["out"], run["out"])
+    np.testing.assert_allclose(run["mean"], sep["mean"], rtol=1e-6, atol=1e-6 * np.sqrt(nchan))
+    np.testing.assert_allclose(run["sigma"], sep["sigma"], rtol=1e-6)
+    ref = oracle.dedisperse(block[:, :nsamp], delays)
+    res = {"D": run["out"].cpu().numpy(), "cands": run["cands"], "total": run["total"],
+           "mean": run["mean"], "sigma": run["sigma"]}
+    assert_detection(wl, ref, res, nsigma, block[:, :nsamp], delays)
+    if nsigma > 100:
+        assert run["total"] == 0
+    if nsigma < 0:
+        assert run["total"] > ref.size // 2
