@@ -96,6 +96,19 @@ int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz, double chan_w
  * plan's device first. */
 int dd_plan_destroy(dd_plan *p);
 
+/* A plan of the same geometry as `src` (channels, band, sampling, DM list,
+ * input dtype, device, kernel path and tile width) that shares src's
+ * plan-time tables -- the delay table and the staged kernels' records and
+ * windows, read only -- instead of building and storing its own; its
+ * workspaces, statistics and status word are its own, so the two plans may
+ * be run independently (each on one stream at a time), in the same batch or
+ * stream wave.  For the identical beams of a multi-beam receiver (the
+ * thesis's back-end dedisperses several beams of one geometry per GPU,
+ * Sec. 3.4).  Shared tables are freed with the last plan that holds them;
+ * retuning a plan (dd_plan_autotune) gives it tables of its own.  Returns
+ * DD_ERR_ARG for a NULL argument, DD_ERR_OOM / DD_ERR_CUDA on failure. */
+int dd_plan_create_like(dd_plan **out, const dd_plan *src);
+
 /* A plan for an explicit delay table instead of the dispersion law: host
  * int32 delays[nchan][ndm] (channel-major, copied), every entry in
  * 0 .. 2^30; out[d][t] = sum_c block[c][t + delays[c][d]] with the same

@@ -49,6 +49,17 @@ class Plan:
                                      device)
         self.maxshift = dd_plan_max_delay(self.handle)
 
+    @classmethod
+    def like(cls, other: "Plan") -> "Plan":
+        """A plan of ``other``'s geometry that shares its tables
+        (dd_plan_create_like): its own workspaces, no table build."""
+        p = cls.__new__(cls)
+        p.nchan, p.dms, p.ndm, p.dtype, p.device = (other.nchan, other.dms, other.ndm,
+                                                     other.dtype, other.device)
+        p.handle = _native.dd_plan_create_like(other.handle)
+        p.maxshift = dd_plan_max_delay(p.handle)
+        return p
+
     def close(self) -> None:
         if getattr(self, "handle", None):
             dd_plan_destroy(self.handle)

@@ -54,6 +54,7 @@ SIGNATURES = [
     ("dd_compute_delays", ctypes.c_int, [_i32, _f64, _f64, _f64, _vp, _i32, _vp, _vp]),
     ("dd_plan_create", ctypes.c_int, [_vp, _i32, _f64, _f64, _f64, _vp, _i32, _i32, _i32]),
     ("dd_plan_destroy", ctypes.c_int, [_vp]),
+    ("dd_plan_create_like", ctypes.c_int, [_vp, _vp]),
     ("dd_plan_max_delay", ctypes.c_int, [_vp, _vp]),
     ("dd_plan_nsamp_out", ctypes.c_int, [_vp, _i64, _vp]),
     ("dd_plan_delays", ctypes.c_int, [_vp, _vp]),
@@ -187,6 +188,13 @@ def dd_plan_create(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dms, dtype, devic
     _check(load().dd_plan_create(ctypes.addressof(handle), int(nchan), float(f_top_mhz),
                                  float(chan_width_mhz), float(t_samp_s), dms.ctypes.data,
                                  int(dms.size), code, int(device)), "dd_plan_create")
+    return handle.value
+
+
+def dd_plan_create_like(src):
+    """A plan of src's geometry sharing its tables; returns the handle."""
+    handle = ctypes.c_void_p()
+    _check(load().dd_plan_create_like(ctypes.addressof(handle), src), "dd_plan_create_like")
     return handle.value
 
 

@@ -112,28 +112,39 @@ int take_device_status(dd_plan *p) {
   return DD_ERR_DEVICE_TIMEOUT;
 }
 
+// Drop this plan's hold on its staged-kernel tables (the device arrays go
+// with the last holder).
 void free_quad(QuadDevice *&q) {
-  if (!q) return;
-  free_device(q->d_recs);
-  free_device(q->d_raw_meta);
   delete q;
   q = nullptr;
 }
 
 void free_octet(OctetDevice *&q) {
-  if (!q) return;
-  free_device(q->d_recs);
-  free_device(q->d_raw_meta);
   delete q;
   q = nullptr;
+}
+
+// A new device array of n int32 holding `host` (n entries; the first
+// `host_n` copied from host, the rest from `tail`).
+int upload_table(const int32_t *host, size_t n, SharedTable *out, const int32_t *tail = nullptr,
+                 size_t tail_n = 0) {
+  SharedTable t(new (std::nothrow) DeviceTable());
+  if (!t) return DD_ERR_OOM;
+  cudaError_t e = cudaMalloc(&t->ptr, (n + tail_n) * sizeof(int32_t));
+  if (e == cudaSuccess && n) e = cudaMemcpy(t->ptr, host, n * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && tail_n)
+    e = cudaMemcpy(t->ptr + n, tail, tail_n * sizeof(int32_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_status(e);
+  *out = std::move(t);
+  return DD_OK;
 }
 
 void destroy_plan(dd_plan *p) {
   if (!p) return;
   free_quad(p->quad);
   free_octet(p->octet);
+  p->delays_store.reset();
   free_device(p->d_next_item);
-  free_device(p->d_delays);
   free_device(p->d_error);
   free_device(p->d_stats);
   free_device(p->d_counts);
@@ -157,56 +168,54 @@ void destroy_plan(dd_plan *p) {
 QuadDevice *make_quad(const dd_plan *p, int nd_thr, int *st) {
   *st = DD_OK;
   ddq::Tables t;
-  if (ddq::build_tables(p->h_delays.data(), p->nchan, p->ndm, nd_thr, &t) != 0) return nullptr;
+  if (ddq::build_tables(p->h_delays->data(), p->nchan, p->ndm, nd_thr, &t) != 0) return nullptr;
   QuadDevice *q = new (std::nothrow) QuadDevice();
   if (!q) {
     *st = DD_ERR_OOM;
     return nullptr;
   }
-  q->tables = std::move(t);
-  const size_t rb = q->tables.recs.size() * sizeof(int32_t);
-  const size_t mb = q->tables.raw_meta.size() * sizeof(int32_t);
-  cudaError_t e = cudaMalloc(&q->d_recs, rb);
-  if (e == cudaSuccess) e = cudaMalloc(&q->d_raw_meta, mb);
-  if (e == cudaSuccess) e = cudaMemcpy(q->d_recs, q->tables.recs.data(), rb, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
+  *st = upload_table(t.recs.data(), t.recs.size(), &q->recs_store);
+  if (*st == DD_OK) *st = upload_table(t.raw_meta.data(), t.raw_meta.size(), &q->meta_store);
+  if (*st != DD_OK) {
     free_quad(q);
-    *st = cuda_status(e);
+    return nullptr;
   }
+  q->d_recs = q->recs_store->ptr;
+  q->d_raw_meta = q->meta_store->ptr;
+  t.recs = {};      // on the device now
+  t.raw_meta = {};
+  q->tables = std::move(t);
   return q;
 }
 
-// Same for the staged f16/f32 kernel.
+// Same for the staged f16/f32 kernel (the queue skews follow the window
+// table in the same device array).
 OctetDevice *make_octet(const dd_plan *p, int nd_thr, int *st) {
   *st = DD_OK;
   ddo::Tables t;
   const int esize = p->dtype == DD_F16 ? 2 : 4;
-  if (ddo::build_tables(p->h_delays.data(), p->nchan, p->ndm, nd_thr, esize, &t) != 0)
+  if (ddo::build_tables(p->h_delays->data(), p->nchan, p->ndm, nd_thr, esize, &t) != 0)
     return nullptr;
   OctetDevice *q = new (std::nothrow) OctetDevice();
   if (!q) {
     *st = DD_ERR_OOM;
     return nullptr;
   }
-  q->tables = std::move(t);
-  const size_t rb = q->tables.recs.size() * sizeof(int32_t);
-  const size_t mb = q->tables.raw_meta.size() * sizeof(int32_t);
-  const size_t sb = q->tables.skew.size() * sizeof(int32_t);
-  cudaError_t e = cudaMalloc(&q->d_recs, rb);
-  // the queue skews follow the window table in the same allocation
-  if (e == cudaSuccess) e = cudaMalloc(&q->d_raw_meta, mb + sb);
-  if (e == cudaSuccess) e = cudaMemcpy(q->d_recs, q->tables.recs.data(), rb, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(q->d_raw_meta, q->tables.raw_meta.data(), mb, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(q->d_raw_meta + q->tables.raw_meta.size(), q->tables.skew.data(), sb,
-                   cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) {
+  *st = upload_table(t.recs.data(), t.recs.size(), &q->recs_store);
+  if (*st == DD_OK)
+    *st = upload_table(t.raw_meta.data(), t.raw_meta.size(), &q->meta_store, t.skew.data(),
+                       t.skew.size());
+  if (*st != DD_OK) {
     free_octet(q);
-    *st = cuda_status(e);
+    return nullptr;
   }
+  q->d_recs = q->recs_store->ptr;
+  q->d_raw_meta = q->meta_store->ptr;
+  q->d_skew = q->d_raw_meta + t.raw_meta.size();
+  t.recs = {};      // on the device now
+  t.raw_meta = {};
+  t.skew = {};
+  q->tables = std::move(t);
   return q;
 }
 
@@ -295,14 +304,13 @@ int finish_plan(dd_plan *p) {
   DeviceScope scope(p->device);
   if (!scope.ok()) return DD_ERR_CUDA;
   cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device);
-  const size_t table_bytes = p->h_delays.size() * sizeof(int32_t);
-  cudaError_t e = cudaMalloc(&p->d_delays, table_bytes);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_error, sizeof(int32_t));
+  const int ds = upload_table(p->h_delays->data(), p->h_delays->size(), &p->delays_store);
+  if (ds != DD_OK) return ds;
+  p->d_delays = p->delays_store->ptr;
+  cudaError_t e = cudaMalloc(&p->d_error, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaMalloc(&p->d_stats, sizeof(dd_row_stats) * p->ndm);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_total, sizeof(int64_t));
   if (e == cudaSuccess) e = cudaMallocHost(&p->h_total, sizeof(int64_t));
-  if (e == cudaSuccess)
-    e = cudaMemcpy(p->d_delays, p->h_delays.data(), table_bytes, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
   if (e != cudaSuccess) return cuda_status(e);
   return p->dtype == DD_U8 ? setup_quad(p) : setup_octet(p);
@@ -326,7 +334,7 @@ dd_plan *new_plan(int32_t nchan, int32_t ndm, int32_t in_dtype, int32_t device) 
   p->ndm = ndm;
   p->dtype = in_dtype;
   try {
-    p->h_delays.resize(static_cast<size_t>(nchan) * ndm);
+    p->h_delays = std::make_shared<std::vector<int32_t>>(static_cast<size_t>(nchan) * ndm);
     p->h_mean.resize(ndm);
     p->h_sigma.resize(ndm);
   } catch (...) {
@@ -356,7 +364,7 @@ extern "C" int dd_plan_create(dd_plan **out, int32_t nchan, double f_top_mhz,
     return DD_ERR_OOM;
   }
   st = dd_compute_delays(nchan, f_top_mhz, chan_width_mhz, t_samp_s, dm_list, ndm,
-                         p->h_delays.data(), &p->maxshift);
+                         p->h_delays->data(), &p->maxshift);
   if (st != DD_OK) {
     delete p;
     return st;
@@ -384,12 +392,61 @@ extern "C" int dd_plan_create_from_delays(dd_plan **out, int32_t nchan, int32_t 
   }
   dd_plan *p = new_plan(nchan, ndm, in_dtype, device);
   if (!p) return DD_ERR_OOM;
-  std::copy(delays, delays + n, p->h_delays.begin());
+  std::copy(delays, delays + n, p->h_delays->begin());
   p->maxshift = mx;
   st = finish_plan(p);
   if (st != DD_OK) {
     destroy_plan(p);
     return st;
+  }
+  *out = p;
+  return DD_OK;
+}
+
+extern "C" int dd_plan_create_like(dd_plan **out, const dd_plan *src) {
+  if (!out) return DD_ERR_ARG;
+  *out = nullptr;
+  if (!src) return DD_ERR_ARG;
+  dd_plan *p = new (std::nothrow) dd_plan();
+  if (!p) return DD_ERR_OOM;
+  p->device = src->device;
+  p->nchan = src->nchan;
+  p->ndm = src->ndm;
+  p->dtype = src->dtype;
+  p->f_top = src->f_top, p->df = src->df, p->t_samp = src->t_samp;
+  p->maxshift = src->maxshift;
+  p->sm_count = src->sm_count;
+  p->path = src->path;
+  p->wait_timeout_ns = src->wait_timeout_ns;
+  // the tables are shared (read only); everything a run writes is the new plan's own
+  p->h_delays = src->h_delays;
+  p->delays_store = src->delays_store;
+  p->d_delays = src->d_delays;
+  try {
+    p->dms = src->dms;
+    p->h_mean.resize(p->ndm);
+    p->h_sigma.resize(p->ndm);
+    if (src->quad) p->quad = new QuadDevice(*src->quad);
+    if (src->octet) p->octet = new OctetDevice(*src->octet);
+  } catch (...) {
+    destroy_plan(p);
+    return DD_ERR_OOM;
+  }
+  DeviceScope scope(p->device);
+  if (!scope.ok()) {
+    destroy_plan(p);
+    return DD_ERR_CUDA;
+  }
+  cudaError_t e = cudaMalloc(&p->d_error, sizeof(int32_t));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_stats, sizeof(dd_row_stats) * p->ndm);
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_total, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_total, sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
+  if (e == cudaSuccess && (p->quad || p->octet))
+    e = cudaMalloc(&p->d_next_item, sizeof(unsigned long long));
+  if (e != cudaSuccess) {
+    destroy_plan(p);
+    return cuda_status(e);
   }
   *out = p;
   return DD_OK;
@@ -418,7 +475,7 @@ extern "C" int dd_plan_nsamp_out(const dd_plan *p, int64_t nsamp_in, int64_t *ns
 
 extern "C" int dd_plan_delays(const dd_plan *p, int32_t *host_out) {
   if (!p || !host_out) return DD_ERR_ARG;
-  std::memcpy(host_out, p->h_delays.data(), p->h_delays.size() * sizeof(int32_t));
+  std::memcpy(host_out, p->h_delays->data(), p->h_delays->size() * sizeof(int32_t));
   return DD_OK;
 }
 
@@ -993,11 +1050,15 @@ extern "C" int dd_stream_bytes(const dd_plan *p, int64_t block_samples, int64_t 
   if (!p || !bytes || block_samples < 1) return DD_ERR_ARG;
   const int64_t es = ddk::elem_size(p->dtype);
   const int64_t pitch = stream_pitch(p, block_samples);
-  const int64_t tiles = ddk::time_tiles(block_samples);
+  // per-tile detection workspace: u8 rows keep a maximum and a count per
+  // 512-sample tile, float rows their partial statistics and a count per
+  // 256-sample tile
+  const int64_t tile_bytes = p->dtype == DD_U8 ? ddk::time_tiles(block_samples) * 8
+                                               : ddk::octet_tiles(block_samples) * 20;
   const int64_t chunks = (block_samples + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
   *bytes = 2 * static_cast<int64_t>(p->nchan) * pitch * es          // double buffer
            + static_cast<int64_t>(p->ndm) * block_samples * 4        // output
-           + static_cast<int64_t>(p->ndm) * (2 * tiles * 4 + 4 * 8)  // tile maxima, counts, rows
+           + static_cast<int64_t>(p->ndm) * (tile_bytes + 4 * 8)     // tiles, row sums/counts
            + static_cast<int64_t>(p->ndm) * chunks * 16              // chunk counts (plain path)
            + static_cast<int64_t>(p->ndm) * static_cast<int64_t>(sizeof(dd_row_stats));
   return DD_OK;

@@ -586,7 +586,7 @@ ddo::Beam octet_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t
   b.out = static_cast<float *>(out);
   b.recs = q.d_recs;
   b.raw_meta = q.d_raw_meta;
-  b.skew = q.d_raw_meta + q.tables.raw_meta.size();
+  b.skew = q.d_skew;
   b.tilestats = tilestats;
   b.max_skew = q.tables.max_skew;
   b.pitch_bytes = pitch * elem_size(p->dtype);

@@ -5,24 +5,44 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <memory>
 #include <vector>
 
 #include "dd.h"
 #include "dd_octet.h"
 #include "dd_quad.h"
 
-// Device copies of the staged quad kernel's plan-time tables.
+// A device array of plan tables, freed with the last plan that holds it:
+// plans made with dd_plan_create_like share their source's tables.
+struct DeviceTable {
+  int32_t *ptr = nullptr;
+  DeviceTable() = default;
+  DeviceTable(const DeviceTable &) = delete;
+  DeviceTable &operator=(const DeviceTable &) = delete;
+  ~DeviceTable() {
+    if (ptr) cudaFree(ptr);
+  }
+};
+using SharedTable = std::shared_ptr<DeviceTable>;
+
+// Device copies of the staged quad kernel's plan-time tables.  `tables`
+// keeps the shape fields (its record and window vectors are emptied once
+// uploaded); d_recs / d_raw_meta alias the shared device arrays.
 struct QuadDevice {
   ddq::Tables tables;
+  SharedTable recs_store, meta_store;
   int32_t *d_recs = nullptr;
   int32_t *d_raw_meta = nullptr;
 };
 
-// Device copies of the staged octet kernel's plan-time tables.
+// Device copies of the staged octet kernel's plan-time tables (and the work
+// queue's per-DM-tile skews, after the window table in the same array).
 struct OctetDevice {
   ddo::Tables tables;
+  SharedTable recs_store, meta_store;
   int32_t *d_recs = nullptr;
   int32_t *d_raw_meta = nullptr;
+  int32_t *d_skew = nullptr;
 };
 
 // Per-DM-row normalisation result written by the statistics kernels, with
@@ -46,11 +66,12 @@ struct dd_plan {
   int32_t dtype = DD_U8;
   double f_top = 0, df = 0, t_samp = 0;
   std::vector<double> dms;
-  std::vector<int32_t> h_delays;  // [nchan][ndm]
+  std::shared_ptr<std::vector<int32_t>> h_delays;  // [nchan][ndm] (shared by like plans)
   int32_t maxshift = 0;
   int sm_count = 0;
 
-  int32_t *d_delays = nullptr;    // [nchan][ndm]
+  SharedTable delays_store;       // device delay table (shared by like plans)
+  int32_t *d_delays = nullptr;    // [nchan][ndm], aliases delays_store
   int32_t *d_error = nullptr;     // sticky device status word (0 = ok)
 
   // detection workspace
