@@ -340,10 +340,16 @@ def run_reference(args):
                       "dms_per_group": SUB_DMS, "parallelism": "replicas1"}
             print_reference(args, value, secs, last, "int32", config)
         return
-    if args.workload in (BATCH, SERVE):
+    if args.workload in (BATCH, BATCH_SMALL, SERVE):
         # the oracle on the first beam (its rate stands for the set)
-        gen = synth.batch_workloads if args.workload == BATCH else synth.serving_workloads
-        wl = gen(args.seed, lambda w: geometry_oracle(w)[1])[0]
+        ms = lambda w: geometry_oracle(w)[1]  # noqa: E731
+        if args.workload == SERVE:
+            wl = synth.serving_workloads(args.seed, ms)[0]
+        elif args.workload == BATCH_SMALL:
+            wl = synth.batch_workloads(args.seed, ms, nchan_choices=(256, 512),
+                                       nsamp_range=(16384, 65536), ndm_range=(128, 512))[0]
+        else:
+            wl = synth.batch_workloads(args.seed, ms)[0]
     else:
         wl = load_workload(args)
     delays, mx, nsamp_out = geometry_oracle(wl)
@@ -352,7 +358,7 @@ def run_reference(args):
         args, lambda t: time_oracle_sample(wl, block, delays, nsamp_out, t))
     last["cpu_model"] = cpu_model()
     config = workload_config(wl, nsamp_out, args.gpus)
-    if args.workload in (BATCH, SERVE):
+    if args.workload in (BATCH, BATCH_SMALL, SERVE):
         config = {"workload": args.workload, "sampled_beam": config,
                   "note": "the oracle's rate on the set's first beam stands for the set"}
         last["sample"] = "first beam of the set: " + last["sample"]
@@ -554,13 +560,19 @@ def run_ours(args):
 # ------------------------------------------------------------- batch
 
 BATCH = "batch32_u8"  # 32 uneven u8 beams (the batching row's configuration)
+# 32 small u8 beams (256 or 512 channels, 128..512 trials): the mix where one
+# shared launch fills the SMs that each beam alone leaves idle
+BATCH_SMALL = "batch32_small_u8"
 
 
-def batch_workloads(seed):
+def batch_workloads(seed, small=False):
     from paper_1401_8258_gb300 import dd_compute_delays
 
     def maxshift(wl):
         return dd_compute_delays(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)[1]
+    if small:
+        return synth.batch_workloads(seed, maxshift, n=32, nchan_choices=(256, 512),
+                                     nsamp_range=(16384, 65536), ndm_range=(128, 512))
     return synth.batch_workloads(seed, maxshift, n=32)
 
 
@@ -574,7 +586,7 @@ def run_batch(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dd.build()
-    wls = batch_workloads(args.seed)
+    wls = batch_workloads(args.seed, small=args.workload == BATCH_SMALL)
     plans = [dd.Plan(w.nchan, w.f_top_mhz, w.chan_width_mhz, w.t_samp_s, w.dms, "u8", local)
              for w in wls]
     # plan time, outside the timed region: the autotuner times every staged
@@ -693,7 +705,7 @@ def run_batch(args):
         "warmup": args.warmup, "ms_per_step": 1e3 * t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": BATCH, "beams": len(wls), "staged_beams": int(staged),
+        "config": {"workload": args.workload, "beams": len(wls), "staged_beams": int(staged),
                    "autotuned_dms_per_cta": [int(t[0]) for t in tuned],
                    "autotuned_staging_depth": depths,
                    "nchan": [w.nchan for w in wls], "ndm": [w.ndm for w in wls],
@@ -724,23 +736,87 @@ def serving_workloads(seed):
     return synth.serving_workloads(seed, maxshift, n=64)
 
 
-def run_serve(args):
-    """Streaming service over 64 beams with 1 s blocks.
+def serve_load(dd, Server, wls, plans, host, nbeams, per_beam, seconds, seed, cap,
+               drain_s=20.0):
+    """One load point through the server: `nbeams` beams of the serving mix
+    (beam i has the geometry of base beam i % 64, its own stream, plan and
+    memory; replicas share their base plan's tables), each sending
+    `seconds` one-second blocks that arrive in real time at phase_i + k
+    seconds (phases uniform in [0, 1)), copied from pinned host memory.
+    Returns latency percentiles over the blocks after the first two of each
+    beam, the GPU's busy share, and whether the load is sustained: every
+    block done, p99 latency below the block duration, the last block
+    finished within one block duration of its arrival."""
+    import threading
+    rng = np.random.default_rng(seed)
+    phases = rng.uniform(0.0, 1.0, nbeams)
+    beam_plans = []
+    for i in range(nbeams):
+        base = plans[i % len(plans)]
+        beam_plans.append(base if i < len(plans) else dd.Plan.like(base))
+    srv = Server(NSIGMA, capacity=cap, per_beam=per_beam)
+    try:
+        for i in range(nbeams):
+            srv.open(i, beam_plans[i], wls[i % len(wls)].nsamp)
+        t0 = time.perf_counter() + 0.5
+        arrivals = sorted((t0 + phases[i] + k, i, k) for i in range(nbeams)
+                          for k in range(seconds))
 
-    Beams are admitted while their bytes (dd_stream_bytes + candidate and
-    input buffers) fit 80% of free HBM.  Block k of beam b arrives at
-    phase_b + k seconds (phases uniform in [0, 1)).  A wave starts as soon as
-    the previous one ends and takes the oldest waiting block of every beam
-    that has one (continuous batching: new blocks join the next wave); the
-    clock advances by each wave's measured GPU time, so latency = wave end -
-    arrival under real-time arrivals.  The same arrivals are replayed with
-    one push (launch set) per beam for comparison, and both again with
-    aligned arrivals (every beam's block at the same instant: the load under
-    which waves carry many beams).  ``value`` is the staggered-arrival wave
-    throughput."""
+        def feed():
+            for t, i, k in arrivals:
+                dt = t - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+                srv.submit(i, host[i % len(host)][k % 2], arrival=t)
+            for i in range(nbeams):
+                srv.close_beam(i)
+
+        th = threading.Thread(target=feed, daemon=True)
+        th.start()
+        th.join()
+        drained = True
+        try:
+            srv.drain(timeout=drain_s)
+        except TimeoutError:
+            drained = False
+        lat = np.array([r.latency for i in range(nbeams) for r in srv.results[i]
+                        if r.seq >= 2])
+        done = sum(len(srv.results[i]) for i in range(nbeams))
+        last = max((r.latency for i in range(nbeams) for r in srv.results[i]
+                    if r.seq == seconds - 1), default=float("inf"))
+        waves = list(srv.waves)
+        busy = sum(b - a for _, a, b in waves)
+        span = arrivals[-1][0] - arrivals[0][0] + 1.0
+        admitted_at_once = srv.peak_used
+    finally:
+        srv.abort()
+        for i in range(len(plans), nbeams):
+            beam_plans[i].close()
+    p99 = float(np.percentile(lat, 99)) if lat.size else float("inf")
+    ok = bool(drained and done == nbeams * seconds and p99 < 1.0 and last < 1.0)
+    return {"beams": nbeams, "p50_latency_s": float(np.percentile(lat, 50)) if lat.size else None,
+            "p99_latency_s": p99, "max_latency_s": float(lat.max()) if lat.size else None,
+            "busy_share": busy / span, "waves": len(waves),
+            "beams_per_wave": float(np.mean([n for n, _, _ in waves])) if waves else 0.0,
+            "blocks_done": done, "peak_admitted_bytes": int(admitted_at_once),
+            "sustained": ok}
+
+
+def run_serve(args):
+    """Real-time serving of the 64-beam mix through the continuous-batching
+    server (paper_1401_8258_gb300.serve.Server): beams opened and admitted by
+    device memory, 1 s blocks arriving in real time from a host thread,
+    copied from pinned memory on the copy stream, waves of every beam with a
+    copied block (or one push per beam, the plain form), wall-clock latency
+    from arrival to candidates on the host.  For each form the largest load
+    (beams of this mix, in steps of 32) sustained with p99 latency below the
+    block duration is searched, three times; ``value`` is the real-time
+    throughput (DM-trial*samples per second of data) of the largest load the
+    waves sustained in every repeat."""
     import torch
 
     import paper_1401_8258_gb300 as dd
+    from paper_1401_8258_gb300.serve import Server
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -750,170 +826,93 @@ def run_serve(args):
     plans = [dd.Plan(w.nchan, w.f_top_mhz, w.chan_width_mhz, w.t_samp_s, w.dms, "u8", local)
              for w in wls]
     cap = 1 << 14
-    free, _ = torch.cuda.mem_get_info(dev)
-    budget, used, admitted = 0.8 * free, 0, []
-    for i, (w, p) in enumerate(zip(wls, plans)):
-        need = dd.Stream.bytes_needed(p, w.nsamp) + 16 * cap + w.nchan * w.nsamp
-        if used + need <= budget:
-            admitted.append(i)
-            used += need
-    wls = [wls[i] for i in admitted]
-    plans = [plans[i] for i in admitted]
-    n = len(wls)
-    streams = [dd.Stream(p, w.nsamp) for p, w in zip(plans, wls)]
     rng = np.random.default_rng(args.seed)
-    blocks = [torch.from_numpy(synth.random_block(rng, w.nchan, w.nsamp, "u8")).to(dev)
-              for w in wls]
-    outs = [torch.empty((w.ndm, w.nsamp), dtype=torch.int32, device=dev) for w in wls]
-    cands = [torch.empty((cap, 16), dtype=torch.uint8, device=dev) for _ in wls]
-    phases = rng.uniform(0.0, 1.0, n)  # staggered arrivals
-    rounds = max(2, args.steps)
-    stream = torch.cuda.current_stream(dev)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    host = [[torch.from_numpy(synth.random_block(rng, w.nchan, w.nsamp, "u8")).pin_memory()
+             for _ in range(2)] for w in wls]
+    seconds = max(20, args.steps)
+    repeats = 3
 
-    def push(idx):
-        dd._native.dd_streams_push([streams[b].handle for b in idx], [blocks[b] for b in idx],
-                                   [blocks[b].stride(0) for b in idx], [outs[b] for b in idx],
-                                   NSIGMA, [cands[b] for b in idx], [cap] * len(idx), stream)
+    # warm-up: every geometry's kernels and the allocator
+    serve_load(dd, Server, wls, plans, host, len(wls), False, 3, args.seed, cap)
 
-    def simulate(per_beam, phases):
-        t, busy, waves, sizes = 0.0, 0.0, 0, []
-        done = [0] * n
-        lat = []
-        while min(done) < rounds:
-            ready = [b for b in range(n) if done[b] < rounds and phases[b] + done[b] <= t]
-            if not ready:
-                t = min(phases[b] + done[b] for b in range(n) if done[b] < rounds)
-                continue
-            ev0.record(stream)
-            if per_beam:
-                for b in ready:
-                    push([b])
-            else:
-                push(ready)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            w = ev0.elapsed_time(ev1) / 1e3
-            t += w
-            busy += w
-            waves += 1
-            sizes.append(len(ready))
-            for b in ready:
-                lat.append(t - (phases[b] + done[b]))
-                done[b] += 1
-        return {"p50_latency_s": float(np.percentile(lat, 50)),
-                "p99_latency_s": float(np.percentile(lat, 99)),
-                "busy_s": busy, "waves": waves, "beams_per_wave": float(np.mean(sizes)),
-                # beam-seconds of data per GPU-second: the number of beams of
-                # this mix the GPU keeps up with in real time
-                "max_realtime_beams": n * rounds * 1.0 / busy,
-                "realtime_factor": rounds * 1.0 / busy}
+    step = 32
 
-    def saturate(per_beam, factor, rounds_sat):
-        """Load sweep: each admitted stream stands for `factor` beams of the
-        same geometry whose 1 s blocks arrive at phases (phase_b + r /
-        factor) + k, so n * factor blocks arrive per second.  The GPU work of
-        a block is that of its stream's push (timing only: the replicas
-        share the stream's buffers); a wave takes at most one waiting block
-        per stream, oldest first.  Returns the p99 latency, the GPU's busy
-        time per second of data (utilisation) and whether the load is
-        sustained: utilisation below 1 (the backlog does not grow) and every
-        block finished, at p99 within one block duration of its arrival."""
-        arr = sorted((phases[b] + r / factor + k, b) for b in range(n) for r in range(factor)
-                     for k in range(rounds_sat))
-        waiting = [[] for _ in range(n)]  # per stream, arrival times (sorted)
-        i, t, lat, busy = 0, 0.0, [], 0.0
-        left = len(arr)
-        while left:
-            while i < len(arr) and arr[i][0] <= t:
-                waiting[arr[i][1]].append(arr[i][0])
-                i += 1
-            ready = [b for b in range(n) if waiting[b]]
-            if not ready:
-                t = arr[i][0]
-                continue
-            ev0.record(stream)
-            if per_beam:
-                for b in ready:
-                    push([b])
-            else:
-                push(ready)
-            ev1.record(stream)
-            torch.cuda.synchronize()
-            w = ev0.elapsed_time(ev1) / 1e3
-            t += w
-            busy += w
-            for b in ready:
-                lat.append(t - waiting[b].pop(0))
-                left -= 1
-            if lat and lat[-1] > 4.0:
-                break  # far past the block duration: the queue grows without bound
-        p99 = float(np.percentile(lat, 99))
-        util = busy / rounds_sat
-        return p99, util, bool(left == 0 and p99 < 1.0 and util < 1.0)
+    def search(per_beam, rep):
+        """Largest sustained load in steps of 32 beams: a run at 768 beams
+        estimates the capacity from its busy share, then loads around the
+        estimate are run until a sustained load and the next one up, not
+        sustained, are found."""
+        tried, seen = [], {}
 
-    def max_beams(per_beam):
-        """Largest load (beams of this mix) kept within one block duration at
-        p99, over a sweep of stream multiplicities."""
-        best, p99_best, tried = 0, None, []
-        for factor in (4, 8, 10, 11, 12, 13, 14, 15, 16, 18, 20):
-            p99, util, ok = saturate(per_beam, factor, 4)
-            tried.append({"beams": n * factor, "p99_latency_s": p99, "utilisation": util,
-                          "sustained": ok})
-            if not ok:
+        def run(nb):
+            if nb not in seen:
+                seen[nb] = serve_load(dd, Server, wls, plans, host, nb, per_beam, seconds,
+                                      args.seed + 1000 * rep + nb, cap)
+                tried.append(seen[nb])
+            return seen[nb]
+
+        first = run(768)
+        est = 768 / max(first["busy_share"], 1e-3)
+        nb = max(step, int(0.97 * est) // step * step)
+        for _ in range(8):
+            ok = run(nb)["sustained"]
+            if ok and (nb + step) in seen and not seen[nb + step]["sustained"]:
                 break
-            best, p99_best = n * factor, p99
-        return {"max_realtime_beams_at_p99_below_block": best, "p99_latency_s": p99_best,
-                "sweep": tried}
+            if not ok and (nb - step) in seen and seen[nb - step]["sustained"]:
+                break
+            nb = nb + step if ok else nb - step
+            if nb < step:
+                break
+        best = max((b for b, r in seen.items() if r["sustained"] and all(
+            seen[c]["sustained"] for c in seen if c < b)), default=0)
+        return best, tried
 
-    for _ in range(max(1, args.warmup)):  # warm-up waves of every beam
-        push(list(range(n)))
-    torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    launches0 = sum(p.launch_count() for p in plans)
-    wave = simulate(False, phases)
-    launches = sum(p.launch_count() for p in plans) - launches0
-    aligned = np.zeros(n)  # every beam's block lands at the same instant
-    wave_aligned = simulate(False, aligned)
+    results = {"waves": [], "per_beam_launches": []}
+    for rep in range(repeats):
+        for form, per_beam in (("waves", False), ("per_beam_launches", True)):
+            best, tried = search(per_beam, rep)
+            results[form].append({"max_realtime_beams": best, "sweep": tried})
     clock = clocks.stop()
-    per_beam = simulate(True, phases)
-    per_beam_aligned = simulate(True, aligned)
-    sat_waves = max_beams(False)
-    sat_plain = max_beams(True)
-    units = sum(w.ndm * w.nsamp for w in wls) * rounds
-    value = units / wave["busy_s"]
-    adds = float(sum(w.ndm * w.nsamp * w.nchan for w in wls)) * rounds
+
+    def summary(form):
+        bests = [r["max_realtime_beams"] for r in results[form]]
+        at = [t for r in results[form] for t in r["sweep"]
+              if t["beams"] == r["max_realtime_beams"]]
+        return {"max_realtime_beams_each_repeat": bests, "min": min(bests), "max": max(bests),
+                "p50_latency_s_at_max": [t["p50_latency_s"] for t in at],
+                "p99_latency_s_at_max": [t["p99_latency_s"] for t in at],
+                "repeats": results[form]}
+
+    sw, sp = summary("waves"), summary("per_beam_launches")
+    beams = sw["min"]
+    units = sum(wls[i % len(wls)].ndm * wls[i % len(wls)].nsamp for i in range(beams))
+    adds = float(sum(wls[i % len(wls)].ndm * wls[i % len(wls)].nsamp * wls[i % len(wls)].nchan
+                     for i in range(beams)))
     props = torch.cuda.get_device_properties(dev)
-    sms = props.multi_processor_count
     peaks = measured_peaks()
-    smax = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = sms * LANES_PER_SM * smax * 1e6 / 1e12
-    achieved = adds / wave["busy_s"] / 1e12
+    peak = props.multi_processor_count * LANES_PER_SM * float(peaks.get("sm_max_mhz", 2070.0)) / 1e6
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": rounds,
-        "warmup": args.warmup, "ms_per_step": 1e3 * wave["busy_s"] / wave["waves"],
+        "metric": METRIC, "value": float(units), "unit": UNIT + " (real time, 1 s blocks)",
+        "n_gpus": 1, "steps": seconds, "warmup": 3, "ms_per_step": 1000.0,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "int32", "data": "synthetic",
-        "config": {"workload": SERVE, "beams_drawn": 64, "beams_admitted": n,
-                   "block_s": 1.0, "rounds": rounds, "nchan": [w.nchan for w in wls],
-                   "ndm": [w.ndm for w in wls], "t_samp_s": [w.t_samp_s for w in wls],
-                   "admission_bytes": int(used), "input_dtype": "u8", "nsigma": NSIGMA,
-                   "parallelism": "replicas1"},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tadd/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "whole waves (copies, shared persistent launches, detection)",
-                     "kernel_ms": 1e3 * wave["busy_s"] / wave["waves"]},
-        "serving": {"staggered_arrivals": {"waves": wave, "per_beam_launches": per_beam},
-                    "aligned_arrivals": {"waves": wave_aligned,
-                                         "per_beam_launches": per_beam_aligned},
-                    "saturation": {"waves": sat_waves, "per_beam_launches": sat_plain,
-                                   "block_s": 1.0}},
-        "cpu_baseline": None, "e2e": None, "clocks": clock, "gpu_launches": int(launches),
+        "config": {"workload": SERVE, "beam_mix": 64, "block_s": 1.0,
+                   "seconds_of_arrivals_per_load": seconds, "repeats": repeats,
+                   "nchan": [w.nchan for w in wls], "ndm": [w.ndm for w in wls],
+                   "t_samp_s": [w.t_samp_s for w in wls], "input_dtype": "u8",
+                   "nsigma": NSIGMA, "parallelism": "replicas1",
+                   "arrivals": "real time from a host thread, staggered phases, pinned host "
+                               "blocks copied on a copy stream"},
+        "roofline": {"bound": "alu", "achieved": adds / 1e12, "peak": peak, "unit": "Tadd/s",
+                     "frac": adds / 1e12 / peak, "traffic": None,
+                     "kernel": "the beams' sample-adds per second of data at the sustained load"},
+        "serving": {"waves": sw, "per_beam_launches": sp,
+                    "margin_beams": sw["min"] - sp["max"]},
+        "cpu_baseline": None, "e2e": None, "clocks": clock, "gpu_launches": None,
     }
     print(json.dumps(line), flush=True)
-    for st in streams:
-        st.close()
     for p in plans:
         p.close()
 
@@ -1294,7 +1293,7 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == BATCH:
+    elif args.workload in (BATCH, BATCH_SMALL):
         run_batch(args)
     elif args.workload == SERVE:
         run_serve(args)

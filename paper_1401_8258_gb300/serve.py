@@ -98,6 +98,7 @@ class Server:
         self.waves = []                           # (beams, start, end) wall-clock
         self.admissions = []                      # (key, opened, admitted)
         self._stop = False
+        self._abort = False
         self._error = None
         self._thread = threading.Thread(target=self._run, name="dd-server", daemon=True)
         self._thread.start()
@@ -165,11 +166,20 @@ class Server:
             self._raise_error()
 
     def shutdown(self):
+        """Stop once nothing copied is left to run; release the streams."""
         with self._cv:
             self._stop = True
             self._cv.notify_all()
         self._thread.join()
         self._raise_error()
+
+    def abort(self):
+        """Stop after the push in flight, dropping queued blocks (an
+        overloaded run); release the streams."""
+        with self._cv:
+            self._stop = self._abort = True
+            self._cv.notify_all()
+        self._thread.join()
 
     def __enter__(self):
         return self
@@ -254,7 +264,8 @@ class Server:
                         self._release()
                         self._admit()
                         # every admitted beam whose next block has been copied
-                        wave = [b for b in self._active if b.copied > b.done]
+                        wave = [] if self._abort else [b for b in self._active
+                                                        if b.copied > b.done]
                         if wave or self._stop:
                             break
                         self._cv.notify_all()
