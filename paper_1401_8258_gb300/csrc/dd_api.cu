@@ -226,18 +226,66 @@ std::vector<int> staged_widths(const dd_plan *p) {
   return {ddo::kNdThr, ddo::kNdThr / 2};
 }
 
-// Shared persistent launches take staged u8 plans of one DM-tile width and
-// one staging depth: group = width index (64, 32, 16 trials) x kDepths +
-// depth - kMinCopyAhead.
+// Shared persistent launches take staged u8 plans of every DM-tile width
+// (the kernel dispatches on each beam's width) at one staging depth.  A
+// batch runs at the depth most of its beams were tuned to (the depth never
+// changes a result, only the number of copies queued ahead); a beam whose
+// tables do not fit shared memory at that depth keeps its own.
 constexpr int kDepths = ddq::kMaxCopyAhead - ddq::kMinCopyAhead + 1;
-constexpr int kQuadGroups = 3 * kDepths;
-int quad_group(const dd_plan *p) {
-  const int nd = p->quad->tables.nd_thr;
-  const int wi = nd == ddq::kNdThr ? 0 : (nd == ddq::kNdThr / 2 ? 1 : 2);
-  return wi * kDepths + p->quad->tables.copy_ahead - ddq::kMinCopyAhead;
+
+// Shared-memory bytes of plan p's staged u8 kernel at staging depth ca.
+int quad_smem_at(const dd_plan *p, int ca) {
+  ddq::Tables t = p->quad->tables;  // the shape fields only (vectors uploaded)
+  return ddq::set_copy_ahead(t, ca) ? t.smem_bytes : INT32_MAX;
 }
-int group_nd_thr(int g) { return ddq::kNdThr >> (g / kDepths); }
-int group_copy_ahead(int g) { return ddq::kMinCopyAhead + g % kDepths; }
+
+// Launch groups (one per staging depth, index depth - kMinCopyAhead) of the
+// staged u8 beams idx (plans[idx[k]]), in the given order.
+std::vector<std::vector<int>> depth_groups(dd_plan *const *plans, const std::vector<int> &idx) {
+  int votes[kDepths] = {};
+  for (int i : idx) ++votes[plans[i]->quad->tables.copy_ahead - ddq::kMinCopyAhead];
+  int common = 0;
+  for (int g = 1; g < kDepths; ++g)
+    if (votes[g] > votes[common]) common = g;
+  std::vector<std::vector<int>> groups(kDepths);
+  for (int i : idx) {
+    const bool fits = quad_smem_at(plans[i], common + ddq::kMinCopyAhead) <= ddq::kMaxSmem;
+    groups[fits ? common : plans[i]->quad->tables.copy_ahead - ddq::kMinCopyAhead].push_back(i);
+  }
+  return groups;
+}
+
+// One shared launch per depth group and per kMaxBeams beams: the beams'
+// descriptors are made by `beam_of(i)`; the launch uses the queue head and
+// status word given (or, with next_item null, those of each group's first
+// plan, whose launch count it adds to).
+template <typename BeamOf>
+int launch_groups(dd_plan *const *plans, const std::vector<std::vector<int>> &groups,
+                  BeamOf beam_of, unsigned long long *next_item, int32_t *status, int sm_count,
+                  cudaStream_t s) {
+  for (int g = 0; g < kDepths; ++g) {
+    const std::vector<int> &idx = groups[g];
+    const int ca = ddq::kMinCopyAhead + g;
+    for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
+      const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
+      std::vector<ddq::Beam> beams;
+      int smem = 0;
+      for (size_t k = lo; k < hi; ++k) {
+        beams.push_back(beam_of(idx[k]));
+        smem = std::max(smem, quad_smem_at(plans[idx[k]], ca));
+      }
+      dd_plan *p0 = plans[idx[lo]];
+      cudaError_t err = cudaSuccess;
+      const int nl = ddk::launch_quad_beams(
+          beams.data(), static_cast<int>(beams.size()), ddq::kNdThr, ca, smem,
+          sm_count > 0 ? sm_count : p0->sm_count, next_item ? next_item : p0->d_next_item,
+          status ? status : p0->d_error, p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
+      if (nl < 0) return cuda_status(err);
+      p0->launches += nl;  // counted on the group's first plan
+    }
+  }
+  return DD_OK;
+}
 
 // Plan-time tables of the staged kernels: the widest width whose delay
 // patterns fit; none if no width fits (plain-load kernel).
@@ -514,7 +562,8 @@ extern "C" int dd_execute_pitched(dd_plan *p, const void *block, int64_t nsamp_i
     n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, out_pitch, nullptr, s,
                                      &err);
   else
-    n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, out_pitch, s, &err);
+    n = ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, out_pitch, nullptr,
+                                      s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
   return DD_OK;
@@ -536,43 +585,26 @@ int execute_plans_pitched(dd_plan *const *plans, int n, const void *const *block
   DeviceScope scope(plans[0]->device);
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // staged u8 work by DM-tile width and staging depth, in the given order
-  std::vector<int> staged[kQuadGroups];
+  // staged u8 work in shared launches, in the given order; the rest alone
+  std::vector<int> staged;
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
     if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
-      staged[quad_group(p)].push_back(i);
+      staged.push_back(i);
     } else {
       const int st =
           dd_execute_pitched(p, block[i], nsamp_in[i], pitch_elems[i], out[i], out_pitch[i], stream);
       if (st != DD_OK) return st;
     }
   }
-  for (int g = 0; g < kQuadGroups; ++g) {
-    const std::vector<int> &idx = staged[g];
-    for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
-      const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
-      std::vector<ddq::Beam> beams;
-      int smem = 0;
-      for (size_t k = lo; k < hi; ++k) {
-        dd_plan *p = plans[idx[k]];
-        beams.push_back(ddk::quad_beam(p, block[idx[k]], pitch_elems[idx[k]], nout[idx[k]],
-                                       out[idx[k]], out_pitch[idx[k]], nullptr, nullptr));
-        smem = std::max(smem, static_cast<int>(p->quad->tables.smem_bytes));
-      }
-      // the first plan's work-queue head and status word serve the launch
-      dd_plan *p0 = plans[idx[lo]];
-      cudaError_t err = cudaSuccess;
-      const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
-                                            group_nd_thr(g), group_copy_ahead(g), smem,
-                                            p0->sm_count,
-                                            p0->d_next_item, p0->d_error, p0->wait_timeout_ns,
-                                            p0->debug_skip_copies, s, &err);
-      if (nl < 0) return cuda_status(err);
-      p0->launches += nl;
-    }
-  }
-  return DD_OK;
+  if (staged.empty()) return DD_OK;
+  return launch_groups(
+      plans, depth_groups(plans, staged),
+      [&](int i) {
+        return ddk::quad_beam(plans[i], block[i], pitch_elems[i], nout[i], out[i], out_pitch[i],
+                              nullptr, nullptr);
+      },
+      nullptr, nullptr, 0, s);
 }
 
 extern "C" int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
@@ -619,16 +651,19 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   const cudaEvent_t ev = static_cast<cudaEvent_t>(event);
-  if (p->path == 0 && ddk::octet_supported(p, block, pitch_elems, nsamp_out)) {
-    // staged float kernel with per-tile partial statistics, then the tiled
-    // detection passes
+  if (p->dtype != DD_U8) {
+    // float input: the staged (or plain-load) float kernel with per-tile
+    // partial statistics, then the tiled detection passes
     st = ensure_tile_workspace(p, static_cast<size_t>(ddk::octet_tiles(nsamp_out)) * p->ndm,
                                true);
     if (st != DD_OK) return st;
     p->stats_valid = false;
     cudaError_t err = cudaSuccess;
-    int n = ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, nsamp_out,
-                                         p->d_tilestats, s, &err);
+    int n = p->path == 0 && ddk::octet_supported(p, block, pitch_elems, nsamp_out)
+                ? ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, nsamp_out,
+                                               p->d_tilestats, s, &err)
+                : ddk::launch_dedisperse_direct(p, block, pitch_elems, nsamp_out, out, nsamp_out,
+                                                p->d_tilestats, s, &err);
     if (n < 0) return cuda_status(err);
     p->launches += n;
     if (ev && cudaEventRecord(ev, s) != cudaSuccess) return DD_ERR_CUDA;
@@ -702,9 +737,9 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t err = cudaSuccess;
-  // staged u8 beams, by DM-tile width (64, 32, 16 trials) and staging
-  // depth; the rest take their own kernels
-  std::vector<int> staged[kQuadGroups];
+  // staged u8 beams in shared launches (fused statistics), staged float
+  // beams with per-tile statistics, the rest through their own kernels
+  std::vector<int> staged;
   std::vector<char> is_staged(n, 0);  // 1: staged u8 (fused), 2: staged float (fused)
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
@@ -714,15 +749,19 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
       if (st != DD_OK) return st;
       err = cudaMemsetAsync(p->d_rowsums, 0, 2 * sizeof(int64_t) * p->ndm, s);
       if (err != cudaSuccess) return cuda_status(err);
-      staged[quad_group(p)].push_back(i);
+      staged.push_back(i);
       is_staged[i] = 1;
-    } else if (p->path == 0 && ddk::octet_supported(p, block[i], pitch_elems[i], nout[i])) {
-      // staged float kernel with per-tile statistics, as dd_run
+    } else if (p->dtype != DD_U8) {
+      // float kernels with per-tile statistics, as dd_run
       const int st = ensure_tile_workspace(
           p, static_cast<size_t>(ddk::octet_tiles(nout[i])) * p->ndm, true);
       if (st != DD_OK) return st;
-      const int nl = ddk::launch_dedisperse_octet(p, block[i], pitch_elems[i], nout[i], out[i],
-                                                  nout[i], p->d_tilestats, s, &err);
+      const int nl =
+          p->path == 0 && ddk::octet_supported(p, block[i], pitch_elems[i], nout[i])
+              ? ddk::launch_dedisperse_octet(p, block[i], pitch_elems[i], nout[i], out[i],
+                                             nout[i], p->d_tilestats, s, &err)
+              : ddk::launch_dedisperse_direct(p, block[i], pitch_elems[i], nout[i], out[i],
+                                              nout[i], p->d_tilestats, s, &err);
       if (nl < 0) return cuda_status(err);
       p->launches += nl;
       is_staged[i] = 2;
@@ -731,42 +770,58 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
       if (st != DD_OK) return st;
     }
   }
-  for (int g = 0; g < kQuadGroups; ++g) {
-    std::vector<int> &idx = staged[g];
-    // costliest beams first (a work item costs about nchan): the queue's
-    // tail then holds the cheap items
-    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
-      return plans[x]->nchan > plans[y]->nchan;
-    });
-    for (size_t lo = 0; lo < idx.size(); lo += ddq::kMaxBeams) {
-      const size_t hi = std::min(idx.size(), lo + static_cast<size_t>(ddq::kMaxBeams));
-      std::vector<ddq::Beam> beams;
-      int smem = 0;
-      for (size_t k = lo; k < hi; ++k) {
-        dd_plan *p = plans[idx[k]];
-        beams.push_back(ddk::quad_beam(p, block[idx[k]], pitch_elems[idx[k]], nout[idx[k]],
-                                       out[idx[k]], nout[idx[k]], p->d_rowsums, p->d_tilemax));
-        smem = std::max(smem, static_cast<int>(p->quad->tables.smem_bytes));
-      }
-      dd_plan *p0 = plans[idx[lo]];
-      const int nl = ddk::launch_quad_beams(beams.data(), static_cast<int>(beams.size()),
-                                            group_nd_thr(g), group_copy_ahead(g), smem,
-                                            sm_count, next_item, status,
-                                            p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
-      if (nl < 0) return cuda_status(err);
-      p0->launches += nl;  // counted on the first beam's plan
-    }
+  // costliest beams first (a work item costs about nchan): the queue's tail
+  // then holds the cheap items
+  std::stable_sort(staged.begin(), staged.end(),
+                   [&](int x, int y) { return plans[x]->nchan > plans[y]->nchan; });
+  if (!staged.empty()) {
+    const int st = launch_groups(
+        plans, depth_groups(plans, staged),
+        [&](int i) {
+          dd_plan *p = plans[i];
+          return ddk::quad_beam(p, block[i], pitch_elems[i], nout[i], out[i], nout[i],
+                                p->d_rowsums, p->d_tilemax);
+        },
+        next_item, status, sm_count, s);
+    if (st != DD_OK) return st;
   }
-  // detection per beam, then one synchronisation for every count
+  // detection: the staged u8 beams together (two launches per kMaxDetectBeams
+  // beams, counted on the first beam's plan), the others per beam; then
+  // each beam's count to its plan's pinned slot, and one synchronisation
+  // (by the caller) for every count
+  for (size_t lo = 0; lo < staged.size(); lo += ddk::kMaxDetectBeams) {
+    const size_t hi = std::min(staged.size(), lo + static_cast<size_t>(ddk::kMaxDetectBeams));
+    std::vector<ddk::DetectBeam> det;
+    for (size_t k = lo; k < hi; ++k) {
+      dd_plan *p = plans[staged[k]];
+      ddk::DetectBeam d;
+      std::memset(&d, 0, sizeof(d));
+      d.D = static_cast<const int32_t *>(out[staged[k]]);
+      d.n = nout[staged[k]];
+      d.ntiles = static_cast<int32_t>(ddk::time_tiles(d.n));
+      d.ndm = p->ndm;
+      d.rowsums = reinterpret_cast<const long long *>(p->d_rowsums);
+      d.tilemax = p->d_tilemax;
+      d.stats = p->d_stats;
+      d.tilecount = p->d_tilecount;
+      d.rowcount = p->d_rowcount;
+      d.cands = cands[staged[k]];
+      d.capacity = capacity[staged[k]];
+      d.total = p->d_total;
+      det.push_back(d);
+    }
+    const int nl = ddk::launch_tiled_detect_beams(det.data(), static_cast<int>(det.size()),
+                                                  nsigma, s, &err);
+    if (nl < 0) return cuda_status(err);
+    plans[staged[lo]]->launches += nl;
+  }
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
-    int nl;
-    if (is_staged[i] == 1) {
-      nl = ddk::launch_tiled_detect(p, out[i], nout[i], nsigma, cands[i], capacity[i], s, &err);
-    } else if (is_staged[i] == 2) {
+    int nl = 0;
+    if (is_staged[i] == 2) {
       nl = ddk::launch_tiled_detect_f32(p, out[i], nout[i], nsigma, cands[i], capacity[i], s,
                                         &err);
-    } else {
+    } else if (!is_staged[i]) {
       const int64_t nchunks = (nout[i] + ddk::kDetectChunk - 1) / ddk::kDetectChunk;
       const int st = ensure_chunk_workspace(p, static_cast<size_t>(nchunks) * p->ndm);
       if (st != DD_OK) return st;

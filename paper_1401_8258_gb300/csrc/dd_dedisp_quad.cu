@@ -287,26 +287,177 @@ __device__ __forceinline__ void drain(uint32_t (&acc)[ND_THR][kPairsPerThread], 
   }
 }
 
+// Arguments of the accumulating role for one work item (the kernel's
+// per-item state the role reads).
+struct AccArgs {
+  const Beam &a;
+  uint8_t *smem;
+  uint32_t bar0, rec_off, rec_bytes;
+  int rec_stages;
+  uint32_t prow_off, prow_bytes, tmem_base;
+  int warp, lane, dg;
+  uint32_t my_pair;
+  int tile, ttile;
+  int64_t t_cta;
+};
+
+// The accumulating role of one work item for a beam of ND_THR trials per
+// thread: per chunk, wait for its rows, add them, signal the stage
+// consumed; drain the 16-bit halves into tensor memory every kFlushQuads
+// quads; write the outputs (and, with rowsums, the row sums and tile
+// maxima).  Returns true if the building warps stopped at a copy wait that
+// ran out.
+template <int ND_THR>
+__device__ __forceinline__ bool acc_item(const AccArgs &g) {
+  constexpr int ND_CTA = kDmGroups * ND_THR;
+  constexpr uint32_t kColsPerThread = 2 * ND_THR * kPairsPerThread;
+  constexpr int kFlushChunks = kFlushQuads / kQuadsPerChunk;
+  const Beam &a = g.a;
+  const int warp = g.warp, lane = g.lane, dg = g.dg, tile = g.tile, ttile = g.ttile;
+  const uint32_t my_pair = g.my_pair;
+  const int64_t t_cta = g.t_cta;
+  volatile int32_t *abort_at = reinterpret_cast<volatile int32_t *>(g.smem + kAbortSlot);
+  auto rec_ptr = [&](int m) {
+    return reinterpret_cast<const int32_t *>(g.smem + g.rec_off + (m % g.rec_stages) * g.rec_bytes);
+  };
+  auto prow_addr = [&](int m) { return g.bar0 + g.prow_off + (m % kRowStages) * g.prow_bytes; };
+  bool aborted = false;
+  const uint32_t taddr = g.tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
+                         static_cast<uint32_t>(warp >> 2) * kColsPerThread;
+  uint32_t acc[ND_THR][kPairsPerThread];
+#pragma unroll
+  for (int i = 0; i < ND_THR; ++i)
+#pragma unroll
+    for (int j = 0; j < kPairsPerThread; ++j) acc[i][j] = 0;
+  bool drained = false;  // tensor memory holds sums of this item
+  for (int k = 0; k < a.nchunks; ++k) {
+    bar_sync(kBarFull + k % kRowStages, kThreads);
+    if (*abort_at == k) {  // rows of chunk k were not built
+      aborted = true;
+      break;
+    }
+    const int32_t *rec = rec_ptr(k);
+    const int nq = rec[2];
+    const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
+    const uint32_t prow = prow_addr(k);
+    int a_next[2][ND_THR];
+    load_offsets<ND_THR>(A, a_next[0]);
+    load_offsets<ND_THR>(A + ND_CTA, a_next[1]);
+#pragma unroll
+    for (int q = 0; q < kQuadsPerChunk; q += 2) {
+      if (q < nq) {
+        int a_cur[2][ND_THR];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int i = 0; i < ND_THR; ++i) a_cur[h][i] = a_next[h][i];
+        if (q + 2 < nq) {
+          load_offsets<ND_THR>(A + (q + 2) * ND_CTA, a_next[0]);
+          load_offsets<ND_THR>(A + (q + 3) * ND_CTA, a_next[1]);
+        }
+        if (q + 1 < nq) {
+#pragma unroll
+          for (int i = 0; i < ND_THR; ++i)
+            AccPairs<0>::two(acc[i],
+                             prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair),
+                             prow + 4u * (static_cast<uint32_t>(a_cur[1][i]) + my_pair));
+        } else {
+#pragma unroll
+          for (int i = 0; i < ND_THR; ++i)
+            AccPairs<0>::one(acc[i],
+                             prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair));
+        }
+      }
+    }
+    bar_arrive(kBarEmpty + k % kRowStages, kThreads);
+    // at most kFlushQuads quads in the 16-bit halves
+    if ((k + 1) % kFlushChunks == 0 && k + 1 < a.nchunks) {
+      drain<ND_THR>(acc, taddr, drained);
+      drained = true;
+    }
+  }
+  if (!aborted) {
+    // final sums: stored part (if any) + the packed halves; pair j of
+    // trial i covers samples my_pair + 32 j and my_pair + 32 j + kHalf.
+    // Per trial, this thread's exact sum, sum of squares and largest
+    // value of the samples it stores (for the detection statistics).
+    long long s1[ND_THR], s2[ND_THR];
+    int32_t mx[ND_THR];
+#pragma unroll
+    for (int i = 0; i < ND_THR; ++i) s1[i] = 0, s2[i] = 0, mx[i] = INT32_MIN;
+#pragma unroll
+    for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
+      uint32_t v[16];
+      if (drained) {
+        tmem_ld16(taddr + 16u * blk, v);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 16; ++e) v[e] = 0;
+      }
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int m = 8 * blk + e;
+        const int i = m / kPairsPerThread, j = m % kPairsPerThread;
+        const int d = tile * ND_CTA + dg * ND_THR + i;
+        if (d >= a.ndm) continue;
+        int32_t *orow = a.out + static_cast<int64_t>(d) * a.out_pitch;
+        const uint32_t w = acc[i][j];
+        const int64_t t = t_cta + my_pair + 32 * j;
+        const int32_t lo = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
+        const int32_t hi = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
+        if (t < a.nsamp_out) {
+          orow[t] = lo;
+          s1[i] += lo, s2[i] += static_cast<long long>(lo) * lo, mx[i] = max(mx[i], lo);
+        }
+        if (t + kHalf < a.nsamp_out) {
+          orow[t + kHalf] = hi;
+          s1[i] += hi, s2[i] += static_cast<long long>(hi) * hi, mx[i] = max(mx[i], hi);
+        }
+      }
+    }
+    if (a.rowsums) {
+      // one warp holds all kTimeTile samples of its trials: reduce over
+      // lanes; integer sums make the row totals independent of order
+#pragma unroll
+      for (int i = 0; i < ND_THR; ++i) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s1[i] += __shfl_xor_sync(0xffffffffu, s1[i], o);
+          s2[i] += __shfl_xor_sync(0xffffffffu, s2[i], o);
+          mx[i] = max(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
+        }
+        const int d = tile * ND_CTA + dg * ND_THR + i;
+        if (lane == 0 && d < a.ndm) {
+          atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d),
+                    static_cast<unsigned long long>(s1[i]));
+          atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d + 1),
+                    static_cast<unsigned long long>(s2[i]));
+          a.tilemax[static_cast<int64_t>(d) * a.ntiles_t + ttile] = mx[i];
+        }
+      }
+    }
+  }
+
+  return aborted;
+}
+
 // Persistent kernel: each CTA takes work items (one DM tile x one time tile
 // of one beam) from the launch's queue until it is empty.  Per item every
 // warp role runs the chunk pipeline below from a clean state (mbarriers
 // re-initialised, every named-barrier phase of the previous item complete);
 // tensor memory is allocated once per CTA.
-template <int ND_THR, int CA>
+template <int CA>
 __global__ void __launch_bounds__(kThreads, 1)
 dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
   // staging depth: copies queued CA chunks ahead, kRaw raw window buffers,
   // kRec records
   constexpr int kRaw = raw_stages(CA), kRec = rec_stages(CA);
-  constexpr int ND_CTA = kDmGroups * ND_THR;
-  constexpr int kSegsOff = units_offset(ND_CTA);
-  constexpr int kStartsOff = warp_start_offset(ND_CTA);
-  // tensor-memory columns: accumulating warp w uses lane quarter w % 4 and
-  // column block w / 4 of 2 * ND_THR * kPairsPerThread columns (one per sum)
-  constexpr uint32_t kColsPerThread = 2 * ND_THR * kPairsPerThread;
-  constexpr uint32_t kTmemCols = kAccThreads / 32 / 4 * kColsPerThread;
+  // tensor-memory columns, for the widest tile: accumulating warp w uses
+  // lane quarter w % 4 and column block w / 4 of 2 * ND_THR *
+  // kPairsPerThread columns (one per sum; narrower tiles use fewer)
+  constexpr uint32_t kTmemCols = kAccThreads / 32 / 4 * (2 * kNdThr * kPairsPerThread);
   static_assert(kAccThreads % 128 == 0, "whole warp quartets");
-  static_assert(ND_THR * kPairsPerThread % 8 == 0 && kTmemCols >= 32 && kTmemCols <= 512 &&
+  static_assert((kNdThr / 4) * kPairsPerThread % 8 == 0 && kTmemCols >= 32 && kTmemCols <= 512 &&
                     (kTmemCols & (kTmemCols - 1)) == 0,
                 "tensor-memory allocation must be a power of two in 32..512 columns");
   static_assert(kFlushQuads % kQuadsPerChunk == 0, "drain at chunk boundaries");
@@ -314,7 +465,6 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
   static_assert(CA >= kMinCopyAhead && CA <= kMaxCopyAhead && 8 * kRaw <= kTmemSlot &&
                     kItemSlot + 8 <= kBarrierBytes,
                 "pipeline depths");
-  constexpr int kFlushChunks = kFlushQuads / kQuadsPerChunk;
   extern __shared__ __align__(128) uint8_t smem[];
   const int tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -393,6 +543,9 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
     bool aborted = false;
     int issued = 0;  // chunks queued (first building warp)
     if (builder) {
+      // this beam's record layout (its tile width)
+      const int nd_cta = kDmGroups * a.nd_thr;
+      const int segs_off = units_offset(nd_cta), starts_off = warp_start_offset(nd_cta);
       const int bw = warp - kAccThreads / 32;
       const bool issuer = bw == 0 && !L.skip_copies;
       if (issuer) {
@@ -424,8 +577,8 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
           issued = m + 1;
         }
         const int32_t *rec = rec_ptr(j);
-        build_rows(rec, raw_addr(j), prow_addr(j), kSegsOff, bw, lane, 0,
-                   warp_segments(rec, bw, kStartsOff), kStartsOff);
+        build_rows(rec, raw_addr(j), prow_addr(j), segs_off, bw, lane, 0,
+                   warp_segments(rec, bw, starts_off), starts_off);
         bar_arrive(kBarFull + j % kRowStages, kThreads);
       }
       if (!aborted) {
@@ -434,121 +587,15 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
           if (m >= 0) bar_sync(kBarEmpty + m % kRowStages, kThreads);
       }
     } else {
-      const uint32_t taddr = tmem_base + (static_cast<uint32_t>(32 * (warp & 3)) << 16) +
-                             static_cast<uint32_t>(warp >> 2) * kColsPerThread;
-      uint32_t acc[ND_THR][kPairsPerThread];
-#pragma unroll
-      for (int i = 0; i < ND_THR; ++i)
-#pragma unroll
-        for (int j = 0; j < kPairsPerThread; ++j) acc[i][j] = 0;
-      bool drained = false;  // tensor memory holds sums of this item
-      for (int k = 0; k < a.nchunks; ++k) {
-        bar_sync(kBarFull + k % kRowStages, kThreads);
-        if (*abort_at == k) {  // rows of chunk k were not built
-          aborted = true;
-          break;
-        }
-        const int32_t *rec = rec_ptr(k);
-        const int nq = rec[2];
-        const int32_t *A = rec + kRecHeader + dg * ND_THR;  // 16-byte aligned
-        const uint32_t prow = prow_addr(k);
-        int a_next[2][ND_THR];
-        load_offsets<ND_THR>(A, a_next[0]);
-        load_offsets<ND_THR>(A + ND_CTA, a_next[1]);
-#pragma unroll
-        for (int q = 0; q < kQuadsPerChunk; q += 2) {
-          if (q < nq) {
-            int a_cur[2][ND_THR];
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-#pragma unroll
-              for (int i = 0; i < ND_THR; ++i) a_cur[h][i] = a_next[h][i];
-            if (q + 2 < nq) {
-              load_offsets<ND_THR>(A + (q + 2) * ND_CTA, a_next[0]);
-              load_offsets<ND_THR>(A + (q + 3) * ND_CTA, a_next[1]);
-            }
-            if (q + 1 < nq) {
-#pragma unroll
-              for (int i = 0; i < ND_THR; ++i)
-                AccPairs<0>::two(acc[i],
-                                 prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair),
-                                 prow + 4u * (static_cast<uint32_t>(a_cur[1][i]) + my_pair));
-            } else {
-#pragma unroll
-              for (int i = 0; i < ND_THR; ++i)
-                AccPairs<0>::one(acc[i],
-                                 prow + 4u * (static_cast<uint32_t>(a_cur[0][i]) + my_pair));
-            }
-          }
-        }
-        bar_arrive(kBarEmpty + k % kRowStages, kThreads);
-        // at most kFlushQuads quads in the 16-bit halves
-        if ((k + 1) % kFlushChunks == 0 && k + 1 < a.nchunks) {
-          drain<ND_THR>(acc, taddr, drained);
-          drained = true;
-        }
-      }
-      if (!aborted) {
-        // final sums: stored part (if any) + the packed halves; pair j of
-        // trial i covers samples my_pair + 32 j and my_pair + 32 j + kHalf.
-        // Per trial, this thread's exact sum, sum of squares and largest
-        // value of the samples it stores (for the detection statistics).
-        long long s1[ND_THR], s2[ND_THR];
-        int32_t mx[ND_THR];
-#pragma unroll
-        for (int i = 0; i < ND_THR; ++i) s1[i] = 0, s2[i] = 0, mx[i] = INT32_MIN;
-#pragma unroll
-        for (int blk = 0; blk < ND_THR * kPairsPerThread / 8; ++blk) {
-          uint32_t v[16];
-          if (drained) {
-            tmem_ld16(taddr + 16u * blk, v);
-          } else {
-#pragma unroll
-            for (int e = 0; e < 16; ++e) v[e] = 0;
-          }
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int m = 8 * blk + e;
-            const int i = m / kPairsPerThread, j = m % kPairsPerThread;
-            const int d = tile * ND_CTA + dg * ND_THR + i;
-            if (d >= a.ndm) continue;
-            int32_t *orow = a.out + static_cast<int64_t>(d) * a.out_pitch;
-            const uint32_t w = acc[i][j];
-            const int64_t t = t_cta + my_pair + 32 * j;
-            const int32_t lo = static_cast<int32_t>(v[2 * e] + (w & 0xffffu));
-            const int32_t hi = static_cast<int32_t>(v[2 * e + 1] + (w >> 16));
-            if (t < a.nsamp_out) {
-              orow[t] = lo;
-              s1[i] += lo, s2[i] += static_cast<long long>(lo) * lo, mx[i] = max(mx[i], lo);
-            }
-            if (t + kHalf < a.nsamp_out) {
-              orow[t + kHalf] = hi;
-              s1[i] += hi, s2[i] += static_cast<long long>(hi) * hi, mx[i] = max(mx[i], hi);
-            }
-          }
-        }
-        if (a.rowsums) {
-          // one warp holds all kTimeTile samples of its trials: reduce over
-          // lanes; integer sums make the row totals independent of order
-#pragma unroll
-          for (int i = 0; i < ND_THR; ++i) {
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
-              s1[i] += __shfl_xor_sync(0xffffffffu, s1[i], o);
-              s2[i] += __shfl_xor_sync(0xffffffffu, s2[i], o);
-              mx[i] = max(mx[i], __shfl_xor_sync(0xffffffffu, mx[i], o));
-            }
-            const int d = tile * ND_CTA + dg * ND_THR + i;
-            if (lane == 0 && d < a.ndm) {
-              atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d),
-                        static_cast<unsigned long long>(s1[i]));
-              atomicAdd(reinterpret_cast<unsigned long long *>(a.rowsums + 2 * d + 1),
-                        static_cast<unsigned long long>(s2[i]));
-              a.tilemax[static_cast<int64_t>(d) * a.ntiles_t + ttile] = mx[i];
-            }
-          }
-        }
-      }
+      // the accumulating role for this beam's tile width
+      const AccArgs args{a,    smem, bar0,    rec_off, rec_bytes, kRec, prow_off, prow_bytes,
+                         tmem_base, warp, lane, dg, my_pair, tile, ttile, t_cta};
+      if (a.nd_thr == kNdThr)
+        aborted = acc_item<kNdThr>(args);
+      else if (a.nd_thr == kNdThr / 2)
+        aborted = acc_item<kNdThr / 2>(args);
+      else
+        aborted = acc_item<kNdThr / 4>(args);
     }
 
     // the item is complete in every warp (tensor-memory accesses waited)
@@ -576,12 +623,11 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
   if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
 }
 
-// The kernel of ND_THR trials per thread at staging depth copy_ahead.
-template <int ND_THR>
+// The kernel at staging depth copy_ahead (every tile width).
 auto pick_depth(int copy_ahead) {
-  return copy_ahead == 1   ? dd_dedisperse_quad_u8<ND_THR, 1>
-         : copy_ahead == 3 ? dd_dedisperse_quad_u8<ND_THR, 3>
-                           : dd_dedisperse_quad_u8<ND_THR, 2>;
+  return copy_ahead == 1   ? dd_dedisperse_quad_u8<1>
+         : copy_ahead == 3 ? dd_dedisperse_quad_u8<3>
+                           : dd_dedisperse_quad_u8<2>;
 }
 
 }  // namespace
@@ -619,9 +665,14 @@ int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int copy_ahead,
     *err = cudaErrorInvalidValue;
     return -1;
   }
-  auto kern = nd_thr == kNdThr       ? pick_depth<kNdThr>(copy_ahead)
-              : nd_thr == kNdThr / 2 ? pick_depth<kNdThr / 2>(copy_ahead)
-                                     : pick_depth<kNdThr / 4>(copy_ahead);
+  for (int i = 0; i < nbeams; ++i) {
+    const int w = beams[i].nd_thr;
+    if (w != kNdThr && w != kNdThr / 2 && w != kNdThr / 4) {
+      *err = cudaErrorInvalidValue;
+      return -1;
+    }
+  }
+  auto kern = pick_depth(copy_ahead);
   *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
   if (*err == cudaSuccess)
@@ -657,6 +708,7 @@ Beam quad_beam(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp
   b.raw_stride = q.tables.raw_stride;
   b.prow_words = q.tables.prow_words;
   b.ntiles_dm = q.tables.ntiles;
+  b.nd_thr = q.tables.nd_thr;
   b.ntiles_t = static_cast<int32_t>((nsamp_out + kTimeTile - 1) / kTimeTile);
   return b;
 }

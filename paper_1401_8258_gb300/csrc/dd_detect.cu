@@ -30,6 +30,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <mutex>
 
 #include "dd_internal.h"
@@ -521,9 +522,120 @@ dd_tile_write(const T *__restrict__ D, int64_t n, int ntiles,
   }
 }
 
+// ---- the same for the staged 8-bit beams of a batch, in two launches ----
+
+struct DetectLaunch {
+  ddk::DetectBeam beams[ddk::kMaxDetectBeams];
+  int32_t nbeams;
+  double thr;
+};
+
+// (beam, row) of CTA `row` of a batched launch (rows of beam b start at
+// beams[b].row_begin).
+__device__ __forceinline__ int beam_of_row(const DetectLaunch &L, int row) {
+  int b = 0;
+  while (b + 1 < L.nbeams && row >= L.beams[b + 1].row_begin) ++b;
+  return b;
+}
+
+// dd_tile_count for every row of every beam of the launch.
+__global__ void __launch_bounds__(kTileThreads)
+dd_tile_count_beams(const __grid_constant__ DetectLaunch L) {
+  __shared__ dd_row_stats s_st;
+  const ddk::DetectBeam &a = L.beams[beam_of_row(L, blockIdx.x)];
+  const int d = blockIdx.x - a.row_begin;
+  if (threadIdx.x == 0) {
+    const unsigned long long s2 = static_cast<unsigned long long>(a.rowsums[2 * d + 1]);
+    s_st = finish_i32(a.rowsums[2 * d], static_cast<unsigned __int128>(s2), a.n, L.thr);
+    a.stats[d] = s_st;
+  }
+  __syncthreads();
+  const dd_row_stats st = s_st;
+  const int32_t *tmax = a.tilemax + static_cast<int64_t>(d) * a.ntiles;
+  count_row_tiles<int32_t, ddk::kTileSamples>(
+      a.D + static_cast<int64_t>(d) * a.n, a.n, a.ntiles, st,
+      [&](int tt) { return static_cast<int64_t>(tmax[tt]) >= st.ithr; },
+      a.tilecount + static_cast<int64_t>(d) * a.ntiles, a.rowcount + d);
+}
+
+// dd_tile_write for every row of every beam of the launch; each row's
+// offset in its beam's candidate list is the sum of the earlier rows'
+// counts (added up by the row's own CTA, so no scan launch is needed), and
+// the CTA of a beam's last row stores the beam's total.
+__global__ void __launch_bounds__(kTileThreads)
+dd_tile_write_beams(const __grid_constant__ DetectLaunch L) {
+  __shared__ long long s_part[kTileThreads / 32];
+  const ddk::DetectBeam &a = L.beams[beam_of_row(L, blockIdx.x)];
+  const int d = blockIdx.x - a.row_begin;
+  long long before = 0;
+  for (int r = threadIdx.x; r < d; r += kTileThreads) before += a.rowcount[r];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = before;
+  __syncthreads();
+  before = 0;
+#pragma unroll
+  for (int w = 0; w < kTileThreads / 32; ++w) before += s_part[w];
+  const int64_t mine = a.rowcount[d];
+  if (d == a.ndm - 1 && threadIdx.x == 0) *a.total = before + mine;
+  if (mine == 0 || before >= a.capacity) return;  // uniform across the CTA
+  const dd_row_stats st = a.stats[d];
+  const int32_t *row = a.D + static_cast<int64_t>(d) * a.n;
+  const int32_t *tcnt = a.tilecount + static_cast<int64_t>(d) * a.ntiles;
+  constexpr int kPer = ddk::kTileSamples / kTileThreads;
+  int64_t run = before;
+  for (int tt = 0; tt < a.ntiles && run < a.capacity; ++tt) {
+    if (tcnt[tt] == 0) continue;  // same in every thread
+    const int64_t t0 = static_cast<int64_t>(tt) * ddk::kTileSamples + threadIdx.x * kPer;
+    unsigned mask = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u)
+      if (t0 + u < a.n && is_candidate(row[t0 + u], st)) mask |= 1u << u;
+    int tile_total = 0;
+    int64_t idx = run + block_exclusive(__popc(mask), &tile_total);
+    while (mask) {
+      const int u = __ffs(mask) - 1;
+      mask &= mask - 1;
+      if (idx < a.capacity) {
+        const double v = static_cast<double>(row[t0 + u]);
+        dd_candidate cd;
+        cd.dm_idx = d;
+        cd.t = static_cast<int32_t>(t0 + u);
+        cd.value = static_cast<float>(v);
+        cd.snr = static_cast<float>(snr_of(v, st.mean, st.sigma));
+        a.cands[idx] = cd;
+      }
+      ++idx;
+    }
+    run += tile_total;
+  }
+}
+
 }  // namespace
 
 namespace ddk {
+
+int launch_tiled_detect_beams(const DetectBeam *beams, int nbeams, float nsigma,
+                              cudaStream_t stream, cudaError_t *err) {
+  if (nbeams < 1 || nbeams > kMaxDetectBeams) {
+    *err = cudaErrorInvalidValue;
+    return -1;
+  }
+  DetectLaunch L;
+  std::memset(&L, 0, sizeof(L));
+  int rows = 0;
+  for (int i = 0; i < nbeams; ++i) {
+    L.beams[i] = beams[i];
+    L.beams[i].row_begin = rows;
+    rows += beams[i].ndm;
+  }
+  L.nbeams = nbeams;
+  L.thr = static_cast<double>(nsigma);
+  dd_tile_count_beams<<<rows, kTileThreads, 0, stream>>>(L);
+  dd_tile_write_beams<<<rows, kTileThreads, 0, stream>>>(L);
+  *err = cudaGetLastError();
+  return *err == cudaSuccess ? 2 : -1;
+}
 
 int launch_stats(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
                  cudaStream_t stream, cudaError_t *err) {

@@ -132,8 +132,11 @@ inline int elem_size(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F
 // Dedispersion: out[d][t] = sum_c block[c][t + delays[c][d]] for t < nsamp_out.
 // Each launcher returns the number of kernels queued, or -1 with the CUDA
 // error in *err.
+// With tilestats non-null (float plans), also each (row, 256-sample time
+// tile)'s partial statistics, as launch_dedisperse_octet.
 int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
-                             void *out, int64_t out_pitch, cudaStream_t stream, cudaError_t *err);
+                             void *out, int64_t out_pitch, float4 *tilestats, cudaStream_t stream,
+                             cudaError_t *err);
 // Staged quad kernel (u8): needs the plan's quad tables, a 16-byte aligned
 // block, a pitch that is a multiple of 16 bytes and at most 65535 time tiles.
 bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
@@ -195,6 +198,26 @@ int launch_candidates(dd_plan *p, const void *out, int64_t nsamp_out, float nsig
 int launch_tiled_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
                         dd_candidate *cands, int64_t capacity, cudaStream_t stream,
                         cudaError_t *err);
+// launch_tiled_detect for up to kMaxDetectBeams staged 8-bit beams at once,
+// in two launches (count, then write with each row's offset summed in place
+// and each beam's total stored to *total): the same statistics, thresholds
+// and candidate lists.
+struct DetectBeam {
+  const int32_t *D;  // [ndm][n] outputs
+  int64_t n;
+  int32_t ntiles, ndm, row_begin;  // row_begin: set by the launcher
+  const long long *rowsums;        // [ndm][2]
+  const int32_t *tilemax;          // [ndm][ntiles]
+  dd_row_stats *stats;             // [ndm]
+  int32_t *tilecount;              // [ndm][ntiles]
+  int64_t *rowcount;               // [ndm]
+  dd_candidate *cands;
+  int64_t capacity;
+  int64_t *total;
+};
+constexpr int kMaxDetectBeams = 64;
+int launch_tiled_detect_beams(const DetectBeam *beams, int nbeams, float nsigma,
+                              cudaStream_t stream, cudaError_t *err);
 // The same from the staged float kernel's per-tile partial statistics
 // (float rows): each row's mean and rms combine its tiles' partials in a
 // fixed order in FP64; candidates as launch_candidates.

@@ -182,6 +182,7 @@ struct Beam {
   int64_t out_pitch;  // elements between output rows (>= nsamp_out)
   int64_t item_begin;
   int32_t ndm, nchunks, nchan_pad, rec_words, raw_stride, prow_words, ntiles_dm, ntiles_t;
+  int32_t nd_thr;  // trials per accumulating thread of this beam's tables (tile width / 16)
 };
 constexpr int kMaxBeams = 64;  // beams per launch (the descriptors travel as kernel parameters)
 

@@ -222,3 +222,44 @@ def test_full_size_batch_of_32_beams_sampled_rows():
     del outs, dblocks
     for p in plans:
         p.close()
+
+
+def test_batch_of_mixed_widths_and_depths_is_one_launch_and_two_detection_launches():
+    """Beams whose plans take 64-, 32- and 16-trial tiles and different
+    staging depths share one persistent launch (the kernel dispatches on each
+    beam's width; the batch runs at its most common depth), and their
+    detection runs as two launches for all of them: at most three kernels per
+    batch step, each beam's results still those of the beam alone."""
+    base = synth.workload("full_block_u8")
+    wide = synth.scaled(base, nchan=256, ndm=160)            # 62.5 kHz channels: 16 trials
+    mid = synth.scaled(base, nchan=512, ndm=200)             # 31.25 kHz channels
+    narrow = synth.scaled(base, nchan=512, ndm=200)
+    narrow.chan_width_mhz = base.chan_width_mhz              # 15.6 kHz: 64 trials
+    workloads = [wide, mid, narrow, synth.scaled(base, nchan=384, ndm=96)]
+    for wl in workloads:
+        wl.nsamp = (maxshift(wl) + 6000 + 15) // 16 * 16  # whole 16-byte rows: staged
+    blocks, _ = make_beams(workloads, seed=41)
+    dblocks = [torch.from_numpy(np.ascontiguousarray(b)).to(DEV) for b in blocks]
+    plans = [plan_of(wl) for wl in workloads]
+    infos = [dd._native.dd_plan_kernel_info(p.handle, b, b.stride(0))
+             for p, b in zip(plans, dblocks)]
+    assert all(i["staged"] for i in infos), infos
+    widths = {i["dms_per_cta"] for i in infos}
+    assert len(widths) >= 2, widths
+    dd._native.dd_plan_set_staging_depth(plans[0].handle, 3)
+    dd._native.dd_plan_set_staging_depth(plans[1].handle, 1)
+    alone = [run_alone(p, b, 4.0, 1 << 16) for p, b in zip(plans, dblocks)]
+    with dd.Batch(plans) as batch:
+        batch.run(dblocks, 4.0)
+        before = sum(p.launch_count() for p in plans)
+        outs, cands, totals = batch.run(dblocks, 4.0)
+        launches = sum(p.launch_count() for p in plans) - before
+        for i in range(len(plans)):
+            out_a, c_a, t_a, m_a, s_a = alone[i]
+            assert totals[i] == t_a and torch.equal(outs[i], out_a)
+            assert np.array_equal(cands[i], c_a)
+            mean, sigma = plans[i].stats()
+            assert np.array_equal(mean, m_a) and np.array_equal(sigma, s_a)
+    assert launches <= 3, launches
+    for p in plans:
+        p.close()

@@ -136,12 +136,29 @@ def test_run_constant_rows_have_no_candidates():
     assert run["total"] == 0 and np.all(run["sigma"] == 0.0)
 
 
-def test_run_float_plan_takes_the_plain_kernel_with_identical_results():
+@pytest.mark.parametrize("dtype", ["f32", "f16"])
+def test_run_float_plan_on_the_plain_kernel_fuses_detection(dtype):
+    """The single-beam geometry (64 wide channels, DM step 1) takes the
+    plain-load kernel, which also keeps per-tile partial statistics for
+    dd_run: output identical to dd_execute, statistics within 1e-6 of the
+    separate pass, statistics and candidates against the FP64 oracle."""
+    from tests.test_gpu_parity import assert_detection
     wl = synth.workload("single_beam_f32")
+    wl.dtype = dtype
     delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
-    block, _ = synth.make_block(wl, seed=2, delays=delays)
+    block, pulses = synth.make_block(wl, seed=2, delays=delays)
     sep, run = both_paths(wl, block, 5.0, expect_staged=False)
-    assert_same(sep, run)
+    assert torch.equal(sep["out"], run["out"]) and sep["st"] == run["st"]
+    np.testing.assert_allclose(run["mean"], sep["mean"], rtol=1e-6, atol=1e-6 * np.sqrt(wl.nchan))
+    np.testing.assert_allclose(run["sigma"], sep["sigma"], rtol=1e-6)
+    ref = oracle.dedisperse(block, delays)
+    res = {"D": run["out"].cpu().numpy(), "cands": run["cands"], "total": run["total"],
+           "mean": run["mean"], "sigma": run["sigma"]}
+    assert_detection(wl, ref, res, 5.0, block, delays)
+    p = pulses[0]
+    hit = (run["cands"]["dm_idx"] == p.dm_idx) & (run["cands"]["t"] >= p.t0) & \
+        (run["cands"]["t"] < p.t0 + p.width)
+    assert hit.any()
 
 
 def test_run_records_the_phase_event():
