@@ -177,8 +177,13 @@ int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma, dd_c
  * dedispersion kernel, for timing the phases.  When the staged kernel runs,
  * it also accumulates each DM row's exact integer sums and the largest value
  * of each 512-sample time tile as it writes out, so the detection reads out
- * only in the tiles that can hold a candidate instead of twice in full.
- * Synchronises `stream` once. */
+ * only in the tiles that can hold a candidate instead of twice in full; the
+ * float kernels keep per-tile partial statistics the same way.  Synchronises
+ * `stream` once -- except for small float beams that the staged float kernel
+ * does not take, whose whole path runs as one cooperative launch: dd_run
+ * then returns as soon as that launch has stored the count in host memory,
+ * when every output, statistic and candidate is written, without waiting
+ * for the launch to retire (later work on `stream` is ordered after it). */
 int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t pitch_elems, void *out,
            float nsigma, dd_candidate *cands, int64_t capacity, int64_t *count, void *stream,
            void *event);
@@ -328,6 +333,8 @@ int dd_plan_set_staging_depth(dd_plan *p, int32_t copy_ahead);
 
 /* Fault injection for tests of the timeout path: with skip_copies != 0 the
  * staged kernel queues none of its bulk copies, so its first bounded wait
+ * runs out, and dd_run's one-launch path for small float beams waits at its
+ * first grid barrier for one arrival more than its grid makes, so that wait
  * runs out (no device fault, no hang).  0 restores normal operation. */
 int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies);
 

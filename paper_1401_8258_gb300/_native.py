@@ -148,12 +148,14 @@ def _check(status: int, what: str, allow=()) -> int:
 
 def _addr(x) -> int | None:
     """Device or host address of a torch tensor / numpy array / int."""
+    try:
+        return x.data_ptr()  # torch tensors, the common case first
+    except AttributeError:
+        pass
     if x is None:
         return None
     if isinstance(x, int):
         return x
-    if hasattr(x, "data_ptr"):
-        return x.data_ptr()
     if isinstance(x, np.ndarray):
         return x.ctypes.data
     raise TypeError(f"cannot take the address of {type(x)}")
@@ -247,9 +249,9 @@ def dd_run(plan, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity, str
     or raw handle) recorded after the dedispersion kernel."""
     cnt = ctypes.c_int64(0)
     ev = None if event is None else int(getattr(event, "cuda_event", event))
-    st = load().dd_run(plan, _addr(block), int(nsamp_in), int(pitch_elems), _addr(out),
-                       float(nsigma), _addr(cands), int(capacity), ctypes.addressof(cnt),
-                       _stream(stream), ev)
+    st = (_lib or load()).dd_run(plan, _addr(block), int(nsamp_in), int(pitch_elems), _addr(out),
+                                 float(nsigma), _addr(cands), int(capacity),
+                                 ctypes.addressof(cnt), _stream(stream), ev)
     _check(st, "dd_run", allow=(DD_ERR_OVERFLOW,))
     return st, int(cnt.value)
 

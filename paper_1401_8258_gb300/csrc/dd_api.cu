@@ -102,6 +102,57 @@ int ensure_tile_workspace(dd_plan *p, size_t entries, bool float_rows = false) {
   return DD_OK;
 }
 
+// The plan's result words: d_total[0] the candidate total, d_total[1] the
+// status word d_error (low half), copied to the pinned h_total together; the
+// arrivals counter of the one-launch path; whether the device takes
+// cooperative launches.
+cudaError_t alloc_result(dd_plan *p) {
+  cudaError_t e = cudaMalloc(&p->d_total, 2 * sizeof(int64_t));
+  if (e == cudaSuccess) p->d_error = reinterpret_cast<int32_t *>(p->d_total + 1);
+  if (e == cudaSuccess) e = cudaMemset(p->d_total, 0, 2 * sizeof(int64_t));
+  if (e == cudaSuccess) e = cudaMallocHost(&p->h_total, 2 * sizeof(int64_t));
+  if (e == cudaSuccess) {
+    p->h_total[0] = p->h_total[1] = 0;
+    e = cudaHostGetDevicePointer(reinterpret_cast<void **>(&p->h_total_dev), p->h_total, 0);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_arrivals, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(p->d_arrivals, 0, sizeof(unsigned long long));
+  p->arrivals_base = 0;
+  int coop = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device);
+  p->coop = coop;
+  return e;
+}
+
+// Queues the copy of the plan's total and status word to h_total.
+cudaError_t queue_result_copy(dd_plan *p, cudaStream_t s) {
+  return cudaMemcpyAsync(p->h_total, p->d_total, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+}
+
+// The status word as copied by queue_result_copy (the caller has
+// synchronised); a set word is cleared on the device.
+int copied_status(dd_plan *p) {
+  int32_t flag = 0;
+  std::memcpy(&flag, p->h_total + 1, sizeof(flag));
+  if (flag == 0) return DD_OK;
+  cudaMemset(p->d_error, 0, sizeof(int32_t));
+  return DD_ERR_DEVICE_TIMEOUT;
+}
+
+// Waits until the one-launch path has stored the candidate total in the
+// pinned h_total[0] (set to -1 before the launch), or until the stream is
+// done (the launch ended without storing it: a wait ran out).
+cudaError_t wait_host_total(const dd_plan *p, cudaStream_t s) {
+  const volatile int64_t *h = p->h_total;
+  for (uint32_t k = 1;; ++k) {
+    if (*h >= 0) return cudaSuccess;
+    if ((k & 63) == 0) {
+      const cudaError_t q = cudaStreamQuery(s);
+      if (q != cudaErrorNotReady) return q;
+    }
+  }
+}
+
 // Reads and clears the sticky device status word (caller has synchronised).
 int take_device_status(dd_plan *p) {
   int32_t flag = 0;
@@ -145,11 +196,11 @@ void destroy_plan(dd_plan *p) {
   free_octet(p->octet);
   p->delays_store.reset();
   free_device(p->d_next_item);
-  free_device(p->d_error);
   free_device(p->d_stats);
   free_device(p->d_counts);
   free_device(p->d_offsets);
-  free_device(p->d_total);
+  free_device(p->d_total);  // with the status word d_error in it
+  free_device(p->d_arrivals);
   free_device(p->d_rowsums);
   free_device(p->d_rowcount);
   free_device(p->d_rowoff);
@@ -355,11 +406,8 @@ int finish_plan(dd_plan *p) {
   const int ds = upload_table(p->h_delays->data(), p->h_delays->size(), &p->delays_store);
   if (ds != DD_OK) return ds;
   p->d_delays = p->delays_store->ptr;
-  cudaError_t e = cudaMalloc(&p->d_error, sizeof(int32_t));
+  cudaError_t e = alloc_result(p);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_stats, sizeof(dd_row_stats) * p->ndm);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_total, sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMallocHost(&p->h_total, sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
   if (e != cudaSuccess) return cuda_status(e);
   return p->dtype == DD_U8 ? setup_quad(p) : setup_octet(p);
 }
@@ -485,11 +533,8 @@ extern "C" int dd_plan_create_like(dd_plan **out, const dd_plan *src) {
     destroy_plan(p);
     return DD_ERR_CUDA;
   }
-  cudaError_t e = cudaMalloc(&p->d_error, sizeof(int32_t));
+  cudaError_t e = alloc_result(p);
   if (e == cudaSuccess) e = cudaMalloc(&p->d_stats, sizeof(dd_row_stats) * p->ndm);
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_total, sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMallocHost(&p->h_total, sizeof(int64_t));
-  if (e == cudaSuccess) e = cudaMemset(p->d_error, 0, sizeof(int32_t));
   if (e == cudaSuccess && (p->quad || p->octet))
     e = cudaMalloc(&p->d_next_item, sizeof(unsigned long long));
   if (e != cudaSuccess) {
@@ -627,10 +672,10 @@ extern "C" int dd_detect(dd_plan *p, const void *out, int64_t nsamp_out, float n
   n = ddk::launch_candidates(p, out, nsamp_out, nsigma, cands, capacity, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
-  err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  err = queue_result_copy(p, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return cuda_status(err);
-  st = take_device_status(p);
+  st = copied_status(p);
   if (st != DD_OK) return st;
   p->stats_valid = true;
   *count = *p->h_total;
@@ -659,6 +704,28 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
     if (st != DD_OK) return st;
     p->stats_valid = false;
     cudaError_t err = cudaSuccess;
+    if (ddk::small_supported(p, block, pitch_elems, nsamp_out)) {
+      // small beam: the whole path in one launch, which stores the total in
+      // the pinned h_total[0] only when every grid wait succeeded
+      p->h_total[0] = -1;
+      if (ddk::launch_run_small(p, block, pitch_elems, nsamp_out, out, nsigma, cands, capacity, s,
+                                &err) < 0)
+        return cuda_status(err);
+      p->launches += 1;
+      if (ev && cudaEventRecord(ev, s) != cudaSuccess) return DD_ERR_CUDA;
+      err = wait_host_total(p, s);
+      if (err != cudaSuccess) return cuda_status(err);
+      if (p->h_total[0] < 0) {
+        // a grid wait ran out: the barrier counter starts again from zero
+        cudaMemset(p->d_arrivals, 0, sizeof(unsigned long long));
+        p->arrivals_base = 0;
+        st = take_device_status(p);
+        return st != DD_OK ? st : DD_ERR_DEVICE_TIMEOUT;
+      }
+      p->stats_valid = true;
+      *count = p->h_total[0];
+      return *count > capacity ? DD_ERR_OVERFLOW : DD_OK;
+    }
     int n = p->path == 0 && ddk::octet_supported(p, block, pitch_elems, nsamp_out)
                 ? ddk::launch_dedisperse_octet(p, block, pitch_elems, nsamp_out, out, nsamp_out,
                                                p->d_tilestats, s, &err)
@@ -670,10 +737,10 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
     n = ddk::launch_tiled_detect_f32(p, out, nsamp_out, nsigma, cands, capacity, s, &err);
     if (n < 0) return cuda_status(err);
     p->launches += n;
-    err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    err = queue_result_copy(p, s);
     if (err == cudaSuccess) err = cudaStreamSynchronize(s);
     if (err != cudaSuccess) return cuda_status(err);
-    st = take_device_status(p);
+    st = copied_status(p);
     if (st != DD_OK) return st;
     p->stats_valid = true;
     *count = *p->h_total;
@@ -700,10 +767,10 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
   n = ddk::launch_tiled_detect(p, out, nsamp_out, nsigma, cands, capacity, s, &err);
   if (n < 0) return cuda_status(err);
   p->launches += n;
-  err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+  err = queue_result_copy(p, s);
   if (err == cudaSuccess) err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return cuda_status(err);
-  st = take_device_status(p);
+  st = copied_status(p);
   if (st != DD_OK) return st;
   p->stats_valid = true;
   *count = *p->h_total;
@@ -833,32 +900,27 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
     }
     if (nl < 0) return cuda_status(err);
     p->launches += nl;
-    // each beam has its own plan, hence its own pinned count slot
-    err = cudaMemcpyAsync(p->h_total, p->d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, s);
+    // each beam has its own plan, hence its own pinned count and status slot
+    err = queue_result_copy(p, s);
     if (err != cudaSuccess) return cuda_status(err);
   }
   return DD_OK;
 }
 
-// Waits for queued beams and collects their status and counts.
-int finish_beams(dd_plan *const *plans, int n, int device, int32_t *status,
-                 const int64_t *capacity, int64_t *counts, void *stream) {
+// Waits for queued beams and collects their status and counts (copied to
+// each plan's pinned h_total by queue_beams; a shared launch records a
+// timeout in its first plan's status word).
+int finish_beams(dd_plan *const *plans, int n, int device, const int64_t *capacity,
+                 int64_t *counts, void *stream) {
   DeviceScope scope(device);
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
   cudaError_t err = cudaStreamSynchronize(s);
   if (err != cudaSuccess) return cuda_status(err);
   int result = DD_OK;
-  int32_t flag = 0;
-  if (cudaMemcpy(&flag, status, sizeof(flag), cudaMemcpyDeviceToHost) != cudaSuccess)
-    return DD_ERR_CUDA;
-  if (flag != 0) {
-    cudaMemset(status, 0, sizeof(int32_t));
-    result = DD_ERR_DEVICE_TIMEOUT;
-  }
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
-    const int st = take_device_status(p);
+    const int st = copied_status(p);
     if (st != DD_OK && result == DD_OK) result = st;
     counts[i] = *p->h_total;
     p->stats_valid = true;
@@ -877,7 +939,7 @@ int run_beams(dd_plan *const *plans, int n, int device, int sm_count,
   const int st = queue_beams(plans, n, device, sm_count, next_item, status, block, nsamp_in,
                              pitch_elems, out, nsigma, cands, capacity, counts, stream);
   if (st != DD_OK) return st;
-  return finish_beams(plans, n, device, status, capacity, counts, stream);
+  return finish_beams(plans, n, device, capacity, counts, stream);
 }
 
 
@@ -891,7 +953,6 @@ struct dd_batch {
   int sm_count = 0;
   std::vector<dd_plan *> plans;
   unsigned long long *d_next_item = nullptr;  // work-queue head of the shared launches
-  int32_t *d_error = nullptr;                 // status word of the shared launches
   int64_t launches = 0;
   cudaStream_t capture = nullptr;       // private stream for graph capture
   cudaGraphExec_t exec = nullptr;       // captured launch sequence (null: none)
@@ -922,12 +983,9 @@ extern "C" int dd_batch_create(dd_batch **out, dd_plan *const *plans, int32_t np
   DeviceScope scope(b->device);
   cudaError_t e = scope.ok() ? cudaSuccess : cudaErrorInvalidDevice;
   if (e == cudaSuccess) e = cudaMalloc(&b->d_next_item, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&b->d_error, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMemset(b->d_error, 0, sizeof(int32_t));
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->capture, cudaStreamNonBlocking);
   if (e != cudaSuccess) {
     free_device(b->d_next_item);
-    free_device(b->d_error);
     if (b->capture) cudaStreamDestroy(b->capture);
     delete b;
     return cuda_status(e);
@@ -941,7 +999,6 @@ extern "C" int dd_batch_destroy(dd_batch *b) {
   DeviceScope scope(b->device);
   if (scope.ok()) cudaDeviceSynchronize();
   free_device(b->d_next_item);
-  free_device(b->d_error);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->capture) cudaStreamDestroy(b->capture);
   delete b;
@@ -997,7 +1054,7 @@ bool capture_batch(dd_batch *b, std::vector<uint64_t> key, const void *const *bl
   }
   if (cudaStreamBeginCapture(b->capture, cudaStreamCaptureModeRelaxed) != cudaSuccess) return false;
   const int st = queue_beams(b->plans.data(), n, b->device, b->sm_count, b->d_next_item,
-                             b->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands,
+                             b->plans[0]->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands,
                              capacity, counts, b->capture);
   cudaGraph_t graph = nullptr;
   const cudaError_t e = cudaStreamEndCapture(b->capture, &graph);
@@ -1048,10 +1105,10 @@ extern "C" int dd_batch_run(dd_batch *b, const void *const *block, const int64_t
       return DD_ERR_CUDA;
     ++b->replays;
     for (int i = 0; i < n; ++i) b->plans[i]->launches += b->graph_launches[i];
-    return finish_beams(b->plans.data(), n, b->device, b->d_error, capacity, counts, stream);
+    return finish_beams(b->plans.data(), n, b->device, capacity, counts, stream);
   }
   const int st = run_beams(b->plans.data(), n, b->device, b->sm_count, b->d_next_item,
-                           b->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity,
+                           b->plans[0]->d_error, block, nsamp_in, pitch_elems, out, nsigma, cands, capacity,
                            counts, stream);
   if (st == DD_OK || st == DD_ERR_OVERFLOW) {
     DeviceScope scope(b->device);
@@ -1080,7 +1137,6 @@ struct dd_stream {
   void *buf[2] = {nullptr, nullptr};  // [nchan][pitch]: tail (maxshift samples), then the block
   int cur = 0;                        // buffer whose first maxshift samples hold the tail
   unsigned long long *d_next_item = nullptr;
-  int32_t *d_error = nullptr;
 };
 
 namespace {
@@ -1095,7 +1151,6 @@ void free_stream(dd_stream *s) {
   free_device(s->buf[0]);
   free_device(s->buf[1]);
   free_device(s->d_next_item);
-  free_device(s->d_error);
   delete s;
 }
 
@@ -1141,8 +1196,6 @@ extern "C" int dd_stream_create(dd_stream **out, dd_plan *p, int64_t block_sampl
     if (e == cudaSuccess) e = cudaMemset(s->buf[k], 0, bytes);  // no samples before the first block
   }
   if (e == cudaSuccess) e = cudaMalloc(&s->d_next_item, sizeof(unsigned long long));
-  if (e == cudaSuccess) e = cudaMalloc(&s->d_error, sizeof(int32_t));
-  if (e == cudaSuccess) e = cudaMemset(s->d_error, 0, sizeof(int32_t));
   if (e != cudaSuccess) {
     free_stream(s);
     return cuda_status(e);
@@ -1192,7 +1245,7 @@ extern "C" int dd_streams_push(dd_stream *const *streams, int32_t n, const void 
     if (e != cudaSuccess) return cuda_status(e);
   }
   const int rc = run_beams(plans.data(), n, plans[0]->device, plans[0]->sm_count,
-                           streams[0]->d_next_item, streams[0]->d_error, bufs.data(), nin.data(),
+                           streams[0]->d_next_item, plans[0]->d_error, bufs.data(), nin.data(),
                            pitch.data(), out, nsigma, cands, capacity, counts, stream);
   if (rc != DD_OK && rc != DD_ERR_OVERFLOW) return rc;
   // the last maxshift samples become the next push's tail, in the other buffer

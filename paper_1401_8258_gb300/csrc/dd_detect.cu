@@ -33,6 +33,7 @@
 #include <cstring>
 #include <mutex>
 
+#include "dd_detect_dev.cuh"
 #include "dd_internal.h"
 
 namespace {
@@ -59,10 +60,6 @@ __device__ double u128_to_double_rn(unsigned __int128 v) {
   return scalbn(__ull2double_rn(top), drop);
 }
 
-__device__ __forceinline__ double snr_of(double v, double mean, double sigma) {
-  return __ddiv_rn(__dsub_rn(v, mean), sigma);
-}
-
 // Smallest int64 v in [INT32_MIN, INT32_MAX + 1] with snr_of(v) > thr, where
 // INT32_MAX + 1 stands for "none".  snr_of is monotone non-decreasing in v
 // (IEEE subtraction and division by sigma > 0 are monotone), so a bisection
@@ -77,32 +74,12 @@ __device__ int64_t int_threshold(double mean, double sigma, double thr) {
   return hi;
 }
 
-// Order-preserving map of non-NaN floats onto uint32.
-__device__ __forceinline__ uint32_t float_order(float x) {
-  const uint32_t b = __float_as_uint(x);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float order_float(uint32_t o) {
-  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
-}
-
-// Smallest float x (-inf .. +inf) with snr_of((double)x) > thr; +inf passes
-// for any finite thr, so it bounds the search.
-__device__ float float_threshold(double mean, double sigma, double thr) {
-  uint32_t lo = float_order(-INFINITY), hi = float_order(INFINITY);
-  if (snr_of(-static_cast<double>(INFINITY), mean, sigma) > thr) return -INFINITY;
-  while (hi - lo > 1) {
-    const uint32_t mid = lo + (hi - lo) / 2;
-    if (snr_of(static_cast<double>(order_float(mid)), mean, sigma) > thr) hi = mid; else lo = mid;
-  }
-  return order_float(hi);
-}
-
 // Statistics of an integer row from its exact sums S1 = sum D, S2 = sum D^2
 // over N samples:
 //   mean = S1 / N,  rms = sqrt((double)(N*S2 - S1^2)) / N
 // (numerator exact in 128 bits, one rounding to double), and the row's
-// integer candidate threshold.
+// integer candidate threshold (int_threshold_window, else the bisection).
+// Called by all 32 lanes of one warp (each computes the same result).
 __device__ dd_row_stats finish_i32(long long s1, unsigned __int128 s2, int64_t n, double thr) {
   const __int128 S1 = s1;
   const __int128 S2 = static_cast<__int128>(s2);
@@ -112,7 +89,9 @@ __device__ dd_row_stats finish_i32(long long s1, unsigned __int128 s2, int64_t n
   st.mean = __ddiv_rn(__ll2double_rn(s1), dn);
   st.sigma = __ddiv_rn(__dsqrt_rn(u128_to_double_rn(static_cast<unsigned __int128>(num))), dn);
   st.any = st.sigma > 0.0;
-  st.ithr = st.any ? int_threshold(st.mean, st.sigma, thr) : static_cast<int64_t>(INT32_MAX) + 1;
+  st.ithr = static_cast<int64_t>(INT32_MAX) + 1;
+  if (st.any && !int_threshold_window(st.mean, st.sigma, thr, &st.ithr))  // uniform in the warp
+    st.ithr = int_threshold(st.mean, st.sigma, thr);
   st.fthr = INFINITY;
   return st;
 }
@@ -149,7 +128,10 @@ dd_stats_i32(const int32_t *__restrict__ D, int64_t n, double thr,
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) stats[blockIdx.x] = finish_i32(s_s1[0], s_s2[0], n, thr);
+  if (threadIdx.x < 32) {
+    const dd_row_stats st = finish_i32(s_s1[0], s_s2[0], n, thr);
+    if (threadIdx.x == 0) stats[blockIdx.x] = st;
+  }
 }
 
 // One CTA per row of f32 values: double sums of (x - K) with K the row's
@@ -179,7 +161,7 @@ dd_stats_f32(const float *__restrict__ D, int64_t n, double thr,
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {  // one warp, every lane the same result
     const double dn = static_cast<double>(n);
     const double m1 = s_s1[0] / dn;
     const double var = s_s2[0] / dn - m1 * m1;
@@ -187,18 +169,12 @@ dd_stats_f32(const float *__restrict__ D, int64_t n, double thr,
     st.mean = K + m1;
     st.sigma = sqrt(var > 0.0 ? var : 0.0);
     st.any = st.sigma > 0.0;
-    st.fthr = st.any ? float_threshold(st.mean, st.sigma, thr) : INFINITY;
+    st.fthr = INFINITY;
+    if (st.any && !float_threshold_window(st.mean, st.sigma, thr, &st.fthr))
+      st.fthr = float_threshold(st.mean, st.sigma, thr);
     st.ithr = static_cast<int64_t>(INT32_MAX) + 1;
-    stats[blockIdx.x] = st;
+    if (threadIdx.x == 0) stats[blockIdx.x] = st;
   }
-}
-
-// The candidate test, equivalent to snr > nsigma in IEEE double.
-__device__ __forceinline__ bool is_candidate(int32_t v, const dd_row_stats &st) {
-  return st.any && static_cast<int64_t>(v) >= st.ithr;
-}
-__device__ __forceinline__ bool is_candidate(float v, const dd_row_stats &st) {
-  return st.any && v >= st.fthr;
 }
 
 template <typename T>
@@ -257,7 +233,7 @@ dd_scan(const int64_t *__restrict__ counts, int64_t m, int64_t *__restrict__ off
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kCountThreads)
+__global__ void __launch_bounds__(kCountThreads, 4)  // 4 CTAs per SM: no spills
 dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__restrict__ stats,
          const int64_t *__restrict__ counts, const int64_t *__restrict__ offsets,
          dd_candidate *__restrict__ cands, int64_t capacity) {
@@ -306,77 +282,6 @@ dd_write(const T *__restrict__ D, int64_t n, int nchunks, const dd_row_stats *__
 
 // ---- tiled detection after the staged kernels ----
 
-constexpr int kTileThreads = 256;
-constexpr int kTileList = 1024;                       // tiles examined per round
-
-// Exclusive prefix of v over the CTA (kTileThreads threads); *total gets the sum.
-__device__ __forceinline__ int block_exclusive(int v, int *total) {
-  __shared__ int s_warp[kTileThreads / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  int inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int u = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += u;
-  }
-  __syncthreads();  // s_warp free from any previous call
-  if (lane == 31) s_warp[w] = inc;
-  __syncthreads();
-  int before = 0, all = 0;
-#pragma unroll
-  for (int k = 0; k < kTileThreads / 32; ++k) {
-    const int x = s_warp[k];
-    before += k < w ? x : 0;
-    all += x;
-  }
-  *total = all;
-  return before + inc - v;
-}
-
-// Row d's candidates per tile of TILE samples: the tiles that `reaches(tt)`
-// admits (their largest value passes the threshold; no other tile can hold a
-// candidate) are read and counted into tcnt[tt], the others get 0; the row
-// total goes to *rowcount.  Called by the whole CTA after st is final.
-template <typename T, int TILE, typename Reaches>
-__device__ void count_row_tiles(const T *__restrict__ row, int64_t n, int ntiles,
-                                const dd_row_stats &st, Reaches reaches,
-                                int32_t *__restrict__ tcnt, int64_t *__restrict__ rowcount) {
-  constexpr int kPer = TILE / kTileThreads;  // consecutive samples per thread
-  static_assert(TILE % kTileThreads == 0, "whole samples per thread");
-  __shared__ int s_list[kTileList];
-  __shared__ int s_nlist;
-  int64_t total = 0;  // thread 0
-  for (int base = 0; base < ntiles; base += kTileList) {
-    if (threadIdx.x == 0) s_nlist = 0;
-    __syncthreads();
-    for (int k = threadIdx.x; k < kTileList && base + k < ntiles; k += kTileThreads) {
-      const int tt = base + k;
-      if (st.any && reaches(tt)) {
-        s_list[atomicAdd(&s_nlist, 1)] = tt;  // order irrelevant: counts go by tile
-      } else {
-        tcnt[tt] = 0;
-      }
-    }
-    __syncthreads();
-    const int nl = s_nlist;
-    for (int k = 0; k < nl; ++k) {
-      const int tt = s_list[k];
-      const int64_t t0 = static_cast<int64_t>(tt) * TILE + threadIdx.x * kPer;
-      int mine = 0;
-#pragma unroll
-      for (int u = 0; u < kPer; ++u) mine += (t0 + u < n && is_candidate(row[t0 + u], st)) ? 1 : 0;
-      int tile_total = 0;
-      block_exclusive(mine, &tile_total);
-      if (threadIdx.x == 0) {
-        tcnt[tt] = tile_total;
-        total += tile_total;
-      }
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *rowcount = total;
-}
-
 // One CTA per row d (int32 rows after the staged u8 kernel): statistics from
 // rowsums[d], then the candidates of each tile whose maximum reaches the
 // threshold; tilecount[d][*] and rowcount[d].
@@ -387,10 +292,10 @@ dd_tile_count(const int32_t *__restrict__ D, int64_t n, int ntiles, double thr,
               int64_t *__restrict__ rowcount) {
   __shared__ dd_row_stats s_st;
   const int d = blockIdx.x;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     const unsigned long long s2 = static_cast<unsigned long long>(rowsums[2 * d + 1]);
-    s_st = finish_i32(rowsums[2 * d], static_cast<unsigned __int128>(s2), n, thr);
-    stats[d] = s_st;
+    const dd_row_stats st = finish_i32(rowsums[2 * d], static_cast<unsigned __int128>(s2), n, thr);
+    if (threadIdx.x == 0) s_st = st, stats[d] = st;
   }
   __syncthreads();
   const dd_row_stats st = s_st;
@@ -401,70 +306,18 @@ dd_tile_count(const int32_t *__restrict__ D, int64_t n, int ntiles, double thr,
       tilecount + static_cast<int64_t>(d) * ntiles, rowcount + d);
 }
 
-// Running (count, mean, sum of squared deviations) of float samples, merged
-// pairwise by the parallel-variance update (Chan, Golub and LeVeque): exact
-// in real arithmetic for any split, evaluated in FP64 in a fixed order.
-struct Moments {
-  double n, mean, m2;
-};
-__device__ __forceinline__ Moments merge(const Moments &a, const Moments &b) {
-  if (a.n == 0.0) return b;
-  if (b.n == 0.0) return a;
-  const double n = a.n + b.n;
-  const double dl = b.mean - a.mean;
-  return {n, a.mean + dl * (b.n / n), a.m2 + b.m2 + dl * dl * (a.n * b.n / n)};
-}
-
-// One CTA per row d (float rows after the staged float kernel): each tile's
-// partials {K, S1 = sum (D - K), S2 = sum (D - K)^2, max} give its moments
-// (mean K + S1/n_t, m2 = S2 - S1^2/n_t, in FP64); thread t merges a
-// contiguous run of tiles in order, then the threads' moments are merged in
-// a fixed tree.  mean and the population rms sqrt(m2 / n) then give the row's
-// float threshold (the same bisection as dd_stats_f32), and the tiles whose
-// maximum reaches it are counted.
+// One CTA per row d (float rows after the float kernels): the row's
+// statistics and float threshold from its tiles' partials (row_stats_f32),
+// then the candidates of the tiles whose maximum reaches the threshold.
 template <int TILE>
-__global__ void __launch_bounds__(kTileThreads)
+__global__ void __launch_bounds__(kTileThreads, 4)  // 4 CTAs per SM: room for its FP64 state
 dd_tile_count_f32(const float *__restrict__ D, int64_t n, int ntiles, double thr,
                   const float4 *__restrict__ tilestats, dd_row_stats *__restrict__ stats,
                   int32_t *__restrict__ tilecount, int64_t *__restrict__ rowcount) {
-  __shared__ double s_m[3][kTileThreads];
-  __shared__ dd_row_stats s_st;
   const int d = blockIdx.x;
   const float4 *ts = tilestats + static_cast<int64_t>(d) * ntiles;
-  const int per = (ntiles + kTileThreads - 1) / kTileThreads;
-  Moments m = {0.0, 0.0, 0.0};
-  for (int tt = threadIdx.x * per; tt < (threadIdx.x + 1) * per && tt < ntiles; ++tt) {
-    const float4 v = ts[tt];
-    const int64_t rest = n - static_cast<int64_t>(tt) * TILE;
-    const double nt = static_cast<double>(rest < TILE ? rest : TILE);
-    const double s1 = v.y, s2 = v.z;
-    const double m2 = s2 - s1 * (s1 / nt);
-    m = merge(m, {nt, static_cast<double>(v.x) + s1 / nt, m2 > 0.0 ? m2 : 0.0});
-  }
-  s_m[0][threadIdx.x] = m.n, s_m[1][threadIdx.x] = m.mean, s_m[2][threadIdx.x] = m.m2;
-  __syncthreads();
-  for (int w = kTileThreads / 2; w > 0; w >>= 1) {
-    if (threadIdx.x < w) {
-      const Moments a = {s_m[0][threadIdx.x], s_m[1][threadIdx.x], s_m[2][threadIdx.x]};
-      const Moments b = {s_m[0][threadIdx.x + w], s_m[1][threadIdx.x + w],
-                         s_m[2][threadIdx.x + w]};
-      const Moments c = merge(a, b);
-      s_m[0][threadIdx.x] = c.n, s_m[1][threadIdx.x] = c.mean, s_m[2][threadIdx.x] = c.m2;
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    dd_row_stats st;
-    st.mean = s_m[1][0];
-    st.sigma = sqrt(s_m[2][0] / static_cast<double>(n));
-    st.any = st.sigma > 0.0;
-    st.fthr = st.any ? float_threshold(st.mean, st.sigma, thr) : INFINITY;
-    st.ithr = static_cast<int64_t>(INT32_MAX) + 1;
-    s_st = st;
-    stats[d] = st;
-  }
-  __syncthreads();
-  const dd_row_stats st = s_st;
+  const dd_row_stats st = row_stats_f32<TILE>(ts, n, ntiles, thr, __drcp_rn(static_cast<double>(n)));
+  if (threadIdx.x == 0) stats[d] = st;
   count_row_tiles<float, TILE>(
       D + static_cast<int64_t>(d) * n, n, ntiles, st, [&](int tt) { return ts[tt].w >= st.fthr; },
       tilecount + static_cast<int64_t>(d) * ntiles, rowcount + d);
@@ -479,47 +332,12 @@ dd_tile_write(const T *__restrict__ D, int64_t n, int ntiles,
               const dd_row_stats *__restrict__ stats, const int32_t *__restrict__ tilecount,
               const int64_t *__restrict__ rowcount, const int64_t *__restrict__ rowoff,
               dd_candidate *__restrict__ cands, int64_t capacity) {
-  constexpr int kPer = TILE / kTileThreads;
   const int d = blockIdx.x;
   if (rowcount[d] == 0) return;  // uniform across the CTA
-  int64_t run = rowoff[d];
+  const int64_t run = rowoff[d];
   if (run >= capacity) return;
-  const dd_row_stats st = stats[d];
-  const T *row = D + static_cast<int64_t>(d) * n;
-  const int32_t *tcnt = tilecount + static_cast<int64_t>(d) * ntiles;
-  __shared__ int s_cnt[kTileList];
-  for (int base = 0; base < ntiles && run < capacity; base += kTileList) {
-    __syncthreads();  // s_cnt free from the previous round
-    for (int k = threadIdx.x; k < kTileList && base + k < ntiles; k += kTileThreads)
-      s_cnt[k] = tcnt[base + k];
-    __syncthreads();
-    const int lim = ntiles - base < kTileList ? ntiles - base : kTileList;
-    for (int k = 0; k < lim && run < capacity; ++k) {
-      if (s_cnt[k] == 0) continue;  // same in every thread
-      const int64_t t0 = static_cast<int64_t>(base + k) * TILE + threadIdx.x * kPer;
-      unsigned mask = 0;
-#pragma unroll
-      for (int u = 0; u < kPer; ++u)
-        if (t0 + u < n && is_candidate(row[t0 + u], st)) mask |= 1u << u;
-      int tile_total = 0;
-      int64_t idx = run + block_exclusive(__popc(mask), &tile_total);
-      while (mask) {
-        const int u = __ffs(mask) - 1;
-        mask &= mask - 1;
-        if (idx < capacity) {
-          const double v = static_cast<double>(row[t0 + u]);
-          dd_candidate cd;
-          cd.dm_idx = d;
-          cd.t = static_cast<int32_t>(t0 + u);
-          cd.value = static_cast<float>(v);
-          cd.snr = static_cast<float>(snr_of(v, st.mean, st.sigma));
-          cands[idx] = cd;
-        }
-        ++idx;
-      }
-      run += tile_total;
-    }
-  }
+  write_row_tiles<T, TILE>(D + static_cast<int64_t>(d) * n, n, ntiles, stats[d],
+                           tilecount + static_cast<int64_t>(d) * ntiles, run, d, cands, capacity);
 }
 
 // ---- the same for the staged 8-bit beams of a batch, in two launches ----
@@ -544,10 +362,11 @@ dd_tile_count_beams(const __grid_constant__ DetectLaunch L) {
   __shared__ dd_row_stats s_st;
   const ddk::DetectBeam &a = L.beams[beam_of_row(L, blockIdx.x)];
   const int d = blockIdx.x - a.row_begin;
-  if (threadIdx.x == 0) {
+  if (threadIdx.x < 32) {
     const unsigned long long s2 = static_cast<unsigned long long>(a.rowsums[2 * d + 1]);
-    s_st = finish_i32(a.rowsums[2 * d], static_cast<unsigned __int128>(s2), a.n, L.thr);
-    a.stats[d] = s_st;
+    const dd_row_stats st =
+        finish_i32(a.rowsums[2 * d], static_cast<unsigned __int128>(s2), a.n, L.thr);
+    if (threadIdx.x == 0) s_st = st, a.stats[d] = st;
   }
   __syncthreads();
   const dd_row_stats st = s_st;
@@ -564,51 +383,16 @@ dd_tile_count_beams(const __grid_constant__ DetectLaunch L) {
 // the CTA of a beam's last row stores the beam's total.
 __global__ void __launch_bounds__(kTileThreads)
 dd_tile_write_beams(const __grid_constant__ DetectLaunch L) {
-  __shared__ long long s_part[kTileThreads / 32];
   const ddk::DetectBeam &a = L.beams[beam_of_row(L, blockIdx.x)];
   const int d = blockIdx.x - a.row_begin;
-  long long before = 0;
-  for (int r = threadIdx.x; r < d; r += kTileThreads) before += a.rowcount[r];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) before += __shfl_xor_sync(0xffffffffu, before, o);
-  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = before;
-  __syncthreads();
-  before = 0;
-#pragma unroll
-  for (int w = 0; w < kTileThreads / 32; ++w) before += s_part[w];
+  const int64_t before = rows_before(a.rowcount, d);
   const int64_t mine = a.rowcount[d];
   if (d == a.ndm - 1 && threadIdx.x == 0) *a.total = before + mine;
   if (mine == 0 || before >= a.capacity) return;  // uniform across the CTA
-  const dd_row_stats st = a.stats[d];
-  const int32_t *row = a.D + static_cast<int64_t>(d) * a.n;
-  const int32_t *tcnt = a.tilecount + static_cast<int64_t>(d) * a.ntiles;
-  constexpr int kPer = ddk::kTileSamples / kTileThreads;
-  int64_t run = before;
-  for (int tt = 0; tt < a.ntiles && run < a.capacity; ++tt) {
-    if (tcnt[tt] == 0) continue;  // same in every thread
-    const int64_t t0 = static_cast<int64_t>(tt) * ddk::kTileSamples + threadIdx.x * kPer;
-    unsigned mask = 0;
-#pragma unroll
-    for (int u = 0; u < kPer; ++u)
-      if (t0 + u < a.n && is_candidate(row[t0 + u], st)) mask |= 1u << u;
-    int tile_total = 0;
-    int64_t idx = run + block_exclusive(__popc(mask), &tile_total);
-    while (mask) {
-      const int u = __ffs(mask) - 1;
-      mask &= mask - 1;
-      if (idx < a.capacity) {
-        const double v = static_cast<double>(row[t0 + u]);
-        dd_candidate cd;
-        cd.dm_idx = d;
-        cd.t = static_cast<int32_t>(t0 + u);
-        cd.value = static_cast<float>(v);
-        cd.snr = static_cast<float>(snr_of(v, st.mean, st.sigma));
-        a.cands[idx] = cd;
-      }
-      ++idx;
-    }
-    run += tile_total;
-  }
+  write_row_tiles<int32_t, ddk::kTileSamples>(a.D + static_cast<int64_t>(d) * a.n, a.n, a.ntiles,
+                                              a.stats[d],
+                                              a.tilecount + static_cast<int64_t>(d) * a.ntiles,
+                                              before, d, a.cands, a.capacity);
 }
 
 }  // namespace

@@ -72,14 +72,17 @@ struct dd_plan {
 
   SharedTable delays_store;       // device delay table (shared by like plans)
   int32_t *d_delays = nullptr;    // [nchan][ndm], aliases delays_store
-  int32_t *d_error = nullptr;     // sticky device status word (0 = ok)
+  // sticky device status word (0 = ok); it lies in d_total's allocation
+  // (word 2), so that one 16-byte copy brings a call's total and status back
+  int32_t *d_error = nullptr;
 
   // detection workspace
   dd_row_stats *d_stats = nullptr;  // [ndm]
   int64_t *d_counts = nullptr;      // [ndm * nchunks] per-chunk candidate counts
   int64_t *d_offsets = nullptr;     // [ndm * nchunks] exclusive prefix of d_counts
-  int64_t *d_total = nullptr;       // [1]
-  int64_t *h_total = nullptr;       // pinned [1]
+  int64_t *d_total = nullptr;       // [2]: candidate total, then the status word d_error
+  int64_t *h_total = nullptr;       // pinned [2]: the copy of d_total[0..1]
+  int64_t *h_total_dev = nullptr;   // device address of h_total (mapped pinned memory)
   size_t chunk_cap = 0;             // entries allocated in d_counts / d_offsets
   std::vector<double> h_mean, h_sigma;
   bool stats_valid = false;
@@ -109,6 +112,12 @@ struct dd_plan {
   uint64_t wait_timeout_ns = 2000000000ull;  // bound on every device-side wait
   int32_t debug_skip_copies = 0;    // fault injection: staged kernel queues no copies
 
+  // one-launch path for small float beams (dd_run): arrivals counter of its
+  // grid barriers; each launch adds its CTAs' arrivals to `arrivals_base`
+  unsigned long long *d_arrivals = nullptr;
+  uint64_t arrivals_base = 0;
+  int32_t coop = 0;  // the device supports cooperative launches
+
   int64_t launches = 0;
   uint64_t ws_gen = 0;  // bumped whenever a workspace buffer is reallocated
 };
@@ -137,6 +146,9 @@ inline int elem_size(int32_t dtype) { return dtype == DD_U8 ? 1 : (dtype == DD_F
 int launch_dedisperse_direct(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out,
                              void *out, int64_t out_pitch, float4 *tilestats, cudaStream_t stream,
                              cudaError_t *err);
+// DM trials per thread of the plain-load kernel for this output length (16,
+// or 4 when 16 would leave fewer than two CTAs per SM).
+int direct_trials_per_thread(const dd_plan *p, int64_t nsamp_out);
 // Staged quad kernel (u8): needs the plan's quad tables, a 16-byte aligned
 // block, a pitch that is a multiple of 16 bytes and at most 65535 time tiles.
 bool quad_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
@@ -224,5 +236,20 @@ int launch_tiled_detect_beams(const DetectBeam *beams, int nbeams, float nsigma,
 int launch_tiled_detect_f32(dd_plan *p, const void *out, int64_t nsamp_out, float nsigma,
                             dd_candidate *cands, int64_t capacity, cudaStream_t stream,
                             cudaError_t *err);
+
+// One-launch dd_run for small float beams that the staged float kernel does
+// not take: the plain-load kernel's sums and per-tile partials, the row
+// statistics, counts and candidates of launch_tiled_detect_f32, in one
+// cooperative launch with two grid barriers (bounded waits).  The results
+// equal those of launch_dedisperse_direct + launch_tiled_detect_f32 bit for
+// bit.  The kernel writes the candidate total to the plan's pinned
+// h_total[0] (and d_total[0]) once every CTA got past both barriers; a wait
+// that ran out records the plan's status word and leaves h_total[0] as the
+// host set it.
+constexpr int64_t kSmallMaxOutputs = int64_t(1) << 22;  // ndm * nsamp_out
+bool small_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
+int launch_run_small(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out, void *out,
+                     float nsigma, dd_candidate *cands, int64_t capacity, cudaStream_t stream,
+                     cudaError_t *err);
 
 }  // namespace ddk
