@@ -446,7 +446,11 @@ __device__ __forceinline__ bool acc_item(const AccArgs &g) {
 // warp role runs the chunk pipeline below from a clean state (mbarriers
 // re-initialised, every named-barrier phase of the previous item complete);
 // tensor memory is allocated once per CTA.
-template <int CA>
+// W: the tile width (trials per accumulating thread) of every beam of the
+// launch, or 0 for launches of mixed widths, which pick each item's width at
+// run time (a kernel that holds all three accumulating loops needs more
+// registers than one that holds one).
+template <int CA, int W>
 __global__ void __launch_bounds__(kThreads, 1)
 dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
   // staging depth: copies queued CA chunks ahead, kRaw raw window buffers,
@@ -590,7 +594,9 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
       // the accumulating role for this beam's tile width
       const AccArgs args{a,    smem, bar0,    rec_off, rec_bytes, kRec, prow_off, prow_bytes,
                          tmem_base, warp, lane, dg, my_pair, tile, ttile, t_cta};
-      if (a.nd_thr == kNdThr)
+      if constexpr (W != 0)
+        aborted = acc_item<W>(args);
+      else if (a.nd_thr == kNdThr)
         aborted = acc_item<kNdThr>(args);
       else if (a.nd_thr == kNdThr / 2)
         aborted = acc_item<kNdThr / 2>(args);
@@ -623,11 +629,18 @@ dd_dedisperse_quad_u8(const __grid_constant__ QuadLaunch L) {
   if (warp == 0) tmem_dealloc(tmem_base, kTmemCols);
 }
 
-// The kernel at staging depth copy_ahead (every tile width).
+// The kernel at staging depth copy_ahead for tile width w (0: mixed).
+template <int W>
 auto pick_depth(int copy_ahead) {
-  return copy_ahead == 1   ? dd_dedisperse_quad_u8<1>
-         : copy_ahead == 3 ? dd_dedisperse_quad_u8<3>
-                           : dd_dedisperse_quad_u8<2>;
+  return copy_ahead == 1   ? dd_dedisperse_quad_u8<1, W>
+         : copy_ahead == 3 ? dd_dedisperse_quad_u8<3, W>
+                           : dd_dedisperse_quad_u8<2, W>;
+}
+auto pick_kernel(int copy_ahead, int w) {
+  return w == kNdThr       ? pick_depth<kNdThr>(copy_ahead)
+         : w == kNdThr / 2 ? pick_depth<kNdThr / 2>(copy_ahead)
+         : w == kNdThr / 4 ? pick_depth<kNdThr / 4>(copy_ahead)
+                           : pick_depth<0>(copy_ahead);
 }
 
 }  // namespace
@@ -665,14 +678,16 @@ int launch_quad_beams(const Beam *beams, int nbeams, int nd_thr, int copy_ahead,
     *err = cudaErrorInvalidValue;
     return -1;
   }
+  int width = beams[0].nd_thr;  // one width for every beam, else 0
   for (int i = 0; i < nbeams; ++i) {
     const int w = beams[i].nd_thr;
     if (w != kNdThr && w != kNdThr / 2 && w != kNdThr / 4) {
       *err = cudaErrorInvalidValue;
       return -1;
     }
+    if (w != width) width = 0;
   }
-  auto kern = pick_depth(copy_ahead);
+  auto kern = pick_kernel(copy_ahead, width);
   *err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   int per_sm = 0;
   if (*err == cudaSuccess)
