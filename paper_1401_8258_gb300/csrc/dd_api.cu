@@ -338,6 +338,49 @@ int launch_groups(dd_plan *const *plans, const std::vector<std::vector<int>> &gr
   return DD_OK;
 }
 
+// Staged float beams idx (plans[idx[k]]) in shared persistent launches of
+// the float kernel: one per input dtype and tile width and per ddo::kMaxBeams
+// beams, beams with the most work first (the queue's tail then holds the
+// cheap items); descriptors made by `beam_of(i)`.  Queue head and status word
+// as for launch_groups.  Each item's sums do not depend on the launch it is
+// in, so the results equal one launch per beam.
+template <typename BeamOf>
+int launch_octet_groups(dd_plan *const *plans, std::vector<int> idx, BeamOf beam_of,
+                        unsigned long long *next_item, int32_t *status, cudaStream_t s) {
+  auto work = [&](int i) {
+    const ddo::Tables &t = plans[i]->octet->tables;
+    return static_cast<double>(plans[i]->nchan) * t.ntiles;  // per time tile
+  };
+  std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+    const ddo::Beam bx = beam_of(x), by = beam_of(y);
+    return work(x) * bx.ntiles_t > work(y) * by.ntiles_t;
+  });
+  std::vector<char> done(idx.size(), 0);
+  for (size_t a = 0; a < idx.size(); ++a) {
+    if (done[a]) continue;
+    dd_plan *p0 = plans[idx[a]];
+    const int32_t dtype = p0->dtype;
+    const int nd = p0->octet->tables.nd_thr;
+    std::vector<ddo::Beam> beams;
+    int smem = 0;
+    for (size_t b = a; b < idx.size() && beams.size() < static_cast<size_t>(ddo::kMaxBeams); ++b) {
+      dd_plan *p = plans[idx[b]];
+      if (done[b] || p->dtype != dtype || p->octet->tables.nd_thr != nd) continue;
+      beams.push_back(beam_of(idx[b]));
+      smem = std::max(smem, static_cast<int>(p->octet->tables.smem_bytes));
+      done[b] = 1;
+    }
+    cudaError_t err = cudaSuccess;
+    const int nl = ddk::launch_octet_beams(
+        beams.data(), static_cast<int>(beams.size()), dtype, nd, smem, p0->sm_count,
+        next_item ? next_item : p0->d_next_item, status ? status : p0->d_error,
+        p0->wait_timeout_ns, p0->debug_skip_copies, s, &err);
+    if (nl < 0) return cuda_status(err);
+    p0->launches += nl;  // counted on the group's first plan
+  }
+  return DD_OK;
+}
+
 // Plan-time tables of the staged kernels: the widest width whose delay
 // patterns fit; none if no width fits (plain-load kernel).
 int setup_quad(dd_plan *p) {
@@ -630,17 +673,30 @@ int execute_plans_pitched(dd_plan *const *plans, int n, const void *const *block
   DeviceScope scope(plans[0]->device);
   if (!scope.ok()) return DD_ERR_CUDA;
   const cudaStream_t s = static_cast<cudaStream_t>(stream);
-  // staged u8 work in shared launches, in the given order; the rest alone
-  std::vector<int> staged;
+  // staged u8 work in shared launches, in the given order; staged float work
+  // in shared launches of the float kernel; the rest alone
+  std::vector<int> staged, floats;
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
     if (p->path == 0 && ddk::quad_supported(p, block[i], pitch_elems[i], nout[i])) {
       staged.push_back(i);
+    } else if (p->path == 0 && ddk::octet_supported(p, block[i], pitch_elems[i], nout[i])) {
+      floats.push_back(i);
     } else {
       const int st =
           dd_execute_pitched(p, block[i], nsamp_in[i], pitch_elems[i], out[i], out_pitch[i], stream);
       if (st != DD_OK) return st;
     }
+  }
+  if (!floats.empty()) {
+    const int st = launch_octet_groups(
+        plans, floats,
+        [&](int i) {
+          return ddk::octet_beam(plans[i], block[i], pitch_elems[i], nout[i], out[i], out_pitch[i],
+                                 nullptr);
+        },
+        nullptr, nullptr, s);
+    if (st != DD_OK) return st;
   }
   if (staged.empty()) return DD_OK;
   return launch_groups(
@@ -806,8 +862,8 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
   cudaError_t err = cudaSuccess;
   // staged u8 beams in shared launches (fused statistics), staged float
   // beams with per-tile statistics, the rest through their own kernels
-  std::vector<int> staged;
-  std::vector<char> is_staged(n, 0);  // 1: staged u8 (fused), 2: staged float (fused)
+  std::vector<int> staged, floats;
+  std::vector<char> is_staged(n, 0);  // 1: staged u8 (fused), 2: float (fused)
   for (int i = 0; i < n; ++i) {
     dd_plan *p = plans[i];
     p->stats_valid = false;
@@ -819,23 +875,35 @@ int queue_beams(dd_plan *const *plans, int n, int device, int sm_count,
       staged.push_back(i);
       is_staged[i] = 1;
     } else if (p->dtype != DD_U8) {
-      // float kernels with per-tile statistics, as dd_run
+      // float kernels with per-tile statistics, as dd_run: the staged float
+      // beams together below, the others through the plain-load kernel
       const int st = ensure_tile_workspace(
           p, static_cast<size_t>(ddk::octet_tiles(nout[i])) * p->ndm, true);
       if (st != DD_OK) return st;
-      const int nl =
-          p->path == 0 && ddk::octet_supported(p, block[i], pitch_elems[i], nout[i])
-              ? ddk::launch_dedisperse_octet(p, block[i], pitch_elems[i], nout[i], out[i],
-                                             nout[i], p->d_tilestats, s, &err)
-              : ddk::launch_dedisperse_direct(p, block[i], pitch_elems[i], nout[i], out[i],
-                                              nout[i], p->d_tilestats, s, &err);
-      if (nl < 0) return cuda_status(err);
-      p->launches += nl;
+      if (p->path == 0 && ddk::octet_supported(p, block[i], pitch_elems[i], nout[i])) {
+        floats.push_back(i);
+      } else {
+        const int nl = ddk::launch_dedisperse_direct(p, block[i], pitch_elems[i], nout[i], out[i],
+                                                     nout[i], p->d_tilestats, s, &err);
+        if (nl < 0) return cuda_status(err);
+        p->launches += nl;
+      }
       is_staged[i] = 2;
     } else {
       const int st = dd_execute(p, block[i], nsamp_in[i], pitch_elems[i], out[i], stream);
       if (st != DD_OK) return st;
     }
+  }
+  if (!floats.empty()) {
+    const int st = launch_octet_groups(
+        plans, floats,
+        [&](int i) {
+          dd_plan *p = plans[i];
+          return ddk::octet_beam(p, block[i], pitch_elems[i], nout[i], out[i], nout[i],
+                                 p->d_tilestats);
+        },
+        next_item, status, s);
+    if (st != DD_OK) return st;
   }
   // costliest beams first (a work item costs about nchan): the queue's tail
   // then holds the cheap items

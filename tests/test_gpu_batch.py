@@ -263,3 +263,40 @@ def test_batch_of_mixed_widths_and_depths_is_one_launch_and_two_detection_launch
     assert launches <= 3, launches
     for p in plans:
         p.close()
+
+
+def test_batch_of_float_beams_shares_float_kernel_launches():
+    """Staged float beams of one input dtype and tile width share one
+    persistent launch of the float kernel (its queue holds every beam's
+    items); the results equal each beam alone bit for bit."""
+    base = synth.workload("lband_f32")
+    workloads = []
+    for nchan, ndm, dtype in [(512, 96, "f32"), (256, 200, "f32"), (384, 64, "f32"),
+                              (256, 128, "f16"), (512, 80, "f16")]:
+        wl = synth.scaled(base, nchan=nchan, ndm=ndm)
+        wl.chan_width_mhz = base.chan_width_mhz
+        wl.dtype = dtype
+        wl.nsamp = (maxshift(wl) + 5000 + 15) // 16 * 16  # whole 16-byte rows: staged
+        workloads.append(wl)
+    blocks, _ = make_beams(workloads, seed=77)
+    dblocks = [torch.from_numpy(np.ascontiguousarray(b)).to(DEV) for b in blocks]
+    plans = [plan_of(wl) for wl in workloads]
+    infos = [dd._native.dd_plan_kernel_info(p.handle, b, b.stride(0)) for p, b in zip(plans, dblocks)]
+    assert all(i["staged"] for i in infos), infos
+    groups = {(wl.dtype, i["dms_per_cta"]) for wl, i in zip(workloads, infos)}
+    alone = [run_alone(p, b, 4.0, 1 << 16) for p, b in zip(plans, dblocks)]
+    with dd.Batch(plans) as batch:
+        before = sum(p.launch_count() for p in plans)
+        outs, cands, totals = batch.run(dblocks, 4.0, capacity=1 << 16)
+        launches = sum(p.launch_count() for p in plans) - before
+    # one dedispersion launch per (dtype, width) group; detection per float
+    # beam: row statistics and counts, scan, write
+    assert launches == len(groups) + 3 * len(plans), (launches, groups)
+    for i, p in enumerate(plans):
+        out_a, c_a, t_a, m_a, s_a = alone[i]
+        assert totals[i] == t_a and torch.equal(outs[i], out_a), i
+        assert np.array_equal(cands[i], c_a), i
+        mean, sigma = p.stats()
+        assert np.array_equal(mean, m_a) and np.array_equal(sigma, s_a), i
+    for p in plans:
+        p.close()
