@@ -123,19 +123,20 @@ __device__ __forceinline__ int block_exclusive(int v, int *total) {
 // admits (their largest value passes the threshold; no other tile can hold a
 // candidate) are read and counted into tcnt[tt], the others get 0; the row
 // total goes to *rowcount.  Called by the whole CTA after st is final.
-template <typename T, int TILE, typename Reaches, typename Ld = PlainLd>
+// LIST: tiles examined per round (shared-memory list size).
+template <typename T, int TILE, typename Reaches, typename Ld = PlainLd, int LIST = kTileList>
 __device__ __forceinline__ void count_row_tiles(const T *row, int64_t n, int ntiles, const dd_row_stats &st,
                                 Reaches reaches, int32_t *tcnt, int64_t *rowcount,
                                 Ld ld = Ld()) {
   constexpr int kPer = TILE / kTileThreads;  // consecutive samples per thread
   static_assert(TILE % kTileThreads == 0, "whole samples per thread");
-  __shared__ int s_list[kTileList];
+  __shared__ int s_list[LIST];
   __shared__ int s_nlist;
   int64_t total = 0;  // thread 0
-  for (int base = 0; base < ntiles; base += kTileList) {
+  for (int base = 0; base < ntiles; base += LIST) {
     if (threadIdx.x == 0) s_nlist = 0;
     __syncthreads();
-    for (int k = threadIdx.x; k < kTileList && base + k < ntiles; k += kTileThreads) {
+    for (int k = threadIdx.x; k < LIST && base + k < ntiles; k += kTileThreads) {
       const int tt = base + k;
       if (st.any && reaches(tt)) {
         s_list[atomicAdd(&s_nlist, 1)] = tt;  // order irrelevant: counts go by tile
@@ -169,19 +170,19 @@ __device__ __forceinline__ void count_row_tiles(const T *row, int64_t n, int nti
 // only tiles with a non-zero count in tcnt are read.  Whole CTA.
 // pre_tile >= 0: the caller already computed, for tile pre_tile, the snr of
 // this thread's candidates (pre_snr[u] for sample u of the thread's kPer).
-template <typename T, int TILE, typename Ld = PlainLd>
+template <typename T, int TILE, typename Ld = PlainLd, int LIST = kTileList>
 __device__ __forceinline__ void write_row_tiles(const T *row, int64_t n, int ntiles, const dd_row_stats &st,
                                 const int32_t *tcnt, int64_t run, int32_t d,
                                 dd_candidate *cands, int64_t capacity, Ld ld = Ld(),
                                 int pre_tile = -1, const float *pre_snr = nullptr) {
   constexpr int kPer = TILE / kTileThreads;
-  __shared__ int s_cnt[kTileList];
-  for (int base = 0; base < ntiles && run < capacity; base += kTileList) {
+  __shared__ int s_cnt[LIST];
+  for (int base = 0; base < ntiles && run < capacity; base += LIST) {
     __syncthreads();  // s_cnt free from the previous round
-    for (int k = threadIdx.x; k < kTileList && base + k < ntiles; k += kTileThreads)
+    for (int k = threadIdx.x; k < LIST && base + k < ntiles; k += kTileThreads)
       s_cnt[k] = ld(tcnt + base + k);
     __syncthreads();
-    const int lim = ntiles - base < kTileList ? ntiles - base : kTileList;
+    const int lim = ntiles - base < LIST ? ntiles - base : LIST;
     // the tiles with candidates, 32 at a time in order (every warp finds the
     // same ones, so the loop below is uniform across the CTA)
     for (int k0 = 0; k0 < lim && run < capacity; k0 += 32) {

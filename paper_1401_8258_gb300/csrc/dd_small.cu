@@ -113,22 +113,26 @@ __device__ __forceinline__ bool grid_wait(const SmallArgs &a, unsigned long long
 }
 
 // Phase 1 of the 4-trial variant on 16-byte aligned rows, with the input
-// staged in shared memory: per delay stage of kDelayChans channels, the
-// delays of the item's trials and each channel's smallest one (wmin); then
-// sub-stages of kSub channels, each channel's window -- kWin samples from
-// t0 + wmin rounded down to a 16-byte unit (t0 the tile's first output) --
-// copied with cp.async (16-byte units, all in flight at once; units past
-// the row's last needed unit are zero-filled), after which the sums read the
-// windows: the same values added in the same channel order as direct_sums,
-// so the same results.  A stage in which some channel's delays over the
-// trials spread too far for a window, or rows that are not 16-byte
-// aligned, are summed from global memory instead (direct_sums' loop).
-constexpr int kWin = 384;  // samples per channel window
-// channels per sub-stage: the windows of one sub-stage fill 48 KB
-template <typename T>
-__host__ __device__ constexpr int sub_chans() { return 32 * 4 / static_cast<int>(sizeof(T)); }
-template <typename T>
-__host__ __device__ constexpr int win_bytes() { return sub_chans<T>() * kWin * static_cast<int>(sizeof(T)); }
+// staged in shared memory: per delay stage of kDelayChans channels,
+// the delays of the item's trials and each channel's smallest one (wmin);
+// then sub-stages of nsub channels, each channel's window -- kWin4 samples
+// from t0 + wmin rounded down to a 16-byte unit (t0 the tile's first
+// output) -- copied with cp.async (16-byte units, all in flight at once;
+// units past the row's last needed unit are zero-filled), after which the
+// sums read the windows through a per-channel table of the trials' offsets:
+// the same values added in the same channel order as direct_sums, so the
+// same results.  A stage in which some channel's delays over the trials
+// spread too far for a window, or rows that are not 16-byte aligned, are
+// summed from global memory instead (direct_sums' loop).  The windows are
+// 384 samples long, in sub-stages that fill 48 KB (32 f32 or 64 f16
+// channels).  (The offsets are kept in groups of four trials, so the code
+// takes any multiple of four.)
+
+// Tile lists of phases 2 and 3 (rounds of this many tiles; small, to keep
+// the kernel's static shared memory low).
+constexpr int kRowList = 64, kL2List = 256;
+constexpr int kWin4 = 384;  // samples per channel window, 4-trial variant
+constexpr int kDyn4 = 48 * 1024;  // its window bytes (32 f32 / 64 f16 channels)
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void *src, uint32_t src_bytes) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(src_bytes)
@@ -157,20 +161,23 @@ struct RowLd {
   }
 };
 
-template <typename T>
+template <typename T, int NDMS>
 __device__ __forceinline__ void staged_sums(const SmallArgs &a, int d0, int64_t t0, bool live,
-                                            float (&acc)[4], T *s_win) {
-  constexpr int NDMS = 4;
+                                            float (&acc)[NDMS], T *s_win) {
+  static_assert(NDMS % 4 == 0, "offsets in groups of four trials");
+  constexpr int kQ = NDMS / 4;
   constexpr int kUnit = 16 / static_cast<int>(sizeof(T));  // samples per 16-byte unit
-  constexpr int kUnits = kWin / kUnit;                     // units per window
-  constexpr int kSub = sub_chans<T>();
-  static_assert(kWin % kUnit == 0, "whole units per window");
   __shared__ int32_t s_dl[kDelayChans][NDMS];
   __shared__ int32_t s_wmin[kDelayChans];
-  __shared__ int4 s_off[kDelayChans];  // per channel: window offsets of the 4 trials, less tid
+  __shared__ int4 s_off[kDelayChans][kQ];  // per channel: window offsets of the trials, less tid
   __shared__ int s_spread_ok;
   const T *in = static_cast<const T *>(a.in);
   const int64_t nsamp_in = a.nsamp_out + a.maxshift;
+  // window geometry (compile-time, so that the copy loop's index
+  // arithmetic is shifts and multiplies)
+  constexpr int stride = kWin4, nsub = kDyn4 / (kWin4 * static_cast<int>(sizeof(T)));
+  constexpr int units = stride / kUnit;
+  static_assert(stride % kUnit == 0 && kDelayChans % nsub == 0, "window tiling");
   // the row's units that hold needed samples (within the row: the pitch is a
   // whole number of units, at least nsamp_in)
   const int64_t row_units = (nsamp_in + kUnit - 1) / kUnit;
@@ -194,12 +201,14 @@ __device__ __forceinline__ void staged_sums(const SmallArgs &a, int d0, int64_t 
       for (int j = 1; j < NDMS; ++j) lo = min(lo, s_dl[tid][j]), hi = max(hi, s_dl[tid][j]);
       const int start = static_cast<int>((t0 + lo) % kUnit);  // offset inside the first unit
       s_wmin[tid] = lo;
-      if (tid < nc && start + kDirectThreads - 1 + (hi - lo) >= kWin) s_spread_ok = 0;
+      if (tid < nc && start + kDirectThreads - 1 + (hi - lo) >= stride) s_spread_ok = 0;
       // channel tid's window starts at sample (t0 + lo) rounded down to a unit:
       // output t0 + i of trial j reads element i + start + (delay_j - lo) of it
-      const int base = (tid % kSub) * kWin + start - lo;
-      s_off[tid] = make_int4(base + s_dl[tid][0], base + s_dl[tid][1], base + s_dl[tid][2],
-                             base + s_dl[tid][3]);
+      const int base = (tid % nsub) * stride + start - lo;
+#pragma unroll
+      for (int q = 0; q < kQ; ++q)
+        s_off[tid][q] = make_int4(base + s_dl[tid][4 * q], base + s_dl[tid][4 * q + 1],
+                                  base + s_dl[tid][4 * q + 2], base + s_dl[tid][4 * q + 3]);
     }
     __syncthreads();
     if (!s_spread_ok) {  // uniform: this stage from global memory
@@ -213,28 +222,31 @@ __device__ __forceinline__ void staged_sums(const SmallArgs &a, int d0, int64_t 
       continue;
     }
     const uint32_t win0 = dddev::smem_addr(s_win);
-    for (int s0 = 0; s0 < nc; s0 += kSub) {
-      const int ns = nc - s0 < kSub ? nc - s0 : kSub;
+    for (int s0 = 0; s0 < nc; s0 += nsub) {
+      const int ns = nc - s0 < nsub ? nc - s0 : nsub;
       if (s0 > 0) __syncthreads();  // every thread is past the previous sub-stage's sums
-      for (int i = tid; i < ns * kUnits; i += kDirectThreads) {
-        const int cc = i / kUnits, u = i % kUnits;
+      for (int i = tid; i < ns * units; i += kDirectThreads) {
+        const int cc = i / units, u = i % units;
         const int64_t unit = (t0 + s_wmin[s0 + cc]) / kUnit + u;
         const T *row = in + static_cast<int64_t>(c0 + s0 + cc) * a.pitch;
         const bool ok = unit < row_units;
-        cp_async16(win0 + static_cast<uint32_t>((cc * kWin + u * kUnit) * sizeof(T)),
+        cp_async16(win0 + static_cast<uint32_t>((cc * stride + u * kUnit) * sizeof(T)),
                    ok ? row + unit * kUnit : row, ok ? 16u : 0u);
       }
       cp_async_wait_all();
       __syncthreads();
       if (live) {
         const T *wt = s_win + tid;
-#pragma unroll 8
+#pragma unroll 4
         for (int cc = 0; cc < ns; ++cc) {
-          const int4 o = s_off[s0 + cc];
-          acc[0] += DirectTraits<T>::load_shared(wt + o.x);
-          acc[1] += DirectTraits<T>::load_shared(wt + o.y);
-          acc[2] += DirectTraits<T>::load_shared(wt + o.z);
-          acc[3] += DirectTraits<T>::load_shared(wt + o.w);
+#pragma unroll
+          for (int q = 0; q < kQ; ++q) {
+            const int4 o = s_off[s0 + cc][q];
+            acc[4 * q] += DirectTraits<T>::load_shared(wt + o.x);
+            acc[4 * q + 1] += DirectTraits<T>::load_shared(wt + o.y);
+            acc[4 * q + 2] += DirectTraits<T>::load_shared(wt + o.z);
+            acc[4 * q + 3] += DirectTraits<T>::load_shared(wt + o.w);
+          }
         }
       }
     }
@@ -243,10 +255,10 @@ __device__ __forceinline__ void staged_sums(const SmallArgs &a, int d0, int64_t 
 
 // Three CTAs per SM: 448 items (the 64 x 8192 single beam) run co-resident.
 template <typename T, int NDMS>
-__global__ void __launch_bounds__(kDirectThreads, 3) dd_run_small(const __grid_constant__ SmallArgs a) {
-  __shared__ int32_t s_delay[kDelayChans][NDMS];
+__global__ void __launch_bounds__(kDirectThreads, 3)
+dd_run_small(const __grid_constant__ SmallArgs a) {
   __shared__ PartialScratch<NDMS> s_part;
-  extern __shared__ __align__(16) unsigned char s_dyn[];  // NDMS == 4: windows, then a row
+  extern __shared__ __align__(16) unsigned char s_dyn[];  // NDMS 4: windows, then a row
   const int64_t n = a.nsamp_out;
   const int ntiles = a.ntiles;
   // 1/n for the row statistics, its FP64 division under phase 1
@@ -260,12 +272,14 @@ __global__ void __launch_bounds__(kDirectThreads, 3) dd_run_small(const __grid_c
     const int64_t t = static_cast<int64_t>(tile) * kDirectThreads + threadIdx.x;
     const bool live = t < n;
     float acc[NDMS];
-    if constexpr (NDMS == 4)
-      staged_sums<T>(a, d0, static_cast<int64_t>(tile) * kDirectThreads, live, acc,
-                     reinterpret_cast<T *>(s_dyn));
-    else
+    if constexpr (NDMS <= 8) {
+      staged_sums<T, NDMS>(a, d0, static_cast<int64_t>(tile) * kDirectThreads, live, acc,
+                           reinterpret_cast<T *>(s_dyn));
+    } else {
+      __shared__ int32_t s_delay[kDelayChans][NDMS];
       direct_sums<T, NDMS>(static_cast<const T *>(a.in), a.pitch, a.delays, a.nchan, a.ndm, d0,
                            t, live, acc, s_delay);
+    }
     if (live) {
 #pragma unroll
       for (int j = 0; j < NDMS; ++j)
@@ -308,9 +322,9 @@ __global__ void __launch_bounds__(kDirectThreads, 3) dd_run_small(const __grid_c
     __syncthreads();
     s_row += first % 4;  // the row's element 0
     if (threadIdx.x == 0) a.stats[d] = st;
-    count_row_tiles<float, kDirectThreads>(s_row, n, ntiles, st,
-                                           [&](int tt) { return s_ts[tt].w >= st.fthr; }, s_tc,
-                                           a.rowcount + d, rl);
+    const auto reaches = [&](int tt) { return s_ts[tt].w >= st.fthr; };
+    count_row_tiles<float, kDirectThreads, decltype(reaches), RowLd, kRowList>(
+        s_row, n, ntiles, st, reaches, s_tc, a.rowcount + d, rl);
     // the snr of this thread's candidate in the row's first tile with any:
     // its FP64 division runs while the CTA waits at barrier 2
     __syncthreads();  // s_tc complete
@@ -333,8 +347,9 @@ __global__ void __launch_bounds__(kDirectThreads, 3) dd_run_small(const __grid_c
     const int64_t mine = rl(a.rowcount + d);
     if (d == a.ndm - 1 && threadIdx.x == 0) *a.total = before + mine;
     if (mine > 0 && before < a.capacity)  // uniform across the CTA
-      write_row_tiles<float, kDirectThreads>(s_row, n, ntiles, st, s_tc, before, d, a.cands,
-                                             a.capacity, rl, pre_tile, &pre_snr);
+      write_row_tiles<float, kDirectThreads, RowLd, kRowList>(s_row, n, ntiles, st, s_tc, before,
+                                                             d, a.cands, a.capacity, rl,
+                                                             pre_tile, &pre_snr);
   } else {
     // phase 2: row statistics and per-tile counts
     const L2Ld ld;
@@ -342,9 +357,9 @@ __global__ void __launch_bounds__(kDirectThreads, 3) dd_run_small(const __grid_c
       const float4 *ts = a.tilestats + static_cast<int64_t>(d) * ntiles;
       const dd_row_stats st = row_stats_f32<kDirectThreads>(ts, n, ntiles, a.thr, rn, ld);
       if (threadIdx.x == 0) a.stats[d] = st;
-      count_row_tiles<float, kDirectThreads>(
-          a.out + static_cast<int64_t>(d) * n, n, ntiles, st,
-          [&](int tt) { return ld(ts + tt).w >= st.fthr; },
+      const auto reaches = [&](int tt) { return ld(ts + tt).w >= st.fthr; };
+      count_row_tiles<float, kDirectThreads, decltype(reaches), L2Ld, kL2List>(
+          a.out + static_cast<int64_t>(d) * n, n, ntiles, st, reaches,
           a.tilecount + static_cast<int64_t>(d) * ntiles, a.rowcount + d, ld);
     }
     grid_arrive(a.arrivals);
@@ -358,9 +373,9 @@ __global__ void __launch_bounds__(kDirectThreads, 3) dd_run_small(const __grid_c
       if (mine == 0 || before >= a.capacity) continue;  // uniform across the CTA
       // stats[d] and the tile counts were written by this CTA in phase 2
       const dd_row_stats st = a.stats[d];
-      write_row_tiles<float, kDirectThreads>(a.out + static_cast<int64_t>(d) * n, n, ntiles, st,
-                                             a.tilecount + static_cast<int64_t>(d) * ntiles,
-                                             before, d, a.cands, a.capacity, ld);
+      write_row_tiles<float, kDirectThreads, L2Ld, kL2List>(
+          a.out + static_cast<int64_t>(d) * n, n, ntiles, st,
+          a.tilecount + static_cast<int64_t>(d) * ntiles, before, d, a.cands, a.capacity, ld);
     }
   }
   // the last row worker to get here stores the total on the host: every
@@ -380,20 +395,16 @@ __global__ void __launch_bounds__(kDirectThreads, 3) dd_run_small(const __grid_c
 
 using SmallKernel = void (*)(SmallArgs);
 
-// Kernel variant for (input dtype, trials per thread).
+// Kernel variant for (input dtype, trials per thread: 4 or 16).
 SmallKernel small_kernel(int32_t dtype, int ndms) {
   if (dtype == DD_F16) return ndms == 16 ? dd_run_small<uint16_t, 16> : dd_run_small<uint16_t, 4>;
   return ndms == 16 ? dd_run_small<float, 16> : dd_run_small<float, 4>;
 }
 
-// Dynamic shared memory of each variant: the 4-trial one stages input
-// windows in phase 1 and a row (outputs, tile partials and counts) in
-// phases 2 and 3.
-constexpr int kSmallDynBytes = win_bytes<float>();
-static_assert(win_bytes<uint16_t>() <= kSmallDynBytes, "windows fit");
-static_assert(kDelayChans % sub_chans<float>() == 0 && kDelayChans % sub_chans<uint16_t>() == 0,
-              "whole sub-stages per delay stage");
-int small_dynamic_smem(int32_t /*dtype*/, int ndms) { return ndms == 4 ? kSmallDynBytes : 0; }
+// Dynamic shared memory: the 4-trial variant stages its windows in kDyn4
+// bytes, then a row (outputs, tile partials and counts) in phases 2 and 3;
+// the 16-trial one none.
+static_assert(kDelayChans * kWin4 * 2 <= kDyn4 && 32 * kWin4 * 4 <= kDyn4, "4-trial windows");
 
 // Co-resident CTAs per SM of each variant (queried once per process; every
 // device of the process is a GB300, the one target of this library).
@@ -404,7 +415,7 @@ int resident_per_sm(int32_t dtype, int ndms) {
     for (int f = 0; f < 2; ++f)
       for (int w = 0; w < 2; ++w) {
         const void *k = reinterpret_cast<const void *>(small_kernel(f ? DD_F16 : DD_F32, w ? 16 : 4));
-        const int dyn = small_dynamic_smem(f ? DD_F16 : DD_F32, w ? 16 : 4);
+        const int dyn = w ? 0 : kDyn4;
         int b = 0;
         if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn) !=
                 cudaSuccess ||
@@ -417,6 +428,20 @@ int resident_per_sm(int32_t dtype, int ndms) {
   return n[dtype == DD_F16 ? 1 : 0][ndms == 16 ? 1 : 0];
 }
 
+struct SmallShape {
+  int ndms;          // trials per thread
+  int dyn;           // dynamic shared memory per CTA
+  int64_t resident;  // co-resident CTAs on the device
+};
+
+// 16 trials per thread when that already gives two CTAs per SM (as the
+// plain-load kernel), else 4 with staged windows.
+SmallShape small_shape(const dd_plan *p, int64_t nsamp_out) {
+  const int ndms = ddk::direct_trials_per_thread(p, nsamp_out);
+  const int64_t resident = static_cast<int64_t>(resident_per_sm(p->dtype, ndms)) * p->sm_count;
+  return {ndms, ndms == 16 ? 0 : kDyn4, resident};
+}
+
 }  // namespace
 
 namespace ddk {
@@ -425,18 +450,18 @@ bool small_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t
   if (p->dtype == DD_U8 || p->path != 0 || !p->coop || !p->d_arrivals) return false;
   if (static_cast<int64_t>(p->ndm) * nsamp_out > kSmallMaxOutputs) return false;
   if (octet_supported(p, block, pitch, nsamp_out)) return false;
-  return resident_per_sm(p->dtype, direct_trials_per_thread(p, nsamp_out)) > 0;
+  return small_shape(p, nsamp_out).resident > 0;
 }
 
 int launch_run_small(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out, void *out,
                      float nsigma, dd_candidate *cands, int64_t capacity, cudaStream_t stream,
                      cudaError_t *err) {
-  const int ndms = direct_trials_per_thread(p, nsamp_out);
+  const SmallShape sh = small_shape(p, nsamp_out);
+  const int ndms = sh.ndms;
   const int64_t ntiles = (nsamp_out + kDirectThreads - 1) / kDirectThreads;
   const int ngroups = (p->ndm + ndms - 1) / ndms;
   const int64_t nitems = ntiles * ngroups;
-  const int64_t resident = static_cast<int64_t>(resident_per_sm(p->dtype, ndms)) * p->sm_count;
-  const int grid = static_cast<int>(nitems < resident ? nitems : resident);
+  const int grid = static_cast<int>(nitems < sh.resident ? nitems : sh.resident);
   SmallArgs a;
   a.in = block;
   a.pitch = pitch;
@@ -469,12 +494,11 @@ int launch_run_small(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp
   // 16 B, then the row in 16-byte units (up to 3 elements before it, 3 after)
   a.row_smem = (a.nworkers == p->ndm && reinterpret_cast<uintptr_t>(out) % 16 == 0 &&
                 ntiles * static_cast<int64_t>(sizeof(float4)) + (ntiles + 3) / 4 * 16 +
-                        (nsamp_out + 6) * 4 <= small_dynamic_smem(p->dtype, ndms))
+                        (nsamp_out + 6) * 4 <= sh.dyn)
                    ? 1 : 0;
   void *args[] = {&a};
   *err = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(small_kernel(p->dtype, ndms)),
-                                     dim3(grid), dim3(kDirectThreads), args,
-                                     small_dynamic_smem(p->dtype, ndms), stream);
+                                     dim3(grid), dim3(kDirectThreads), args, sh.dyn, stream);
   if (*err != cudaSuccess) return -1;
   p->arrivals_base += static_cast<uint64_t>(grid) + 2 * static_cast<uint64_t>(a.nworkers);
   return 1;
