@@ -315,6 +315,57 @@ __device__ __noinline__ void line_f32(double sy, double sty, float y0, int64_t n
   line[1] = b;
 }
 
+// One 16-sample chunk of an int32 row starting at sample t: its exact sums of
+// y, t y and y^2 added to sy, sty, syy.
+__device__ __forceinline__ void chunk_sums_i32(const int32_t (&v)[kDtChunk], int64_t t, i128 &sy,
+                                               i128 &sty, i128 &syy) {
+  long long c1 = 0, c2 = 0;  // chunk sums of y and of k y, k = 0..15
+  u128 c3 = 0;
+#pragma unroll
+  for (int k = 0; k < kDtChunk; ++k) {
+    const long long y = v[k];
+    c1 += y;
+    c2 += static_cast<long long>(k) * y;
+    c3 += static_cast<u128>(static_cast<unsigned long long>(y * y));
+  }
+  sy += c1;
+  sty += static_cast<i128>(t) * c1 + c2;
+  syy += static_cast<i128>(c3);
+}
+
+// The chunk's detrended, normalised samples z[t + k] = (v[k] - (a + b (t+k))) / s
+// for t + k < lim (the line evaluated as in the thesis: base = a + b t in
+// double, split into integer and fraction, then per sample in float).
+template <typename X>
+__device__ __forceinline__ void chunk_out(const X (&v)[kDtChunk], int64_t t, int64_t lim,
+                                          double a, double b, float bf, float inv, float *z,
+                                          bool zvec) {
+  const double base = fma(b, static_cast<double>(t), a);
+  const double hi = floor(base);
+  const float lo = static_cast<float>(base - hi);
+  float r[kDtChunk];
+#pragma unroll
+  for (int k = 0; k < kDtChunk; ++k) {
+    const float line = fmaf(bf, static_cast<float>(k), lo);
+    if constexpr (std::is_integral<X>::value) {
+      r[k] = static_cast<float>(static_cast<long long>(v[k]) - static_cast<long long>(hi)) - line;
+    } else {
+      r[k] = (v[k] - static_cast<float>(hi)) - line;
+    }
+    r[k] *= inv;
+  }
+  if (zvec && t + kDtChunk <= lim) {
+    float4 *p = reinterpret_cast<float4 *>(z + t);
+#pragma unroll
+    for (int q = 0; q < kDtChunk / 4; ++q)
+      p[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < kDtChunk; ++k)
+      if (t + k < lim) z[t + k] = r[k];
+  }
+}
+
 // Chunks of a row: the head [0, head) up to the first 16-byte boundary of the
 // row (thread 0), then whole 16-sample chunks from `head`, one per thread
 // in turn; `head` < 4.
@@ -346,18 +397,7 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
     for_chunks(n, head, [&](int64_t t, int64_t lim) {
       X v[kDtChunk];
       load16<X>(x, t, lim, v);
-      long long c1 = 0, c2 = 0;  // chunk sums of y and of k y, k = 0..15
-      u128 c3 = 0;
-#pragma unroll
-      for (int k = 0; k < kDtChunk; ++k) {
-        const long long y = v[k];
-        c1 += y;
-        c2 += static_cast<long long>(k) * y;
-        c3 += static_cast<u128>(static_cast<unsigned long long>(y * y));
-      }
-      sy += c1;
-      sty += static_cast<i128>(t) * c1 + c2;
-      syy += static_cast<i128>(c3);
+      chunk_sums_i32(v, t, sy, sty, syy);
     });
     sy = block_sum(sy, s_i);
     sty = block_sum(sty, s_i);
@@ -415,30 +455,7 @@ dd_detrend_rows(const X *in, int64_t in_pitch, int64_t n, float *out, int64_t ou
   for_chunks(n, head, [&](int64_t t, int64_t lim) {
     X v[kDtChunk];
     load16<X>(x, t, lim, v);
-    const double base = fma(b, static_cast<double>(t), a);
-    const double hi = floor(base);
-    const float lo = static_cast<float>(base - hi);
-    float r[kDtChunk];
-#pragma unroll
-    for (int k = 0; k < kDtChunk; ++k) {
-      const float line = fmaf(bf, static_cast<float>(k), lo);
-      if constexpr (std::is_integral<X>::value) {
-        r[k] = static_cast<float>(static_cast<long long>(v[k]) - static_cast<long long>(hi)) - line;
-      } else {
-        r[k] = (v[k] - static_cast<float>(hi)) - line;
-      }
-      r[k] *= inv;
-    }
-    if (zvec && t + kDtChunk <= lim) {
-      float4 *p = reinterpret_cast<float4 *>(z + t);
-#pragma unroll
-      for (int q = 0; q < kDtChunk / 4; ++q)
-        p[q] = make_float4(r[4 * q], r[4 * q + 1], r[4 * q + 2], r[4 * q + 3]);
-    } else {
-#pragma unroll
-      for (int k = 0; k < kDtChunk; ++k)
-        if (t + k < lim) z[t + k] = r[k];
-    }
+    chunk_out(v, t, lim, a, b, bf, inv, z, zvec);
   });
 }
 

@@ -109,7 +109,8 @@ def check_detrend(x, z_gpu, coef_gpu):
 
 @pytest.mark.parametrize("dtype", ["i32", "f32"])
 @pytest.mark.parametrize("ncols,slope", [(1, 0.0), (3, 1.0), (33, 0.3), (4099, 0.02),
-                                         (57723, 0.001), (20000, 5.0)])
+                                         (57723, 0.001), (20000, 5.0),
+                                         (73729, 0.01)])
 def test_detrend_matches_oracle_within_bound(dtype, ncols, slope):
     level = 130000.0 if dtype == "i32" else 3.0
     full, x = rows_of(ncols + 1, 6, ncols, dtype, pitch=ncols + (4 if ncols % 2 else 0),
