@@ -14,7 +14,12 @@
 //   2. the first min(grid, ndm) CTAs (the row workers) wait for barrier 1
 //      and take rows d: the row's mean, rms and threshold (row_stats_f32)
 //      and its per-tile candidate counts (count_row_tiles), then arrive at
-//      barrier 2 (the other CTAs are done);
+//      barrier 2 (the other CTAs are done).  When every worker has one row
+//      that fits, the row's outputs and tile partials are first copied into
+//      shared memory (the partials in their own copy group, so the
+//      statistics start while the row lands), phases 2 and 3 read them from
+//      there, and the snr divisions of the row's first candidate tile are
+//      issued before the barrier, whose wait hides their latency;
 //   3. the row workers wait for barrier 2 and write each row's candidates at
 //      the sum of the earlier rows' counts (write_row_tiles); the CTA of the
 //      last row stores the total in device memory, and the last row worker
