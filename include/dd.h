@@ -334,7 +334,7 @@ int dd_plan_set_staging_depth(dd_plan *p, int32_t copy_ahead);
 /* Fault injection for tests of the timeout path: with skip_copies != 0 the
  * staged kernel queues none of its bulk copies, so its first bounded wait
  * runs out, and dd_run's one-launch path for small float beams waits at its
- * first grid barrier for one arrival more than its grid makes, so that wait
+ * grid barrier for one arrival more than its grid makes, so that wait
  * runs out (no device fault, no hang).  0 restores normal operation. */
 int dd_plan_inject_fault(dd_plan *p, int32_t skip_copies);
 

@@ -117,6 +117,8 @@ cudaError_t alloc_result(dd_plan *p) {
   }
   if (e == cudaSuccess) e = cudaMalloc(&p->d_arrivals, sizeof(unsigned long long));
   if (e == cudaSuccess) e = cudaMemset(p->d_arrivals, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_published, sizeof(unsigned long long) * p->ndm);
+  if (e == cudaSuccess) e = cudaMemset(p->d_published, 0, sizeof(unsigned long long) * p->ndm);
   p->arrivals_base = 0;
   int coop = 0;
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, p->device);
@@ -201,6 +203,7 @@ void destroy_plan(dd_plan *p) {
   free_device(p->d_offsets);
   free_device(p->d_total);  // with the status word d_error in it
   free_device(p->d_arrivals);
+  free_device(p->d_published);
   free_device(p->d_rowsums);
   free_device(p->d_rowcount);
   free_device(p->d_rowoff);
@@ -772,8 +775,10 @@ extern "C" int dd_run(dd_plan *p, const void *block, int64_t nsamp_in, int64_t p
       err = wait_host_total(p, s);
       if (err != cudaSuccess) return cuda_status(err);
       if (p->h_total[0] < 0) {
-        // a grid wait ran out: the barrier counter starts again from zero
+        // a grid wait ran out: the barrier counter starts again from zero,
+        // and so do the launch epochs of the published row counts
         cudaMemset(p->d_arrivals, 0, sizeof(unsigned long long));
+        cudaMemset(p->d_published, 0, sizeof(unsigned long long) * p->ndm);
         p->arrivals_base = 0;
         st = take_device_status(p);
         return st != DD_OK ? st : DD_ERR_DEVICE_TIMEOUT;

@@ -113,9 +113,12 @@ struct dd_plan {
   int32_t debug_skip_copies = 0;    // fault injection: staged kernel queues no copies
 
   // one-launch path for small float beams (dd_run): arrivals counter of its
-  // grid barriers; each launch adds its CTAs' arrivals to `arrivals_base`
+  // grid barrier; each launch adds its CTAs' arrivals to `arrivals_base`
   unsigned long long *d_arrivals = nullptr;
   uint64_t arrivals_base = 0;
+  // and each row's candidate count as published in its launch ([ndm]:
+  // launch epoch << 24 | count; zero before the first launch)
+  unsigned long long *d_published = nullptr;
   int32_t coop = 0;  // the device supports cooperative launches
 
   int64_t launches = 0;
@@ -240,12 +243,12 @@ int launch_tiled_detect_f32(dd_plan *p, const void *out, int64_t nsamp_out, floa
 // One-launch dd_run for small float beams that the staged float kernel does
 // not take: the plain-load kernel's sums and per-tile partials, the row
 // statistics, counts and candidates of launch_tiled_detect_f32, in one
-// cooperative launch with two grid barriers (bounded waits).  The results
-// equal those of launch_dedisperse_direct + launch_tiled_detect_f32 bit for
-// bit.  The kernel writes the candidate total to the plan's pinned
-// h_total[0] (and d_total[0]) once every CTA got past both barriers; a wait
-// that ran out records the plan's status word and leaves h_total[0] as the
-// host set it.
+// cooperative launch with a grid barrier and a look-back over the rows'
+// published counts (bounded waits).  The results equal those of
+// launch_dedisperse_direct + launch_tiled_detect_f32 bit for bit.  The
+// kernel writes the candidate total to the plan's pinned h_total[0] (and
+// d_total[0]) once every row worker is done; a wait that ran out records the
+// plan's status word and leaves h_total[0] as the host set it.
 constexpr int64_t kSmallMaxOutputs = int64_t(1) << 22;  // ndm * nsamp_out
 bool small_supported(const dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out);
 int launch_run_small(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp_out, void *out,

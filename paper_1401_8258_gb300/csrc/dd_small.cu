@@ -9,19 +9,20 @@
 //   1. every CTA takes (time tile, DM group) items: the plain-load kernel's
 //      channel sums (with 4 trials per thread on aligned rows from input
 //      windows staged in shared memory, staged_sums; else direct_sums) and
-//      its tile's partial statistics (tile_partials), then arrives at grid
-//      barrier 1;
-//   2. the first min(grid, ndm) CTAs (the row workers) wait for barrier 1
+//      its tile's partial statistics (tile_partials), then arrives at the
+//      grid barrier;
+//   2. the first min(grid, ndm) CTAs (the row workers) wait at the barrier
 //      and take rows d: the row's mean, rms and threshold (row_stats_f32)
-//      and its per-tile candidate counts (count_row_tiles), then arrive at
-//      barrier 2 (the other CTAs are done).  When every worker has one row
-//      that fits, the row's outputs and tile partials are first copied into
+//      and its per-tile candidate counts (count_row_tiles), then publish
+//      the row's count (the other CTAs are done).  When every worker has
+//      one row that fits, the row's outputs and tile partials are copied into
 //      shared memory (the partials in their own copy group, so the
 //      statistics start while the row lands), phases 2 and 3 read them from
 //      there, and the snr divisions of the row's first candidate tile are
-//      issued before the barrier, whose wait hides their latency;
-//   3. the row workers wait for barrier 2 and write each row's candidates at
-//      the sum of the earlier rows' counts (write_row_tiles); the CTA of the
+//      issued before the look-back, whose wait hides their latency;
+//   3. each row worker sums the earlier rows' published counts (a decoupled
+//      look-back in place of a second grid barrier) and writes its row's
+//      candidates at that position (write_row_tiles); the CTA of the
 //      last row stores the total in device memory, and the last row worker
 //      to finish copies it to the plan's pinned host word, which the host
 //      polls (so dd_run returns without waiting for the launch to retire).
@@ -29,14 +30,16 @@
 // launch_tiled_detect_f32 (the same device functions), so outputs,
 // statistics and candidates equal that path's bit for bit.
 //
-// Grid barriers: a 64-bit arrivals counter that only grows; launch k waits
-// for base_k + (arrivals of its barrier), base_k being the arrivals of all
-// earlier launches (kept by the host).  Every wait is bounded (globaltimer):
-// a CTA whose wait runs out records the status word and returns, the CTAs
-// waiting on it then run out too, the total is never stored, and the host
-// resets the counter.  With the plan's fault injection on, barrier 1 waits
-// for one arrival more than the grid makes, so its waits run out.  The data
-// other CTAs wrote before a barrier are read through L2 (ld.global.cg).
+// The grid barrier: a 64-bit arrivals counter that only grows; launch k
+// waits for base_k + grid arrivals, base_k being the arrivals of all earlier
+// launches (kept by the host); the row counts are published tagged with
+// epoch base_k + 1.  Every wait is bounded (globaltimer): a CTA whose wait
+// runs out records the status word and returns, the CTAs waiting on it then
+// run out too, the total is never stored, and the host resets the counter
+// and the published counts.  With the plan's fault injection on, the barrier
+// waits for one arrival more than the grid makes, so its waits run out.  The
+// data other CTAs wrote before the barrier are read through L2
+// (ld.global.cg).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -73,9 +76,10 @@ struct SmallArgs {
   int32_t *status;         // sticky status word
   unsigned long long *arrivals;
   unsigned long long base;  // arrivals of earlier launches
+  unsigned long long *published;  // [ndm] epoch << 24 | row count (epoch = base + 1)
   uint64_t timeout_ns;
   int32_t ntiles, ngroups, nworkers;
-  int32_t extra_wait;  // fault injection: barrier 1 waits for this many arrivals more
+  int32_t extra_wait;  // fault injection: the barrier waits for this many arrivals more
   int32_t row_smem;    // one row per worker, copied to shared memory for phases 2 and 3
 };
 
@@ -115,6 +119,57 @@ __device__ __forceinline__ bool grid_wait(const SmallArgs &a, unsigned long long
   }
   __syncthreads();
   return s_ok != 0;
+}
+
+// Row d's candidate count, published for this launch (thread 0, once the
+// count is final): tagged with the launch's epoch, base + 1 (a count fits
+// 24 bits: rows have at most kSmallMaxOutputs samples).
+__device__ __forceinline__ void publish_count(const SmallArgs &a, int d, int64_t count) {
+  const unsigned long long word = ((a.base + 1) << 24) | static_cast<unsigned long long>(count);
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(a.published + d), "l"(word) : "memory");
+}
+
+// Sum of the counts of rows 0 .. d-1 as published in this launch (decoupled
+// look-back: each thread polls some rows with acquire loads until their
+// words carry this launch's epoch, bounded); false if a wait ran out (the
+// status word is then set).  Whole CTA; every thread gets the sum.
+__device__ __forceinline__ bool rows_before_published(const SmallArgs &a, int d, int64_t *before) {
+  __shared__ long long s_part[kDirectThreads / 32];
+  __shared__ int s_fail;
+  const unsigned long long epoch = (a.base + 1) & ((1ull << 40) - 1);
+  if (threadIdx.x == 0) s_fail = 0;
+  __syncthreads();
+  long long sum = 0;
+  bool ok = true;
+  for (int r = threadIdx.x; r < d && ok; r += kDirectThreads) {
+    unsigned long long v = ld_acquire(a.published + r);
+    if ((v >> 24) != epoch) {
+      const uint64_t t0 = dddev::global_timer();
+      while (((v = ld_acquire(a.published + r)) >> 24) != epoch) {
+        if (dddev::global_timer() - t0 > a.timeout_ns) {
+          ok = false;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    if (ok) sum += static_cast<long long>(v & 0xffffffull);
+  }
+  if (!ok) {
+    s_fail = 1;
+    atomicExch(a.status, 1);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = sum;
+  __syncthreads();
+  long long total = 0;
+#pragma unroll
+  for (int w = 0; w < kDirectThreads / 32; ++w) total += s_part[w];
+  *before = total;
+  const bool failed = s_fail != 0;
+  __syncthreads();  // s_part / s_fail free for a later call
+  return !failed;
 }
 
 // Phase 1 of the 4-trial variant on 16-byte aligned rows, with the input
@@ -330,8 +385,10 @@ dd_run_small(const __grid_constant__ SmallArgs a) {
     const auto reaches = [&](int tt) { return s_ts[tt].w >= st.fthr; };
     count_row_tiles<float, kDirectThreads, decltype(reaches), RowLd, kRowList>(
         s_row, n, ntiles, st, reaches, s_tc, a.rowcount + d, rl);
+    // publish the row's count (thread 0 wrote it)
+    if (threadIdx.x == 0) publish_count(a, d, a.rowcount[d]);
     // the snr of this thread's candidate in the row's first tile with any:
-    // its FP64 division runs while the CTA waits at barrier 2
+    // its FP64 division runs while the CTA waits for the earlier rows' counts
     __syncthreads();  // s_tc complete
     int pre_tile = -1;
     float pre_snr = 0.f;
@@ -345,11 +402,10 @@ dd_run_small(const __grid_constant__ SmallArgs a) {
       if (t < n && is_candidate(s_row[t], st))
         pre_snr = static_cast<float>(snr_of(static_cast<double>(s_row[t]), st.mean, st.sigma));
     }
-    grid_arrive(a.arrivals);
-    if (!grid_wait(a, a.base + gridDim.x + a.nworkers)) return;
-    // phase 3: the row's candidates
-    const int64_t before = rows_before(a.rowcount, d, rl);
-    const int64_t mine = rl(a.rowcount + d);
+    // phase 3: the row's candidates, after the earlier rows' counts
+    int64_t before = 0;
+    if (!rows_before_published(a, d, &before)) return;
+    const int64_t mine = a.rowcount[d];  // this CTA's write
     if (d == a.ndm - 1 && threadIdx.x == 0) *a.total = before + mine;
     if (mine > 0 && before < a.capacity)  // uniform across the CTA
       write_row_tiles<float, kDirectThreads, RowLd, kRowList>(s_row, n, ntiles, st, s_tc, before,
@@ -366,13 +422,13 @@ dd_run_small(const __grid_constant__ SmallArgs a) {
       count_row_tiles<float, kDirectThreads, decltype(reaches), L2Ld, kL2List>(
           a.out + static_cast<int64_t>(d) * n, n, ntiles, st, reaches,
           a.tilecount + static_cast<int64_t>(d) * ntiles, a.rowcount + d, ld);
+      if (threadIdx.x == 0) publish_count(a, d, a.rowcount[d]);  // thread 0 wrote it
     }
-    grid_arrive(a.arrivals);
-    if (!grid_wait(a, a.base + gridDim.x + a.nworkers)) return;
 
-    // phase 3: candidates, rows in order
+    // phase 3: candidates, rows in order, each after the earlier rows' counts
     for (int d = blockIdx.x; d < a.ndm; d += a.nworkers) {
-      const int64_t before = rows_before(a.rowcount, d, ld);
+      int64_t before = 0;
+      if (!rows_before_published(a, d, &before)) return;
       const int64_t mine = ld(a.rowcount + d);
       if (d == a.ndm - 1 && threadIdx.x == 0) *a.total = before + mine;
       if (mine == 0 || before >= a.capacity) continue;  // uniform across the CTA
@@ -389,7 +445,7 @@ dd_run_small(const __grid_constant__ SmallArgs a) {
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned long long before = atomicAdd(a.arrivals, 1ull);
-    if (before == a.base + gridDim.x + 2ull * a.nworkers - 1) {
+    if (before == a.base + gridDim.x + a.nworkers - 1) {
       __threadfence();
       const long long total = __ldcg(reinterpret_cast<const long long *>(a.total));
       *reinterpret_cast<volatile long long *>(a.host_total) = total;
@@ -490,6 +546,7 @@ int launch_run_small(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp
   a.status = p->d_error;
   a.arrivals = p->d_arrivals;
   a.base = p->arrivals_base;
+  a.published = p->d_published;
   a.timeout_ns = p->wait_timeout_ns;
   a.ntiles = static_cast<int32_t>(ntiles);
   a.ngroups = ngroups;
@@ -505,7 +562,7 @@ int launch_run_small(dd_plan *p, const void *block, int64_t pitch, int64_t nsamp
   *err = cudaLaunchCooperativeKernel(reinterpret_cast<const void *>(small_kernel(p->dtype, ndms)),
                                      dim3(grid), dim3(kDirectThreads), args, sh.dyn, stream);
   if (*err != cudaSuccess) return -1;
-  p->arrivals_base += static_cast<uint64_t>(grid) + 2 * static_cast<uint64_t>(a.nworkers);
+  p->arrivals_base += static_cast<uint64_t>(grid) + static_cast<uint64_t>(a.nworkers);
   return 1;
 }
 

@@ -4,7 +4,7 @@ float kernel does not take).
 
 The one-launch path runs the plain-load kernel's sums, the per-tile partial
 statistics, the row statistics (Sec. 3.5) and the candidate extraction
-(Sec. 3.6) in one cooperative launch with grid barriers.  It uses the same
+(Sec. 3.6) in one cooperative launch with a grid barrier.  It uses the same
 device arithmetic as the multi-launch plain-kernel path (dd_run on a plan
 held to the plain-load kernel, itself pinned to the oracle in
 test_gpu_run.py), so outputs, statistics and candidates must equal that
@@ -146,8 +146,9 @@ def test_one_launch_capacity_overflow_keeps_the_first_candidates():
 
 
 def test_one_launch_repeats_and_changing_sizes():
-    """The grid barriers' arrivals counter carries over launches of different
-    grid sizes on one plan: every run equals a fresh multi-launch run."""
+    """The grid barrier's arrivals counter and the launch epochs of the
+    published row counts carry over launches of different grid sizes on one
+    plan: every run equals a fresh multi-launch run."""
     wl = single_beam("f32")
     delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
     rng = np.random.default_rng(11)
@@ -164,7 +165,7 @@ def test_one_launch_repeats_and_changing_sizes():
 
 
 def test_one_launch_wait_that_runs_out_is_reported_and_recovered():
-    """With the plan's fault injection on, the first grid barrier waits for
+    """With the plan's fault injection on, the grid barrier waits for
     one arrival more than the grid makes: every row worker's wait runs out
     after the plan's bound, records the status and returns, no total is
     stored, and dd_run returns DD_ERR_DEVICE_TIMEOUT (no device fault, no
