@@ -216,8 +216,8 @@ __device__ __forceinline__ void build_selects(const uint32_t (&addr)[kGroup],
   }
 }
 
-// Build all pattern rows of an octet, one build unit (dd_octet.h) at a
-// time: lane l builds row word first+l of every row -- per pattern the sum,
+// Build the pattern rows of one build unit (dd_octet.h): lane l builds row
+// word first+l of each of the unit's rows -- per pattern the sum,
 // in channel order, of each channel's sample at its shift.  When every shift
 // of the unit is at most 2 (the common case) the candidate samples are loaded
 // once and selected per pattern; otherwise each pattern's samples are loaded

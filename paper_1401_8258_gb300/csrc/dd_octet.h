@@ -26,9 +26,10 @@
 //                              of the row word that holds output sample 0 of
 //                              the tile for that octet and trial
 //   units[kMaxUnits][16]: one warp-wide build step each -- items first ..
-//     first+31 (item = one row word) of every pattern row of one octet; lane
-//     l builds item first+l:
-//     [0] row-area word offset of item `first` of row 0 | items << 20
+//     first+31 (item = one row word) of the consecutive pattern rows p0 ..
+//     p0+patterns-1 of one octet (those that some trial of the tile reads
+//     there, or a half of them); lane l builds item first+l:
+//     [0] row-area word offset of item `first` of row p0 | items << 20
 //     [1] patterns | L << 8 | shift bound << 29 (every shift of the unit is
 //         at most 1: 1; at most 2: 2; otherwise 0)
 //     [2..5] element offsets, from the raw stage's zero area, of channels
@@ -36,8 +37,8 @@
 //         needs for item `first`; padding channels point into the zero area
 //     [6] per channel k, its largest shift over the patterns (bits 2k ..
 //         2k+1)
-//     [8..15] shift codes, two patterns per word (16 bits each): for
-//         channel k the 2-bit element shift 0..3 of the pattern's sample
+//     [8..15] shift codes of rows p0 .., two patterns per word (16 bits
+//         each): for channel k the 2-bit element shift 0..3 of the pattern's sample
 //         past that offset, at bits 2k .. 2k+1 (0 for the reference channel)
 //   warp_start[kBuildWarps + 1] (int16 pairs, after the units): building
 //     warp w builds units warp_start[w] .. warp_start[w+1]-1 (balanced on the

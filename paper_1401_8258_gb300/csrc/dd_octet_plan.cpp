@@ -56,6 +56,9 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
   struct Octet {
     int32_t row_off, L, npat;
     int32_t shift[kMaxPatterns][kGroup];  // e_k(p) - emin[k]
+    // row words of pattern p that some trial reads: lo[p] .. hi[p]-1 (the
+    // reference delays of its trials, less b, plus the tile's samples)
+    int32_t lo[kMaxPatterns], hi[kMaxPatterns];
     bool pad[kGroup];
     int32_t raw_off[kGroup];               // element offset of time b + emin[k] in its window
   };
@@ -120,8 +123,13 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
             O.raw_off[k] = 0;
           }
         }
-        for (int i = 0; i < nd_cta; ++i)
-          A[o * nd_cta + i] = row_words + pid[i] * O.L + delay(tile, cref, i) - b;
+        for (int p = 0; p < O.npat; ++p) O.lo[p] = INT32_MAX, O.hi[p] = INT32_MIN;
+        for (int i = 0; i < nd_cta; ++i) {
+          const int32_t w0 = delay(tile, cref, i) - b;
+          A[o * nd_cta + i] = row_words + pid[i] * O.L + w0;
+          O.lo[pid[i]] = std::min(O.lo[pid[i]], w0);
+          O.hi[pid[i]] = std::max(O.hi[pid[i]], w0 + kTimeTile);
+        }
         row_words += O.npat * O.L;
         octs.push_back(O);
       }
@@ -140,68 +148,128 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
   constexpr int kWarps = kBuildWarps;
   for (size_t rc = 0; rc < chunk_octets.size(); ++rc) {
     int32_t *rec = &t.recs[rc * t.rec_words];
-    std::vector<std::array<int32_t, kUnitWords>> list;
+    // A build unit covers 32 row words of the consecutive patterns p0 ..
+    // p1-1 of one octet: those whose trials read any of the 32 words (the
+    // patterns in between included).
+    auto make_unit = [&](const Octet &O, int o, int first, int p0, int p1) {
+      std::array<int32_t, kUnitWords> u{};
+      u[0] = (O.row_off + p0 * O.L + first) | (std::min(32, O.L - first) << 20);
+      // per channel, the largest shift over the unit's patterns; the unit's
+      // bound is the largest over its channels if at most 2 (the kernel then
+      // loads each channel's candidate samples once and selects per
+      // pattern), 0 otherwise (it loads each pattern's samples)
+      int32_t smax = 0;
+      uint32_t chan_bounds = 0;
+      for (int k = 0; k < kGroup; ++k) {
+        int32_t bk = 0;
+        for (int p = p0; p < p1; ++p)
+          if (!O.pad[k]) bk = std::max(bk, O.shift[p][k]);
+        chan_bounds |= static_cast<uint32_t>(bk) << (2 * k);
+        smax = std::max(smax, bk);
+      }
+      const int32_t bound = smax <= 2 ? std::max(smax, 1) : 0;
+      u[1] = (p1 - p0) | (O.L << 8) | (bound << 29);
+      for (int k = 0; k < kGroup; ++k) {
+        // element offsets from the start of the zero area; the raw buffer
+        // follows it (kZeroElems elements)
+        const uint32_t e =
+            O.pad[k] ? 0u
+                     : static_cast<uint32_t>(kZeroElems + (kGroup * o + k) * raw_stride +
+                                             O.raw_off[k] + first);
+        u[2 + k / 2] |= static_cast<int32_t>(e << (16 * (k & 1)));
+      }
+      // pattern-major shift codes: word kCodesWord + q/2 for the unit's q-th
+      // pattern, 16 bits per pattern (two per word), channel k's shift at
+      // bits 2k .. 2k+1 of its half; the reference channel's shift is 0
+      for (int p = p0; p < p1; ++p) {
+        uint32_t code = 0;
+        for (int k = 0; k < kGroup; ++k)
+          code |= static_cast<uint32_t>(O.pad[k] ? 0 : O.shift[p][k]) << (2 * k);
+        const int q = p - p0;
+        u[kCodesWord + q / 2] |= static_cast<int32_t>(code << (16 * (q & 1)));
+      }
+      u[kBoundsWord] = static_cast<int32_t>(chan_bounds);
+      return u;
+    };
+    // instructions of a unit, roughly: a fixed part (header, addresses),
+    // the candidate loads and per pattern and channel a select per
+    // candidate past the first and an add (or, on the general path, 8 loads
+    // and adds per pattern)
+    auto cost = [](const std::array<int32_t, kUnitWords> &u) {
+      const int32_t npat = u[1] & 0xff, bound = (u[1] >> 29) & 3;
+      return 24 + (bound ? 8 * (bound + 1) + npat * (7 * (1 + 2 * bound) + 3) : 4 + 24 * npat);
+    };
+    struct Cand {
+      std::array<int32_t, kUnitWords> whole, half[2];
+      int cost;
+      bool split;  // has two pattern halves (two or more patterns)
+    };
+    std::vector<Cand> cands;
     for (size_t o = 0; o < chunk_octets[rc].size(); ++o) {
       const Octet &O = chunk_octets[rc][o];
       for (int first = 0; first < O.L; first += 32) {
-        std::array<int32_t, kUnitWords> u{};
-        u[0] = (O.row_off + first) | (std::min(32, O.L - first) << 20);
-        // per channel, the largest shift over the patterns; the unit's bound
-        // is the largest over its channels if at most 2 (the kernel then
-        // loads each channel's candidate samples once and selects per
-        // pattern), 0 otherwise (it loads each pattern's samples)
-        int32_t smax = 0;
-        uint32_t chan_bounds = 0;
-        for (int k = 0; k < kGroup; ++k) {
-          int32_t b = 0;
-          for (int p = 0; p < O.npat; ++p)
-            if (!O.pad[k]) b = std::max(b, O.shift[p][k]);
-          chan_bounds |= static_cast<uint32_t>(b) << (2 * k);
-          smax = std::max(smax, b);
+        int p0 = O.npat, p1 = 0;
+        for (int p = 0; p < O.npat; ++p)
+          if (O.lo[p] < first + 32 && O.hi[p] > first) p0 = std::min(p0, p), p1 = p + 1;
+        if (p0 >= p1) continue;  // words past every trial's reach
+        Cand c;
+        c.whole = make_unit(O, static_cast<int>(o), first, p0, p1);
+        c.cost = cost(c.whole);
+        c.split = p1 - p0 >= 2;
+        if (c.split) {
+          const int pm = p0 + (p1 - p0) / 2;
+          c.half[0] = make_unit(O, static_cast<int>(o), first, p0, pm);
+          c.half[1] = make_unit(O, static_cast<int>(o), first, pm, p1);
         }
-        const int32_t bound = smax <= 2 ? std::max(smax, 1) : 0;
-        u[1] = O.npat | (O.L << 8) | (bound << 29);
-        for (int k = 0; k < kGroup; ++k) {
-          // element offsets from the start of the zero area; the raw buffer
-          // follows it (kZeroElems elements)
-          const uint32_t e =
-              O.pad[k] ? 0u
-                       : static_cast<uint32_t>(kZeroElems +
-                                               (kGroup * static_cast<int>(o) + k) * raw_stride +
-                                               O.raw_off[k] + first);
-          u[2 + k / 2] |= static_cast<int32_t>(e << (16 * (k & 1)));
-        }
-        // pattern-major shift codes: word kCodesWord + p/2, 16 bits per
-        // pattern (two patterns per word), channel k's shift at bits 2k ..
-        // 2k+1 of its half; the reference channel's shift is 0
-        for (int p = 0; p < O.npat; ++p) {
-          uint32_t code = 0;
-          for (int k = 0; k < kGroup; ++k)
-            code |= static_cast<uint32_t>(O.pad[k] ? 0 : O.shift[p][k]) << (2 * k);
-          u[kCodesWord + p / 2] |= static_cast<int32_t>(code << (16 * (p & 1)));
-        }
-        u[kBoundsWord] = static_cast<int32_t>(chan_bounds);
-        list.push_back(u);
+        cands.push_back(c);
       }
     }
-    if (static_cast<int>(list.size()) > kMaxUnits) return 1;
-    // balance: costliest unit first onto the least loaded warp
-    std::vector<int> order(list.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
-    // instructions of a unit, roughly: per pattern and channel a select per
-    // candidate past the first and an add, plus the candidate loads (or, on
-    // the general path, 8 loads and adds per pattern)
-    auto cost = [&](int i) {
-      const int32_t npat = list[i][1] & 0xff, bound = (list[i][1] >> 29) & 3;
-      return bound ? 8 * (bound + 1) + npat * (7 * (1 + 2 * bound) + 3) : 4 + 24 * npat;
-    };
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    // The building warps meet once per chunk, so the chunk takes as long as
+    // its busiest warp: costliest unit first onto the least loaded warp,
+    // with the 0 .. kMaxSplits costliest units split in two pattern halves
+    // (each half reloads its candidates), whichever count leaves the busiest
+    // warp least loaded.
+    std::stable_sort(cands.begin(), cands.end(),
+                     [](const Cand &x, const Cand &y) { return x.cost > y.cost; });
+    constexpr int kMaxSplits = 6;
+    std::vector<std::array<int32_t, kUnitWords>> list;
+    std::vector<int> order;
+    int best_span = INT32_MAX;
+    for (int nsplit = 0; nsplit <= kMaxSplits; ++nsplit) {
+      std::vector<std::array<int32_t, kUnitWords>> l;
+      for (size_t i = 0; i < cands.size(); ++i) {
+        if (static_cast<int>(i) < nsplit && cands[i].split) {
+          l.push_back(cands[i].half[0]);
+          l.push_back(cands[i].half[1]);
+        } else {
+          l.push_back(cands[i].whole);
+        }
+      }
+      if (static_cast<int>(l.size()) > kMaxUnits) break;
+      std::vector<int> ord(l.size());
+      for (size_t i = 0; i < ord.size(); ++i) ord[i] = static_cast<int>(i);
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](int x, int y) { return cost(l[x]) > cost(l[y]); });
+      std::vector<int> ld(kWarps, 0);
+      for (int i : ord) {
+        const int w = static_cast<int>(
+            std::min_element(ld.begin() + kFirstBuilder, ld.end()) - ld.begin());
+        ld[w] += cost(l[i]);
+      }
+      const int span = *std::max_element(ld.begin(), ld.end());
+      if (span < best_span) {
+        best_span = span;
+        list.swap(l);
+        order.swap(ord);
+      }
+    }
+    if (best_span == INT32_MAX) return 1;  // more units than a record holds
     std::vector<int> load(kWarps, 0);
     std::vector<std::vector<int>> per_warp(kWarps);
     for (int i : order) {
       const int w = static_cast<int>(
           std::min_element(load.begin() + kFirstBuilder, load.end()) - load.begin());
-      load[w] += cost(i);
+      load[w] += cost(list[i]);
       per_warp[w].push_back(i);
     }
     int32_t *units = rec + units_offset(nd_cta);
