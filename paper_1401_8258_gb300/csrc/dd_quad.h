@@ -27,15 +27,16 @@
 //                                area, of the row word that holds output
 //                                pair 0 of the tile for that quad and trial
 //   units[kMaxUnits][20]: one warp-wide build step each -- items first ..
-//     first+31 (item = 4 row words) of every pattern row of one quad; lane l
-//     builds item first+l of each row:
+//     first+31 (item = 4 row words) of the consecutive pattern rows p0 .. of
+//     one quad (those that some trial of the tile reads there, or a half of
+//     them); lane l builds item first+l of each row:
 //     [0] raw-buffer byte offsets of channels 0 | 1 << 16, [1] of 2 | 3 << 16:
 //         the aligned word holding the earliest sample any pattern of the
 //         quad needs for this item block (0xffff = padding channel, zeros);
-//     [2] row-area word offset of item `first` of row 0 | items << 20 |
+//     [2] row-area word offset of item `first` of row p0 | items << 20 |
 //         patterns << 26;
 //     [3] row length L in words | channel 0's byte selector << 16;
-//     [4 + 2p], [5 + 2p] for pattern p: byte selectors (prmt) of channels
+//     [4 + 2p], [5 + 2p] for the unit's p-th pattern: byte selectors (prmt) of channels
 //         1 | 2 << 16, and 3: for a byte shift s (0..4) of the pattern's
 //         first sample within the two loaded words, 0x3210 + 0x1111 s (the
 //         same shift serves the second half, kHalf bytes on).  Channel 0's

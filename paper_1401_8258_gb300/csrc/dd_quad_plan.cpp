@@ -59,6 +59,9 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     int32_t shift[kMaxPatterns][4];  // e_k(p) - emin[k]
     bool pad[4];
     int32_t raw_off[4];            // byte offset of time b + emin[k] in channel k's window
+    // row words of pattern p that some trial reads: lo[p] .. hi[p]-1 (the
+    // channel-0 delays of its trials, less b, plus the tile's pairs)
+    int32_t lo[kMaxPatterns], hi[kMaxPatterns];
   };
   // slack x (row origin b - x) for which every real channel's byte shifts
   // (b - x + emin) & 3 .. + spread stay within 0..4, i.e. inside two words
@@ -131,8 +134,13 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
             Q.raw_off[k] = 0;
           }
         }
-        for (int i = 0; i < nd_cta; ++i)
-          A[q * nd_cta + i] = row_words + pid[i] * Q.L + delay(tile, c0, i) - b;
+        for (int p = 0; p < Q.npat; ++p) Q.lo[p] = INT32_MAX, Q.hi[p] = INT32_MIN;
+        for (int i = 0; i < nd_cta; ++i) {
+          const int32_t w0 = delay(tile, c0, i) - b;
+          A[q * nd_cta + i] = row_words + pid[i] * Q.L + w0;
+          Q.lo[pid[i]] = std::min(Q.lo[pid[i]], w0);
+          Q.hi[pid[i]] = std::max(Q.hi[pid[i]], w0 + kHalf);
+        }
         row_words += Q.npat * Q.L;
         quads.push_back(Q);
       }
@@ -150,44 +158,106 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
   constexpr int kWarps = kBuildWarps;
   for (size_t rc = 0; rc < chunk_quads.size(); ++rc) {
     int32_t *rec = &t.recs[rc * t.rec_words];
-    std::vector<std::array<int32_t, kUnitWords>> list;
+    // A build unit covers items first .. first+31 (4 row words each) of the
+    // consecutive patterns p0 .. p1-1 of one quad: those whose trials read
+    // any of its words (the patterns in between included).
+    auto make_unit = [&](const Quad &Q, int q, int first, int p0, int p1) {
+      const int items = Q.L / 4;
+      uint32_t addr[4];
+      for (int k = 0; k < 4; ++k)
+        addr[k] = Q.pad[k] ? 0xffffu
+                           : static_cast<uint32_t>((4 * q + k) * raw_stride +
+                                                   (Q.raw_off[k] & ~3) + 4 * first);
+      std::array<int32_t, kUnitWords> u{};
+      u[0] = static_cast<int32_t>(addr[0] | (addr[1] << 16));
+      u[1] = static_cast<int32_t>(addr[2] | (addr[3] << 16));
+      u[2] = (Q.row_off + p0 * Q.L + 4 * first) | (std::min(32, items - first) << 20) |
+             ((p1 - p0) << 26);
+      // prmt selector of the 4 bytes starting s bytes into two words
+      auto sel = [&](int p, int k) {
+        return 0x3210u + 0x1111u * static_cast<uint32_t>((Q.raw_off[k] & 3) + Q.shift[p][k]);
+      };
+      u[3] = static_cast<int32_t>(static_cast<uint32_t>(Q.L) | (sel(0, 0) << 16));
+      for (int p = p0; p < p1; ++p) {
+        u[4 + 2 * (p - p0)] = static_cast<int32_t>(sel(p, 1) | (sel(p, 2) << 16));
+        u[5 + 2 * (p - p0)] = static_cast<int32_t>(sel(p, 3));
+      }
+      return u;
+    };
+    // cost of a unit ~ its loads + one row store per pattern
+    auto cost = [](const std::array<int32_t, kUnitWords> &u) {
+      return 2 + static_cast<int>(static_cast<uint32_t>(u[2]) >> 26);
+    };
+    struct Cand {
+      std::array<int32_t, kUnitWords> whole, half[2];
+      int cost;
+      bool split;  // has two pattern halves (two or more patterns)
+    };
+    std::vector<Cand> cands;
     for (size_t q = 0; q < chunk_quads[rc].size(); ++q) {
       const Quad &Q = chunk_quads[rc][q];
       const int items = Q.L / 4;
       for (int first = 0; first < items; first += 32) {
-        uint32_t addr[4];
-        for (int k = 0; k < 4; ++k)
-          addr[k] = Q.pad[k] ? 0xffffu
-                             : static_cast<uint32_t>((4 * static_cast<int>(q) + k) * raw_stride +
-                                                     (Q.raw_off[k] & ~3) + 4 * first);
-        std::array<int32_t, kUnitWords> u{};
-        u[0] = static_cast<int32_t>(addr[0] | (addr[1] << 16));
-        u[1] = static_cast<int32_t>(addr[2] | (addr[3] << 16));
-        u[2] = (Q.row_off + 4 * first) | (std::min(32, items - first) << 20) | (Q.npat << 26);
-        // prmt selector of the 4 bytes starting s bytes into two words
-        auto sel = [&](int p, int k) {
-          return 0x3210u + 0x1111u * static_cast<uint32_t>((Q.raw_off[k] & 3) + Q.shift[p][k]);
-        };
-        u[3] = static_cast<int32_t>(static_cast<uint32_t>(Q.L) | (sel(0, 0) << 16));
-        for (int p = 0; p < Q.npat; ++p) {
-          u[4 + 2 * p] = static_cast<int32_t>(sel(p, 1) | (sel(p, 2) << 16));
-          u[5 + 2 * p] = static_cast<int32_t>(sel(p, 3));
+        int p0 = Q.npat, p1 = 0;
+        for (int p = 0; p < Q.npat; ++p)
+          if (Q.lo[p] < 4 * (first + 32) && Q.hi[p] > 4 * first) p0 = std::min(p0, p), p1 = p + 1;
+        if (p0 >= p1) continue;  // words past every trial's reach
+        Cand c;
+        c.whole = make_unit(Q, static_cast<int>(q), first, p0, p1);
+        c.cost = cost(c.whole);
+        c.split = p1 - p0 >= 2;
+        if (c.split) {
+          const int pm = p0 + (p1 - p0) / 2;
+          c.half[0] = make_unit(Q, static_cast<int>(q), first, p0, pm);
+          c.half[1] = make_unit(Q, static_cast<int>(q), first, pm, p1);
         }
-        list.push_back(u);
+        cands.push_back(c);
       }
     }
-    if (static_cast<int>(list.size()) > kMaxUnits) return 1;
-    // balance: largest unit first onto the least loaded warp (cost ~ loads +
-    // one row store per pattern), then order the units by warp
-    std::vector<int> order(list.size());
-    for (size_t i = 0; i < order.size(); ++i) order[i] = static_cast<int>(i);
-    auto cost = [&](int i) { return 2 + (static_cast<uint32_t>(list[i][2]) >> 26); };
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    // The building warps meet once per chunk, so the chunk takes as long as
+    // its busiest warp: largest unit first onto the least loaded warp, with
+    // the 0 .. kMaxSplits largest units split in two pattern halves (each
+    // half reloads its words), whichever count leaves the busiest warp least
+    // loaded; then the units are ordered by warp.
+    std::stable_sort(cands.begin(), cands.end(),
+                     [](const Cand &x, const Cand &y) { return x.cost > y.cost; });
+    constexpr int kMaxSplits = 6;
+    std::vector<std::array<int32_t, kUnitWords>> list;
+    std::vector<int> order;
+    int best_span = INT32_MAX;
+    for (int nsplit = 0; nsplit <= kMaxSplits; ++nsplit) {
+      std::vector<std::array<int32_t, kUnitWords>> l;
+      for (size_t i = 0; i < cands.size(); ++i) {
+        if (static_cast<int>(i) < nsplit && cands[i].split) {
+          l.push_back(cands[i].half[0]);
+          l.push_back(cands[i].half[1]);
+        } else {
+          l.push_back(cands[i].whole);
+        }
+      }
+      if (static_cast<int>(l.size()) > kMaxUnits) break;
+      std::vector<int> ord(l.size());
+      for (size_t i = 0; i < ord.size(); ++i) ord[i] = static_cast<int>(i);
+      std::stable_sort(ord.begin(), ord.end(),
+                       [&](int x, int y) { return cost(l[x]) > cost(l[y]); });
+      std::vector<int> ld(kWarps, 0);
+      for (int i : ord) {
+        const int w = static_cast<int>(std::min_element(ld.begin(), ld.end()) - ld.begin());
+        ld[w] += cost(l[i]);
+      }
+      const int span = *std::max_element(ld.begin(), ld.end());
+      if (span < best_span) {
+        best_span = span;
+        list.swap(l);
+        order.swap(ord);
+      }
+    }
+    if (best_span == INT32_MAX) return 1;  // more units than a record holds
     std::vector<int> load(kWarps, 0);
     std::vector<std::vector<int>> per_warp(kWarps);
     for (int i : order) {
       const int w = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
-      load[w] += cost(i);
+      load[w] += cost(list[i]);
       per_warp[w].push_back(i);
     }
     int32_t *units = rec + units_offset(nd_cta);
