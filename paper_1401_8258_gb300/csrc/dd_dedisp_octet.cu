@@ -206,13 +206,25 @@ __device__ __forceinline__ void build_selects(const uint32_t (&addr)[kGroup],
     const R lo = ((code >> (2 * k)) & 1u) ? r1[k] : r0[k];
     return MAXB == 1 ? lo : (((code >> (2 * k)) & 2u) ? r2[k] : lo);
   };
-#pragma unroll 2
-  for (uint32_t p = 0; p < npat; ++p) {
-    const uint32_t code = codes[p >> 1] >> (16 * (p & 1));
+  // every code word read up front and the pattern loop unrolled, so that
+  // the code loads and the two patterns' selects need not wait in turn
+  const int4 c03 = reinterpret_cast<const int4 *>(codes)[0];
+  const int4 c47 = reinterpret_cast<const int4 *>(codes)[1];
+  const uint32_t cw[8] = {static_cast<uint32_t>(c03.x), static_cast<uint32_t>(c03.y),
+                          static_cast<uint32_t>(c03.z), static_cast<uint32_t>(c03.w),
+                          static_cast<uint32_t>(c47.x), static_cast<uint32_t>(c47.y),
+                          static_cast<uint32_t>(c47.z), static_cast<uint32_t>(c47.w)};
+  auto pattern = [&](uint32_t code, uint32_t a) {
     float v = E::widen(pick(code, 0));
 #pragma unroll
     for (int k = 1; k < kGroup; ++k) v = E::add(v, k == kRefChan ? r0[k] : pick(code, k));
-    stsf(dst + p * row_bytes, v);
+    stsf(a, v);
+  };
+#pragma unroll
+  for (uint32_t p = 0; p < kMaxPatterns; p += 2) {
+    if (p >= npat) break;
+    pattern(cw[p >> 1], dst + p * row_bytes);
+    if (p + 1 < npat) pattern(cw[p >> 1] >> 16, dst + (p + 1) * row_bytes);
   }
 }
 
