@@ -154,18 +154,23 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
     auto make_unit = [&](const Octet &O, int o, int first, int p0, int p1) {
       std::array<int32_t, kUnitWords> u{};
       u[0] = (O.row_off + p0 * O.L + first) | (std::min(32, O.L - first) << 20);
-      // per channel, the largest shift over the unit's patterns; the unit's
+      // per channel, the smallest shift over the unit's patterns (the unit's
+      // offsets and codes count from it) and the largest past it; the unit's
       // bound is the largest over its channels if at most 2 (the kernel then
       // loads each channel's candidate samples once and selects per
       // pattern), 0 otherwise (it loads each pattern's samples)
+      int32_t base[kGroup];
       int32_t smax = 0;
       uint32_t chan_bounds = 0;
       for (int k = 0; k < kGroup; ++k) {
-        int32_t bk = 0;
-        for (int p = p0; p < p1; ++p)
-          if (!O.pad[k]) bk = std::max(bk, O.shift[p][k]);
-        chan_bounds |= static_cast<uint32_t>(bk) << (2 * k);
-        smax = std::max(smax, bk);
+        int32_t lo = INT32_MAX, hi = 0;
+        for (int p = p0; p < p1; ++p) {
+          lo = std::min(lo, O.pad[k] ? 0 : O.shift[p][k]);
+          hi = std::max(hi, O.pad[k] ? 0 : O.shift[p][k]);
+        }
+        base[k] = lo;
+        chan_bounds |= static_cast<uint32_t>(hi - lo) << (2 * k);
+        smax = std::max(smax, hi - lo);
       }
       const int32_t bound = smax <= 2 ? std::max(smax, 1) : 0;
       u[1] = (p1 - p0) | (O.L << 8) | (bound << 29);
@@ -175,7 +180,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
         const uint32_t e =
             O.pad[k] ? 0u
                      : static_cast<uint32_t>(kZeroElems + (kGroup * o + k) * raw_stride +
-                                             O.raw_off[k] + first);
+                                             O.raw_off[k] + base[k] + first);
         u[2 + k / 2] |= static_cast<int32_t>(e << (16 * (k & 1)));
       }
       // pattern-major shift codes: word kCodesWord + q/2 for the unit's q-th
@@ -184,7 +189,7 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
       for (int p = p0; p < p1; ++p) {
         uint32_t code = 0;
         for (int k = 0; k < kGroup; ++k)
-          code |= static_cast<uint32_t>(O.pad[k] ? 0 : O.shift[p][k]) << (2 * k);
+          code |= static_cast<uint32_t>(O.pad[k] ? 0 : O.shift[p][k] - base[k]) << (2 * k);
         const int q = p - p0;
         u[kCodesWord + q / 2] |= static_cast<int32_t>(code << (16 * (q & 1)));
       }
@@ -212,16 +217,36 @@ int build_tables(const int32_t *delays, int32_t nchan, int32_t ndm, int nd_thr, 
         for (int p = 0; p < O.npat; ++p)
           if (O.lo[p] < first + 32 && O.hi[p] > first) p0 = std::min(p0, p), p1 = p + 1;
         if (p0 >= p1) continue;  // words past every trial's reach
-        Cand c;
-        c.whole = make_unit(O, static_cast<int>(o), first, p0, p1);
-        c.cost = cost(c.whole);
-        c.split = p1 - p0 >= 2;
-        if (c.split) {
-          const int pm = p0 + (p1 - p0) / 2;
-          c.half[0] = make_unit(O, static_cast<int>(o), first, p0, pm);
-          c.half[1] = make_unit(O, static_cast<int>(o), first, pm, p1);
+        auto add = [&](int a, int z) {
+          Cand c;
+          c.whole = make_unit(O, static_cast<int>(o), first, a, z);
+          c.cost = cost(c.whole);
+          c.split = z - a >= 2;
+          if (c.split) {
+            const int pm = a + (z - a) / 2;
+            c.half[0] = make_unit(O, static_cast<int>(o), first, a, pm);
+            c.half[1] = make_unit(O, static_cast<int>(o), first, pm, z);
+          }
+          cands.push_back(c);
+        };
+        // a unit whose channels span three shifts selects among three
+        // candidates per channel; where two units on either side of some
+        // pattern cost less in all, it is built as those two
+        const auto whole = make_unit(O, static_cast<int>(o), first, p0, p1);
+        int best = cost(whole), cut = -1;
+        if (((whole[1] >> 29) & 3) == 2) {
+          for (int q = p0 + 1; q < p1; ++q) {
+            const int c = cost(make_unit(O, static_cast<int>(o), first, p0, q)) +
+                          cost(make_unit(O, static_cast<int>(o), first, q, p1));
+            if (c < best) best = c, cut = q;
+          }
         }
-        cands.push_back(c);
+        if (cut < 0) {
+          add(p0, p1);
+        } else {
+          add(p0, cut);
+          add(cut, p1);
+        }
       }
     }
     // The building warps meet once per chunk, so the chunk takes as long as
