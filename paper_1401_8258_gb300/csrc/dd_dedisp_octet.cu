@@ -185,25 +185,26 @@ __device__ void issue_chunk(const Beam &a, int opc, int esize, int tile, int64_t
 // the selects below stay exact without a branch), then each pattern sums, in
 // channel order, each channel's candidate at the pattern's shift -- shift
 // bit 0 picks r1 over r0, bit 1 (MAXB 2) picks r2 -- two patterns at a time.
-// The reference channel's shift is 0 in every pattern: it adds r0.
+// The reference channel's shift is 0 in every pattern: it adds r0.  f16
+// candidates are widened to FP32 once, as they are loaded (exact); each
+// FP32 add of a widened sample rounds as the mixed f32 + f16 add does.
 template <typename T, int MAXB>
 __device__ __forceinline__ void build_selects(const uint32_t (&addr)[kGroup],
                                               const uint32_t *codes, uint32_t cb, uint32_t npat,
                                               uint32_t dst, uint32_t row_bytes) {
   using E = Elem<T>;
-  using R = typename E::raw;
   constexpr uint32_t es = sizeof(T);
-  R r0[kGroup], r1[kGroup], r2[kGroup];
+  float r0[kGroup], r1[kGroup], r2[kGroup];
 #pragma unroll
   for (int k = 0; k < kGroup; ++k) {
     const uint32_t bk = (cb >> (2 * k)) & 3u;
-    r0[k] = E::load(addr[k]);
+    r0[k] = E::widen(E::load(addr[k]));
     if (k == kRefChan) continue;
-    r1[k] = bk >= 1 ? E::load(addr[k] + es) : r0[k];
-    r2[k] = MAXB >= 2 && bk >= 2 ? E::load(addr[k] + 2 * es) : r1[k];
+    r1[k] = bk >= 1 ? E::widen(E::load(addr[k] + es)) : r0[k];
+    r2[k] = MAXB >= 2 && bk >= 2 ? E::widen(E::load(addr[k] + 2 * es)) : r1[k];
   }
-  auto pick = [&](uint32_t code, int k) -> R {
-    const R lo = ((code >> (2 * k)) & 1u) ? r1[k] : r0[k];
+  auto pick = [&](uint32_t code, int k) -> float {
+    const float lo = ((code >> (2 * k)) & 1u) ? r1[k] : r0[k];
     return MAXB == 1 ? lo : (((code >> (2 * k)) & 2u) ? r2[k] : lo);
   };
   // every code word read up front and the pattern loop unrolled, so that
@@ -215,9 +216,9 @@ __device__ __forceinline__ void build_selects(const uint32_t (&addr)[kGroup],
                           static_cast<uint32_t>(c47.x), static_cast<uint32_t>(c47.y),
                           static_cast<uint32_t>(c47.z), static_cast<uint32_t>(c47.w)};
   auto pattern = [&](uint32_t code, uint32_t a) {
-    float v = E::widen(pick(code, 0));
+    float v = pick(code, 0);
 #pragma unroll
-    for (int k = 1; k < kGroup; ++k) v = E::add(v, k == kRefChan ? r0[k] : pick(code, k));
+    for (int k = 1; k < kGroup; ++k) v = __fadd_rn(v, k == kRefChan ? r0[k] : pick(code, k));
     stsf(a, v);
   };
 #pragma unroll
