@@ -199,3 +199,32 @@ def test_octet_tables_refuse_geometries_with_too_many_patterns():
     delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
     assert octet_tables(delays, wl.nchan, wl.ndm, ND_THR, 4) is None
     assert octet_tables(delays, wl.nchan, wl.ndm, ND_THR // 2, 4) is None
+
+
+def test_lband_units_select_between_two_candidates_and_stay_balanced():
+    """The plan's unit choices on the L-band geometry (Sec. 2.1.1 delays):
+    every build unit counts its shifts from its own smallest one, so that
+    each channel selects between two candidates (bound 1), and the busiest
+    building warp of a chunk carries little more than an even share."""
+    wl = synth.workload("lband_f32")
+    delays, _ = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    tb = octet_tables(delays, wl.nchan, wl.ndm, ND_THR, 4)
+    nd = tb["nd_cta"]
+    units_off = REC_HEADER + MAX_OCTETS_PER_CHUNK * nd
+    starts_off = units_off + UNIT_WORDS * MAX_UNITS
+    total = busiest = 0
+    for t in range(tb["ntiles"]):
+        for c in range(tb["nchunks"]):
+            rec = tb["recs"][t, c]
+            n = int(rec[3])
+            units = (rec[units_off:units_off + UNIT_WORDS * n].astype(np.int64) & 0xFFFFFFFF)
+            units = units.reshape(-1, UNIT_WORDS)
+            assert np.all((units[:, 1] >> 29) & 3 == 1)
+            npat = units[:, 1] & 0xFF
+            starts = rec[starts_off:].view(np.uint16)[:NWARPS + 1].astype(int)
+            loads = [int(npat[starts[w]:starts[w + 1]].sum()) + 2 * (starts[w + 1] - starts[w])
+                     for w in range(1, NWARPS)]
+            total += sum(loads)
+            busiest += max(loads) * len(loads)
+    # pattern rows (plus a unit's fixed part) per warp: within 20% of even
+    assert total / busiest > 0.8
