@@ -4,10 +4,13 @@
 // The kernel adds eight channels per shared-memory word: for each group of
 // eight adjacent channels ("octet") and each DM trial of the CTA's tile it
 // reads a row whose word i holds the sum of the eight channels' samples that
-// the trial adds at output time i.  Within an octet the delays of channels
-// 1..7 relative to channel 0 take only a few distinct values over a tile of
-// trials (differences of two rounded delays, Sec. 2.1.1), so one row per
-// distinct relative pattern serves every trial of the tile that has it.
+// the trial adds at output time i.  Within an octet the delays of the
+// channels relative to its reference channel (the middle one, kRefChan) take
+// only a few distinct values over a tile of trials (differences of two
+// rounded delays, Sec. 2.1.1), so one row per distinct relative pattern
+// serves every trial of the tile that has it.  The rows are built by build
+// units of 32 row words (dd_octet.h), planned here: which patterns each unit
+// builds, the shifts it counts from, and which building warp takes it.
 //
 // Everything here is integer bookkeeping on the plan's delay table; no part
 // of the dedispersion sum happens on the host.
