@@ -228,3 +228,59 @@ def test_lband_units_select_between_two_candidates_and_stay_balanced():
             busiest += max(loads) * len(loads)
     # pattern rows (plus a unit's fixed part) per warp: within 20% of even
     assert total / busiest > 0.8
+
+
+def three_shift_splits(tb):
+    """Count the 32-word ranges of a pattern-row area that the plan built as
+    several units whose patterns together span three or more shifts of some
+    channel (each unit counts its shifts from its own smallest one, so the
+    span is taken over element offset + code)."""
+    nd = tb["nd_cta"]
+    units_off = REC_HEADER + MAX_OCTETS_PER_CHUNK * nd
+    n = 0
+    for t in range(tb["ntiles"]):
+        for c in range(tb["nchunks"]):
+            rec = tb["recs"][t, c].astype(np.int64) & 0xFFFFFFFF
+            units = rec[units_off:units_off + UNIT_WORDS * rec[3]].reshape(-1, UNIT_WORDS)
+            ranges = {}
+            for u in units:  # the reference channel's offset names the (octet, range)
+                ranges.setdefault(int(u[2 + REF_CHAN // 2]) >> (16 * (REF_CHAN & 1)) & 0xFFFF,
+                                  []).append(u)
+            for us in ranges.values():
+                if len(us) < 2:
+                    continue
+                span = 0
+                for k in range(GROUP):
+                    vals = [((int(u[2 + k // 2]) >> (16 * (k & 1))) & 0xFFFF)
+                            + ((int(u[CODES_WORD + p // 2]) >> (16 * (p & 1) + 2 * k)) & 3)
+                            for u in us for p in range(int(u[1]) & 0xFF)]
+                    span = max(span, max(vals) - min(vals))
+                n += span >= 2
+    return n
+
+
+@pytest.mark.parametrize("esize", [4, 2])
+def test_octet_kernel_model_with_three_shift_units_split(esize):
+    """Low in the L-band (256 channels from 1228.2 MHz down, DMs 38.4-51.1 in
+    steps of 0.1, Sec. 2.1.1 delays) some octets' channels take three shifts
+    over a unit's patterns; the plan builds those words as two units that
+    each select between two candidates.  The kernel model on such tables
+    must still equal the oracle exactly."""
+    base = synth.workload("lband_f32")
+    wl = synth.scaled(base, nchan=256, ndm=128)
+    wl.chan_width_mhz = base.chan_width_mhz
+    wl.f_top_mhz = 1228.2
+    wl.dms = 38.4 + 0.1 * np.arange(128)
+    delays, mx = oracle.delay_table(wl.nchan, wl.f_top_mhz, wl.chan_width_mhz, wl.t_samp_s, wl.dms)
+    tb = octet_tables(delays, wl.nchan, wl.ndm, ND_THR, esize)
+    assert tb is not None
+    assert three_shift_splits(tb) > 0
+    nsamp = mx + 700
+    align = 16 // esize
+    pitch = (nsamp + align - 1) // align * align
+    rng = np.random.default_rng(11)
+    block = rng.integers(-8, 9, size=(wl.nchan, pitch)).astype(np.float64)
+    block[:, nsamp:] = 1e6  # row padding must never reach a stored output
+    got = emulate(block, tb, wl.ndm, nsamp - mx)
+    ref = oracle.dedisperse(block[:, :nsamp].astype(np.float32), delays, nsamp_in=nsamp)
+    assert np.array_equal(got, ref)
